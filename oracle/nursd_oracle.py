@@ -1,0 +1,370 @@
+"""FP64 CPU oracle of the NURSD / SRSD operator (arXiv 2501.05244).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline legs of ``bench.py``; never by the CUDA product path.
+
+Everything is a direct, unfused statement of the paper's definitions in FP64:
+non-uniform and scaled transforms are explicit sums (matrix products of
+explicit exponentials), uniform length-M DFTs of the transfer function use
+``numpy.fft`` as a textbook routine.  Conventions (paper ambiguities resolved;
+each is listed in the design doc):
+
+* index sets I_L = {l : -L/2 <= l < L/2} (Sec. 4.1), row-major arrays with x
+  fastest: ``U[f][ky][kx]``, ``V[z][my][mx]``;
+* forward DFTs carry e^{-i}, the temporal transform e^{-i w t}, and the
+  back-propagation kernel is G = e^{+i k r} / r (Eq. 3), so a delay tau gives a
+  phasor e^{-i w tau} that G cancels at focus;
+* relay positions map to theta = 2 pi (x - c) / (M delta) in [-pi/2, pi/2]
+  (the rescaling to [-pi, pi) of Sec. 6);
+* the phasor-field band-pass uses sigma_w = w_c / 5 (Eq. PFPacket read in
+  frequency units) on F contiguous bins of a zero-padded length-t_pad DFT.
+
+Parity status: every public function below is pinned by ``tests/test_oracle_*``
+(closed forms, brute force, on-lattice equality with direct back-projection,
+adjoint identity, finite differences).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+C = 299_792_458.0  # speed of light [m/s]
+
+__all__ = [
+    "C", "index_set", "phasor_frequencies", "temporal_dft", "relay_theta",
+    "nudft_type1", "nudft_type1_modes", "nudft_type2", "rsd_kernel", "transfer_function",
+    "transfer_functions", "propagate", "propagate_depth", "nursd_forward", "fbp_direct",
+    "propagate_points", "idft_grid", "scaled_dft_matrix", "srsd_from_grid", "srsd_forward",
+    "adjoint_spectrum", "nursd_adjoint", "nursd_loss", "nursd_gradients",
+    "frustum_volume", "frustum_extra_volume", "data_compression", "lateral_resolution",
+]
+
+
+# --------------------------------------------------------------- notation ---
+
+def index_set(L: int) -> np.ndarray:
+    """I_L = {l in Z : -L/2 <= l < L/2} (Sec. 4.1, used for modes and lattices)."""
+    return np.arange(-(L // 2), L - L // 2)
+
+
+# ------------------------------------------------- a1: temporal transform ---
+
+def phasor_frequencies(lambda_c: float, dt: float, t_pad: int, F: int):
+    """Frequencies and Gaussian weights of the phasor-field kernel (Eq. PFPacket).
+
+    lambda_c = 2 pi c / w_c; the filter is exp(-(w - w_c)^2 / (2 sigma^2)) with
+    sigma = w_c / 5 (the paper's sigma = c / (5 lambda_c) read as a frequency).
+    The F frequencies are contiguous bins of a length-``t_pad`` DFT of step
+    ``dt``: w_f = 2 pi (f0 + f) / (t_pad dt), f0 = round(f_c t_pad dt) - F/2.
+    Returns (omega [F] rad/s, weight [F]).
+    """
+    f_c = C / lambda_c
+    f0 = math.floor(f_c * t_pad * dt + 0.5) - F // 2
+    omega = 2.0 * math.pi * (f0 + np.arange(F, dtype=np.float64)) / (t_pad * dt)
+    omega_c = 2.0 * math.pi * f_c
+    sigma = omega_c / 5.0
+    weight = np.exp(-((omega - omega_c) ** 2) / (2.0 * sigma * sigma))
+    return omega, weight
+
+
+def temporal_dft(h: np.ndarray, t0: float, dt: float, omega: np.ndarray, weight: np.ndarray) -> np.ndarray:
+    """Phasors P[l, f] = w_f * sum_n h_l[n] exp(-i w_f (t0 + n dt)) (Eq. PF_Response).
+
+    The virtual response is the histogram convolved with the phasor-field
+    illumination; in the frequency domain that is the histogram's DTFT at w_f
+    times the filter weight.  h: [L][T] -> complex128 [L][F].
+    """
+    h = np.asarray(h, dtype=np.float64)
+    t = t0 + dt * np.arange(h.shape[1], dtype=np.float64)
+    E = np.exp(-1j * t[:, None] * np.asarray(omega, dtype=np.float64)[None, :])
+    return (h @ E) * np.asarray(weight, dtype=np.float64)[None, :]
+
+
+# ------------------------------------------- a2-a5: non-uniform transforms ---
+
+def relay_theta(xy: np.ndarray, center, pitch: float, M: int) -> np.ndarray:
+    """Rescale metric positions to the NUFFT's periodic domain (Sec. 6).
+
+    theta = 2 pi (x - c) / (M delta): the M-point lattice c + delta*I_M maps to
+    2 pi I_M / M, so the aperture |x - c| <= N delta / 2 lands in [-pi/2, pi/2].
+    """
+    xy = np.asarray(xy, dtype=np.float64)
+    c = np.asarray(center, dtype=np.float64)
+    return 2.0 * math.pi * (xy - c[None, :]) / (M * pitch)
+
+
+def nudft_type1(P: np.ndarray, theta: np.ndarray, M: int) -> np.ndarray:
+    """Type-1 non-uniform DFT, U_f[ky, kx] = sum_l P[l, f] exp(-i (kx th_x + ky th_y)).
+
+    (Sec. 6, NUFFT-1) evaluated exactly for every mode (kx, ky) in I_M^2 by the
+    separable product of explicit exponentials.  P: [L][F] -> [F][M][M].
+    """
+    P = np.asarray(P, dtype=np.complex128)
+    k = index_set(M).astype(np.float64)
+    Ex = np.exp(-1j * k[:, None] * theta[None, :, 0])  # [kx][l]
+    Ey = np.exp(-1j * k[:, None] * theta[None, :, 1])  # [ky][l]
+    U = np.empty((P.shape[1], M, M), dtype=np.complex128)
+    for f in range(P.shape[1]):
+        U[f] = (Ey * P[None, :, f]) @ Ex.T
+    return U
+
+
+def nudft_type1_modes(P: np.ndarray, theta: np.ndarray, kxy: np.ndarray) -> np.ndarray:
+    """Type-1 sum at selected modes only: out[q, f] = sum_l P[l, f] e^{-i k_q . theta_l}."""
+    kxy = np.asarray(kxy, dtype=np.float64)
+    E = np.exp(-1j * (kxy[:, 0:1] * theta[None, :, 0] + kxy[:, 1:2] * theta[None, :, 1]))
+    return E @ np.asarray(P, dtype=np.complex128)
+
+
+def nudft_type2(U: np.ndarray, theta: np.ndarray) -> np.ndarray:
+    """Type-2 non-uniform DFT, u[l, f] = sum_k U_f[k] exp(+i (kx th_x + ky th_y)).
+
+    (Sec. 6, NUFFT-2: the adjoint of type 1.)  U: [F][M][M] -> [L][F].
+    """
+    U = np.asarray(U, dtype=np.complex128)
+    M = U.shape[-1]
+    k = index_set(M).astype(np.float64)
+    Ex = np.exp(1j * k[:, None] * theta[None, :, 0])  # [kx][l]
+    Ey = np.exp(1j * k[:, None] * theta[None, :, 1])  # [ky][l]
+    out = np.empty((theta.shape[0], U.shape[0]), dtype=np.complex128)
+    for f in range(U.shape[0]):
+        out[:, f] = np.sum(Ey * (U[f] @ Ex), axis=0)
+    return out
+
+
+# ------------------------------------------- a6-a7: RSD propagation -------
+
+def rsd_kernel(M: int, pitch: float, z: float, k: float) -> np.ndarray:
+    """Propagation kernel G(j delta, z) = exp(+i k r) / r on the M x M offsets j in I_M^2.
+
+    r = sqrt((jx delta)^2 + (jy delta)^2 + z^2) (Eq. RSD_conv); [jy][jx].
+    """
+    j = index_set(M).astype(np.float64) * pitch
+    r = np.sqrt(j[None, :] ** 2 + j[:, None] ** 2 + z * z)
+    return np.exp(1j * k * r) / r
+
+
+def transfer_function(g: np.ndarray) -> np.ndarray:
+    """Transfer function Ghat[k] = sum_{j in I_M^2} g[j] exp(-2 pi i k.j / M), k in I_M^2.
+
+    (The FFT{G} factor of Eq. 4.)  A plain length-M 2D DFT with centred index
+    sets, computed with numpy.fft (shifts move index 0 to the front and back).
+    """
+    return np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(g)))
+
+
+def transfer_functions(depths, omega, M: int, pitch: float) -> np.ndarray:
+    """Ghat[z][f][ky][kx] for every depth plane and frequency (k_f = w_f / c)."""
+    depths = np.asarray(depths, dtype=np.float64)
+    omega = np.asarray(omega, dtype=np.float64)
+    out = np.empty((len(depths), len(omega), M, M), dtype=np.complex128)
+    for iz, z in enumerate(depths):
+        for f, w in enumerate(omega):
+            out[iz, f] = transfer_function(rsd_kernel(M, pitch, z, w / C))
+    return out
+
+
+def _idft_crop_matrix(M: int, N: int) -> np.ndarray:
+    """B[m, k] = exp(+2 pi i k m / M) for m in I_N, k in I_M."""
+    m = index_set(N).astype(np.float64)
+    k = index_set(M).astype(np.float64)
+    return np.exp(2j * math.pi * np.outer(m, k) / M)
+
+
+def propagate(U: np.ndarray, Ghat: np.ndarray, N: int) -> np.ndarray:
+    """NURSD-1 propagation and coherent frequency sum (Eq. NURSD1 with Eq. PF_RSD_Defn).
+
+    Y_z(k) = sum_f U_f(k) Ghat_{z,f}(k), then the inverse DFT evaluated on the
+    N x N output lattice: V_z[m] = M^-2 sum_k Y_z(k) exp(+2 pi i k.m / M),
+    m in I_N^2.  U: [F][M][M], Ghat: [Z][F][M][M] -> V: [Z][N][N].
+    """
+    M = U.shape[-1]
+    Y = np.einsum("fyx,zfyx->zyx", U, Ghat)
+    B = _idft_crop_matrix(M, N)
+    return np.stack([B @ Y[z] @ B.T for z in range(Y.shape[0])]) / (M * M)
+
+
+def propagate_depth(U: np.ndarray, z: float, omega, pitch: float, N: int) -> np.ndarray:
+    """One depth plane of :func:`propagate`, building Ghat_{z,f} one frequency at a time."""
+    M = U.shape[-1]
+    Y = np.zeros((M, M), dtype=np.complex128)
+    for f, w in enumerate(np.asarray(omega, dtype=np.float64)):
+        Y += U[f] * transfer_function(rsd_kernel(M, pitch, z, w / C))
+    B = _idft_crop_matrix(M, N)
+    return (B @ Y @ B.T) / (M * M)
+
+
+def nursd_forward(P, xy, center, pitch: float, N: int, depths, omega) -> np.ndarray:
+    """The full NURSD-1 operator: phasors at irregular relay samples -> V[z][my][mx].
+
+    IFFT{ NUFFT-1{P_F(x_l)} . FFT{G(m delta, n delta, z_v)} } (Eq. NURSD1), with the
+    frequency integral of Eq. PF_RSD_Defn taken as the sum over the F phasor bins.
+    """
+    M = 2 * N
+    U = nudft_type1(P, relay_theta(xy, center, pitch, M), M)
+    return propagate(U, transfer_functions(depths, omega, M, pitch), N)
+
+
+def fbp_direct(P, xy, omega, vox, chunk: int = 256) -> np.ndarray:
+    """Direct back-projection (the gold-standard sum of Eq. PF_RSD_Defn's inner integral).
+
+    V(x_v) = sum_f sum_l P[l, f] exp(+i k_f |x_v - x_l|) / |x_v - x_l|, relay
+    samples on z = 0, voxels ``vox`` [V][3] (x, y, z).  Costs L*F per voxel.
+    """
+    P = np.asarray(P, dtype=np.complex128)
+    xy = np.asarray(xy, dtype=np.float64)
+    vox = np.asarray(vox, dtype=np.float64)
+    k = np.asarray(omega, dtype=np.float64) / C
+    out = np.zeros(vox.shape[0], dtype=np.complex128)
+    for v0 in range(0, vox.shape[0], chunk):
+        v = vox[v0:v0 + chunk]
+        r = np.sqrt((v[:, None, 0] - xy[None, :, 0]) ** 2 + (v[:, None, 1] - xy[None, :, 1]) ** 2
+                    + v[:, None, 2] ** 2)
+        acc = np.zeros(v.shape[0], dtype=np.complex128)
+        for f in range(P.shape[1]):
+            acc += (np.exp(1j * k[f] * r) / r) @ P[:, f]
+        out[v0:v0 + chunk] = acc
+    return out
+
+
+# ------------------------------------------- a8: arbitrary output voxels ---
+
+def propagate_points(U: np.ndarray, Ghat: np.ndarray, theta_v: np.ndarray) -> np.ndarray:
+    """NURSD-2/3 output: V_z(x_v) = M^-2 sum_k Y_z(k) exp(+i k . theta_v) (Eqs. NURSD2-3).
+
+    Y_z as in :func:`propagate`; ``theta_v`` [Z][K][2] are the per-plane voxel
+    positions rescaled like relay samples.  Returns [Z][K].
+    """
+    M = U.shape[-1]
+    Y = np.einsum("fyx,zfyx->zyx", U, Ghat)
+    out = np.empty(theta_v.shape[:2], dtype=np.complex128)
+    for z in range(Y.shape[0]):
+        out[z] = nudft_type2(Y[z][None], theta_v[z])[:, 0] / (M * M)
+    return out
+
+
+# ------------------------------------------------------------ a9: SRSD ----
+
+def idft_grid(U: np.ndarray) -> np.ndarray:
+    """Gridded field u_f[n] = M^-2 sum_k U_f(k) exp(+2 pi i k.n / M), n in I_M^2.
+
+    The regular-grid input that SRSD requires (Supp. C, SRSD on non-uniform
+    acquisition: interpolate to a regular grid, here by the NUFFT-1 spectrum).
+    """
+    M = U.shape[-1]
+    B = _idft_crop_matrix(M, M)
+    return np.stack([B @ U[f] @ B.T for f in range(U.shape[0])]) / (M * M)
+
+
+def scaled_dft_matrix(M: int, s: float) -> np.ndarray:
+    """A[kappa, n] = exp(-2 pi i kappa n / (M s)), kappa, n in I_M (scaled DFT, Sec. 4.1).
+
+    s = 1/alpha is the ratio of output to input pitch.
+    """
+    k = index_set(M).astype(np.float64)
+    return np.exp(-2j * math.pi * np.outer(k, k) / (M * s))
+
+
+def srsd_from_grid(u: np.ndarray, depths, scales, omega, pitch: float, N: int) -> np.ndarray:
+    """Scaled RSD on a gridded input (Eq. SRSD_conv / SFFT, fusion form of Supp. C).
+
+    Per depth z with scale s_z: Phat_{z,f} = A_z u_f A_z^T (the scaled DFT as an
+    explicit sum), Y_z = sum_f Phat_{z,f} . Ghat^(s)_{z,f} where Ghat^(s) is the
+    DFT of G sampled at pitch s_z delta, and V_z = M^-2 IDFT crop to I_N^2.
+    The output of plane z lies on the lattice c + s_z delta I_N^2.
+    u: [F][M][M] -> [Z][N][N].
+    """
+    M = u.shape[-1]
+    B = _idft_crop_matrix(M, N)
+    out = np.empty((len(depths), N, N), dtype=np.complex128)
+    for iz, (z, s) in enumerate(zip(np.asarray(depths, float), np.asarray(scales, float))):
+        A = scaled_dft_matrix(M, s)
+        Y = np.zeros((M, M), dtype=np.complex128)
+        for f, w in enumerate(np.asarray(omega, dtype=np.float64)):
+            Y += (A @ u[f] @ A.T) * transfer_function(rsd_kernel(M, s * pitch, z, w / C))
+        out[iz] = (B @ Y @ B.T) / (M * M)
+    return out
+
+
+def srsd_forward(P, xy, center, pitch: float, N: int, depths, scales, omega) -> np.ndarray:
+    """SRSD of non-uniform relay samples: NUFFT-1 spectrum -> grid -> scaled RSD."""
+    M = 2 * N
+    U = nudft_type1(P, relay_theta(xy, center, pitch, M), M)
+    return srsd_from_grid(idft_grid(U), depths, scales, omega, pitch, N)
+
+
+# --------------------------------------------------- a10-a11: adjoint, grad ---
+
+def adjoint_spectrum(V: np.ndarray, Ghat: np.ndarray) -> np.ndarray:
+    """R_f(k) = sum_z conj(Ghat_{z,f}(k)) Vt_z(k), Vt_z(k) = M^-2 sum_{m in I_N^2} V_z[m] e^{-2 pi i k.m/M}.
+
+    The adjoint of :func:`propagate` up to the type-1 step.  V: [Z][N][N] -> [F][M][M].
+    """
+    M = Ghat.shape[-1]
+    D = np.conj(_idft_crop_matrix(M, V.shape[-1])).T  # [k][m] = e^{-2 pi i k m / M}
+    Vt = np.stack([D @ V[z] @ D.T for z in range(V.shape[0])]) / (M * M)
+    return np.einsum("zfyx,zyx->fyx", np.conj(Ghat), Vt)
+
+
+def nursd_adjoint(V, xy, center, pitch: float, N: int, depths, omega) -> np.ndarray:
+    """A^H of :func:`nursd_forward`: V [Z][N][N] -> phasors [L][F].
+
+    Type-2 is the adjoint of type-1 (Sec. 6), so A^H = NUFFT-2 o conj(Ghat) o DFT.
+    """
+    M = 2 * N
+    Ghat = transfer_functions(depths, omega, M, pitch)
+    return nudft_type2(adjoint_spectrum(np.asarray(V, np.complex128), Ghat),
+                       relay_theta(xy, center, pitch, M))
+
+
+def nursd_loss(P, xy, center, pitch, N, depths, omega, V_target) -> float:
+    """L = || A(P, x) - V_target ||^2 over the complex output volume."""
+    r = nursd_forward(P, xy, center, pitch, N, depths, omega) - V_target
+    return float(np.sum(np.abs(r) ** 2))
+
+
+def nursd_gradients(P, xy, center, pitch, N, depths, omega, V_target):
+    """Analytic gradients of :func:`nursd_loss`.
+
+    grad_P = 2 A^H (A P - V_t) (the conjugate-Wirtinger convention for a real
+    loss of complex inputs); with R_f the adjoint spectrum of the residual,
+    dL/dx_l = (2 pi / (M delta)) * 2 Re sum_f P[l,f] conj(sum_k i kx R_f(k) e^{i k.theta_l})
+    and likewise for y.  Returns (grad_P [L][F] complex, grad_xy [L][2] real).
+    """
+    M = 2 * N
+    P = np.asarray(P, dtype=np.complex128)
+    theta = relay_theta(xy, center, pitch, M)
+    Ghat = transfer_functions(depths, omega, M, pitch)
+    resid = propagate(nudft_type1(P, theta, M), Ghat, N) - V_target
+    R = adjoint_spectrum(resid, Ghat)
+    grad_P = 2.0 * nudft_type2(R, theta)
+    k = index_set(M).astype(np.float64)
+    dx = nudft_type2(1j * k[None, None, :] * R, theta)
+    dy = nudft_type2(1j * k[None, :, None] * R, theta)
+    scale = 2.0 * math.pi / (M * pitch)
+    gx = 2.0 * np.real(np.sum(P * np.conj(dx), axis=1)) * scale
+    gy = 2.0 * np.real(np.sum(P * np.conj(dy), axis=1)) * scale
+    return grad_P, np.stack([gx, gy], axis=1)
+
+
+# ------------------------------------------------ plan-level closed forms ---
+
+def frustum_volume(x_in: float, alpha: float, z: float) -> float:
+    """V_F = z x_in^2 + z^2 x_in / alpha + z^3 / (3 alpha^2) (Sec. 4.2, Supp. A.2)."""
+    return z * x_in ** 2 + z ** 2 * x_in / alpha + z ** 3 / (3.0 * alpha ** 2)
+
+
+def frustum_extra_volume(alpha: float, z: float) -> float:
+    """Delta V = V_F - V_C = (1/alpha + 1/(3 alpha^2)) z^3 with x_in = z (Eq. Vol_Frustum)."""
+    return (1.0 / alpha + 1.0 / (3.0 * alpha ** 2)) * z ** 3
+
+
+def data_compression(N: int, T: int, D: int, F: int) -> float:
+    """N^2 T / ((N/D)^2 * 2F): histograms vs subsampled complex phasors (Sec. 7.2, data savings)."""
+    return (N * N * T) / ((N / D) ** 2 * 2.0 * F)
+
+
+def lateral_resolution(lambda_c: float, z: float, D: float) -> float:
+    """Delta x = 1.22 lambda_c z / D (Eq. Focusing_Res)."""
+    return 1.22 * lambda_c * z / D

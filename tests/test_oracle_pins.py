@@ -1,0 +1,436 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Nothing here re-types an oracle formula to compare it with itself: each check
+uses brute-force loops, a closed form, a textbook library routine (scipy
+convolution, numpy FFT), a physical special case (exact focus of a point
+source, on-lattice equality with direct back-projection), an identity
+(adjointness, finite differences) or a value printed in the paper.
+"""
+import cmath
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy.signal import convolve2d
+
+import oracle as O
+from workloads import (geometry_c1, relay_lattice, relay_uniform, random_phasors, workload_c1)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+rng = np.random.default_rng(1234)
+
+
+def _golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    return vals
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+# ------------------------------------------------------------------ a1 -----
+
+def test_frequency_band_matches_workload_statement():
+    # 16 bins of a 256-point DFT at 16 ps span 3.906 GHz around f_c = c / 6 cm.
+    om, w = O.phasor_frequencies(0.06, 16e-12, 256, 16)
+    f = om / (2 * math.pi)
+    assert np.allclose(np.diff(f), 1.0 / (256 * 16e-12), rtol=1e-12)
+    assert abs(f[-1] - f[0] + (f[1] - f[0]) - 3.90625e9) < 1.0
+    fc = 299_792_458.0 / 0.06
+    assert abs(0.5 * (f[7] + f[8]) - fc) <= (f[1] - f[0])
+
+
+def test_frequency_weight_fwhm_is_that_of_sigma_fc_over_5():
+    # Sample the filter finely and measure its full width at half maximum; a
+    # Gaussian with sigma = f_c / 5 has FWHM = 2 sqrt(2 ln 2) f_c / 5.
+    om, w = O.phasor_frequencies(0.06, 1e-12, 2 ** 20, 20000)
+    f = om / (2 * math.pi)
+    above = f[w >= 0.5]
+    fwhm = above[-1] - above[0]
+    fc = 299_792_458.0 / 0.06
+    assert abs(fwhm - 2 * math.sqrt(2 * math.log(2)) * fc / 5) < 2 * (f[1] - f[0])
+    assert abs(f[np.argmax(w)] - fc) <= (f[1] - f[0])
+
+
+def test_temporal_dft_brute_force_small():
+    L, T, F = 3, 7, 4
+    h = rng.standard_normal((L, T))
+    om = rng.uniform(1e10, 4e10, F)
+    wt = rng.uniform(0.2, 1.0, F)
+    t0, dt = 1.3e-9, 7e-12
+    got = O.temporal_dft(h, t0, dt, om, wt)
+    for l in range(L):
+        for f in range(F):
+            s = 0j
+            for n in range(T):
+                s += h[l, n] * cmath.exp(-1j * om[f] * (t0 + n * dt))
+            assert abs(got[l, f] - wt[f] * s) < 1e-12 * (1 + abs(s))
+
+
+def test_temporal_dft_of_a_gaussian_pulse_matches_its_fourier_transform():
+    # A well-sampled Gaussian pulse centred at tau has DTFT ~ (sqrt(2 pi) s / dt) e^{-w^2 s^2/2} e^{-i w tau}
+    # (Poisson summation; aliasing is below 1e-30 for dt << s).  Pins the sign and the time origin.
+    dt, T, t0 = 4e-12, 1024, 2.0e-9
+    s = 65e-12 / (2 * math.sqrt(2 * math.log(2)))
+    tau = t0 + 400.3 * dt
+    t = t0 + dt * np.arange(T)
+    h = np.exp(-((t - tau) ** 2) / (2 * s * s))[None, :]
+    om, w = O.phasor_frequencies(0.06, dt, 8192, 64)
+    got = O.temporal_dft(h, t0, dt, om, np.ones_like(om))[0]
+    want = math.sqrt(2 * math.pi) * s / dt * np.exp(-(om ** 2) * s * s / 2) * np.exp(-1j * om * tau)
+    assert rel(got, want) < 1e-10
+
+
+# -------------------------------------------------------------- a2-a5 ------
+
+def test_type1_brute_force_tiny():
+    L, M, F = 4, 6, 2
+    th = rng.uniform(-math.pi, math.pi, (L, 2))
+    P = rng.standard_normal((L, F)) + 1j * rng.standard_normal((L, F))
+    U = O.nudft_type1(P, th, M)
+    for f in range(F):
+        for iy, ky in enumerate(range(-M // 2, M // 2)):
+            for ix, kx in enumerate(range(-M // 2, M // 2)):
+                s = sum(P[l, f] * cmath.exp(-1j * (kx * th[l, 0] + ky * th[l, 1])) for l in range(L))
+                assert abs(U[f, iy, ix] - s) < 1e-12
+
+
+def test_type1_on_lattice_is_the_fft_of_the_gridded_samples():
+    M, F = 16, 3
+    n = rng.choice(M * M, 40, replace=False)
+    ny, nx = n // M - M // 2, n % M - M // 2
+    th = 2 * math.pi * np.stack([nx, ny], axis=1) / M
+    P = rng.standard_normal((40, F)) + 1j * rng.standard_normal((40, F))
+    U = O.nudft_type1(P, th, M)
+    for f in range(F):
+        grid = np.zeros((M, M), complex)
+        grid[ny + M // 2, nx + M // 2] = P[:, f]
+        want = np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(grid)))
+        assert rel(U[f], want) < 1e-13
+
+
+def test_type2_brute_force_and_adjointness():
+    L, M, F = 5, 4, 2
+    th = rng.uniform(-math.pi, math.pi, (L, 2))
+    U = rng.standard_normal((F, M, M)) + 1j * rng.standard_normal((F, M, M))
+    u = O.nudft_type2(U, th)
+    for l in range(L):
+        for f in range(F):
+            s = 0j
+            for iy, ky in enumerate(range(-M // 2, M // 2)):
+                for ix, kx in enumerate(range(-M // 2, M // 2)):
+                    s += U[f, iy, ix] * cmath.exp(1j * (kx * th[l, 0] + ky * th[l, 1]))
+            assert abs(u[l, f] - s) < 1e-12
+    P = rng.standard_normal((L, F)) + 1j * rng.standard_normal((L, F))
+    lhs = np.vdot(O.nudft_type1(P, th, M), U)
+    rhs = np.vdot(P, O.nudft_type2(U, th))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_type1_selected_modes_equal_full_sum():
+    L, M, F = 30, 8, 3
+    th = rng.uniform(-math.pi / 2, math.pi / 2, (L, 2))
+    P = rng.standard_normal((L, F)) + 1j * rng.standard_normal((L, F))
+    U = O.nudft_type1(P, th, M)
+    kxy = np.array([[-4, -4], [3, -1], [0, 0], [-2, 3]])
+    got = O.nudft_type1_modes(P, th, kxy)
+    want = np.stack([U[:, ky + M // 2, kx + M // 2] for kx, ky in kxy])
+    assert rel(got, want) < 1e-13
+
+
+# -------------------------------------------------------------- a6-a7 ------
+
+def test_transfer_function_brute_force():
+    M = 4
+    g = O.rsd_kernel(M, 0.1, 0.5, 40.0)
+    G = O.transfer_function(g)
+    for iy, ky in enumerate(range(-2, 2)):
+        for ix, kx in enumerate(range(-2, 2)):
+            s = 0j
+            for jy_i, jy in enumerate(range(-2, 2)):
+                for jx_i, jx in enumerate(range(-2, 2)):
+                    s += g[jy_i, jx_i] * cmath.exp(-2j * math.pi * (kx * jx + ky * jy) / M)
+            assert abs(G[iy, ix] - s) < 1e-12
+    # the kernel itself: e^{ikr}/r at offset (jx, jy) = (1, -2) cells
+    r = math.sqrt(0.1 ** 2 + 0.2 ** 2 + 0.25)
+    assert abs(g[0, 3] - cmath.exp(40j * r) / r) < 1e-14
+
+
+def _lattice_case(N=8, pitch=0.02, L=25, F=3, Z=2, seed=5):
+    r = np.random.default_rng(seed)
+    lat = relay_lattice(N, pitch, (0.1, -0.05), dtype=np.float64)
+    xy = lat[r.choice(N * N, L, replace=False)]
+    P = r.standard_normal((L, F)) + 1j * r.standard_normal((L, F))
+    om = np.array([2 * math.pi * 3e9, 2 * math.pi * 4e9, 2 * math.pi * 5.5e9])[:F]
+    depths = np.array([0.3, 0.55])[:Z]
+    return dict(P=P, xy=xy, center=(0.1, -0.05), pitch=pitch, N=N, depths=depths, omega=om)
+
+
+def pin_on_lattice_equals_direct_backprojection(case=None):
+    """max relative error of NURSD-1 vs direct back-projection for on-lattice samples."""
+    c = case or _lattice_case()
+    V = O.nursd_forward(c["P"], c["xy"], c["center"], c["pitch"], c["N"], c["depths"], c["omega"])
+    m = O.index_set(c["N"]) * c["pitch"]
+    X, Y = np.meshgrid(m + c["center"][0], m + c["center"][1], indexing="xy")
+    err = 0.0
+    for iz, z in enumerate(c["depths"]):
+        vox = np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], axis=1)
+        d = O.fbp_direct(c["P"], c["xy"], c["omega"], vox).reshape(X.shape)
+        err = max(err, rel(V[iz], d))
+    return err
+
+
+def test_on_lattice_nursd_equals_direct_backprojection():
+    # The paper's NURSD-1 = RSD equivalence on the full uniform grid (Sec. 8.1), and
+    # RSD on a lattice is exactly the direct back-projection sum (M = 2N: no wrap).
+    assert pin_on_lattice_equals_direct_backprojection() < 1e-12
+
+
+def test_on_lattice_nursd_equals_scipy_linear_convolution():
+    c = _lattice_case(N=6, L=20, F=2, Z=1)
+    N, M = c["N"], 2 * c["N"]
+    V = O.nursd_forward(c["P"], c["xy"], c["center"], c["pitch"], N, c["depths"], c["omega"])[0]
+    idx = np.rint((c["xy"] - np.array(c["center"])) / c["pitch"]).astype(int) + N // 2
+    want = np.zeros((N, N), complex)
+    for f in range(2):
+        grid = np.zeros((N, N), complex)
+        grid[idx[:, 1], idx[:, 0]] = c["P"][:, f]
+        g = O.rsd_kernel(M, c["pitch"], c["depths"][0], c["omega"][f] / O.C)  # offsets I_M
+        full = convolve2d(grid, g, mode="full")
+        # full[a] = sum_b grid[b] g[a - b]; array index b <-> n = b - N/2, c <-> j = c - N,
+        # so output lattice point m sits at a = m + 3N/2, i.e. the block [N, 2N).
+        want += full[N:2 * N, N:2 * N]
+    assert rel(V, want) < 1e-12
+
+
+def test_point_source_focus_closed_form():
+    # Analytic phasors of a point source, P = e^{-i k d}/d, focus exactly:
+    # V(x_s) = F * sum_l 1/d_l^2 (all phases cancel).
+    xy = relay_uniform(300, 0.5, seed=3).astype(np.float64)
+    om, _ = O.phasor_frequencies(0.06, 16e-12, 256, 16)
+    xs = np.array([0.07, -0.12, 0.8])
+    d = np.sqrt((xy[:, 0] - xs[0]) ** 2 + (xy[:, 1] - xs[1]) ** 2 + xs[2] ** 2)
+    P = np.exp(-1j * np.outer(d, om / O.C)) / d[:, None]
+    v = O.fbp_direct(P, xy, om, xs[None, :])[0]
+    assert abs(v - 16 * np.sum(1 / d ** 2)) < 1e-10 * abs(v)
+
+
+def test_reconstruction_of_simulated_scatterers_focuses_on_them():
+    # End to end through the temporal transform: the max-intensity projection of the
+    # tiny workload's three on-axis scatterers (0.6/0.9/1.2 m) peaks at the centre of
+    # the lateral lattice and within one depth plane of each scatterer.
+    wl = workload_c1()
+    g = wl.geom
+    om, wt = O.phasor_frequencies(g.lambda_c, g.dt, g.t_pad, g.F)
+    P = O.temporal_dft(wl.hist, g.t0, g.dt, om, wt)
+    V = O.nursd_forward(P, wl.xy, g.center, g.pitch, g.N, g.depths, om)
+    I = np.abs(V)
+    prof = I[:, g.N // 2 - 1:g.N // 2 + 1, g.N // 2 - 1:g.N // 2 + 1].max(axis=(1, 2))
+    dz = g.depths[1] - g.depths[0]
+    for zs in (0.6, 0.9, 1.2):
+        iz = int(np.argmin(np.abs(g.depths - zs)))
+        # the lateral maximum on the plane nearest the scatterer is on-axis (within one voxel)
+        my, mx = np.unravel_index(np.argmax(I[iz]), I[iz].shape)
+        assert abs(my - g.N // 2) <= 1 and abs(mx - g.N // 2) <= 1, (zs, my, mx)
+    # the depth profile has local maxima near each scatterer
+    peaks = [iz for iz in range(1, g.Z - 1) if prof[iz] >= prof[iz - 1] and prof[iz] >= prof[iz + 1]]
+    for zs in (0.6, 0.9, 1.2):
+        assert min(abs(g.depths[p] - zs) for p in peaks) <= 1.5 * dz
+
+
+def test_lateral_psf_width_is_of_the_diffraction_limit_order():
+    # Eq. Focusing_Res: Delta x = 1.22 lambda z / D.  Loose (factor 2) check of the
+    # half-maximum width of the reconstructed analytic point source.
+    N, pitch = 64, 1.0 / 64
+    xy = relay_lattice(N, pitch, dtype=np.float64)
+    om, wt = O.phasor_frequencies(0.06, 16e-12, 256, 16)
+    zs = 0.8
+    d = np.sqrt(xy[:, 0] ** 2 + xy[:, 1] ** 2 + zs ** 2)
+    P = np.exp(-1j * np.outer(d, om / O.C)) * wt[None, :]
+    m = O.index_set(N) * pitch
+    vox = np.stack([m, np.zeros(N), np.full(N, zs)], axis=1)
+    prof = np.abs(O.fbp_direct(P, xy, om, vox))
+    above = m[prof >= 0.5 * prof.max()]
+    fwhm = above[-1] - above[0] + pitch
+    dx = O.lateral_resolution(0.06, zs, 1.0)
+    assert 0.5 * dx < fwhm < 2.0 * dx
+
+
+# ------------------------------------------------------------------ a8 -----
+
+def test_type2_output_at_lattice_voxels_equals_lattice_crop():
+    c = _lattice_case()
+    N, M = c["N"], 2 * c["N"]
+    U = O.nudft_type1(c["P"], O.relay_theta(c["xy"], c["center"], c["pitch"], M), M)
+    Gh = O.transfer_functions(c["depths"], c["omega"], M, c["pitch"])
+    V = O.propagate(U, Gh, N)
+    lat = relay_lattice(N, c["pitch"], c["center"], dtype=np.float64)
+    th = O.relay_theta(lat, c["center"], c["pitch"], M)
+    Vp = O.propagate_points(U, Gh, np.broadcast_to(th, (len(c["depths"]),) + th.shape))
+    assert rel(Vp, V.reshape(len(c["depths"]), -1)) < 1e-12
+
+
+# ------------------------------------------------------------------ a9 -----
+
+def test_idft_grid_recovers_on_lattice_samples():
+    c = _lattice_case(N=6, L=12, F=2)
+    N, M = c["N"], 2 * c["N"]
+    U = O.nudft_type1(c["P"], O.relay_theta(c["xy"], c["center"], c["pitch"], M), M)
+    u = O.idft_grid(U)
+    idx = np.rint((c["xy"] - np.array(c["center"])) / c["pitch"]).astype(int) + M // 2
+    want = np.zeros((2, M, M), complex)
+    for f in range(2):
+        want[f, idx[:, 1], idx[:, 0]] = c["P"][:, f]
+    assert rel(u, want) < 1e-12
+
+
+def _bluestein(x, s):
+    """Independent chirp-z evaluation of sum_n x[n] e^{-2 pi i kappa n/(M s)} (n, kappa in I_M)."""
+    M = len(x)
+    n = np.arange(-M // 2, M // 2)
+    a = 1.0 / (M * s)
+    chirp = np.exp(-1j * math.pi * a * n ** 2)
+    d = np.arange(-(M - 1), M)
+    b = np.exp(1j * math.pi * a * d ** 2)
+    Lc = 1 << int(math.ceil(math.log2(3 * M)))
+    conv = np.fft.ifft(np.fft.fft(x * chirp, Lc) * np.fft.fft(b, Lc))
+    # out[kappa] = chirp(kappa) * sum_n (x chirp)[n] b[kappa - n]; index of (kappa - n) in b is kappa - n + M - 1
+    return chirp * conv[np.arange(M) + M - 1]
+
+
+def test_scaled_dft_matches_independent_chirp_z_and_reduces_to_dft():
+    M = 16
+    x = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    for s in (1.0, 1.37, 2.5, 4.096):
+        A = O.scaled_dft_matrix(M, s)
+        assert rel(A @ x, _bluestein(x, s)) < 1e-12
+    A1 = O.scaled_dft_matrix(M, 1.0)
+    assert rel(A1 @ x, np.fft.fftshift(np.fft.fft(np.fft.ifftshift(x)))) < 1e-13
+
+
+def test_srsd_with_unit_scale_equals_nursd():
+    c = _lattice_case()
+    N, M = c["N"], 2 * c["N"]
+    xy = c["xy"] + np.random.default_rng(9).uniform(-0.4, 0.4, c["xy"].shape) * c["pitch"]
+    V1 = O.nursd_forward(c["P"], xy, c["center"], c["pitch"], N, c["depths"], c["omega"])
+    Vs = O.srsd_forward(c["P"], xy, c["center"], c["pitch"], N, c["depths"], np.ones(len(c["depths"])), c["omega"])
+    assert rel(Vs, V1) < 1e-12
+
+
+def test_srsd_with_input_on_the_scaled_lattice_equals_direct_sum():
+    # If the gridded input is non-zero only at n that are multiples of s, the
+    # trigonometric interpolant of G on the scaled lattice is sampled at lattice
+    # points, so SRSD equals the direct sum  sum_n u[n] G(m s delta - n delta).
+    N, M, pitch, s, z = 8, 16, 0.02, 2.0, 0.4
+    om = np.array([2 * math.pi * 4e9, 2 * math.pi * 5e9])
+    r = np.random.default_rng(11)
+    u = np.zeros((2, M, M), complex)
+    pts = [(-4, 2), (0, 0), (2, -2), (-2, -4)]
+    for f in range(2):
+        for nx, ny in pts:
+            u[f, ny + M // 2, nx + M // 2] = r.standard_normal() + 1j * r.standard_normal()
+    V = O.srsd_from_grid(u, [z], [s], om, pitch, N)[0]
+    m = O.index_set(N)
+    want = np.zeros((N, N), complex)
+    for f in range(2):
+        k = om[f] / O.C
+        for nx, ny in pts:
+            dx = (m[None, :] * s - nx) * pitch
+            dy = (m[:, None] * s - ny) * pitch
+            rr = np.sqrt(dx ** 2 + dy ** 2 + z * z)
+            want += u[f, ny + M // 2, nx + M // 2] * np.exp(1j * k * rr) / rr
+    assert rel(V, want) < 1e-12
+
+
+# -------------------------------------------------------------- a10-a11 ----
+
+def test_adjoint_identity():
+    c = _lattice_case()
+    xy = c["xy"] + np.random.default_rng(2).uniform(-0.5, 0.5, c["xy"].shape) * c["pitch"]
+    P = c["P"]
+    r = np.random.default_rng(3)
+    V = r.standard_normal((2, c["N"], c["N"])) + 1j * r.standard_normal((2, c["N"], c["N"]))
+    AP = O.nursd_forward(P, xy, c["center"], c["pitch"], c["N"], c["depths"], c["omega"])
+    AhV = O.nursd_adjoint(V, xy, c["center"], c["pitch"], c["N"], c["depths"], c["omega"])
+    lhs, rhs = np.vdot(V, AP), np.vdot(AhV, P)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_gradients_match_central_differences():
+    c = _lattice_case(N=6, L=10, F=2, Z=2)
+    r = np.random.default_rng(4)
+    xy = c["xy"] + r.uniform(-0.5, 0.5, c["xy"].shape) * c["pitch"]
+    args = (c["center"], c["pitch"], c["N"], c["depths"], c["omega"])
+    Vt = r.standard_normal((2, 6, 6)) + 1j * r.standard_normal((2, 6, 6))
+    gP, gx = O.nursd_gradients(c["P"], xy, *args, Vt)
+    h = 1e-6
+    for (l, f) in [(0, 0), (3, 1), (9, 0)]:
+        for part, unit in (("re", 1.0), ("im", 1j)):
+            Pp = c["P"].copy(); Pp[l, f] += h * unit
+            Pm = c["P"].copy(); Pm[l, f] -= h * unit
+            fd = (O.nursd_loss(Pp, xy, *args, Vt) - O.nursd_loss(Pm, xy, *args, Vt)) / (2 * h)
+            an = gP[l, f].real if part == "re" else gP[l, f].imag
+            assert abs(fd - an) < 1e-6 * (1 + abs(an)), (l, f, part, fd, an)
+    hx = 1e-7
+    for l in (1, 5, 8):
+        for a in (0, 1):
+            xp = xy.copy(); xp[l, a] += hx
+            xm = xy.copy(); xm[l, a] -= hx
+            fd = (O.nursd_loss(c["P"], xp, *args, Vt) - O.nursd_loss(c["P"], xm, *args, Vt)) / (2 * hx)
+            assert abs(fd - gx[l, a]) < 1e-5 * (1 + abs(gx[l, a])), (l, a, fd, gx[l, a])
+
+
+# ------------------------------------------------------- printed values ----
+
+def test_frustum_worked_example_from_the_paper():
+    g = _golden("frustum_example.txt")
+    a, z = g["alpha"], g["z"]
+    VF = O.frustum_volume(z, a, z)
+    VC = z ** 3
+    dV = O.frustum_extra_volume(a, z)
+    assert abs(VC - g["V_C"]) < 0.5
+    assert abs(VF - g["V_F"]) < 0.5
+    assert abs(dV - g["dV"]) < 0.5
+    assert abs(100 * dV / VC - g["percent"]) < 0.5
+    assert abs((VF - VC) - dV) < 1e-9
+
+
+def test_data_savings_example_from_the_paper():
+    g = _golden("data_savings.txt")
+    T = 1000
+    F = int(T / g["T_over_F"])
+    assert abs(O.data_compression(250, T, int(g["D"]), F) - g["compression"]) < 1e-9
+
+
+# ----------------------------------------------- the pins catch mistakes ----
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    """Each plausible oracle mistake, planted on the CPU, breaks a pin."""
+    base = pin_on_lattice_equals_direct_backprojection()
+    assert base < 1e-12
+    orig_kernel, orig_prop, orig_theta = O.rsd_kernel, O.propagate, O.relay_theta
+    import oracle.nursd_oracle as mod
+
+    def flipped_kernel(M, pitch, z, k):  # wrong sign of the propagation phase
+        return orig_kernel(M, pitch, z, -k)
+
+    def no_norm(U, G, N):  # dropped M^-2
+        return orig_prop(U, G, N) * (U.shape[-1] ** 2)
+
+    def swapped_theta(xy, center, pitch, M):  # transposed operand (x <-> y)
+        return orig_theta(xy, center, pitch, M)[:, ::-1]
+
+    for name, bad in (("rsd_kernel", flipped_kernel), ("propagate", no_norm), ("relay_theta", swapped_theta)):
+        monkeypatch.setattr(mod, name, bad)
+        assert pin_on_lattice_equals_direct_backprojection() > 1e-3, name
+        monkeypatch.setattr(mod, name, {"rsd_kernel": orig_kernel, "propagate": orig_prop,
+                                        "relay_theta": orig_theta}[name])
+    assert pin_on_lattice_equals_direct_backprojection() < 1e-12
