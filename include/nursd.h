@@ -1,0 +1,180 @@
+/*
+ * libnursd -- GB300 (sm_103a) implementation of the non-uniform
+ * Rayleigh-Sommerfeld diffraction (NURSD) operator of "Optimized Sampling for
+ * Non-Line-of-Sight Imaging Using Modified Fast Fourier Transforms"
+ * (arXiv 2501.05244).
+ *
+ * The operator back-propagates a phasor field measured at an unordered list of
+ * relay-wall samples (x_l, y_l) (Sec. 6) into N x N voxel planes at depths z_v:
+ *
+ *   P[l][f]  = w_f sum_n h_l[n] exp(-i w_f (t0 + n dt))          Eq. PF_Response, PFPacket
+ *   U_f(k)   = sum_l P[l][f] exp(-i k . theta_l)                 NUFFT-1 (Sec. 6)
+ *   Y_z(k)   = sum_f U_f(k) Ghat_{z,f}(k)                        Eq. 4 product + frequency sum (Eq. 2)
+ *   V_z[m]   = M^-2 sum_k Y_z(k) exp(+2 pi i k.m / M), m in I_N^2  Eq. NURSD1
+ *
+ * with theta_l = 2 pi (x_l - c) / (M delta), M = 2N, k in I_M^2 =
+ * {-M/2..M/2-1}^2 and Ghat_{z,f} the M x M DFT of G = exp(+i k_f r)/r,
+ * r = sqrt(|j delta|^2 + z^2) (Eq. RSD_conv).
+ *
+ * Conventions for every entry point:
+ *  - All arrays are row-major with the LAST index contiguous; complex values
+ *    are interleaved (re, im) float pairs (nursd_c64).
+ *  - "d_" pointers are device pointers on the plan's device, "h_" pointers
+ *    are host pointers.  The caller owns every input and output buffer; the
+ *    plan owns its workspace and tables.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    stream-ordered and asynchronous: nothing synchronises the host except
+ *    nursd_plan_create (which builds the transfer-function table) and
+ *    nursd_sync_status.
+ *  - Errors are returned as nursd_status values; no exception crosses the
+ *    ABI.  Argument errors are detected on the host before any launch.
+ *  - One plan must not be used from two host threads at once; distinct
+ *    plans are independent.
+ */
+#ifndef NURSD_H
+#define NURSD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nursd_plan_s* nursd_plan_t;
+typedef struct {
+  float re, im;
+} nursd_c64;
+/* A cudaStream_t passed as an opaque pointer. */
+typedef void* nursd_stream_t;
+
+typedef enum {
+  NURSD_OK = 0,
+  NURSD_ERR_INVALID_ARG = 1,        /* bad pointer, size or plan state      */
+  NURSD_ERR_OOM = 2,                /* device allocation failed              */
+  NURSD_ERR_CUDA = 3,               /* a CUDA call or launch failed          */
+  NURSD_ERR_TIMEOUT = 4,            /* a bounded device wait gave up         */
+  NURSD_ERR_UNSUPPORTED = 5,        /* size or feature not built             */
+  NURSD_ERR_POINT_OUT_OF_RANGE = 6  /* a sample lies outside the aperture    */
+} nursd_status;
+
+/* Plan flags. */
+#define NURSD_OUTPUT_MAGNITUDE 0x1u /* nursd_forward* write |V| (float32) instead of V */
+
+/*
+ * Plan descriptor.  Geometry of Sec. 3.1 / Eq. 4: an N x N output lattice of
+ * pitch `pitch` (metres) centred at (center_x, center_y) on the relay plane
+ * z = 0, Z depth planes, F phasor frequencies.
+ */
+typedef struct {
+  int32_t N;                 /* output lattice size, power of two, 8..512          */
+  double pitch;              /* lattice pitch delta [m]                            */
+  double center_x, center_y; /* lattice centre c [m]                               */
+  int32_t Z;                 /* number of depth planes, 1..4096                    */
+  const double* h_depths;    /* [Z] plane depths z_v > 0 [m] (copied)              */
+  int32_t F;                 /* number of frequencies, 1..256                      */
+  const double* h_omega;     /* [F] angular frequencies w_f [rad/s] (copied)       */
+  const double* h_weight;    /* [F] filter weights w_f, or NULL for all ones       */
+  int32_t T;                 /* histogram bins (0 = no histogram input)            */
+  double t0, dt;             /* time of bin 0 and bin width [s]                    */
+  int32_t upsample;          /* NUFFT oversampling sigma (only 2 is built)         */
+  int32_t kernel_width;      /* ES kernel width w, 4..8 (6 gives ~1e-5)            */
+  uint32_t flags;            /* NURSD_* flags                                      */
+  int32_t max_points;        /* capacity for relay samples L                       */
+} nursd_desc;
+
+/* Text for a status code (static storage). */
+const char* nursd_status_string(int status);
+
+/*
+ * Phasor-field frequencies and weights of Eq. PFPacket (host only): F
+ * contiguous bins of a zero-padded length-t_pad DFT of step dt around
+ * f_c = c / lambda_c, w_f = 2 pi (f0 + f) / (t_pad dt) with
+ * f0 = round(f_c t_pad dt) - F/2, and Gaussian weights
+ * exp(-(w - w_c)^2 / (2 sigma^2)), sigma = w_c / 5.  Writes F values to each
+ * of h_omega and h_weight.  INVALID_ARG for non-positive inputs.
+ */
+int nursd_phasor_frequencies(double lambda_c, double dt, int32_t t_pad, int32_t F, double* h_omega,
+                             double* h_weight);
+
+/*
+ * Create a plan: validates the descriptor, allocates the workspace on the
+ * current device and builds, on `stream`, the transfer-function table
+ * Ghat_{z,f} of Eq. 4 (FP64 phase k r reduced mod 2 pi, FP32 DFT), stored once
+ * per class of the 8-fold symmetry Ghat(kx,ky) = Ghat(+-kx,+-ky) = Ghat(ky,kx).
+ * Synchronises `stream` before returning.  On error *out is NULL and nothing
+ * is leaked.
+ */
+int nursd_plan_create(const nursd_desc* desc, nursd_stream_t stream, nursd_plan_t* out);
+
+/* Free a plan and all its device memory (NULL is accepted). */
+int nursd_plan_destroy(nursd_plan_t plan);
+
+/* Device bytes held by the plan (tables + workspace), or -1 for NULL. */
+int64_t nursd_plan_bytes(nursd_plan_t plan);
+
+/* Sizes the plan derived: M = 2N, the fine-grid size, the number of
+ * symmetry classes of the transfer-function table. Any pointer may be NULL. */
+int nursd_plan_dims(nursd_plan_t plan, int32_t* M, int32_t* fine_n, int32_t* n_classes);
+
+/*
+ * Set the relay samples (Sec. 6: an unordered list rescaled to [-pi, pi)^2):
+ * d_xy is [L][2] float32 metres on the relay plane, L <= max_points.  Computes
+ * each sample's fine-grid footprint and ES weights and sorts the samples
+ * (stably) into spreading tiles.  The plan copies what it needs; the caller
+ * keeps d_xy.  A sample with |x - c| > N delta / 2 in either axis is an error:
+ * its weights are zeroed and NURSD_ERR_POINT_OUT_OF_RANGE is reported by the
+ * next nursd_sync_status.
+ */
+int nursd_set_points(nursd_plan_t plan, int32_t L, const float* d_xy, nursd_stream_t stream);
+
+/*
+ * Temporal transform (Eq. PF_Response with the filter of Eq. PFPacket):
+ * d_hist [L][T] float32 histograms -> d_phasor [L][F] complex64,
+ * P[l][f] = w_f sum_n h[l][n] exp(-i w_f (t0 + n dt)).  Needs T > 0 in the
+ * descriptor; L <= max_points.  Independent of nursd_set_points.
+ */
+int nursd_temporal_dft(nursd_plan_t plan, int32_t L, const float* d_hist, nursd_c64* d_phasor,
+                       nursd_stream_t stream);
+
+/*
+ * NUFFT type 1 of the current relay samples (Sec. 6: spread with the ES
+ * kernel, FFT, deconvolve): d_phasor [L][F] -> d_spectrum [M][M][F] with
+ * d_spectrum[ky+M/2][kx+M/2][f] ~= sum_l P[l][f] exp(-i (kx th_x + ky th_y)).
+ * Requires nursd_set_points.
+ */
+int nursd_nufft1(nursd_plan_t plan, const nursd_c64* d_phasor, nursd_c64* d_spectrum,
+                 nursd_stream_t stream);
+
+/*
+ * RSD propagation of a spectrum (Eq. NURSD1 after the NUFFT): frequency sum of
+ * U_f Ghat_{z,f} and inverse DFT cropped to the N x N lattice:
+ * d_spectrum [M][M][F] -> d_out [Z][N][N] (complex64, or float32 magnitude
+ * with NURSD_OUTPUT_MAGNITUDE).
+ */
+int nursd_propagate(nursd_plan_t plan, const nursd_c64* d_spectrum, void* d_out, nursd_stream_t stream);
+
+/*
+ * Full NURSD-1 forward from phasors: nursd_nufft1 then nursd_propagate.
+ * d_phasor [L][F] -> d_out [Z][N][N].  Requires nursd_set_points.
+ */
+int nursd_forward_phasor(nursd_plan_t plan, const nursd_c64* d_phasor, void* d_out,
+                         nursd_stream_t stream);
+
+/*
+ * Full NURSD-1 forward from histograms (temporal transform, NUFFT-1, RSD,
+ * frequency sum, inverse DFT): d_hist [L][T] float32 -> d_out [Z][N][N], L the
+ * count given to nursd_set_points.
+ */
+int nursd_forward(nursd_plan_t plan, const float* d_hist, void* d_out, nursd_stream_t stream);
+
+/*
+ * Synchronise `stream`, read and clear the plan's device error word.
+ * Returns NURSD_OK, NURSD_ERR_POINT_OUT_OF_RANGE or NURSD_ERR_TIMEOUT.
+ */
+int nursd_sync_status(nursd_plan_t plan, nursd_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NURSD_H */

@@ -1,0 +1,486 @@
+// C ABI of libnursd: plan lifecycle, argument validation and the launch
+// sequences of each entry point (see include/nursd.h for the contract).
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "nursd_internal.cuh"
+
+using namespace nursd;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr double kC = 299792458.0;  // speed of light [m/s]
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(long long v) {
+  int r = 0;
+  while ((1LL << r) < v) ++r;
+  return r;
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on P_n.
+void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int j = 1; j < n; ++j) {
+        const double p2 = ((2.0 * j + 1.0) * z * p1 - j * p0) / (j + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// ES kernel phi(z) = exp(beta (sqrt(1 - z^2) - 1)) on |z| < 1.
+double es_kernel(double z, double beta) { return std::fabs(z) < 1.0 ? std::exp(beta * (std::sqrt(1.0 - z * z) - 1.0)) : 0.0; }
+
+}  // namespace
+
+struct nursd_plan_s {
+  int device = 0;
+  // geometry
+  int N = 0, M = 0, nf = 0, Z = 0, F = 0, T = 0, w = 0, W = 0, tiles = 0, g0 = 0, ncls = 0, maxL = 0, L = -1;
+  double pitch = 0, cx = 0, cy = 0, t0 = 0, dt = 0;
+  float beta = 0;
+  uint32_t flags = 0;
+  std::vector<double> depths, omega, weight;
+  // tables
+  float2* twiddle = nullptr;
+  float* deconv = nullptr;
+  int2* cls = nullptr;
+  float2* Gc = nullptr;
+  float* Bt = nullptr;  // temporal twiddles [T][2F]
+  // points
+  int* bin_of = nullptr;
+  int2* i0_orig = nullptr;
+  float* w_orig = nullptr;
+  int* counts = nullptr;
+  int* bin_start = nullptr;
+  int* sorted_l = nullptr;
+  int2* i0_sorted = nullptr;
+  float* w_sorted = nullptr;
+  // workspace
+  float2* phasor = nullptr;
+  float2* fine = nullptr;
+  float2* R1 = nullptr;
+  float2* U = nullptr;
+  float2* Y = nullptr;
+  float2* T1 = nullptr;
+  int* status = nullptr;
+  int64_t bytes = 0;
+  std::vector<void*> allocs;
+
+  template <class T>
+  bool alloc(T*& p, size_t count) {
+    if (count == 0) count = 1;
+    void* q = nullptr;
+    if (cudaMalloc(&q, sizeof(T) * count) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    allocs.push_back(q);
+    bytes += (int64_t)(sizeof(T) * count);
+    p = static_cast<T*>(q);
+    return true;
+  }
+  ~nursd_plan_s() {
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
+namespace {
+
+int from_cuda(cudaError_t e) { return e == cudaSuccess ? NURSD_OK : NURSD_ERR_CUDA; }
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+PanelArgs panel_base(const nursd_plan_s* p) {
+  PanelArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.scale = 1.f;
+  a.CHI = 1;
+  a.hi_total = 1;
+  a.batch = 1;
+  a.twiddle = p->twiddle;
+  return a;
+}
+
+// Channel-last 1-D pass along an axis of length n_axis (window nin at offset in_off,
+// nout bins at out_off), for C contiguous channels and `batch` items.
+cudaError_t axis_pass(const nursd_plan_s* p, const float2* in, float2* out, int logn, bool inv, int C, int batch,
+                      long long in_sb, long long in_si, long long out_sb, long long out_si, int nin, int in_off,
+                      int nout, int out_off, const float* mul_o, const float* mul_b, float scale, cudaStream_t s) {
+  PanelArgs a = panel_base(p);
+  a.in = in;
+  a.out = out;
+  a.in_sb = in_sb;
+  a.in_si = in_si;
+  a.in_slo = 1;
+  a.out_sb = out_sb;
+  a.out_si = out_si;
+  a.out_slo = 1;
+  a.nin = nin;
+  a.in_off = in_off;
+  a.nout = nout;
+  a.out_off = out_off;
+  a.lo_total = C;
+  a.CLO = panel_width(logn);
+  a.batch = batch;
+  a.mul_o = mul_o;
+  a.mul_b = mul_b;
+  a.scale = scale;
+  return launch_panel_fft(logn, inv, a, s);
+}
+
+int build_transfer_table(nursd_plan_s* p, cudaStream_t s) {
+  const int M = p->M, F = p->F, Z = p->Z;
+  const long long per_depth = (long long)M * M * F;
+  int ZB = (int)std::max<long long>(1, (1LL << 28) / per_depth);  // ~2 GiB per buffer at most
+  ZB = std::min(ZB, Z);
+  float2 *g = nullptr, *tmp = nullptr;
+  double *dz = nullptr, *dk = nullptr;
+  int rc = NURSD_OK;
+  if (cudaMalloc(&g, sizeof(float2) * per_depth * ZB) != cudaSuccess ||
+      cudaMalloc(&tmp, sizeof(float2) * per_depth * ZB) != cudaSuccess || cudaMalloc(&dz, sizeof(double) * Z) != cudaSuccess ||
+      cudaMalloc(&dk, sizeof(double) * F) != cudaSuccess) {
+    cudaGetLastError();
+    rc = NURSD_ERR_OOM;
+  }
+  std::vector<double> k(F);
+  for (int f = 0; f < F; ++f) k[f] = p->omega[f] / kC;
+  if (rc == NURSD_OK) {
+    rc = from_cuda(cudaMemcpyAsync(dz, p->depths.data(), sizeof(double) * Z, cudaMemcpyHostToDevice, s));
+    if (rc == NURSD_OK) rc = from_cuda(cudaMemcpyAsync(dk, k.data(), sizeof(double) * F, cudaMemcpyHostToDevice, s));
+  }
+  const int logM = ilog2(M);
+  for (int z0 = 0; rc == NURSD_OK && z0 < Z; z0 += ZB) {
+    const int zb = std::min(ZB, Z - z0);
+    const int C = zb * F;
+    rc = from_cuda(launch_gtf_generate(g, M, p->pitch, dz + z0, zb, dk, F, s));
+    if (rc == NURSD_OK)  // along jx, for each row jy
+      rc = from_cuda(axis_pass(p, g, tmp, logM, false, C, M, (long long)M * C, C, (long long)M * C, C, M, -M / 2, M,
+                               -M / 2, nullptr, nullptr, 1.f, s));
+    if (rc == NURSD_OK)  // along jy, for each column kx
+      rc = from_cuda(axis_pass(p, tmp, g, logM, false, C, M, C, (long long)M * C, C, (long long)M * C, M, -M / 2, M,
+                               -M / 2, nullptr, nullptr, 1.f, s));
+    if (rc == NURSD_OK) rc = from_cuda(launch_gtf_compress(g, p->cls, p->ncls, M, F, zb, Z, z0, p->Gc, s));
+  }
+  if (rc == NURSD_OK) rc = from_cuda(cudaStreamSynchronize(s));
+  cudaFree(g);
+  cudaFree(tmp);
+  cudaFree(dz);
+  cudaFree(dk);
+  return rc;
+}
+
+int run_nufft1(nursd_plan_s* p, const float2* phasor, float2* spec, cudaStream_t s) {
+  const int F = p->F, M = p->M, W = p->W;
+  const int logf = ilog2(p->nf);
+  cudaError_t e = launch_spread(phasor, F, p->bin_start, p->sorted_l, p->i0_sorted, p->w_sorted, p->w, p->tiles, W,
+                                p->fine, s);
+  if (e == cudaSuccess)  // FFT along x of every window row, keep kx in I_M
+    e = axis_pass(p, p->fine, p->R1, logf, false, F, W, (long long)W * F, F, (long long)M * F, F, W, p->g0, M, -M / 2,
+                  nullptr, nullptr, 1.f, s);
+  if (e == cudaSuccess)  // FFT along y of every kx column, keep ky in I_M, divide by psi_hat(kx) psi_hat(ky)
+    e = axis_pass(p, p->R1, spec, logf, false, F, M, F, (long long)M * F, F, (long long)M * F, W, p->g0, M, -M / 2,
+                  p->deconv, p->deconv, 1.f, s);
+  return from_cuda(e);
+}
+
+int run_propagate(nursd_plan_s* p, const float2* spec, void* out, cudaStream_t s) {
+  const int M = p->M, N = p->N, Z = p->Z, F = p->F;
+  const int logM = ilog2(M);
+  cudaError_t e = launch_contract(spec, p->Gc, p->cls, p->ncls, M, F, Z, p->Y, s);
+  if (e == cudaSuccess)  // inverse FFT along kx, keep mx in I_N
+    e = axis_pass(p, p->Y, p->T1, logM, true, Z, M, (long long)M * Z, Z, (long long)N * Z, Z, M, -M / 2, N, -N / 2,
+                  nullptr, nullptr, 1.f, s);
+  if (e == cudaSuccess) {  // inverse FFT along ky for every (mx, z), keep my in I_N, write V[z][my][mx]
+    PanelArgs a = panel_base(p);
+    a.in = p->T1;
+    a.in_si = (long long)N * Z;
+    a.in_shi = Z;
+    a.in_slo = 1;
+    const bool mag = (p->flags & NURSD_OUTPUT_MAGNITUDE) != 0;
+    if (mag)
+      a.out_mag = static_cast<float*>(out);
+    else
+      a.out = static_cast<float2*>(out);
+    a.out_si = N;
+    a.out_shi = 1;
+    a.out_slo = (long long)N * N;
+    a.nin = M;
+    a.in_off = -M / 2;
+    a.nout = N;
+    a.out_off = -N / 2;
+    a.hi_total = N;
+    a.lo_total = Z;
+    const int cp = panel_width(logM);
+    a.CLO = Z >= 4 ? 4 : (Z >= 2 ? 2 : 1);
+    a.CHI = cp / a.CLO;
+    a.scale = 1.f / ((float)M * (float)M);
+    a.store_hi_fastest = 1;
+    e = launch_panel_fft(logM, true, a, s);
+  }
+  return from_cuda(e);
+}
+
+int check_plan(nursd_plan_t p) { return p ? NURSD_OK : NURSD_ERR_INVALID_ARG; }
+
+}  // namespace
+
+extern "C" {
+
+const char* nursd_status_string(int status) {
+  switch (status) {
+    case NURSD_OK: return "ok";
+    case NURSD_ERR_INVALID_ARG: return "invalid argument";
+    case NURSD_ERR_OOM: return "device out of memory";
+    case NURSD_ERR_CUDA: return "CUDA error";
+    case NURSD_ERR_TIMEOUT: return "bounded device wait timed out";
+    case NURSD_ERR_UNSUPPORTED: return "unsupported size or feature";
+    case NURSD_ERR_POINT_OUT_OF_RANGE: return "relay sample outside the aperture";
+    default: return "unknown status";
+  }
+}
+
+int nursd_phasor_frequencies(double lambda_c, double dt, int32_t t_pad, int32_t F, double* h_omega, double* h_weight) {
+  if (!(lambda_c > 0) || !(dt > 0) || t_pad <= 0 || F <= 0 || !h_omega || !h_weight) return NURSD_ERR_INVALID_ARG;
+  const double f_c = kC / lambda_c;
+  const double f0 = std::floor(f_c * t_pad * dt + 0.5) - (double)(F / 2);
+  const double w_c = 2.0 * kPi * f_c, sigma = w_c / 5.0;
+  for (int f = 0; f < F; ++f) {
+    const double w = 2.0 * kPi * (f0 + f) / ((double)t_pad * dt);
+    h_omega[f] = w;
+    h_weight[f] = std::exp(-(w - w_c) * (w - w_c) / (2.0 * sigma * sigma));
+  }
+  return NURSD_OK;
+}
+
+int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* out) {
+  if (!out) return NURSD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!d) return NURSD_ERR_INVALID_ARG;
+  if (!is_pow2(d->N) || d->N < 8 || d->N > 512) return NURSD_ERR_UNSUPPORTED;
+  if (!(d->pitch > 0) || !std::isfinite(d->pitch) || !std::isfinite(d->center_x) || !std::isfinite(d->center_y))
+    return NURSD_ERR_INVALID_ARG;
+  if (d->Z < 1 || d->Z > 4096 || !d->h_depths || d->F < 1 || d->F > 256 || !d->h_omega) return NURSD_ERR_INVALID_ARG;
+  for (int i = 0; i < d->Z; ++i)
+    if (!(d->h_depths[i] > 0) || !std::isfinite(d->h_depths[i])) return NURSD_ERR_INVALID_ARG;
+  for (int i = 0; i < d->F; ++i) {
+    if (!std::isfinite(d->h_omega[i]) || d->h_omega[i] < 0) return NURSD_ERR_INVALID_ARG;
+    if (d->h_weight && !std::isfinite(d->h_weight[i])) return NURSD_ERR_INVALID_ARG;
+  }
+  if (d->T < 0 || (d->T > 0 && (d->T % 8 != 0 || !(d->dt > 0) || !std::isfinite(d->t0)))) return NURSD_ERR_INVALID_ARG;
+  if (d->upsample != 2) return NURSD_ERR_UNSUPPORTED;
+  if (d->kernel_width < 4 || d->kernel_width > kMaxKernelWidth) return NURSD_ERR_UNSUPPORTED;
+  if (d->max_points < 0 || d->max_points > (1 << 26)) return NURSD_ERR_INVALID_ARG;
+  if ((d->flags & ~NURSD_OUTPUT_MAGNITUDE) != 0) return NURSD_ERR_UNSUPPORTED;
+
+  nursd_plan_s* p = new (std::nothrow) nursd_plan_s();
+  if (!p) return NURSD_ERR_OOM;
+  cudaGetDevice(&p->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  p->N = d->N;
+  p->M = 2 * d->N;
+  p->nf = d->upsample * p->M;
+  p->Z = d->Z;
+  p->F = d->F;
+  p->T = d->T;
+  p->w = d->kernel_width;
+  p->pitch = d->pitch;
+  p->cx = d->center_x;
+  p->cy = d->center_y;
+  p->t0 = d->t0;
+  p->dt = d->dt;
+  p->flags = d->flags;
+  p->maxL = d->max_points;
+  p->beta = (float)(2.30 * p->w);
+  p->depths.assign(d->h_depths, d->h_depths + d->Z);
+  p->omega.assign(d->h_omega, d->h_omega + d->F);
+  p->weight.assign(d->F, 1.0);
+  if (d->h_weight) p->weight.assign(d->h_weight, d->h_weight + d->F);
+  // fine-grid window: every footprint of a sample with |x - c| <= N delta / 2, plus a margin
+  const int need = d->upsample * p->N + p->w + 2;
+  p->W = (need + kTile - 1) / kTile * kTile;
+  p->tiles = p->W / kTile;
+  p->g0 = -p->W / 2;
+  if (p->W > p->nf) {
+    delete p;
+    return NURSD_ERR_UNSUPPORTED;
+  }
+  const int half = p->M / 2;
+  p->ncls = (half + 1) * (half + 2) / 2;
+
+  // ---- host tables
+  std::vector<float2> tw(1 << kTwiddleLog);
+  for (int q = 0; q < (1 << kTwiddleLog); ++q) {
+    const double a = -2.0 * kPi * q / (double)(1 << kTwiddleLog);
+    tw[q] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  std::vector<double> gx, gw;
+  gauss_legendre(256, gx, gw);
+  std::vector<float> dec(p->M);
+  for (int i = 0; i < p->M; ++i) {
+    const double k = i - half;
+    double s_ = 0.0;
+    for (size_t j = 0; j < gx.size(); ++j)
+      s_ += gw[j] * es_kernel(gx[j], p->beta) * std::cos(kPi * k * p->w * gx[j] / p->nf);
+    dec[i] = (float)(1.0 / (0.5 * p->w * s_));
+  }
+  std::vector<int2> cls;
+  cls.reserve(p->ncls);
+  for (int pp = 0; pp <= half; ++pp)
+    for (int qq = 0; qq <= pp; ++qq) cls.push_back(make_int2(pp, qq));
+  std::vector<float> Bt;
+  if (p->T > 0) {
+    Bt.resize((size_t)p->T * 2 * p->F);
+    for (int n = 0; n < p->T; ++n) {
+      const double t = p->t0 + n * p->dt;
+      for (int f = 0; f < p->F; ++f) {
+        const double ph = p->omega[f] * t;
+        Bt[(size_t)n * 2 * p->F + 2 * f] = (float)(p->weight[f] * std::cos(ph));
+        Bt[(size_t)n * 2 * p->F + 2 * f + 1] = (float)(-p->weight[f] * std::sin(ph));
+      }
+    }
+  }
+
+  // ---- device memory
+  const int maxL = std::max(1, p->maxL);
+  const int nbins = p->tiles * p->tiles;
+  const int nchunks = (maxL + 1023) / 1024;
+  bool ok = p->alloc(p->twiddle, tw.size()) && p->alloc(p->deconv, p->M) && p->alloc(p->cls, p->ncls) &&
+            p->alloc(p->Gc, (size_t)p->ncls * p->F * p->Z) && p->alloc(p->status, 1) &&
+            p->alloc(p->bin_of, maxL) && p->alloc(p->i0_orig, maxL) && p->alloc(p->w_orig, (size_t)maxL * 2 * p->w) &&
+            p->alloc(p->counts, (size_t)nbins * nchunks) && p->alloc(p->bin_start, nbins + 1) &&
+            p->alloc(p->sorted_l, maxL) && p->alloc(p->i0_sorted, maxL) &&
+            p->alloc(p->w_sorted, (size_t)maxL * 2 * p->w) && p->alloc(p->phasor, (size_t)maxL * p->F) &&
+            p->alloc(p->fine, (size_t)p->W * p->W * p->F) && p->alloc(p->R1, (size_t)p->W * p->M * p->F) &&
+            p->alloc(p->U, (size_t)p->M * p->M * p->F) && p->alloc(p->Y, (size_t)p->M * p->M * p->Z) &&
+            p->alloc(p->T1, (size_t)p->M * p->N * p->Z);
+  if (ok && p->T > 0) ok = p->alloc(p->Bt, Bt.size());
+  if (!ok) {
+    delete p;
+    return NURSD_ERR_OOM;
+  }
+  int rc = from_cuda(cudaMemcpyAsync(p->twiddle, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice, s));
+  if (rc == NURSD_OK)
+    rc = from_cuda(cudaMemcpyAsync(p->deconv, dec.data(), sizeof(float) * dec.size(), cudaMemcpyHostToDevice, s));
+  if (rc == NURSD_OK)
+    rc = from_cuda(cudaMemcpyAsync(p->cls, cls.data(), sizeof(int2) * cls.size(), cudaMemcpyHostToDevice, s));
+  if (rc == NURSD_OK && p->T > 0)
+    rc = from_cuda(cudaMemcpyAsync(p->Bt, Bt.data(), sizeof(float) * Bt.size(), cudaMemcpyHostToDevice, s));
+  if (rc == NURSD_OK) rc = from_cuda(cudaMemsetAsync(p->status, 0, sizeof(int), s));
+  if (rc == NURSD_OK) rc = from_cuda(cudaMemsetAsync(p->bin_start, 0, sizeof(int) * (nbins + 1), s));
+  if (rc == NURSD_OK) rc = build_transfer_table(p, s);
+  if (rc != NURSD_OK) {
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return NURSD_OK;
+}
+
+int nursd_plan_destroy(nursd_plan_t plan) {
+  delete plan;
+  return NURSD_OK;
+}
+
+int64_t nursd_plan_bytes(nursd_plan_t plan) { return plan ? plan->bytes : -1; }
+
+int nursd_plan_dims(nursd_plan_t plan, int32_t* M, int32_t* fine_n, int32_t* n_classes) {
+  if (!plan) return NURSD_ERR_INVALID_ARG;
+  if (M) *M = plan->M;
+  if (fine_n) *fine_n = plan->nf;
+  if (n_classes) *n_classes = plan->ncls;
+  return NURSD_OK;
+}
+
+int nursd_set_points(nursd_plan_t p, int32_t L, const float* d_xy, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || L < 0 || L > p->maxL || (L > 0 && (!d_xy || !aligned(d_xy, 8))))
+    return NURSD_ERR_INVALID_ARG;
+  PointsArgs a;
+  a.xy = d_xy;
+  a.L = L;
+  a.cx = p->cx;
+  a.cy = p->cy;
+  a.inv_fine_pitch = 2.0 / p->pitch;  // sigma / delta
+  a.half_extent = 0.5 * p->N * p->pitch;
+  a.g0 = p->g0;
+  a.W = p->W;
+  a.tiles = p->tiles;
+  a.width = p->w;
+  a.beta = p->beta;
+  a.status = p->status;
+  const int rc = from_cuda(launch_points(a, p->bin_of, p->i0_orig, p->w_orig, p->counts, p->bin_start, p->sorted_l,
+                                         p->i0_sorted, p->w_sorted, static_cast<cudaStream_t>(stream)));
+  if (rc == NURSD_OK) p->L = L;
+  return rc;
+}
+
+int nursd_temporal_dft(nursd_plan_t p, int32_t L, const float* d_hist, nursd_c64* d_phasor, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || p->T <= 0 || L < 0 || L > p->maxL) return NURSD_ERR_INVALID_ARG;
+  if (L > 0 && (!d_hist || !d_phasor || !aligned(d_hist, 16) || !aligned(d_phasor, 8))) return NURSD_ERR_INVALID_ARG;
+  return from_cuda(launch_temporal_dft(d_hist, p->Bt, reinterpret_cast<float*>(d_phasor), L, p->T, 2 * p->F,
+                                       static_cast<cudaStream_t>(stream)));
+}
+
+int nursd_nufft1(nursd_plan_t p, const nursd_c64* d_phasor, nursd_c64* d_spectrum, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || p->L < 0 || !d_spectrum || !aligned(d_spectrum, 8)) return NURSD_ERR_INVALID_ARG;
+  if (p->L > 0 && (!d_phasor || !aligned(d_phasor, 8))) return NURSD_ERR_INVALID_ARG;
+  return run_nufft1(p, reinterpret_cast<const float2*>(d_phasor), reinterpret_cast<float2*>(d_spectrum),
+                    static_cast<cudaStream_t>(stream));
+}
+
+int nursd_propagate(nursd_plan_t p, const nursd_c64* d_spectrum, void* d_out, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || !d_spectrum || !d_out || !aligned(d_spectrum, 8) || !aligned(d_out, 8))
+    return NURSD_ERR_INVALID_ARG;
+  return run_propagate(p, reinterpret_cast<const float2*>(d_spectrum), d_out, static_cast<cudaStream_t>(stream));
+}
+
+int nursd_forward_phasor(nursd_plan_t p, const nursd_c64* d_phasor, void* d_out, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || p->L < 0 || !d_out || !aligned(d_out, 8)) return NURSD_ERR_INVALID_ARG;
+  if (p->L > 0 && (!d_phasor || !aligned(d_phasor, 8))) return NURSD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = run_nufft1(p, reinterpret_cast<const float2*>(d_phasor), p->U, s);
+  if (rc == NURSD_OK) rc = run_propagate(p, p->U, d_out, s);
+  return rc;
+}
+
+int nursd_forward(nursd_plan_t p, const float* d_hist, void* d_out, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || p->T <= 0 || p->L < 0 || !d_out || !aligned(d_out, 8)) return NURSD_ERR_INVALID_ARG;
+  if (p->L > 0 && (!d_hist || !aligned(d_hist, 16))) return NURSD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = from_cuda(launch_temporal_dft(d_hist, p->Bt, reinterpret_cast<float*>(p->phasor), p->L, p->T, 2 * p->F, s));
+  if (rc == NURSD_OK) rc = run_nufft1(p, p->phasor, p->U, s);
+  if (rc == NURSD_OK) rc = run_propagate(p, p->U, d_out, s);
+  return rc;
+}
+
+int nursd_sync_status(nursd_plan_t p, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK) return NURSD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int h = 0;
+  if (cudaMemcpyAsync(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return NURSD_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return NURSD_ERR_CUDA;
+  if (h != 0 && cudaMemsetAsync(p->status, 0, sizeof(int), s) != cudaSuccess) return NURSD_ERR_CUDA;
+  if (h & 2) return NURSD_ERR_TIMEOUT;
+  if (h & 1) return NURSD_ERR_POINT_OUT_OF_RANGE;
+  return NURSD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,132 @@
+// RSD transfer-function multiply with the coherent frequency sum (Eq. 4 product,
+// frequency integral of Eq. 2): Y_z(k) = sum_f U_f(k) Ghat_{z,f}(k).
+//
+// Ghat_{z,f} is even in kx and ky and symmetric under kx <-> ky (G depends on
+// |j| only), so it is stored once per class {(+-p, +-q), (+-q, +-p)},
+// 0 <= q <= p <= M/2, as Gc[class][f][z] -- 1/8 of the full table.  One warp
+// owns one class: it stages the class's 8 spectrum rows U[k_s][0..F) in shared
+// memory (each a contiguous F-vector), then streams the class's F x Z table
+// (contiguous, each lane holding ZPL consecutive depths) once, accumulating
+// ZPL x 8 complex sums in registers, and finally writes the 8 depth rows
+// Y[k_s][0..Z) (contiguous).  Duplicate members of degenerate classes
+// (q = 0, q = p, p = M/2) are recomputed and rewritten with identical values
+// by the same lane.  HBM traffic: the table once, U once, Y once.
+#include "nursd_internal.cuh"
+
+namespace nursd {
+namespace {
+
+constexpr int kClsPerCta = 8;
+
+__device__ __forceinline__ int wrap_index(int k, int M) { return (k + M / 2) & (M - 1); }
+
+template <int ZPL>
+__global__ void __launch_bounds__(kClsPerCta * 32, 2) contract_kernel(const float2* __restrict__ U,
+                                                                   const float2* __restrict__ Gc,
+                                                                   const int2* __restrict__ cls_pq, int ncls, int M,
+                                                                   int F, int Z, float2* __restrict__ Y) {
+  extern __shared__ float4 us4[];  // [kClsPerCta][F][8 slots] complex as float4 pairs
+  float2* us = reinterpret_cast<float2*>(us4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * kClsPerCta + warp;
+  if (c >= ncls) return;  // whole warp leaves; nothing below synchronises across warps
+  const int2 pq = __ldg(cls_pq + c);
+  const int p = pq.x, q = pq.y;
+  const int kx[8] = {p, -p, p, -p, q, -q, q, -q};
+  const int ky[8] = {q, q, -q, -q, p, p, -p, -p};
+  unsigned off[8];  // mode index ky*M + kx of each class member (M <= 1024)
+#pragma unroll
+  for (int s = 0; s < 8; ++s) off[s] = (unsigned)(wrap_index(ky[s], M) * M + wrap_index(kx[s], M));
+
+  float2* my = us + (size_t)warp * F * 8;
+#pragma unroll
+  for (int s = 0; s < 8; ++s)
+    for (int f = lane; f < F; f += 32) my[f * 8 + s] = __ldg(U + (size_t)off[s] * F + f);
+  __syncwarp();
+
+  const int z0 = blockIdx.y * (32 * ZPL) + lane * ZPL;
+  float2 acc[ZPL][8];
+#pragma unroll
+  for (int i = 0; i < ZPL; ++i)
+#pragma unroll
+    for (int s = 0; s < 8; ++s) acc[i][s] = make_float2(0.f, 0.f);
+
+  const float2* __restrict__ g = Gc + (size_t)c * F * Z + z0;
+  // 16-byte vector access needs an even Z (all row offsets are then even)
+  const bool full = (z0 + ZPL <= Z) && ((Z & 1) == 0);
+#pragma unroll 2
+  for (int f = 0; f < F; ++f) {
+    float2 gv[ZPL];
+    if (full && (ZPL % 2 == 0)) {
+#pragma unroll
+      for (int i = 0; i < ZPL; i += 2) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(g + (size_t)f * Z + i));
+        gv[i] = make_float2(t.x, t.y);
+        gv[i + 1] = make_float2(t.z, t.w);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < ZPL; ++i)
+        gv[i] = (z0 + i < Z) ? __ldg(g + (size_t)f * Z + i) : make_float2(0.f, 0.f);
+    }
+    const float4* u4 = reinterpret_cast<const float4*>(my + f * 8);
+    float2 u[8];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const float4 t = u4[s];
+      u[2 * s] = make_float2(t.x, t.y);
+      u[2 * s + 1] = make_float2(t.z, t.w);
+    }
+#pragma unroll
+    for (int i = 0; i < ZPL; ++i)
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        acc[i][s].x = fmaf(gv[i].x, u[s].x, acc[i][s].x);
+        acc[i][s].x = fmaf(-gv[i].y, u[s].y, acc[i][s].x);
+        acc[i][s].y = fmaf(gv[i].x, u[s].y, acc[i][s].y);
+        acc[i][s].y = fmaf(gv[i].y, u[s].x, acc[i][s].y);
+      }
+  }
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    float2* dst = Y + (size_t)off[s] * Z + z0;
+    if (full && (ZPL % 2 == 0)) {
+#pragma unroll
+      for (int i = 0; i < ZPL; i += 2)
+        *reinterpret_cast<float4*>(dst + i) = make_float4(acc[i][s].x, acc[i][s].y, acc[i + 1][s].x, acc[i + 1][s].y);
+    } else {
+#pragma unroll
+      for (int i = 0; i < ZPL; ++i)
+        if (z0 + i < Z) dst[i] = acc[i][s];
+    }
+  }
+}
+
+template <int ZPL>
+cudaError_t launch_zpl(const float2* U, const float2* Gc, const int2* cls_pq, int ncls, int M, int F, int Z,
+                       float2* Y, cudaStream_t s) {
+  const size_t smem = sizeof(float2) * kClsPerCta * F * 8;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(contract_kernel<ZPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(float2) * kClsPerCta * 256 * 8));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  dim3 grid((ncls + kClsPerCta - 1) / kClsPerCta, (Z + 32 * ZPL - 1) / (32 * ZPL));
+  contract_kernel<ZPL><<<grid, kClsPerCta * 32, smem, s>>>(U, Gc, cls_pq, ncls, M, F, Z, Y);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_contract(const float2* U, const float2* Gc, const int2* cls_pq, int ncls, int M, int F, int Z,
+                            float2* Y, cudaStream_t s) {
+  if (F > 256) return cudaErrorInvalidValue;
+  // depths per lane (a CTA column covers 32*ZPL depths): 4 for deep volumes, fewer for shallow ones.
+  if (Z > 64) return launch_zpl<4>(U, Gc, cls_pq, ncls, M, F, Z, Y, s);
+  if (Z > 32) return launch_zpl<2>(U, Gc, cls_pq, ncls, M, F, Z, Y, s);
+  return launch_zpl<1>(U, Gc, cls_pq, ncls, M, F, Z, Y, s);
+}
+
+}  // namespace nursd

@@ -1,0 +1,101 @@
+// Internal declarations of libnursd (not part of the public C ABI).
+//
+// Data layouts (all row-major, the last index contiguous):
+//   phasors      P    [L][F]            complex64, f fastest
+//   fine grid    Bf   [W][W][F]         the non-zero window of the oversampled
+//                                       NUFFT grid (fine index g = i + g0)
+//   row spectra  R1   [W][M][F]         after the FFT along x, kx in I_M
+//   spectrum     U    [M][M][F]         (ky, kx) in I_M^2, f fastest
+//   transfer fn  Gc   [ncls][F][Z]      one entry per 8-fold symmetry class
+//   depth spectra Y   [M][M][Z]         sum over f of U * Ghat
+//   half IDFT    T1   [M][N][Z]         after the inverse FFT along kx
+//   volume       V    [Z][N][N]         complex64 or magnitude float32
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nursd.h"
+
+namespace nursd {
+
+constexpr int kTile = 16;          // spreading tile edge (fine cells)
+constexpr int kTwiddleLog = 12;    // shared FFT twiddle table has 2^12 entries
+constexpr int kMaxKernelWidth = 8;
+
+__host__ __device__ inline float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// ---------------------------------------------------------------- panel FFT
+// One CTA transforms CHI*CLO "channels" of one batch item along the FFT axis.
+// Input element (b, i, hi, lo) sits at in[b*in_sb + i*in_si + hi*in_shi + lo*in_slo]
+// and lands at FFT position (i + in_off) mod n; output o is FFT bin
+// (o + out_off) mod n and goes to out[b*out_sb + o*out_si + hi*out_shi + lo*out_slo].
+struct PanelArgs {
+  const float2* in;
+  float2* out;
+  float* out_mag;  // if non-null: write |value| here instead of out
+  long long in_sb, in_si, in_shi, in_slo;
+  long long out_sb, out_si, out_shi, out_slo;
+  int nin, in_off;
+  int nout, out_off;
+  int hi_total, lo_total;  // channel extents
+  int CHI, CLO;            // panel shape, CHI*CLO == CP
+  int batch;
+  const float* mul_o;  // optional real factor per output index
+  const float* mul_b;  // optional real factor per batch item
+  float scale;
+  int store_hi_fastest;
+  const float2* twiddle;  // e^{-2 pi i q / 2^kTwiddleLog}
+};
+
+// Launches the panel FFT of length 2^logn (4 <= 2^logn <= 2048). Returns a cudaError_t.
+cudaError_t launch_panel_fft(int logn, bool inverse, const PanelArgs& a, cudaStream_t s);
+// Panel width (channels per CTA) used for a given transform length.
+int panel_width(int logn);
+
+// ------------------------------------------------------------- temporal DFT
+// P[l][f] = sum_n h[l][n] * B[n][2f..2f+1] as a real GEMM C[L][2F] = H[L][T] B[T][2F].
+cudaError_t launch_temporal_dft(const float* h, const float* B, float* C, int L, int T, int twoF,
+                                cudaStream_t s);
+
+// ---------------------------------------------------------------- points
+struct PointsArgs {
+  const float* xy;     // [L][2] metres
+  int L;
+  double cx, cy, inv_fine_pitch;  // fine coordinate u = (x - c) * inv_fine_pitch
+  double half_extent;             // |x - c| <= half_extent is in range
+  int g0;                         // fine index of window cell 0
+  int W, tiles;                   // window width and tiles per axis
+  int width;                      // ES kernel width w
+  float beta;                     // ES kernel shape
+  int* status;                    // device error word
+};
+// Prepare and sort the relay samples.  Scratch in original order: bin_of [L],
+// i0_orig [L], w_orig [L][2w]; counts needs nbins*nchunks ints (nchunks =
+// ceil(L/1024)).  Sorted outputs: sorted_l [L] (original index), i0_sorted,
+// w_sorted, and bin_start [nbins+1] (first sorted slot of each tile).
+cudaError_t launch_points(const PointsArgs& a, int* bin_of, int2* i0_orig, float* w_orig, int* counts,
+                          int* bin_start, int* sorted_l, int2* i0_sorted, float* w_sorted, cudaStream_t s);
+
+// ---------------------------------------------------------------- spread
+cudaError_t launch_spread(const float2* P, int F, const int* bin_start, const int* sorted_l,
+                          const int2* i0, const float* wts, int width, int tiles, int W,
+                          float2* fine, cudaStream_t s);
+
+// ------------------------------------------------------------- contraction
+// Y[k][z] = sum_f U[k][f] * Gc[cls(k)][f][z] for every mode k of every class.
+cudaError_t launch_contract(const float2* U, const float2* Gc, const int2* cls_pq, int ncls, int M,
+                            int F, int Z, float2* Y, cudaStream_t s);
+
+// ------------------------------------------------------- transfer function
+// g[jy][jx][zb*F + f] = exp(i k_f r)/r, r = sqrt((jx d)^2 + (jy d)^2 + z_zb^2), FP64 phase.
+cudaError_t launch_gtf_generate(float2* g, int M, double pitch, const double* d_z, int ZB,
+                                const double* d_k, int F, cudaStream_t s);
+// Gc[(c*F + f)*Z + z0 + zb] = Gfull[rep(c)][zb*F + f]
+cudaError_t launch_gtf_compress(const float2* Gfull, const int2* cls_pq, int ncls, int M, int F,
+                                int ZB, int Z, int z0, float2* Gc, cudaStream_t s);
+
+}  // namespace nursd

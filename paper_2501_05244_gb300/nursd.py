@@ -1,0 +1,266 @@
+"""Thin Python binding of libnursd (ctypes): argument marshalling only.
+
+Every computation runs in the CUDA library; this module checks tensor
+devices / dtypes / shapes, passes ``data_ptr()`` and the current CUDA stream,
+and turns non-zero status codes into exceptions.  There is no CPU fallback:
+if the library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libnursd.so")
+
+NURSD_OK = 0
+NURSD_ERR_INVALID_ARG = 1
+NURSD_ERR_OOM = 2
+NURSD_ERR_CUDA = 3
+NURSD_ERR_TIMEOUT = 4
+NURSD_ERR_UNSUPPORTED = 5
+NURSD_ERR_POINT_OUT_OF_RANGE = 6
+NURSD_OUTPUT_MAGNITUDE = 0x1
+
+#: every entry point declared in include/nursd.h
+EXPORTS = (
+    "nursd_status_string", "nursd_phasor_frequencies", "nursd_plan_create", "nursd_plan_destroy",
+    "nursd_plan_bytes", "nursd_plan_dims", "nursd_set_points", "nursd_temporal_dft", "nursd_nufft1",
+    "nursd_propagate", "nursd_forward_phasor", "nursd_forward", "nursd_sync_status",
+)
+
+
+class NursdError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [
+        ("N", ctypes.c_int32), ("pitch", ctypes.c_double), ("center_x", ctypes.c_double),
+        ("center_y", ctypes.c_double), ("Z", ctypes.c_int32), ("h_depths", ctypes.POINTER(ctypes.c_double)),
+        ("F", ctypes.c_int32), ("h_omega", ctypes.POINTER(ctypes.c_double)),
+        ("h_weight", ctypes.POINTER(ctypes.c_double)), ("T", ctypes.c_int32), ("t0", ctypes.c_double),
+        ("dt", ctypes.c_double), ("upsample", ctypes.c_int32), ("kernel_width", ctypes.c_int32),
+        ("flags", ctypes.c_uint32), ("max_points", ctypes.c_int32),
+    ]
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libnursd and declare the C signatures (raises if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libnursd is not built ({path} missing); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    sig = {
+        "nursd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "nursd_phasor_frequencies": (ctypes.c_int, [dbl, dbl, i32, i32, dp, dp]),
+        "nursd_plan_create": (ctypes.c_int, [ctypes.POINTER(_Desc), vp, ctypes.POINTER(vp)]),
+        "nursd_plan_destroy": (ctypes.c_int, [vp]),
+        "nursd_plan_bytes": (i64, [vp]),
+        "nursd_plan_dims": (ctypes.c_int, [vp, ip, ip, ip]),
+        "nursd_set_points": (ctypes.c_int, [vp, i32, vp, vp]),
+        "nursd_temporal_dft": (ctypes.c_int, [vp, i32, vp, vp, vp]),
+        "nursd_nufft1": (ctypes.c_int, [vp, vp, vp, vp]),
+        "nursd_propagate": (ctypes.c_int, [vp, vp, vp, vp]),
+        "nursd_forward_phasor": (ctypes.c_int, [vp, vp, vp, vp]),
+        "nursd_forward": (ctypes.c_int, [vp, vp, vp, vp]),
+        "nursd_sync_status": (ctypes.c_int, [vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load_library().nursd_status_string(status).decode()
+    except RuntimeError:
+        return f"status {status}"
+
+
+def _check(rc: int, where: str):
+    if rc != NURSD_OK:
+        raise NursdError(rc, where)
+
+
+def phasor_frequencies(lambda_c: float, dt: float, t_pad: int, F: int):
+    """Frequencies [rad/s] and weights of the phasor-field band-pass (computed by libnursd)."""
+    lib = load_library()
+    om = (ctypes.c_double * F)()
+    wt = (ctypes.c_double * F)()
+    _check(lib.nursd_phasor_frequencies(lambda_c, dt, t_pad, F, om, wt), "nursd_phasor_frequencies")
+    return np.array(om[:], dtype=np.float64), np.array(wt[:], dtype=np.float64)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _dev(t, dtype, shape, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """A NURSD plan: geometry, transfer-function table and workspace on the current GPU."""
+
+    def __init__(self, N: int, pitch: float, center, depths, omega, weight=None, T: int = 0, t0: float = 0.0,
+                 dt: float = 0.0, max_points: int = 0, kernel_width: int = 6, upsample: int = 2,
+                 magnitude: bool = False, stream=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libnursd needs a CUDA GPU; none is available")
+        self._lib = load_library()
+        self.depths = np.ascontiguousarray(depths, dtype=np.float64)
+        self.omega = np.ascontiguousarray(omega, dtype=np.float64)
+        self.weight = None if weight is None else np.ascontiguousarray(weight, dtype=np.float64)
+        self.N, self.Z, self.F, self.T = int(N), len(self.depths), len(self.omega), int(T)
+        self.magnitude = bool(magnitude)
+        d = _Desc()
+        d.N = self.N
+        d.pitch = float(pitch)
+        d.center_x, d.center_y = float(center[0]), float(center[1])
+        d.Z = self.Z
+        d.h_depths = self.depths.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.F = self.F
+        d.h_omega = self.omega.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.h_weight = (self.weight.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if self.weight is not None
+                      else ctypes.POINTER(ctypes.c_double)())
+        d.T, d.t0, d.dt = self.T, float(t0), float(dt)
+        d.upsample, d.kernel_width = int(upsample), int(kernel_width)
+        d.flags = NURSD_OUTPUT_MAGNITUDE if magnitude else 0
+        d.max_points = int(max_points)
+        self._desc = d
+        h = ctypes.c_void_p()
+        _check(self._lib.nursd_plan_create(ctypes.byref(d), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)),
+               "nursd_plan_create")
+        self._h = h
+        M, nf, nc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.nursd_plan_dims(h, ctypes.byref(M), ctypes.byref(nf), ctypes.byref(nc)), "nursd_plan_dims")
+        self.M, self.fine_n, self.n_classes = M.value, nf.value, nc.value
+        self.max_points = int(max_points)
+        self.L = None
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.nursd_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nbytes(self) -> int:
+        return int(self._lib.nursd_plan_bytes(self._h))
+
+    def out_shape(self):
+        return (self.Z, self.N, self.N)
+
+    def out_dtype(self):
+        torch = _torch()
+        return torch.float32 if self.magnitude else torch.complex64
+
+    def empty_output(self):
+        torch = _torch()
+        return torch.empty(self.out_shape(), dtype=self.out_dtype(), device="cuda")
+
+    # -- entry points
+    def set_points(self, xy, stream=None):
+        torch = _torch()
+        L = int(xy.shape[0])
+        p = _dev(xy, torch.float32, (L, 2), "xy")
+        _check(self._lib.nursd_set_points(self._h, L, p, ctypes.c_void_p(_stream_ptr(stream))), "nursd_set_points")
+        self.L = L
+
+    def temporal_dft(self, hist, out=None, stream=None):
+        torch = _torch()
+        L = int(hist.shape[0])
+        h = _dev(hist, torch.float32, (L, self.T), "hist")
+        if out is None:
+            out = torch.empty((L, self.F), dtype=torch.complex64, device=hist.device)
+        o = _dev(out, torch.complex64, (L, self.F), "phasor")
+        _check(self._lib.nursd_temporal_dft(self._h, L, h, o, ctypes.c_void_p(_stream_ptr(stream))),
+               "nursd_temporal_dft")
+        return out
+
+    def nufft1(self, phasor, out=None, stream=None):
+        torch = _torch()
+        self._need_points()
+        p = _dev(phasor, torch.complex64, (self.L, self.F), "phasor")
+        if out is None:
+            out = torch.empty((self.M, self.M, self.F), dtype=torch.complex64, device=phasor.device)
+        o = _dev(out, torch.complex64, (self.M, self.M, self.F), "spectrum")
+        _check(self._lib.nursd_nufft1(self._h, p, o, ctypes.c_void_p(_stream_ptr(stream))), "nursd_nufft1")
+        return out
+
+    def propagate(self, spectrum, out=None, stream=None):
+        torch = _torch()
+        s = _dev(spectrum, torch.complex64, (self.M, self.M, self.F), "spectrum")
+        if out is None:
+            out = self.empty_output()
+        o = _dev(out, self.out_dtype(), self.out_shape(), "out")
+        _check(self._lib.nursd_propagate(self._h, s, o, ctypes.c_void_p(_stream_ptr(stream))), "nursd_propagate")
+        return out
+
+    def forward_phasor(self, phasor, out=None, stream=None):
+        torch = _torch()
+        self._need_points()
+        p = _dev(phasor, torch.complex64, (self.L, self.F), "phasor")
+        if out is None:
+            out = self.empty_output()
+        o = _dev(out, self.out_dtype(), self.out_shape(), "out")
+        _check(self._lib.nursd_forward_phasor(self._h, p, o, ctypes.c_void_p(_stream_ptr(stream))),
+               "nursd_forward_phasor")
+        return out
+
+    def forward(self, hist, out=None, stream=None):
+        torch = _torch()
+        self._need_points()
+        h = _dev(hist, torch.float32, (self.L, self.T), "hist")
+        if out is None:
+            out = self.empty_output()
+        o = _dev(out, self.out_dtype(), self.out_shape(), "out")
+        _check(self._lib.nursd_forward(self._h, h, o, ctypes.c_void_p(_stream_ptr(stream))), "nursd_forward")
+        return out
+
+    def sync_status(self, stream=None) -> int:
+        return int(self._lib.nursd_sync_status(self._h, ctypes.c_void_p(_stream_ptr(stream))))
+
+    def _need_points(self):
+        if self.L is None:
+            raise RuntimeError("set_points() must be called first")

@@ -1,0 +1,279 @@
+"""GPU parity: libnursd (called through the C ABI) against the FP64 oracle.
+
+Gate (FP32 CUDA path vs FP64 oracle): relative L2 error <= 1e-4 on complex
+outputs, on the same seeded inputs.  Full-output comparisons run at the tiny
+(32^2 x 16, 1,024 samples) and mid (64^2 x 16, 4,096 samples) sizes; at the
+65,536-sample SPAD-array size (256^2 x 128, 128 frequencies, the benchmark's
+launch configuration) the oracle checks sampled outputs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+import paper_2501_05244_gb300 as nursd
+from workloads import (BASE_SEED, geometry_c1, geometry_c2, geometry_mid, random_phasors, random_spectrum,
+                       relay_lattice, relay_uniform, workload_c1, workload_c2, workload_c2_lattice, workload_mid)
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+def rel(a, b):
+    a = np.asarray(a, np.complex128).ravel()
+    b = np.asarray(b, np.complex128).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    nursd.build()
+    nursd.load_library()
+
+
+def make_plan(g, L, **kw):
+    om, wt = nursd.phasor_frequencies(g.lambda_c, g.dt, g.t_pad, g.F)
+    return nursd.Plan(g.N, g.pitch, g.center, g.depths, om, wt, T=g.T, t0=g.t0, dt=g.dt, max_points=L, **kw)
+
+
+def oracle_freqs(g):
+    return O.phasor_frequencies(g.lambda_c, g.dt, g.t_pad, g.F)
+
+
+def spectrum_to_oracle(U_gpu):
+    """[M][M][F] (f fastest) -> [F][M][M]"""
+    return np.transpose(U_gpu, (2, 0, 1))
+
+
+# ------------------------------------------------------------ tiny / mid ---
+
+@pytest.mark.parametrize("wlf", [workload_c1, workload_mid])
+def test_forward_from_histograms_matches_oracle(wlf):
+    wl = wlf()
+    g = wl.geom
+    plan = make_plan(g, len(wl.xy))
+    plan.set_points(torch.from_numpy(wl.xy).cuda())
+    V = plan.forward(torch.from_numpy(wl.hist).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    om, wt = oracle_freqs(g)
+    P = O.temporal_dft(wl.hist, g.t0, g.dt, om, wt)
+    V_ref = O.nursd_forward(P, wl.xy, g.center, g.pitch, g.N, g.depths, om)
+    assert rel(V, V_ref) < TOL
+
+
+@pytest.mark.parametrize("wlf", [workload_c1, workload_mid])
+def test_stages_match_oracle(wlf):
+    wl = wlf()
+    g = wl.geom
+    plan = make_plan(g, len(wl.xy))
+    xy = torch.from_numpy(wl.xy).cuda()
+    plan.set_points(xy)
+    om, wt = oracle_freqs(g)
+    # a1: temporal transform
+    P_gpu = plan.temporal_dft(torch.from_numpy(wl.hist).cuda())
+    P_ref = O.temporal_dft(wl.hist, g.t0, g.dt, om, wt)
+    assert rel(P_gpu.cpu().numpy(), P_ref) < 1e-5
+    # a2-a5: NUFFT-1 of seeded random phasors against the exact non-uniform DFT
+    Pr = random_phasors(len(wl.xy), g.F, seed=BASE_SEED + 40)
+    U_gpu = plan.nufft1(torch.from_numpy(Pr).cuda()).cpu().numpy()
+    U_ref = O.nudft_type1(Pr, O.relay_theta(wl.xy, g.center, g.pitch, g.M), g.M)
+    assert rel(spectrum_to_oracle(U_gpu), U_ref) < TOL
+    # a6-a7: propagation of a seeded random spectrum
+    S = random_spectrum(g.M, g.F, seed=BASE_SEED + 41)
+    V_gpu = plan.propagate(torch.from_numpy(S).cuda()).cpu().numpy()
+    V_ref = O.propagate(spectrum_to_oracle(S).astype(np.complex128), O.transfer_functions(g.depths, om, g.M, g.pitch), g.N)
+    assert rel(V_gpu, V_ref) < TOL
+    # the fused entry point equals the staged ones
+    V1 = plan.forward_phasor(P_gpu).cpu().numpy()
+    V2 = plan.propagate(plan.nufft1(P_gpu)).cpu().numpy()
+    assert rel(V1, V2) < 1e-6
+
+
+def test_results_are_deterministic():
+    wl = workload_c1()
+    g = wl.geom
+    plan = make_plan(g, len(wl.xy))
+    plan.set_points(torch.from_numpy(wl.xy).cuda())
+    h = torch.from_numpy(wl.hist).cuda()
+    a = plan.forward(h).cpu()
+    plan.set_points(torch.from_numpy(wl.xy).cuda())
+    b = plan.forward(h).cpu()
+    assert torch.equal(a, b)
+
+
+def test_magnitude_output_is_abs_of_complex_output():
+    wl = workload_c1()
+    g = wl.geom
+    pc = make_plan(g, len(wl.xy))
+    pm = make_plan(g, len(wl.xy), magnitude=True)
+    xy = torch.from_numpy(wl.xy).cuda()
+    h = torch.from_numpy(wl.hist).cuda()
+    pc.set_points(xy)
+    pm.set_points(xy)
+    Vc = pc.forward(h).cpu().numpy()
+    Vm = pm.forward(h).cpu().numpy()
+    assert Vm.dtype == np.float32
+    assert np.allclose(Vm, np.abs(Vc), rtol=1e-6, atol=1e-6 * np.abs(Vc).max())
+
+
+# ----------------------------------------------------------- edge cases ---
+
+def _random_case(N, L, F, Z, seed, pitch=0.02, center=(0.03, -0.02), edge=False):
+    r = np.random.default_rng(seed)
+    half = N * pitch / 2
+    xy = r.uniform(-half, half, (L, 2)) + np.asarray(center)
+    if edge and L >= 4:  # samples on the aperture boundary and at its corners (inside by ~1e-7)
+        e = half * (1 - 1e-6)
+        xy[0] = (center[0] - e, center[1] - e)
+        xy[1] = (center[0] + e, center[1] + e)
+        xy[2] = (center[0] + e, center[1] - e)
+        xy[3] = (center[0], center[1] + e)
+    xy = xy.astype(np.float32)
+    P = random_phasors(L, F, seed=seed + 1)
+    om = 2 * math.pi * np.linspace(3e9, 6e9, F)
+    depths = np.linspace(0.3, 0.9, Z)
+    return xy, P, om, depths, pitch, center
+
+
+@pytest.mark.parametrize("N,L,F,Z", [(8, 1, 1, 1), (16, 37, 3, 5), (16, 1025, 33, 70), (32, 700, 48, 130),
+                                     (8, 64, 2, 3)])
+def test_ragged_sizes_match_oracle(N, L, F, Z):
+    xy, P, om, depths, pitch, center = _random_case(N, L, F, Z, seed=N * 1000 + L, edge=True)
+    plan = nursd.Plan(N, pitch, center, depths, om, max_points=L)
+    plan.set_points(torch.from_numpy(xy).cuda())
+    V = plan.forward_phasor(torch.from_numpy(P).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    V_ref = O.nursd_forward(P, xy, center, pitch, N, depths, om)
+    assert rel(V, V_ref) < TOL
+
+
+def test_empty_point_set_gives_zero_volume():
+    xy, P, om, depths, pitch, center = _random_case(16, 8, 4, 3, seed=3)
+    plan = nursd.Plan(16, pitch, center, depths, om, max_points=8)
+    plan.set_points(torch.zeros((0, 2), dtype=torch.float32, device="cuda"))
+    V = plan.forward_phasor(torch.zeros((0, 4), dtype=torch.complex64, device="cuda"))
+    assert float(V.abs().max()) == 0.0
+    assert plan.sync_status() == 0
+
+
+def test_out_of_aperture_sample_is_reported_and_ignored():
+    xy, P, om, depths, pitch, center = _random_case(16, 40, 4, 3, seed=5)
+    bad = xy.copy()
+    bad[7, 0] = center[0] + 16 * pitch * 0.51
+    plan = nursd.Plan(16, pitch, center, depths, om, max_points=40)
+    plan.set_points(torch.from_numpy(bad).cuda())
+    V = plan.forward_phasor(torch.from_numpy(P).cuda()).cpu().numpy()
+    assert plan.sync_status() == nursd.nursd.NURSD_ERR_POINT_OUT_OF_RANGE
+    assert plan.sync_status() == 0  # the flag is cleared once read
+    keep = np.ones(40, bool)
+    keep[7] = False
+    V_ref = O.nursd_forward(P[keep], xy[keep], center, pitch, 16, depths, om)
+    assert rel(V, V_ref) < TOL
+
+
+def test_invalid_calls_raise():
+    xy, P, om, depths, pitch, center = _random_case(16, 8, 4, 3, seed=7)
+    plan = nursd.Plan(16, pitch, center, depths, om, max_points=8)
+    with pytest.raises(RuntimeError):
+        plan.forward_phasor(torch.from_numpy(P).cuda())  # no points yet
+    with pytest.raises(nursd.NursdError):
+        plan.set_points(torch.zeros((9, 2), dtype=torch.float32, device="cuda"))  # over capacity
+    with pytest.raises(TypeError):
+        plan.set_points(torch.zeros((4, 2), dtype=torch.float64, device="cuda"))
+
+
+def test_large_lattice_n512_on_lattice_equals_direct_backprojection():
+    # N = 512 (fine grid 2048, the radix-2 FFT path): few on-lattice samples, checked
+    # at sampled voxels against direct back-projection, which is exact on the lattice.
+    N, pitch, center = 512, 2.0 / 512, (0.0, 0.0)
+    lat = relay_lattice(N, pitch, center)
+    r = np.random.default_rng(21)
+    idx = r.choice(N * N, 300, replace=False)
+    xy = lat[idx]
+    F = 4
+    om = 2 * math.pi * np.linspace(4e9, 5e9, F)
+    depths = np.array([0.8, 1.7])
+    P = random_phasors(len(xy), F, seed=22)
+    plan = nursd.Plan(N, pitch, center, depths, om, max_points=len(xy))
+    plan.set_points(torch.from_numpy(xy).cuda())
+    V = plan.forward_phasor(torch.from_numpy(P).cuda()).cpu().numpy()
+    m = r.integers(0, N, size=(64, 2))
+    for iz, z in enumerate(depths):
+        vox = np.stack([(m[:, 0] - N // 2) * pitch, (m[:, 1] - N // 2) * pitch, np.full(64, z)], axis=1)
+        ref = O.fbp_direct(P, xy.astype(np.float64), om, vox)
+        assert rel(V[iz, m[:, 1], m[:, 0]], ref) < TOL
+
+
+# ------------------------------------------- 65k-sample SPAD-array size ---
+
+@pytest.fixture(scope="module")
+def c2():
+    wl = workload_c2()
+    g = wl.geom
+    plan = make_plan(g, len(wl.xy))
+    plan.set_points(torch.from_numpy(wl.xy).cuda())
+    return wl, plan
+
+
+def test_spad_temporal_transform_sampled(c2):
+    wl, plan = c2
+    g = wl.geom
+    P = plan.temporal_dft(torch.from_numpy(wl.hist).cuda()).cpu().numpy()
+    idx = np.random.default_rng(1).choice(len(wl.xy), 512, replace=False)
+    om, wt = oracle_freqs(g)
+    assert rel(P[idx], O.temporal_dft(wl.hist[idx], g.t0, g.dt, om, wt)) < 1e-5
+
+
+def test_spad_nufft1_sampled_modes(c2):
+    wl, plan = c2
+    g = wl.geom
+    Pr = random_phasors(len(wl.xy), g.F, seed=BASE_SEED + 50)
+    U = plan.nufft1(torch.from_numpy(Pr).cuda()).cpu().numpy()
+    r = np.random.default_rng(2)
+    kxy = r.integers(-g.M // 2, g.M // 2, size=(1024, 2))
+    fs = np.array([0, 37, 64, 127])
+    th = O.relay_theta(wl.xy, g.center, g.pitch, g.M)
+    ref = np.concatenate([O.nudft_type1_modes(Pr[:, fs], th, kxy[i:i + 256]) for i in range(0, 1024, 256)])
+    got = U[kxy[:, 1] + g.M // 2, kxy[:, 0] + g.M // 2][:, fs]
+    assert rel(got, ref) < TOL
+
+
+def test_spad_propagate_sampled_depths(c2):
+    wl, plan = c2
+    g = wl.geom
+    S = random_spectrum(g.M, g.F, seed=BASE_SEED + 51)
+    V = plan.propagate(torch.from_numpy(S).cuda()).cpu().numpy()
+    om, _ = oracle_freqs(g)
+    U = spectrum_to_oracle(S).astype(np.complex128)
+    for iz in (0, 77, g.Z - 1):
+        assert rel(V[iz], O.propagate_depth(U, g.depths[iz], om, g.pitch, g.N)) < TOL
+
+
+def test_spad_forward_equals_staged_calls(c2):
+    wl, plan = c2
+    h = torch.from_numpy(wl.hist).cuda()
+    V = plan.forward(h)
+    V2 = plan.propagate(plan.nufft1(plan.temporal_dft(h)))
+    assert float((V - V2).abs().max()) == 0.0
+
+
+def test_spad_lattice_variant_equals_direct_backprojection():
+    # 65,536 = 256^2 samples on the lattice itself: NURSD-1 equals direct back-projection
+    # exactly, so sampled voxels of the whole forward (histograms in) are an exact gate.
+    wl = workload_c2_lattice()
+    g = wl.geom
+    plan = make_plan(g, len(wl.xy))
+    plan.set_points(torch.from_numpy(wl.xy).cuda())
+    V = plan.forward(torch.from_numpy(wl.hist).cuda()).cpu().numpy()
+    om, wt = oracle_freqs(g)
+    P = O.temporal_dft(wl.hist, g.t0, g.dt, om, wt)
+    r = np.random.default_rng(3)
+    vz = r.integers(0, g.Z, 32)
+    m = r.integers(0, g.N, size=(32, 2))
+    vox = np.stack([(m[:, 0] - g.N // 2) * g.pitch, (m[:, 1] - g.N // 2) * g.pitch, g.depths[vz]], axis=1)
+    ref = O.fbp_direct(P, wl.xy.astype(np.float64), om, vox)
+    assert rel(V[vz, m[:, 1], m[:, 0]], ref) < TOL
