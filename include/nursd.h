@@ -169,6 +169,41 @@ int nursd_forward_phasor(nursd_plan_t plan, const nursd_c64* d_phasor, void* d_o
 int nursd_forward(nursd_plan_t plan, const float* d_hist, void* d_out, nursd_stream_t stream);
 
 /*
+ * Stage profiling.  Stages of the forward path, each one or more kernel
+ * launches: relay-sample preparation and sort, temporal transform, spread,
+ * FFT along x, FFT along y with deconvolution, transfer-function contraction,
+ * inverse FFT along kx, inverse FFT along ky with crop.
+ */
+typedef enum {
+  NURSD_STAGE_POINTS = 0,
+  NURSD_STAGE_TEMPORAL = 1,
+  NURSD_STAGE_SPREAD = 2,
+  NURSD_STAGE_FFT_X = 3,
+  NURSD_STAGE_FFT_Y = 4,
+  NURSD_STAGE_CONTRACT = 5,
+  NURSD_STAGE_IFFT_X = 6,
+  NURSD_STAGE_IFFT_Y = 7,
+  NURSD_NUM_STAGES = 8
+} nursd_stage;
+
+/*
+ * enable != 0: from now on every stage brackets its launches with a pair of
+ * CUDA events recorded on the caller's stream; enable == 0 stops recording.
+ * Either way the recorded events are discarded.
+ */
+int nursd_profile_enable(nursd_plan_t plan, int enable);
+
+/*
+ * For stage `stage`: *h_ms = summed device time of the launches recorded
+ * since profiling was enabled (or last read), *h_count = number of recorded
+ * stage executions.  Synchronises on the recorded events; resets them.
+ */
+int nursd_profile_read(nursd_plan_t plan, int stage, double* h_ms, int64_t* h_count);
+
+/* Number of kernel launches the plan has issued since it was created. */
+int64_t nursd_launch_count(nursd_plan_t plan);
+
+/*
  * Synchronise `stream`, read and clear the plan's device error word.
  * Returns NURSD_OK, NURSD_ERR_POINT_OUT_OF_RANGE or NURSD_ERR_TIMEOUT.
  */

@@ -84,6 +84,11 @@ struct nursd_plan_s {
   int* status = nullptr;
   int64_t bytes = 0;
   std::vector<void*> allocs;
+  // profiling: per stage, a list of (start, stop) events and how many are in use
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[NURSD_NUM_STAGES];
+  size_t ev_used[NURSD_NUM_STAGES] = {};
+  int64_t launches = 0;
 
   template <class T>
   bool alloc(T*& p, size_t count) {
@@ -99,9 +104,47 @@ struct nursd_plan_s {
     return true;
   }
   ~nursd_plan_s() {
+    for (auto& v : ev)
+      for (auto& e : v) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+      }
     for (void* p : allocs) cudaFree(p);
   }
 };
+
+namespace {
+
+// Records a stage's start/stop events on the launching stream while profiling is on.
+class StageTimer {
+ public:
+  StageTimer(nursd_plan_s* p, int stage, cudaStream_t s, int launches) : p_(p), stage_(stage), s_(s) {
+    p->launches += launches;
+    if (!p->profiling) return;
+    auto& v = p->ev[stage];
+    if (p->ev_used[stage] == v.size()) {
+      std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
+      if (cudaEventCreate(&e.first) != cudaSuccess || cudaEventCreate(&e.second) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+      }
+      v.push_back(e);
+    }
+    pair_ = &v[p->ev_used[stage]++];
+    cudaEventRecord(pair_->first, s);
+  }
+  ~StageTimer() {
+    if (pair_) cudaEventRecord(pair_->second, s_);
+  }
+
+ private:
+  nursd_plan_s* p_;
+  int stage_;
+  cudaStream_t s_;
+  std::pair<cudaEvent_t, cudaEvent_t>* pair_ = nullptr;
+};
+
+}  // namespace
 
 namespace {
 
@@ -191,25 +234,39 @@ int build_transfer_table(nursd_plan_s* p, cudaStream_t s) {
 int run_nufft1(nursd_plan_s* p, const float2* phasor, float2* spec, cudaStream_t s) {
   const int F = p->F, M = p->M, W = p->W;
   const int logf = ilog2(p->nf);
-  cudaError_t e = launch_spread(phasor, F, p->bin_start, p->sorted_l, p->i0_sorted, p->w_sorted, p->w, p->tiles, W,
-                                p->fine, s);
-  if (e == cudaSuccess)  // FFT along x of every window row, keep kx in I_M
+  cudaError_t e;
+  {
+    StageTimer t(p, NURSD_STAGE_SPREAD, s, 1);
+    e = launch_spread(phasor, F, p->bin_start, p->sorted_l, p->i0_sorted, p->w_sorted, p->w, p->tiles, W, p->fine, s);
+  }
+  if (e == cudaSuccess) {  // FFT along x of every window row, keep kx in I_M
+    StageTimer t(p, NURSD_STAGE_FFT_X, s, 1);
     e = axis_pass(p, p->fine, p->R1, logf, false, F, W, (long long)W * F, F, (long long)M * F, F, W, p->g0, M, -M / 2,
                   nullptr, nullptr, 1.f, s);
-  if (e == cudaSuccess)  // FFT along y of every kx column, keep ky in I_M, divide by psi_hat(kx) psi_hat(ky)
+  }
+  if (e == cudaSuccess) {  // FFT along y of every kx column, keep ky in I_M, divide by psi_hat(kx) psi_hat(ky)
+    StageTimer t(p, NURSD_STAGE_FFT_Y, s, 1);
     e = axis_pass(p, p->R1, spec, logf, false, F, M, F, (long long)M * F, F, (long long)M * F, W, p->g0, M, -M / 2,
                   p->deconv, p->deconv, 1.f, s);
+  }
   return from_cuda(e);
 }
 
 int run_propagate(nursd_plan_s* p, const float2* spec, void* out, cudaStream_t s) {
   const int M = p->M, N = p->N, Z = p->Z, F = p->F;
   const int logM = ilog2(M);
-  cudaError_t e = launch_contract(spec, p->Gc, p->cls, p->ncls, M, F, Z, p->Y, s);
-  if (e == cudaSuccess)  // inverse FFT along kx, keep mx in I_N
+  cudaError_t e;
+  {
+    StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
+    e = launch_contract(spec, p->Gc, p->cls, p->ncls, M, F, Z, p->Y, s);
+  }
+  if (e == cudaSuccess) {  // inverse FFT along kx, keep mx in I_N
+    StageTimer t(p, NURSD_STAGE_IFFT_X, s, 1);
     e = axis_pass(p, p->Y, p->T1, logM, true, Z, M, (long long)M * Z, Z, (long long)N * Z, Z, M, -M / 2, N, -N / 2,
                   nullptr, nullptr, 1.f, s);
+  }
   if (e == cudaSuccess) {  // inverse FFT along ky for every (mx, z), keep my in I_N, write V[z][my][mx]
+    StageTimer t(p, NURSD_STAGE_IFFT_Y, s, 1);
     PanelArgs a = panel_base(p);
     a.in = p->T1;
     a.in_si = (long long)N * Z;
@@ -426,8 +483,12 @@ int nursd_set_points(nursd_plan_t p, int32_t L, const float* d_xy, nursd_stream_
   a.width = p->w;
   a.beta = p->beta;
   a.status = p->status;
-  const int rc = from_cuda(launch_points(a, p->bin_of, p->i0_orig, p->w_orig, p->counts, p->bin_start, p->sorted_l,
-                                         p->i0_sorted, p->w_sorted, static_cast<cudaStream_t>(stream)));
+  int rc;
+  {
+    StageTimer t(p, NURSD_STAGE_POINTS, static_cast<cudaStream_t>(stream), L > 0 ? 4 : 0);
+    rc = from_cuda(launch_points(a, p->bin_of, p->i0_orig, p->w_orig, p->counts, p->bin_start, p->sorted_l,
+                                 p->i0_sorted, p->w_sorted, static_cast<cudaStream_t>(stream)));
+  }
   if (rc == NURSD_OK) p->L = L;
   return rc;
 }
@@ -435,6 +496,7 @@ int nursd_set_points(nursd_plan_t p, int32_t L, const float* d_xy, nursd_stream_
 int nursd_temporal_dft(nursd_plan_t p, int32_t L, const float* d_hist, nursd_c64* d_phasor, nursd_stream_t stream) {
   if (check_plan(p) != NURSD_OK || p->T <= 0 || L < 0 || L > p->maxL) return NURSD_ERR_INVALID_ARG;
   if (L > 0 && (!d_hist || !d_phasor || !aligned(d_hist, 16) || !aligned(d_phasor, 8))) return NURSD_ERR_INVALID_ARG;
+  StageTimer t(p, NURSD_STAGE_TEMPORAL, static_cast<cudaStream_t>(stream), L > 0 ? 1 : 0);
   return from_cuda(launch_temporal_dft(d_hist, p->Bt, reinterpret_cast<float*>(d_phasor), L, p->T, 2 * p->F,
                                        static_cast<cudaStream_t>(stream)));
 }
@@ -465,11 +527,41 @@ int nursd_forward(nursd_plan_t p, const float* d_hist, void* d_out, nursd_stream
   if (check_plan(p) != NURSD_OK || p->T <= 0 || p->L < 0 || !d_out || !aligned(d_out, 8)) return NURSD_ERR_INVALID_ARG;
   if (p->L > 0 && (!d_hist || !aligned(d_hist, 16))) return NURSD_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int rc = from_cuda(launch_temporal_dft(d_hist, p->Bt, reinterpret_cast<float*>(p->phasor), p->L, p->T, 2 * p->F, s));
+  int rc;
+  {
+    StageTimer t(p, NURSD_STAGE_TEMPORAL, s, p->L > 0 ? 1 : 0);
+    rc = from_cuda(launch_temporal_dft(d_hist, p->Bt, reinterpret_cast<float*>(p->phasor), p->L, p->T, 2 * p->F, s));
+  }
   if (rc == NURSD_OK) rc = run_nufft1(p, p->phasor, p->U, s);
   if (rc == NURSD_OK) rc = run_propagate(p, p->U, d_out, s);
   return rc;
 }
+
+int nursd_profile_enable(nursd_plan_t p, int enable) {
+  if (check_plan(p) != NURSD_OK) return NURSD_ERR_INVALID_ARG;
+  p->profiling = enable != 0;
+  for (auto& u : p->ev_used) u = 0;
+  return NURSD_OK;
+}
+
+int nursd_profile_read(nursd_plan_t p, int stage, double* h_ms, int64_t* h_count) {
+  if (check_plan(p) != NURSD_OK || stage < 0 || stage >= NURSD_NUM_STAGES || !h_ms || !h_count)
+    return NURSD_ERR_INVALID_ARG;
+  double total = 0.0;
+  for (size_t i = 0; i < p->ev_used[stage]; ++i) {
+    auto& e = p->ev[stage][i];
+    if (cudaEventSynchronize(e.second) != cudaSuccess) return NURSD_ERR_CUDA;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.first, e.second) != cudaSuccess) return NURSD_ERR_CUDA;
+    total += ms;
+  }
+  *h_ms = total;
+  *h_count = (int64_t)p->ev_used[stage];
+  p->ev_used[stage] = 0;
+  return NURSD_OK;
+}
+
+int64_t nursd_launch_count(nursd_plan_t p) { return p ? p->launches : -1; }
 
 int nursd_sync_status(nursd_plan_t p, nursd_stream_t stream) {
   if (check_plan(p) != NURSD_OK) return NURSD_ERR_INVALID_ARG;

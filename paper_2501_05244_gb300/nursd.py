@@ -30,7 +30,11 @@ EXPORTS = (
     "nursd_status_string", "nursd_phasor_frequencies", "nursd_plan_create", "nursd_plan_destroy",
     "nursd_plan_bytes", "nursd_plan_dims", "nursd_set_points", "nursd_temporal_dft", "nursd_nufft1",
     "nursd_propagate", "nursd_forward_phasor", "nursd_forward", "nursd_sync_status",
+    "nursd_profile_enable", "nursd_profile_read", "nursd_launch_count",
 )
+
+#: stage names in nursd_stage order
+STAGES = ("points", "temporal", "spread", "fft_x", "fft_y", "contract", "ifft_x", "ifft_y")
 
 
 class NursdError(RuntimeError):
@@ -78,6 +82,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "nursd_forward_phasor": (ctypes.c_int, [vp, vp, vp, vp]),
         "nursd_forward": (ctypes.c_int, [vp, vp, vp, vp]),
         "nursd_sync_status": (ctypes.c_int, [vp, vp]),
+        "nursd_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
+        "nursd_profile_read": (ctypes.c_int, [vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int64)]),
+        "nursd_launch_count": (i64, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -260,6 +267,23 @@ class Plan:
 
     def sync_status(self, stream=None) -> int:
         return int(self._lib.nursd_sync_status(self._h, ctypes.c_void_p(_stream_ptr(stream))))
+
+    # -- profiling
+    def profile(self, enable: bool = True):
+        _check(self._lib.nursd_profile_enable(self._h, 1 if enable else 0), "nursd_profile_enable")
+
+    def profile_read(self):
+        """{stage: (total_ms, executions)} since profiling was enabled or last read."""
+        out = {}
+        for i, name in enumerate(STAGES):
+            ms, n = ctypes.c_double(), ctypes.c_int64()
+            _check(self._lib.nursd_profile_read(self._h, i, ctypes.byref(ms), ctypes.byref(n)), "nursd_profile_read")
+            out[name] = (ms.value, n.value)
+        return out
+
+    @property
+    def launch_count(self) -> int:
+        return int(self._lib.nursd_launch_count(self._h))
 
     def _need_points(self):
         if self.L is None:

@@ -32,5 +32,6 @@ from .configs import (  # noqa: F401
     workload_mid,
     workload_c2,
     workload_c2_lattice,
+    workload_c5,
     batch_sizes_c4,
 )

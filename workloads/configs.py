@@ -127,3 +127,14 @@ def workload_c2_lattice(seed: int = BASE_SEED + 2, with_hist: bool = True) -> Wo
     g = geometry_c2(t0=dmin / C_LIGHT - 32 * g0.dt)
     h = simulate_histograms(xy, src, alb, g.T, g.dt, g.t0, seed=seed + 100) if with_hist else None
     return Workload(g, xy, h, src)
+
+
+def workload_c5(seed: int = BASE_SEED + 5, with_hist: bool = True) -> Workload:
+    """65,536 keystone samples reconstructed on the 128^2 x 64 grid of the gradient workload."""
+    xy = relay_keystone(seed=seed)
+    src, alb, dmin = _c2_scene(xy, seed + 7)
+    g0 = geometry_c5()
+    g = Geometry(name=g0.name, N=g0.N, pitch=g0.pitch, center=g0.center, depths=g0.depths, T=g0.T, dt=g0.dt,
+                 t0=dmin / C_LIGHT - 32 * g0.dt, lambda_c=g0.lambda_c, t_pad=g0.t_pad, F=g0.F)
+    h = simulate_histograms(xy, src, alb, g.T, g.dt, g.t0, seed=seed + 100) if with_hist else None
+    return Workload(g, xy, h, src)
