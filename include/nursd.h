@@ -204,6 +204,36 @@ int nursd_profile_read(nursd_plan_t plan, int stage, double* h_ms, int64_t* h_co
 int64_t nursd_launch_count(nursd_plan_t plan);
 
 /*
+ * NUFFT type 1 that allocates nothing.  The paper has no counterpart: this is
+ * a library facility.  Some callers cannot call cudaMalloc at all -- engines
+ * that own every byte of device memory through a pre-reserved pool, and
+ * plugins running inside them, where an extra allocation would synchronise the
+ * device or escape the pool.  For them this computes what nursd_set_points
+ * followed by nursd_nufft1 computes for a plan with the same N, pitch, centre,
+ * kernel width and upsample 2: d_xy [L][2] float32 metres and d_phasor [L][F]
+ * complex64 in, d_spectrum [M][M][F] complex64 out (M = 2N), all owned by the
+ * caller.  No plan is needed and no device memory is allocated or freed.
+ *
+ * Its scratch is one fixed 24 MiB device array inside libnursd, present on
+ * every GPU that loads the library until the process exits.  Per call it needs
+ * 4M + 4 + L(24 + 16w) + 4 tiles^2 (ceil(L/1024) + 1) + 8 W F (W + M) bytes plus
+ * alignment, with W = 16 ceil((2N + w + 2)/16) and tiles = W/16 (for example
+ * N = 64, F = 32, L = 16,384 and w = 6 take about 12 MiB); larger requests
+ * return NURSD_ERR_UNSUPPORTED before any device work.
+ *
+ * The first call on each device does a one-time set-up with that device
+ * current: it looks up the array's device address and fills its fixed tables
+ * with a small kernel, synchronising `stream`.  Make that first call before any
+ * stream capture.  Every call shares the same array and leaves its contents
+ * behind, so calls that overlap on the GPU (different streams, or different
+ * host threads) race and must be serialised by the caller.  Samples outside
+ * |x - c| <= N pitch / 2 get zero weight; they are not reported.
+ */
+int nursd_nufft1_noalloc(int32_t N, double pitch, double center_x, double center_y, int32_t kernel_width, int32_t L,
+                         const float* d_xy, int32_t F, const nursd_c64* d_phasor, nursd_c64* d_spectrum,
+                         nursd_stream_t stream);
+
+/*
  * Synchronise `stream`, read and clear the plan's device error word.
  * Returns NURSD_OK, NURSD_ERR_POINT_OUT_OF_RANGE or NURSD_ERR_TIMEOUT.
  */

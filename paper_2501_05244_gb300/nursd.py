@@ -30,7 +30,7 @@ EXPORTS = (
     "nursd_status_string", "nursd_phasor_frequencies", "nursd_plan_create", "nursd_plan_destroy",
     "nursd_plan_bytes", "nursd_plan_dims", "nursd_set_points", "nursd_temporal_dft", "nursd_nufft1",
     "nursd_propagate", "nursd_forward_phasor", "nursd_forward", "nursd_sync_status",
-    "nursd_profile_enable", "nursd_profile_read", "nursd_launch_count",
+    "nursd_profile_enable", "nursd_profile_read", "nursd_launch_count", "nursd_nufft1_noalloc",
 )
 
 #: stage names in nursd_stage order
@@ -85,6 +85,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "nursd_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
         "nursd_profile_read": (ctypes.c_int, [vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int64)]),
         "nursd_launch_count": (i64, [vp]),
+        "nursd_nufft1_noalloc": (ctypes.c_int, [i32, dbl, dbl, dbl, i32, i32, vp, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
