@@ -60,6 +60,8 @@ typedef enum {
 
 /* Plan flags. */
 #define NURSD_OUTPUT_MAGNITUDE 0x1u /* nursd_forward* write |V| (float32) instead of V */
+#define NURSD_ENABLE_ADJOINT 0x2u   /* also build the transposed table used by nursd_adjoint and
+                                       nursd_grad_points (doubles the table memory; Z <= 256) */
 
 /*
  * Plan descriptor.  Geometry of Sec. 3.1 / Eq. 4: an N x N output lattice of
@@ -167,6 +169,42 @@ int nursd_forward_phasor(nursd_plan_t plan, const nursd_c64* d_phasor, void* d_o
  * count given to nursd_set_points.
  */
 int nursd_forward(nursd_plan_t plan, const float* d_hist, void* d_out, nursd_stream_t stream);
+
+/*
+ * NURSD-2/3 output (Eqs. NURSD2 and NURSD3): the forward from phasors evaluated
+ * at arbitrary voxels of each depth plane instead of the lattice:
+ *   V_z(x_v) = M^-2 sum_k Y_z(k) exp(+i k . theta_v),  theta_v = 2 pi (x_v - c) / (M delta),
+ * with Y_z as in nursd_propagate.  Computed by type-2 NUFFT (deconvolve,
+ * inverse fine-grid FFT, ES interpolation).  d_vox_xy [Z][K][2] float32
+ * metres (K voxels per plane, plane z at depth z_z), d_out [Z][K] complex64.
+ * Voxels outside |x - c| <= N delta / 2 give 0 and set the out-of-range
+ * status bit.  Requires nursd_set_points.
+ */
+int nursd_forward_points(nursd_plan_t plan, const nursd_c64* d_phasor, int32_t K, const float* d_vox_xy,
+                         nursd_c64* d_out, nursd_stream_t stream);
+
+/*
+ * Adjoint of nursd_forward_phasor (type 2 is the adjoint of type 1, Sec. 6):
+ *   P^H[l][f] = sum_k R_f(k) exp(+i k . theta_l),
+ *   R_f(k) = sum_z conj(Ghat_{z,f}(k)) M^-2 sum_{m in I_N^2} V_z[m] exp(-2 pi i k.m / M).
+ * d_vol [Z][N][N] complex64 -> d_phasor [L][F] complex64 at the current relay
+ * samples.  Needs a plan created with NURSD_ENABLE_ADJOINT.
+ */
+int nursd_adjoint(nursd_plan_t plan, const nursd_c64* d_vol, nursd_c64* d_phasor, nursd_stream_t stream);
+
+/*
+ * Gradients of a real loss L(V), V = A(P, x) the complex NURSD-1 forward, given
+ * d_w = 2 dL/d conj(V) [Z][N][N] (for L = ||V - V_t||^2, d_w = 2 (V - V_t)):
+ *   d_grad_phasor [L][F] = A^H w                           (conjugate-Wirtinger
+ *                                                            gradient w.r.t. P)
+ *   d_grad_xy[l] = Re sum_f P[l][f] conj(d (A^H w)[l][f] / d(x_l, y_l))   [L][2]
+ * The position derivative differentiates the ES interpolation, i.e. it is the
+ * exact derivative of the implemented (NUFFT-approximated) operator.  Either
+ * output may be NULL (not both); d_phasor is needed for d_grad_xy.  Needs
+ * NURSD_ENABLE_ADJOINT.
+ */
+int nursd_grad_points(nursd_plan_t plan, const nursd_c64* d_w, const nursd_c64* d_phasor, nursd_c64* d_grad_phasor,
+                      float* d_grad_xy, nursd_stream_t stream);
 
 /*
  * Stage profiling.  Stages of the forward path, each one or more kernel

@@ -37,7 +37,7 @@ __all__ = [
     "transfer_functions", "propagate", "propagate_depth", "nursd_forward", "fbp_direct",
     "propagate_points", "idft_grid", "scaled_dft_matrix", "srsd_from_grid", "srsd_forward",
     "adjoint_spectrum", "nursd_adjoint", "nursd_loss", "nursd_gradients",
-    "frustum_volume", "frustum_extra_volume", "data_compression", "lateral_resolution",
+    "adjoint_spectrum_depthwise", "nudft_type1_lattice", "gradients_from_w", "frustum_volume", "frustum_extra_volume", "data_compression", "lateral_resolution",
 ]
 
 
@@ -346,6 +346,59 @@ def nursd_gradients(P, xy, center, pitch, N, depths, omega, V_target):
     gx = 2.0 * np.real(np.sum(P * np.conj(dx), axis=1)) * scale
     gy = 2.0 * np.real(np.sum(P * np.conj(dy), axis=1)) * scale
     return grad_P, np.stack([gx, gy], axis=1)
+
+
+def adjoint_spectrum_depthwise(V: np.ndarray, depths, omega, pitch: float) -> np.ndarray:
+    """:func:`adjoint_spectrum` building Ghat_{z,f} one (z, f) at a time (no full table in memory).
+
+    V: [Z][N][N] -> R [F][M][M], M = 2N.
+    """
+    V = np.asarray(V, dtype=np.complex128)
+    N = V.shape[-1]
+    M = 2 * N
+    D = np.conj(_idft_crop_matrix(M, N)).T
+    omega = np.asarray(omega, dtype=np.float64)
+    R = np.zeros((len(omega), M, M), dtype=np.complex128)
+    for iz, z in enumerate(np.asarray(depths, dtype=np.float64)):
+        Vt = (D @ V[iz] @ D.T) / (M * M)
+        for f, w in enumerate(omega):
+            R[f] += np.conj(transfer_function(rsd_kernel(M, pitch, z, w / C))) * Vt
+    return R
+
+
+def nudft_type1_lattice(P: np.ndarray, n_xy: np.ndarray, M: int) -> np.ndarray:
+    """:func:`nudft_type1` for samples on the lattice, theta = 2 pi n / M with integer n in I_M.
+
+    Then exp(-i k.theta) = exp(-2 pi i k.n / M), so the sum is the M x M DFT of the
+    gridded samples (computed with numpy.fft).  P: [L][F], n_xy: [L][2] ints -> [F][M][M].
+    """
+    P = np.asarray(P, dtype=np.complex128)
+    n_xy = np.asarray(n_xy)
+    U = np.empty((P.shape[1], M, M), dtype=np.complex128)
+    for f in range(P.shape[1]):
+        grid = np.zeros((M, M), dtype=np.complex128)
+        np.add.at(grid, (n_xy[:, 1] + M // 2, n_xy[:, 0] + M // 2), P[:, f])
+        U[f] = np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(grid)))
+    return U
+
+
+def gradients_from_w(R: np.ndarray, P_rows: np.ndarray, theta_rows: np.ndarray, pitch: float):
+    """Gradients at selected samples given the adjoint spectrum R of w = 2 dL/d conj(V).
+
+    grad_P[l] = sum_k R_f(k) e^{i k.theta_l} (= A^H w), and
+    grad_x[l] = (2 pi / (M delta)) Re sum_f P[l,f] conj(sum_k i kx R_f(k) e^{i k.theta_l})
+    (likewise y).  R: [F][M][M]; P_rows [S][F]; theta_rows [S][2].
+    """
+    M = R.shape[-1]
+    k = index_set(M).astype(np.float64)
+    gP = nudft_type2(R, theta_rows)
+    dx = nudft_type2(1j * k[None, None, :] * R, theta_rows)
+    dy = nudft_type2(1j * k[None, :, None] * R, theta_rows)
+    scale = 2.0 * math.pi / (M * pitch)
+    P_rows = np.asarray(P_rows, dtype=np.complex128)
+    gx = np.real(np.sum(P_rows * np.conj(dx), axis=1)) * scale
+    gy = np.real(np.sum(P_rows * np.conj(dy), axis=1)) * scale
+    return gP, np.stack([gx, gy], axis=1)
 
 
 # ------------------------------------------------ plan-level closed forms ---

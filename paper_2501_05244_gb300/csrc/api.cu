@@ -64,7 +64,8 @@ struct nursd_plan_s {
   float* deconv = nullptr;
   int2* cls = nullptr;
   float2* Gc = nullptr;
-  float* Bt = nullptr;  // temporal twiddles [T][2F]
+  float2* GcT = nullptr;  // transposed table [ncls][Z][F] for the adjoint (NURSD_ENABLE_ADJOINT)
+  float* Bt = nullptr;    // temporal twiddles [T][2F]
   // points
   int* bin_of = nullptr;
   int2* i0_orig = nullptr;
@@ -74,6 +75,8 @@ struct nursd_plan_s {
   int* sorted_l = nullptr;
   int2* i0_sorted = nullptr;
   float* w_sorted = nullptr;
+  float2* frac_orig = nullptr;
+  float2* frac_sorted = nullptr;
   // workspace
   float2* phasor = nullptr;
   float2* fine = nullptr;
@@ -221,7 +224,8 @@ int build_transfer_table(nursd_plan_s* p, cudaStream_t s) {
     if (rc == NURSD_OK)  // along jy, for each column kx
       rc = from_cuda(axis_pass(p, tmp, g, logM, false, C, M, C, (long long)M * C, C, (long long)M * C, M, -M / 2, M,
                                -M / 2, nullptr, nullptr, 1.f, s));
-    if (rc == NURSD_OK) rc = from_cuda(launch_gtf_compress(g, p->cls, p->ncls, M, F, zb, Z, z0, p->Gc, s));
+    if (rc == NURSD_OK)
+      rc = from_cuda(launch_gtf_compress(g, p->cls, p->ncls, M, F, zb, Z, z0, p->Gc, p->GcT, s));
   }
   if (rc == NURSD_OK) rc = from_cuda(cudaStreamSynchronize(s));
   cudaFree(g);
@@ -296,6 +300,115 @@ int run_propagate(nursd_plan_s* p, const float2* spec, void* out, cudaStream_t s
   return from_cuda(e);
 }
 
+// Adjoint of run_propagate up to the spectrum: R[k][f] = sum_z conj(Ghat) * M^-2 DFT_M[pad V_z](k),
+// V [Z][N][N] -> p->U [M][M][F].
+int run_adjoint_spectrum(nursd_plan_s* p, const float2* vol, cudaStream_t s) {
+  const int M = p->M, N = p->N, Z = p->Z, F = p->F;
+  const int logM = ilog2(M);
+  cudaError_t e;
+  {  // DFT along mx of every (z, my) row (contiguous in memory), full kx in I_M
+    StageTimer t(p, NURSD_STAGE_IFFT_Y, s, 1);
+    PanelArgs a = panel_base(p);
+    a.in = vol;
+    a.in_sb = N;
+    a.in_si = 1;
+    a.in_slo = (long long)N * N;
+    a.load_i_fastest = 1;
+    a.out = p->T1;
+    a.out_sb = (long long)M * Z;
+    a.out_si = Z;
+    a.out_slo = 1;
+    a.nin = N;
+    a.in_off = -N / 2;
+    a.nout = M;
+    a.out_off = -M / 2;
+    a.lo_total = Z;
+    a.CLO = panel_width(logM);
+    a.batch = N;
+    e = launch_panel_fft(logM, false, a, s);
+  }
+  if (e == cudaSuccess) {  // DFT along my for every kx, full ky, scaled by M^-2
+    StageTimer t(p, NURSD_STAGE_IFFT_X, s, 1);
+    e = axis_pass(p, p->T1, p->Y, logM, false, Z, M, Z, (long long)M * Z, Z, (long long)M * Z, N, -N / 2, M, -M / 2,
+                  nullptr, nullptr, 1.f / ((float)M * (float)M), s);
+  }
+  if (e == cudaSuccess) {
+    StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
+    e = launch_contract_adjoint(p->Y, p->GcT, p->cls, p->ncls, M, F, Z, p->U, s);
+  }
+  return from_cuda(e);
+}
+
+// Type 2 from a spectrum [M][M][C] onto the fine window: divide by
+// psi_hat(kx) psi_hat(ky) (folded into the first pass's input and batch
+// factors), zero-pad to the fine grid, inverse FFT along kx, then along ky.
+// plane_major = false: fine [W][W][C] (channel-last, for relay samples);
+// plane_major = true: fine [C][W][W] (one plane per channel, for voxel sets).
+int run_type2_to_fine(nursd_plan_s* p, const float2* spec, int C, bool plane_major, float scale, cudaStream_t s) {
+  const int M = p->M, W = p->W;
+  const int logf = ilog2(p->nf);
+  cudaError_t e;
+  {
+    StageTimer t(p, NURSD_STAGE_FFT_Y, s, 1);
+    PanelArgs a = panel_base(p);
+    a.in = spec;
+    a.in_sb = (long long)M * C;
+    a.in_si = C;
+    a.in_slo = 1;
+    a.mul_i = p->deconv;  // 1/psi_hat(kx), input index i <-> kx = i - M/2
+    a.mul_b = p->deconv;  // 1/psi_hat(ky), batch b <-> ky = b - M/2
+    a.out = p->R1;
+    a.out_sb = (long long)W * C;
+    a.out_si = C;
+    a.out_slo = 1;
+    a.nin = M;
+    a.in_off = -M / 2;
+    a.nout = W;
+    a.out_off = p->g0;
+    a.lo_total = C;
+    a.CLO = panel_width(logf);
+    a.batch = M;
+    e = launch_panel_fft(logf, true, a, s);
+  }
+  if (e == cudaSuccess) {
+    StageTimer t(p, NURSD_STAGE_FFT_X, s, 1);
+    PanelArgs a = panel_base(p);
+    a.in = p->R1;
+    a.nin = M;
+    a.in_off = -M / 2;
+    a.nout = W;
+    a.out_off = p->g0;
+    a.out = p->fine;
+    a.scale = scale;
+    const int cp = panel_width(logf);
+    if (!plane_major) {  // batch over x, channels c
+      a.in_sb = C;
+      a.in_si = (long long)W * C;
+      a.in_slo = 1;
+      a.out_sb = C;
+      a.out_si = (long long)W * C;
+      a.out_slo = 1;
+      a.lo_total = C;
+      a.CLO = cp;
+      a.batch = W;
+    } else {  // channels (x, c), written as fine[c][y][x] with x fastest
+      a.in_si = (long long)W * C;
+      a.in_shi = C;
+      a.in_slo = 1;
+      a.out_si = W;
+      a.out_shi = 1;
+      a.out_slo = (long long)W * W;
+      a.hi_total = W;
+      a.lo_total = C;
+      a.CLO = C >= 4 ? 4 : (C >= 2 ? 2 : 1);
+      a.CHI = cp / a.CLO;
+      a.store_hi_fastest = 1;
+    }
+    e = launch_panel_fft(logf, true, a, s);
+  }
+  return from_cuda(e);
+}
+
 int check_plan(nursd_plan_t p) { return p ? NURSD_OK : NURSD_ERR_INVALID_ARG; }
 
 }  // namespace
@@ -346,7 +459,8 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
   if (d->upsample != 2) return NURSD_ERR_UNSUPPORTED;
   if (d->kernel_width < 4 || d->kernel_width > kMaxKernelWidth) return NURSD_ERR_UNSUPPORTED;
   if (d->max_points < 0 || d->max_points > (1 << 26)) return NURSD_ERR_INVALID_ARG;
-  if ((d->flags & ~NURSD_OUTPUT_MAGNITUDE) != 0) return NURSD_ERR_UNSUPPORTED;
+  if ((d->flags & ~(NURSD_OUTPUT_MAGNITUDE | NURSD_ENABLE_ADJOINT)) != 0) return NURSD_ERR_UNSUPPORTED;
+  if ((d->flags & NURSD_ENABLE_ADJOINT) && d->Z > 256) return NURSD_ERR_UNSUPPORTED;
 
   nursd_plan_s* p = new (std::nothrow) nursd_plan_s();
   if (!p) return NURSD_ERR_OOM;
@@ -426,10 +540,13 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
             p->alloc(p->counts, (size_t)nbins * nchunks) && p->alloc(p->bin_start, nbins + 1) &&
             p->alloc(p->sorted_l, maxL) && p->alloc(p->i0_sorted, maxL) &&
             p->alloc(p->w_sorted, (size_t)maxL * 2 * p->w) && p->alloc(p->phasor, (size_t)maxL * p->F) &&
-            p->alloc(p->fine, (size_t)p->W * p->W * p->F) && p->alloc(p->R1, (size_t)p->W * p->M * p->F) &&
+            p->alloc(p->frac_orig, maxL) && p->alloc(p->frac_sorted, maxL) &&
+            p->alloc(p->fine, (size_t)p->W * p->W * std::max(p->F, p->Z)) &&
+            p->alloc(p->R1, (size_t)p->W * p->M * std::max(p->F, p->Z)) &&
             p->alloc(p->U, (size_t)p->M * p->M * p->F) && p->alloc(p->Y, (size_t)p->M * p->M * p->Z) &&
             p->alloc(p->T1, (size_t)p->M * p->N * p->Z);
   if (ok && p->T > 0) ok = p->alloc(p->Bt, Bt.size());
+  if (ok && (p->flags & NURSD_ENABLE_ADJOINT)) ok = p->alloc(p->GcT, (size_t)p->ncls * p->F * p->Z);
   if (!ok) {
     delete p;
     return NURSD_ERR_OOM;
@@ -487,7 +604,8 @@ int nursd_set_points(nursd_plan_t p, int32_t L, const float* d_xy, nursd_stream_
   {
     StageTimer t(p, NURSD_STAGE_POINTS, static_cast<cudaStream_t>(stream), L > 0 ? 4 : 0);
     rc = from_cuda(launch_points(a, p->bin_of, p->i0_orig, p->w_orig, p->counts, p->bin_start, p->sorted_l,
-                                 p->i0_sorted, p->w_sorted, static_cast<cudaStream_t>(stream)));
+                                 p->i0_sorted, p->w_sorted, static_cast<cudaStream_t>(stream), p->frac_orig,
+                                 p->frac_sorted));
   }
   if (rc == NURSD_OK) p->L = L;
   return rc;
@@ -534,6 +652,103 @@ int nursd_forward(nursd_plan_t p, const float* d_hist, void* d_out, nursd_stream
   }
   if (rc == NURSD_OK) rc = run_nufft1(p, p->phasor, p->U, s);
   if (rc == NURSD_OK) rc = run_propagate(p, p->U, d_out, s);
+  return rc;
+}
+
+int nursd_adjoint(nursd_plan_t p, const nursd_c64* d_vol, nursd_c64* d_phasor, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || !p->GcT || p->L < 0 || !d_vol || !aligned(d_vol, 8)) return NURSD_ERR_INVALID_ARG;
+  if (p->L > 0 && (!d_phasor || !aligned(d_phasor, 8))) return NURSD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = run_adjoint_spectrum(p, reinterpret_cast<const float2*>(d_vol), s);
+  if (rc == NURSD_OK) rc = run_type2_to_fine(p, p->U, p->F, false, 1.f, s);
+  if (rc == NURSD_OK) {
+    StageTimer t(p, NURSD_STAGE_SPREAD, s, p->L > 0 ? 1 : 0);
+    InterpArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.fine = p->fine;
+    a.W = p->W;
+    a.F = p->F;
+    a.width = p->w;
+    a.L = p->L;
+    a.beta = p->beta;
+    a.sorted_l = p->sorted_l;
+    a.i0 = p->i0_sorted;
+    a.wts = p->w_sorted;
+    a.frac = p->frac_sorted;
+    a.scale = 1.f;
+    a.out = reinterpret_cast<float2*>(d_phasor);
+    rc = from_cuda(launch_interp_points(a, s));
+  }
+  return rc;
+}
+
+int nursd_grad_points(nursd_plan_t p, const nursd_c64* d_w, const nursd_c64* d_phasor, nursd_c64* d_grad_phasor,
+                      float* d_grad_xy, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || !p->GcT || p->L < 0 || !d_w || !aligned(d_w, 8)) return NURSD_ERR_INVALID_ARG;
+  if (!d_grad_phasor && !d_grad_xy) return NURSD_ERR_INVALID_ARG;
+  if (p->L > 0 && d_grad_xy && (!d_phasor || !aligned(d_phasor, 8) || !aligned(d_grad_xy, 8)))
+    return NURSD_ERR_INVALID_ARG;
+  if (p->L > 0 && d_grad_phasor && !aligned(d_grad_phasor, 8)) return NURSD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = run_adjoint_spectrum(p, reinterpret_cast<const float2*>(d_w), s);
+  if (rc == NURSD_OK) rc = run_type2_to_fine(p, p->U, p->F, false, 1.f, s);
+  if (rc == NURSD_OK) {
+    StageTimer t(p, NURSD_STAGE_SPREAD, s, p->L > 0 ? 1 : 0);
+    InterpArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.fine = p->fine;
+    a.W = p->W;
+    a.F = p->F;
+    a.width = p->w;
+    a.L = p->L;
+    a.beta = p->beta;
+    a.dudx = (float)(2.0 / p->pitch);
+    a.sorted_l = p->sorted_l;
+    a.i0 = p->i0_sorted;
+    a.wts = p->w_sorted;
+    a.frac = p->frac_sorted;
+    a.scale = 1.f;
+    a.out = reinterpret_cast<float2*>(d_grad_phasor);
+    a.P = reinterpret_cast<const float2*>(d_phasor);
+    a.gxy = d_grad_xy;
+    rc = from_cuda(launch_interp_points(a, s));
+  }
+  return rc;
+}
+
+int nursd_forward_points(nursd_plan_t p, const nursd_c64* d_phasor, int32_t K, const float* d_vox_xy,
+                         nursd_c64* d_out, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || p->L < 0 || K < 0) return NURSD_ERR_INVALID_ARG;
+  if (p->L > 0 && (!d_phasor || !aligned(d_phasor, 8))) return NURSD_ERR_INVALID_ARG;
+  if (K > 0 && (!d_vox_xy || !d_out || !aligned(d_vox_xy, 8) || !aligned(d_out, 8))) return NURSD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int M = p->M;
+  int rc = run_nufft1(p, reinterpret_cast<const float2*>(d_phasor), p->U, s);
+  if (rc == NURSD_OK) {
+    StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
+    rc = from_cuda(launch_contract(p->U, p->Gc, p->cls, p->ncls, M, p->F, p->Z, p->Y, s));
+  }
+  if (rc == NURSD_OK) rc = run_type2_to_fine(p, p->Y, p->Z, true, 1.f / ((float)M * (float)M), s);
+  if (rc == NURSD_OK && K > 0) {
+    StageTimer t(p, NURSD_STAGE_IFFT_Y, s, 1);
+    PlaneInterpArgs a;
+    a.fine = p->fine;
+    a.W = p->W;
+    a.Z = p->Z;
+    a.K = K;
+    a.width = p->w;
+    a.g0 = p->g0;
+    a.beta = p->beta;
+    a.cx = p->cx;
+    a.cy = p->cy;
+    a.inv_fine_pitch = 2.0 / p->pitch;
+    a.half_extent = 0.5 * p->N * p->pitch;
+    a.vox = d_vox_xy;
+    a.scale = 1.f;
+    a.out = reinterpret_cast<float2*>(d_out);
+    a.status = p->status;
+    rc = from_cuda(launch_interp_planes(a, s));
+  }
   return rc;
 }
 

@@ -1,5 +1,10 @@
 // RSD transfer-function multiply with the coherent frequency sum (Eq. 4 product,
-// frequency integral of Eq. 2): Y_z(k) = sum_f U_f(k) Ghat_{z,f}(k).
+// frequency integral of Eq. 2): Y_z(k) = sum_f U_f(k) Ghat_{z,f}(k), and its
+// adjoint R_f(k) = sum_z conj(Ghat_{z,f}(k)) Y'_z(k).
+//
+// Generic form: Out[k][j] = sum_r In[k][r] * T[class(k)][r][j] (T conjugated for
+// the adjoint), with (r, j) = (f, z) forward on the table Gc[class][f][z] and
+// (r, j) = (z, f) for the adjoint on its transposed copy GcT[class][z][f].
 //
 // Ghat_{z,f} is even in kx and ky and symmetric under kx <-> ky (G depends on
 // |j| only), so it is stored once per class {(+-p, +-q), (+-q, +-p)},
@@ -20,7 +25,8 @@ constexpr int kClsPerCta = 8;
 
 __device__ __forceinline__ int wrap_index(int k, int M) { return (k + M / 2) & (M - 1); }
 
-template <int ZPL>
+// Names follow the forward direction: F is the reduced extent, Z the per-lane one.
+template <int ZPL, bool CONJ>
 __global__ void __launch_bounds__(kClsPerCta * 32, 2) contract_kernel(const float2* __restrict__ U,
                                                                    const float2* __restrict__ Gc,
                                                                    const int2* __restrict__ cls_pq, int ncls, int M,
@@ -69,6 +75,10 @@ __global__ void __launch_bounds__(kClsPerCta * 32, 2) contract_kernel(const floa
       for (int i = 0; i < ZPL; ++i)
         gv[i] = (z0 + i < Z) ? __ldg(g + (size_t)f * Z + i) : make_float2(0.f, 0.f);
     }
+    if (CONJ) {
+#pragma unroll
+      for (int i = 0; i < ZPL; ++i) gv[i].y = -gv[i].y;
+    }
     const float4* u4 = reinterpret_cast<const float4*>(my + f * 8);
     float2 u[8];
 #pragma unroll
@@ -102,31 +112,42 @@ __global__ void __launch_bounds__(kClsPerCta * 32, 2) contract_kernel(const floa
   }
 }
 
-template <int ZPL>
+template <int ZPL, bool CONJ>
 cudaError_t launch_zpl(const float2* U, const float2* Gc, const int2* cls_pq, int ncls, int M, int F, int Z,
                        float2* Y, cudaStream_t s) {
   const size_t smem = sizeof(float2) * kClsPerCta * F * 8;
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(contract_kernel<ZPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(contract_kernel<ZPL, CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(sizeof(float2) * kClsPerCta * 256 * 8));
     if (e != cudaSuccess) return e;
     configured = true;
   }
   dim3 grid((ncls + kClsPerCta - 1) / kClsPerCta, (Z + 32 * ZPL - 1) / (32 * ZPL));
-  contract_kernel<ZPL><<<grid, kClsPerCta * 32, smem, s>>>(U, Gc, cls_pq, ncls, M, F, Z, Y);
+  contract_kernel<ZPL, CONJ><<<grid, kClsPerCta * 32, smem, s>>>(U, Gc, cls_pq, ncls, M, F, Z, Y);
   return cudaGetLastError();
+}
+
+template <bool CONJ>
+cudaError_t launch_dir(const float2* In, const float2* T, const int2* cls_pq, int ncls, int M, int R, int J,
+                       float2* Out, cudaStream_t s) {
+  if (R > 256) return cudaErrorInvalidValue;
+  // outputs per lane (a CTA column covers 32*ZPL of them): 4 for deep extents, fewer for shallow ones.
+  if (J > 64) return launch_zpl<4, CONJ>(In, T, cls_pq, ncls, M, R, J, Out, s);
+  if (J > 32) return launch_zpl<2, CONJ>(In, T, cls_pq, ncls, M, R, J, Out, s);
+  return launch_zpl<1, CONJ>(In, T, cls_pq, ncls, M, R, J, Out, s);
 }
 
 }  // namespace
 
 cudaError_t launch_contract(const float2* U, const float2* Gc, const int2* cls_pq, int ncls, int M, int F, int Z,
                             float2* Y, cudaStream_t s) {
-  if (F > 256) return cudaErrorInvalidValue;
-  // depths per lane (a CTA column covers 32*ZPL depths): 4 for deep volumes, fewer for shallow ones.
-  if (Z > 64) return launch_zpl<4>(U, Gc, cls_pq, ncls, M, F, Z, Y, s);
-  if (Z > 32) return launch_zpl<2>(U, Gc, cls_pq, ncls, M, F, Z, Y, s);
-  return launch_zpl<1>(U, Gc, cls_pq, ncls, M, F, Z, Y, s);
+  return launch_dir<false>(U, Gc, cls_pq, ncls, M, F, Z, Y, s);
+}
+
+cudaError_t launch_contract_adjoint(const float2* Yt, const float2* GcT, const int2* cls_pq, int ncls, int M, int F,
+                                    int Z, float2* R, cudaStream_t s) {
+  return launch_dir<true>(Yt, GcT, cls_pq, ncls, M, Z, F, R, s);
 }
 
 }  // namespace nursd

@@ -40,6 +40,7 @@ __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int q) 
 template <int LOGN, int CP, int NT, int R, bool INV>
 __device__ __forceinline__ void stockham_pass(float2* sm, int Ns, const float2* __restrict__ tw) {
   constexpr int n = 1 << LOGN;
+  constexpr int SR = CP + 1;  // padded row stride: conflict-free for both load orders
   constexpr int NB = (n / R) * CP;
   constexpr int PER = (NB + NT - 1) / NT;
   float2 v[PER][R];
@@ -51,7 +52,7 @@ __device__ __forceinline__ void stockham_pass(float2* sm, int Ns, const float2* 
       const int j = jb / CP, q = jb % CP;
       const int k = j & (Ns - 1);
 #pragma unroll
-      for (int t = 0; t < R; ++t) v[r][t] = sm[(j + t * (n / R)) * CP + q];
+      for (int t = 0; t < R; ++t) v[r][t] = sm[(j + t * (n / R)) * SR + q];
       if (Ns > 1) {
 #pragma unroll
         for (int t = 1; t < R; ++t) v[r][t] = cmul(v[r][t], twiddle<INV>(tw, (k * t) << twstride_log));
@@ -74,7 +75,7 @@ __device__ __forceinline__ void stockham_pass(float2* sm, int Ns, const float2* 
       const int k = j & (Ns - 1);
       const int o = (j - k) * R + k;
 #pragma unroll
-      for (int t = 0; t < R; ++t) sm[(o + t * Ns) * CP + q] = v[r][t];
+      for (int t = 0; t < R; ++t) sm[(o + t * Ns) * SR + q] = v[r][t];
     }
   }
   __syncthreads();
@@ -83,6 +84,7 @@ __device__ __forceinline__ void stockham_pass(float2* sm, int Ns, const float2* 
 template <int LOGN, int CP, int NT, bool INV>
 __global__ void __launch_bounds__(NT) panel_fft_kernel(const PanelArgs a) {
   constexpr int n = 1 << LOGN;
+  constexpr int SR = CP + 1;
   extern __shared__ float2 sm[];
   const int tid = threadIdx.x;
   const int nlo = (a.lo_total + a.CLO - 1) / a.CLO;
@@ -93,17 +95,30 @@ __global__ void __launch_bounds__(NT) panel_fft_kernel(const PanelArgs a) {
   // ---- load the input window (zero elsewhere)
   const float2* __restrict__ inb = a.in + (long long)b * a.in_sb;
   for (int idx = tid; idx < a.nin * CP; idx += NT) {
-    const int i = idx / CP, q = idx % CP;
+    int i, q;
+    if (a.load_i_fastest) {
+      i = idx % a.nin;
+      q = idx / a.nin;
+    } else {
+      i = idx / CP;
+      q = idx % CP;
+    }
     const int qh = q / a.CLO, ql = q % a.CLO;
     const int hi = hi0 + qh, lo = lo0 + ql;
     float2 v = make_float2(0.f, 0.f);
-    if (qh < a.CHI && hi < a.hi_total && lo < a.lo_total)
+    if (hi < a.hi_total && lo < a.lo_total) {
       v = __ldg(inb + i * a.in_si + hi * a.in_shi + lo * a.in_slo);
-    sm[((i + a.in_off) & (n - 1)) * CP + q] = v;
+      if (a.mul_i) {
+        const float m = __ldg(a.mul_i + i);
+        v.x *= m;
+        v.y *= m;
+      }
+    }
+    sm[((i + a.in_off) & (n - 1)) * SR + q] = v;
   }
   for (int idx = tid; idx < (n - a.nin) * CP; idx += NT) {
     const int j = idx / CP + a.nin, q = idx % CP;
-    sm[((j + a.in_off) & (n - 1)) * CP + q] = make_float2(0.f, 0.f);
+    sm[((j + a.in_off) & (n - 1)) * SR + q] = make_float2(0.f, 0.f);
   }
   __syncthreads();
 
@@ -120,7 +135,12 @@ __global__ void __launch_bounds__(NT) panel_fft_kernel(const PanelArgs a) {
   const float sb = a.scale * (a.mul_b ? a.mul_b[b] : 1.f);
   for (int idx = tid; idx < a.nout * CP; idx += NT) {
     int o, qh, ql;
-    if (a.store_hi_fastest) {
+    if (a.store_o_fastest) {
+      o = idx % a.nout;
+      const int q = idx / a.nout;
+      qh = q / a.CLO;
+      ql = q % a.CLO;
+    } else if (a.store_hi_fastest) {
       qh = idx % a.CHI;
       const int rest = idx / a.CHI;
       ql = rest % a.CLO;
@@ -132,8 +152,8 @@ __global__ void __launch_bounds__(NT) panel_fft_kernel(const PanelArgs a) {
       ql = q % a.CLO;
     }
     const int hi = hi0 + qh, lo = lo0 + ql;
-    if (qh >= a.CHI || hi >= a.hi_total || lo >= a.lo_total) continue;
-    float2 v = sm[((o + a.out_off) & (n - 1)) * CP + qh * a.CLO + ql];
+    if (hi >= a.hi_total || lo >= a.lo_total) continue;
+    float2 v = sm[((o + a.out_off) & (n - 1)) * SR + qh * a.CLO + ql];
     const float s = sb * (a.mul_o ? __ldg(a.mul_o + o) : 1.f);
     v.x *= s;
     v.y *= s;
@@ -148,7 +168,7 @@ __global__ void __launch_bounds__(NT) panel_fft_kernel(const PanelArgs a) {
 
 template <int LOGN, int CP, int NT, bool INV>
 cudaError_t launch_one(const PanelArgs& a, cudaStream_t s) {
-  const size_t smem = sizeof(float2) * (size_t(1) << LOGN) * CP;
+  const size_t smem = sizeof(float2) * (size_t(1) << LOGN) * (CP + 1);
   static bool configured = false;  // one attribute call per instantiation and process
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(panel_fft_kernel<LOGN, CP, NT, INV>,
@@ -170,7 +190,10 @@ cudaError_t launch_dir(bool inverse, const PanelArgs& a, cudaStream_t s) {
 
 }  // namespace
 
-int panel_width(int logn) { return logn >= 11 ? 8 : 16; }
+// Channels per CTA: 16 up to n = 512, then fewer so that a CTA's buffer stays
+// near 68 KB and three CTAs share an SM (overlapping one's loads with another's
+// transform).
+int panel_width(int logn) { return logn <= 9 ? 16 : (logn == 10 ? 8 : 4); }
 
 cudaError_t launch_panel_fft(int logn, bool inverse, const PanelArgs& a, cudaStream_t s) {
   if (a.CHI * a.CLO != panel_width(logn) || a.nin > (1 << logn) || a.nout > (1 << logn) || a.batch < 1 ||
@@ -183,9 +206,9 @@ cudaError_t launch_panel_fft(int logn, bool inverse, const PanelArgs& a, cudaStr
     case 6: return launch_dir<6, 16, 256>(inverse, a, s);
     case 7: return launch_dir<7, 16, 256>(inverse, a, s);
     case 8: return launch_dir<8, 16, 256>(inverse, a, s);
-    case 9: return launch_dir<9, 16, 512>(inverse, a, s);
-    case 10: return launch_dir<10, 16, 512>(inverse, a, s);
-    case 11: return launch_dir<11, 8, 512>(inverse, a, s);
+    case 9: return launch_dir<9, 16, 256>(inverse, a, s);
+    case 10: return launch_dir<10, 8, 256>(inverse, a, s);
+    case 11: return launch_dir<11, 4, 256>(inverse, a, s);
     default: return cudaErrorInvalidValue;
   }
 }

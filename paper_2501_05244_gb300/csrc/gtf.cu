@@ -31,7 +31,8 @@ __global__ void gtf_generate_kernel(float2* __restrict__ g, int M, double pitch,
 }
 
 __global__ void gtf_compress_kernel(const float2* __restrict__ Gfull, const int2* __restrict__ cls_pq, int ncls,
-                                    int M, int F, int ZB, int Z, int z0, float2* __restrict__ Gc) {
+                                    int M, int F, int ZB, int Z, int z0, float2* __restrict__ Gc,
+                                    float2* __restrict__ GcT) {
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long total = (long long)ncls * F * ZB;
   if (idx >= total) return;
@@ -40,7 +41,9 @@ __global__ void gtf_compress_kernel(const float2* __restrict__ Gfull, const int2
   const int c = (int)(idx / ((long long)ZB * F));
   const int2 pq = cls_pq[c];
   const int ix = (pq.x + M / 2) & (M - 1), iy = (pq.y + M / 2) & (M - 1);  // representative (kx, ky) = (p, q)
-  Gc[((size_t)c * F + f) * Z + z0 + zb] = Gfull[((size_t)iy * M + ix) * ZB * F + (size_t)zb * F + f];
+  const float2 v = Gfull[((size_t)iy * M + ix) * ZB * F + (size_t)zb * F + f];
+  Gc[((size_t)c * F + f) * Z + z0 + zb] = v;
+  if (GcT) GcT[((size_t)c * Z + z0 + zb) * F + f] = v;
 }
 
 }  // namespace
@@ -53,9 +56,10 @@ cudaError_t launch_gtf_generate(float2* g, int M, double pitch, const double* d_
 }
 
 cudaError_t launch_gtf_compress(const float2* Gfull, const int2* cls_pq, int ncls, int M, int F, int ZB, int Z,
-                                int z0, float2* Gc, cudaStream_t s) {
+                                int z0, float2* Gc, float2* GcT, cudaStream_t s) {
   const long long total = (long long)ncls * F * ZB;
-  gtf_compress_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(Gfull, cls_pq, ncls, M, F, ZB, Z, z0, Gc);
+  gtf_compress_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(Gfull, cls_pq, ncls, M, F, ZB, Z, z0, Gc,
+                                                                       GcT);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,176 @@
+// NUFFT type-2 interpolation (Sec. 6: NUFFT-2 reverses the three type-1 steps,
+// the last being interpolation of the blurred signal at the non-uniform points).
+//
+// After deconvolution and the inverse fine-grid FFT, the value at a point with
+// fine coordinate u is sum over its w x w footprint of b[g] phi(2(gx-ux)/w)
+// phi(2(gy-uy)/w) -- exactly the adjoint of the spread.
+//
+// interp_points: relay samples on a channel-last grid [W][W][F]; one warp per
+//   sample, one lane per channel, so each tap is a 256-byte coalesced row.  With
+//   GRAD the same taps also give d/du of the value through phi'(z) and are
+//   reduced against the sample's phasors into the position gradient.
+// interp_planes: voxels of each depth plane on a plane-major grid [Z][W][W];
+//   one thread per voxel (rows of w contiguous cells).
+#include "nursd_internal.cuh"
+
+namespace nursd {
+namespace {
+
+template <int WID, bool GRAD>
+__global__ void __launch_bounds__(256) interp_points_kernel(const InterpArgs a) {
+  const int slot = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (slot >= a.L) return;
+  const int l = __ldg(a.sorted_l + slot);
+  const int2 o = __ldg(a.i0 + slot);
+  float wx[WID], wy[WID], dwx[WID], dwy[WID];
+#pragma unroll
+  for (int t = 0; t < WID; ++t) {
+    wx[t] = __ldg(a.wts + (size_t)slot * 2 * WID + t);
+    wy[t] = __ldg(a.wts + (size_t)slot * 2 * WID + WID + t);
+  }
+  if (GRAD) {
+    // d/du phi(2 (i0 + t - u) / w) = phi(z) beta z (2/w) / sqrt(1 - z^2), z = 2 (t - frac) / w
+    const float2 fr = __ldg(a.frac + slot);
+#pragma unroll
+    for (int t = 0; t < WID; ++t) {
+      const float zx = 2.f * ((float)t - fr.x) / WID, zy = 2.f * ((float)t - fr.y) / WID;
+      const float qx = 1.f - zx * zx, qy = 1.f - zy * zy;
+      dwx[t] = qx > 0.f ? wx[t] * a.beta * zx * (2.f / WID) * rsqrtf(qx) : 0.f;
+      dwy[t] = qy > 0.f ? wy[t] * a.beta * zy * (2.f / WID) * rsqrtf(qy) : 0.f;
+    }
+  }
+  float gsx = 0.f, gsy = 0.f;
+  for (int f0 = 0; f0 < a.F; f0 += 32) {
+    const int f = f0 + lane;
+    if (f >= a.F) break;
+    float2 acc = make_float2(0.f, 0.f), ax = make_float2(0.f, 0.f), ay = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int ty = 0; ty < WID; ++ty) {
+      const float2* row = a.fine + ((size_t)(o.y + ty) * a.W + o.x) * a.F + f;
+      float2 rs = make_float2(0.f, 0.f), rd = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int tx = 0; tx < WID; ++tx) {
+        const float2 v = __ldg(row + (size_t)tx * a.F);
+        rs.x = fmaf(v.x, wx[tx], rs.x);
+        rs.y = fmaf(v.y, wx[tx], rs.y);
+        if (GRAD) {
+          rd.x = fmaf(v.x, dwx[tx], rd.x);
+          rd.y = fmaf(v.y, dwx[tx], rd.y);
+        }
+      }
+      acc.x = fmaf(rs.x, wy[ty], acc.x);
+      acc.y = fmaf(rs.y, wy[ty], acc.y);
+      if (GRAD) {
+        ax.x = fmaf(rd.x, wy[ty], ax.x);
+        ax.y = fmaf(rd.y, wy[ty], ax.y);
+        ay.x = fmaf(rs.x, dwy[ty], ay.x);
+        ay.y = fmaf(rs.y, dwy[ty], ay.y);
+      }
+    }
+    if (a.out) a.out[(size_t)l * a.F + f] = make_float2(acc.x * a.scale, acc.y * a.scale);
+    if (GRAD) {
+      const float2 p = __ldg(a.P + (size_t)l * a.F + f);
+      gsx += p.x * ax.x + p.y * ax.y;  // Re(p conj(ax))
+      gsy += p.x * ay.x + p.y * ay.y;
+    }
+  }
+  if (GRAD) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      gsx += __shfl_xor_sync(0xffffffffu, gsx, off);
+      gsy += __shfl_xor_sync(0xffffffffu, gsy, off);
+    }
+    if (lane == 0) {
+      const float s = a.scale * a.dudx;
+      a.gxy[2 * l] = gsx * s;
+      a.gxy[2 * l + 1] = gsy * s;
+    }
+  }
+}
+
+template <int WID>
+__global__ void __launch_bounds__(256) interp_planes_kernel(const PlaneInterpArgs a) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)a.Z * a.K) return;
+  const int z = (int)(idx / a.K);
+  const double dx = (double)a.vox[2 * idx] - a.cx, dy = (double)a.vox[2 * idx + 1] - a.cy;
+  if (!(fabs(dx) <= a.half_extent && fabs(dy) <= a.half_extent)) {
+    atomicOr(a.status, 1);
+    a.out[idx] = make_float2(0.f, 0.f);
+    return;
+  }
+  const double ux = dx * a.inv_fine_pitch, uy = dy * a.inv_fine_pitch;
+  const int ix = (int)ceil(ux - 0.5 * WID), iy = (int)ceil(uy - 0.5 * WID);
+  float wx[WID], wy[WID];
+#pragma unroll
+  for (int t = 0; t < WID; ++t) {
+    const float zx = (float)(((double)(ix + t) - ux) * (2.0 / WID));
+    const float zy = (float)(((double)(iy + t) - uy) * (2.0 / WID));
+    wx[t] = fabsf(zx) < 1.f ? expf(a.beta * (sqrtf(1.f - zx * zx) - 1.f)) : 0.f;
+    wy[t] = fabsf(zy) < 1.f ? expf(a.beta * (sqrtf(1.f - zy * zy) - 1.f)) : 0.f;
+  }
+  const int rx = min(max(ix - a.g0, 0), a.W - WID), ry = min(max(iy - a.g0, 0), a.W - WID);
+  const float2* plane = a.fine + (size_t)z * a.W * a.W;
+  float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int ty = 0; ty < WID; ++ty) {
+    const float2* row = plane + (size_t)(ry + ty) * a.W + rx;
+    float2 rs = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int tx = 0; tx < WID; ++tx) {
+      const float2 v = __ldg(row + tx);
+      rs.x = fmaf(v.x, wx[tx], rs.x);
+      rs.y = fmaf(v.y, wx[tx], rs.y);
+    }
+    acc.x = fmaf(rs.x, wy[ty], acc.x);
+    acc.y = fmaf(rs.y, wy[ty], acc.y);
+  }
+  a.out[idx] = make_float2(acc.x * a.scale, acc.y * a.scale);
+}
+
+template <int WID>
+cudaError_t points_w(const InterpArgs& a, cudaStream_t s) {
+  const unsigned blocks = (unsigned)(((long long)a.L * 32 + 255) / 256);
+  if (a.gxy)
+    interp_points_kernel<WID, true><<<blocks, 256, 0, s>>>(a);
+  else
+    interp_points_kernel<WID, false><<<blocks, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int WID>
+cudaError_t planes_w(const PlaneInterpArgs& a, cudaStream_t s) {
+  const long long n = (long long)a.Z * a.K;
+  interp_planes_kernel<WID><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_interp_points(const InterpArgs& a, cudaStream_t s) {
+  if (a.L <= 0) return cudaSuccess;
+  if (a.gxy && (!a.P || !a.frac)) return cudaErrorInvalidValue;
+  switch (a.width) {
+    case 4: return points_w<4>(a, s);
+    case 5: return points_w<5>(a, s);
+    case 6: return points_w<6>(a, s);
+    case 7: return points_w<7>(a, s);
+    case 8: return points_w<8>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_interp_planes(const PlaneInterpArgs& a, cudaStream_t s) {
+  if ((long long)a.Z * a.K <= 0) return cudaSuccess;
+  switch (a.width) {
+    case 4: return planes_w<4>(a, s);
+    case 5: return planes_w<5>(a, s);
+    case 6: return planes_w<6>(a, s);
+    case 7: return planes_w<7>(a, s);
+    case 8: return planes_w<8>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace nursd

@@ -44,10 +44,13 @@ struct PanelArgs {
   int hi_total, lo_total;  // channel extents
   int CHI, CLO;            // panel shape, CHI*CLO == CP
   int batch;
+  const float* mul_i;  // optional real factor per input index (applied on load)
   const float* mul_o;  // optional real factor per output index
   const float* mul_b;  // optional real factor per batch item
   float scale;
-  int store_hi_fastest;
+  int load_i_fastest;    // consecutive threads load consecutive i (FFT axis contiguous in memory)
+  int store_hi_fastest;  // consecutive threads store consecutive hi channels
+  int store_o_fastest;   // consecutive threads store consecutive outputs o
   const float2* twiddle;  // e^{-2 pi i q / 2^kTwiddleLog}
 };
 
@@ -77,8 +80,10 @@ struct PointsArgs {
 // i0_orig [L], w_orig [L][2w]; counts needs nbins*nchunks ints (nchunks =
 // ceil(L/1024)).  Sorted outputs: sorted_l [L] (original index), i0_sorted,
 // w_sorted, and bin_start [nbins+1] (first sorted slot of each tile).
+// frac_sorted (optional) receives u - i0 per axis of each sorted sample.
 cudaError_t launch_points(const PointsArgs& a, int* bin_of, int2* i0_orig, float* w_orig, int* counts,
-                          int* bin_start, int* sorted_l, int2* i0_sorted, float* w_sorted, cudaStream_t s);
+                          int* bin_start, int* sorted_l, int2* i0_sorted, float* w_sorted, cudaStream_t s,
+                          float2* frac_orig = nullptr, float2* frac_sorted = nullptr);
 
 // ---------------------------------------------------------------- spread
 cudaError_t launch_spread(const float2* P, int F, const int* bin_start, const int* sorted_l,
@@ -90,12 +95,53 @@ cudaError_t launch_spread(const float2* P, int F, const int* bin_start, const in
 cudaError_t launch_contract(const float2* U, const float2* Gc, const int2* cls_pq, int ncls, int M,
                             int F, int Z, float2* Y, cudaStream_t s);
 
+// Adjoint: R[k][f] = sum_z Yt[k][z] * conj(GcT[cls(k)][z][f]).
+cudaError_t launch_contract_adjoint(const float2* Yt, const float2* GcT, const int2* cls_pq, int ncls, int M, int F,
+                                    int Z, float2* R, cudaStream_t s);
+
+// ------------------------------------------------------------ interpolation
+// Type-2 interpolation at the sorted relay samples from a channel-last fine
+// grid [W][W][F]: out[l][f] = scale * sum_taps fine[i0y+ty][i0x+tx][f] wx wy.
+// With grad: also d/dx, d/dy of that value (ES kernel derivative) reduced
+// against P: gxy[l] = scale_g * Re sum_f P[l][f] conj(d out[l][f] / d(x,y)).
+struct InterpArgs {
+  const float2* fine;
+  int W, F, width, L;
+  float beta, dudx;           // ES shape; fine cells per metre (sigma / delta)
+  const int* sorted_l;
+  const int2* i0;
+  const float* wts;           // [L][2w] sorted
+  const float2* frac;         // [L] sorted: u - i0 per axis
+  float scale;
+  float2* out;                // [L][F] (original sample order) or null
+  const float2* P;            // [L][F] for the gradient reduction
+  float* gxy;                 // [L][2] or null
+};
+cudaError_t launch_interp_points(const InterpArgs& a, cudaStream_t s);
+
+// Type-2 interpolation at per-plane voxels from a plane-major fine grid
+// [Z][W][W]: out[z][v] = scale * sum_taps fine[z][..][..] wx wy, positions
+// vox[z][v] (metres) mapped like relay samples; out-of-aperture voxels flag
+// status bit 1 and give 0.
+struct PlaneInterpArgs {
+  const float2* fine;
+  int W, Z, K, width, g0;
+  float beta;
+  double cx, cy, inv_fine_pitch, half_extent;
+  const float* vox;  // [Z][K][2]
+  float scale;
+  float2* out;       // [Z][K]
+  int* status;
+};
+cudaError_t launch_interp_planes(const PlaneInterpArgs& a, cudaStream_t s);
+
 // ------------------------------------------------------- transfer function
 // g[jy][jx][zb*F + f] = exp(i k_f r)/r, r = sqrt((jx d)^2 + (jy d)^2 + z_zb^2), FP64 phase.
 cudaError_t launch_gtf_generate(float2* g, int M, double pitch, const double* d_z, int ZB,
                                 const double* d_k, int F, cudaStream_t s);
-// Gc[(c*F + f)*Z + z0 + zb] = Gfull[rep(c)][zb*F + f]
+// Gc[(c*F + f)*Z + z0 + zb] = Gfull[rep(c)][zb*F + f]; with GcT non-null also
+// GcT[(c*Z + z0 + zb)*F + f] = the same value.
 cudaError_t launch_gtf_compress(const float2* Gfull, const int2* cls_pq, int ncls, int M, int F,
-                                int ZB, int Z, int z0, float2* Gc, cudaStream_t s);
+                                int ZB, int Z, int z0, float2* Gc, float2* GcT, cudaStream_t s);
 
 }  // namespace nursd

@@ -18,7 +18,7 @@ namespace {
 constexpr int kChunk = 1024;  // points per ranking warp
 
 __global__ void points_prepare(const PointsArgs a, int2* __restrict__ i0_out, float* __restrict__ w_out,
-                               int* __restrict__ bin_of) {
+                               int* __restrict__ bin_of, float2* __restrict__ frac_out) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= a.L) return;
   double dx = (double)a.xy[2 * l] - a.cx, dy = (double)a.xy[2 * l + 1] - a.cy;
@@ -44,6 +44,7 @@ __global__ void points_prepare(const PointsArgs a, int2* __restrict__ i0_out, fl
   // guards the bin index against rounding at the aperture edge.
   const int rx = min(max(ix - a.g0, 0), a.W - 1), ry = min(max(iy - a.g0, 0), a.W - 1);
   i0_out[l] = make_int2(rx, ry);
+  if (frac_out) frac_out[l] = make_float2((float)(ux - ix), (float)(uy - iy));
   bin_of[l] = (ry / kTile) * a.tiles + (rx / kTile);
 }
 
@@ -95,7 +96,8 @@ __global__ void points_scan(int* __restrict__ data, int n, int nbins, int nchunk
 __global__ void points_scatter(const int* __restrict__ bin_of, const int* __restrict__ offsets, int L, int nbins,
                                int nchunks, const int2* __restrict__ i0_in, const float* __restrict__ w_in,
                                int width, int* __restrict__ sorted_l, int2* __restrict__ i0_out,
-                               float* __restrict__ w_out) {
+                               float* __restrict__ w_out, const float2* __restrict__ frac_in,
+                               float2* __restrict__ frac_out) {
   extern __shared__ int sc[];
   const int lane = threadIdx.x;
   for (int i = lane; i < nbins; i += 32) sc[i] = 0;
@@ -110,6 +112,7 @@ __global__ void points_scatter(const int* __restrict__ bin_of, const int* __rest
       const int pos = offsets[(size_t)bin * nchunks + blockIdx.x] + sc[bin] + rank;
       sorted_l[pos] = l;
       i0_out[pos] = i0_in[l];
+      if (frac_out) frac_out[pos] = frac_in[l];
       for (int t = 0; t < 2 * width; ++t) w_out[(size_t)pos * 2 * width + t] = w_in[(size_t)l * 2 * width + t];
     }
     __syncwarp();
@@ -121,19 +124,21 @@ __global__ void points_scatter(const int* __restrict__ bin_of, const int* __rest
 }  // namespace
 
 cudaError_t launch_points(const PointsArgs& a, int* bin_of, int2* i0_orig, float* w_orig, int* counts,
-                               int* bin_start, int* sorted_l, int2* i0_sorted, float* w_sorted, cudaStream_t s) {
+                          int* bin_start, int* sorted_l, int2* i0_sorted, float* w_sorted, cudaStream_t s,
+                          float2* frac_orig, float2* frac_sorted) {
+  if ((frac_orig == nullptr) != (frac_sorted == nullptr)) return cudaErrorInvalidValue;
   const int nbins = a.tiles * a.tiles;
   if (a.L <= 0) {
     cudaError_t e = cudaMemsetAsync(bin_start, 0, sizeof(int) * (nbins + 1), s);
     return e;
   }
   const int nchunks = (a.L + kChunk - 1) / kChunk;
-  points_prepare<<<(a.L + 255) / 256, 256, 0, s>>>(a, i0_orig, w_orig, bin_of);
+  points_prepare<<<(a.L + 255) / 256, 256, 0, s>>>(a, i0_orig, w_orig, bin_of, frac_orig);
   const size_t smem = sizeof(int) * nbins;
   points_count<<<nchunks, 32, smem, s>>>(bin_of, a.L, nbins, nchunks, counts);
   points_scan<<<1, 1024, 0, s>>>(counts, nbins * nchunks, nbins, nchunks, bin_start, a.L);
   points_scatter<<<nchunks, 32, smem, s>>>(bin_of, counts, a.L, nbins, nchunks, i0_orig, w_orig, a.width, sorted_l,
-                                          i0_sorted, w_sorted);
+                                          i0_sorted, w_sorted, frac_orig, frac_sorted);
   return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@ NURSD_ERR_TIMEOUT = 4
 NURSD_ERR_UNSUPPORTED = 5
 NURSD_ERR_POINT_OUT_OF_RANGE = 6
 NURSD_OUTPUT_MAGNITUDE = 0x1
+NURSD_ENABLE_ADJOINT = 0x2
 
 #: every entry point declared in include/nursd.h
 EXPORTS = (
@@ -31,6 +32,7 @@ EXPORTS = (
     "nursd_plan_bytes", "nursd_plan_dims", "nursd_set_points", "nursd_temporal_dft", "nursd_nufft1",
     "nursd_propagate", "nursd_forward_phasor", "nursd_forward", "nursd_sync_status",
     "nursd_profile_enable", "nursd_profile_read", "nursd_launch_count", "nursd_nufft1_noalloc",
+    "nursd_forward_points", "nursd_adjoint", "nursd_grad_points",
 )
 
 #: stage names in nursd_stage order
@@ -86,6 +88,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "nursd_profile_read": (ctypes.c_int, [vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int64)]),
         "nursd_launch_count": (i64, [vp]),
         "nursd_nufft1_noalloc": (ctypes.c_int, [i32, dbl, dbl, dbl, i32, i32, vp, i32, vp, vp, vp]),
+        "nursd_forward_points": (ctypes.c_int, [vp, vp, i32, vp, vp, vp]),
+        "nursd_adjoint": (ctypes.c_int, [vp, vp, vp, vp]),
+        "nursd_grad_points": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -145,7 +150,7 @@ class Plan:
 
     def __init__(self, N: int, pitch: float, center, depths, omega, weight=None, T: int = 0, t0: float = 0.0,
                  dt: float = 0.0, max_points: int = 0, kernel_width: int = 6, upsample: int = 2,
-                 magnitude: bool = False, stream=None):
+                 magnitude: bool = False, adjoint: bool = False, stream=None):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("libnursd needs a CUDA GPU; none is available")
@@ -167,7 +172,7 @@ class Plan:
                       else ctypes.POINTER(ctypes.c_double)())
         d.T, d.t0, d.dt = self.T, float(t0), float(dt)
         d.upsample, d.kernel_width = int(upsample), int(kernel_width)
-        d.flags = NURSD_OUTPUT_MAGNITUDE if magnitude else 0
+        d.flags = (NURSD_OUTPUT_MAGNITUDE if magnitude else 0) | (NURSD_ENABLE_ADJOINT if adjoint else 0)
         d.max_points = int(max_points)
         self._desc = d
         h = ctypes.c_void_p()
@@ -265,6 +270,44 @@ class Plan:
         o = _dev(out, self.out_dtype(), self.out_shape(), "out")
         _check(self._lib.nursd_forward(self._h, h, o, ctypes.c_void_p(_stream_ptr(stream))), "nursd_forward")
         return out
+
+    def forward_points(self, phasor, vox, out=None, stream=None):
+        """NURSD-2/3: values at per-plane voxels vox [Z][K][2] (metres) -> [Z][K] complex64."""
+        torch = _torch()
+        self._need_points()
+        p = _dev(phasor, torch.complex64, (self.L, self.F), "phasor")
+        K = int(vox.shape[1])
+        v = _dev(vox, torch.float32, (self.Z, K, 2), "vox")
+        if out is None:
+            out = torch.empty((self.Z, K), dtype=torch.complex64, device=phasor.device)
+        o = _dev(out, torch.complex64, (self.Z, K), "out")
+        _check(self._lib.nursd_forward_points(self._h, p, K, v, o, ctypes.c_void_p(_stream_ptr(stream))),
+               "nursd_forward_points")
+        return out
+
+    def adjoint(self, vol, out=None, stream=None):
+        """A^H: complex volume [Z][N][N] -> phasors [L][F] at the current relay samples."""
+        torch = _torch()
+        self._need_points()
+        v = _dev(vol, torch.complex64, self.out_shape(), "vol")
+        if out is None:
+            out = torch.empty((self.L, self.F), dtype=torch.complex64, device=vol.device)
+        o = _dev(out, torch.complex64, (self.L, self.F), "phasor")
+        _check(self._lib.nursd_adjoint(self._h, v, o, ctypes.c_void_p(_stream_ptr(stream))), "nursd_adjoint")
+        return out
+
+    def grad_points(self, w, phasor, want_phasor=True, want_xy=True, stream=None):
+        """(A^H w, Re sum_f P conj(d(A^H w)/dx)) for w = 2 dL/d conj(V)."""
+        torch = _torch()
+        self._need_points()
+        wv = _dev(w, torch.complex64, self.out_shape(), "w")
+        p = _dev(phasor, torch.complex64, (self.L, self.F), "phasor")
+        gp = torch.empty((self.L, self.F), dtype=torch.complex64, device=w.device) if want_phasor else None
+        gx = torch.empty((self.L, 2), dtype=torch.float32, device=w.device) if want_xy else None
+        _check(self._lib.nursd_grad_points(self._h, wv, p, None if gp is None else ctypes.c_void_p(gp.data_ptr()),
+                                           None if gx is None else ctypes.c_void_p(gx.data_ptr()),
+                                           ctypes.c_void_p(_stream_ptr(stream))), "nursd_grad_points")
+        return gp, gx
 
     def sync_status(self, stream=None) -> int:
         return int(self._lib.nursd_sync_status(self._h, ctypes.c_void_p(_stream_ptr(stream))))

@@ -434,3 +434,30 @@ def test_planted_mistakes_are_caught(monkeypatch):
         monkeypatch.setattr(mod, name, {"rsd_kernel": orig_kernel, "propagate": orig_prop,
                                         "relay_theta": orig_theta}[name])
     assert pin_on_lattice_equals_direct_backprojection() < 1e-12
+
+
+def test_depthwise_adjoint_spectrum_and_gradients_from_w_agree_with_the_full_forms():
+    c = _lattice_case(N=6, L=10, F=2, Z=2)
+    r = np.random.default_rng(8)
+    xy = c["xy"] + r.uniform(-0.5, 0.5, c["xy"].shape) * c["pitch"]
+    M = 2 * c["N"]
+    Gh = O.transfer_functions(c["depths"], c["omega"], M, c["pitch"])
+    V = r.standard_normal((2, 6, 6)) + 1j * r.standard_normal((2, 6, 6))
+    R = O.adjoint_spectrum(V, Gh)
+    assert rel(O.adjoint_spectrum_depthwise(V, c["depths"], c["omega"], c["pitch"]), R) < 1e-13
+    # with w = 2 (A P - V_t), gradients_from_w reproduces nursd_gradients
+    Vt = r.standard_normal((2, 6, 6)) + 1j * r.standard_normal((2, 6, 6))
+    args = (c["center"], c["pitch"], c["N"], c["depths"], c["omega"])
+    gP, gx = O.nursd_gradients(c["P"], xy, *args, Vt)
+    w = 2 * (O.nursd_forward(c["P"], xy, *args) - Vt)
+    th = O.relay_theta(xy, c["center"], c["pitch"], M)
+    gP2, gx2 = O.gradients_from_w(O.adjoint_spectrum(w, Gh), c["P"], th, c["pitch"])
+    assert rel(gP2, gP) < 1e-12 and rel(gx2, gx) < 1e-12
+
+
+def test_lattice_type1_equals_the_general_sum():
+    M, L, F = 12, 30, 2
+    r = np.random.default_rng(9)
+    n = np.stack([r.integers(-M // 2, M // 2, L), r.integers(-M // 2, M // 2, L)], axis=1)
+    P = r.standard_normal((L, F)) + 1j * r.standard_normal((L, F))
+    assert rel(O.nudft_type1_lattice(P, n, M), O.nudft_type1(P, 2 * math.pi * n / M, M)) < 1e-13
