@@ -83,6 +83,8 @@ typedef struct {
   int32_t kernel_width;      /* ES kernel width w, 4..8 (6 gives ~1e-5)            */
   uint32_t flags;            /* NURSD_* flags                                      */
   int32_t max_points;        /* capacity for relay samples L                       */
+  const double* h_srsd_pitch; /* [Z] SRSD output pitch delta_o(z) per depth [m] (copied),
+                                 or NULL: no SRSD tables are built                  */
 } nursd_desc;
 
 /* Text for a status code (static storage). */
@@ -207,6 +209,24 @@ int nursd_grad_points(nursd_plan_t plan, const nursd_c64* d_w, const nursd_c64* 
                       float* d_grad_xy, nursd_stream_t stream);
 
 /*
+ * Scaled RSD (Sec. 4, Eq. SRSD_conv with the SFFT of Supp. A.1, applied to a
+ * non-uniform acquisition as in Supp. C): plane z is reconstructed on the
+ * lattice c + delta_o(z) I_N^2 (delta_o from the descriptor's h_srsd_pitch,
+ * scale s_z = delta_o(z) / delta >= any positive value).  From the NUFFT-1
+ * spectrum U_f the gridded input u_f = M^-2 IDFT_M[U_f] (on I_M^2, pitch delta)
+ * is formed, then per depth and frequency the scaled DFT
+ *   Phat_{z,f}(kappa) = sum_{n in I_M^2} u_f[n] exp(-2 pi i kappa.n / (M s_z))
+ * by Bluestein's chirp-z (separable x then y, convolution length 2M), the
+ * frequency sum Y_z = sum_f Phat_{z,f} Ghat^(s_z)_{z,f} with G sampled at pitch
+ * s_z delta, and the inverse DFT cropped to I_N^2:
+ *   V_z[m] = M^-2 sum_kappa Y_z(kappa) exp(+2 pi i kappa.m / M).
+ * d_phasor [L][F] -> d_out [Z][N][N] (complex64, or |V| with
+ * NURSD_OUTPUT_MAGNITUDE).  Needs h_srsd_pitch at plan creation and
+ * nursd_set_points.
+ */
+int srsd_forward(nursd_plan_t plan, const nursd_c64* d_phasor, void* d_out, nursd_stream_t stream);
+
+/*
  * Stage profiling.  Stages of the forward path, each one or more kernel
  * launches: relay-sample preparation and sort, temporal transform, spread,
  * FFT along x, FFT along y with deconvolution, transfer-function contraction,
@@ -221,7 +241,8 @@ typedef enum {
   NURSD_STAGE_CONTRACT = 5,
   NURSD_STAGE_IFFT_X = 6,
   NURSD_STAGE_IFFT_Y = 7,
-  NURSD_NUM_STAGES = 8
+  NURSD_STAGE_SRSD = 8, /* scaled transforms and per-depth contractions of srsd_forward */
+  NURSD_NUM_STAGES = 9
 } nursd_stage;
 
 /*

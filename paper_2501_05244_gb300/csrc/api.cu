@@ -66,6 +66,11 @@ struct nursd_plan_s {
   float2* Gc = nullptr;
   float2* GcT = nullptr;  // transposed table [ncls][Z][F] for the adjoint (NURSD_ENABLE_ADJOINT)
   float* Bt = nullptr;    // temporal twiddles [T][2F]
+  // SRSD tables (h_srsd_pitch given): scaled transfer table [Z][ncls][F], chirps [Z][M], FFT(b)/(2M) [Z][2M]
+  std::vector<double> srsd_pitch;
+  float2* Gs = nullptr;
+  float2* chirp = nullptr;
+  float2* bhat = nullptr;
   // points
   int* bin_of = nullptr;
   int2* i0_orig = nullptr;
@@ -193,17 +198,21 @@ cudaError_t axis_pass(const nursd_plan_s* p, const float2* in, float2* out, int 
   return launch_panel_fft(logn, inv, a, s);
 }
 
-int build_transfer_table(nursd_plan_s* p, cudaStream_t s) {
+// Builds Ghat_{z,f} = DFT_M[exp(i k_f r)/r] for every depth in z-batches (FP64 phase, panel FFTs)
+// and compresses it by symmetry class.  srsd = false: lattice pitch delta, into Gc (and GcT);
+// srsd = true: pitch s_z delta per depth, into the depth-major SRSD table Gs.
+int build_table(nursd_plan_s* p, bool srsd, cudaStream_t s) {
   const int M = p->M, F = p->F, Z = p->Z;
   const long long per_depth = (long long)M * M * F;
   int ZB = (int)std::max<long long>(1, (1LL << 28) / per_depth);  // ~2 GiB per buffer at most
   ZB = std::min(ZB, Z);
   float2 *g = nullptr, *tmp = nullptr;
-  double *dz = nullptr, *dk = nullptr;
+  double *dz = nullptr, *dk = nullptr, *dp = nullptr;
   int rc = NURSD_OK;
   if (cudaMalloc(&g, sizeof(float2) * per_depth * ZB) != cudaSuccess ||
-      cudaMalloc(&tmp, sizeof(float2) * per_depth * ZB) != cudaSuccess || cudaMalloc(&dz, sizeof(double) * Z) != cudaSuccess ||
-      cudaMalloc(&dk, sizeof(double) * F) != cudaSuccess) {
+      cudaMalloc(&tmp, sizeof(float2) * per_depth * ZB) != cudaSuccess ||
+      cudaMalloc(&dz, sizeof(double) * Z) != cudaSuccess || cudaMalloc(&dk, sizeof(double) * F) != cudaSuccess ||
+      cudaMalloc(&dp, sizeof(double) * Z) != cudaSuccess) {
     cudaGetLastError();
     rc = NURSD_ERR_OOM;
   }
@@ -212,26 +221,83 @@ int build_transfer_table(nursd_plan_s* p, cudaStream_t s) {
   if (rc == NURSD_OK) {
     rc = from_cuda(cudaMemcpyAsync(dz, p->depths.data(), sizeof(double) * Z, cudaMemcpyHostToDevice, s));
     if (rc == NURSD_OK) rc = from_cuda(cudaMemcpyAsync(dk, k.data(), sizeof(double) * F, cudaMemcpyHostToDevice, s));
+    if (rc == NURSD_OK && srsd)
+      rc = from_cuda(cudaMemcpyAsync(dp, p->srsd_pitch.data(), sizeof(double) * Z, cudaMemcpyHostToDevice, s));
   }
   const int logM = ilog2(M);
   for (int z0 = 0; rc == NURSD_OK && z0 < Z; z0 += ZB) {
     const int zb = std::min(ZB, Z - z0);
     const int C = zb * F;
-    rc = from_cuda(launch_gtf_generate(g, M, p->pitch, dz + z0, zb, dk, F, s));
+    rc = from_cuda(launch_gtf_generate(g, M, p->pitch, dz + z0, zb, dk, F, s, srsd ? dp + z0 : nullptr));
     if (rc == NURSD_OK)  // along jx, for each row jy
       rc = from_cuda(axis_pass(p, g, tmp, logM, false, C, M, (long long)M * C, C, (long long)M * C, C, M, -M / 2, M,
                                -M / 2, nullptr, nullptr, 1.f, s));
     if (rc == NURSD_OK)  // along jy, for each column kx
       rc = from_cuda(axis_pass(p, tmp, g, logM, false, C, M, C, (long long)M * C, C, (long long)M * C, M, -M / 2, M,
                                -M / 2, nullptr, nullptr, 1.f, s));
-    if (rc == NURSD_OK)
-      rc = from_cuda(launch_gtf_compress(g, p->cls, p->ncls, M, F, zb, Z, z0, p->Gc, p->GcT, s));
+    if (rc == NURSD_OK) {
+      if (srsd)
+        rc = from_cuda(launch_gtf_compress_depthmajor(g, p->cls, p->ncls, M, F, zb, z0, p->Gs, s));
+      else
+        rc = from_cuda(launch_gtf_compress(g, p->cls, p->ncls, M, F, zb, Z, z0, p->Gc, p->GcT, s));
+    }
   }
   if (rc == NURSD_OK) rc = from_cuda(cudaStreamSynchronize(s));
   cudaFree(g);
   cudaFree(tmp);
   cudaFree(dz);
   cudaFree(dk);
+  cudaFree(dp);
+  return rc;
+}
+
+// SRSD chirps c_z(n) = exp(-pi i n^2 / (M s_z)) on I_M and bhat_z = FFT_2M[b_z] / (2M) with
+// b_z(d) = exp(+pi i d^2 / (M s_z)), |d| < M, placed at d mod 2M (phases in FP64).
+int build_srsd_chirps(nursd_plan_s* p, cudaStream_t s) {
+  const int M = p->M, Z = p->Z, L2 = 2 * M;
+  std::vector<float2> ch((size_t)Z * M), b((size_t)Z * L2, make_float2(0.f, 0.f));
+  for (int z = 0; z < Z; ++z) {
+    const double sc = p->srsd_pitch[z] / p->pitch;
+    for (int i = 0; i < M; ++i) {
+      const double n = i - M / 2;
+      const double ph = std::fmod(kPi * n * n / (M * sc), 2.0 * kPi);
+      ch[(size_t)z * M + i] = make_float2((float)std::cos(ph), (float)-std::sin(ph));
+    }
+    for (int d = -(M - 1); d <= M - 1; ++d) {
+      const double ph = std::fmod(kPi * (double)d * d / (M * sc), 2.0 * kPi);
+      b[(size_t)z * L2 + ((d + L2) % L2)] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+    }
+  }
+  float2* db = nullptr;
+  if (cudaMalloc(&db, sizeof(float2) * b.size()) != cudaSuccess) {
+    cudaGetLastError();
+    return NURSD_ERR_OOM;
+  }
+  int rc = from_cuda(cudaMemcpyAsync(p->chirp, ch.data(), sizeof(float2) * ch.size(), cudaMemcpyHostToDevice, s));
+  if (rc == NURSD_OK) rc = from_cuda(cudaMemcpyAsync(db, b.data(), sizeof(float2) * b.size(), cudaMemcpyHostToDevice, s));
+  if (rc == NURSD_OK) {  // FFT of each depth's contiguous row of 2M values
+    const int logL = ilog2(L2);
+    PanelArgs a = panel_base(p);
+    a.in = db;
+    a.out = p->bhat;
+    a.in_sb = L2;
+    a.in_si = 1;
+    a.in_slo = 1;
+    a.out_sb = L2;
+    a.out_si = 1;
+    a.out_slo = 1;
+    a.load_i_fastest = 1;
+    a.store_o_fastest = 1;
+    a.nin = L2;
+    a.nout = L2;
+    a.lo_total = 1;
+    a.CLO = panel_width(logL);
+    a.batch = Z;
+    a.scale = 1.f / (float)L2;
+    rc = from_cuda(launch_panel_fft(logL, false, a, s));
+  }
+  if (rc == NURSD_OK) rc = from_cuda(cudaStreamSynchronize(s));
+  cudaFree(db);
   return rc;
 }
 
@@ -256,15 +322,12 @@ int run_nufft1(nursd_plan_s* p, const float2* phasor, float2* spec, cudaStream_t
   return from_cuda(e);
 }
 
-int run_propagate(nursd_plan_s* p, const float2* spec, void* out, cudaStream_t s) {
-  const int M = p->M, N = p->N, Z = p->Z, F = p->F;
+// V[z][my][mx] = M^-2 sum_k Y[k][z] e^{+2 pi i k.m / M} on I_N^2 (two pruned inverse passes).
+int run_idft_crop(nursd_plan_s* p, void* out, cudaStream_t s) {
+  const int M = p->M, N = p->N, Z = p->Z;
   const int logM = ilog2(M);
-  cudaError_t e;
-  {
-    StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
-    e = launch_contract(spec, p->Gc, p->cls, p->ncls, M, F, Z, p->Y, s);
-  }
-  if (e == cudaSuccess) {  // inverse FFT along kx, keep mx in I_N
+  cudaError_t e = cudaSuccess;
+  {  // inverse FFT along kx, keep mx in I_N
     StageTimer t(p, NURSD_STAGE_IFFT_X, s, 1);
     e = axis_pass(p, p->Y, p->T1, logM, true, Z, M, (long long)M * Z, Z, (long long)N * Z, Z, M, -M / 2, N, -N / 2,
                   nullptr, nullptr, 1.f, s);
@@ -298,6 +361,67 @@ int run_propagate(nursd_plan_s* p, const float2* spec, void* out, cudaStream_t s
     e = launch_panel_fft(logM, true, a, s);
   }
   return from_cuda(e);
+}
+
+int run_propagate(nursd_plan_s* p, const float2* spec, void* out, cudaStream_t s) {
+  cudaError_t e;
+  {
+    StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
+    e = launch_contract(spec, p->Gc, p->cls, p->ncls, p->M, p->F, p->Z, p->Y, s);
+  }
+  if (e != cudaSuccess) return from_cuda(e);
+  return run_idft_crop(p, out, s);
+}
+
+// Scaled RSD from a NUFFT-1 spectrum U (in p->U): see srsd_forward in nursd.h.
+int run_srsd(nursd_plan_s* p, void* out, cudaStream_t s) {
+  const int M = p->M, F = p->F, Z = p->Z;
+  const int logM = ilog2(M), logL = logM + 1;
+  cudaError_t e;
+  {  // gridded input u = M^-2 IDFT_M[U]: along kx (rows ky), then along ky (columns nx)
+    StageTimer t(p, NURSD_STAGE_SRSD, s, 2);
+    e = axis_pass(p, p->U, p->R1, logM, true, F, M, (long long)M * F, F, (long long)M * F, F, M, -M / 2, M, -M / 2,
+                  nullptr, nullptr, 1.f, s);
+    if (e == cudaSuccess)
+      e = axis_pass(p, p->R1, p->fine, logM, true, F, M, F, (long long)M * F, F, (long long)M * F, M, -M / 2, M,
+                    -M / 2, nullptr, nullptr, 1.f / ((float)M * (float)M), s);
+  }
+  for (int z = 0; e == cudaSuccess && z < Z; ++z) {
+    StageTimer t(p, NURSD_STAGE_SRSD, s, 3);
+    const float2* ch = p->chirp + (size_t)z * M;
+    const float2* bh = p->bhat + (size_t)z * 2 * M;
+    PanelArgs a = panel_base(p);  // scaled DFT along nx for every (ny, f): u -> Q [ny][kx'][F]
+    a.in = p->fine;
+    a.out = p->R1;
+    a.in_sb = (long long)M * F;
+    a.in_si = F;
+    a.in_slo = 1;
+    a.out_sb = (long long)M * F;
+    a.out_si = F;
+    a.out_slo = 1;
+    a.nin = M;
+    a.in_off = -M / 2;
+    a.nout = M;
+    a.out_off = -M / 2;
+    a.lo_total = F;
+    a.CLO = panel_width(logL);
+    a.batch = M;
+    e = launch_panel_bluestein(logL, a, ch, bh, ch, s);
+    if (e == cudaSuccess) {  // scaled DFT along ny for every (kx', f): Q -> Phat [ky'][kx'][F]
+      PanelArgs b = a;
+      b.in = p->R1;
+      b.out = p->U;
+      b.in_sb = F;
+      b.in_si = (long long)M * F;
+      b.out_sb = F;
+      b.out_si = (long long)M * F;
+      e = launch_panel_bluestein(logL, b, ch, bh, ch, s);
+    }
+    if (e == cudaSuccess)
+      e = launch_contract_depth(p->U, p->Gs + (size_t)z * p->ncls * F, p->cls, p->ncls, M, F, Z, z, p->Y, s);
+  }
+  if (e != cudaSuccess) return from_cuda(e);
+  return run_idft_crop(p, out, s);
 }
 
 // Adjoint of run_propagate up to the spectrum: R[k][f] = sum_z conj(Ghat) * M^-2 DFT_M[pad V_z](k),
@@ -459,6 +583,9 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
   if (d->upsample != 2) return NURSD_ERR_UNSUPPORTED;
   if (d->kernel_width < 4 || d->kernel_width > kMaxKernelWidth) return NURSD_ERR_UNSUPPORTED;
   if (d->max_points < 0 || d->max_points > (1 << 26)) return NURSD_ERR_INVALID_ARG;
+  if (d->h_srsd_pitch)
+    for (int i = 0; i < d->Z; ++i)
+      if (!(d->h_srsd_pitch[i] > 0) || !std::isfinite(d->h_srsd_pitch[i])) return NURSD_ERR_INVALID_ARG;
   if ((d->flags & ~(NURSD_OUTPUT_MAGNITUDE | NURSD_ENABLE_ADJOINT)) != 0) return NURSD_ERR_UNSUPPORTED;
   if ((d->flags & NURSD_ENABLE_ADJOINT) && d->Z > 256) return NURSD_ERR_UNSUPPORTED;
 
@@ -484,6 +611,7 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
   p->depths.assign(d->h_depths, d->h_depths + d->Z);
   p->omega.assign(d->h_omega, d->h_omega + d->F);
   p->weight.assign(d->F, 1.0);
+  if (d->h_srsd_pitch) p->srsd_pitch.assign(d->h_srsd_pitch, d->h_srsd_pitch + d->Z);
   if (d->h_weight) p->weight.assign(d->h_weight, d->h_weight + d->F);
   // fine-grid window: every footprint of a sample with |x - c| <= N delta / 2, plus a margin
   const int need = d->upsample * p->N + p->w + 2;
@@ -547,6 +675,9 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
             p->alloc(p->T1, (size_t)p->M * p->N * p->Z);
   if (ok && p->T > 0) ok = p->alloc(p->Bt, Bt.size());
   if (ok && (p->flags & NURSD_ENABLE_ADJOINT)) ok = p->alloc(p->GcT, (size_t)p->ncls * p->F * p->Z);
+  if (ok && !p->srsd_pitch.empty())
+    ok = p->alloc(p->Gs, (size_t)p->ncls * p->F * p->Z) && p->alloc(p->chirp, (size_t)p->Z * p->M) &&
+         p->alloc(p->bhat, (size_t)p->Z * 2 * p->M);
   if (!ok) {
     delete p;
     return NURSD_ERR_OOM;
@@ -560,7 +691,9 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
     rc = from_cuda(cudaMemcpyAsync(p->Bt, Bt.data(), sizeof(float) * Bt.size(), cudaMemcpyHostToDevice, s));
   if (rc == NURSD_OK) rc = from_cuda(cudaMemsetAsync(p->status, 0, sizeof(int), s));
   if (rc == NURSD_OK) rc = from_cuda(cudaMemsetAsync(p->bin_start, 0, sizeof(int) * (nbins + 1), s));
-  if (rc == NURSD_OK) rc = build_transfer_table(p, s);
+  if (rc == NURSD_OK) rc = build_table(p, false, s);
+  if (rc == NURSD_OK && p->Gs) rc = build_table(p, true, s);
+  if (rc == NURSD_OK && p->Gs) rc = build_srsd_chirps(p, s);
   if (rc != NURSD_OK) {
     delete p;
     return rc;
@@ -749,6 +882,15 @@ int nursd_forward_points(nursd_plan_t p, const nursd_c64* d_phasor, int32_t K, c
     a.status = p->status;
     rc = from_cuda(launch_interp_planes(a, s));
   }
+  return rc;
+}
+
+int srsd_forward(nursd_plan_t p, const nursd_c64* d_phasor, void* d_out, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || !p->Gs || p->L < 0 || !d_out || !aligned(d_out, 8)) return NURSD_ERR_INVALID_ARG;
+  if (p->L > 0 && (!d_phasor || !aligned(d_phasor, 8))) return NURSD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = run_nufft1(p, reinterpret_cast<const float2*>(d_phasor), p->U, s);
+  if (rc == NURSD_OK) rc = run_srsd(p, d_out, s);
   return rc;
 }
 

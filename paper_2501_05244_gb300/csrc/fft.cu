@@ -166,6 +166,84 @@ __global__ void __launch_bounds__(NT) panel_fft_kernel(const PanelArgs a) {
   }
 }
 
+// Scaled DFT by Bluestein's chirp-z (Supp. A.1): X[kappa] = c(kappa) sum_n (x[n] c(n)) b(kappa - n)
+// with c(n) = e^{-pi i n^2 / (M s)}, b(d) = e^{+pi i d^2 / (M s)}.  The linear convolution is a
+// circular one of length n = 2M >= 2M - 1: chirp the window, FFT, multiply by bhat = FFT(b)/n,
+// inverse FFT, chirp the kept outputs.  cpre/cpost are per input / output index.
+template <int LOGN, int CP, int NT>
+__global__ void __launch_bounds__(NT, 2) panel_bluestein_kernel(const PanelArgs a, const float2* __restrict__ cpre,
+                                                            const float2* __restrict__ bhat,
+                                                            const float2* __restrict__ cpost) {
+  constexpr int n = 1 << LOGN;
+  constexpr int SR = CP + 1;
+  extern __shared__ float2 sm[];
+  const int tid = threadIdx.x;
+  const int nlo = (a.lo_total + a.CLO - 1) / a.CLO;
+  const int hi0 = (blockIdx.x / nlo) * a.CHI;
+  const int lo0 = (blockIdx.x % nlo) * a.CLO;
+  const int b = blockIdx.y;
+  const float2* __restrict__ inb = a.in + (long long)b * a.in_sb;
+  for (int idx = tid; idx < a.nin * CP; idx += NT) {
+    const int i = idx / CP, q = idx % CP;
+    const int qh = q / a.CLO, ql = q % a.CLO;
+    const int hi = hi0 + qh, lo = lo0 + ql;
+    float2 v = make_float2(0.f, 0.f);
+    if (hi < a.hi_total && lo < a.lo_total) v = cmul(__ldg(inb + i * a.in_si + hi * a.in_shi + lo * a.in_slo), __ldg(cpre + i));
+    sm[((i + a.in_off) & (n - 1)) * SR + q] = v;
+  }
+  for (int idx = tid; idx < (n - a.nin) * CP; idx += NT) {
+    const int j = idx / CP + a.nin, q = idx % CP;
+    sm[((j + a.in_off) & (n - 1)) * SR + q] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  int Ns = 1;
+#pragma unroll
+  for (int p = 0; p < LOGN / 2; ++p) {
+    stockham_pass<LOGN, CP, NT, 4, false>(sm, Ns, a.twiddle);
+    Ns <<= 2;
+  }
+  if (LOGN & 1) stockham_pass<LOGN, CP, NT, 2, false>(sm, Ns, a.twiddle);
+  for (int idx = tid; idx < n * CP; idx += NT) {
+    const int j = idx / CP, q = idx % CP;
+    sm[j * SR + q] = cmul(sm[j * SR + q], __ldg(bhat + j));
+  }
+  __syncthreads();
+  Ns = 1;
+#pragma unroll
+  for (int p = 0; p < LOGN / 2; ++p) {
+    stockham_pass<LOGN, CP, NT, 4, true>(sm, Ns, a.twiddle);
+    Ns <<= 2;
+  }
+  if (LOGN & 1) stockham_pass<LOGN, CP, NT, 2, true>(sm, Ns, a.twiddle);
+  for (int idx = tid; idx < a.nout * CP; idx += NT) {
+    const int q = idx % CP, o = idx / CP;
+    const int qh = q / a.CLO, ql = q % a.CLO;
+    const int hi = hi0 + qh, lo = lo0 + ql;
+    if (hi >= a.hi_total || lo >= a.lo_total) continue;
+    const float2 v = cmul(sm[((o + a.out_off) & (n - 1)) * SR + q], __ldg(cpost + o));
+    a.out[(long long)b * a.out_sb + (long long)o * a.out_si + (long long)hi * a.out_shi + (long long)lo * a.out_slo] =
+        v;
+  }
+}
+
+template <int LOGN, int CP, int NT>
+cudaError_t launch_bluestein_one(const PanelArgs& a, const float2* cpre, const float2* bhat, const float2* cpost,
+                                 cudaStream_t s) {
+  const size_t smem = sizeof(float2) * (size_t(1) << LOGN) * (CP + 1);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(panel_bluestein_kernel<LOGN, CP, NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const int nhi = (a.hi_total + a.CHI - 1) / a.CHI;
+  const int nlo = (a.lo_total + a.CLO - 1) / a.CLO;
+  dim3 grid(nhi * nlo, a.batch);
+  panel_bluestein_kernel<LOGN, CP, NT><<<grid, NT, smem, s>>>(a, cpre, bhat, cpost);
+  return cudaGetLastError();
+}
+
 template <int LOGN, int CP, int NT, bool INV>
 cudaError_t launch_one(const PanelArgs& a, cudaStream_t s) {
   const size_t smem = sizeof(float2) * (size_t(1) << LOGN) * (CP + 1);
@@ -194,6 +272,23 @@ cudaError_t launch_dir(bool inverse, const PanelArgs& a, cudaStream_t s) {
 // near 68 KB and three CTAs share an SM (overlapping one's loads with another's
 // transform).
 int panel_width(int logn) { return logn <= 9 ? 16 : (logn == 10 ? 8 : 4); }
+
+cudaError_t launch_panel_bluestein(int logn, const PanelArgs& a, const float2* cpre, const float2* bhat,
+                                   const float2* cpost, cudaStream_t s) {
+  if (a.CHI * a.CLO != panel_width(logn) || a.nin > (1 << logn) || a.nout > (1 << logn) || a.batch < 1 ||
+      a.batch > 65535)
+    return cudaErrorInvalidValue;
+  switch (logn) {
+    case 5: return launch_bluestein_one<5, 16, 128>(a, cpre, bhat, cpost, s);
+    case 6: return launch_bluestein_one<6, 16, 256>(a, cpre, bhat, cpost, s);
+    case 7: return launch_bluestein_one<7, 16, 256>(a, cpre, bhat, cpost, s);
+    case 8: return launch_bluestein_one<8, 16, 256>(a, cpre, bhat, cpost, s);
+    case 9: return launch_bluestein_one<9, 16, 256>(a, cpre, bhat, cpost, s);
+    case 10: return launch_bluestein_one<10, 8, 256>(a, cpre, bhat, cpost, s);
+    case 11: return launch_bluestein_one<11, 4, 256>(a, cpre, bhat, cpost, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_panel_fft(int logn, bool inverse, const PanelArgs& a, cudaStream_t s) {
   if (a.CHI * a.CLO != panel_width(logn) || a.nin > (1 << logn) || a.nout > (1 << logn) || a.batch < 1 ||

@@ -58,6 +58,10 @@ struct PanelArgs {
 cudaError_t launch_panel_fft(int logn, bool inverse, const PanelArgs& a, cudaStream_t s);
 // Panel width (channels per CTA) used for a given transform length.
 int panel_width(int logn);
+// Bluestein scaled DFT along the panel axis: window * cpre[i] -> FFT_n -> * bhat[bin] ->
+// inverse FFT_n -> kept bins * cpost[o] (store order: channels fastest).
+cudaError_t launch_panel_bluestein(int logn, const PanelArgs& a, const float2* cpre, const float2* bhat,
+                                   const float2* cpost, cudaStream_t s);
 
 // ------------------------------------------------------------- temporal DFT
 // P[l][f] = sum_n h[l][n] * B[n][2f..2f+1] as a real GEMM C[L][2F] = H[L][T] B[T][2F].
@@ -136,9 +140,16 @@ struct PlaneInterpArgs {
 cudaError_t launch_interp_planes(const PlaneInterpArgs& a, cudaStream_t s);
 
 // ------------------------------------------------------- transfer function
-// g[jy][jx][zb*F + f] = exp(i k_f r)/r, r = sqrt((jx d)^2 + (jy d)^2 + z_zb^2), FP64 phase.
+// g[jy][jx][zb*F + f] = exp(i k_f r)/r, r = sqrt((jx d)^2 + (jy d)^2 + z_zb^2), FP64 phase;
+// d = d_pitch[zb] when d_pitch is non-null (SRSD's scaled lattice), else `pitch`.
 cudaError_t launch_gtf_generate(float2* g, int M, double pitch, const double* d_z, int ZB,
-                                const double* d_k, int F, cudaStream_t s);
+                                const double* d_k, int F, cudaStream_t s, const double* d_pitch = nullptr);
+// Gs[((z0 + zb) * ncls + c) * F + f] = Gfull[rep(c)][zb*F + f] (per-depth blocks, f fastest)
+cudaError_t launch_gtf_compress_depthmajor(const float2* Gfull, const int2* cls_pq, int ncls, int M, int F, int ZB,
+                                           int z0, float2* Gs, cudaStream_t s);
+// SRSD contraction for one depth: Y[k][z] = sum_f Phat[k][f] * Gs_z[cls(k)][f].
+cudaError_t launch_contract_depth(const float2* Phat, const float2* Gs_z, const int2* cls_pq, int ncls, int M, int F,
+                                  int Z, int z, float2* Y, cudaStream_t s);
 // Gc[(c*F + f)*Z + z0 + zb] = Gfull[rep(c)][zb*F + f]; with GcT non-null also
 // GcT[(c*Z + z0 + zb)*F + f] = the same value.
 cudaError_t launch_gtf_compress(const float2* Gfull, const int2* cls_pq, int ncls, int M, int F,

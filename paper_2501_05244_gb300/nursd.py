@@ -32,11 +32,11 @@ EXPORTS = (
     "nursd_plan_bytes", "nursd_plan_dims", "nursd_set_points", "nursd_temporal_dft", "nursd_nufft1",
     "nursd_propagate", "nursd_forward_phasor", "nursd_forward", "nursd_sync_status",
     "nursd_profile_enable", "nursd_profile_read", "nursd_launch_count", "nursd_nufft1_noalloc",
-    "nursd_forward_points", "nursd_adjoint", "nursd_grad_points",
+    "nursd_forward_points", "nursd_adjoint", "nursd_grad_points", "srsd_forward",
 )
 
 #: stage names in nursd_stage order
-STAGES = ("points", "temporal", "spread", "fft_x", "fft_y", "contract", "ifft_x", "ifft_y")
+STAGES = ("points", "temporal", "spread", "fft_x", "fft_y", "contract", "ifft_x", "ifft_y", "srsd")
 
 
 class NursdError(RuntimeError):
@@ -53,6 +53,7 @@ class _Desc(ctypes.Structure):
         ("h_weight", ctypes.POINTER(ctypes.c_double)), ("T", ctypes.c_int32), ("t0", ctypes.c_double),
         ("dt", ctypes.c_double), ("upsample", ctypes.c_int32), ("kernel_width", ctypes.c_int32),
         ("flags", ctypes.c_uint32), ("max_points", ctypes.c_int32),
+        ("h_srsd_pitch", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -91,6 +92,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "nursd_forward_points": (ctypes.c_int, [vp, vp, i32, vp, vp, vp]),
         "nursd_adjoint": (ctypes.c_int, [vp, vp, vp, vp]),
         "nursd_grad_points": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
+        "srsd_forward": (ctypes.c_int, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -150,7 +152,7 @@ class Plan:
 
     def __init__(self, N: int, pitch: float, center, depths, omega, weight=None, T: int = 0, t0: float = 0.0,
                  dt: float = 0.0, max_points: int = 0, kernel_width: int = 6, upsample: int = 2,
-                 magnitude: bool = False, adjoint: bool = False, stream=None):
+                 magnitude: bool = False, adjoint: bool = False, srsd_pitch=None, stream=None):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("libnursd needs a CUDA GPU; none is available")
@@ -174,6 +176,9 @@ class Plan:
         d.upsample, d.kernel_width = int(upsample), int(kernel_width)
         d.flags = (NURSD_OUTPUT_MAGNITUDE if magnitude else 0) | (NURSD_ENABLE_ADJOINT if adjoint else 0)
         d.max_points = int(max_points)
+        self.srsd_pitch = None if srsd_pitch is None else np.ascontiguousarray(srsd_pitch, dtype=np.float64)
+        d.h_srsd_pitch = (self.srsd_pitch.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+                          if self.srsd_pitch is not None else ctypes.POINTER(ctypes.c_double)())
         self._desc = d
         h = ctypes.c_void_p()
         _check(self._lib.nursd_plan_create(ctypes.byref(d), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)),
@@ -283,6 +288,17 @@ class Plan:
         o = _dev(out, torch.complex64, (self.Z, K), "out")
         _check(self._lib.nursd_forward_points(self._h, p, K, v, o, ctypes.c_void_p(_stream_ptr(stream))),
                "nursd_forward_points")
+        return out
+
+    def srsd_forward(self, phasor, out=None, stream=None):
+        """Scaled RSD: plane z on the lattice of pitch srsd_pitch[z] -> [Z][N][N]."""
+        torch = _torch()
+        self._need_points()
+        p = _dev(phasor, torch.complex64, (self.L, self.F), "phasor")
+        if out is None:
+            out = self.empty_output()
+        o = _dev(out, self.out_dtype(), self.out_shape(), "out")
+        _check(self._lib.srsd_forward(self._h, p, o, ctypes.c_void_p(_stream_ptr(stream))), "srsd_forward")
         return out
 
     def adjoint(self, vol, out=None, stream=None):

@@ -1,0 +1,88 @@
+"""GPU parity of the scaled RSD (a9) against the FP64 oracle (explicit scaled-DFT
+matrices, no chirp-z, no FFT of the data), through the C ABI.  Gate: 1e-4
+relative L2 on the complex output."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+import paper_2501_05244_gb300 as nursd
+from workloads import BASE_SEED, random_phasors, relay_lattice, srsd_depths_c3b, srsd_pitches_c3b
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+def rel(a, b):
+    a = np.asarray(a, np.complex128).ravel()
+    b = np.asarray(b, np.complex128).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    nursd.build()
+
+
+def case(N, L, F, Z, seed, pitch=0.02, center=(0.01, -0.03), smax=4.1):
+    r = np.random.default_rng(seed)
+    half = N * pitch / 2
+    xy = (r.uniform(-half, half, (L, 2)) * 0.999 + np.asarray(center)).astype(np.float32)
+    P = random_phasors(L, F, seed=seed + 1)
+    om = 2 * math.pi * np.linspace(3e9, 6e9, F)
+    depths = np.linspace(0.3, 0.9, Z)
+    scales = np.linspace(1.0, smax, Z)
+    return xy, P, om, depths, scales * pitch, pitch, center
+
+
+@pytest.mark.parametrize("N,L,F,Z,seed", [(16, 300, 6, 5, 1), (32, 1200, 16, 7, 2), (8, 20, 2, 2, 3)])
+def test_srsd_matches_oracle(N, L, F, Z, seed):
+    xy, P, om, depths, out_pitch, pitch, center = case(N, L, F, Z, seed)
+    plan = nursd.Plan(N, pitch, center, depths, om, max_points=L, srsd_pitch=out_pitch)
+    plan.set_points(torch.from_numpy(xy).cuda())
+    V = plan.srsd_forward(torch.from_numpy(P).cuda()).cpu().numpy()
+    ref = O.srsd_forward(P, xy, center, pitch, N, depths, out_pitch / pitch, om)
+    assert rel(V, ref) < TOL
+
+
+def test_srsd_with_unit_scale_equals_nursd_on_gpu():
+    xy, P, om, depths, _, pitch, center = case(32, 900, 8, 4, 5)
+    plan = nursd.Plan(32, pitch, center, depths, om, max_points=900, srsd_pitch=np.full(4, pitch))
+    plan.set_points(torch.from_numpy(xy).cuda())
+    Pg = torch.from_numpy(P).cuda()
+    assert rel(plan.srsd_forward(Pg).cpu().numpy(), plan.forward_phasor(Pg).cpu().numpy()) < 1e-5
+
+
+def test_srsd_magnitude_output():
+    xy, P, om, depths, out_pitch, pitch, center = case(16, 200, 4, 3, 6)
+    pc = nursd.Plan(16, pitch, center, depths, om, max_points=200, srsd_pitch=out_pitch)
+    pm = nursd.Plan(16, pitch, center, depths, om, max_points=200, srsd_pitch=out_pitch, magnitude=True)
+    for p in (pc, pm):
+        p.set_points(torch.from_numpy(xy).cuda())
+    Vc = pc.srsd_forward(torch.from_numpy(P).cuda()).cpu().numpy()
+    Vm = pm.srsd_forward(torch.from_numpy(P).cuda()).cpu().numpy()
+    assert np.allclose(Vm, np.abs(Vc), rtol=1e-5, atol=1e-6 * np.abs(Vc).max())
+
+
+def test_srsd_at_the_65k_sample_size_sampled_planes():
+    # 65,536 samples on the 256^2 lattice, 128 planes over 1-4 m, output pitch 8 mm -> 32 mm
+    # (scales 1.024 -> 4.096); the oracle evaluates planes 0 and 127 with explicit scaled DFTs.
+    N, pitch, F = 256, 2.0 / 256, 128
+    depths = srsd_depths_c3b()
+    out_pitch = srsd_pitches_c3b(depths)
+    lat = relay_lattice(N, pitch)
+    om, _ = O.phasor_frequencies(0.06, 4e-12, 8192, F)
+    plan = nursd.Plan(N, pitch, (0.0, 0.0), depths, om, max_points=len(lat), srsd_pitch=out_pitch)
+    plan.set_points(torch.from_numpy(lat).cuda())
+    P = random_phasors(len(lat), F, seed=BASE_SEED + 80)
+    V = plan.srsd_forward(torch.from_numpy(P).cuda()).cpu().numpy()
+    M = 2 * N
+    n_xy = np.rint(lat.astype(np.float64) / pitch).astype(int)
+    u = O.idft_grid(O.nudft_type1_lattice(P, n_xy, M))
+    for z in (0, len(depths) - 1):
+        ref = O.srsd_from_grid(u, depths[z:z + 1], out_pitch[z:z + 1] / pitch, om, pitch, N)[0]
+        assert rel(V[z], ref) < TOL

@@ -65,6 +65,7 @@ def _desc(**kw):
     d.h_depths = depths.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     d.h_omega = omega.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     d.h_weight = ctypes.POINTER(ctypes.c_double)()
+    d.h_srsd_pitch = ctypes.POINTER(ctypes.c_double)()
     for k, v in kw.items():
         setattr(d, k, v)
     return d, keep
