@@ -85,7 +85,17 @@ typedef struct {
   int32_t max_points;        /* capacity for relay samples L                       */
   const double* h_srsd_pitch; /* [Z] SRSD output pitch delta_o(z) per depth [m] (copied),
                                  or NULL: no SRSD tables are built                  */
+  int32_t max_batch;          /* capacity of nursd_forward_batched (0: not used), <= 256 */
 } nursd_desc;
+
+/* One reconstruction of a batch: L relay samples d_xy [L][2], histograms
+ * d_hist [L][T], output d_out [Z][N][N] (complex64 or magnitude float32). */
+typedef struct {
+  int32_t L;
+  const float* d_xy;
+  const float* d_hist;
+  void* d_out;
+} nursd_batch_item;
 
 /* Text for a status code (static storage). */
 const char* nursd_status_string(int status);
@@ -225,6 +235,18 @@ int nursd_grad_points(nursd_plan_t plan, const nursd_c64* d_w, const nursd_c64* 
  * nursd_set_points.
  */
 int srsd_forward(nursd_plan_t plan, const nursd_c64* d_phasor, void* d_out, nursd_stream_t stream);
+
+/*
+ * B independent reconstructions with their own relay samples and histograms
+ * (uneven L_b <= max_points), sharing the plan's geometry and transfer table:
+ * for each item, what nursd_set_points + nursd_forward compute.  The temporal
+ * transforms of all items are one persistent launch whose CTAs take 128-row
+ * tiles of the ragged batch from a device work counter; the contraction is one
+ * launch over all items that reads each table block from HBM once.  h_items is
+ * a host array read during the call.  Allocates nothing, so the call can be
+ * captured in a CUDA graph by the caller.  B <= max_batch.
+ */
+int nursd_forward_batched(nursd_plan_t plan, int32_t B, const nursd_batch_item* h_items, nursd_stream_t stream);
 
 /*
  * Stage profiling.  Stages of the forward path, each one or more kernel

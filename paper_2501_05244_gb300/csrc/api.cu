@@ -71,6 +71,12 @@ struct nursd_plan_s {
   float2* Gs = nullptr;
   float2* chirp = nullptr;
   float2* bhat = nullptr;
+  // batched reconstructions (max_batch > 0): per-item phasors, spectra and depth spectra
+  int maxB = 0;
+  float2* phasor_all = nullptr;  // [maxB][maxL][F]
+  float2* U_all = nullptr;       // [maxB][M][M][F]
+  float2* Y_all = nullptr;       // [maxB][M][M][Z]
+  int* counter = nullptr;
   // points
   int* bin_of = nullptr;
   int2* i0_orig = nullptr;
@@ -323,13 +329,14 @@ int run_nufft1(nursd_plan_s* p, const float2* phasor, float2* spec, cudaStream_t
 }
 
 // V[z][my][mx] = M^-2 sum_k Y[k][z] e^{+2 pi i k.m / M} on I_N^2 (two pruned inverse passes).
-int run_idft_crop(nursd_plan_s* p, void* out, cudaStream_t s) {
+int run_idft_crop(nursd_plan_s* p, void* out, cudaStream_t s, const float2* Ysrc = nullptr) {
+  if (!Ysrc) Ysrc = p->Y;
   const int M = p->M, N = p->N, Z = p->Z;
   const int logM = ilog2(M);
   cudaError_t e = cudaSuccess;
   {  // inverse FFT along kx, keep mx in I_N
     StageTimer t(p, NURSD_STAGE_IFFT_X, s, 1);
-    e = axis_pass(p, p->Y, p->T1, logM, true, Z, M, (long long)M * Z, Z, (long long)N * Z, Z, M, -M / 2, N, -N / 2,
+    e = axis_pass(p, Ysrc, p->T1, logM, true, Z, M, (long long)M * Z, Z, (long long)N * Z, Z, M, -M / 2, N, -N / 2,
                   nullptr, nullptr, 1.f, s);
   }
   if (e == cudaSuccess) {  // inverse FFT along ky for every (mx, z), keep my in I_N, write V[z][my][mx]
@@ -583,6 +590,8 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
   if (d->upsample != 2) return NURSD_ERR_UNSUPPORTED;
   if (d->kernel_width < 4 || d->kernel_width > kMaxKernelWidth) return NURSD_ERR_UNSUPPORTED;
   if (d->max_points < 0 || d->max_points > (1 << 26)) return NURSD_ERR_INVALID_ARG;
+  if (d->max_batch < 0 || d->max_batch > kMaxBatch) return NURSD_ERR_INVALID_ARG;
+  if (d->max_batch > 0 && d->T <= 0) return NURSD_ERR_INVALID_ARG;
   if (d->h_srsd_pitch)
     for (int i = 0; i < d->Z; ++i)
       if (!(d->h_srsd_pitch[i] > 0) || !std::isfinite(d->h_srsd_pitch[i])) return NURSD_ERR_INVALID_ARG;
@@ -607,6 +616,7 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
   p->dt = d->dt;
   p->flags = d->flags;
   p->maxL = d->max_points;
+  p->maxB = d->max_batch;
   p->beta = (float)(2.30 * p->w);
   p->depths.assign(d->h_depths, d->h_depths + d->Z);
   p->omega.assign(d->h_omega, d->h_omega + d->F);
@@ -675,6 +685,10 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
             p->alloc(p->T1, (size_t)p->M * p->N * p->Z);
   if (ok && p->T > 0) ok = p->alloc(p->Bt, Bt.size());
   if (ok && (p->flags & NURSD_ENABLE_ADJOINT)) ok = p->alloc(p->GcT, (size_t)p->ncls * p->F * p->Z);
+  if (ok && p->maxB > 0)
+    ok = p->alloc(p->phasor_all, (size_t)p->maxB * maxL * p->F) &&
+         p->alloc(p->U_all, (size_t)p->maxB * p->M * p->M * p->F) &&
+         p->alloc(p->Y_all, (size_t)p->maxB * p->M * p->M * p->Z) && p->alloc(p->counter, 1);
   if (ok && !p->srsd_pitch.empty())
     ok = p->alloc(p->Gs, (size_t)p->ncls * p->F * p->Z) && p->alloc(p->chirp, (size_t)p->Z * p->M) &&
          p->alloc(p->bhat, (size_t)p->Z * 2 * p->M);
@@ -891,6 +905,46 @@ int srsd_forward(nursd_plan_t p, const nursd_c64* d_phasor, void* d_out, nursd_s
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc = run_nufft1(p, reinterpret_cast<const float2*>(d_phasor), p->U, s);
   if (rc == NURSD_OK) rc = run_srsd(p, d_out, s);
+  return rc;
+}
+
+int nursd_forward_batched(nursd_plan_t p, int32_t B, const nursd_batch_item* items, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || p->maxB <= 0 || B < 1 || B > p->maxB || !items) return NURSD_ERR_INVALID_ARG;
+  for (int b = 0; b < B; ++b) {
+    const nursd_batch_item& it = items[b];
+    if (it.L < 0 || it.L > p->maxL || !it.d_out || !aligned(it.d_out, 8)) return NURSD_ERR_INVALID_ARG;
+    if (it.L > 0 && (!it.d_xy || !it.d_hist || !aligned(it.d_xy, 8) || !aligned(it.d_hist, 16)))
+      return NURSD_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int M = p->M, F = p->F, Z = p->Z;
+  const size_t phasor_stride = (size_t)std::max(1, p->maxL) * F;
+  const long long u_stride = (long long)M * M * F, y_stride = (long long)M * M * Z;
+  int rc = NURSD_OK;
+  {  // temporal transforms of every item: one persistent launch over the ragged tile list
+    StageTimer t(p, NURSD_STAGE_TEMPORAL, s, 1);
+    TemporalBatch bt;
+    bt.n = B;
+    bt.tile_start[0] = 0;
+    const int ncol = (2 * F + 127) / 128;
+    for (int b = 0; b < B; ++b) {
+      bt.A[b] = items[b].d_hist;
+      bt.C[b] = reinterpret_cast<float*>(p->phasor_all + b * phasor_stride);
+      bt.L[b] = items[b].L;
+      bt.tile_start[b + 1] = bt.tile_start[b] + ((items[b].L + 127) / 128) * ncol;
+    }
+    rc = from_cuda(launch_temporal_dft_batched(bt, p->Bt, p->T, 2 * F, p->counter, s));
+  }
+  for (int b = 0; rc == NURSD_OK && b < B; ++b) {  // per item: sort, spread, fine-grid FFTs -> U_all[b]
+    rc = nursd_set_points(p, items[b].L, items[b].d_xy, stream);
+    if (rc == NURSD_OK) rc = run_nufft1(p, p->phasor_all + b * phasor_stride, p->U_all + b * u_stride, s);
+  }
+  if (rc == NURSD_OK) {
+    StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
+    rc = from_cuda(
+        launch_contract_batched(p->U_all, u_stride, p->Gc, p->cls, p->ncls, M, F, Z, p->Y_all, y_stride, B, s));
+  }
+  for (int b = 0; rc == NURSD_OK && b < B; ++b) rc = run_idft_crop(p, items[b].d_out, s, p->Y_all + b * y_stride);
   return rc;
 }
 

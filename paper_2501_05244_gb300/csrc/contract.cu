@@ -26,16 +26,21 @@ constexpr int kClsPerCta = 8;
 __device__ __forceinline__ int wrap_index(int k, int M) { return (k + M / 2) & (M - 1); }
 
 // Names follow the forward direction: F is the reduced extent, Z the per-lane one.
+// Grid: x = batch item (fastest, so all items of a class group run back to back and
+// share the group's table block in L2), y = class group, z = chunk of 32*ZPL outputs.
 template <int ZPL, bool CONJ>
 __global__ void __launch_bounds__(kClsPerCta * 32, 2) contract_kernel(const float2* __restrict__ U,
                                                                    const float2* __restrict__ Gc,
                                                                    const int2* __restrict__ cls_pq, int ncls, int M,
-                                                                   int F, int Z, float2* __restrict__ Y) {
+                                                                   int F, int Z, float2* __restrict__ Y,
+                                                                   long long u_stride, long long y_stride) {
   extern __shared__ float4 us4[];  // [kClsPerCta][F][8 slots] complex as float4 pairs
   float2* us = reinterpret_cast<float2*>(us4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = blockIdx.x * kClsPerCta + warp;
-  if (c >= ncls) return;  // whole warp leaves; nothing below synchronises across warps
+  const int c = blockIdx.y * kClsPerCta + warp;
+  if (c >= ncls) return;
+  U += blockIdx.x * u_stride;
+  Y += blockIdx.x * y_stride;  // whole warp leaves; nothing below synchronises across warps
   const int2 pq = __ldg(cls_pq + c);
   const int p = pq.x, q = pq.y;
   const int kx[8] = {p, -p, p, -p, q, -q, q, -q};
@@ -50,7 +55,7 @@ __global__ void __launch_bounds__(kClsPerCta * 32, 2) contract_kernel(const floa
     for (int f = lane; f < F; f += 32) my[f * 8 + s] = __ldg(U + (size_t)off[s] * F + f);
   __syncwarp();
 
-  const int z0 = blockIdx.y * (32 * ZPL) + lane * ZPL;
+  const int z0 = blockIdx.z * (32 * ZPL) + lane * ZPL;
   float2 acc[ZPL][8];
 #pragma unroll
   for (int i = 0; i < ZPL; ++i)
@@ -114,7 +119,7 @@ __global__ void __launch_bounds__(kClsPerCta * 32, 2) contract_kernel(const floa
 
 template <int ZPL, bool CONJ>
 cudaError_t launch_zpl(const float2* U, const float2* Gc, const int2* cls_pq, int ncls, int M, int F, int Z,
-                       float2* Y, cudaStream_t s) {
+                       float2* Y, cudaStream_t s, int B = 1, long long u_stride = 0, long long y_stride = 0) {
   const size_t smem = sizeof(float2) * kClsPerCta * F * 8;
   static bool configured = false;
   if (!configured) {
@@ -123,8 +128,9 @@ cudaError_t launch_zpl(const float2* U, const float2* Gc, const int2* cls_pq, in
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  dim3 grid((ncls + kClsPerCta - 1) / kClsPerCta, (Z + 32 * ZPL - 1) / (32 * ZPL));
-  contract_kernel<ZPL, CONJ><<<grid, kClsPerCta * 32, smem, s>>>(U, Gc, cls_pq, ncls, M, F, Z, Y);
+  dim3 grid(B, (ncls + kClsPerCta - 1) / kClsPerCta, (Z + 32 * ZPL - 1) / (32 * ZPL));
+  if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
+  contract_kernel<ZPL, CONJ><<<grid, kClsPerCta * 32, smem, s>>>(U, Gc, cls_pq, ncls, M, F, Z, Y, u_stride, y_stride);
   return cudaGetLastError();
 }
 
@@ -143,6 +149,15 @@ cudaError_t launch_dir(const float2* In, const float2* T, const int2* cls_pq, in
 cudaError_t launch_contract(const float2* U, const float2* Gc, const int2* cls_pq, int ncls, int M, int F, int Z,
                             float2* Y, cudaStream_t s) {
   return launch_dir<false>(U, Gc, cls_pq, ncls, M, F, Z, Y, s);
+}
+
+cudaError_t launch_contract_batched(const float2* U, long long u_stride, const float2* Gc, const int2* cls_pq,
+                                   int ncls, int M, int F, int Z, float2* Y, long long y_stride, int B,
+                                   cudaStream_t s) {
+  if (F > 256 || B < 1) return cudaErrorInvalidValue;
+  if (Z > 64) return launch_zpl<4, false>(U, Gc, cls_pq, ncls, M, F, Z, Y, s, B, u_stride, y_stride);
+  if (Z > 32) return launch_zpl<2, false>(U, Gc, cls_pq, ncls, M, F, Z, Y, s, B, u_stride, y_stride);
+  return launch_zpl<1, false>(U, Gc, cls_pq, ncls, M, F, Z, Y, s, B, u_stride, y_stride);
 }
 
 cudaError_t launch_contract_adjoint(const float2* Yt, const float2* GcT, const int2* cls_pq, int ncls, int M, int F,

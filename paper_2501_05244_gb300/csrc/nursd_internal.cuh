@@ -21,6 +21,7 @@ namespace nursd {
 constexpr int kTile = 16;          // spreading tile edge (fine cells)
 constexpr int kTwiddleLog = 12;    // shared FFT twiddle table has 2^12 entries
 constexpr int kMaxKernelWidth = 8;
+constexpr int kMaxBatch = 256;     // reconstructions per batched call
 
 __host__ __device__ inline float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -68,6 +69,18 @@ cudaError_t launch_panel_bluestein(int logn, const PanelArgs& a, const float2* c
 cudaError_t launch_temporal_dft(const float* h, const float* B, float* C, int L, int T, int twoF,
                                 cudaStream_t s);
 
+// Ragged batch of temporal transforms: item b has L[b] rows at A[b] -> C[b];
+// tile_start[b] = number of 128 x 128 output tiles of items 0..b-1.
+struct TemporalBatch {
+  int n;
+  const float* A[kMaxBatch];
+  float* C[kMaxBatch];
+  int L[kMaxBatch];
+  int tile_start[kMaxBatch + 1];
+};
+cudaError_t launch_temporal_dft_batched(const TemporalBatch& bt, const float* B, int T, int twoF, int* counter,
+                                        cudaStream_t s);
+
 // ---------------------------------------------------------------- points
 struct PointsArgs {
   const float* xy;     // [L][2] metres
@@ -99,6 +112,11 @@ cudaError_t launch_spread(const float2* P, int F, const int* bin_start, const in
 cudaError_t launch_contract(const float2* U, const float2* Gc, const int2* cls_pq, int ncls, int M,
                             int F, int Z, float2* Y, cudaStream_t s);
 
+// Batched: B spectra U + b*u_stride -> Y + b*y_stride, consecutive CTAs sweeping the
+// batch for one class group so that each table block is read from HBM once.
+cudaError_t launch_contract_batched(const float2* U, long long u_stride, const float2* Gc, const int2* cls_pq,
+                                   int ncls, int M, int F, int Z, float2* Y, long long y_stride, int B,
+                                   cudaStream_t s);
 // Adjoint: R[k][f] = sum_z Yt[k][z] * conj(GcT[cls(k)][z][f]).
 cudaError_t launch_contract_adjoint(const float2* Yt, const float2* GcT, const int2* cls_pq, int ncls, int M, int F,
                                     int Z, float2* R, cudaStream_t s);

@@ -5,6 +5,8 @@
 // B[n][2f+1] = -w_f sin(w_f t_n) (built in FP64 on the host), and C read as
 // interleaved complex64 [L][F].  SIMT FP32 tiled GEMM: 128x128 CTA tile, k-step
 // 8, double-buffered shared-memory tiles, 8x8 outputs per thread.
+#include <algorithm>
+
 #include "nursd_internal.cuh"
 
 namespace nursd {
@@ -12,12 +14,17 @@ namespace {
 
 constexpr int BM = 128, BN = 128, BK = 8, NT = 256;
 
-__global__ void __launch_bounds__(NT, 2) sgemm_hb_kernel(const float* __restrict__ A, const float* __restrict__ B,
-                                                       float* __restrict__ C, int L, int K, int NC) {
-  __shared__ __align__(16) float As[2][BK][BM + 4];
-  __shared__ __align__(16) float Bs[2][BK][BN];
+struct GemmSmem {
+  float As[2][BK][BM + 4];
+  float Bs[2][BK][BN];
+};
+
+// One 128 x 128 output tile of C = A B (rows m0.., columns n0..).
+__device__ __forceinline__ void gemm_tile(GemmSmem& sm, const float* __restrict__ A, const float* __restrict__ B,
+                                          float* __restrict__ C, int L, int K, int NC, int m0, int n0) {
+  auto& As = sm.As;
+  auto& Bs = sm.Bs;
   const int tid = threadIdx.x;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int a_row = tid >> 1, a_k = (tid & 1) * 4;     // 128 rows x 8 k as float4
   const int tx = tid & 15, ty = tid >> 4;              // 16 x 16 compute grid
 
@@ -95,7 +102,48 @@ __global__ void __launch_bounds__(NT, 2) sgemm_hb_kernel(const float* __restrict
   }
 }
 
+__global__ void __launch_bounds__(NT, 2) sgemm_hb_kernel(const float* __restrict__ A, const float* __restrict__ B,
+                                                       float* __restrict__ C, int L, int K, int NC) {
+  __shared__ __align__(16) GemmSmem sm;
+  gemm_tile(sm, A, B, C, L, K, NC, blockIdx.y * BM, blockIdx.x * BN);
+}
+
+// Persistent form over a ragged batch: tiles of every item are numbered
+// consecutively (item b owns tiles [tile_start[b], tile_start[b+1])), and each
+// CTA takes the next tile from a device counter until none are left.
+__global__ void __launch_bounds__(NT, 2) sgemm_hb_batched_kernel(const TemporalBatch bt, const float* __restrict__ B,
+                                                               int K, int NC, int* __restrict__ counter) {
+  __shared__ __align__(16) GemmSmem sm;
+  __shared__ int tile;
+  const int ncol = (NC + BN - 1) / BN;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) tile = atomicAdd(counter, 1);
+    __syncthreads();
+    const int t = tile;
+    if (t >= bt.tile_start[bt.n]) break;
+    int b = 0;
+    while (t >= bt.tile_start[b + 1]) ++b;
+    const int local = t - bt.tile_start[b];
+    gemm_tile(sm, bt.A[b], B, bt.C[b], bt.L[b], K, NC, (local / ncol) * BM, (local % ncol) * BN);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_temporal_dft_batched(const TemporalBatch& bt, const float* B, int T, int twoF, int* counter,
+                                        cudaStream_t s) {
+  if (T % BK != 0 || bt.n < 1 || bt.n > kMaxBatch) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int tiles = bt.tile_start[bt.n];
+  const int grid = std::max(1, std::min(tiles, 2 * sms));
+  sgemm_hb_batched_kernel<<<grid, NT, 0, s>>>(bt, B, T, twoF, counter);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_temporal_dft(const float* h, const float* B, float* C, int L, int T, int twoF, cudaStream_t s) {
   if (L <= 0) return cudaSuccess;

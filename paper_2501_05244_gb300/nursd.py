@@ -32,7 +32,7 @@ EXPORTS = (
     "nursd_plan_bytes", "nursd_plan_dims", "nursd_set_points", "nursd_temporal_dft", "nursd_nufft1",
     "nursd_propagate", "nursd_forward_phasor", "nursd_forward", "nursd_sync_status",
     "nursd_profile_enable", "nursd_profile_read", "nursd_launch_count", "nursd_nufft1_noalloc",
-    "nursd_forward_points", "nursd_adjoint", "nursd_grad_points", "srsd_forward",
+    "nursd_forward_points", "nursd_adjoint", "nursd_grad_points", "srsd_forward", "nursd_forward_batched",
 )
 
 #: stage names in nursd_stage order
@@ -53,8 +53,13 @@ class _Desc(ctypes.Structure):
         ("h_weight", ctypes.POINTER(ctypes.c_double)), ("T", ctypes.c_int32), ("t0", ctypes.c_double),
         ("dt", ctypes.c_double), ("upsample", ctypes.c_int32), ("kernel_width", ctypes.c_int32),
         ("flags", ctypes.c_uint32), ("max_points", ctypes.c_int32),
-        ("h_srsd_pitch", ctypes.POINTER(ctypes.c_double)),
+        ("h_srsd_pitch", ctypes.POINTER(ctypes.c_double)), ("max_batch", ctypes.c_int32),
     ]
+
+
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("d_xy", ctypes.c_void_p), ("d_hist", ctypes.c_void_p),
+                ("d_out", ctypes.c_void_p)]
 
 
 _lib: Optional[ctypes.CDLL] = None
@@ -93,6 +98,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "nursd_adjoint": (ctypes.c_int, [vp, vp, vp, vp]),
         "nursd_grad_points": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
         "srsd_forward": (ctypes.c_int, [vp, vp, vp, vp]),
+        "nursd_forward_batched": (ctypes.c_int, [vp, i32, ctypes.POINTER(_BatchItem), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -152,7 +158,8 @@ class Plan:
 
     def __init__(self, N: int, pitch: float, center, depths, omega, weight=None, T: int = 0, t0: float = 0.0,
                  dt: float = 0.0, max_points: int = 0, kernel_width: int = 6, upsample: int = 2,
-                 magnitude: bool = False, adjoint: bool = False, srsd_pitch=None, stream=None):
+                 magnitude: bool = False, adjoint: bool = False, srsd_pitch=None, max_batch: int = 0,
+                 stream=None):
         torch = _torch()
         if not torch.cuda.is_available():
             raise RuntimeError("libnursd needs a CUDA GPU; none is available")
@@ -179,6 +186,7 @@ class Plan:
         self.srsd_pitch = None if srsd_pitch is None else np.ascontiguousarray(srsd_pitch, dtype=np.float64)
         d.h_srsd_pitch = (self.srsd_pitch.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
                           if self.srsd_pitch is not None else ctypes.POINTER(ctypes.c_double)())
+        d.max_batch = int(max_batch)
         self._desc = d
         h = ctypes.c_void_p()
         _check(self._lib.nursd_plan_create(ctypes.byref(d), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)),
@@ -289,6 +297,25 @@ class Plan:
         _check(self._lib.nursd_forward_points(self._h, p, K, v, o, ctypes.c_void_p(_stream_ptr(stream))),
                "nursd_forward_points")
         return out
+
+    def forward_batched(self, xys, hists, outs=None, stream=None):
+        """B reconstructions (lists of xy [L_b][2], hist [L_b][T]) in one call -> list of volumes."""
+        torch = _torch()
+        B = len(xys)
+        if outs is None:
+            outs = [self.empty_output() for _ in range(B)]
+        items = (_BatchItem * B)()
+        for b in range(B):
+            L = int(xys[b].shape[0])
+            items[b].L = L
+            items[b].d_xy = _dev(xys[b], torch.float32, (L, 2), "xy").value
+            items[b].d_hist = _dev(hists[b], torch.float32, (L, self.T), "hist").value
+            items[b].d_out = _dev(outs[b], self.out_dtype(), self.out_shape(), "out").value
+        self._batch_items = items  # keep alive while the call is enqueued
+        _check(self._lib.nursd_forward_batched(self._h, B, items, ctypes.c_void_p(_stream_ptr(stream))),
+               "nursd_forward_batched")
+        self.L = int(xys[-1].shape[0])
+        return outs
 
     def srsd_forward(self, phasor, out=None, stream=None):
         """Scaled RSD: plane z on the lattice of pitch srsd_pitch[z] -> [Z][N][N]."""

@@ -1,0 +1,105 @@
+"""GPU tests of the batched form (a12): uneven reconstructions in one call equal
+the single-reconstruction path (which the other GPU tests pin to the oracle),
+one item is checked against the FP64 oracle directly, and the call replays
+from a captured CUDA graph."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle as O
+import paper_2501_05244_gb300 as nursd
+from workloads import (BASE_SEED, batch_layouts_c4, batch_scenes_c4, batch_sizes_c4, device_histograms, geometry_c4,
+                       relay_uniform)
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+def rel(a, b):
+    a = np.asarray(a, np.complex128).ravel()
+    b = np.asarray(b, np.complex128).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    nursd.build()
+
+
+def small_batch(sizes, N=16, F=6, Z=4, T=64, seed=3):
+    pitch, center = 0.02, (0.0, 0.0)
+    r = np.random.default_rng(seed)
+    xys = [relay_uniform(L, N * pitch / 2 * 0.999, seed=seed + i) for i, L in enumerate(sizes)]
+    hists = [r.poisson(5.0, size=(L, T)).astype(np.float32) for L in sizes]
+    om = 2 * math.pi * np.linspace(3e9, 6e9, F)
+    return dict(N=N, pitch=pitch, center=center, xys=xys, hists=hists, om=om, depths=np.linspace(0.3, 0.9, Z),
+                T=T, t0=1e-9, dt=16e-12)
+
+
+def make_plan(c, B):
+    return nursd.Plan(c["N"], c["pitch"], c["center"], c["depths"], c["om"], T=c["T"], t0=c["t0"], dt=c["dt"],
+                      max_points=max(max(len(x) for x in c["xys"]), 1), max_batch=B)
+
+
+def test_batched_equals_single_reconstructions_and_the_oracle():
+    sizes = [100, 1, 700, 0, 2049]
+    c = small_batch(sizes)
+    plan = make_plan(c, len(sizes))
+    xys = [torch.from_numpy(x).cuda() for x in c["xys"]]
+    hists = [torch.from_numpy(h).cuda() for h in c["hists"]]
+    outs = plan.forward_batched(xys, hists)
+    for b in range(len(sizes)):
+        plan.set_points(xys[b])
+        single = plan.forward(hists[b])
+        assert torch.equal(outs[b], single), b
+    assert float(outs[3].abs().max()) == 0.0
+    P = O.temporal_dft(c["hists"][2], c["t0"], c["dt"], c["om"], np.ones(len(c["om"])))
+    ref = O.nursd_forward(P, c["xys"][2], c["center"], c["pitch"], c["N"], c["depths"], c["om"])
+    assert rel(outs[2].cpu().numpy(), ref) < TOL
+
+
+def test_batched_call_replays_from_a_cuda_graph():
+    sizes = [300, 50, 1200]
+    c = small_batch(sizes, seed=9)
+    plan = make_plan(c, 3)
+    xys = [torch.from_numpy(x).cuda() for x in c["xys"]]
+    hists = [torch.from_numpy(h).cuda() for h in c["hists"]]
+    outs = [plan.empty_output() for _ in sizes]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plan.forward_batched(xys, hists, outs)  # warm-up outside capture
+    torch.cuda.current_stream().wait_stream(s)
+    ref = [o.clone() for o in outs]
+    for o in outs:
+        o.zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.forward_batched(xys, hists, outs)
+    graph.replay()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, ref):
+        assert torch.equal(o, r)
+
+
+def test_batched_workload_of_64_uneven_reconstructions():
+    # 64 reconstructions with L_b log-uniform in [4096, 65536], T = 512 @ 8 ps, F = 64,
+    # 128^2 x 64 voxels; four items (smallest, largest, two others) against single calls.
+    g = geometry_c4()
+    sizes = batch_sizes_c4()
+    layouts = batch_layouts_c4(sizes)
+    scenes = batch_scenes_c4(len(sizes))
+    om, wt = nursd.phasor_frequencies(g.lambda_c, g.dt, g.t_pad, g.F)
+    plan = nursd.Plan(g.N, g.pitch, g.center, g.depths, om, wt, T=g.T, t0=g.t0, dt=g.dt,
+                      max_points=int(sizes.max()), max_batch=len(sizes))
+    xys = [torch.from_numpy(x).cuda() for x in layouts]
+    hists = [device_histograms(xys[b], *scenes[b], g.T, g.dt, g.t0, seed=BASE_SEED + 500 + b)
+             for b in range(len(sizes))]
+    outs = plan.forward_batched(xys, hists)
+    for b in {int(np.argmin(sizes)), int(np.argmax(sizes)), 7, 40}:
+        plan.set_points(xys[b])
+        assert torch.equal(outs[b], plan.forward(hists[b])), b

@@ -66,6 +66,7 @@ def _desc(**kw):
     d.h_omega = omega.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
     d.h_weight = ctypes.POINTER(ctypes.c_double)()
     d.h_srsd_pitch = ctypes.POINTER(ctypes.c_double)()
+    d.max_batch = 0
     for k, v in kw.items():
         setattr(d, k, v)
     return d, keep
@@ -86,6 +87,8 @@ def _desc(**kw):
     ("kernel_width", 12, binding.NURSD_ERR_UNSUPPORTED),
     ("max_points", -1, binding.NURSD_ERR_INVALID_ARG),
     ("flags", 0x80, binding.NURSD_ERR_UNSUPPORTED),
+    ("max_batch", 257, binding.NURSD_ERR_INVALID_ARG),
+    ("max_batch", -1, binding.NURSD_ERR_INVALID_ARG),
 ])
 def test_descriptor_validation_happens_on_the_host(lib, field, value, code):
     d, keep = _desc(**{field: value})

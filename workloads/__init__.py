@@ -14,6 +14,7 @@ from .generators import (  # noqa: F401
     relay_keystone,
     relay_lattice,
     simulate_histograms,
+    device_histograms,
     random_phasors,
     random_spectrum,
     random_plane_points,
@@ -34,4 +35,6 @@ from .configs import (  # noqa: F401
     workload_c2_lattice,
     workload_c5,
     batch_sizes_c4,
+    batch_layouts_c4,
+    batch_scenes_c4,
 )

@@ -138,3 +138,27 @@ def workload_c5(seed: int = BASE_SEED + 5, with_hist: bool = True) -> Workload:
                  t0=dmin / C_LIGHT - 32 * g0.dt, lambda_c=g0.lambda_c, t_pad=g0.t_pad, F=g0.F)
     h = simulate_histograms(xy, src, alb, g.T, g.dt, g.t0, seed=seed + 100) if with_hist else None
     return Workload(g, xy, h, src)
+
+
+def batch_layouts_c4(sizes, seed: int = BASE_SEED + 40):
+    """Relay layouts of the batched workload: even items uniform-random on the 2 m
+    aperture, odd items the keystone layout subsampled (seeded) to the item's size."""
+    rng = np.random.default_rng(seed)
+    key = relay_keystone(seed=seed + 1)
+    out = []
+    for b, L in enumerate(np.asarray(sizes)):
+        if b % 2 == 0:
+            out.append(relay_uniform(int(L), 0.985, seed=seed + 100 + b))
+        else:
+            out.append(key[rng.choice(len(key), int(L), replace=False)])
+    return out
+
+
+def batch_scenes_c4(B: int, seed: int = BASE_SEED + 41):
+    """Per-item point scenes (5 sources at 1-2.5 m) of the batched workload."""
+    rng = np.random.default_rng(seed)
+    scenes = []
+    for _ in range(B):
+        src = np.stack([rng.uniform(-0.7, 0.7, 5), rng.uniform(-0.7, 0.7, 5), rng.uniform(1.0, 2.5, 5)], axis=1)
+        scenes.append((src, rng.uniform(0.5, 1.0, 5)))
+    return scenes

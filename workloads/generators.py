@@ -176,3 +176,30 @@ def lattice_plane_points(Z: int, N: int, pitch: float, center=(0.0, 0.0)) -> np.
     """The N*N lattice voxels repeated on each of ``Z`` planes, float32 [Z][N*N][2]."""
     lat = relay_lattice(N, pitch, center)
     return np.broadcast_to(lat[None], (Z,) + lat.shape).copy()
+
+
+def device_histograms(xy, sources, albedo, T: int, dt: float, t0: float, peak_counts: float = 100.0,
+                      background: float = 0.01, fwhm: float = 65e-12, seed: int = 0, device="cuda"):
+    """:func:`simulate_histograms` generated on a torch device (for multi-GB batches).
+
+    Same model (Gaussian pulses at the one-way delays, amplitude albedo / r^2,
+    peak scaled to ``peak_counts`` over this call, 1% uniform background,
+    Poisson counts), drawn with a seeded torch generator.  ``xy`` is a float32
+    tensor [L][2] on ``device``; returns float32 [L][T] on ``device``.
+    """
+    import torch
+
+    sig = fwhm / (2.0 * math.sqrt(2.0 * math.log(2.0)))
+    t = t0 + dt * torch.arange(T, device=device, dtype=torch.float64)
+    xyd = xy.to(torch.float64)
+    mean = torch.zeros((xy.shape[0], T), device=device, dtype=torch.float64)
+    for src, alb in zip(np.asarray(sources, dtype=np.float64), np.asarray(albedo, dtype=np.float64)):
+        d = torch.sqrt((xyd[:, 0] - src[0]) ** 2 + (xyd[:, 1] - src[1]) ** 2 + src[2] ** 2)
+        mean += (alb / d ** 2)[:, None] * torch.exp(-((t[None, :] - d[:, None] / C_LIGHT) ** 2) / (2 * sig * sig))
+    mx = mean.max()
+    if float(mx) > 0:
+        mean *= peak_counts / mx
+    mean += background * peak_counts
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return torch.poisson(mean.to(torch.float32), generator=g)
