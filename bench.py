@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=60)
+    ap.add_argument("--no-rows", action="store_true",
+                    help="skip the per-row measurements (type-2 voxels, SRSD, adjoint, gradients, batched)")
     ap.add_argument("--workload", choices=["spad", "grid128"], default="spad",
                     help="spad: the 65k-sample 256^2x128 workload (the metric); grid128: the same samples on "
                          "128^2x64 voxels (a smaller case for profiler captures)")
@@ -162,6 +164,171 @@ def oracle_rate(wl, seconds: float, rng_seed: int = 7):
 
 
 # ---------------------------------------------------------------- GPU side ---
+
+def _time(fn, steps, warmup, stream):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def _stage_ms(plan):
+    return {k: v[0] / max(v[1], 1) for k, v in plan.profile_read().items() if v[1]}
+
+
+def measure_rows(wl, peak):
+    """Per-row measurements of the other hot-path rows on the same GPU (one entry each)."""
+    import numpy as np
+    import torch
+
+    import paper_2501_05244_gb300 as nursd
+    from workloads import (BASE_SEED, batch_layouts_c4, batch_scenes_c4, batch_sizes_c4, device_histograms,
+                           geometry_c4, random_phasors, random_plane_points, relay_keystone, srsd_depths_c3b,
+                           srsd_pitches_c3b)
+
+    stream = torch.cuda.current_stream()
+    rows = {}
+    g = wl.geom
+    om, wt = nursd.phasor_frequencies(g.lambda_c, g.dt, g.t_pad, g.F)
+    L = len(wl.xy)
+    d_xy = torch.from_numpy(wl.xy).cuda()
+    d_hist = torch.from_numpy(wl.hist).cuda()
+
+    def guarded(name, fn):
+        try:
+            rows[name] = fn()
+        except Exception as exc:  # a failing row is reported, not fatal to the headline line
+            rows[name] = {"error": f"{type(exc).__name__}: {exc}"}
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
+    def type2():
+        plan = nursd.Plan(g.N, g.pitch, g.center, g.depths, om, wt, T=g.T, t0=g.t0, dt=g.dt, max_points=L)
+        plan.set_points(d_xy)
+        P = plan.temporal_dft(d_hist)
+        K = 16384
+        vox = torch.from_numpy(random_plane_points(g.Z, K, 0.999, seed=BASE_SEED + 30)).cuda()
+        out = torch.empty((g.Z, K), dtype=torch.complex64, device="cuda")
+        plan.profile(True)
+        ms = _time(lambda: plan.forward_points(P, vox, out), 10, 2, stream)
+        st = _stage_ms(plan)
+        assert plan.sync_status() == 0
+        plan.close()
+        units = g.Z * K * g.F
+        return {"workload": "65,536 keystone samples -> 128 planes x 16,384 random voxels (2,097,152), F=128",
+                "ms": ms, "voxel_freq_per_s": units / (ms / 1e3), "stages_ms": st}
+
+    def srsd():
+        depths = srsd_depths_c3b()
+        plan = nursd.Plan(g.N, g.pitch, g.center, depths, om, wt, T=g.T, t0=g.t0, dt=g.dt, max_points=L,
+                          srsd_pitch=srsd_pitches_c3b(depths))
+        plan.set_points(d_xy)
+        P = plan.temporal_dft(d_hist)
+        out = plan.empty_output()
+        plan.profile(True)
+        ms = _time(lambda: plan.srsd_forward(P, out), 3, 1, stream)
+        prof = plan.profile_read()
+        plan.close()
+        M, F, Z = 2 * g.N, g.F, len(depths)
+        ncls = (M // 2 + 1) * (M // 2 + 2) // 2
+        s_ms = prof["srsd"][0] / 3
+        bytes_ = Z * (5 * M * M * F * 8 + ncls * F * 8 + M * M * 8) + 2 * 2 * M * M * F * 8
+        flops = Z * 2 * (M * F) * 2 * 5 * (2 * M) * np.log2(2 * M)
+        units = Z * g.N * g.N * F
+        return {"workload": "65,536 keystone samples -> 256^2 x 128 planes over 1-4 m, pitch 8 -> 32 mm, F=128",
+                "ms": ms, "voxel_freq_per_s": units / (ms / 1e3),
+                "srsd_stage": {"ms": s_ms, "algorithmic_bytes": bytes_, "achieved_gbs": bytes_ / (s_ms / 1e3) / 1e9,
+                               "hbm_frac": bytes_ / (s_ms / 1e3) / 1e9 / peak,
+                               "fft_tflops": flops / (s_ms / 1e3) / 1e12},
+                "stages_ms": {k: v[0] / 3 for k, v in prof.items() if v[1]}}
+
+    def adjoint():
+        plan = nursd.Plan(g.N, g.pitch, g.center, g.depths, om, wt, max_points=L, adjoint=True)
+        plan.set_points(d_xy)
+        r = np.random.default_rng(5)
+        V = torch.from_numpy((r.standard_normal((g.Z, g.N, g.N)) + 1j * r.standard_normal((g.Z, g.N, g.N)))
+                             .astype(np.complex64)).cuda()
+        out = torch.empty((L, g.F), dtype=torch.complex64, device="cuda")
+        plan.profile(True)
+        ms = _time(lambda: plan.adjoint(V, out), 10, 2, stream)
+        st = _stage_ms(plan)
+        plan.close()
+        units = g.Z * g.N * g.N * g.F
+        return {"workload": "spad-65k adjoint: 256^2 x 128 volume -> 65,536 x 128 phasors", "ms": ms,
+                "voxel_freq_per_s": units / (ms / 1e3), "stages_ms": st}
+
+    def grad():
+        N, Z, F = 128, 64, 128
+        xy = relay_keystone(seed=BASE_SEED + 5)
+        depths = np.linspace(0.5, 3.0, Z)
+        plan = nursd.Plan(N, 2.0 / N, (0.0, 0.0), depths, om, wt, max_points=len(xy), adjoint=True)
+        dxy = torch.from_numpy(xy).cuda()
+        P = torch.from_numpy(random_phasors(len(xy), F, seed=BASE_SEED + 6)).cuda()
+        Vt = torch.zeros((Z, N, N), dtype=torch.complex64, device="cuda")
+
+        def step():  # loss = ||A(P, x) - V_t||^2: forward, then both gradients
+            plan.set_points(dxy)
+            V = plan.forward_phasor(P)
+            plan.grad_points(2 * (V - Vt), P)
+
+        plan.profile(True)
+        ms = _time(step, 10, 2, stream)
+        st = _stage_ms(plan)
+        plan.close()
+        return {"workload": "65,536 keystone samples, F=128, 128^2 x 64: forward + gradients w.r.t. phasors "
+                            "and positions", "ms": ms, "stages_ms": st}
+
+    def batched():
+        gb = geometry_c4()
+        sizes = batch_sizes_c4()
+        layouts = batch_layouts_c4(sizes)
+        scenes = batch_scenes_c4(len(sizes))
+        omb, wtb = nursd.phasor_frequencies(gb.lambda_c, gb.dt, gb.t_pad, gb.F)
+        plan = nursd.Plan(gb.N, gb.pitch, gb.center, gb.depths, omb, wtb, T=gb.T, t0=gb.t0, dt=gb.dt,
+                          max_points=int(sizes.max()), max_batch=len(sizes))
+        xys = [torch.from_numpy(x).cuda() for x in layouts]
+        hists = [device_histograms(xys[b], *scenes[b], gb.T, gb.dt, gb.t0, seed=BASE_SEED + 500 + b)
+                 for b in range(len(sizes))]
+        outs = [plan.empty_output() for _ in sizes]
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            plan.forward_batched(xys, hists, outs)
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            plan.forward_batched(xys, hists, outs)
+        ms_graph = _time(graph.replay, 5, 1, stream)
+
+        def singles():
+            for b in range(len(sizes)):
+                plan.set_points(xys[b])
+                plan.forward(hists[b], outs[b])
+
+        ms_single = _time(singles, 3, 1, stream)
+        plan.close()
+        units = len(sizes) * gb.Z * gb.N * gb.N * gb.F
+        return {"workload": "64 reconstructions, L log-uniform 4,096-65,536 (sum %d), T=512 @ 8 ps, F=64, "
+                            "128^2 x 64 each" % int(sizes.sum()),
+                "ms_graph": ms_graph, "recon_per_s": len(sizes) / (ms_graph / 1e3),
+                "voxel_freq_per_s": units / (ms_graph / 1e3), "ms_64_single_calls": ms_single,
+                "speedup_vs_single_calls": ms_single / ms_graph}
+
+    guarded("a8_type2_voxels", type2)
+    guarded("a9_srsd", srsd)
+    guarded("a10_adjoint", adjoint)
+    guarded("a11_gradients", grad)
+    guarded("a12_batched", batched)
+    return rows
+
 
 def run_ours(args, rank, world, local):
     import numpy as np
@@ -297,6 +464,9 @@ def run_ours(args, rank, world, local):
                 "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size())},
         "clocks": clk,
     }
+    if rank == 0 and world == 1 and not args.no_rows and args.workload == "spad":
+        plan.close()
+        line["rows"] = measure_rows(wl, peak)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, desc, _ = oracle_rate(wl, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}

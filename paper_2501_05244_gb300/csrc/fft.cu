@@ -271,21 +271,21 @@ cudaError_t launch_dir(bool inverse, const PanelArgs& a, cudaStream_t s) {
 // Channels per CTA: 16 up to n = 512, then fewer so that a CTA's buffer stays
 // near 68 KB and three CTAs share an SM (overlapping one's loads with another's
 // transform).
-int panel_width(int logn) { return logn <= 9 ? 16 : (logn == 10 ? 8 : 4); }
+// Lengths 512-2048 use the register-resident kernels of fft_reg.cu (512 threads,
+// 16 / 8 / 4 channels); shorter ones this shared-memory Stockham kernel.
+int panel_width(int logn) { return logn >= 9 ? panel_width_reg(logn) : 16; }
 
 cudaError_t launch_panel_bluestein(int logn, const PanelArgs& a, const float2* cpre, const float2* bhat,
                                    const float2* cpost, cudaStream_t s) {
   if (a.CHI * a.CLO != panel_width(logn) || a.nin > (1 << logn) || a.nout > (1 << logn) || a.batch < 1 ||
       a.batch > 65535)
     return cudaErrorInvalidValue;
+  if (logn >= 9) return launch_panel_bluestein_reg(logn, a, cpre, bhat, cpost, s);
   switch (logn) {
     case 5: return launch_bluestein_one<5, 16, 128>(a, cpre, bhat, cpost, s);
     case 6: return launch_bluestein_one<6, 16, 256>(a, cpre, bhat, cpost, s);
     case 7: return launch_bluestein_one<7, 16, 256>(a, cpre, bhat, cpost, s);
     case 8: return launch_bluestein_one<8, 16, 256>(a, cpre, bhat, cpost, s);
-    case 9: return launch_bluestein_one<9, 16, 256>(a, cpre, bhat, cpost, s);
-    case 10: return launch_bluestein_one<10, 8, 256>(a, cpre, bhat, cpost, s);
-    case 11: return launch_bluestein_one<11, 4, 256>(a, cpre, bhat, cpost, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -301,9 +301,9 @@ cudaError_t launch_panel_fft(int logn, bool inverse, const PanelArgs& a, cudaStr
     case 6: return launch_dir<6, 16, 256>(inverse, a, s);
     case 7: return launch_dir<7, 16, 256>(inverse, a, s);
     case 8: return launch_dir<8, 16, 256>(inverse, a, s);
-    case 9: return launch_dir<9, 16, 256>(inverse, a, s);
-    case 10: return launch_dir<10, 8, 256>(inverse, a, s);
-    case 11: return launch_dir<11, 4, 256>(inverse, a, s);
+    case 9:
+    case 10:
+    case 11: return launch_panel_fft_reg(logn, inverse, a, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -59,6 +59,11 @@ struct PanelArgs {
 cudaError_t launch_panel_fft(int logn, bool inverse, const PanelArgs& a, cudaStream_t s);
 // Panel width (channels per CTA) used for a given transform length.
 int panel_width(int logn);
+// Register-resident kernels for 2^9..2^11 (fft_reg.cu).
+int panel_width_reg(int logn);
+cudaError_t launch_panel_fft_reg(int logn, bool inverse, const PanelArgs& a, cudaStream_t s);
+cudaError_t launch_panel_bluestein_reg(int logn, const PanelArgs& a, const float2* cpre, const float2* bhat,
+                                       const float2* cpost, cudaStream_t s);
 // Bluestein scaled DFT along the panel axis: window * cpre[i] -> FFT_n -> * bhat[bin] ->
 // inverse FFT_n -> kept bins * cpost[o] (store order: channels fastest).
 cudaError_t launch_panel_bluestein(int logn, const PanelArgs& a, const float2* cpre, const float2* bhat,
