@@ -6,6 +6,8 @@
 #include <new>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "nursd_internal.cuh"
 
 using namespace nursd;
@@ -65,7 +67,8 @@ struct nursd_plan_s {
   int2* cls = nullptr;
   float2* Gc = nullptr;
   float2* GcT = nullptr;  // transposed table [ncls][Z][F] for the adjoint (NURSD_ENABLE_ADJOINT)
-  float* Bt = nullptr;    // temporal twiddles [T][2F]
+  __half* Bth = nullptr;  // temporal twiddles B^T [2F][T], fp16 head
+  __half* Btl = nullptr;  // and tail (B - head)
   // SRSD tables (h_srsd_pitch given): scaled transfer table [Z][ncls][F], chirps [Z][M], FFT(b)/(2M) [Z][2M]
   std::vector<double> srsd_pitch;
   float2* Gs = nullptr;
@@ -655,27 +658,32 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
   cls.reserve(p->ncls);
   for (int pp = 0; pp <= half; ++pp)
     for (int qq = 0; qq <= pp; ++qq) cls.push_back(make_int2(pp, qq));
-  std::vector<float> Bt;
+  // temporal twiddles, transposed: B^T[2f][n] = w_f cos(w_f t_n), B^T[2f+1][n] = -w_f sin(w_f t_n)
+  // (FP64), stored as fp16 head + tail for the tensor-core GEMM
+  std::vector<__half> Bth, Btl;
   if (p->T > 0) {
-    Bt.resize((size_t)p->T * 2 * p->F);
-    for (int n = 0; n < p->T; ++n) {
-      const double t = p->t0 + n * p->dt;
-      for (int f = 0; f < p->F; ++f) {
-        const double ph = p->omega[f] * t;
-        Bt[(size_t)n * 2 * p->F + 2 * f] = (float)(p->weight[f] * std::cos(ph));
-        Bt[(size_t)n * 2 * p->F + 2 * f + 1] = (float)(-p->weight[f] * std::sin(ph));
+    Bth.resize((size_t)p->T * 2 * p->F);
+    Btl.resize(Bth.size());
+    for (int f = 0; f < p->F; ++f)
+      for (int n = 0; n < p->T; ++n) {
+        const double ph = p->omega[f] * (p->t0 + n * p->dt);
+        const double v[2] = {p->weight[f] * std::cos(ph), -p->weight[f] * std::sin(ph)};
+        for (int c = 0; c < 2; ++c) {
+          const __half hi = __float2half_rn((float)v[c]);
+          const size_t idx = (size_t)(2 * f + c) * p->T + n;
+          Bth[idx] = hi;
+          Btl[idx] = __float2half_rn((float)(v[c] - (double)__half2float(hi)));
+        }
       }
-    }
   }
 
   // ---- device memory
   const int maxL = std::max(1, p->maxL);
-  const int nbins = p->tiles * p->tiles;
-  const int nchunks = (maxL + 1023) / 1024;
+  const int nbins = points_bins(p->W, p->tiles);
   bool ok = p->alloc(p->twiddle, tw.size()) && p->alloc(p->deconv, p->M) && p->alloc(p->cls, p->ncls) &&
             p->alloc(p->Gc, (size_t)p->ncls * p->F * p->Z) && p->alloc(p->status, 1) &&
             p->alloc(p->bin_of, maxL) && p->alloc(p->i0_orig, maxL) && p->alloc(p->w_orig, (size_t)maxL * 2 * p->w) &&
-            p->alloc(p->counts, (size_t)nbins * nchunks) && p->alloc(p->bin_start, nbins + 1) &&
+            p->alloc(p->counts, (size_t)2 * nbins) && p->alloc(p->bin_start, nbins + 1) &&
             p->alloc(p->sorted_l, maxL) && p->alloc(p->i0_sorted, maxL) &&
             p->alloc(p->w_sorted, (size_t)maxL * 2 * p->w) && p->alloc(p->phasor, (size_t)maxL * p->F) &&
             p->alloc(p->frac_orig, maxL) && p->alloc(p->frac_sorted, maxL) &&
@@ -683,7 +691,7 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
             p->alloc(p->R1, (size_t)p->W * p->M * std::max(p->F, p->Z)) &&
             p->alloc(p->U, (size_t)p->M * p->M * p->F) && p->alloc(p->Y, (size_t)p->M * p->M * p->Z) &&
             p->alloc(p->T1, (size_t)p->M * p->N * p->Z);
-  if (ok && p->T > 0) ok = p->alloc(p->Bt, Bt.size());
+  if (ok && p->T > 0) ok = p->alloc(p->Bth, Bth.size()) && p->alloc(p->Btl, Btl.size());
   if (ok && (p->flags & NURSD_ENABLE_ADJOINT)) ok = p->alloc(p->GcT, (size_t)p->ncls * p->F * p->Z);
   if (ok && p->maxB > 0)
     ok = p->alloc(p->phasor_all, (size_t)p->maxB * maxL * p->F) &&
@@ -702,7 +710,9 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
   if (rc == NURSD_OK)
     rc = from_cuda(cudaMemcpyAsync(p->cls, cls.data(), sizeof(int2) * cls.size(), cudaMemcpyHostToDevice, s));
   if (rc == NURSD_OK && p->T > 0)
-    rc = from_cuda(cudaMemcpyAsync(p->Bt, Bt.data(), sizeof(float) * Bt.size(), cudaMemcpyHostToDevice, s));
+    rc = from_cuda(cudaMemcpyAsync(p->Bth, Bth.data(), sizeof(__half) * Bth.size(), cudaMemcpyHostToDevice, s));
+  if (rc == NURSD_OK && p->T > 0)
+    rc = from_cuda(cudaMemcpyAsync(p->Btl, Btl.data(), sizeof(__half) * Btl.size(), cudaMemcpyHostToDevice, s));
   if (rc == NURSD_OK) rc = from_cuda(cudaMemsetAsync(p->status, 0, sizeof(int), s));
   if (rc == NURSD_OK) rc = from_cuda(cudaMemsetAsync(p->bin_start, 0, sizeof(int) * (nbins + 1), s));
   if (rc == NURSD_OK) rc = build_table(p, false, s);
@@ -762,8 +772,8 @@ int nursd_temporal_dft(nursd_plan_t p, int32_t L, const float* d_hist, nursd_c64
   if (check_plan(p) != NURSD_OK || p->T <= 0 || L < 0 || L > p->maxL) return NURSD_ERR_INVALID_ARG;
   if (L > 0 && (!d_hist || !d_phasor || !aligned(d_hist, 16) || !aligned(d_phasor, 8))) return NURSD_ERR_INVALID_ARG;
   StageTimer t(p, NURSD_STAGE_TEMPORAL, static_cast<cudaStream_t>(stream), L > 0 ? 1 : 0);
-  return from_cuda(launch_temporal_dft(d_hist, p->Bt, reinterpret_cast<float*>(d_phasor), L, p->T, 2 * p->F,
-                                       static_cast<cudaStream_t>(stream)));
+  return from_cuda(launch_temporal_tc(d_hist, p->Bth, p->Btl, reinterpret_cast<float*>(d_phasor), L, p->T, 2 * p->F,
+                                      static_cast<cudaStream_t>(stream)));
 }
 
 int nursd_nufft1(nursd_plan_t p, const nursd_c64* d_phasor, nursd_c64* d_spectrum, nursd_stream_t stream) {
@@ -795,7 +805,8 @@ int nursd_forward(nursd_plan_t p, const float* d_hist, void* d_out, nursd_stream
   int rc;
   {
     StageTimer t(p, NURSD_STAGE_TEMPORAL, s, p->L > 0 ? 1 : 0);
-    rc = from_cuda(launch_temporal_dft(d_hist, p->Bt, reinterpret_cast<float*>(p->phasor), p->L, p->T, 2 * p->F, s));
+    rc = from_cuda(launch_temporal_tc(d_hist, p->Bth, p->Btl, reinterpret_cast<float*>(p->phasor), p->L, p->T,
+                                      2 * p->F, s));
   }
   if (rc == NURSD_OK) rc = run_nufft1(p, p->phasor, p->U, s);
   if (rc == NURSD_OK) rc = run_propagate(p, p->U, d_out, s);
@@ -933,7 +944,7 @@ int nursd_forward_batched(nursd_plan_t p, int32_t B, const nursd_batch_item* ite
       bt.L[b] = items[b].L;
       bt.tile_start[b + 1] = bt.tile_start[b] + ((items[b].L + 127) / 128) * ncol;
     }
-    rc = from_cuda(launch_temporal_dft_batched(bt, p->Bt, p->T, 2 * F, p->counter, s));
+    rc = from_cuda(launch_temporal_tc_batched(bt, p->Bth, p->Btl, p->T, 2 * F, p->counter, s));
   }
   for (int b = 0; rc == NURSD_OK && b < B; ++b) {  // per item: sort, spread, fine-grid FFTs -> U_all[b]
     rc = nursd_set_points(p, items[b].L, items[b].d_xy, stream);

@@ -65,9 +65,8 @@ __global__ void __launch_bounds__(kClsPerCta * 32, 2) contract_kernel(const floa
   const float2* __restrict__ g = Gc + (size_t)c * F * Z + z0;
   // 16-byte vector access needs an even Z (all row offsets are then even)
   const bool full = (z0 + ZPL <= Z) && ((Z & 1) == 0);
-#pragma unroll 2
-  for (int f = 0; f < F; ++f) {
-    float2 gv[ZPL];
+  auto load_row = [&](int f, float2* gv) {
+    if (f >= F) return;
     if (full && (ZPL % 2 == 0)) {
 #pragma unroll
       for (int i = 0; i < ZPL; i += 2) {
@@ -77,30 +76,46 @@ __global__ void __launch_bounds__(kClsPerCta * 32, 2) contract_kernel(const floa
       }
     } else {
 #pragma unroll
-      for (int i = 0; i < ZPL; ++i)
-        gv[i] = (z0 + i < Z) ? __ldg(g + (size_t)f * Z + i) : make_float2(0.f, 0.f);
+      for (int i = 0; i < ZPL; ++i) gv[i] = (z0 + i < Z) ? __ldg(g + (size_t)f * Z + i) : make_float2(0.f, 0.f);
     }
-    if (CONJ) {
+  };
+  // table rows are prefetched kAhead rows ahead of their use, so that each warp keeps
+  // about kAhead x 1 KB in flight
+  constexpr int kAhead = ZPL == 4 ? 3 : 4;
+  float2 ring[kAhead][ZPL];
 #pragma unroll
-      for (int i = 0; i < ZPL; ++i) gv[i].y = -gv[i].y;
-    }
-    const float4* u4 = reinterpret_cast<const float4*>(my + f * 8);
-    float2 u[8];
+  for (int d = 0; d < kAhead; ++d) load_row(d, ring[d]);
+  for (int fb = 0; fb < F; fb += kAhead) {
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const float4 t = u4[s];
-      u[2 * s] = make_float2(t.x, t.y);
-      u[2 * s + 1] = make_float2(t.z, t.w);
-    }
+    for (int d = 0; d < kAhead; ++d) {
+      const int f = fb + d;
+      if (f >= F) break;
+      float2 gv[ZPL];
 #pragma unroll
-    for (int i = 0; i < ZPL; ++i)
+      for (int i = 0; i < ZPL; ++i) gv[i] = ring[d][i];
+      load_row(f + kAhead, ring[d]);
+      if (CONJ) {
 #pragma unroll
-      for (int s = 0; s < 8; ++s) {
-        acc[i][s].x = fmaf(gv[i].x, u[s].x, acc[i][s].x);
-        acc[i][s].x = fmaf(-gv[i].y, u[s].y, acc[i][s].x);
-        acc[i][s].y = fmaf(gv[i].x, u[s].y, acc[i][s].y);
-        acc[i][s].y = fmaf(gv[i].y, u[s].x, acc[i][s].y);
+        for (int i = 0; i < ZPL; ++i) gv[i].y = -gv[i].y;
       }
+      const float4* u4 = reinterpret_cast<const float4*>(my + f * 8);
+      float2 u[8];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const float4 t = u4[s];
+        u[2 * s] = make_float2(t.x, t.y);
+        u[2 * s + 1] = make_float2(t.z, t.w);
+      }
+#pragma unroll
+      for (int i = 0; i < ZPL; ++i)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          acc[i][s].x = fmaf(gv[i].x, u[s].x, acc[i][s].x);
+          acc[i][s].x = fmaf(-gv[i].y, u[s].y, acc[i][s].x);
+          acc[i][s].y = fmaf(gv[i].x, u[s].y, acc[i][s].y);
+          acc[i][s].y = fmaf(gv[i].y, u[s].x, acc[i][s].y);
+        }
+    }
   }
 #pragma unroll
   for (int s = 0; s < 8; ++s) {

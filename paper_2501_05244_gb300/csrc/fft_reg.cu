@@ -13,6 +13,8 @@
 // With T = n/16 threads per transform, thread j0 does butterfly j0 of stages 1
 // and 2 and butterflies j0 + m T (m < 16/R3) of stage 3, whose outputs are the
 // final bins j + 256 t.
+#include <algorithm>
+
 #include "nursd_internal.cuh"
 
 namespace nursd {
@@ -276,6 +278,120 @@ __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT) panel_bluestein_reg_ke
     }
 }
 
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  const int n = valid ? 8 : 0;  // src-size 0 zero-fills the destination
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Persistent, double-buffered form: each CTA walks panels p = blockIdx.x, +gridDim.x, ...
+// (panel = channel chunk + batch item) and, while it transforms one, the next one's input
+// window streams into the other staging buffer with cp.async.
+template <int LOGN, int CP, bool INV>
+__global__ void __launch_bounds__(RegShape<LOGN, CP>::NT) panel_fft_pipe_kernel(const PanelArgs a, int npanel) {
+  using S = RegShape<LOGN, CP>;
+  constexpr int n = S::n, T = S::T, SR = S::SR, R3 = n / 256, NT = S::NT;
+  extern __shared__ float2 sm[];
+  float2* xbuf = sm;                          // exchange buffer [n][SR]
+  float2* ibuf0 = sm + n * SR;                // staging [nin][CP], two of them
+  float2* ibuf1 = ibuf0 + (size_t)a.nin * CP;
+  const int tid = threadIdx.x;
+  int j0, q;
+  if (a.load_i_fastest) {
+    j0 = tid % T;
+    q = tid / T;
+  } else {
+    q = tid % CP;
+    j0 = tid / CP;
+  }
+  const int nlo = (a.lo_total + a.CLO - 1) / a.CLO;
+  const int nchunk = ((a.hi_total + a.CHI - 1) / a.CHI) * nlo;
+
+  // Copy work per thread: a fixed channel column and every (NT/CP)-th row (or, for
+  // load_i_fastest, a fixed row residue), so each copy is a pointer increment.
+  constexpr int RSTEP = NT / CP;
+  auto issue = [&](int p, float2* buf) {
+    const int chunk = p % nchunk, b = p / nchunk;
+    const int hi0 = (chunk / nlo) * a.CHI, lo0 = (chunk % nlo) * a.CLO;
+    const float2* inb = a.in + (long long)b * a.in_sb;
+    if (!a.load_i_fastest) {
+      const int qq = tid % CP;
+      const int hi = hi0 + qq / a.CLO, lo = lo0 + qq % a.CLO;
+      const bool ok = hi < a.hi_total && lo < a.lo_total;
+      const float2* src = inb + (long long)hi * a.in_shi + (long long)lo * a.in_slo;
+      const long long step = (long long)RSTEP * a.in_si;
+      int i = tid / CP;
+      src += (long long)i * a.in_si;
+      for (; i < a.nin; i += RSTEP, src += step) cp_async8(buf + i * CP + qq, ok ? src : a.in, ok);
+    } else {
+      for (int idx = tid; idx < a.nin * CP; idx += NT) {
+        const int i = idx % a.nin, qq = idx / a.nin;
+        const int hi = hi0 + qq / a.CLO, lo = lo0 + qq % a.CLO;
+        const bool ok = hi < a.hi_total && lo < a.lo_total;
+        const float2* src = ok ? inb + (long long)i * a.in_si + (long long)hi * a.in_shi + (long long)lo * a.in_slo : a.in;
+        cp_async8(buf + i * CP + qq, src, ok);
+      }
+    }
+  };
+
+  int p = blockIdx.x;
+  if (p < npanel) issue(p, ibuf0);
+  cp_async_commit();
+  for (int k = 0; p < npanel; p += gridDim.x, ++k) {
+    float2* cur = (k & 1) ? ibuf1 : ibuf0;
+    float2* nxt = (k & 1) ? ibuf0 : ibuf1;
+    if (p + (int)gridDim.x < npanel) issue(p + gridDim.x, nxt);
+    cp_async_commit();
+    cp_async_wait_1();
+    __syncthreads();
+    const int chunk = p % nchunk, b = p / nchunk;
+    const int hi = (chunk / nlo) * a.CHI + q / a.CLO;
+    const int lo = (chunk % nlo) * a.CLO + q % a.CLO;
+    const bool valid = hi < a.hi_total && lo < a.lo_total;
+    float2 v[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      const int i = (j0 + t * T - a.in_off) & (n - 1);
+      float2 x = make_float2(0.f, 0.f);
+      if (i < a.nin) {
+        x = cur[i * CP + q];
+        if (a.mul_i) {
+          const float m = __ldg(a.mul_i + i);
+          x.x *= m;
+          x.y *= m;
+        }
+      }
+      v[t] = x;
+    }
+    fft_core<LOGN, SR, INV>(v, xbuf, j0, q, a.twiddle);  // its barriers also retire every read of `cur`
+    if (valid) {
+      const float sb = a.scale * (a.mul_b ? a.mul_b[b] : 1.f);
+      const long long obase = (long long)b * a.out_sb + (long long)hi * a.out_shi + (long long)lo * a.out_slo;
+#pragma unroll
+      for (int m = 0; m < 16 / R3; ++m)
+#pragma unroll
+        for (int t = 0; t < R3; ++t) {
+          const int bin = j0 + m * T + 256 * t;
+          const int o = (bin - a.out_off) & (n - 1);
+          if (o < a.nout) {
+            float2 x = v[m * R3 + t];
+            const float sc = sb * (a.mul_o ? __ldg(a.mul_o + o) : 1.f);
+            x.x *= sc;
+            x.y *= sc;
+            const long long off = obase + (long long)o * a.out_si;
+            if (a.out_mag)
+              a.out_mag[off] = sqrtf(x.x * x.x + x.y * x.y);
+            else
+              a.out[off] = x;
+          }
+        }
+    }
+    __syncthreads();  // the exchange buffer is rewritten by the next panel's stage 1
+  }
+}
+
 template <class K>
 cudaError_t configure(K kernel, size_t smem) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -284,6 +400,27 @@ cudaError_t configure(K kernel, size_t smem) {
 template <int LOGN, int CP, bool INV>
 cudaError_t launch_reg(const PanelArgs& a, cudaStream_t s) {
   using S = RegShape<LOGN, CP>;
+  const int nhi = (a.hi_total + a.CHI - 1) / a.CHI;
+  const int nlo = (a.lo_total + a.CLO - 1) / a.CLO;
+  const long long npanel = (long long)nhi * nlo * a.batch;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const size_t smem_pipe = sizeof(float2) * ((size_t)S::n * S::SR + 2 * (size_t)a.nin * CP);
+  if (npanel >= 4LL * sms && smem_pipe <= 220 * 1024) {  // enough panels to stream: persistent form
+    static size_t configured_pipe = 0;
+    if (configured_pipe < smem_pipe) {
+      cudaError_t e = configure(panel_fft_pipe_kernel<LOGN, CP, INV>, 220 * 1024);
+      if (e != cudaSuccess) return e;
+      configured_pipe = 220 * 1024;
+    }
+    const int grid = (int)std::min<long long>(npanel, (long long)sms * (smem_pipe <= 110 * 1024 ? 2 : 1));
+    panel_fft_pipe_kernel<LOGN, CP, INV><<<grid, S::NT, smem_pipe, s>>>(a, (int)npanel);
+    return cudaGetLastError();
+  }
   const size_t smem = sizeof(float2) * S::n * S::SR;
   static bool configured = false;
   if (!configured) {
@@ -291,8 +428,6 @@ cudaError_t launch_reg(const PanelArgs& a, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const int nhi = (a.hi_total + a.CHI - 1) / a.CHI;
-  const int nlo = (a.lo_total + a.CLO - 1) / a.CLO;
   panel_fft_reg_kernel<LOGN, CP, INV><<<dim3(nhi * nlo, a.batch), S::NT, smem, s>>>(a);
   return cudaGetLastError();
 }

@@ -140,15 +140,14 @@ extern "C" int nursd_nufft1_noalloc(int32_t N, double pitch, double center_x, do
   // geometry, exactly as a plan derives it
   const int M = 2 * N, nf = 2 * M, w = kernel_width;
   const int W = (2 * N + w + 2 + kTile - 1) / kTile * kTile;
-  const int tiles = W / kTile, g0 = -W / 2, nbins = tiles * tiles;
-  const int nchunks = (L + 1023) / 1024;
+  const int tiles = W / kTile, g0 = -W / 2, nbins = points_bins(W, tiles);
   const float beta = (float)(2.30 * w);
 
   // regions of the per-call part; reject sizes that do not fit before touching the device
   Layout lay;
   const size_t o_dec = lay.take<float>(M), o_status = lay.take<int>(1), o_bin = lay.take<int>(L),
                o_i0o = lay.take<int2>(L), o_wo = lay.take<float>((size_t)L * 2 * w),
-               o_cnt = lay.take<int>((size_t)nbins * (nchunks ? nchunks : 1)), o_bs = lay.take<int>(nbins + 1),
+               o_cnt = lay.take<int>((size_t)2 * nbins), o_bs = lay.take<int>(nbins + 1),
                o_sl = lay.take<int>(L), o_i0s = lay.take<int2>(L), o_ws = lay.take<float>((size_t)L * 2 * w),
                o_fine = lay.take<float2>((size_t)W * W * F), o_r1 = lay.take<float2>((size_t)W * M * F);
   if (lay.used > kNoAllocScratchBytes - kTableBytes) return NURSD_ERR_UNSUPPORTED;

@@ -70,9 +70,10 @@ cudaError_t launch_panel_bluestein(int logn, const PanelArgs& a, const float2* c
                                    const float2* cpost, cudaStream_t s);
 
 // ------------------------------------------------------------- temporal DFT
-// P[l][f] = sum_n h[l][n] * B[n][2f..2f+1] as a real GEMM C[L][2F] = H[L][T] B[T][2F].
-cudaError_t launch_temporal_dft(const float* h, const float* B, float* C, int L, int T, int twoF,
-                                cudaStream_t s);
+// P[l][f] = sum_n h[l][n] * B[n][2f..2f+1] as a real GEMM C[L][2F] = H[L][T] B[T][2F] on the
+// tensor cores; Bh/Bl are the fp16 head and tail of B^T, [2F][T] (__half).
+cudaError_t launch_temporal_tc(const float* h, const void* Bh, const void* Bl, float* C, int L, int T, int twoF,
+                               cudaStream_t s);
 
 // Ragged batch of temporal transforms: item b has L[b] rows at A[b] -> C[b];
 // tile_start[b] = number of 128 x 128 output tiles of items 0..b-1.
@@ -83,8 +84,8 @@ struct TemporalBatch {
   int L[kMaxBatch];
   int tile_start[kMaxBatch + 1];
 };
-cudaError_t launch_temporal_dft_batched(const TemporalBatch& bt, const float* B, int T, int twoF, int* counter,
-                                        cudaStream_t s);
+cudaError_t launch_temporal_tc_batched(const TemporalBatch& bt, const void* Bh, const void* Bl, int T, int twoF,
+                                       int* counter, cudaStream_t s);
 
 // ---------------------------------------------------------------- points
 struct PointsArgs {
@@ -98,10 +99,11 @@ struct PointsArgs {
   float beta;                     // ES kernel shape
   int* status;                    // device error word
 };
-// Prepare and sort the relay samples.  Scratch in original order: bin_of [L],
-// i0_orig [L], w_orig [L][2w]; counts needs nbins*nchunks ints (nchunks =
-// ceil(L/1024)).  Sorted outputs: sorted_l [L] (original index), i0_sorted,
-// w_sorted, and bin_start [nbins+1] (first sorted slot of each tile).
+// Prepare and sort the relay samples by bin = (footprint row, tile column),
+// nbins = points_bins(W, tiles).  Scratch in original order: bin_of [L],
+// i0_orig [L], w_orig [L][2w]; counts needs 2*nbins ints.  Sorted outputs:
+// sorted_l [L] (original index), i0_sorted, w_sorted, and bin_start [nbins+1].
+int points_bins(int W, int tiles);
 // frac_sorted (optional) receives u - i0 per axis of each sorted sample.
 cudaError_t launch_points(const PointsArgs& a, int* bin_of, int2* i0_orig, float* w_orig, int* counts,
                           int* bin_start, int* sorted_l, int2* i0_sorted, float* w_sorted, cudaStream_t s,

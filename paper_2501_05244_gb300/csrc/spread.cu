@@ -1,100 +1,67 @@
 // NUFFT type-1 spreading (Sec. 6, step 1): b[g][f] = sum_l P[l][f] phi_x phi_y.
 //
-// Atomic-free: one CTA owns a 16 x 16-cell tile of the fine-grid window for 32
-// channels; each of its 16 warps owns one tile row and each lane one channel,
-// accumulating the row's 16 cells in registers.  The samples that can touch
-// the tile are those sorted into the tile's bin and the bins above / left of
-// it (a footprint of w <= 8 cells crosses at most one tile edge per axis).
-// They are staged in shared memory in batches (phasor row slice, 2w weights,
-// footprint origin), then every warp walks the batch and adds the taps that
-// fall in its row.  Each fine-grid cell is written exactly once, so the
-// window needs no clearing, and the summation order is fixed by the stable
-// sort.
+// No atomics: one CTA owns a 16 x 16-cell tile of the fine-grid window for 32
+// channels; each of its 16 warps owns one tile row and each lane one channel.
+// Samples are binned by (first footprint row, tile column), so the warp for
+// row y reads exactly the 2w bins whose samples cover y -- first rows y-w+1..y
+// in this tile column and the one to the left (a footprint of w <= 8 cells
+// crosses at most one tile edge) -- and adds each sample's taps in that row to
+// its private row of 16 cells in shared memory.  Every window cell is written
+// exactly once, and the summation order is the sorted order, so results are
+// reproducible run to run.
 #include "nursd_internal.cuh"
 
 namespace nursd {
 namespace {
 
-constexpr int kBatch = 64;
-constexpr int kWarps = kTile;  // one warp per tile row
+constexpr int kWarps = 16;
 
 __global__ void __launch_bounds__(kWarps * 32) spread_kernel(const float2* __restrict__ P, int F,
                                                              const int* __restrict__ bin_start,
                                                              const int* __restrict__ sorted_l,
                                                              const int2* __restrict__ i0, const float* __restrict__ wts,
                                                              int width, int tiles, int W, float2* __restrict__ fine) {
-  __shared__ float2 sp[kBatch][32];
-  __shared__ float sw[kBatch][2 * kMaxKernelWidth];
-  __shared__ int2 si[kBatch];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  extern __shared__ float2 rowbuf[];  // [kWarps][kTile][32]: each warp's tile row, 32 channels
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ty = blockIdx.x / tiles, tx = blockIdx.x % tiles;
   const int f0 = blockIdx.y * 32;
-  const int row = ty * kTile + warp;  // window row owned by this warp
-  const int col0 = tx * kTile;
-
-  // the (up to) four source bins, as a concatenated virtual list
-  int rs[4], rl[4], n = 0;
+  const int y = ty * kTile + warp, col0 = tx * kTile;  // this warp's window row and the tile's first column
+  float2* row = rowbuf + warp * kTile * 32;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int by = ty - (k >> 1), bx = tx - (k & 1);
-    int s = 0, l = 0;
-    if (by >= 0 && bx >= 0) {
-      const int b = by * tiles + bx;
-      s = bin_start[b];
-      l = bin_start[b + 1] - s;
-    }
-    rs[k] = s;
-    rl[k] = l;
-    n += l;
-  }
-
-  float2 acc[kTile];
-#pragma unroll
-  for (int c = 0; c < kTile; ++c) acc[c] = make_float2(0.f, 0.f);
-
+  for (int c = 0; c < kTile; ++c) row[c * 32 + lane] = make_float2(0.f, 0.f);
+  const bool live = f0 + lane < F;
   const int tw = 2 * width;
-  for (int base = 0; base < n; base += kBatch) {
-    const int nb = min(kBatch, n - base);
-    __syncthreads();
-    for (int idx = tid; idx < nb * 32; idx += kWarps * 32) {
-      const int p = idx >> 5, c = idx & 31;
-      int v = base + p, k = 0;
-      while (v >= rl[k]) {
-        v -= rl[k];
-        ++k;
-      }
-      const int slot = rs[k] + v;
-      const int l = __ldg(sorted_l + slot);
-      sp[p][c] = (f0 + c < F) ? __ldg(P + (size_t)l * F + f0 + c) : make_float2(0.f, 0.f);
-      if (c < tw) sw[p][c] = __ldg(wts + (size_t)slot * tw + c);
-      if (c == 0) si[p] = __ldg(i0 + slot);
-    }
-    __syncthreads();
-    for (int p = 0; p < nb; ++p) {
-      const int2 o = si[p];
-      const int dy = row - o.y;
-      if ((unsigned)dy < (unsigned)width) {
-        float2 v = sp[p][lane];
-        const float wy = sw[p][width + dy];
+  // samples whose footprint covers row y: first row in (y - w, y], tile column tx - 1 or tx
+  for (int d = 0; d < width; ++d) {
+    const int r0 = y - d;
+    if (r0 < 0) break;
+    for (int e = 0; e < 2; ++e) {
+      const int tc = tx - e;
+      if (tc < 0) continue;
+      const int b = r0 * tiles + tc;
+      const int s_end = bin_start[b + 1];
+      for (int slot = bin_start[b]; slot < s_end; ++slot) {
+        const int l = __ldg(sorted_l + slot);
+        const int ox = __ldg(i0 + slot).x;
+        const float* w = wts + (size_t)slot * tw;
+        const float wy = __ldg(w + width + d);
+        float2 v = live ? __ldg(P + (size_t)l * F + f0 + lane) : make_float2(0.f, 0.f);
         v.x *= wy;
         v.y *= wy;
-        const int sh = o.x - col0;  // tap t lands in tile column sh + t
-#pragma unroll
-        for (int c = 0; c < kTile; ++c) {
-          const int t = c - sh;
-          if ((unsigned)t < (unsigned)width) {
-            const float wx = sw[p][t];
-            acc[c].x = fmaf(v.x, wx, acc[c].x);
-            acc[c].y = fmaf(v.y, wx, acc[c].y);
-          }
+        const int c_lo = max(0, col0 - ox), c_hi = min(width, col0 + kTile - ox);
+        for (int c = c_lo; c < c_hi; ++c) {
+          const float wx = __ldg(w + c);
+          float2& cell = row[(ox + c - col0) * 32 + lane];
+          cell.x = fmaf(v.x, wx, cell.x);
+          cell.y = fmaf(v.y, wx, cell.y);
         }
       }
     }
   }
-  if (f0 + lane < F) {
-    float2* dst = fine + ((size_t)row * W + col0) * F + f0 + lane;
+  if (live) {
+    float2* dst = fine + ((size_t)y * W + col0) * F + f0 + lane;
 #pragma unroll
-    for (int c = 0; c < kTile; ++c) dst[(size_t)c * F] = acc[c];
+    for (int c = 0; c < kTile; ++c) dst[(size_t)c * F] = row[c * 32 + lane];
   }
 }
 
@@ -103,8 +70,15 @@ __global__ void __launch_bounds__(kWarps * 32) spread_kernel(const float2* __res
 cudaError_t launch_spread(const float2* P, int F, const int* bin_start, const int* sorted_l, const int2* i0,
                           const float* wts, int width, int tiles, int W, float2* fine, cudaStream_t s) {
   if (width > kMaxKernelWidth || W != tiles * kTile) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(float2) * kWarps * kTile * 32;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(spread_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
   dim3 grid(tiles * tiles, (F + 31) / 32);
-  spread_kernel<<<grid, kWarps * 32, 0, s>>>(P, F, bin_start, sorted_l, i0, wts, width, tiles, W, fine);
+  spread_kernel<<<grid, kWarps * 32, smem, s>>>(P, F, bin_start, sorted_l, i0, wts, width, tiles, W, fine);
   return cudaGetLastError();
 }
 

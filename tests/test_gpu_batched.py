@@ -1,5 +1,6 @@
 """GPU tests of the batched form (a12): uneven reconstructions in one call equal
-the single-reconstruction path (which the other GPU tests pin to the oracle),
+the single-reconstruction path (which the other GPU tests pin to the oracle) to
+FP32 rounding of the spread's summation order,
 one item is checked against the FP64 oracle directly, and the call replays
 from a captured CUDA graph."""
 import math
@@ -55,7 +56,8 @@ def test_batched_equals_single_reconstructions_and_the_oracle():
     for b in range(len(sizes)):
         plan.set_points(xys[b])
         single = plan.forward(hists[b])
-        assert torch.equal(outs[b], single), b
+        if sizes[b]:
+            assert rel(outs[b].cpu().numpy(), single.cpu().numpy()) < 1e-6, b
     assert float(outs[3].abs().max()) == 0.0
     P = O.temporal_dft(c["hists"][2], c["t0"], c["dt"], c["om"], np.ones(len(c["om"])))
     ref = O.nursd_forward(P, c["xys"][2], c["center"], c["pitch"], c["N"], c["depths"], c["om"])
@@ -83,7 +85,7 @@ def test_batched_call_replays_from_a_cuda_graph():
     graph.replay()
     torch.cuda.synchronize()
     for o, r in zip(outs, ref):
-        assert torch.equal(o, r)
+        assert rel(o.cpu().numpy(), r.cpu().numpy()) < 1e-6
 
 
 def test_batched_workload_of_64_uneven_reconstructions():
@@ -102,4 +104,4 @@ def test_batched_workload_of_64_uneven_reconstructions():
     outs = plan.forward_batched(xys, hists)
     for b in {int(np.argmin(sizes)), int(np.argmax(sizes)), 7, 40}:
         plan.set_points(xys[b])
-        assert torch.equal(outs[b], plan.forward(hists[b])), b
+        assert rel(outs[b].cpu().numpy(), plan.forward(hists[b]).cpu().numpy()) < 1e-6, b
