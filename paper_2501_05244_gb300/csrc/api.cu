@@ -377,7 +377,7 @@ int run_propagate(nursd_plan_s* p, const float2* spec, void* out, cudaStream_t s
   cudaError_t e;
   {
     StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
-    e = launch_contract(spec, p->Gc, p->cls, p->ncls, p->M, p->F, p->Z, p->Y, s);
+    e = launch_contract(spec, p->Gc, p->cls, p->ncls, p->M, p->F, p->Z, p->Y, s, p->status);
   }
   if (e != cudaSuccess) return from_cuda(e);
   return run_idft_crop(p, out, s);
@@ -468,7 +468,7 @@ int run_adjoint_spectrum(nursd_plan_s* p, const float2* vol, cudaStream_t s) {
   }
   if (e == cudaSuccess) {
     StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
-    e = launch_contract_adjoint(p->Y, p->GcT, p->cls, p->ncls, M, F, Z, p->U, s);
+    e = launch_contract_adjoint(p->Y, p->GcT, p->cls, p->ncls, M, F, Z, p->U, s, p->status);
   }
   return from_cuda(e);
 }
@@ -884,7 +884,7 @@ int nursd_forward_points(nursd_plan_t p, const nursd_c64* d_phasor, int32_t K, c
   int rc = run_nufft1(p, reinterpret_cast<const float2*>(d_phasor), p->U, s);
   if (rc == NURSD_OK) {
     StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
-    rc = from_cuda(launch_contract(p->U, p->Gc, p->cls, p->ncls, M, p->F, p->Z, p->Y, s));
+    rc = from_cuda(launch_contract(p->U, p->Gc, p->cls, p->ncls, M, p->F, p->Z, p->Y, s, p->status));
   }
   if (rc == NURSD_OK) rc = run_type2_to_fine(p, p->Y, p->Z, true, 1.f / ((float)M * (float)M), s);
   if (rc == NURSD_OK && K > 0) {
@@ -953,7 +953,8 @@ int nursd_forward_batched(nursd_plan_t p, int32_t B, const nursd_batch_item* ite
   if (rc == NURSD_OK) {
     StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
     rc = from_cuda(
-        launch_contract_batched(p->U_all, u_stride, p->Gc, p->cls, p->ncls, M, F, Z, p->Y_all, y_stride, B, s));
+        launch_contract_batched(p->U_all, u_stride, p->Gc, p->cls, p->ncls, M, F, Z, p->Y_all, y_stride, B, s,
+                                p->status));
   }
   for (int b = 0; rc == NURSD_OK && b < B; ++b) rc = run_idft_crop(p, items[b].d_out, s, p->Y_all + b * y_stride);
   return rc;

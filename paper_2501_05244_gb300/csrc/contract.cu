@@ -132,6 +132,188 @@ __global__ void __launch_bounds__(kClsPerCta * 32, 2) contract_kernel(const floa
   }
 }
 
+// ------------------------------------------------------------------ bulk-copy form
+// Same arithmetic; each warp streams its class through a 3-stage shared-memory
+// ring filled by cp.async.bulk (the TMA's 1-D mode) and completed on an
+// mbarrier with a transaction count.  A stage holds kRows table rows (one
+// contiguous copy of kRows x ZS values) and the class's 8 spectrum segments of
+// those rows (8 copies of kRows values).  16 warps per CTA (one class each)
+// keep ~200 KB per SM in flight.  Used when every CTA column is full
+// (J % (32 ZPL) == 0) and R % kRows == 0, so every copy is a whole number of
+// 16-byte units.  Every barrier wait is bounded: on time-out the kernel sets
+// status bit 2 and returns.
+constexpr int kTmaWarps = 16, kStages = 3, kRows = 4;
+constexpr long long kWaitLimit = 1LL << 22;
+
+__device__ __forceinline__ unsigned sm_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(sm_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sm_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   sm_addr(dst)),
+               "l"(src), "r"(bytes), "r"(sm_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(sm_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <int ZPL>
+struct TmaShape {
+  static constexpr int ZS = 32 * ZPL;
+  static constexpr int kStageTable = kRows * ZS;  // float2
+  static constexpr int kStageU = 8 * kRows;       // float2
+  static constexpr int kStage = kStageTable + kStageU;
+  static constexpr size_t kSmem =
+      sizeof(float2) * kTmaWarps * kStages * kStage + sizeof(unsigned long long) * kTmaWarps * kStages;
+};
+
+template <int ZPL, bool CONJ>
+__global__ void __launch_bounds__(kTmaWarps * 32, 1) contract_tma_kernel(const float2* __restrict__ U,
+                                                                      const float2* __restrict__ Gc,
+                                                                      const int2* __restrict__ cls_pq, int ncls,
+                                                                      int M, int F, int Z, float2* __restrict__ Y,
+                                                                      long long u_stride, long long y_stride,
+                                                                      int* __restrict__ status) {
+  using S = TmaShape<ZPL>;
+  constexpr int ZS = S::ZS;
+  extern __shared__ __align__(16) unsigned char raw[];
+  float2* ring = reinterpret_cast<float2*>(raw);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(raw + sizeof(float2) * kTmaWarps * kStages * S::kStage);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.y * kTmaWarps + warp;
+  if (c >= ncls) return;  // whole warp; nothing below synchronises across warps
+  U += blockIdx.x * u_stride;
+  Y += blockIdx.x * y_stride;
+  const int zc0 = blockIdx.z * ZS;
+  float2* myring = ring + (size_t)warp * kStages * S::kStage;
+  unsigned long long* mybar = bars + warp * kStages;
+  const float2* __restrict__ g = Gc + (size_t)c * F * Z + zc0;
+
+  const int2 pq = __ldg(cls_pq + c);
+  const int p = pq.x, q = pq.y;
+  const int kx[8] = {p, -p, p, -p, q, -q, q, -q};
+  const int ky[8] = {q, q, -q, -q, p, p, -p, -p};
+  unsigned off[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) off[s] = (unsigned)(wrap_index(ky[s], M) * M + wrap_index(kx[s], M));
+
+  const int nchunk = F / kRows;
+  auto issue = [&](int chunk) {  // lane 0 only
+    const int st = chunk % kStages, f0 = chunk * kRows;
+    float2* dst = myring + st * S::kStage;
+    mbar_expect(mybar + st, (unsigned)(sizeof(float2) * (kRows * ZS + 8 * kRows)));
+    if (ZS == Z) {  // the stage's rows are contiguous in the table
+      bulk_g2s(dst, g + (size_t)f0 * Z, (unsigned)(sizeof(float2) * kRows * ZS), mybar + st);
+    } else {
+      for (int r = 0; r < kRows; ++r)
+        bulk_g2s(dst + r * ZS, g + (size_t)(f0 + r) * Z, (unsigned)(sizeof(float2) * ZS), mybar + st);
+    }
+#pragma unroll
+    for (int s = 0; s < 8; ++s)
+      bulk_g2s(dst + S::kStageTable + s * kRows, U + (size_t)off[s] * F + f0, (unsigned)(sizeof(float2) * kRows),
+               mybar + st);
+  };
+  if (lane == 0) {
+    for (int st = 0; st < kStages; ++st) mbar_init(mybar + st, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    for (int ch = 0; ch < kStages && ch < nchunk; ++ch) issue(ch);
+  }
+  __syncwarp();
+
+  const int zl = lane * ZPL;
+  float2 acc[ZPL][8];
+#pragma unroll
+  for (int i = 0; i < ZPL; ++i)
+#pragma unroll
+    for (int s = 0; s < 8; ++s) acc[i][s] = make_float2(0.f, 0.f);
+  bool ok = true;
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const int st = ch % kStages;
+    if (!mbar_wait(mybar + st, (unsigned)((ch / kStages) & 1))) {
+      ok = false;
+      break;
+    }
+    const float2* stage = myring + st * S::kStage;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      float2 gv[ZPL], u[8];
+#pragma unroll
+      for (int i = 0; i < ZPL; i += 2) {
+        const float4 t = *reinterpret_cast<const float4*>(stage + r * ZS + zl + i);
+        gv[i] = make_float2(t.x, t.y);
+        gv[i + 1] = make_float2(t.z, t.w);
+      }
+#pragma unroll
+      for (int s = 0; s < 8; ++s) u[s] = stage[S::kStageTable + s * kRows + r];
+      if (CONJ) {
+#pragma unroll
+        for (int i = 0; i < ZPL; ++i) gv[i].y = -gv[i].y;
+      }
+#pragma unroll
+      for (int i = 0; i < ZPL; ++i)
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          acc[i][s].x = fmaf(gv[i].x, u[s].x, acc[i][s].x);
+          acc[i][s].x = fmaf(-gv[i].y, u[s].y, acc[i][s].x);
+          acc[i][s].y = fmaf(gv[i].x, u[s].y, acc[i][s].y);
+          acc[i][s].y = fmaf(gv[i].y, u[s].x, acc[i][s].y);
+        }
+    }
+    __syncwarp();  // every lane has read this stage
+    if (lane == 0 && ch + kStages < nchunk) issue(ch + kStages);
+  }
+  if (!ok) {
+    if (lane == 0) atomicOr(status, 2);
+    // let this warp's copies in flight land (bounded) before the CTA's shared memory goes away
+    for (int st = 0; st < kStages; ++st) {
+      mbar_wait(mybar + st, 0);
+      mbar_wait(mybar + st, 1);
+    }
+    return;
+  }
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    float2* dst = Y + (size_t)off[s] * Z + zc0 + zl;
+#pragma unroll
+    for (int i = 0; i < ZPL; i += 2)
+      *reinterpret_cast<float4*>(dst + i) = make_float4(acc[i][s].x, acc[i][s].y, acc[i + 1][s].x, acc[i + 1][s].y);
+  }
+}
+
+template <int ZPL, bool CONJ>
+cudaError_t launch_tma(const float2* U, const float2* Gc, const int2* cls_pq, int ncls, int M, int F, int Z, float2* Y,
+                       cudaStream_t s, int B, long long u_stride, long long y_stride, int* status) {
+  constexpr int ZS = TmaShape<ZPL>::ZS;
+  const size_t smem = TmaShape<ZPL>::kSmem;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(contract_tma_kernel<ZPL, CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  dim3 grid(B, (ncls + kTmaWarps - 1) / kTmaWarps, (Z + ZS - 1) / ZS);
+  if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
+  contract_tma_kernel<ZPL, CONJ><<<grid, kTmaWarps * 32, smem, s>>>(U, Gc, cls_pq, ncls, M, F, Z, Y, u_stride,
+                                                                   y_stride, status);
+  return cudaGetLastError();
+}
+
 template <int ZPL, bool CONJ>
 cudaError_t launch_zpl(const float2* U, const float2* Gc, const int2* cls_pq, int ncls, int M, int F, int Z,
                        float2* Y, cudaStream_t s, int B = 1, long long u_stride = 0, long long y_stride = 0) {
@@ -151,8 +333,12 @@ cudaError_t launch_zpl(const float2* U, const float2* Gc, const int2* cls_pq, in
 
 template <bool CONJ>
 cudaError_t launch_dir(const float2* In, const float2* T, const int2* cls_pq, int ncls, int M, int R, int J,
-                       float2* Out, cudaStream_t s) {
+                       float2* Out, cudaStream_t s, int* status) {
   if (R > 256) return cudaErrorInvalidValue;
+  if (status && R % kRows == 0) {  // whole 16-byte copies and full CTA columns: the bulk-copy pipeline
+    if (J % 128 == 0) return launch_tma<4, CONJ>(In, T, cls_pq, ncls, M, R, J, Out, s, 1, 0, 0, status);
+    if (J == 64) return launch_tma<2, CONJ>(In, T, cls_pq, ncls, M, R, J, Out, s, 1, 0, 0, status);
+  }
   // outputs per lane (a CTA column covers 32*ZPL of them): 4 for deep extents, fewer for shallow ones.
   if (J > 64) return launch_zpl<4, CONJ>(In, T, cls_pq, ncls, M, R, J, Out, s);
   if (J > 32) return launch_zpl<2, CONJ>(In, T, cls_pq, ncls, M, R, J, Out, s);
@@ -162,22 +348,26 @@ cudaError_t launch_dir(const float2* In, const float2* T, const int2* cls_pq, in
 }  // namespace
 
 cudaError_t launch_contract(const float2* U, const float2* Gc, const int2* cls_pq, int ncls, int M, int F, int Z,
-                            float2* Y, cudaStream_t s) {
-  return launch_dir<false>(U, Gc, cls_pq, ncls, M, F, Z, Y, s);
+                            float2* Y, cudaStream_t s, int* status) {
+  return launch_dir<false>(U, Gc, cls_pq, ncls, M, F, Z, Y, s, status);
 }
 
 cudaError_t launch_contract_batched(const float2* U, long long u_stride, const float2* Gc, const int2* cls_pq,
                                    int ncls, int M, int F, int Z, float2* Y, long long y_stride, int B,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, int* status) {
   if (F > 256 || B < 1) return cudaErrorInvalidValue;
+  if (status && F % kRows == 0) {
+    if (Z % 128 == 0) return launch_tma<4, false>(U, Gc, cls_pq, ncls, M, F, Z, Y, s, B, u_stride, y_stride, status);
+    if (Z == 64) return launch_tma<2, false>(U, Gc, cls_pq, ncls, M, F, Z, Y, s, B, u_stride, y_stride, status);
+  }
   if (Z > 64) return launch_zpl<4, false>(U, Gc, cls_pq, ncls, M, F, Z, Y, s, B, u_stride, y_stride);
   if (Z > 32) return launch_zpl<2, false>(U, Gc, cls_pq, ncls, M, F, Z, Y, s, B, u_stride, y_stride);
   return launch_zpl<1, false>(U, Gc, cls_pq, ncls, M, F, Z, Y, s, B, u_stride, y_stride);
 }
 
 cudaError_t launch_contract_adjoint(const float2* Yt, const float2* GcT, const int2* cls_pq, int ncls, int M, int F,
-                                    int Z, float2* R, cudaStream_t s) {
-  return launch_dir<true>(Yt, GcT, cls_pq, ncls, M, Z, F, R, s);
+                                    int Z, float2* R, cudaStream_t s, int* status) {
+  return launch_dir<true>(Yt, GcT, cls_pq, ncls, M, Z, F, R, s, status);
 }
 
 }  // namespace nursd

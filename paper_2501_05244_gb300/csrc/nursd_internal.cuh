@@ -116,17 +116,18 @@ cudaError_t launch_spread(const float2* P, int F, const int* bin_start, const in
 
 // ------------------------------------------------------------- contraction
 // Y[k][z] = sum_f U[k][f] * Gc[cls(k)][f][z] for every mode k of every class.
+// status (device int, may be null): bulk-copy form's wait time-outs set bit 2.
 cudaError_t launch_contract(const float2* U, const float2* Gc, const int2* cls_pq, int ncls, int M,
-                            int F, int Z, float2* Y, cudaStream_t s);
+                            int F, int Z, float2* Y, cudaStream_t s, int* status = nullptr);
 
 // Batched: B spectra U + b*u_stride -> Y + b*y_stride, consecutive CTAs sweeping the
 // batch for one class group so that each table block is read from HBM once.
 cudaError_t launch_contract_batched(const float2* U, long long u_stride, const float2* Gc, const int2* cls_pq,
                                    int ncls, int M, int F, int Z, float2* Y, long long y_stride, int B,
-                                   cudaStream_t s);
+                                   cudaStream_t s, int* status = nullptr);
 // Adjoint: R[k][f] = sum_z Yt[k][z] * conj(GcT[cls(k)][z][f]).
 cudaError_t launch_contract_adjoint(const float2* Yt, const float2* GcT, const int2* cls_pq, int ncls, int M, int F,
-                                    int Z, float2* R, cudaStream_t s);
+                                    int Z, float2* R, cudaStream_t s, int* status = nullptr);
 
 // ------------------------------------------------------------ interpolation
 // Type-2 interpolation at the sorted relay samples from a channel-last fine
