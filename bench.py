@@ -59,6 +59,40 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_max(value: float, dist, device=None) -> float:
+    """Max of a per-rank scalar over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(value)
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job rate: every rank processes `units_per_rank` in the slowest rank's time."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
+def measured_traffic():
+    """Per-launch DRAM traffic of the contraction from the committed ncu summary, or None
+    when the kernel source changed since the counters were taken."""
+    import hashlib
+    import re
+
+    try:
+        text = open(os.path.join(ROOT, "profiles", "contract_kernel_spad65k.md")).read()
+        src = open(os.path.join(ROOT, "paper_2501_05244_gb300", "csrc", "contract.cu"), "rb").read()
+    except OSError:
+        return None
+    m_t = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
+    m_h = re.search(r"sha256\[:16\]\s*([0-9a-f]{16})", text)
+    if not m_t or not m_h or hashlib.sha256(src).hexdigest()[:16] != m_h.group(1):
+        return None
+    return int(m_t.group(1))
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -388,11 +422,7 @@ def run_ours(args, rank, world, local):
     launches = plan.launch_count - launches0
     stages = plan.profile_read()
     plan.profile(False)
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps, dist, "cuda")
 
     # ---- end to end through the public API with host buffers (pinned), copies inside the timed region
     h_hist = torch.from_numpy(wl.hist).pin_memory()
@@ -416,16 +446,12 @@ def run_ours(args, rank, world, local):
     f1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms_e2e = f0.elapsed_time(f1) / ke
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = reduce_max(f0.elapsed_time(f1) / ke, dist, "cuda")
     if plan.sync_status() != 0:
         raise RuntimeError("device status error in the timed region")
 
     units = g.Z * g.N * g.N * g.F  # voxel*freq per reconstruction
-    value = units * world / (ms / 1e3)
+    value = job_throughput(units, world, ms)
     peak, peak_src = peaks()
     M, Z, F, N = plan.M, g.Z, g.F, g.N
     # algorithmic bytes of the contraction launch: table once, spectrum once, depth spectra once
@@ -453,13 +479,14 @@ def run_ours(args, rank, world, local):
         "recon_per_s": world * 1e3 / ms,
         "roofline": {"bound": "hbm", "kernel": "contract_kernel (transfer-function multiply + frequency sum)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_source": f"{peak_src} hbm_gbs", "traffic": None,
+                     "peak_source": f"{peak_src} hbm_gbs",
+                     "traffic": measured_traffic() if args.workload == "spad" else None,
                      "algorithmic_bytes": contract_bytes, "avg_launch_ms": c_avg},
         "step_hbm": {"algorithmic_bytes": step_bytes, "achieved_gbs": step_bytes / (ms / 1e3) / 1e9,
                      "frac": step_bytes / (ms / 1e3) / 1e9 / peak},
         "stages_ms": {k: (v[0] / max(v[1], 1)) for k, v in stages.items()},
         "gpu_launches": int(launches),
-        "e2e": {"value": units * world / (ms_e2e / 1e3), "unit": UNIT, "ms_per_step": ms_e2e,
+        "e2e": {"value": job_throughput(units, world, ms_e2e), "unit": UNIT, "ms_per_step": ms_e2e,
                 "h2d_bytes_per_step": int(h_hist.numel() * 4 + h_xy.numel() * 4),
                 "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size())},
         "clocks": clk,

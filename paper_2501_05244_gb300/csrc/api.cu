@@ -759,7 +759,7 @@ int nursd_set_points(nursd_plan_t p, int32_t L, const float* d_xy, nursd_stream_
   a.status = p->status;
   int rc;
   {
-    StageTimer t(p, NURSD_STAGE_POINTS, static_cast<cudaStream_t>(stream), L > 0 ? 4 : 0);
+    StageTimer t(p, NURSD_STAGE_POINTS, static_cast<cudaStream_t>(stream), L > 0 ? 5 : 0);
     rc = from_cuda(launch_points(a, p->bin_of, p->i0_orig, p->w_orig, p->counts, p->bin_start, p->sorted_l,
                                  p->i0_sorted, p->w_sorted, static_cast<cudaStream_t>(stream), p->frac_orig,
                                  p->frac_sorted));

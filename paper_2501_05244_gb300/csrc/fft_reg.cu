@@ -284,19 +284,19 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc, bool
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(n) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-// Persistent, double-buffered form: each CTA walks panels p = blockIdx.x, +gridDim.x, ...
-// (panel = channel chunk + batch item) and, while it transforms one, the next one's input
-// window streams into the other staging buffer with cp.async.
+// Persistent form: each CTA walks panels p = blockIdx.x, +gridDim.x, ... (panel =
+// channel chunk + batch item).  A panel's input window is staged in shared memory by
+// cp.async; once every thread has copied its 16 values into registers, the next
+// panel's copy is started into the same buffer and runs under this panel's
+// transform and stores.
 template <int LOGN, int CP, bool INV>
 __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT) panel_fft_pipe_kernel(const PanelArgs a, int npanel) {
   using S = RegShape<LOGN, CP>;
   constexpr int n = S::n, T = S::T, SR = S::SR, R3 = n / 256, NT = S::NT;
   extern __shared__ float2 sm[];
-  float2* xbuf = sm;                          // exchange buffer [n][SR]
-  float2* ibuf0 = sm + n * SR;                // staging [nin][CP], two of them
-  float2* ibuf1 = ibuf0 + (size_t)a.nin * CP;
+  float2* xbuf = sm;            // exchange buffer [n][SR]
+  float2* ibuf = sm + n * SR;   // staging [nin][CP]
   const int tid = threadIdx.x;
   int j0, q;
   if (a.load_i_fastest) {
@@ -337,15 +337,11 @@ __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT) panel_fft_pipe_kernel(
   };
 
   int p = blockIdx.x;
-  if (p < npanel) issue(p, ibuf0);
+  if (p < npanel) issue(p, ibuf);
   cp_async_commit();
-  for (int k = 0; p < npanel; p += gridDim.x, ++k) {
-    float2* cur = (k & 1) ? ibuf1 : ibuf0;
-    float2* nxt = (k & 1) ? ibuf0 : ibuf1;
-    if (p + (int)gridDim.x < npanel) issue(p + gridDim.x, nxt);
-    cp_async_commit();
-    cp_async_wait_1();
-    __syncthreads();
+  for (; p < npanel; p += gridDim.x) {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();  // the staged window is complete, and the previous panel's exchanges are done
     const int chunk = p % nchunk, b = p / nchunk;
     const int hi = (chunk / nlo) * a.CHI + q / a.CLO;
     const int lo = (chunk % nlo) * a.CLO + q % a.CLO;
@@ -356,7 +352,7 @@ __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT) panel_fft_pipe_kernel(
       const int i = (j0 + t * T - a.in_off) & (n - 1);
       float2 x = make_float2(0.f, 0.f);
       if (i < a.nin) {
-        x = cur[i * CP + q];
+        x = ibuf[i * CP + q];
         if (a.mul_i) {
           const float m = __ldg(a.mul_i + i);
           x.x *= m;
@@ -365,7 +361,10 @@ __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT) panel_fft_pipe_kernel(
       }
       v[t] = x;
     }
-    fft_core<LOGN, SR, INV>(v, xbuf, j0, q, a.twiddle);  // its barriers also retire every read of `cur`
+    __syncthreads();  // every thread holds its values: the buffer may be refilled
+    if (p + (int)gridDim.x < npanel) issue(p + gridDim.x, ibuf);
+    cp_async_commit();
+    fft_core<LOGN, SR, INV>(v, xbuf, j0, q, a.twiddle);
     if (valid) {
       const float sb = a.scale * (a.mul_b ? a.mul_b[b] : 1.f);
       const long long obase = (long long)b * a.out_sb + (long long)hi * a.out_shi + (long long)lo * a.out_slo;
@@ -388,7 +387,6 @@ __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT) panel_fft_pipe_kernel(
           }
         }
     }
-    __syncthreads();  // the exchange buffer is rewritten by the next panel's stage 1
   }
 }
 
@@ -409,7 +407,7 @@ cudaError_t launch_reg(const PanelArgs& a, cudaStream_t s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
-  const size_t smem_pipe = sizeof(float2) * ((size_t)S::n * S::SR + 2 * (size_t)a.nin * CP);
+  const size_t smem_pipe = sizeof(float2) * ((size_t)S::n * S::SR + (size_t)a.nin * CP);
   if (npanel >= 4LL * sms && smem_pipe <= 220 * 1024) {  // enough panels to stream: persistent form
     static size_t configured_pipe = 0;
     if (configured_pipe < smem_pipe) {
