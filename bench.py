@@ -17,6 +17,7 @@ host cores instead, each step a bounded voxel sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -46,9 +47,11 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=60)
     ap.add_argument("--no-rows", action="store_true",
                     help="skip the per-row measurements (type-2 voxels, SRSD, adjoint, gradients, batched)")
-    ap.add_argument("--workload", choices=["spad", "grid128"], default="spad",
+    ap.add_argument("--workload", choices=["spad", "grid128", "spad-z8"], default="spad",
                     help="spad: the 65k-sample 256^2x128 workload (the metric); grid128: the same samples on "
-                         "128^2x64 voxels (a smaller case for profiler captures)")
+                         "128^2x64 voxels; spad-z8: the spad workload with 8 of its 128 depth planes (same "
+                         "spread and FFT launches, 1/16 of the table); the last two are small cases for "
+                         "profiler captures")
     return ap.parse_args()
 
 
@@ -377,10 +380,12 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
     nursd.build()
-    if args.workload == "spad":
-        wl = workload_c2(seed=BASE_SEED + 2 + rank)  # each rank reconstructs its own measurement
-    else:
+    if args.workload == "grid128":
         wl = workload_c5(seed=BASE_SEED + 5 + rank)
+    else:
+        wl = workload_c2(seed=BASE_SEED + 2 + rank)  # each rank reconstructs its own measurement
+    if args.workload == "spad-z8":
+        wl.geom = dataclasses.replace(wl.geom, depths=wl.geom.depths[::16].copy())
     g = wl.geom
     L = len(wl.xy)
     om, wt = nursd.phasor_frequencies(g.lambda_c, g.dt, g.t_pad, g.F)
@@ -499,8 +504,9 @@ def run_ours(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
         "data": "synthetic (seeded keystone layout, Poisson histograms of 5 point scatterers)",
-        "config": {"workload": WORKLOAD if args.workload == "spad" else "grid128: " + WORKLOAD.replace(
-                       "256x256x128", "128x128x64"), "L": L, "T": g.T, "F": F, "N": N, "Z": Z, "M": M, "fine_n": plan.fine_n,
+        "config": {"workload": {"spad": WORKLOAD,
+                                "grid128": "grid128: " + WORKLOAD.replace("256x256x128", "128x128x64"),
+                                "spad-z8": "spad-z8: " + WORKLOAD.replace("256x256x128", "256x256x8")}[args.workload], "L": L, "T": g.T, "F": F, "N": N, "Z": Z, "M": M, "fine_n": plan.fine_n,
                    "parallelism": f"replicas x{world} (one reconstruction per GPU)",
                    "l2": "inputs larger than L2 (histograms 268 MB, transfer table %.2f GB); no flush" %
                          (plan.n_classes * F * Z * 8 / 1e9)},

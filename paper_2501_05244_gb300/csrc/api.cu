@@ -639,10 +639,12 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
   p->ncls = (half + 1) * (half + 2) / 2;
 
   // ---- host tables
-  std::vector<float2> tw(1 << kTwiddleLog);
-  for (int q = 0; q < (1 << kTwiddleLog); ++q) {
-    const double a = -2.0 * kPi * q / (double)(1 << kTwiddleLog);
-    tw[q] = make_float2((float)std::cos(a), (float)std::sin(a));
+  std::vector<float2> tw(kTwiddleEntries);
+  for (int e = 0; e < kTwiddleEntries; ++e) {
+    int num = 0, lg = 0;
+    twiddle_exponent(e, &num, &lg);
+    const double a = -2.0 * kPi * num / (double)(1 << lg);
+    tw[e] = make_float2((float)std::cos(a), (float)std::sin(a));
   }
   std::vector<double> gx, gw;
   gauss_legendre(256, gx, gw);

@@ -3,16 +3,21 @@
 // Same contract as panel_fft_kernel (PanelArgs: a window of nin inputs placed
 // at (i + in_off) mod n, nout bins kept at (o + out_off) mod n, CP channels per
 // CTA), but each thread keeps 16 complex values in registers and the transform
-// is three self-sorting Stockham stages of radix 16, 16 and n/256.  Inputs go
-// straight from global memory into registers, outputs straight back, and the
-// data crosses shared memory only between stages: two exchanges per transform
-// instead of a shared-memory round trip per radix-4 pass.
+// is three self-sorting Stockham stages of radix 16, 16 and n/256.  Data crosses
+// shared memory only between stages: two exchanges per transform instead of a
+// shared-memory round trip per radix-4 pass.
 //
 // Stage s (radix R, stride Ns) maps butterfly j: inputs x[j + t n/R],
 // twiddle e^{-+2 pi i (j mod Ns) t / (Ns R)}, outputs x'[(j - j mod Ns) R + j mod Ns + t Ns].
 // With T = n/16 threads per transform, thread j0 does butterfly j0 of stages 1
 // and 2 and butterflies j0 + m T (m < 16/R3) of stage 3, whose outputs are the
 // final bins j + 256 t.
+//
+// Exchange layout: element e of channel q sits at row e + PAD (e >> 4), column q
+// (rows of CP values, one spare row after every 16 when CP < 16).  A half-warp
+// (16 threads x 8 bytes) then hits 16 distinct bank pairs in every exchange, and
+// each thread's 16 accesses are one base address plus compile-time offsets.
+// Twiddles come from per-thread rows of the FFT table (two per 16-byte load).
 #include <algorithm>
 
 #include "nursd_internal.cuh"
@@ -24,21 +29,40 @@ constexpr float kC8 = 0.70710678118654752440f;  // cos(pi/4)
 constexpr float kC16 = 0.92387953251128675613f; // cos(pi/8)
 constexpr float kS16 = 0.38268343236508977173f; // sin(pi/8)
 
-template <bool INV>
-__device__ __forceinline__ float2 mul_negi(float2 d) {  // forward: -i d; inverse: +i d
-  return INV ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
+// Two-lane fp32 add and subtract in one instruction (each lane rounds as a scalar fadd would).
+__device__ __forceinline__ float2 padd(float2 a, float2 b) {
+  float2 r;
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " add.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  float2 r;
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
 }
 
+// 4-point DFT in place; the -+i rotation of the odd difference is folded into the last adds.
 template <bool INV>
 __device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
-  const float2 a = cadd(x0, x2), b = csub(x0, x2), c = cadd(x1, x3), d = mul_negi<INV>(csub(x1, x3));
-  x0 = cadd(a, c);
-  x2 = csub(a, c);
-  x1 = cadd(b, d);
-  x3 = csub(b, d);
+  const float2 a = padd(x0, x2), b = psub(x0, x2), c = padd(x1, x3), d = psub(x1, x3);
+  x0 = padd(a, c);
+  x2 = psub(a, c);
+  if (INV) {  // b +- i d
+    x1 = make_float2(b.x - d.y, b.y + d.x);
+    x3 = make_float2(b.x + d.y, b.y - d.x);
+  } else {    // b -+ i d
+    x1 = make_float2(b.x + d.y, b.y - d.x);
+    x3 = make_float2(b.x - d.y, b.y + d.x);
+  }
 }
 
-// e^{-+2 pi i m / 16} for m = 1, 2, 3 (constants of the regular 16-gon)
+// e^{-+2 pi i m / 16} for m = 1, 2, 3, 4, 6, 9 (constants of the regular 16-gon)
 template <bool INV>
 __device__ __forceinline__ float2 w16(int m) {
   const float s = INV ? 1.f : -1.f;
@@ -91,70 +115,31 @@ __device__ __forceinline__ void dft8(float2* v) {
   o1 = cmul(o1, make_float2(kC8, s * kC8));
   o2 = cmul(o2, make_float2(0.f, s));
   o3 = cmul(o3, make_float2(-kC8, s * kC8));
-  v[0] = cadd(e0, o0);
-  v[4] = csub(e0, o0);
-  v[1] = cadd(e1, o1);
-  v[5] = csub(e1, o1);
-  v[2] = cadd(e2, o2);
-  v[6] = csub(e2, o2);
-  v[3] = cadd(e3, o3);
-  v[7] = csub(e3, o3);
+  v[0] = padd(e0, o0);
+  v[4] = psub(e0, o0);
+  v[1] = padd(e1, o1);
+  v[5] = psub(e1, o1);
+  v[2] = padd(e2, o2);
+  v[6] = psub(e2, o2);
+  v[3] = padd(e3, o3);
+  v[7] = psub(e3, o3);
 }
 
+// a * w (forward) or a * conj(w) (inverse), w from the forward table.
 template <bool INV>
-__device__ __forceinline__ float2 tw(const float2* __restrict__ table, int q) {
-  float2 w = __ldg(table + (q & ((1 << kTwiddleLog) - 1)));
-  if (INV) w.y = -w.y;
-  return w;
+__device__ __forceinline__ float2 twmul(float2 a, float2 w) {
+  return INV ? make_float2(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y) : cmul(a, w);
 }
 
-// The transform on registers v[16] of thread j0 (channel column q of a panel with row stride SR).
-// Entry: v[t] = x[j0 + t n/16].  Exit: v[m R3 + t] = X[j0 + m T + 256 t].
-template <int LOGN, int SR, bool INV>
-__device__ __forceinline__ void fft_core(float2* v, float2* sm, int j0, int q, const float2* __restrict__ table) {
-  constexpr int n = 1 << LOGN;
-  constexpr int T = n / 16;
-  constexpr int R3 = n / 256;
-  // stage 1: radix 16, Ns = 1
-  dft16<INV>(v);
+// v[t] *= row[t] for t = 1 .. R-1, row = R consecutive table entries (16-byte aligned).
+template <int R, bool INV>
+__device__ __forceinline__ void twiddle_row(float2* v, const float2* __restrict__ row) {
+  const float4* r4 = reinterpret_cast<const float4*>(row);
 #pragma unroll
-  for (int t = 0; t < 16; ++t) sm[(16 * j0 + t) * SR + q] = v[t];
-  __syncthreads();
-  // stage 2: radix 16, Ns = 16, twiddle e^{-+2 pi i (j0 mod 16) t / 256}
-#pragma unroll
-  for (int t = 0; t < 16; ++t) v[t] = sm[(j0 + t * T) * SR + q];
-  {
-    const int k = j0 & 15;
-#pragma unroll
-    for (int t = 1; t < 16; ++t) v[t] = cmul(v[t], tw<INV>(table, (k * t) << (kTwiddleLog - 8)));
-  }
-  dft16<INV>(v);
-  __syncthreads();
-  {
-    const int k = j0 & 15;
-    const int base = (j0 - k) * 16 + k;
-#pragma unroll
-    for (int t = 0; t < 16; ++t) sm[(base + 16 * t) * SR + q] = v[t];
-  }
-  __syncthreads();
-  // stage 3: radix R3, Ns = 256, butterflies j = j0 + m T (j < 256): inputs x[j + t 256/... ]
-#pragma unroll
-  for (int m = 0; m < 16 / R3; ++m) {
-    const int j = j0 + m * T;
-#pragma unroll
-    for (int t = 0; t < R3; ++t) v[m * R3 + t] = sm[(j + t * (n / R3)) * SR + q];
-#pragma unroll
-    for (int t = 1; t < R3; ++t)
-      v[m * R3 + t] = cmul(v[m * R3 + t], tw<INV>(table, (j * t) << (kTwiddleLog - LOGN)));
-    if (R3 == 2) {
-      const float2 a = v[m * 2];
-      v[m * 2] = cadd(a, v[m * 2 + 1]);
-      v[m * 2 + 1] = csub(a, v[m * 2 + 1]);
-    } else if (R3 == 4) {
-      dft4<INV>(v[m * 4], v[m * 4 + 1], v[m * 4 + 2], v[m * 4 + 3]);
-    } else {
-      dft8<INV>(v + m * 8);
-    }
+  for (int u = 0; u < R / 2; ++u) {
+    const float4 w = __ldg(r4 + u);
+    if (u > 0) v[2 * u] = twmul<INV>(v[2 * u], make_float2(w.x, w.y));
+    v[2 * u + 1] = twmul<INV>(v[2 * u + 1], make_float2(w.z, w.w));
   }
 }
 
@@ -163,17 +148,127 @@ struct RegShape {
   static constexpr int n = 1 << LOGN;
   static constexpr int T = n / 16;
   static constexpr int NT = T * CP;
-  static constexpr int SR = CP + 1;
+  static constexpr int PAD = CP < 16 ? 1 : 0;
+  static constexpr int XROWS = n + PAD * (n / 16);  // exchange buffer rows
+  __device__ static int row(int e) { return e + PAD * (e >> 4); }
 };
 
+// The transform on registers v[16] of thread j0 (channel column q).
+// Entry: v[t] = x[j0 + t n/16].  Exit: v[m R3 + t] = X[j0 + m T + 256 t].
 template <int LOGN, int CP, bool INV>
-__global__ void __launch_bounds__(RegShape<LOGN, CP>::NT) panel_fft_reg_kernel(const PanelArgs a) {
+__device__ __forceinline__ void fft_core(float2* v, float2* sm, int j0, int q, const float2* __restrict__ table) {
   using S = RegShape<LOGN, CP>;
-  constexpr int n = S::n, T = S::T, SR = S::SR, R3 = n / 256;
+  constexpr int n = S::n, T = S::T, R3 = n / 256, PAD = S::PAD;
+  // stage 1: radix 16, Ns = 1; outputs 16 j0 + t at rows (16 + PAD) j0 + t
+  dft16<INV>(v);
+  {
+    float2* w = sm + (16 + PAD) * j0 * CP + q;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) w[t * (CP)] = v[t];
+  }
+  __syncthreads();
+  // stage 2: radix 16, Ns = 16; inputs j0 + t T at rows row(j0) + t (T + PAD T/16)
+  {
+    const float2* r = sm + S::row(j0) * CP + q;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) v[t] = r[t * (T + PAD * (T / 16)) * CP];
+  }
+  twiddle_row<16, INV>(v, table + kTw2Offset + 16 * (j0 & 15));
+  dft16<INV>(v);
+  __syncthreads();
+  {  // outputs base + 16 t, base = (j0 - k) 16 + k, at rows base + PAD (j0 - k) + t (16 + PAD)
+    const int k = j0 & 15;
+    float2* w = sm + ((j0 - k) * 16 + k + PAD * (j0 - k)) * CP + q;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) w[t * (16 + PAD) * CP] = v[t];
+  }
+  __syncthreads();
+  // stage 3: radix R3, Ns = 256, butterflies j = j0 + m T: inputs j + 256 t at rows row(j) + t (256 + 16 PAD)
+#pragma unroll
+  for (int m = 0; m < 16 / R3; ++m) {
+    const int j = j0 + m * T;
+    const float2* r = sm + S::row(j) * CP + q;
+#pragma unroll
+    for (int t = 0; t < R3; ++t) v[m * R3 + t] = r[t * (256 + 16 * PAD) * CP];
+    twiddle_row<R3, INV>(v + m * R3, table + tw3_offset(LOGN) + j * R3);
+    if (R3 == 2) {
+      const float2 a = v[m * 2];
+      v[m * 2] = padd(a, v[m * 2 + 1]);
+      v[m * 2 + 1] = psub(a, v[m * 2 + 1]);
+    } else if (R3 == 4) {
+      dft4<INV>(v[m * 4], v[m * 4 + 1], v[m * 4 + 2], v[m * 4 + 3]);
+    } else {
+      dft8<INV>(v + m * 8);
+    }
+  }
+}
+
+// Stores the kept bins of thread j0: bin j0 + m T + 256 t -> output o = (bin - out_off) mod n if o < nout,
+// scaled by scale * mul_b[b] * mul_o[o] (or written as a magnitude).
+template <int LOGN>
+__device__ __forceinline__ void store_bins(const PanelArgs& a, const float2* v, int j0, long long obase, int b) {
+  constexpr int n = 1 << LOGN, T = n / 16, R3 = n / 256;
+  const int opos = (j0 - a.out_off) & (n - 1);
+  const int osi = (int)a.out_si;
+  const float sb = a.scale * (a.mul_b ? __ldg(a.mul_b + b) : 1.f);
+  if (a.out_mag) {
+    float* op = a.out_mag + obase;
+#pragma unroll
+    for (int m = 0; m < 16 / R3; ++m)
+#pragma unroll
+      for (int t = 0; t < R3; ++t) {
+        const int o = (opos + m * T + 256 * t) & (n - 1);
+        if (o < a.nout) {
+          const float sc = sb * (a.mul_o ? __ldg(a.mul_o + o) : 1.f);
+          const float2 x = make_float2(v[m * R3 + t].x * sc, v[m * R3 + t].y * sc);
+          op[(long long)o * osi] = sqrtf(x.x * x.x + x.y * x.y);
+        }
+      }
+  } else if (a.mul_o || sb != 1.f) {
+    float2* op = a.out + obase;
+#pragma unroll
+    for (int m = 0; m < 16 / R3; ++m)
+#pragma unroll
+      for (int t = 0; t < R3; ++t) {
+        const int o = (opos + m * T + 256 * t) & (n - 1);
+        if (o < a.nout) {
+          const float sc = sb * (a.mul_o ? __ldg(a.mul_o + o) : 1.f);
+          op[(long long)o * osi] = make_float2(v[m * R3 + t].x * sc, v[m * R3 + t].y * sc);
+        }
+      }
+  } else {
+    float2* op = a.out + obase;
+#pragma unroll
+    for (int m = 0; m < 16 / R3; ++m)
+#pragma unroll
+      for (int t = 0; t < R3; ++t) {
+        const int o = (opos + m * T + 256 * t) & (n - 1);
+        if (o < a.nout) op[(long long)o * osi] = v[m * R3 + t];
+      }
+  }
+}
+
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  const int n = valid ? 8 : 0;  // src-size 0 zero-fills the destination
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  const int n = valid ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+// One panel per CTA, inputs read from global memory straight into registers.
+template <int LOGN, int CP, bool INV>
+__global__ void __launch_bounds__(RegShape<LOGN, CP>::NT, 2) panel_fft_reg_kernel(const PanelArgs a) {
+  using S = RegShape<LOGN, CP>;
+  constexpr int n = S::n, T = S::T;
   extern __shared__ float2 sm[];
   const int tid = threadIdx.x;
   int j0, q;
-  if (a.load_i_fastest) {
+  if (a.load_i_fastest) {  // consecutive threads read consecutive inputs
     j0 = tid % T;
     q = tid / T;
   } else {
@@ -186,15 +281,15 @@ __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT) panel_fft_reg_kernel(c
   const bool valid = hi < a.hi_total && lo < a.lo_total;
   const int b = blockIdx.y;
   const float2* __restrict__ in = a.in + (long long)b * a.in_sb + (long long)hi * a.in_shi + (long long)lo * a.in_slo;
-
+  const int isi = (int)a.in_si;
+  const int lpos = (j0 - a.in_off) & (n - 1);  // input index at FFT position j0
   float2 v[16];
 #pragma unroll
   for (int t = 0; t < 16; ++t) {
-    const int pos = j0 + t * T;
-    const int i = (pos - a.in_off) & (n - 1);
+    const int i = (lpos + t * T) & (n - 1);
     float2 x = make_float2(0.f, 0.f);
     if (valid && i < a.nin) {
-      x = __ldg(in + (long long)i * a.in_si);
+      x = __ldg(in + (long long)i * isi);
       if (a.mul_i) {
         const float m = __ldg(a.mul_i + i);
         x.x *= m;
@@ -203,28 +298,9 @@ __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT) panel_fft_reg_kernel(c
     }
     v[t] = x;
   }
-  fft_core<LOGN, SR, INV>(v, sm, j0, q, a.twiddle);
+  fft_core<LOGN, CP, INV>(v, sm, j0, q, a.twiddle);
   if (!valid) return;
-  const float sb = a.scale * (a.mul_b ? a.mul_b[b] : 1.f);
-  const long long obase = (long long)b * a.out_sb + (long long)hi * a.out_shi + (long long)lo * a.out_slo;
-#pragma unroll
-  for (int m = 0; m < 16 / R3; ++m)
-#pragma unroll
-    for (int t = 0; t < R3; ++t) {
-      const int bin = j0 + m * T + 256 * t;
-      const int o = (bin - a.out_off) & (n - 1);
-      if (o < a.nout) {
-        float2 x = v[m * R3 + t];
-        const float s = sb * (a.mul_o ? __ldg(a.mul_o + o) : 1.f);
-        x.x *= s;
-        x.y *= s;
-        const long long off = obase + (long long)o * a.out_si;
-        if (a.out_mag)
-          a.out_mag[off] = sqrtf(x.x * x.x + x.y * x.y);
-        else
-          a.out[off] = x;
-      }
-    }
+  store_bins<LOGN>(a, v, j0, (long long)b * a.out_sb + (long long)hi * a.out_shi + (long long)lo * a.out_slo, b);
 }
 
 // Bluestein form: chirp the window, forward transform, multiply by bhat, inverse transform,
@@ -235,7 +311,7 @@ __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT) panel_bluestein_reg_ke
     const PanelArgs a, const float2* __restrict__ cpre, const float2* __restrict__ bhat,
     const float2* __restrict__ cpost) {
   using S = RegShape<LOGN, CP>;
-  constexpr int n = S::n, T = S::T, SR = S::SR, R3 = n / 256;
+  constexpr int n = S::n, T = S::T, R3 = n / 256;
   extern __shared__ float2 sm[];
   const int tid = threadIdx.x;
   const int q = tid % CP, j0 = tid / CP;
@@ -245,148 +321,148 @@ __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT) panel_bluestein_reg_ke
   const bool valid = hi < a.hi_total && lo < a.lo_total;
   const int b = blockIdx.y;
   const float2* __restrict__ in = a.in + (long long)b * a.in_sb + (long long)hi * a.in_shi + (long long)lo * a.in_slo;
+  const int isi = (int)a.in_si, osi = (int)a.out_si;
+  const int lpos = (j0 - a.in_off) & (n - 1);
   float2 v[16];
 #pragma unroll
   for (int t = 0; t < 16; ++t) {
-    const int pos = j0 + t * T;
-    const int i = (pos - a.in_off) & (n - 1);
-    v[t] = (valid && i < a.nin) ? cmul(__ldg(in + (long long)i * a.in_si), __ldg(cpre + i)) : make_float2(0.f, 0.f);
+    const int i = (lpos + t * T) & (n - 1);
+    v[t] = (valid && i < a.nin) ? cmul(__ldg(in + (long long)i * isi), __ldg(cpre + i)) : make_float2(0.f, 0.f);
   }
-  fft_core<LOGN, SR, false>(v, sm, j0, q, a.twiddle);
+  fft_core<LOGN, CP, false>(v, sm, j0, q, a.twiddle);
   __syncthreads();  // every thread has read its stage-3 inputs; reuse the buffer
 #pragma unroll
   for (int m = 0; m < 16 / R3; ++m)
 #pragma unroll
     for (int t = 0; t < R3; ++t) {
       const int bin = j0 + m * T + 256 * t;
-      sm[bin * SR + q] = cmul(v[m * R3 + t], __ldg(bhat + bin));
+      sm[S::row(bin) * CP + q] = cmul(v[m * R3 + t], __ldg(bhat + bin));
     }
   __syncthreads();
 #pragma unroll
-  for (int t = 0; t < 16; ++t) v[t] = sm[(j0 + t * T) * SR + q];
+  for (int t = 0; t < 16; ++t) v[t] = sm[S::row(j0 + t * T) * CP + q];
   __syncthreads();
-  fft_core<LOGN, SR, true>(v, sm, j0, q, a.twiddle);
+  fft_core<LOGN, CP, true>(v, sm, j0, q, a.twiddle);
   if (!valid) return;
-  const long long obase = (long long)b * a.out_sb + (long long)hi * a.out_shi + (long long)lo * a.out_slo;
+  float2* op = a.out + (long long)b * a.out_sb + (long long)hi * a.out_shi + (long long)lo * a.out_slo;
+  const int opos = (j0 - a.out_off) & (n - 1);
 #pragma unroll
   for (int m = 0; m < 16 / R3; ++m)
 #pragma unroll
     for (int t = 0; t < R3; ++t) {
-      const int bin = j0 + m * T + 256 * t;
-      const int o = (bin - a.out_off) & (n - 1);
-      if (o < a.nout) a.out[obase + (long long)o * a.out_si] = cmul(v[m * R3 + t], __ldg(cpost + o));
+      const int o = (opos + m * T + 256 * t) & (n - 1);
+      if (o < a.nout) op[(long long)o * osi] = cmul(v[m * R3 + t], __ldg(cpost + o));
     }
 }
 
-__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc, bool valid) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-  const int n = valid ? 8 : 0;  // src-size 0 zero-fills the destination
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(n) : "memory");
+// floor(x / d) for 0 <= x < 2^22 and d >= 1, with inv = 1.f / d: the rounded float
+// quotient is within 1 of the exact one, and one correction step makes it exact.
+__device__ __forceinline__ int small_div(int x, int d, float inv) {
+  int qt = __float2int_rz(__int2float_rz(x) * inv);
+  const int r = x - qt * d;
+  qt += (r >= d) - (r < 0);
+  return qt;
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 
-// Persistent form: each CTA walks panels p = blockIdx.x, +gridDim.x, ... (panel =
-// channel chunk + batch item).  A panel's input window is staged in shared memory by
-// cp.async; once every thread has copied its 16 values into registers, the next
-// panel's copy is started into the same buffer and runs under this panel's
-// transform and stores.
+// Persistent form: each CTA walks panels p = blockIdx.x, +gridDim.x, ... (panel p =
+// batch item p / nchunk, channel chunk p mod nchunk).  A panel's input window is
+// staged in shared memory ([nin][CP]) by cp.async; once every thread has copied its
+// 16 values into registers, the next panel's copy is started into the same buffer
+// and runs under this panel's transform and stores.  vec2: the window rows are
+// 16-byte aligned pairs of channels, copied two channels at a time.
 template <int LOGN, int CP, bool INV>
-__global__ void __launch_bounds__(RegShape<LOGN, CP>::NT) panel_fft_pipe_kernel(const PanelArgs a, int npanel) {
+__global__ void __launch_bounds__(RegShape<LOGN, CP>::NT, 2) panel_fft_pipe_kernel(const PanelArgs a, int npanel,
+                                                                                    int vec2) {
   using S = RegShape<LOGN, CP>;
-  constexpr int n = S::n, T = S::T, SR = S::SR, R3 = n / 256, NT = S::NT;
+  constexpr int n = S::n, T = S::T, NT = S::NT;
   extern __shared__ float2 sm[];
-  float2* xbuf = sm;            // exchange buffer [n][SR]
-  float2* ibuf = sm + n * SR;   // staging [nin][CP]
+  float2* xbuf = sm;                   // exchange buffer [XROWS][CP]
+  float2* ibuf = sm + S::XROWS * CP;   // staging [nin][CP]
   const int tid = threadIdx.x;
-  int j0, q;
-  if (a.load_i_fastest) {
-    j0 = tid % T;
-    q = tid / T;
-  } else {
-    q = tid % CP;
-    j0 = tid / CP;
-  }
+  const int q = tid % CP, j0 = tid / CP;
   const int nlo = (a.lo_total + a.CLO - 1) / a.CLO;
   const int nchunk = ((a.hi_total + a.CHI - 1) / a.CHI) * nlo;
+  const float inv_nlo = 1.f / (float)nlo;
+  const int qhi = q / a.CLO, qlo = q % a.CLO;
+  // copy roles: channel pair cq2, cq2 + 1 (vec2) or channel q, of rows crow + k RSTEP
+  const int cq2 = 2 * (tid % (CP / 2));
+  const int cq2hi = cq2 / a.CLO, cq2lo = cq2 % a.CLO;
 
-  // Copy work per thread: a fixed channel column and every (NT/CP)-th row (or, for
-  // load_i_fastest, a fixed row residue), so each copy is a pointer increment.
-  constexpr int RSTEP = NT / CP;
-  auto issue = [&](int p, float2* buf) {
-    const int chunk = p % nchunk, b = p / nchunk;
-    const int hi0 = (chunk / nlo) * a.CHI, lo0 = (chunk % nlo) * a.CLO;
+  auto issue = [&](int b, int chunk) {
+    const int hc = small_div(chunk, nlo, inv_nlo);
+    const int hi0 = hc * a.CHI, lo0 = (chunk - hc * nlo) * a.CLO;
     const float2* inb = a.in + (long long)b * a.in_sb;
-    if (!a.load_i_fastest) {
-      const int qq = tid % CP;
-      const int hi = hi0 + qq / a.CLO, lo = lo0 + qq % a.CLO;
-      const bool ok = hi < a.hi_total && lo < a.lo_total;
-      const float2* src = inb + (long long)hi * a.in_shi + (long long)lo * a.in_slo;
-      const long long step = (long long)RSTEP * a.in_si;
-      int i = tid / CP;
-      src += (long long)i * a.in_si;
-      for (; i < a.nin; i += RSTEP, src += step) cp_async8(buf + i * CP + qq, ok ? src : a.in, ok);
-    } else {
+    if (a.load_i_fastest) {  // the axis is contiguous in memory: consecutive threads copy consecutive i
       for (int idx = tid; idx < a.nin * CP; idx += NT) {
         const int i = idx % a.nin, qq = idx / a.nin;
         const int hi = hi0 + qq / a.CLO, lo = lo0 + qq % a.CLO;
         const bool ok = hi < a.hi_total && lo < a.lo_total;
         const float2* src = ok ? inb + (long long)i * a.in_si + (long long)hi * a.in_shi + (long long)lo * a.in_slo : a.in;
-        cp_async8(buf + i * CP + qq, src, ok);
+        cp_async8(ibuf + i * CP + qq, src, ok);
       }
+    } else if (vec2) {
+      constexpr int RSTEP = NT / (CP / 2);
+      const int hi = hi0 + cq2hi, lo = lo0 + cq2lo;
+      const bool ok = hi < a.hi_total && lo < a.lo_total;
+      int i = tid / (CP / 2);
+      const float2* src = inb + (long long)hi * a.in_shi + lo + (long long)i * a.in_si;
+      const long long step = (long long)RSTEP * a.in_si;
+      for (; i < a.nin; i += RSTEP, src += step) cp_async16(ibuf + i * CP + cq2, ok ? src : a.in, ok);
+    } else {
+      constexpr int RSTEP = NT / CP;
+      const int hi = hi0 + qhi, lo = lo0 + qlo;
+      const bool ok = hi < a.hi_total && lo < a.lo_total;
+      int i = tid / CP;
+      const float2* src = inb + (long long)hi * a.in_shi + (long long)lo * a.in_slo + (long long)i * a.in_si;
+      const long long step = (long long)RSTEP * a.in_si;
+      for (; i < a.nin; i += RSTEP, src += step) cp_async8(ibuf + i * CP + q, ok ? src : a.in, ok);
     }
   };
 
+  const int lpos = (j0 - a.in_off) & (n - 1);  // input index at FFT position j0
+  const float2* rq = ibuf + q;
+  const int step_b = gridDim.x / nchunk, step_c = gridDim.x % nchunk;
   int p = blockIdx.x;
-  if (p < npanel) issue(p, ibuf);
+  int cb = p / nchunk, cc = p % nchunk;  // batch item and chunk of panel p
+  if (p < npanel) issue(cb, cc);
   cp_async_commit();
   for (; p < npanel; p += gridDim.x) {
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();  // the staged window is complete, and the previous panel's exchanges are done
-    const int chunk = p % nchunk, b = p / nchunk;
-    const int hi = (chunk / nlo) * a.CHI + q / a.CLO;
-    const int lo = (chunk % nlo) * a.CLO + q % a.CLO;
+    const int hc = small_div(cc, nlo, inv_nlo);
+    const int hi = hc * a.CHI + qhi;
+    const int lo = (cc - hc * nlo) * a.CLO + qlo;
     const bool valid = hi < a.hi_total && lo < a.lo_total;
+    const int b = cb;
     float2 v[16];
 #pragma unroll
     for (int t = 0; t < 16; ++t) {
-      const int i = (j0 + t * T - a.in_off) & (n - 1);
-      float2 x = make_float2(0.f, 0.f);
-      if (i < a.nin) {
-        x = ibuf[i * CP + q];
-        if (a.mul_i) {
+      const int i = (lpos + t * T) & (n - 1);
+      v[t] = i < a.nin ? rq[i * CP] : make_float2(0.f, 0.f);
+    }
+    if (a.mul_i) {
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        const int i = (lpos + t * T) & (n - 1);
+        if (i < a.nin) {
           const float m = __ldg(a.mul_i + i);
-          x.x *= m;
-          x.y *= m;
+          v[t].x *= m;
+          v[t].y *= m;
         }
       }
-      v[t] = x;
     }
     __syncthreads();  // every thread holds its values: the buffer may be refilled
-    if (p + (int)gridDim.x < npanel) issue(p + gridDim.x, ibuf);
-    cp_async_commit();
-    fft_core<LOGN, SR, INV>(v, xbuf, j0, q, a.twiddle);
-    if (valid) {
-      const float sb = a.scale * (a.mul_b ? a.mul_b[b] : 1.f);
-      const long long obase = (long long)b * a.out_sb + (long long)hi * a.out_shi + (long long)lo * a.out_slo;
-#pragma unroll
-      for (int m = 0; m < 16 / R3; ++m)
-#pragma unroll
-        for (int t = 0; t < R3; ++t) {
-          const int bin = j0 + m * T + 256 * t;
-          const int o = (bin - a.out_off) & (n - 1);
-          if (o < a.nout) {
-            float2 x = v[m * R3 + t];
-            const float sc = sb * (a.mul_o ? __ldg(a.mul_o + o) : 1.f);
-            x.x *= sc;
-            x.y *= sc;
-            const long long off = obase + (long long)o * a.out_si;
-            if (a.out_mag)
-              a.out_mag[off] = sqrtf(x.x * x.x + x.y * x.y);
-            else
-              a.out[off] = x;
-          }
-        }
+    cb += step_b;
+    cc += step_c;
+    if (cc >= nchunk) {
+      cc -= nchunk;
+      ++cb;
     }
+    if (p + (int)gridDim.x < npanel) issue(cb, cc);
+    cp_async_commit();
+    fft_core<LOGN, CP, INV>(v, xbuf, j0, q, a.twiddle);
+    if (valid)
+      store_bins<LOGN>(a, v, j0, (long long)b * a.out_sb + (long long)hi * a.out_shi + (long long)lo * a.out_slo, b);
   }
 }
 
@@ -395,38 +471,63 @@ cudaError_t configure(K kernel, size_t smem) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-template <int LOGN, int CP, bool INV>
-cudaError_t launch_reg(const PanelArgs& a, cudaStream_t s) {
-  using S = RegShape<LOGN, CP>;
-  const int nhi = (a.hi_total + a.CHI - 1) / a.CHI;
-  const int nlo = (a.lo_total + a.CLO - 1) / a.CLO;
-  const long long npanel = (long long)nhi * nlo * a.batch;
+int sm_count() {
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
-  const size_t smem_pipe = sizeof(float2) * ((size_t)S::n * S::SR + (size_t)a.nin * CP);
-  if (npanel >= 4LL * sms && smem_pipe <= 220 * 1024) {  // enough panels to stream: persistent form
-    static size_t configured_pipe = 0;
-    if (configured_pipe < smem_pipe) {
-      cudaError_t e = configure(panel_fft_pipe_kernel<LOGN, CP, INV>, 220 * 1024);
+  return sms;
+}
+
+// Element offsets along the axis are 32-bit in the kernels: n * stride must fit.
+bool axis_offsets_fit(int n, const PanelArgs& a) {
+  const long long lim = 1LL << 31;
+  return a.in_si >= 0 && a.out_si >= 0 && (long long)n * a.in_si < lim && (long long)n * a.out_si < lim;
+}
+
+template <int LOGN, int CP, bool INV>
+cudaError_t launch_reg(const PanelArgs& a, cudaStream_t s) {
+  using S = RegShape<LOGN, CP>;
+  if (!axis_offsets_fit(S::n, a)) return cudaErrorInvalidValue;
+  const int nhi = (a.hi_total + a.CHI - 1) / a.CHI;
+  const int nlo = (a.lo_total + a.CLO - 1) / a.CLO;
+  const long long npanel = (long long)nhi * nlo * a.batch;
+  const int sms = sm_count();
+  const size_t xbytes = sizeof(float2) * (size_t)S::XROWS * CP;
+  const size_t smem_pipe = xbytes + sizeof(float2) * (size_t)a.nin * CP;
+  if (npanel >= 4LL * sms && smem_pipe <= 220 * 1024 && (long long)nhi * nlo < (1LL << 22)) {  // persistent form
+    auto kern = panel_fft_pipe_kernel<LOGN, CP, INV>;
+    static bool configured = false;
+    static size_t occ_smem = 0;
+    static int occ = 1;
+    if (!configured) {
+      cudaError_t e = configure(kern, 220 * 1024);
       if (e != cudaSuccess) return e;
-      configured_pipe = 220 * 1024;
+      configured = true;
     }
-    const int grid = (int)std::min<long long>(npanel, (long long)sms * (smem_pipe <= 110 * 1024 ? 2 : 1));
-    panel_fft_pipe_kernel<LOGN, CP, INV><<<grid, S::NT, smem_pipe, s>>>(a, (int)npanel);
+    if (occ_smem != smem_pipe) {
+      int nb = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, S::NT, smem_pipe);
+      if (e != cudaSuccess) return e;
+      occ = std::max(nb, 1);
+      occ_smem = smem_pipe;
+    }
+    const int vec2 = !a.load_i_fastest && a.in_slo == 1 && a.CLO % 2 == 0 && a.lo_total % 2 == 0 &&
+                     reinterpret_cast<uintptr_t>(a.in) % 16 == 0 && a.in_sb % 2 == 0 && a.in_si % 2 == 0 &&
+                     a.in_shi % 2 == 0;
+    const int grid = (int)std::min<long long>(npanel, (long long)sms * occ);
+    kern<<<grid, S::NT, smem_pipe, s>>>(a, (int)npanel, vec2);
     return cudaGetLastError();
   }
-  const size_t smem = sizeof(float2) * S::n * S::SR;
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = configure(panel_fft_reg_kernel<LOGN, CP, INV>, smem);
+    cudaError_t e = configure(panel_fft_reg_kernel<LOGN, CP, INV>, xbytes);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  panel_fft_reg_kernel<LOGN, CP, INV><<<dim3(nhi * nlo, a.batch), S::NT, smem, s>>>(a);
+  panel_fft_reg_kernel<LOGN, CP, INV><<<dim3(nhi * nlo, a.batch), S::NT, xbytes, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -434,7 +535,8 @@ template <int LOGN, int CP>
 cudaError_t launch_bluestein_reg(const PanelArgs& a, const float2* cpre, const float2* bhat, const float2* cpost,
                                  cudaStream_t s) {
   using S = RegShape<LOGN, CP>;
-  const size_t smem = sizeof(float2) * S::n * S::SR;
+  if (!axis_offsets_fit(S::n, a)) return cudaErrorInvalidValue;
+  const size_t smem = sizeof(float2) * (size_t)S::XROWS * CP;
   static bool configured = false;
   if (!configured) {
     cudaError_t e = configure(panel_bluestein_reg_kernel<LOGN, CP>, smem);

@@ -25,8 +25,10 @@ using namespace nursd;
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(24) << 20;  // 24 MiB, shared by every call
-constexpr size_t kTableBytes = size_t(64) << 10;          // twiddles + quadrature nodes
+constexpr size_t kTableBytes = size_t(128) << 10;         // FFT table + quadrature nodes
 constexpr int kQuadNodes = 256;
+static_assert(sizeof(float2) * kTwiddleEntries + 2 * sizeof(double) * kQuadNodes <= kTableBytes,
+              "fixed tables exceed their part of the scratch array");
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_nursd_noalloc_scratch[kNoAllocScratchBytes];
@@ -38,13 +40,15 @@ struct DeviceScratch {
 std::mutex g_mutex;
 DeviceScratch g_devices[kMaxDevices];
 
-// Fixed tables (once per device): FFT twiddles e^{-2 pi i q / 4096} and
+// Fixed tables (once per device): the FFT table (twiddle_exponent) and
 // 256-node Gauss-Legendre nodes/weights on [-1, 1] (Newton's method on P_n).
 __global__ void noalloc_tables_kernel(float2* twiddle, double* gx, double* gw) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < (1 << kTwiddleLog)) {
+  if (t < kTwiddleEntries) {
+    int num = 0, lg = 0;
+    twiddle_exponent(t, &num, &lg);
     double s, c;
-    sincospi(-2.0 * t / (double)(1 << kTwiddleLog), &s, &c);
+    sincospi(-2.0 * num / (double)(1 << lg), &s, &c);
     twiddle[t] = make_float2((float)c, (float)s);
   }
   if (t < kQuadNodes) {
@@ -111,9 +115,9 @@ int device_scratch(cudaStream_t s, unsigned char** out) {
     }
     unsigned char* base = static_cast<unsigned char*>(ptr);
     float2* tw = reinterpret_cast<float2*>(base);
-    double* gx = reinterpret_cast<double*>(base + sizeof(float2) * (1 << kTwiddleLog));
+    double* gx = reinterpret_cast<double*>(base + sizeof(float2) * kTwiddleEntries);
     double* gw = gx + kQuadNodes;
-    noalloc_tables_kernel<<<(1 << kTwiddleLog) / 256, 256, 0, s>>>(tw, gx, gw);
+    noalloc_tables_kernel<<<(kTwiddleEntries + 255) / 256, 256, 0, s>>>(tw, gx, gw);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return NURSD_ERR_CUDA;
     d.base = base;
     d.ready = true;
@@ -157,7 +161,7 @@ extern "C" int nursd_nufft1_noalloc(int32_t N, double pitch, double center_x, do
   int rc = device_scratch(s, &base);
   if (rc != NURSD_OK) return rc;
   const float2* tw = reinterpret_cast<const float2*>(base);
-  const double* gx = reinterpret_cast<const double*>(base + sizeof(float2) * (1 << kTwiddleLog));
+  const double* gx = reinterpret_cast<const double*>(base + sizeof(float2) * kTwiddleEntries);
   const double* gw = gx + kQuadNodes;
   unsigned char* call = base + kTableBytes;
   float* dec = reinterpret_cast<float*>(call + o_dec);

@@ -19,9 +19,35 @@
 namespace nursd {
 
 constexpr int kTile = 16;          // spreading tile edge (fine cells)
-constexpr int kTwiddleLog = 12;    // shared FFT twiddle table has 2^12 entries
+constexpr int kTwiddleLog = 12;    // shared FFT twiddle table has 2^12 entries, then the per-thread rows below
 constexpr int kMaxKernelWidth = 8;
 constexpr int kMaxBatch = 256;     // reconstructions per batched call
+
+// The FFT table (kTwiddleEntries complex64 values):
+//   [0, 2^12)                   e^{-2 pi i q / 2^12}
+//   kTw2Offset + 16 k + t       W_256^{k t}            (k, t < 16; the radix-16 x 16 middle stage)
+//   tw3_offset(lg) + R j + t    W_{2^lg}^{j t}         (j < 256, t < R = 2^lg / 256; the last stage)
+// so that a thread reads its whole row of twiddles at one base address.
+constexpr int kTw2Offset = 1 << kTwiddleLog;
+constexpr int kTw3Offset = kTw2Offset + 256;
+__host__ __device__ constexpr int tw3_offset(int lg) { return kTw3Offset + (lg == 9 ? 0 : (lg == 10 ? 512 : 1536)); }
+constexpr int kTwiddleEntries = kTw3Offset + 512 + 1024 + 2048;
+// Entry e of the table is exp(-2 pi i num / 2^lg).
+__host__ __device__ inline void twiddle_exponent(int e, int* num, int* lg) {
+  if (e < kTw2Offset) {
+    *num = e;
+    *lg = kTwiddleLog;
+  } else if (e < kTw3Offset) {
+    const int r = e - kTw2Offset;
+    *num = (r >> 4) * (r & 15);
+    *lg = 8;
+  } else {
+    const int l = e < tw3_offset(10) ? 9 : (e < tw3_offset(11) ? 10 : 11);
+    const int r = e - tw3_offset(l), R = 1 << (l - 8);
+    *num = (r / R) * (r % R);
+    *lg = l;
+  }
+}
 
 __host__ __device__ inline float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -52,7 +78,7 @@ struct PanelArgs {
   int load_i_fastest;    // consecutive threads load consecutive i (FFT axis contiguous in memory)
   int store_hi_fastest;  // consecutive threads store consecutive hi channels
   int store_o_fastest;   // consecutive threads store consecutive outputs o
-  const float2* twiddle;  // e^{-2 pi i q / 2^kTwiddleLog}
+  const float2* twiddle;  // the FFT table (kTwiddleEntries values, 16-byte aligned)
 };
 
 // Launches the panel FFT of length 2^logn (4 <= 2^logn <= 2048). Returns a cudaError_t.
