@@ -47,11 +47,12 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=60)
     ap.add_argument("--no-rows", action="store_true",
                     help="skip the per-row measurements (type-2 voxels, SRSD, adjoint, gradients, batched)")
-    ap.add_argument("--workload", choices=["spad", "grid128", "spad-z8"], default="spad",
+    ap.add_argument("--workload", choices=["spad", "grid128", "spad-z8", "spad-n128"], default="spad",
                     help="spad: the 65k-sample 256^2x128 workload (the metric); grid128: the same samples on "
                          "128^2x64 voxels; spad-z8: the spad workload with 8 of its 128 depth planes (same "
-                         "spread and FFT launches, 1/16 of the table); the last two are small cases for "
-                         "profiler captures")
+                         "spread and FFT launches, 1/16 of the table); spad-n128: the spad workload on "
+                         "128^2x128 voxels (same contraction kernel, 1/4 of the table); the last three are "
+                         "small cases for profiler captures")
     return ap.parse_args()
 
 
@@ -386,6 +387,8 @@ def run_ours(args, rank, world, local):
         wl = workload_c2(seed=BASE_SEED + 2 + rank)  # each rank reconstructs its own measurement
     if args.workload == "spad-z8":
         wl.geom = dataclasses.replace(wl.geom, depths=wl.geom.depths[::16].copy())
+    if args.workload == "spad-n128":
+        wl.geom = dataclasses.replace(wl.geom, N=128, pitch=2.0 * wl.geom.pitch)
     g = wl.geom
     L = len(wl.xy)
     om, wt = nursd.phasor_frequencies(g.lambda_c, g.dt, g.t_pad, g.F)
@@ -506,7 +509,9 @@ def run_ours(args, rank, world, local):
         "data": "synthetic (seeded keystone layout, Poisson histograms of 5 point scatterers)",
         "config": {"workload": {"spad": WORKLOAD,
                                 "grid128": "grid128: " + WORKLOAD.replace("256x256x128", "128x128x64"),
-                                "spad-z8": "spad-z8: " + WORKLOAD.replace("256x256x128", "256x256x8")}[args.workload], "L": L, "T": g.T, "F": F, "N": N, "Z": Z, "M": M, "fine_n": plan.fine_n,
+                                "spad-z8": "spad-z8: " + WORKLOAD.replace("256x256x128", "256x256x8"),
+                                "spad-n128": "spad-n128: " + WORKLOAD.replace("256x256x128", "128x128x128")}[
+                                    args.workload], "L": L, "T": g.T, "F": F, "N": N, "Z": Z, "M": M, "fine_n": plan.fine_n,
                    "parallelism": f"replicas x{world} (one reconstruction per GPU)",
                    "l2": "inputs larger than L2 (histograms 268 MB, transfer table %.2f GB); no flush" %
                          (plan.n_classes * F * Z * 8 / 1e9)},

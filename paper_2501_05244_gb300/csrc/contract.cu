@@ -16,6 +16,8 @@
 // Y[k_s][0..Z) (contiguous).  Duplicate members of degenerate classes
 // (q = 0, q = p, p = M/2) are recomputed and rewritten with identical values
 // by the same lane.  HBM traffic: the table once, U once, Y once.
+#include <algorithm>
+
 #include "nursd_internal.cuh"
 
 namespace nursd {
@@ -133,15 +135,24 @@ __global__ void __launch_bounds__(kClsPerCta * 32, 2) contract_kernel(const floa
 }
 
 // ------------------------------------------------------------------ bulk-copy form
-// Same arithmetic; each warp streams its class through a 3-stage shared-memory
-// ring filled by cp.async.bulk (the TMA's 1-D mode) and completed on an
-// mbarrier with a transaction count.  A stage holds kRows table rows (one
-// contiguous copy of kRows x ZS values) and the class's 8 spectrum segments of
-// those rows (8 copies of kRows values).  16 warps per CTA (one class each)
-// keep ~200 KB per SM in flight.  Used when every CTA column is full
-// (J % (32 ZPL) == 0) and R % kRows == 0, so every copy is a whole number of
-// 16-byte units.  Every barrier wait is bounded: on time-out the kernel sets
-// status bit 2 and returns.
+// Same sums, persistent: warp w of the grid takes the units w, w + W, w + 2W, ...
+// (W = warps in the grid; unit = class x column of 32 ZPL outputs x batch item,
+// batch item fastest so a class's table block is re-read from L2 for the later
+// items).  Each warp streams its units through a 3-stage shared-memory ring
+// filled by cp.async.bulk (the TMA's 1-D mode) and completed on an mbarrier with
+// a transaction count; the ring runs on across unit boundaries, so the next
+// unit's rows are in flight while the current one finishes.  A stage holds
+// kRows table rows (one contiguous copy of kRows x ZS values, or one per row when
+// the column is narrower than the row) and the class's 8 spectrum segments of
+// those rows.  Used when every column is full (J % (32 ZPL) == 0) and
+// R % kRows == 0, so every copy is a whole number of 16-byte units.  Every
+// barrier wait is bounded: on time-out the kernel sets status bit 2 and returns.
+//
+// Arithmetic: each spectrum value u is expanded once per stage to (ux, ux, -uy, uy)
+// and acc += (ux, ux) * (gx, gy) + (-uy, uy) * (gy, gx) in two fma.rn.f32x2 per
+// (output, member).  The conjugate form accumulates conj(u) g and conjugates the sum.
+// Lane L holds outputs 2L, 2L + 1 (+ 64 k) of its column: 16-byte shared loads and
+// global stores are contiguous across the warp.
 constexpr int kTmaWarps = 16, kStages = 3, kRows = 4;
 constexpr long long kWaitLimit = 1LL << 22;
 
@@ -172,110 +183,164 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
   return false;
 }
 
+// d = a * b + c, lane-wise on two fp32 values, one instruction.
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+  float2 r;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+      " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return r;
+}
+
 template <int ZPL>
 struct TmaShape {
   static constexpr int ZS = 32 * ZPL;
   static constexpr int kStageTable = kRows * ZS;  // float2
   static constexpr int kStageU = 8 * kRows;       // float2
   static constexpr int kStage = kStageTable + kStageU;
+  static constexpr size_t kRingBytes = sizeof(float2) * kTmaWarps * kStages * kStage;
+  static constexpr size_t kExpBytes = sizeof(float4) * kTmaWarps * 8 * kRows;  // expanded spectrum values
+  static constexpr size_t kPtrBytes = sizeof(void*) * kTmaWarps * 9;            // producer's source rows
   static constexpr size_t kSmem =
-      sizeof(float2) * kTmaWarps * kStages * kStage + sizeof(unsigned long long) * kTmaWarps * kStages;
+      kRingBytes + kExpBytes + kPtrBytes + sizeof(unsigned long long) * kTmaWarps * kStages;
 };
+
+// Mode index ky*M + kx of member s (s < 8) of class (p, q): (+-p, +-q), (+-q, +-p).
+__device__ __forceinline__ unsigned member_offset(int p, int q, int s, int M) {
+  const int a = (s < 4) ? p : q, b = (s < 4) ? q : p;
+  const int kx = (s & 1) ? -a : a, ky = (s & 2) ? -b : b;
+  return (unsigned)(wrap_index(ky, M) * M + wrap_index(kx, M));
+}
 
 template <int ZPL, bool CONJ>
 __global__ void __launch_bounds__(kTmaWarps * 32, 1) contract_tma_kernel(const float2* __restrict__ U,
                                                                       const float2* __restrict__ Gc,
                                                                       const int2* __restrict__ cls_pq, int ncls,
                                                                       int M, int F, int Z, float2* __restrict__ Y,
-                                                                      long long u_stride, long long y_stride,
+                                                                      long long u_stride, long long y_stride, int B,
                                                                       int* __restrict__ status) {
   using S = TmaShape<ZPL>;
   constexpr int ZS = S::ZS;
   extern __shared__ __align__(16) unsigned char raw[];
-  float2* ring = reinterpret_cast<float2*>(raw);
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(raw + sizeof(float2) * kTmaWarps * kStages * S::kStage);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = blockIdx.y * kTmaWarps + warp;
-  if (c >= ncls) return;  // whole warp; nothing below synchronises across warps
-  U += blockIdx.x * u_stride;
-  Y += blockIdx.x * y_stride;
-  const int zc0 = blockIdx.z * ZS;
-  float2* myring = ring + (size_t)warp * kStages * S::kStage;
-  unsigned long long* mybar = bars + warp * kStages;
-  const float2* __restrict__ g = Gc + (size_t)c * F * Z + zc0;
+  float2* myring = reinterpret_cast<float2*>(raw) + (size_t)warp * kStages * S::kStage;
+  float4* myexp = reinterpret_cast<float4*>(raw + S::kRingBytes) + warp * 8 * kRows;
+  // producer's source rows of its current unit (each slot is written and read by one lane only):
+  // slots 0..7 = the members' spectrum rows (lanes 0..7), slot 8 = the table column (lane 0)
+  const float2** mysrc = reinterpret_cast<const float2**>(raw + S::kRingBytes + S::kExpBytes) + warp * 9;
+  unsigned long long* mybar =
+      reinterpret_cast<unsigned long long*>(raw + S::kRingBytes + S::kExpBytes + S::kPtrBytes) + warp * kStages;
+  const int nz = Z / ZS, nchunk = F / kRows;
+  const int nunit = ncls * nz * B;
+  const int W = gridDim.x * kTmaWarps;
+  const int w0 = blockIdx.x * kTmaWarps + warp;
+  if (w0 >= nunit) return;  // whole warp; nothing below synchronises across warps
 
-  const int2 pq = __ldg(cls_pq + c);
-  const int p = pq.x, q = pq.y;
-  const int kx[8] = {p, -p, p, -p, q, -q, q, -q};
-  const int ky[8] = {q, q, -q, -q, p, p, -p, -p};
-  unsigned off[8];
-#pragma unroll
-  for (int s = 0; s < 8; ++s) off[s] = (unsigned)(wrap_index(ky[s], M) * M + wrap_index(kx[s], M));
-
-  const int nchunk = F / kRows;
-  auto issue = [&](int chunk) {  // lane 0 only
-    const int st = chunk % kStages, f0 = chunk * kRows;
-    float2* dst = myring + st * S::kStage;
-    mbar_expect(mybar + st, (unsigned)(sizeof(float2) * (kRows * ZS + 8 * kRows)));
-    if (ZS == Z) {  // the stage's rows are contiguous in the table
-      bulk_g2s(dst, g + (size_t)f0 * Z, (unsigned)(sizeof(float2) * kRows * ZS), mybar + st);
-    } else {
-      for (int r = 0; r < kRows; ++r)
-        bulk_g2s(dst + r * ZS, g + (size_t)(f0 + r) * Z, (unsigned)(sizeof(float2) * ZS), mybar + st);
+  // ---- producer: unit iu, chunk ich, ring sequence number seq; lane 0 copies the table rows,
+  // lanes 0..7 each copy one member's spectrum segment
+  int iu = w0, ich = 0;
+  auto issue = [&](unsigned seq) {
+    if (iu >= nunit) return;
+    if (ich == 0) {
+      const int b = iu % B, rest = iu / B;
+      const int zc = rest % nz, c = rest / nz;
+      const int2 pq = __ldg(cls_pq + c);
+      if (lane < 8) mysrc[lane] = U + b * u_stride + (size_t)member_offset(pq.x, pq.y, lane, M) * F;
+      if (lane == 0) mysrc[8] = Gc + (size_t)c * F * Z + (size_t)zc * ZS;
     }
-#pragma unroll
-    for (int s = 0; s < 8; ++s)
-      bulk_g2s(dst + S::kStageTable + s * kRows, U + (size_t)off[s] * F + f0, (unsigned)(sizeof(float2) * kRows),
+    const int st = seq % kStages, f0 = ich * kRows;
+    float2* dst = myring + st * S::kStage;
+    if (lane == 0) mbar_expect(mybar + st, (unsigned)(sizeof(float2) * (kRows * ZS + 8 * kRows)));
+    __syncwarp();
+    if (lane == 0) {
+      const float2* g = mysrc[8];
+      if (ZS == Z) {  // the stage's rows are contiguous in the table
+        bulk_g2s(dst, g + (size_t)f0 * Z, (unsigned)(sizeof(float2) * kRows * ZS), mybar + st);
+      } else {
+        for (int r = 0; r < kRows; ++r)
+          bulk_g2s(dst + r * ZS, g + (size_t)(f0 + r) * Z, (unsigned)(sizeof(float2) * ZS), mybar + st);
+      }
+    }
+    if (lane < 8)
+      bulk_g2s(dst + S::kStageTable + lane * kRows, mysrc[lane] + f0, (unsigned)(sizeof(float2) * kRows),
                mybar + st);
+    if (++ich == nchunk) {
+      ich = 0;
+      iu += W;
+    }
   };
   if (lane == 0) {
     for (int st = 0; st < kStages; ++st) mbar_init(mybar + st, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    for (int ch = 0; ch < kStages && ch < nchunk; ++ch) issue(ch);
   }
   __syncwarp();
+  for (unsigned k = 0; k < kStages; ++k) issue(k);
 
-  const int zl = lane * ZPL;
-  float2 acc[ZPL][8];
-#pragma unroll
-  for (int i = 0; i < ZPL; ++i)
-#pragma unroll
-    for (int s = 0; s < 8; ++s) acc[i][s] = make_float2(0.f, 0.f);
+  // ---- consumer
+  unsigned cseq = 0;
+  const int zl = 2 * lane;  // outputs zl, zl + 1 (+ 64 h, h < ZPL / 2) of the column
   bool ok = true;
-  for (int ch = 0; ch < nchunk; ++ch) {
-    const int st = ch % kStages;
-    if (!mbar_wait(mybar + st, (unsigned)((ch / kStages) & 1))) {
-      ok = false;
-      break;
-    }
-    const float2* stage = myring + st * S::kStage;
+  for (int cu = w0; cu < nunit && ok; cu += W) {
+    float2 acc[ZPL][8];
 #pragma unroll
-    for (int r = 0; r < kRows; ++r) {
-      float2 gv[ZPL], u[8];
+    for (int i = 0; i < ZPL; ++i)
 #pragma unroll
-      for (int i = 0; i < ZPL; i += 2) {
-        const float4 t = *reinterpret_cast<const float4*>(stage + r * ZS + zl + i);
-        gv[i] = make_float2(t.x, t.y);
-        gv[i + 1] = make_float2(t.z, t.w);
+      for (int s = 0; s < 8; ++s) acc[i][s] = make_float2(0.f, 0.f);
+    for (int ch = 0; ch < nchunk; ++ch) {
+      const int st = cseq % kStages;
+      if (!mbar_wait(mybar + st, (cseq / kStages) & 1)) {
+        ok = false;
+        break;
       }
-#pragma unroll
-      for (int s = 0; s < 8; ++s) u[s] = stage[S::kStageTable + s * kRows + r];
-      if (CONJ) {
-#pragma unroll
-        for (int i = 0; i < ZPL; ++i) gv[i].y = -gv[i].y;
+      const float2* stage = myring + st * S::kStage;
+      {  // expand this stage's 8 x kRows spectrum values, one per lane
+        const float2 u = stage[S::kStageTable + lane];
+        myexp[lane] = CONJ ? make_float4(u.x, u.x, u.y, -u.y) : make_float4(u.x, u.x, -u.y, u.y);
       }
+      __syncwarp();
 #pragma unroll
-      for (int i = 0; i < ZPL; ++i)
+      for (int r = 0; r < kRows; ++r) {
+        float2 gv[ZPL], gs[ZPL];
+#pragma unroll
+        for (int h = 0; h < ZPL / 2; ++h) {
+          const float4 t = *reinterpret_cast<const float4*>(stage + r * ZS + 64 * h + zl);
+          gv[2 * h] = make_float2(t.x, t.y);
+          gv[2 * h + 1] = make_float2(t.z, t.w);
+        }
+#pragma unroll
+        for (int i = 0; i < ZPL; ++i) gs[i] = make_float2(gv[i].y, gv[i].x);
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
-          acc[i][s].x = fmaf(gv[i].x, u[s].x, acc[i][s].x);
-          acc[i][s].x = fmaf(-gv[i].y, u[s].y, acc[i][s].x);
-          acc[i][s].y = fmaf(gv[i].x, u[s].y, acc[i][s].y);
-          acc[i][s].y = fmaf(gv[i].y, u[s].x, acc[i][s].y);
+          const float4 e = myexp[s * kRows + r];
+          const float2 uu = make_float2(e.x, e.y), vv = make_float2(e.z, e.w);
+#pragma unroll
+          for (int i = 0; i < ZPL; ++i) {
+            acc[i][s] = pfma(uu, gv[i], acc[i][s]);
+            acc[i][s] = pfma(vv, gs[i], acc[i][s]);
+          }
         }
+      }
+      __syncwarp();  // every lane has read this stage and the expanded values
+      issue(cseq + kStages);
+      ++cseq;
     }
-    __syncwarp();  // every lane has read this stage
-    if (lane == 0 && ch + kStages < nchunk) issue(ch + kStages);
+    if (!ok) break;
+    const int b = cu % B, rest = cu / B;
+    const int zc = rest % nz, c = rest / nz;
+    const int2 pq = __ldg(cls_pq + c);
+    const unsigned moff = member_offset(pq.x, pq.y, lane & 7, M);
+    float2* yb = Y + b * y_stride + (size_t)zc * ZS + zl;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      float2* dst = yb + (size_t)__shfl_sync(0xffffffffu, moff, s) * Z;
+#pragma unroll
+      for (int h = 0; h < ZPL / 2; ++h) {
+        const float2 a0 = acc[2 * h][s], a1 = acc[2 * h + 1][s];
+        *reinterpret_cast<float4*>(dst + 64 * h) =
+            CONJ ? make_float4(a0.x, -a0.y, a1.x, -a1.y) : make_float4(a0.x, a0.y, a1.x, a1.y);
+      }
+    }
   }
   if (!ok) {
     if (lane == 0) atomicOr(status, 2);
@@ -284,14 +349,6 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) contract_tma_kernel(const f
       mbar_wait(mybar + st, 0);
       mbar_wait(mybar + st, 1);
     }
-    return;
-  }
-#pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    float2* dst = Y + (size_t)off[s] * Z + zc0 + zl;
-#pragma unroll
-    for (int i = 0; i < ZPL; i += 2)
-      *reinterpret_cast<float4*>(dst + i) = make_float4(acc[i][s].x, acc[i][s].y, acc[i + 1][s].x, acc[i + 1][s].y);
   }
 }
 
@@ -301,16 +358,21 @@ cudaError_t launch_tma(const float2* U, const float2* Gc, const int2* cls_pq, in
   constexpr int ZS = TmaShape<ZPL>::ZS;
   const size_t smem = TmaShape<ZPL>::kSmem;
   static bool configured = false;
+  static int sms = 0;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(contract_tma_kernel<ZPL, CONJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     configured = true;
   }
-  dim3 grid(B, (ncls + kTmaWarps - 1) / kTmaWarps, (Z + ZS - 1) / ZS);
-  if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidValue;
+  const long long nunit = (long long)ncls * (Z / ZS) * B;
+  if (nunit >= (1LL << 31)) return cudaErrorInvalidValue;
+  const int grid = (int)std::min<long long>(sms, (nunit + kTmaWarps - 1) / kTmaWarps);
   contract_tma_kernel<ZPL, CONJ><<<grid, kTmaWarps * 32, smem, s>>>(U, Gc, cls_pq, ncls, M, F, Z, Y, u_stride,
-                                                                   y_stride, status);
+                                                                   y_stride, B, status);
   return cudaGetLastError();
 }
 
