@@ -5,7 +5,9 @@
 // because |u| reaches sigma N / 2 = 256 cells and the fractional part must stay
 // exact to ~1e-9.  Its footprint is the w cells i0..i0+w-1, i0 = ceil(u - w/2),
 // with ES weights phi(2 (i - u) / w), phi(z) = exp(beta (sqrt(1 - z^2) - 1)).
-// Samples are then sorted by bin = (first footprint row, 16-cell tile column):
+// Samples are then sorted by bin = (16-cell tile column, first footprint row), tile
+// column major, so the samples of one tile column over a run of rows are one
+// contiguous slot range:
 // counts, one exclusive scan, a scatter, an insertion sort of each (small) bin
 // by sample index and a gather of the per-sample data into sorted order.  The
 // order inside every bin is thus fixed, so the spread -- and the FP32 rounding
@@ -43,7 +45,7 @@ __global__ void points_prepare(const PointsArgs a, int2* __restrict__ i0_out, fl
   const int rx = min(max(ix - a.g0, 0), a.W - 1), ry = min(max(iy - a.g0, 0), a.W - 1);
   i0_out[l] = make_int2(rx, ry);
   if (frac_out) frac_out[l] = make_float2((float)(ux - ix), (float)(uy - iy));
-  const int bin = ry * a.tiles + rx / kTile;  // (footprint row, tile column)
+  const int bin = (rx / kTile) * a.W + ry;  // (tile column, footprint row)
   bin_of[l] = bin;
   atomicAdd(counts + bin, 1);
 }
