@@ -31,6 +31,7 @@ struct SpreadSmem {
   float wy[kCap][8];    // y weights
   int ox[kCap];         // first footprint column (window index)
   int oy[kCap];         // first footprint row
+  int l[kCap];          // sample index (row of P)
 };
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc, bool valid) {
@@ -101,23 +102,29 @@ __global__ void __launch_bounds__(kWarps * 32, 2) spread_kernel(const float2* __
   for (int c0 = 0; c0 < n; c0 += kCap) {
     const int cn = min(kCap, n - c0);
     __syncthreads();  // the previous chunk has been consumed
-    for (int s = warp; s < cn; s += kWarps) {  // one warp per sample: its 32 channels
+    // phase 1, one thread per sample (all loads in flight at once): index, origin, weights
+    for (int s = threadIdx.x; s < cn; s += kWarps * 32) {
       const int v = c0 + s;
       const int slot = v < nA ? aS + v : bS + (v - nA);
       const int l = __ldg(sorted_l + slot);
-      cp_async8(&sm.p[s][lane], live ? P + (size_t)l * F + f0 + lane : P, live);
-      if (lane < 2 * KW) {
-        const float wt = __ldg(wts + (size_t)slot * 2 * KW + lane);
-        if (lane < KW)
-          sm.wx[s][lane] = wt;
-        else
-          sm.wy[s][lane - KW] = wt;
-      } else if (lane == 31) {
-        const int2 o = __ldg(i0 + slot);
-        sm.ox[s] = o.x;
-        sm.oy[s] = o.y;
+      const int2 o = __ldg(i0 + slot);
+      const float* w = wts + (size_t)slot * 2 * KW;
+      float wv[2 * KW];
+#pragma unroll
+      for (int t = 0; t < 2 * KW; ++t) wv[t] = __ldg(w + t);
+      sm.l[s] = l;
+      sm.ox[s] = o.x;
+      sm.oy[s] = o.y;
+#pragma unroll
+      for (int t = 0; t < KW; ++t) {
+        sm.wx[s][t] = wv[t];
+        sm.wy[s][t] = wv[KW + t];
       }
     }
+    __syncthreads();
+    // phase 2, one warp per sample: its 32 channels of P
+    for (int s = warp; s < cn; s += kWarps)
+      cp_async8(&sm.p[s][lane], live ? P + (size_t)sm.l[s] * F + f0 + lane : P, live);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
