@@ -69,6 +69,7 @@ struct nursd_plan_s {
   float2* GcT = nullptr;  // transposed table [ncls][Z][F] for the adjoint (NURSD_ENABLE_ADJOINT)
   __half* Bth = nullptr;  // temporal twiddles B^T [2F][T], fp16 head
   __half* Btl = nullptr;  // and tail (B - head)
+  TemporalMaps tmaps{};   // TMA descriptors of Bth/Btl for the tcgen05 form (ok = 0: mma.sync form)
   // SRSD tables (h_srsd_pitch given): scaled transfer table [Z][ncls][F], chirps [Z][M], FFT(b)/(2M) [Z][2M]
   std::vector<double> srsd_pitch;
   float2* Gs = nullptr;
@@ -168,6 +169,14 @@ namespace {
 int from_cuda(cudaError_t e) { return e == cudaSuccess ? NURSD_OK : NURSD_ERR_CUDA; }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// C[L][2F] = H[L][T] B: tcgen05 form when the plan has its descriptors and both buffers are
+// 16-byte aligned, mma.sync form otherwise.
+cudaError_t run_temporal(const nursd_plan_s* p, const float* h, float* C, int L, cudaStream_t s) {
+  if (p->tmaps.ok && aligned(h, 16) && aligned(C, 16))
+    return launch_temporal_umma(p->tmaps, h, C, L, p->T, 2 * p->F, p->status, s);
+  return launch_temporal_tc(h, p->Bth, p->Btl, C, L, p->T, 2 * p->F, s);
+}
 
 PanelArgs panel_base(const nursd_plan_s* p) {
   PanelArgs a;
@@ -717,6 +726,7 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
     rc = from_cuda(cudaMemcpyAsync(p->Btl, Btl.data(), sizeof(__half) * Btl.size(), cudaMemcpyHostToDevice, s));
   if (rc == NURSD_OK) rc = from_cuda(cudaMemsetAsync(p->status, 0, sizeof(int), s));
   if (rc == NURSD_OK) rc = from_cuda(cudaMemsetAsync(p->bin_start, 0, sizeof(int) * (nbins + 1), s));
+  if (rc == NURSD_OK && p->T > 0) make_temporal_maps(p->Bth, p->Btl, p->T, 2 * p->F, &p->tmaps);
   if (rc == NURSD_OK) rc = build_table(p, false, s);
   if (rc == NURSD_OK && p->Gs) rc = build_table(p, true, s);
   if (rc == NURSD_OK && p->Gs) rc = build_srsd_chirps(p, s);
@@ -774,8 +784,7 @@ int nursd_temporal_dft(nursd_plan_t p, int32_t L, const float* d_hist, nursd_c64
   if (check_plan(p) != NURSD_OK || p->T <= 0 || L < 0 || L > p->maxL) return NURSD_ERR_INVALID_ARG;
   if (L > 0 && (!d_hist || !d_phasor || !aligned(d_hist, 16) || !aligned(d_phasor, 8))) return NURSD_ERR_INVALID_ARG;
   StageTimer t(p, NURSD_STAGE_TEMPORAL, static_cast<cudaStream_t>(stream), L > 0 ? 1 : 0);
-  return from_cuda(launch_temporal_tc(d_hist, p->Bth, p->Btl, reinterpret_cast<float*>(d_phasor), L, p->T, 2 * p->F,
-                                      static_cast<cudaStream_t>(stream)));
+  return from_cuda(run_temporal(p, d_hist, reinterpret_cast<float*>(d_phasor), L, static_cast<cudaStream_t>(stream)));
 }
 
 int nursd_nufft1(nursd_plan_t p, const nursd_c64* d_phasor, nursd_c64* d_spectrum, nursd_stream_t stream) {
@@ -807,8 +816,7 @@ int nursd_forward(nursd_plan_t p, const float* d_hist, void* d_out, nursd_stream
   int rc;
   {
     StageTimer t(p, NURSD_STAGE_TEMPORAL, s, p->L > 0 ? 1 : 0);
-    rc = from_cuda(launch_temporal_tc(d_hist, p->Bth, p->Btl, reinterpret_cast<float*>(p->phasor), p->L, p->T,
-                                      2 * p->F, s));
+    rc = from_cuda(run_temporal(p, d_hist, reinterpret_cast<float*>(p->phasor), p->L, s));
   }
   if (rc == NURSD_OK) rc = run_nufft1(p, p->phasor, p->U, s);
   if (rc == NURSD_OK) rc = run_propagate(p, p->U, d_out, s);
@@ -995,7 +1003,7 @@ int nursd_sync_status(nursd_plan_t p, nursd_stream_t stream) {
   if (cudaMemcpyAsync(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return NURSD_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return NURSD_ERR_CUDA;
   if (h != 0 && cudaMemsetAsync(p->status, 0, sizeof(int), s) != cudaSuccess) return NURSD_ERR_CUDA;
-  if (h & 2) return NURSD_ERR_TIMEOUT;
+  if (h & 6) return NURSD_ERR_TIMEOUT;  // a bounded barrier wait gave up (contraction: 2, temporal: 4)
   if (h & 1) return NURSD_ERR_POINT_OUT_OF_RANGE;
   return NURSD_OK;
 }

@@ -11,6 +11,7 @@
 //   half IDFT    T1   [M][N][Z]         after the inverse FFT along kx
 //   volume       V    [Z][N][N]         complex64 or magnitude float32
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -100,6 +101,19 @@ cudaError_t launch_panel_bluestein(int logn, const PanelArgs& a, const float2* c
 // tensor cores; Bh/Bl are the fp16 head and tail of B^T, [2F][T] (__half).
 cudaError_t launch_temporal_tc(const float* h, const void* Bh, const void* Bl, float* C, int L, int T, int twoF,
                                cudaStream_t s);
+
+// The same transform with tcgen05.mma (temporal_umma.cu), for T % 64 == 0 and 2F in {32, 64, 128, 256}.
+// TMA descriptors of B's head and tail ([2F][T] fp16) are encoded once per plan.
+struct TemporalMaps {
+  CUtensorMap hi;
+  CUtensorMap lo;
+  int ok;
+};
+bool temporal_umma_supported(int T, int twoF);
+bool make_temporal_maps(const void* Bh, const void* Bl, int T, int twoF, TemporalMaps* m);
+// status: bit 4 is set if a barrier wait timed out (the output is then incomplete).
+cudaError_t launch_temporal_umma(const TemporalMaps& m, const float* h, float* C, int L, int T, int twoF,
+                                 int* status, cudaStream_t s);
 
 // Ragged batch of temporal transforms: item b has L[b] rows at A[b] -> C[b];
 // tile_start[b] = number of 128 x 128 output tiles of items 0..b-1.

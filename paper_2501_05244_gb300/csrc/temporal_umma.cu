@@ -1,0 +1,425 @@
+// Temporal transform on the 5th-generation tensor cores (Eq. PF_Response with Eq. PFPacket):
+// C[L][2F] = H[L][T] * B[T][2F], B[n][2f] = w_f cos(w_f t_n), B[n][2f+1] = -w_f sin(w_f t_n),
+// as tcgen05.mma (kind::f16: fp16 operands, fp32 accumulation in tensor memory).
+//
+// FP32 accuracy from fp16 products, as in the mma.sync form: x = x_hi + x_lo with
+// x_lo = fp16(x - x_hi), and C = H_hi B_hi + H_hi B_lo + H_lo B_hi, every product
+// exact in the fp32 accumulator.  B's head and tail are split once at plan time
+// ([2F][T], K-major); H is split as it is staged, and a K-block whose H_lo is all
+// zero (photon counts below 2048 are exact in fp16) skips the H_lo product.
+//
+// One CTA per SM walks 128-row tiles of H (tile blockIdx.x + j gridDim.x).  Warp roles:
+//   0-3  epilogue: tcgen05.ld of the 128 x 2F accumulator (one row per thread), fp32 stores;
+//        two accumulators in tensor memory, so a tile's epilogue overlaps the next tile's MMAs
+//   4-7  H producers: global loads one K-block ahead, fp16 head/tail split, stores into the
+//        128-byte-swizzled K-major operand layout
+//   8    B producer (one thread): TMA tiled copies of the 64 x 2F head and tail blocks
+//   9    MMA issuer (one thread): 4 k-steps of 16 per K-block, tcgen05.commit to the
+//        stage's "empty" barrier and, after the tile's last K-block, to the accumulator's
+//        "full" barrier
+// Stages (2) hold A_hi, A_lo (128 x 64 fp16 each) and B_hi, B_lo (2F x 64 fp16 each).
+// Every mbarrier wait is bounded: on time-out the waiting role sets an abort flag (and
+// status bit 4), every role stops issuing work, copies and MMAs in flight are drained,
+// and tensor memory is released before the CTA exits.
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "nursd_internal.cuh"
+
+namespace nursd {
+namespace {
+
+constexpr int kBM = 128, kBK = 64, kUStages = 2;
+constexpr int kEpiWarps = 4, kCvtWarps = 4;
+constexpr int kProducerWarp = kEpiWarps + kCvtWarps, kMmaWarp = kProducerWarp + 1;
+constexpr int kUThreads = (kMmaWarp + 1) * 32;
+constexpr long long kUSpin = 1LL << 22;
+
+template <int N2>
+struct UShape {
+  static constexpr int kA = kBM * 128;  // one A tile: 128 rows x 64 fp16
+  static constexpr int kB = N2 * 128;   // one B tile: N2 rows x 64 fp16
+  static constexpr int kStage = 2 * kA + 2 * kB;
+  static constexpr int kAcc = N2 < 32 ? 32 : N2;  // tensor-memory columns per accumulator
+  static constexpr size_t kSmem = 1024 + (size_t)kUStages * kStage + 512;
+};
+
+struct Ctl {
+  unsigned long long full_a[kUStages], full_b[kUStages], empty[kUStages];
+  unsigned long long acc_full[2], acc_empty[2], drain;
+  unsigned tmem;
+  int abort;
+  int lo[kUStages][kCvtWarps];
+};
+
+__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(sa(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(unsigned long long* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(sa(b)) : "memory");
+}
+__device__ __forceinline__ void bar_expect_tx(unsigned long long* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(sa(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool bar_try(unsigned long long* b, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(sa(b)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Bounded wait for the phase of parity `parity`; gives up early once another role aborted.
+__device__ __forceinline__ bool bar_wait(unsigned long long* b, unsigned parity, volatile int* abort) {
+  for (long long i = 0; i < kUSpin; ++i) {
+    if (bar_try(b, parity)) return true;
+    if ((i & 255) == 255 && *abort) return false;
+  }
+  *abort = 1;
+  return false;
+}
+
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte swizzle layout
+// (rows of 128 bytes, 8-row groups 1024 bytes apart, tile base 1024-byte aligned).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                           // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                           // descriptor version
+  d |= (uint64_t)2 << 61;                           // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor, kind::f16: fp16 A and B (K-major), fp32 D, M x N.
+__host__ __device__ constexpr uint32_t f16_idesc(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(unsigned long long* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(sa(b))
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x, int y, unsigned long long* b) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          sa(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(sa(b))
+      : "memory");
+}
+
+// 32 consecutive fp32 columns of this warp's 32 tensor-memory lanes (one per thread).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+// fp16 head of two floats packed (low half = a), and the fp16 tail of what the head misses.
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(a, b);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+template <int N2>
+__global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float* __restrict__ H,
+                                                                     float* __restrict__ C, int L, int T,
+                                                                     const __grid_constant__ CUtensorMap tm_hi,
+                                                                     const __grid_constant__ CUtensorMap tm_lo,
+                                                                     int* __restrict__ status) {
+  using S = UShape<N2>;
+  extern __shared__ unsigned char raw[];
+  const uint32_t raw_addr = sa(raw);
+  unsigned char* base = raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
+  const uint32_t base_addr = sa(base);
+  Ctl& ctl = *reinterpret_cast<Ctl*>(base + kUStages * S::kStage);
+  volatile int* abort = &ctl.abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = (L + kBM - 1) / kBM, nkb = T / kBK;
+  const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int my_iters = my_tiles * nkb;
+  auto a_hi = [&](int st) { return base + st * S::kStage; };
+  auto a_lo = [&](int st) { return base + st * S::kStage + S::kA; };
+  auto b_hi = [&](int st) { return base + st * S::kStage + 2 * S::kA; };
+  auto b_lo = [&](int st) { return base + st * S::kStage + 2 * S::kA + S::kB; };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kUStages; ++s) {
+      bar_init(&ctl.full_a[s], kCvtWarps);
+      bar_init(&ctl.full_b[s], 1);
+      bar_init(&ctl.empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      bar_init(&ctl.acc_full[s], 1);
+      bar_init(&ctl.acc_empty[s], kEpiWarps);
+    }
+    bar_init(&ctl.drain, 1);
+    ctl.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(sa(&ctl.tmem)),
+                 "r"(2 * S::kAcc)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    fence_before_sync();
+  }
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = ctl.tmem;
+
+  if (warp < kEpiWarps) {
+    // ---------------------------------------------------------------- epilogue
+    for (int j = 0; j < my_tiles; ++j) {
+      const int ab = j & 1;
+      if (!bar_wait(&ctl.acc_full[ab], (j >> 1) & 1, abort)) break;
+      fence_after_sync();
+      const int row = ((int)blockIdx.x + j * (int)gridDim.x) * kBM + warp * 32 + lane;
+      const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * S::kAcc);
+#pragma unroll 1
+      for (int c0 = 0; c0 < N2; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(tb + c0, r);
+        if (row < L) {
+          float4* dst = reinterpret_cast<float4*>(C + (size_t)row * N2 + c0);
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                 __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+        }
+      }
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) bar_arrive(&ctl.acc_empty[ab]);
+    }
+  } else if (warp < kEpiWarps + kCvtWarps) {
+    // ---------------------------------------------------------------- H producers
+    const int cw = warp - kEpiWarps, ct = cw * 32 + lane;
+    // task q: row ct / 8 + 16 q of the tile, 16-byte chunk ct % 8 (8 consecutive K values)
+    const int r0 = ct >> 3, ch = ct & 7;
+    auto load = [&](float4 (&v)[16], int it) {
+      const int j = it / nkb, kb = it - j * nkb;
+      const int m0 = ((int)blockIdx.x + j * (int)gridDim.x) * kBM;
+      const float* src = H + (size_t)(m0 + r0) * T + kb * kBK + ch * 8;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const bool ok = m0 + r0 + 16 * q < L;
+        const float4* s4 = reinterpret_cast<const float4*>(src + (size_t)16 * q * T);
+        v[2 * q] = ok ? __ldg(s4) : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[2 * q + 1] = ok ? __ldg(s4 + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    auto stage = [&](const float4 (&v)[16], int it) -> bool {
+      const int st = it % kUStages, ph = (it / kUStages) & 1;
+      if (!bar_wait(&ctl.empty[st], ph ^ 1, abort)) return false;
+      unsigned char* ah = a_hi(st);
+      unsigned char* al = a_lo(st);
+      uint32_t any = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int r = r0 + 16 * q;
+        const float4 x = v[2 * q], y = v[2 * q + 1];
+        uint4 h, l;
+        split2(x.x, x.y, h.x, l.x);
+        split2(x.z, x.w, h.y, l.y);
+        split2(y.x, y.y, h.z, l.z);
+        split2(y.z, y.w, h.w, l.w);
+        any |= (l.x | l.y | l.z | l.w) & 0x7fff7fffu;
+        const int off = r * 128 + ((ch ^ (r & 7)) << 4);
+        *reinterpret_cast<uint4*>(ah + off) = h;
+        *reinterpret_cast<uint4*>(al + off) = l;
+      }
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      const int warp_any = __any_sync(0xffffffffu, any != 0);
+      __syncwarp();
+      if (lane == 0) {
+        ctl.lo[st][cw] = warp_any;
+        bar_arrive(&ctl.full_a[st]);
+      }
+      return true;
+    };
+    float4 va[16], vb[16];
+    if (my_iters > 0) load(va, 0);
+    for (int it = 0; it < my_iters; it += 2) {
+      if (it + 1 < my_iters) load(vb, it + 1);
+      if (!stage(va, it)) break;
+      if (it + 1 >= my_iters) break;
+      if (it + 2 < my_iters) load(va, it + 2);
+      if (!stage(vb, it + 1)) break;
+    }
+  } else if (warp == kProducerWarp) {
+    // ---------------------------------------------------------------- B producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < my_iters; ++it) {
+        const int kb = it % nkb, st = it % kUStages, ph = (it / kUStages) & 1;
+        if (!bar_wait(&ctl.empty[st], ph ^ 1, abort)) break;
+        bar_expect_tx(&ctl.full_b[st], (unsigned)(2 * S::kB));
+        tma_2d(b_hi(st), &tm_hi, kb * kBK, 0, &ctl.full_b[st]);
+        tma_2d(b_lo(st), &tm_lo, kb * kBK, 0, &ctl.full_b[st]);
+        issued = it + 1;
+      }
+      // the last copies have landed before the CTA can exit (already true unless a role aborted)
+      for (int it = max(0, issued - kUStages); it < issued; ++it) {
+        for (long long i = 0; i < kUSpin; ++i)
+          if (bar_try(&ctl.full_b[it % kUStages], (it / kUStages) & 1)) break;
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = f16_idesc(kBM, N2);
+      int it = 0;
+      bool ok = true;
+      for (int j = 0; j < my_tiles && ok; ++j) {
+        const int ab = j & 1;
+        if (!bar_wait(&ctl.acc_empty[ab], ((j >> 1) & 1) ^ 1, abort)) break;
+        fence_after_sync();
+        const uint32_t d = tmem + (uint32_t)(ab * S::kAcc);
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int st = it % kUStages, ph = (it / kUStages) & 1;
+          if (!bar_wait(&ctl.full_b[st], ph, abort) || !bar_wait(&ctl.full_a[st], ph, abort)) {
+            ok = false;
+            break;
+          }
+          fence_after_sync();
+          int lo = 0;
+#pragma unroll
+          for (int w = 0; w < kCvtWarps; ++w) lo |= ctl.lo[st][w];
+          const uint64_t dah = sw128_desc(sa(a_hi(st))), dal = sw128_desc(sa(a_lo(st)));
+          const uint64_t dbh = sw128_desc(sa(b_hi(st))), dbl = sw128_desc(sa(b_lo(st)));
+#pragma unroll
+          for (int kk = 0; kk < kBK / 16; ++kk) {  // 16 fp16 = 32 bytes along K per instruction
+            const uint64_t adv = (uint64_t)(2 * kk);
+            umma_f16(d, dah + adv, dbh + adv, idesc, (kb | kk) != 0);
+            umma_f16(d, dah + adv, dbl + adv, idesc, 1u);
+            if (lo) umma_f16(d, dal + adv, dbh + adv, idesc, 1u);
+          }
+          umma_commit(&ctl.empty[st]);
+        }
+        if (ok) umma_commit(&ctl.acc_full[ab]);
+      }
+      // every MMA issued has completed before the CTA tears down
+      umma_commit(&ctl.drain);
+      for (long long i = 0; i < kUSpin; ++i)
+        if (bar_try(&ctl.drain, 0)) break;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && ctl.abort) atomicOr(status, 4);
+  if (warp == 0) {
+    fence_after_sync();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(2 * S::kAcc)
+                 : "memory");
+  }
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// [rows][T] fp16, K-major, 64 x rows boxes in the 128-byte swizzle.
+bool encode_b(CUtensorMap* m, const void* ptr, int T, int rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)T, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)T * sizeof(__half)};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int N2>
+cudaError_t launch_n(const TemporalMaps& m, const float* h, float* C, int L, int T, int* status, cudaStream_t s) {
+  using S = UShape<N2>;
+  static bool configured = false;
+  static int sms = 0;
+  if (!configured) {
+    cudaError_t e =
+        cudaFuncSetAttribute(temporal_umma_kernel<N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    configured = true;
+  }
+  const int ntiles = (L + kBM - 1) / kBM;
+  const int grid = std::min(ntiles, sms);
+  temporal_umma_kernel<N2><<<grid, kUThreads, S::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool temporal_umma_supported(int T, int twoF) {
+  return T > 0 && T % kBK == 0 && (twoF == 32 || twoF == 64 || twoF == 128 || twoF == 256);
+}
+
+bool make_temporal_maps(const void* Bh, const void* Bl, int T, int twoF, TemporalMaps* m) {
+  m->ok = 0;
+  if (!temporal_umma_supported(T, twoF)) return false;
+  if (reinterpret_cast<uintptr_t>(Bh) % 16 != 0 || reinterpret_cast<uintptr_t>(Bl) % 16 != 0) return false;
+  if (!encode_b(&m->hi, Bh, T, twoF) || !encode_b(&m->lo, Bl, T, twoF)) return false;
+  m->ok = 1;
+  return true;
+}
+
+cudaError_t launch_temporal_umma(const TemporalMaps& m, const float* h, float* C, int L, int T, int twoF,
+                                 int* status, cudaStream_t s) {
+  if (L <= 0) return cudaSuccess;
+  if (!m.ok || !temporal_umma_supported(T, twoF) || reinterpret_cast<uintptr_t>(h) % 16 != 0 ||
+      reinterpret_cast<uintptr_t>(C) % 16 != 0)
+    return cudaErrorInvalidValue;
+  switch (twoF) {
+    case 32: return launch_n<32>(m, h, C, L, T, status, s);
+    case 64: return launch_n<64>(m, h, C, L, T, status, s);
+    case 128: return launch_n<128>(m, h, C, L, T, status, s);
+    default: return launch_n<256>(m, h, C, L, T, status, s);
+  }
+}
+
+}  // namespace nursd
