@@ -364,29 +364,93 @@ __device__ __forceinline__ int small_div(int x, int d, float inv) {
   return qt;
 }
 
+// Writes the kept bins of the panel held in xbuf as [bin][CP] (dense) to global memory:
+// output o = (bin - out_off) mod n for o < nout, scaled by scale * mul_b[b] * mul_o[o]
+// (or as magnitudes).  Threads take fixed channels (pairs of adjacent channels when
+// vec2) and every (NT / channels)-th row, so consecutive threads store consecutive
+// addresses along the contiguous channel axis.
+template <int LOGN, int CP, int NT>
+__device__ __forceinline__ void copy_out(const PanelArgs& a, const float2* xbuf, int b, int hi0, int lo0,
+                                         int vec2) {
+  constexpr int n = 1 << LOGN;
+  const int tid = threadIdx.x;
+  const float sb = a.scale * (a.mul_b ? __ldg(a.mul_b + b) : 1.f);
+  const bool scaled = a.mul_o != nullptr || sb != 1.f;
+  const long long obase = (long long)b * a.out_sb;
+  if (vec2) {  // out_slo == 1, channel pairs (qq, qq + 1) share hi and are 16-byte aligned
+    constexpr int CP2 = CP / 2, RSTEP = NT / CP2;
+    const int qq = 2 * (tid % CP2);
+    const int hi = hi0 + qq / a.CLO, lo = lo0 + qq % a.CLO;
+    if (hi >= a.hi_total || lo >= a.lo_total) return;
+    const long long cbase = obase + (long long)hi * a.out_shi + lo;
+    for (int o = tid / CP2; o < a.nout; o += RSTEP) {
+      const int bin = (o + a.out_off) & (n - 1);
+      float4 x = *reinterpret_cast<const float4*>(xbuf + bin * CP + qq);
+      if (scaled) {
+        const float sc = sb * (a.mul_o ? __ldg(a.mul_o + o) : 1.f);
+        x.x *= sc;
+        x.y *= sc;
+        x.z *= sc;
+        x.w *= sc;
+      }
+      const long long off = cbase + (long long)o * a.out_si;
+      if (a.out_mag)
+        *reinterpret_cast<float2*>(a.out_mag + off) =
+            make_float2(sqrtf(x.x * x.x + x.y * x.y), sqrtf(x.z * x.z + x.w * x.w));
+      else
+        *reinterpret_cast<float4*>(a.out + off) = x;
+    }
+  } else {  // one channel per thread; hi fastest across threads when hi is the contiguous axis
+    constexpr int RSTEP = NT / CP;
+    const int c = tid % CP;
+    const int qq = a.store_hi_fastest ? (c % a.CHI) * a.CLO + c / a.CHI : c;
+    const int hi = hi0 + qq / a.CLO, lo = lo0 + qq % a.CLO;
+    if (hi >= a.hi_total || lo >= a.lo_total) return;
+    const long long cbase = obase + (long long)hi * a.out_shi + (long long)lo * a.out_slo;
+    for (int o = tid / CP; o < a.nout; o += RSTEP) {
+      const int bin = (o + a.out_off) & (n - 1);
+      float2 x = xbuf[bin * CP + qq];
+      if (scaled) {
+        const float sc = sb * (a.mul_o ? __ldg(a.mul_o + o) : 1.f);
+        x.x *= sc;
+        x.y *= sc;
+      }
+      const long long off = cbase + (long long)o * a.out_si;
+      if (a.out_mag)
+        a.out_mag[off] = sqrtf(x.x * x.x + x.y * x.y);
+      else
+        a.out[off] = x;
+    }
+  }
+}
+
 // Persistent form: each CTA walks panels p = blockIdx.x, +gridDim.x, ... (panel p =
 // batch item p / nchunk, channel chunk p mod nchunk).  A panel's input window is
-// staged in shared memory ([nin][CP]) by cp.async; once every thread has copied its
-// 16 values into registers, the next panel's copy is started into the same buffer
-// and runs under this panel's transform and stores.  vec2: the window rows are
-// 16-byte aligned pairs of channels, copied two channels at a time.
+// staged in shared memory ([nin][CP], followed by one all-zero row that FFT positions
+// outside the window read) by cp.async; once every thread has copied its 16 values
+// into registers, the next panel's copy is started into the same buffer and runs
+// under this panel's transform.  The transform's bins are then written back to the
+// exchange buffer in natural order and copied out row by row (copy_out).
+// in_vec2 / out_vec2: the window rows (output rows) are 16-byte aligned pairs of
+// channels, moved two channels at a time.
 template <int LOGN, int CP, bool INV>
 __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT, 2) panel_fft_pipe_kernel(const PanelArgs a, int npanel,
-                                                                                    int vec2) {
+                                                                                    int in_vec2, int out_vec2) {
   using S = RegShape<LOGN, CP>;
-  constexpr int n = S::n, T = S::T, NT = S::NT;
+  constexpr int n = S::n, T = S::T, NT = S::NT, R3 = n / 256;
   extern __shared__ float2 sm[];
   float2* xbuf = sm;                   // exchange buffer [XROWS][CP]
-  float2* ibuf = sm + S::XROWS * CP;   // staging [nin][CP]
+  float2* ibuf = sm + S::XROWS * CP;   // staging [nin + 1][CP]
   const int tid = threadIdx.x;
   const int q = tid % CP, j0 = tid / CP;
   const int nlo = (a.lo_total + a.CLO - 1) / a.CLO;
   const int nchunk = ((a.hi_total + a.CHI - 1) / a.CHI) * nlo;
   const float inv_nlo = 1.f / (float)nlo;
   const int qhi = q / a.CLO, qlo = q % a.CLO;
-  // copy roles: channel pair cq2, cq2 + 1 (vec2) or channel q, of rows crow + k RSTEP
+  // copy roles: channel pair cq2, cq2 + 1 (in_vec2) or channel q, of rows crow + k RSTEP
   const int cq2 = 2 * (tid % (CP / 2));
   const int cq2hi = cq2 / a.CLO, cq2lo = cq2 % a.CLO;
+  if (tid < CP) ibuf[a.nin * CP + tid] = make_float2(0.f, 0.f);  // the zero row
 
   auto issue = [&](int b, int chunk) {
     const int hc = small_div(chunk, nlo, inv_nlo);
@@ -400,7 +464,7 @@ __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT, 2) panel_fft_pipe_kern
         const float2* src = ok ? inb + (long long)i * a.in_si + (long long)hi * a.in_shi + (long long)lo * a.in_slo : a.in;
         cp_async8(ibuf + i * CP + qq, src, ok);
       }
-    } else if (vec2) {
+    } else if (in_vec2) {
       constexpr int RSTEP = NT / (CP / 2);
       const int hi = hi0 + cq2hi, lo = lo0 + cq2lo;
       const bool ok = hi < a.hi_total && lo < a.lo_total;
@@ -428,18 +492,13 @@ __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT, 2) panel_fft_pipe_kern
   cp_async_commit();
   for (; p < npanel; p += gridDim.x) {
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-    __syncthreads();  // the staged window is complete, and the previous panel's exchanges are done
+    __syncthreads();  // the staged window is complete, and the previous panel's copy-out is done
     const int hc = small_div(cc, nlo, inv_nlo);
-    const int hi = hc * a.CHI + qhi;
-    const int lo = (cc - hc * nlo) * a.CLO + qlo;
-    const bool valid = hi < a.hi_total && lo < a.lo_total;
+    const int hi0 = hc * a.CHI, lo0 = (cc - hc * nlo) * a.CLO;
     const int b = cb;
     float2 v[16];
 #pragma unroll
-    for (int t = 0; t < 16; ++t) {
-      const int i = (lpos + t * T) & (n - 1);
-      v[t] = i < a.nin ? rq[i * CP] : make_float2(0.f, 0.f);
-    }
+    for (int t = 0; t < 16; ++t) v[t] = rq[min((lpos + t * T) & (n - 1), a.nin) * CP];
     if (a.mul_i) {
 #pragma unroll
       for (int t = 0; t < 16; ++t) {
@@ -461,8 +520,16 @@ __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT, 2) panel_fft_pipe_kern
     if (p + (int)gridDim.x < npanel) issue(cb, cc);
     cp_async_commit();
     fft_core<LOGN, CP, INV>(v, xbuf, j0, q, a.twiddle);
-    if (valid)
-      store_bins<LOGN>(a, v, j0, (long long)b * a.out_sb + (long long)hi * a.out_shi + (long long)lo * a.out_slo, b);
+    __syncthreads();  // every thread has read its last-stage inputs
+    {
+      float2* w = xbuf + j0 * CP + q;
+#pragma unroll
+      for (int m = 0; m < 16 / R3; ++m)
+#pragma unroll
+        for (int t = 0; t < R3; ++t) w[(m * T + 256 * t) * CP] = v[m * R3 + t];
+    }
+    __syncthreads();
+    copy_out<LOGN, CP, NT>(a, xbuf, b, hi0, lo0, out_vec2);
   }
 }
 
@@ -496,7 +563,7 @@ cudaError_t launch_reg(const PanelArgs& a, cudaStream_t s) {
   const long long npanel = (long long)nhi * nlo * a.batch;
   const int sms = sm_count();
   const size_t xbytes = sizeof(float2) * (size_t)S::XROWS * CP;
-  const size_t smem_pipe = xbytes + sizeof(float2) * (size_t)a.nin * CP;
+  const size_t smem_pipe = xbytes + sizeof(float2) * (size_t)(a.nin + 1) * CP;
   if (npanel >= 4LL * sms && smem_pipe <= 220 * 1024 && (long long)nhi * nlo < (1LL << 22)) {  // persistent form
     auto kern = panel_fft_pipe_kernel<LOGN, CP, INV>;
     static bool configured = false;
@@ -514,11 +581,15 @@ cudaError_t launch_reg(const PanelArgs& a, cudaStream_t s) {
       occ = std::max(nb, 1);
       occ_smem = smem_pipe;
     }
-    const int vec2 = !a.load_i_fastest && a.in_slo == 1 && a.CLO % 2 == 0 && a.lo_total % 2 == 0 &&
-                     reinterpret_cast<uintptr_t>(a.in) % 16 == 0 && a.in_sb % 2 == 0 && a.in_si % 2 == 0 &&
-                     a.in_shi % 2 == 0;
+    const int in_vec2 = !a.load_i_fastest && a.in_slo == 1 && a.CLO % 2 == 0 && a.lo_total % 2 == 0 &&
+                        reinterpret_cast<uintptr_t>(a.in) % 16 == 0 && a.in_sb % 2 == 0 && a.in_si % 2 == 0 &&
+                        a.in_shi % 2 == 0;
+    const void* optr = a.out_mag ? static_cast<const void*>(a.out_mag) : static_cast<const void*>(a.out);
+    const int out_vec2 = a.out_slo == 1 && a.CLO % 2 == 0 && a.lo_total % 2 == 0 &&
+                         reinterpret_cast<uintptr_t>(optr) % (a.out_mag ? 8 : 16) == 0 && a.out_sb % 2 == 0 &&
+                         a.out_si % 2 == 0 && a.out_shi % 2 == 0;
     const int grid = (int)std::min<long long>(npanel, (long long)sms * occ);
-    kern<<<grid, S::NT, smem_pipe, s>>>(a, (int)npanel, vec2);
+    kern<<<grid, S::NT, smem_pipe, s>>>(a, (int)npanel, in_vec2, out_vec2);
     return cudaGetLastError();
   }
   static bool configured = false;
