@@ -31,10 +31,14 @@ __global__ void points_prepare(const PointsArgs a, int2* __restrict__ i0_out, fl
   const double ux = dx * a.inv_fine_pitch, uy = dy * a.inv_fine_pitch;
   const double hw = 0.5 * a.width;
   const int ix = (int)ceil(ux - hw), iy = (int)ceil(uy - hw);
+  // tap t sits at z = (i0 + t - u) / (w / 2): the offset i0 - u in (-w/2 - 1, -w/2] is exact
+  // enough in fp32 once taken in fp64, so the taps need no fp64 division
+  const float fx = (float)((double)ix - ux), fy = (float)((double)iy - uy);
+  const float inv_hw = 2.f / (float)a.width;
   float* w = w_out + (size_t)l * 2 * a.width;
   for (int t = 0; t < a.width; ++t) {
-    const float zx = (float)(((double)(ix + t) - ux) / hw);
-    const float zy = (float)(((double)(iy + t) - uy) / hw);
+    const float zx = (fx + (float)t) * inv_hw;
+    const float zy = (fy + (float)t) * inv_hw;
     const float px = (fabsf(zx) < 1.f) ? expf(a.beta * (sqrtf(1.f - zx * zx) - 1.f)) : 0.f;
     const float py = (fabsf(zy) < 1.f) ? expf(a.beta * (sqrtf(1.f - zy * zy) - 1.f)) : 0.f;
     w[t] = ok ? px : 0.f;
@@ -51,25 +55,55 @@ __global__ void points_prepare(const PointsArgs a, int2* __restrict__ i0_out, fl
 }
 
 // Exclusive scan of the bin counts in one CTA: bin_start[b] = first sorted slot of bin b.
-__global__ void points_scan(const int* __restrict__ counts, int nbins, int* __restrict__ bin_start, int L) {
-  __shared__ int part[1024];
-  const int tid = threadIdx.x;
-  const int per = (nbins + 1023) / 1024;
-  const int s = tid * per, e = min(nbins, s + per);
-  int sum = 0;
-  for (int i = s; i < e; ++i) sum += counts[i];
-  part[tid] = sum;
-  __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    const int v = (tid >= off) ? part[tid - off] : 0;
+// The counts are staged in shared memory with coalesced loads (kScanChunk at a time);
+// each thread scans a contiguous run, the runs' totals are scanned with warp shuffles.
+constexpr int kScanThreads = 1024, kScanChunk = 8192;
+__global__ void __launch_bounds__(kScanThreads) points_scan(const int* __restrict__ counts, int nbins,
+                                                           int* __restrict__ bin_start, int L) {
+  __shared__ int buf[kScanChunk];
+  __shared__ int warp_sum[kScanThreads / 32];
+  __shared__ int carry;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int per = kScanChunk / kScanThreads;
+  if (tid == 0) carry = 0;
+  for (int c0 = 0; c0 < nbins; c0 += kScanChunk) {
+    const int cn = min(kScanChunk, nbins - c0);
+    for (int i = tid; i < kScanChunk; i += kScanThreads) buf[i] = i < cn ? counts[c0 + i] : 0;
     __syncthreads();
-    part[tid] += v;
+    int run = 0;
+#pragma unroll
+    for (int k = 0; k < per; ++k) run += buf[tid * per + k];
+    int incl = run;  // inclusive scan of the runs within the warp
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += v;
+    }
+    if (lane == 31) warp_sum[warp] = incl;
     __syncthreads();
-  }
-  int run = tid ? part[tid - 1] : 0;
-  for (int i = s; i < e; ++i) {
-    bin_start[i] = run;
-    run += counts[i];
+    if (warp == 0) {
+      int ws = warp_sum[lane];
+      int wincl = ws;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, wincl, off);
+        if (lane >= off) wincl += v;
+      }
+      warp_sum[lane] = wincl - ws;  // exclusive
+    }
+    __syncthreads();
+    int pos = carry + warp_sum[warp] + incl - run;
+    const int total = carry + warp_sum[kScanThreads / 32 - 1] + __shfl_sync(0xffffffffu, incl, 31);
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+      const int v = buf[tid * per + k];
+      buf[tid * per + k] = pos;
+      pos += v;
+    }
+    __syncthreads();
+    for (int i = tid; i < cn; i += kScanThreads) bin_start[c0 + i] = buf[i];
+    if (tid == kScanThreads - 1) carry = total;
+    __syncthreads();
   }
   if (tid == 0) bin_start[nbins] = L;
 }
@@ -83,11 +117,29 @@ __global__ void points_scatter(const int* __restrict__ bin_of, const int* __rest
 }
 
 // Order each bin by sample index (insertion sort; bins hold a handful of samples), so
-// the spread's summation order does not depend on the scatter's arrival order.
+// the spread's summation order does not depend on the scatter's arrival order.  Bins of
+// up to kSortLocal samples are sorted in a thread-local array, larger ones in place.
+constexpr int kSortLocal = 32;
 __global__ void points_sort_bins(const int* __restrict__ bin_start, int nbins, int* __restrict__ sorted_l) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nbins) return;
   const int s = bin_start[b], e = bin_start[b + 1];
+  if (e - s <= kSortLocal) {
+    int v[kSortLocal];
+    const int k = e - s;
+    for (int i = 0; i < k; ++i) v[i] = sorted_l[s + i];
+    for (int i = 1; i < k; ++i) {
+      const int x = v[i];
+      int j = i - 1;
+      while (j >= 0 && v[j] > x) {
+        v[j + 1] = v[j];
+        --j;
+      }
+      v[j + 1] = x;
+    }
+    for (int i = 0; i < k; ++i) sorted_l[s + i] = v[i];
+    return;
+  }
   for (int i = s + 1; i < e; ++i) {
     const int v = sorted_l[i];
     int j = i - 1;
@@ -125,7 +177,7 @@ cudaError_t launch_points(const PointsArgs& a, int* bin_of, int2* i0_orig, float
   if (a.L <= 0) return cudaMemsetAsync(bin_start, 0, sizeof(int) * (nbins + 1), s);
   const int blocks = (a.L + 255) / 256;
   points_prepare<<<blocks, 256, 0, s>>>(a, i0_orig, w_orig, bin_of, frac_orig, counts);
-  points_scan<<<1, 1024, 0, s>>>(counts, nbins, bin_start, a.L);
+  points_scan<<<1, kScanThreads, 0, s>>>(counts, nbins, bin_start, a.L);
   points_scatter<<<blocks, 256, 0, s>>>(bin_of, bin_start, a.L, counts + nbins, sorted_l);
   points_sort_bins<<<(nbins + 255) / 256, 256, 0, s>>>(bin_start, nbins, sorted_l);
   points_gather<<<blocks, 256, 0, s>>>(sorted_l, a.L, a.width, i0_orig, w_orig, frac_orig, i0_sorted, w_sorted,

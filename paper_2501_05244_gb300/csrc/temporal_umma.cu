@@ -11,10 +11,10 @@
 // One CTA per SM walks 128-row tiles of H (tile blockIdx.x + j gridDim.x).  Warp roles:
 //   0-3  epilogue: tcgen05.ld of the 128 x 2F accumulator (one row per thread), fp32 stores;
 //        two accumulators in tensor memory, so a tile's epilogue overlaps the next tile's MMAs
-//   4-7  H producers: global loads one K-block ahead, fp16 head/tail split, stores into the
-//        128-byte-swizzled K-major operand layout
-//   8    B producer (one thread): TMA tiled copies of the 64 x 2F head and tail blocks
-//   9    MMA issuer (one thread): 4 k-steps of 16 per K-block, tcgen05.commit to the
+//   4-11 H producers: global loads three K-blocks ahead (~96 KB per SM in flight), fp16
+//        head/tail split, stores into the 128-byte-swizzled K-major operand layout
+//   12   B producer (one thread): TMA tiled copies of the 64 x 2F head and tail blocks
+//   13   MMA issuer (one thread): 4 k-steps of 16 per K-block, tcgen05.commit to the
 //        stage's "empty" barrier and, after the tile's last K-block, to the accumulator's
 //        "full" barrier
 // Stages (2) hold A_hi, A_lo (128 x 64 fp16 each) and B_hi, B_lo (2F x 64 fp16 each).
@@ -32,7 +32,7 @@ namespace nursd {
 namespace {
 
 constexpr int kBM = 128, kBK = 64, kUStages = 2;
-constexpr int kEpiWarps = 4, kCvtWarps = 4;
+constexpr int kEpiWarps = 4, kCvtWarps = 8;
 constexpr int kProducerWarp = kEpiWarps + kCvtWarps, kMmaWarp = kProducerWarp + 1;
 constexpr int kUThreads = (kMmaWarp + 1) * 32;
 constexpr long long kUSpin = 1LL << 22;
@@ -221,29 +221,30 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
   } else if (warp < kEpiWarps + kCvtWarps) {
     // ---------------------------------------------------------------- H producers
     const int cw = warp - kEpiWarps, ct = cw * 32 + lane;
-    // task q: row ct / 8 + 16 q of the tile, 16-byte chunk ct % 8 (8 consecutive K values)
+    // task q < 4: row ct / 8 + 32 q of the tile, 16-byte chunk ct % 8 (8 consecutive K values)
     const int r0 = ct >> 3, ch = ct & 7;
-    auto load = [&](float4 (&v)[16], int it) {
+    auto load = [&](float4 (&v)[8], int it) {
+      if (it >= my_iters) return;
       const int j = it / nkb, kb = it - j * nkb;
       const int m0 = ((int)blockIdx.x + j * (int)gridDim.x) * kBM;
       const float* src = H + (size_t)(m0 + r0) * T + kb * kBK + ch * 8;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const bool ok = m0 + r0 + 16 * q < L;
-        const float4* s4 = reinterpret_cast<const float4*>(src + (size_t)16 * q * T);
+      for (int q = 0; q < 4; ++q) {
+        const bool ok = m0 + r0 + 32 * q < L;
+        const float4* s4 = reinterpret_cast<const float4*>(src + (size_t)32 * q * T);
         v[2 * q] = ok ? __ldg(s4) : make_float4(0.f, 0.f, 0.f, 0.f);
         v[2 * q + 1] = ok ? __ldg(s4 + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     };
-    auto stage = [&](const float4 (&v)[16], int it) -> bool {
+    auto stage = [&](const float4 (&v)[8], int it) -> bool {
       const int st = it % kUStages, ph = (it / kUStages) & 1;
       if (!bar_wait(&ctl.empty[st], ph ^ 1, abort)) return false;
       unsigned char* ah = a_hi(st);
       unsigned char* al = a_lo(st);
       uint32_t any = 0;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int r = r0 + 16 * q;
+      for (int q = 0; q < 4; ++q) {
+        const int r = r0 + 32 * q;
         const float4 x = v[2 * q], y = v[2 * q + 1];
         uint4 h, l;
         split2(x.x, x.y, h.x, l.x);
@@ -264,14 +265,18 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
       }
       return true;
     };
-    float4 va[16], vb[16];
-    if (my_iters > 0) load(va, 0);
-    for (int it = 0; it < my_iters; it += 2) {
-      if (it + 1 < my_iters) load(vb, it + 1);
+    // three register sets in rotation: K-blocks it + 1 .. it + 3 are in flight while `it` is staged
+    float4 va[8], vb[8], vc[8];
+    load(va, 0);
+    load(vb, 1);
+    load(vc, 2);
+    for (int it = 0; it < my_iters; it += 3) {
       if (!stage(va, it)) break;
-      if (it + 1 >= my_iters) break;
-      if (it + 2 < my_iters) load(va, it + 2);
-      if (!stage(vb, it + 1)) break;
+      load(va, it + 3);
+      if (it + 1 >= my_iters || !stage(vb, it + 1)) break;
+      load(vb, it + 4);
+      if (it + 2 >= my_iters || !stage(vc, it + 2)) break;
+      load(vc, it + 5);
     }
   } else if (warp == kProducerWarp) {
     // ---------------------------------------------------------------- B producer
