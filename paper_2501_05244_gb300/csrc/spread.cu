@@ -26,12 +26,13 @@ constexpr int kCh = 32;        // channels per CTA
 constexpr int kCap = 256;      // samples staged per chunk
 
 struct SpreadSmem {
-  float2 p[kCap][kCh];  // phasor slices
-  float wx[kCap][8];    // x weights (first w used)
-  float wy[kCap][8];    // y weights
-  int ox[kCap];         // first footprint column (window index)
-  int oy[kCap];         // first footprint row
-  int l[kCap];          // sample index (row of P)
+  float2 p[kCap][kCh];   // phasor slices
+  float wx[kCap][8];     // x weights (first w used)
+  float wy[kCap][8];     // y weights
+  float wt[kCap][kTile]; // y weight of each row of the tile (0 where the footprint misses it)
+  int o[kCap];           // first footprint column relative to the tile's
+  int oy[kCap];          // first footprint row relative to the tile's
+  int l[kCap];           // sample index (row of P)
 };
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc, bool valid) {
@@ -113,8 +114,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) spread_kernel(const float2* __
 #pragma unroll
       for (int t = 0; t < 2 * KW; ++t) wv[t] = __ldg(w + t);
       sm.l[s] = l;
-      sm.ox[s] = o.x;
-      sm.oy[s] = o.y;
+      sm.o[s] = o.x - col0;
+      sm.oy[s] = o.y - ty * kTile;
 #pragma unroll
       for (int t = 0; t < KW; ++t) {
         sm.wx[s][t] = wv[t];
@@ -122,30 +123,38 @@ __global__ void __launch_bounds__(kWarps * 32, 2) spread_kernel(const float2* __
       }
     }
     __syncthreads();
-    // phase 2, one warp per sample: its 32 channels of P
-    for (int s = warp; s < cn; s += kWarps)
+    // phase 2, one warp per sample: its 32 channels of P, and its y weight for each tile row
+    for (int s = warp; s < cn; s += kWarps) {
       cp_async8(&sm.p[s][lane], live ? P + (size_t)sm.l[s] * F + f0 + lane : P, live);
+      if (lane < kTile) {
+        const int d = lane - sm.oy[s];
+        sm.wt[s][lane] = (d >= 0 && d < KW) ? sm.wy[s][d] : 0.f;
+      }
+    }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     const int c1 = c0 + cn;
-    for (int part = 0; part < 2; ++part) {
-      const int v0 = max(part ? wb0 : wa0, c0), v1 = min(part ? wb1 : wa1, c1);
-      for (int v = v0; v < v1; ++v) {
-        const int s = v - c0;
-        const int o = sm.ox[s] - col0;
-        if (o <= -KW) continue;  // a left-column sample that ends before this tile
-        const float wyv = sm.wy[s][y - sm.oy[s]];
-        float2 pv = sm.p[s][lane];
-        pv.x *= wyv;
-        pv.y *= wyv;
-        float wx[8];
-        const float4 w0 = *reinterpret_cast<const float4*>(&sm.wx[s][0]);
-        const float4 w1 = *reinterpret_cast<const float4*>(&sm.wx[s][4]);
-        wx[0] = w0.x; wx[1] = w0.y; wx[2] = w0.z; wx[3] = w0.w;
-        wx[4] = w1.x; wx[5] = w1.y; wx[6] = w1.z; wx[7] = w1.w;
-        add_sample<KW>(acc, o, pv, wx);
-      }
+    auto visit = [&](int s) {
+      const float wyv = sm.wt[s][warp];
+      float2 pv = sm.p[s][lane];
+      pv.x *= wyv;
+      pv.y *= wyv;
+      float wx[8];
+      const float4 w0 = *reinterpret_cast<const float4*>(&sm.wx[s][0]);
+      const float4 w1 = *reinterpret_cast<const float4*>(&sm.wx[s][4]);
+      wx[0] = w0.x; wx[1] = w0.y; wx[2] = w0.z; wx[3] = w0.w;
+      wx[4] = w1.x; wx[5] = w1.y; wx[6] = w1.z; wx[7] = w1.w;
+      add_sample<KW>(acc, sm.o[s], pv, wx);
+    };
+    {  // left tile column: only samples whose footprint reaches this tile
+      const int s1 = min(wa1, c1) - c0;
+      for (int s = max(wa0, c0) - c0; s < s1; ++s)
+        if (sm.o[s] > -KW) visit(s);
+    }
+    {  // this tile column
+      const int s1 = min(wb1, c1) - c0;
+      for (int s = max(wb0, c0) - c0; s < s1; ++s) visit(s);
     }
   }
   if (live) {
