@@ -533,6 +533,204 @@ __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT, 2) panel_fft_pipe_kern
   }
 }
 
+// ------------------------------------------------------------------ radix-32 form
+// For n = 512, 1024: two Stockham stages, radix 32 then R2 = n / 32.  T = n / 32 threads per
+// transform, 32 values each.  Stage 1: thread j0 < T does butterfly j0 (a 32-point DFT of
+// x[j0 + T t]) and writes x'[32 j0 + k].  Stage 2: butterflies j < 32 (32 / R2 per thread,
+// j = j0 + T m) read x'[j + 32 t], t < R2, twiddle W_n^{j t}, and give X[j + 32 k].  One
+// exchange; element e sits at row e + PADX (e >> 5) (a spare row after every 32 when a
+// half-warp spans two rows), so both exchange directions are conflict-free.
+
+constexpr float kW32C1 = 0.98078528040323044913f, kW32S1 = 0.19509032201612826785f;
+constexpr float kW32C2 = 0.92387953251128675613f, kW32S2 = 0.38268343236508977173f;
+constexpr float kW32C3 = 0.83146961230254523708f, kW32S3 = 0.55557023301960222474f;
+constexpr float kW32C4 = 0.70710678118654752440f;
+
+// a * W32^{-+m} (forward e^{-2 pi i m / 32}, inverse e^{+2 pi i m / 32}) for a constant m < 32.
+template <bool INV, int M>
+__device__ __forceinline__ float2 rot32(float2 a) {
+  constexpr int m = M & 31;
+  if (m == 0) return a;
+  if (m == 8) return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+  if (m == 16) return make_float2(-a.x, -a.y);
+  if (m == 24) return INV ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+  // cos and sin of 2 pi m / 32 from the first octant
+  constexpr int o = m & 7, q = m >> 3;
+  constexpr float c0 = o == 0 ? 1.f : o == 1 ? kW32C1 : o == 2 ? kW32C2 : o == 3 ? kW32C3 : o == 4 ? kW32C4
+                       : o == 5 ? kW32S3 : o == 6 ? kW32S2 : kW32S1;
+  constexpr float s0 = o == 0 ? 0.f : o == 1 ? kW32S1 : o == 2 ? kW32S2 : o == 3 ? kW32S3 : o == 4 ? kW32C4
+                       : o == 5 ? kW32C3 : o == 6 ? kW32C2 : kW32C1;
+  // rotate the octant angle by q quarter turns: (c, s) -> (-s, c)
+  constexpr float c = q == 0 ? c0 : q == 1 ? -s0 : q == 2 ? -c0 : s0;
+  constexpr float sn = q == 0 ? s0 : q == 1 ? c0 : q == 2 ? -s0 : -c0;
+  return cmul(a, make_float2(c, INV ? sn : -sn));
+}
+
+template <bool INV, int N1, int K2>
+__device__ __forceinline__ void rot32_at(float2* y) { y[N1 * 8 + K2] = rot32<INV, N1 * K2>(y[N1 * 8 + K2]); }
+
+// In-place 32-point DFT: out[8 k1 + k2] = sum_n x[n] W32^{n k}, via 8-point DFTs over n2 of
+// x[n1 + 4 n2], twiddles W32^{n1 k2}, and 4-point DFTs over n1.
+template <bool INV>
+__device__ __forceinline__ void dft32(float2* v) {
+  float2 y[32];
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) {
+    float2 t[8];
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) t[n2] = v[n1 + 4 * n2];
+    dft8<INV>(t);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) y[n1 * 8 + k2] = t[k2];
+  }
+  rot32_at<INV, 1, 1>(y); rot32_at<INV, 1, 2>(y); rot32_at<INV, 1, 3>(y); rot32_at<INV, 1, 4>(y);
+  rot32_at<INV, 1, 5>(y); rot32_at<INV, 1, 6>(y); rot32_at<INV, 1, 7>(y);
+  rot32_at<INV, 2, 1>(y); rot32_at<INV, 2, 2>(y); rot32_at<INV, 2, 3>(y); rot32_at<INV, 2, 4>(y);
+  rot32_at<INV, 2, 5>(y); rot32_at<INV, 2, 6>(y); rot32_at<INV, 2, 7>(y);
+  rot32_at<INV, 3, 1>(y); rot32_at<INV, 3, 2>(y); rot32_at<INV, 3, 3>(y); rot32_at<INV, 3, 4>(y);
+  rot32_at<INV, 3, 5>(y); rot32_at<INV, 3, 6>(y); rot32_at<INV, 3, 7>(y);
+#pragma unroll
+  for (int k2 = 0; k2 < 8; ++k2) {
+    float2 a = y[k2], b = y[8 + k2], c = y[16 + k2], d = y[24 + k2];
+    dft4<INV>(a, b, c, d);
+    v[k2] = a;
+    v[8 + k2] = b;
+    v[16 + k2] = c;
+    v[24 + k2] = d;
+  }
+}
+
+template <int LOGN, int CP>
+struct R32Shape {
+  static constexpr int n = 1 << LOGN;
+  static constexpr int T = n / 32;        // threads per transform
+  static constexpr int R2 = n / 32;       // radix of the second stage
+  static constexpr int NT = T * CP;
+  static constexpr int PADX = (CP < 16) ? 1 : 0;
+  static constexpr int XROWS = n + PADX * (n / 32);
+};
+
+// Persistent radix-32 form: same panels, staging, zero row and copy-out as
+// panel_fft_pipe_kernel; four CTA barriers per panel.
+template <int LOGN, int CP, bool INV>
+__global__ void __launch_bounds__(R32Shape<LOGN, CP>::NT, R32Shape<LOGN, CP>::NT >= 256 ? 2 : 3) panel_fft32_kernel(const PanelArgs a, int npanel,
+                                                                             int in_vec2, int out_vec2) {
+  using S = R32Shape<LOGN, CP>;
+  constexpr int n = S::n, T = S::T, R2 = S::R2, NT = S::NT, PADX = S::PADX;
+  extern __shared__ float2 sm[];
+  float2* xbuf = sm;                   // exchange buffer [XROWS][CP], then the bins [n][CP]
+  float2* ibuf = sm + S::XROWS * CP;   // staging [nin + 1][CP]
+  const int tid = threadIdx.x;
+  const int q = tid % CP, j0 = tid / CP;
+  const int nlo = (a.lo_total + a.CLO - 1) / a.CLO;
+  const int nchunk = ((a.hi_total + a.CHI - 1) / a.CHI) * nlo;
+  const float inv_nlo = 1.f / (float)nlo;
+  const int qhi = q / a.CLO, qlo = q % a.CLO;
+  const int cq2 = 2 * (tid % (CP / 2));
+  const int cq2hi = cq2 / a.CLO, cq2lo = cq2 % a.CLO;
+  if (tid < CP) ibuf[a.nin * CP + tid] = make_float2(0.f, 0.f);  // the zero row
+
+  auto issue = [&](int b, int chunk) {
+    const int hc = small_div(chunk, nlo, inv_nlo);
+    const int hi0 = hc * a.CHI, lo0 = (chunk - hc * nlo) * a.CLO;
+    const float2* inb = a.in + (long long)b * a.in_sb;
+    if (a.load_i_fastest) {
+      for (int idx = tid; idx < a.nin * CP; idx += NT) {
+        const int i = idx % a.nin, qq = idx / a.nin;
+        const int hi = hi0 + qq / a.CLO, lo = lo0 + qq % a.CLO;
+        const bool ok = hi < a.hi_total && lo < a.lo_total;
+        const float2* src = ok ? inb + (long long)i * a.in_si + (long long)hi * a.in_shi + (long long)lo * a.in_slo : a.in;
+        cp_async8(ibuf + i * CP + qq, src, ok);
+      }
+    } else if (in_vec2) {
+      constexpr int RSTEP = NT / (CP / 2);
+      const int hi = hi0 + cq2hi, lo = lo0 + cq2lo;
+      const bool ok = hi < a.hi_total && lo < a.lo_total;
+      int i = tid / (CP / 2);
+      const float2* src = inb + (long long)hi * a.in_shi + lo + (long long)i * a.in_si;
+      const long long step = (long long)RSTEP * a.in_si;
+      for (; i < a.nin; i += RSTEP, src += step) cp_async16(ibuf + i * CP + cq2, ok ? src : a.in, ok);
+    } else {
+      constexpr int RSTEP = NT / CP;
+      const int hi = hi0 + qhi, lo = lo0 + qlo;
+      const bool ok = hi < a.hi_total && lo < a.lo_total;
+      int i = tid / CP;
+      const float2* src = inb + (long long)hi * a.in_shi + (long long)lo * a.in_slo + (long long)i * a.in_si;
+      const long long step = (long long)RSTEP * a.in_si;
+      for (; i < a.nin; i += RSTEP, src += step) cp_async8(ibuf + i * CP + q, ok ? src : a.in, ok);
+    }
+  };
+
+  const int lpos = (j0 - a.in_off) & (n - 1);  // input index at FFT position j0
+  const float2* rq = ibuf + q;
+  const float2* __restrict__ tw2 = a.twiddle + tw32_offset(LOGN);
+  const int step_b = gridDim.x / nchunk, step_c = gridDim.x % nchunk;
+  int p = blockIdx.x;
+  int cb = p / nchunk, cc = p % nchunk;
+  if (p < npanel) issue(cb, cc);
+  cp_async_commit();
+  for (; p < npanel; p += gridDim.x) {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();  // the staged window is complete, and the previous panel's copy-out is done
+    const int hc = small_div(cc, nlo, inv_nlo);
+    const int hi0 = hc * a.CHI, lo0 = (cc - hc * nlo) * a.CLO;
+    const int b = cb;
+    float2 v[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) v[t] = rq[min((lpos + t * T) & (n - 1), a.nin) * CP];
+    if (a.mul_i) {
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        const int i = (lpos + t * T) & (n - 1);
+        if (i < a.nin) {
+          const float m = __ldg(a.mul_i + i);
+          v[t].x *= m;
+          v[t].y *= m;
+        }
+      }
+    }
+    // stage 1: outputs 32 j0 + k at rows 32 j0 + k + PADX j0
+    dft32<INV>(v);
+    {
+      float2* w = xbuf + (32 + PADX) * j0 * CP + q;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) w[k * CP] = v[k];
+    }
+    __syncthreads();  // stage-1 outputs are in place, and every thread has read the staged window
+    cb += step_b;
+    cc += step_c;
+    if (cc >= nchunk) {
+      cc -= nchunk;
+      ++cb;
+    }
+    if (p + (int)gridDim.x < npanel) issue(cb, cc);
+    cp_async_commit();
+    // stage 2: butterflies j = j0 + T m read rows j + (32 + PADX) t
+#pragma unroll
+    for (int m = 0; m < 32 / R2; ++m) {
+      const int j = j0 + T * m;
+      const float2* r = xbuf + j * CP + q;
+#pragma unroll
+      for (int t = 0; t < R2; ++t) v[m * R2 + t] = r[t * (32 + PADX) * CP];
+      twiddle_row<R2, INV>(v + m * R2, tw2 + j * R2);
+      if (R2 == 32)
+        dft32<INV>(v + m * R2);
+      else
+        dft16<INV>(v + m * R2);
+    }
+    __syncthreads();  // every thread has read its stage-2 inputs
+    {  // bins j + 32 k in natural order
+      float2* w = xbuf + j0 * CP + q;
+#pragma unroll
+      for (int m = 0; m < 32 / R2; ++m)
+#pragma unroll
+        for (int k = 0; k < R2; ++k) w[(T * m + 32 * k) * CP] = v[m * R2 + k];
+    }
+    __syncthreads();
+    copy_out<LOGN, CP, NT>(a, xbuf, b, hi0, lo0, out_vec2);
+  }
+}
+
 template <class K>
 cudaError_t configure(K kernel, size_t smem) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -564,6 +762,38 @@ cudaError_t launch_reg(const PanelArgs& a, cudaStream_t s) {
   const int sms = sm_count();
   const size_t xbytes = sizeof(float2) * (size_t)S::XROWS * CP;
   const size_t smem_pipe = xbytes + sizeof(float2) * (size_t)(a.nin + 1) * CP;
+  const void* optr = a.out_mag ? static_cast<const void*>(a.out_mag) : static_cast<const void*>(a.out);
+  const int in_vec2 = !a.load_i_fastest && a.in_slo == 1 && a.CLO % 2 == 0 && a.lo_total % 2 == 0 &&
+                      reinterpret_cast<uintptr_t>(a.in) % 16 == 0 && a.in_sb % 2 == 0 && a.in_si % 2 == 0 &&
+                      a.in_shi % 2 == 0;
+  const int out_vec2 = a.out_slo == 1 && a.CLO % 2 == 0 && a.lo_total % 2 == 0 &&
+                       reinterpret_cast<uintptr_t>(optr) % (a.out_mag ? 8 : 16) == 0 && a.out_sb % 2 == 0 &&
+                       a.out_si % 2 == 0 && a.out_shi % 2 == 0;
+  if constexpr (LOGN == 9 || LOGN == 10) {  // radix-32 persistent form
+    using R = R32Shape<LOGN, CP>;
+    const size_t smem32 = sizeof(float2) * ((size_t)R::XROWS * CP + (size_t)(a.nin + 1) * CP);
+    if (npanel >= 4LL * sms && smem32 <= 220 * 1024 && (long long)nhi * nlo < (1LL << 22)) {
+      auto kern = panel_fft32_kernel<LOGN, CP, INV>;
+      static bool configured32 = false;
+      static size_t occ_smem32 = 0;
+      static int occ32 = 1;
+      if (!configured32) {
+        cudaError_t e = configure(kern, 220 * 1024);
+        if (e != cudaSuccess) return e;
+        configured32 = true;
+      }
+      if (occ_smem32 != smem32) {
+        int nb = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, R::NT, smem32);
+        if (e != cudaSuccess) return e;
+        occ32 = std::max(nb, 1);
+        occ_smem32 = smem32;
+      }
+      const int grid = (int)std::min<long long>(npanel, (long long)sms * occ32);
+      kern<<<grid, R::NT, smem32, s>>>(a, (int)npanel, in_vec2, out_vec2);
+      return cudaGetLastError();
+    }
+  }
   if (npanel >= 4LL * sms && smem_pipe <= 220 * 1024 && (long long)nhi * nlo < (1LL << 22)) {  // persistent form
     auto kern = panel_fft_pipe_kernel<LOGN, CP, INV>;
     static bool configured = false;
@@ -581,13 +811,6 @@ cudaError_t launch_reg(const PanelArgs& a, cudaStream_t s) {
       occ = std::max(nb, 1);
       occ_smem = smem_pipe;
     }
-    const int in_vec2 = !a.load_i_fastest && a.in_slo == 1 && a.CLO % 2 == 0 && a.lo_total % 2 == 0 &&
-                        reinterpret_cast<uintptr_t>(a.in) % 16 == 0 && a.in_sb % 2 == 0 && a.in_si % 2 == 0 &&
-                        a.in_shi % 2 == 0;
-    const void* optr = a.out_mag ? static_cast<const void*>(a.out_mag) : static_cast<const void*>(a.out);
-    const int out_vec2 = a.out_slo == 1 && a.CLO % 2 == 0 && a.lo_total % 2 == 0 &&
-                         reinterpret_cast<uintptr_t>(optr) % (a.out_mag ? 8 : 16) == 0 && a.out_sb % 2 == 0 &&
-                         a.out_si % 2 == 0 && a.out_shi % 2 == 0;
     const int grid = (int)std::min<long long>(npanel, (long long)sms * occ);
     kern<<<grid, S::NT, smem_pipe, s>>>(a, (int)npanel, in_vec2, out_vec2);
     return cudaGetLastError();
@@ -622,12 +845,12 @@ cudaError_t launch_bluestein_reg(const PanelArgs& a, const float2* cpre, const f
 
 }  // namespace
 
-// Panel widths of the register kernels: 512 threads per CTA.
-int panel_width_reg(int logn) { return logn == 9 ? 16 : (logn == 10 ? 8 : 4); }
+// Panel widths (channels per CTA) of the register kernels.
+int panel_width_reg(int logn) { return logn == 11 ? 4 : 8; }
 
 cudaError_t launch_panel_fft_reg(int logn, bool inverse, const PanelArgs& a, cudaStream_t s) {
   switch (logn) {
-    case 9: return inverse ? launch_reg<9, 16, true>(a, s) : launch_reg<9, 16, false>(a, s);
+    case 9: return inverse ? launch_reg<9, 8, true>(a, s) : launch_reg<9, 8, false>(a, s);
     case 10: return inverse ? launch_reg<10, 8, true>(a, s) : launch_reg<10, 8, false>(a, s);
     case 11: return inverse ? launch_reg<11, 4, true>(a, s) : launch_reg<11, 4, false>(a, s);
     default: return cudaErrorInvalidValue;
@@ -637,7 +860,7 @@ cudaError_t launch_panel_fft_reg(int logn, bool inverse, const PanelArgs& a, cud
 cudaError_t launch_panel_bluestein_reg(int logn, const PanelArgs& a, const float2* cpre, const float2* bhat,
                                        const float2* cpost, cudaStream_t s) {
   switch (logn) {
-    case 9: return launch_bluestein_reg<9, 16>(a, cpre, bhat, cpost, s);
+    case 9: return launch_bluestein_reg<9, 8>(a, cpre, bhat, cpost, s);
     case 10: return launch_bluestein_reg<10, 8>(a, cpre, bhat, cpost, s);
     case 11: return launch_bluestein_reg<11, 4>(a, cpre, bhat, cpost, s);
     default: return cudaErrorInvalidValue;

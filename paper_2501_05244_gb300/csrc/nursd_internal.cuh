@@ -28,11 +28,15 @@ constexpr int kMaxBatch = 256;     // reconstructions per batched call
 //   [0, 2^12)                   e^{-2 pi i q / 2^12}
 //   kTw2Offset + 16 k + t       W_256^{k t}            (k, t < 16; the radix-16 x 16 middle stage)
 //   tw3_offset(lg) + R j + t    W_{2^lg}^{j t}         (j < 256, t < R = 2^lg / 256; the last stage)
+//   tw32_offset(lg) + R j + t   W_{2^lg}^{j t}         (j < 32, t < R = 2^lg / 32; the second stage of
+//                                                       the radix-32 form, lg = 9, 10)
 // so that a thread reads its whole row of twiddles at one base address.
 constexpr int kTw2Offset = 1 << kTwiddleLog;
 constexpr int kTw3Offset = kTw2Offset + 256;
 __host__ __device__ constexpr int tw3_offset(int lg) { return kTw3Offset + (lg == 9 ? 0 : (lg == 10 ? 512 : 1536)); }
-constexpr int kTwiddleEntries = kTw3Offset + 512 + 1024 + 2048;
+constexpr int kTw32Offset = kTw3Offset + 512 + 1024 + 2048;
+__host__ __device__ constexpr int tw32_offset(int lg) { return kTw32Offset + (lg == 9 ? 0 : 512); }
+constexpr int kTwiddleEntries = kTw32Offset + 512 + 1024;
 // Entry e of the table is exp(-2 pi i num / 2^lg).
 __host__ __device__ inline void twiddle_exponent(int e, int* num, int* lg) {
   if (e < kTw2Offset) {
@@ -42,9 +46,14 @@ __host__ __device__ inline void twiddle_exponent(int e, int* num, int* lg) {
     const int r = e - kTw2Offset;
     *num = (r >> 4) * (r & 15);
     *lg = 8;
-  } else {
+  } else if (e < kTw32Offset) {
     const int l = e < tw3_offset(10) ? 9 : (e < tw3_offset(11) ? 10 : 11);
     const int r = e - tw3_offset(l), R = 1 << (l - 8);
+    *num = (r / R) * (r % R);
+    *lg = l;
+  } else {
+    const int l = e < tw32_offset(10) ? 9 : 10;
+    const int r = e - tw32_offset(l), R = 1 << (l - 5);
     *num = (r / R) * (r % R);
     *lg = l;
   }
