@@ -370,12 +370,27 @@ __device__ __forceinline__ int small_div(int x, int d, float inv) {
 // vec2) and every (NT / channels)-th row, so consecutive threads store consecutive
 // addresses along the contiguous channel axis.
 template <int LOGN, int CP, int NT>
-__device__ __forceinline__ void copy_out(const PanelArgs& a, const float2* xbuf, int b, int hi0, int lo0,
-                                         int vec2) {
+// floor(x / d) for 0 <= x < 2^22 and d >= 1, with inv = 1.f / d: the rounded float
+// quotient is within 1 of the exact one, and one correction step makes it exact.
+__device__ __forceinline__ int small_div(int x, int d, float inv) {
+  int qt = __float2int_rz(__int2float_rz(x) * inv);
+  const int r = x - qt * d;
+  qt += (r >= d) - (r < 0);
+  return qt;
+}
+
+// Writes the kept bins of the panel held in xbuf as [bin][CP] (dense) to global memory:
+// output o = (bin - out_off) mod n for o < nout, scaled by scale * mul_b[b] * mul_o[o]
+// (or as magnitudes).  Threads take fixed channels (pairs of adjacent channels when
+// vec2) and every (NT / channels)-th row, so consecutive threads store consecutive
+// addresses along the contiguous channel axis.
+template <int LOGN, int CP, int NT>
+__device__ __forceinline__ void copy_out(const PanelArgs& a, const float2* xbuf, const float* mo, int b, int hi0,
+                                         int lo0, int vec2) {
   constexpr int n = 1 << LOGN;
   const int tid = threadIdx.x;
   const float sb = a.scale * (a.mul_b ? __ldg(a.mul_b + b) : 1.f);
-  const bool scaled = a.mul_o != nullptr || sb != 1.f;
+  const bool scaled = a.mul_o != nullptr || sb != 1.f;  // mo: shared-memory copy of mul_o[0..nout)
   const long long obase = (long long)b * a.out_sb;
   if (vec2) {  // out_slo == 1, channel pairs (qq, qq + 1) share hi and are 16-byte aligned
     constexpr int CP2 = CP / 2, RSTEP = NT / CP2;
@@ -451,6 +466,9 @@ __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT, 2) panel_fft_pipe_kern
   const int cq2 = 2 * (tid % (CP / 2));
   const int cq2hi = cq2 / a.CLO, cq2lo = cq2 % a.CLO;
   if (tid < CP) ibuf[a.nin * CP + tid] = make_float2(0.f, 0.f);  // the zero row
+  float* mo = reinterpret_cast<float*>(ibuf + (a.nin + 1) * CP);  // mul_o[0..nout), if any
+  if (a.mul_o)
+    for (int o = tid; o < a.nout; o += NT) mo[o] = __ldg(a.mul_o + o);
 
   auto issue = [&](int b, int chunk) {
     const int hc = small_div(chunk, nlo, inv_nlo);
@@ -529,7 +547,7 @@ __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT, 2) panel_fft_pipe_kern
         for (int t = 0; t < R3; ++t) w[(m * T + 256 * t) * CP] = v[m * R3 + t];
     }
     __syncthreads();
-    copy_out<LOGN, CP, NT>(a, xbuf, b, hi0, lo0, out_vec2);
+    copy_out<LOGN, CP, NT>(a, xbuf, mo, b, hi0, lo0, out_vec2);
   }
 }
 
@@ -629,6 +647,9 @@ __global__ void __launch_bounds__(R32Shape<LOGN, CP>::NT, R32Shape<LOGN, CP>::NT
   const int cq2 = 2 * (tid % (CP / 2));
   const int cq2hi = cq2 / a.CLO, cq2lo = cq2 % a.CLO;
   if (tid < CP) ibuf[a.nin * CP + tid] = make_float2(0.f, 0.f);  // the zero row
+  float* mo = reinterpret_cast<float*>(ibuf + (a.nin + 1) * CP);  // mul_o[0..nout), if any
+  if (a.mul_o)
+    for (int o = tid; o < a.nout; o += NT) mo[o] = __ldg(a.mul_o + o);
 
   auto issue = [&](int b, int chunk) {
     const int hc = small_div(chunk, nlo, inv_nlo);
@@ -727,7 +748,7 @@ __global__ void __launch_bounds__(R32Shape<LOGN, CP>::NT, R32Shape<LOGN, CP>::NT
         for (int k = 0; k < R2; ++k) w[(T * m + 32 * k) * CP] = v[m * R2 + k];
     }
     __syncthreads();
-    copy_out<LOGN, CP, NT>(a, xbuf, b, hi0, lo0, out_vec2);
+    copy_out<LOGN, CP, NT>(a, xbuf, mo, b, hi0, lo0, out_vec2);
   }
 }
 
@@ -761,7 +782,8 @@ cudaError_t launch_reg(const PanelArgs& a, cudaStream_t s) {
   const long long npanel = (long long)nhi * nlo * a.batch;
   const int sms = sm_count();
   const size_t xbytes = sizeof(float2) * (size_t)S::XROWS * CP;
-  const size_t smem_pipe = xbytes + sizeof(float2) * (size_t)(a.nin + 1) * CP;
+  const size_t mo_bytes = a.mul_o ? sizeof(float) * (size_t)a.nout : 0;  // shared copy of mul_o
+  const size_t smem_pipe = xbytes + sizeof(float2) * (size_t)(a.nin + 1) * CP + mo_bytes;
   const void* optr = a.out_mag ? static_cast<const void*>(a.out_mag) : static_cast<const void*>(a.out);
   const int in_vec2 = !a.load_i_fastest && a.in_slo == 1 && a.CLO % 2 == 0 && a.lo_total % 2 == 0 &&
                       reinterpret_cast<uintptr_t>(a.in) % 16 == 0 && a.in_sb % 2 == 0 && a.in_si % 2 == 0 &&
@@ -771,7 +793,7 @@ cudaError_t launch_reg(const PanelArgs& a, cudaStream_t s) {
                        a.out_si % 2 == 0 && a.out_shi % 2 == 0;
   if constexpr (LOGN == 9 || LOGN == 10) {  // radix-32 persistent form
     using R = R32Shape<LOGN, CP>;
-    const size_t smem32 = sizeof(float2) * ((size_t)R::XROWS * CP + (size_t)(a.nin + 1) * CP);
+    const size_t smem32 = sizeof(float2) * ((size_t)R::XROWS * CP + (size_t)(a.nin + 1) * CP) + mo_bytes;
     if (npanel >= 4LL * sms && smem32 <= 220 * 1024 && (long long)nhi * nlo < (1LL << 22)) {
       auto kern = panel_fft32_kernel<LOGN, CP, INV>;
       static bool configured32 = false;
