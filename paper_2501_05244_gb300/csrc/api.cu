@@ -84,6 +84,7 @@ struct nursd_plan_s {
   // points
   int* bin_of = nullptr;
   int2* i0_orig = nullptr;
+  int* slot_of = nullptr;  // sorted slot of each sample (inverse of sorted_l)
   float* w_orig = nullptr;
   int* counts = nullptr;
   int* bin_start = nullptr;
@@ -171,11 +172,12 @@ int from_cuda(cudaError_t e) { return e == cudaSuccess ? NURSD_OK : NURSD_ERR_CU
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 // C[L][2F] = H[L][T] B: tcgen05 form when the plan has its descriptors and both buffers are
-// 16-byte aligned, mma.sync form otherwise.
-cudaError_t run_temporal(const nursd_plan_s* p, const float* h, float* C, int L, cudaStream_t s) {
+// 16-byte aligned, mma.sync form otherwise.  row_slot (optional): row l goes to row row_slot[l].
+cudaError_t run_temporal(const nursd_plan_s* p, const float* h, float* C, int L, cudaStream_t s,
+                         const int* row_slot = nullptr) {
   if (p->tmaps.ok && aligned(h, 16) && aligned(C, 16))
-    return launch_temporal_umma(p->tmaps, h, C, L, p->T, 2 * p->F, p->status, s);
-  return launch_temporal_tc(h, p->Bth, p->Btl, C, L, p->T, 2 * p->F, s);
+    return launch_temporal_umma(p->tmaps, h, C, L, p->T, 2 * p->F, p->status, s, row_slot);
+  return launch_temporal_tc(h, p->Bth, p->Btl, C, L, p->T, 2 * p->F, s, row_slot);
 }
 
 PanelArgs panel_base(const nursd_plan_s* p) {
@@ -319,13 +321,15 @@ int build_srsd_chirps(nursd_plan_s* p, cudaStream_t s) {
   return rc;
 }
 
-int run_nufft1(nursd_plan_s* p, const float2* phasor, float2* spec, cudaStream_t s) {
+// phasor rows in sample order, or (slot_ordered) already in the spread's sorted order.
+int run_nufft1(nursd_plan_s* p, const float2* phasor, float2* spec, cudaStream_t s, bool slot_ordered = false) {
   const int F = p->F, M = p->M, W = p->W;
   const int logf = ilog2(p->nf);
   cudaError_t e;
   {
     StageTimer t(p, NURSD_STAGE_SPREAD, s, 1);
-    e = launch_spread(phasor, F, p->bin_start, p->sorted_l, p->i0_sorted, p->w_sorted, p->w, p->tiles, W, p->fine, s);
+    e = launch_spread(phasor, F, p->bin_start, slot_ordered ? nullptr : p->sorted_l, p->i0_sorted, p->w_sorted, p->w,
+                      p->tiles, W, p->fine, s);
   }
   if (e == cudaSuccess) {  // FFT along x of every window row, keep kx in I_M
     StageTimer t(p, NURSD_STAGE_FFT_X, s, 1);
@@ -695,7 +699,7 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
             p->alloc(p->Gc, (size_t)p->ncls * p->F * p->Z) && p->alloc(p->status, 1) &&
             p->alloc(p->bin_of, maxL) && p->alloc(p->i0_orig, maxL) && p->alloc(p->w_orig, (size_t)maxL * 2 * p->w) &&
             p->alloc(p->counts, (size_t)2 * nbins) && p->alloc(p->bin_start, nbins + 1) &&
-            p->alloc(p->sorted_l, maxL) && p->alloc(p->i0_sorted, maxL) &&
+            p->alloc(p->sorted_l, maxL) && p->alloc(p->slot_of, maxL) && p->alloc(p->i0_sorted, maxL) &&
             p->alloc(p->w_sorted, (size_t)maxL * 2 * p->w) && p->alloc(p->phasor, (size_t)maxL * p->F) &&
             p->alloc(p->frac_orig, maxL) && p->alloc(p->frac_sorted, maxL) &&
             p->alloc(p->fine, (size_t)p->W * p->W * std::max(p->F, p->Z)) &&
@@ -774,7 +778,7 @@ int nursd_set_points(nursd_plan_t p, int32_t L, const float* d_xy, nursd_stream_
     StageTimer t(p, NURSD_STAGE_POINTS, static_cast<cudaStream_t>(stream), L > 0 ? 5 : 0);
     rc = from_cuda(launch_points(a, p->bin_of, p->i0_orig, p->w_orig, p->counts, p->bin_start, p->sorted_l,
                                  p->i0_sorted, p->w_sorted, static_cast<cudaStream_t>(stream), p->frac_orig,
-                                 p->frac_sorted));
+                                 p->frac_sorted, p->slot_of));
   }
   if (rc == NURSD_OK) p->L = L;
   return rc;
@@ -816,9 +820,10 @@ int nursd_forward(nursd_plan_t p, const float* d_hist, void* d_out, nursd_stream
   int rc;
   {
     StageTimer t(p, NURSD_STAGE_TEMPORAL, s, p->L > 0 ? 1 : 0);
-    rc = from_cuda(run_temporal(p, d_hist, reinterpret_cast<float*>(p->phasor), p->L, s));
+    // phasors straight into the spread's sorted order (the internal buffer is read only by the spread)
+    rc = from_cuda(run_temporal(p, d_hist, reinterpret_cast<float*>(p->phasor), p->L, s, p->slot_of));
   }
-  if (rc == NURSD_OK) rc = run_nufft1(p, p->phasor, p->U, s);
+  if (rc == NURSD_OK) rc = run_nufft1(p, p->phasor, p->U, s, true);
   if (rc == NURSD_OK) rc = run_propagate(p, p->U, d_out, s);
   return rc;
 }

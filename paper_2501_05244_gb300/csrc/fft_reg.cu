@@ -551,6 +551,48 @@ __global__ void __launch_bounds__(RegShape<LOGN, CP>::NT, 2) panel_fft_pipe_kern
   }
 }
 
+// Copies panel (b, chunk)'s input window into the staging buffer [nin][CP] with cp.async
+// (the caller commits): two channels per 16-byte copy when in_vec2, one per 8-byte copy
+// otherwise, or consecutive rows per thread when the axis is contiguous in memory.
+template <int CP, int NT>
+struct WindowStager {
+  const PanelArgs& a;
+  float2* ibuf;
+  int tid, nlo, in_vec2;
+  float inv_nlo;
+  __device__ __forceinline__ void operator()(int b, int chunk) const {
+    const int q = tid % CP, cq2 = 2 * (tid % (CP / 2));
+    const int hc = small_div(chunk, nlo, inv_nlo);
+    const int hi0 = hc * a.CHI, lo0 = (chunk - hc * nlo) * a.CLO;
+    const float2* inb = a.in + (long long)b * a.in_sb;
+    if (a.load_i_fastest) {
+      for (int idx = tid; idx < a.nin * CP; idx += NT) {
+        const int i = idx % a.nin, qq = idx / a.nin;
+        const int hi = hi0 + qq / a.CLO, lo = lo0 + qq % a.CLO;
+        const bool ok = hi < a.hi_total && lo < a.lo_total;
+        const float2* src = ok ? inb + (long long)i * a.in_si + (long long)hi * a.in_shi + (long long)lo * a.in_slo : a.in;
+        cp_async8(ibuf + i * CP + qq, src, ok);
+      }
+    } else if (in_vec2) {
+      constexpr int RSTEP = NT / (CP / 2);
+      const int hi = hi0 + cq2 / a.CLO, lo = lo0 + cq2 % a.CLO;
+      const bool ok = hi < a.hi_total && lo < a.lo_total;
+      int i = tid / (CP / 2);
+      const float2* src = inb + (long long)hi * a.in_shi + lo + (long long)i * a.in_si;
+      const long long step = (long long)RSTEP * a.in_si;
+      for (; i < a.nin; i += RSTEP, src += step) cp_async16(ibuf + i * CP + cq2, ok ? src : a.in, ok);
+    } else {
+      constexpr int RSTEP = NT / CP;
+      const int hi = hi0 + q / a.CLO, lo = lo0 + q % a.CLO;
+      const bool ok = hi < a.hi_total && lo < a.lo_total;
+      int i = tid / CP;
+      const float2* src = inb + (long long)hi * a.in_shi + (long long)lo * a.in_slo + (long long)i * a.in_si;
+      const long long step = (long long)RSTEP * a.in_si;
+      for (; i < a.nin; i += RSTEP, src += step) cp_async8(ibuf + i * CP + q, ok ? src : a.in, ok);
+    }
+  }
+};
+
 // ------------------------------------------------------------------ radix-32 form
 // For n = 512, 1024: two Stockham stages, radix 32 then R2 = n / 32.  T = n / 32 threads per
 // transform, 32 values each.  Stage 1: thread j0 < T does butterfly j0 (a 32-point DFT of
@@ -628,13 +670,56 @@ struct R32Shape {
   static constexpr int XROWS = n + PADX * (n / 32);
 };
 
+// The two radix-32 stages on v[32] (thread j0, channel column q): entry v[t] = x[j0 + T t],
+// exit v[m R2 + k] = X[j0 + T m + 32 k].  after_exchange() runs right after the exchange
+// barrier (every thread has finished its stage-1 work).
+template <int LOGN, int CP, bool INV, class Hook>
+__device__ __forceinline__ void fft32_core(float2* v, float2* xbuf, int j0, int q, const float2* __restrict__ tw2,
+                                           Hook&& after_exchange) {
+  using S = R32Shape<LOGN, CP>;
+  constexpr int T = S::T, R2 = S::R2, PADX = S::PADX;
+  // stage 1: outputs 32 j0 + k at rows 32 j0 + k + PADX j0
+  dft32<INV>(v);
+  {
+    float2* w = xbuf + (32 + PADX) * j0 * CP + q;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) w[k * CP] = v[k];
+  }
+  __syncthreads();
+  after_exchange();
+  // stage 2: butterflies j = j0 + T m read rows j + (32 + PADX) t
+#pragma unroll
+  for (int m = 0; m < 32 / R2; ++m) {
+    const int j = j0 + T * m;
+    const float2* r = xbuf + j * CP + q;
+#pragma unroll
+    for (int t = 0; t < R2; ++t) v[m * R2 + t] = r[t * (32 + PADX) * CP];
+    twiddle_row<R2, INV>(v + m * R2, tw2 + j * R2);
+    if (R2 == 32)
+      dft32<INV>(v + m * R2);
+    else
+      dft16<INV>(v + m * R2);
+  }
+}
+
+// Bins of v (fft32_core exit order) -> xbuf rows in natural order, [n][CP].
+template <int LOGN, int CP>
+__device__ __forceinline__ void store_bins32(const float2* v, float2* xbuf, int j0, int q) {
+  using S = R32Shape<LOGN, CP>;
+  float2* w = xbuf + j0 * CP + q;
+#pragma unroll
+  for (int m = 0; m < 32 / S::R2; ++m)
+#pragma unroll
+    for (int k = 0; k < S::R2; ++k) w[(S::T * m + 32 * k) * CP] = v[m * S::R2 + k];
+}
+
 // Persistent radix-32 form: same panels, staging, zero row and copy-out as
 // panel_fft_pipe_kernel; four CTA barriers per panel.
 template <int LOGN, int CP, bool INV>
-__global__ void __launch_bounds__(R32Shape<LOGN, CP>::NT, R32Shape<LOGN, CP>::NT >= 256 ? 2 : 3) panel_fft32_kernel(const PanelArgs a, int npanel,
-                                                                             int in_vec2, int out_vec2) {
+__global__ void __launch_bounds__(R32Shape<LOGN, CP>::NT, R32Shape<LOGN, CP>::NT >= 256 ? 2 : 3) panel_fft32_kernel(
+    const PanelArgs a, int npanel, int in_vec2, int out_vec2) {
   using S = R32Shape<LOGN, CP>;
-  constexpr int n = S::n, T = S::T, R2 = S::R2, NT = S::NT, PADX = S::PADX;
+  constexpr int n = S::n, T = S::T, NT = S::NT;
   extern __shared__ float2 sm[];
   float2* xbuf = sm;                   // exchange buffer [XROWS][CP], then the bins [n][CP]
   float2* ibuf = sm + S::XROWS * CP;   // staging [nin + 1][CP]
@@ -643,44 +728,11 @@ __global__ void __launch_bounds__(R32Shape<LOGN, CP>::NT, R32Shape<LOGN, CP>::NT
   const int nlo = (a.lo_total + a.CLO - 1) / a.CLO;
   const int nchunk = ((a.hi_total + a.CHI - 1) / a.CHI) * nlo;
   const float inv_nlo = 1.f / (float)nlo;
-  const int qhi = q / a.CLO, qlo = q % a.CLO;
-  const int cq2 = 2 * (tid % (CP / 2));
-  const int cq2hi = cq2 / a.CLO, cq2lo = cq2 % a.CLO;
   if (tid < CP) ibuf[a.nin * CP + tid] = make_float2(0.f, 0.f);  // the zero row
   float* mo = reinterpret_cast<float*>(ibuf + (a.nin + 1) * CP);  // mul_o[0..nout), if any
   if (a.mul_o)
     for (int o = tid; o < a.nout; o += NT) mo[o] = __ldg(a.mul_o + o);
-
-  auto issue = [&](int b, int chunk) {
-    const int hc = small_div(chunk, nlo, inv_nlo);
-    const int hi0 = hc * a.CHI, lo0 = (chunk - hc * nlo) * a.CLO;
-    const float2* inb = a.in + (long long)b * a.in_sb;
-    if (a.load_i_fastest) {
-      for (int idx = tid; idx < a.nin * CP; idx += NT) {
-        const int i = idx % a.nin, qq = idx / a.nin;
-        const int hi = hi0 + qq / a.CLO, lo = lo0 + qq % a.CLO;
-        const bool ok = hi < a.hi_total && lo < a.lo_total;
-        const float2* src = ok ? inb + (long long)i * a.in_si + (long long)hi * a.in_shi + (long long)lo * a.in_slo : a.in;
-        cp_async8(ibuf + i * CP + qq, src, ok);
-      }
-    } else if (in_vec2) {
-      constexpr int RSTEP = NT / (CP / 2);
-      const int hi = hi0 + cq2hi, lo = lo0 + cq2lo;
-      const bool ok = hi < a.hi_total && lo < a.lo_total;
-      int i = tid / (CP / 2);
-      const float2* src = inb + (long long)hi * a.in_shi + lo + (long long)i * a.in_si;
-      const long long step = (long long)RSTEP * a.in_si;
-      for (; i < a.nin; i += RSTEP, src += step) cp_async16(ibuf + i * CP + cq2, ok ? src : a.in, ok);
-    } else {
-      constexpr int RSTEP = NT / CP;
-      const int hi = hi0 + qhi, lo = lo0 + qlo;
-      const bool ok = hi < a.hi_total && lo < a.lo_total;
-      int i = tid / CP;
-      const float2* src = inb + (long long)hi * a.in_shi + (long long)lo * a.in_slo + (long long)i * a.in_si;
-      const long long step = (long long)RSTEP * a.in_si;
-      for (; i < a.nin; i += RSTEP, src += step) cp_async8(ibuf + i * CP + q, ok ? src : a.in, ok);
-    }
-  };
+  const WindowStager<CP, NT> issue{a, ibuf, tid, nlo, in_vec2, inv_nlo};
 
   const int lpos = (j0 - a.in_off) & (n - 1);  // input index at FFT position j0
   const float2* rq = ibuf + q;
@@ -710,45 +762,114 @@ __global__ void __launch_bounds__(R32Shape<LOGN, CP>::NT, R32Shape<LOGN, CP>::NT
         }
       }
     }
-    // stage 1: outputs 32 j0 + k at rows 32 j0 + k + PADX j0
-    dft32<INV>(v);
-    {
-      float2* w = xbuf + (32 + PADX) * j0 * CP + q;
-#pragma unroll
-      for (int k = 0; k < 32; ++k) w[k * CP] = v[k];
-    }
-    __syncthreads();  // stage-1 outputs are in place, and every thread has read the staged window
-    cb += step_b;
-    cc += step_c;
-    if (cc >= nchunk) {
-      cc -= nchunk;
-      ++cb;
-    }
-    if (p + (int)gridDim.x < npanel) issue(cb, cc);
-    cp_async_commit();
-    // stage 2: butterflies j = j0 + T m read rows j + (32 + PADX) t
-#pragma unroll
-    for (int m = 0; m < 32 / R2; ++m) {
-      const int j = j0 + T * m;
-      const float2* r = xbuf + j * CP + q;
-#pragma unroll
-      for (int t = 0; t < R2; ++t) v[m * R2 + t] = r[t * (32 + PADX) * CP];
-      twiddle_row<R2, INV>(v + m * R2, tw2 + j * R2);
-      if (R2 == 32)
-        dft32<INV>(v + m * R2);
-      else
-        dft16<INV>(v + m * R2);
-    }
+    fft32_core<LOGN, CP, INV>(v, xbuf, j0, q, tw2, [&] {
+      // every thread has read the staged window: start the next panel's copy
+      cb += step_b;
+      cc += step_c;
+      if (cc >= nchunk) {
+        cc -= nchunk;
+        ++cb;
+      }
+      if (p + (int)gridDim.x < npanel) issue(cb, cc);
+      cp_async_commit();
+    });
     __syncthreads();  // every thread has read its stage-2 inputs
-    {  // bins j + 32 k in natural order
-      float2* w = xbuf + j0 * CP + q;
-#pragma unroll
-      for (int m = 0; m < 32 / R2; ++m)
-#pragma unroll
-        for (int k = 0; k < R2; ++k) w[(T * m + 32 * k) * CP] = v[m * R2 + k];
-    }
+    store_bins32<LOGN, CP>(v, xbuf, j0, q);
     __syncthreads();
     copy_out<LOGN, CP, NT>(a, xbuf, mo, b, hi0, lo0, out_vec2);
+  }
+}
+
+// Persistent Bluestein form for n = 512, 1024: the staged window times cpre, the forward
+// transform, times bhat, regrouped through shared memory into the entry order, the inverse
+// transform, and the kept bins times cpost, copied out row by row.
+template <int LOGN, int CP>
+__global__ void __launch_bounds__(R32Shape<LOGN, CP>::NT, R32Shape<LOGN, CP>::NT >= 256 ? 2 : 3)
+    panel_bluestein32_kernel(const PanelArgs a, int npanel, int in_vec2, int out_vec2,
+                             const float2* __restrict__ cpre, const float2* __restrict__ bhat,
+                             const float2* __restrict__ cpost) {
+  using S = R32Shape<LOGN, CP>;
+  constexpr int n = S::n, T = S::T, NT = S::NT, R2 = S::R2;
+  extern __shared__ float2 sm[];
+  float2* xbuf = sm;
+  float2* ibuf = sm + S::XROWS * CP;
+  const int tid = threadIdx.x;
+  const int q = tid % CP, j0 = tid / CP;
+  const int nlo = (a.lo_total + a.CLO - 1) / a.CLO;
+  const int nchunk = ((a.hi_total + a.CHI - 1) / a.CHI) * nlo;
+  const float inv_nlo = 1.f / (float)nlo;
+  if (tid < CP) ibuf[a.nin * CP + tid] = make_float2(0.f, 0.f);  // the zero row
+  const WindowStager<CP, NT> issue{a, ibuf, tid, nlo, in_vec2, inv_nlo};
+  const int lpos = (j0 - a.in_off) & (n - 1);
+  const float2* rq = ibuf + q;
+  const float2* __restrict__ tw2 = a.twiddle + tw32_offset(LOGN);
+  const int step_b = gridDim.x / nchunk, step_c = gridDim.x % nchunk;
+  int p = blockIdx.x;
+  int cb = p / nchunk, cc = p % nchunk;
+  if (p < npanel) issue(cb, cc);
+  cp_async_commit();
+  for (; p < npanel; p += gridDim.x) {
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    const int b = cb, c_cur = cc;
+    float2 v[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) v[t] = rq[min((lpos + t * T) & (n - 1), a.nin) * CP];  // zero row outside
+#pragma unroll
+    for (int t = 0; t < 32; ++t) v[t] = cmul(v[t], __ldg(cpre + min((lpos + t * T) & (n - 1), a.nin - 1)));
+    fft32_core<LOGN, CP, false>(v, xbuf, j0, q, tw2, [&] {
+      cb += step_b;
+      cc += step_c;
+      if (cc >= nchunk) {
+        cc -= nchunk;
+        ++cb;
+      }
+      if (p + (int)gridDim.x < npanel) issue(cb, cc);
+      cp_async_commit();
+    });
+#pragma unroll
+    for (int m = 0; m < 32 / R2; ++m)
+#pragma unroll
+      for (int k = 0; k < R2; ++k) v[m * R2 + k] = cmul(v[m * R2 + k], __ldg(bhat + j0 + T * m + 32 * k));
+    __syncthreads();
+    store_bins32<LOGN, CP>(v, xbuf, j0, q);
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 32; ++t) v[t] = xbuf[(j0 + T * t) * CP + q];
+    __syncthreads();
+    fft32_core<LOGN, CP, true>(v, xbuf, j0, q, tw2, [] {});
+    __syncthreads();
+    store_bins32<LOGN, CP>(v, xbuf, j0, q);
+    __syncthreads();
+    // kept bins times cpost[o]
+    const int hc = small_div(c_cur, nlo, inv_nlo);
+    const int hi0 = hc * a.CHI, lo0 = (c_cur - hc * nlo) * a.CLO;
+    const long long obase = (long long)b * a.out_sb;
+    if (out_vec2) {
+      constexpr int CP2 = CP / 2, RSTEP = NT / CP2;
+      const int qq = 2 * (tid % CP2);
+      const int hi = hi0 + qq / a.CLO, lo = lo0 + qq % a.CLO;
+      if (hi < a.hi_total && lo < a.lo_total) {
+        const long long cbase = obase + (long long)hi * a.out_shi + lo;
+        for (int o = tid / CP2; o < a.nout; o += RSTEP) {
+          const int bin = (o + a.out_off) & (n - 1);
+          const float4 x = *reinterpret_cast<const float4*>(xbuf + bin * CP + qq);
+          const float2 c = __ldg(cpost + o);
+          const float2 y0 = cmul(make_float2(x.x, x.y), c), y1 = cmul(make_float2(x.z, x.w), c);
+          *reinterpret_cast<float4*>(a.out + cbase + (long long)o * a.out_si) = make_float4(y0.x, y0.y, y1.x, y1.y);
+        }
+      }
+    } else {
+      constexpr int RSTEP = NT / CP;
+      const int hi = hi0 + q / a.CLO, lo = lo0 + q % a.CLO;
+      if (hi < a.hi_total && lo < a.lo_total) {
+        const long long cbase = obase + (long long)hi * a.out_shi + (long long)lo * a.out_slo;
+        for (int o = tid / CP; o < a.nout; o += RSTEP) {
+          const int bin = (o + a.out_off) & (n - 1);
+          a.out[cbase + (long long)o * a.out_si] = cmul(xbuf[bin * CP + q], __ldg(cpost + o));
+        }
+      }
+    }
   }
 }
 
@@ -852,6 +973,42 @@ cudaError_t launch_bluestein_reg(const PanelArgs& a, const float2* cpre, const f
                                  cudaStream_t s) {
   using S = RegShape<LOGN, CP>;
   if (!axis_offsets_fit(S::n, a)) return cudaErrorInvalidValue;
+  if constexpr (LOGN == 9 || LOGN == 10) {  // radix-32 persistent form
+    using R = R32Shape<LOGN, CP>;
+    const int nhi = (a.hi_total + a.CHI - 1) / a.CHI;
+    const int nlo = (a.lo_total + a.CLO - 1) / a.CLO;
+    const long long npanel = (long long)nhi * nlo * a.batch;
+    const int sms = sm_count();
+    const size_t smem32 = sizeof(float2) * ((size_t)R::XROWS * CP + (size_t)(a.nin + 1) * CP);
+    if (npanel >= 4LL * sms && smem32 <= 220 * 1024 && (long long)nhi * nlo < (1LL << 22) && a.nin >= 1 &&
+        !a.load_i_fastest) {
+      auto kern = panel_bluestein32_kernel<LOGN, CP>;
+      static bool configured32 = false;
+      static size_t occ_smem32 = 0;
+      static int occ32 = 1;
+      if (!configured32) {
+        cudaError_t e = configure(kern, 220 * 1024);
+        if (e != cudaSuccess) return e;
+        configured32 = true;
+      }
+      if (occ_smem32 != smem32) {
+        int nb = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, R::NT, smem32);
+        if (e != cudaSuccess) return e;
+        occ32 = std::max(nb, 1);
+        occ_smem32 = smem32;
+      }
+      const int in_vec2 = a.in_slo == 1 && a.CLO % 2 == 0 && a.lo_total % 2 == 0 &&
+                          reinterpret_cast<uintptr_t>(a.in) % 16 == 0 && a.in_sb % 2 == 0 && a.in_si % 2 == 0 &&
+                          a.in_shi % 2 == 0;
+      const int out_vec2 = a.out_slo == 1 && a.CLO % 2 == 0 && a.lo_total % 2 == 0 &&
+                           reinterpret_cast<uintptr_t>(a.out) % 16 == 0 && a.out_sb % 2 == 0 && a.out_si % 2 == 0 &&
+                           a.out_shi % 2 == 0;
+      const int grid = (int)std::min<long long>(npanel, (long long)sms * occ32);
+      kern<<<grid, R::NT, smem32, s>>>(a, (int)npanel, in_vec2, out_vec2, cpre, bhat, cpost);
+      return cudaGetLastError();
+    }
+  }
   const size_t smem = sizeof(float2) * (size_t)S::XROWS * CP;
   static bool configured = false;
   if (!configured) {

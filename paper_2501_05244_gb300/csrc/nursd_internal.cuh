@@ -107,9 +107,10 @@ cudaError_t launch_panel_bluestein(int logn, const PanelArgs& a, const float2* c
 
 // ------------------------------------------------------------- temporal DFT
 // P[l][f] = sum_n h[l][n] * B[n][2f..2f+1] as a real GEMM C[L][2F] = H[L][T] B[T][2F] on the
-// tensor cores; Bh/Bl are the fp16 head and tail of B^T, [2F][T] (__half).
+// tensor cores; Bh/Bl are the fp16 head and tail of B^T, [2F][T] (__half).  row_slot (optional):
+// row l of C is written at row row_slot[l] (the spread's sorted order).
 cudaError_t launch_temporal_tc(const float* h, const void* Bh, const void* Bl, float* C, int L, int T, int twoF,
-                               cudaStream_t s);
+                               cudaStream_t s, const int* row_slot = nullptr);
 
 // The same transform with tcgen05.mma (temporal_umma.cu), for T % 64 == 0 and 2F in {32, 64, 128, 256}.
 // TMA descriptors of B's head and tail ([2F][T] fp16) are encoded once per plan.
@@ -122,7 +123,7 @@ bool temporal_umma_supported(int T, int twoF);
 bool make_temporal_maps(const void* Bh, const void* Bl, int T, int twoF, TemporalMaps* m);
 // status: bit 4 is set if a barrier wait timed out (the output is then incomplete).
 cudaError_t launch_temporal_umma(const TemporalMaps& m, const float* h, float* C, int L, int T, int twoF,
-                                 int* status, cudaStream_t s);
+                                 int* status, cudaStream_t s, const int* row_slot = nullptr);
 
 // Ragged batch of temporal transforms: item b has L[b] rows at A[b] -> C[b];
 // tile_start[b] = number of 128 x 128 output tiles of items 0..b-1.
@@ -148,17 +149,19 @@ struct PointsArgs {
   float beta;                     // ES kernel shape
   int* status;                    // device error word
 };
-// Prepare and sort the relay samples by bin = (footprint row, tile column),
+// Prepare and sort the relay samples by bin = (tile column, footprint row),
 // nbins = points_bins(W, tiles).  Scratch in original order: bin_of [L],
 // i0_orig [L], w_orig [L][2w]; counts needs 2*nbins ints.  Sorted outputs:
 // sorted_l [L] (original index), i0_sorted, w_sorted, and bin_start [nbins+1].
 int points_bins(int W, int tiles);
-// frac_sorted (optional) receives u - i0 per axis of each sorted sample.
+// frac_sorted (optional) receives u - i0 per axis of each sorted sample; slot_of (optional) the
+// inverse of sorted_l (the sorted slot of each sample).
 cudaError_t launch_points(const PointsArgs& a, int* bin_of, int2* i0_orig, float* w_orig, int* counts,
                           int* bin_start, int* sorted_l, int2* i0_sorted, float* w_sorted, cudaStream_t s,
-                          float2* frac_orig = nullptr, float2* frac_sorted = nullptr);
+                          float2* frac_orig = nullptr, float2* frac_sorted = nullptr, int* slot_of = nullptr);
 
 // ---------------------------------------------------------------- spread
+// sorted_l == nullptr: P is already in sorted-slot order (row s of P is sorted sample s).
 cudaError_t launch_spread(const float2* P, int F, const int* bin_start, const int* sorted_l,
                           const int2* i0, const float* wts, int width, int tiles, int W,
                           float2* fine, cudaStream_t s);

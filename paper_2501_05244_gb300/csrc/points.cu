@@ -153,10 +153,12 @@ __global__ void points_sort_bins(const int* __restrict__ bin_start, int nbins, i
 
 __global__ void points_gather(const int* __restrict__ sorted_l, int L, int width, const int2* __restrict__ i0_in,
                               const float* __restrict__ w_in, const float2* __restrict__ frac_in,
-                              int2* __restrict__ i0_out, float* __restrict__ w_out, float2* __restrict__ frac_out) {
+                              int2* __restrict__ i0_out, float* __restrict__ w_out, float2* __restrict__ frac_out,
+                              int* __restrict__ slot_of) {
   const int pos = blockIdx.x * blockDim.x + threadIdx.x;
   if (pos >= L) return;
   const int l = sorted_l[pos];
+  if (slot_of) slot_of[l] = pos;
   i0_out[pos] = i0_in[l];
   if (frac_out) frac_out[pos] = frac_in[l];
   for (int t = 0; t < 2 * width; ++t) w_out[(size_t)pos * 2 * width + t] = w_in[(size_t)l * 2 * width + t];
@@ -168,7 +170,7 @@ int points_bins(int W, int tiles) { return W * tiles; }
 
 cudaError_t launch_points(const PointsArgs& a, int* bin_of, int2* i0_orig, float* w_orig, int* counts,
                           int* bin_start, int* sorted_l, int2* i0_sorted, float* w_sorted, cudaStream_t s,
-                          float2* frac_orig, float2* frac_sorted) {
+                          float2* frac_orig, float2* frac_sorted, int* slot_of) {
   if ((frac_orig == nullptr) != (frac_sorted == nullptr)) return cudaErrorInvalidValue;
   const int nbins = points_bins(a.W, a.tiles);
   // counts holds 2 * nbins ints: the bin counts, then the scatter cursors
@@ -181,7 +183,7 @@ cudaError_t launch_points(const PointsArgs& a, int* bin_of, int2* i0_orig, float
   points_scatter<<<blocks, 256, 0, s>>>(bin_of, bin_start, a.L, counts + nbins, sorted_l);
   points_sort_bins<<<(nbins + 255) / 256, 256, 0, s>>>(bin_start, nbins, sorted_l);
   points_gather<<<blocks, 256, 0, s>>>(sorted_l, a.L, a.width, i0_orig, w_orig, frac_orig, i0_sorted, w_sorted,
-                                      frac_sorted);
+                                      frac_sorted, slot_of);
   return cudaGetLastError();
 }
 

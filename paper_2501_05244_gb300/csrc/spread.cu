@@ -8,8 +8,9 @@
 // its left (a footprint of w <= 8 cells crosses at most one tile edge) -- are
 // two contiguous slot ranges.  The CTA stages them in shared memory (the 32
 // channels of each sample's phasor, its footprint origin and its x and y
-// weights) in chunks, and the warp for row y adds the samples whose first row is
-// in y-w+1 .. y (again two contiguous sub-ranges).  A sample's taps land on cells
+// weights) in chunks -- one round of loads when P is already in sorted-slot order,
+// two when its rows are found through the sorted index -- and the warp for row y
+// adds the samples whose first row is in y-w+1 .. y (again two contiguous sub-ranges).  A sample's taps land on cells
 // o .. o+w-1 of the row, o = its first column minus the tile's; a warp-uniform
 // switch on o selects a fully unrolled update of the registers it touches.
 // Every window cell is written exactly once, and the summation order is the
@@ -103,11 +104,18 @@ __global__ void __launch_bounds__(kWarps * 32, 2) spread_kernel(const float2* __
   for (int c0 = 0; c0 < n; c0 += kCap) {
     const int cn = min(kCap, n - c0);
     __syncthreads();  // the previous chunk has been consumed
-    // phase 1, one thread per sample (all loads in flight at once): index, origin, weights
+    // phase 1, one thread per sample (all loads in flight at once): index, origin, weights; when P
+    // is in slot order its copies need no index and start here too
+    if (!sorted_l)
+      for (int s = warp; s < cn; s += kWarps) {
+        const int v = c0 + s;
+        const int slot = v < nA ? aS + v : bS + (v - nA);
+        cp_async8(&sm.p[s][lane], live ? P + (size_t)slot * F + f0 + lane : P, live);
+      }
     for (int s = threadIdx.x; s < cn; s += kWarps * 32) {
       const int v = c0 + s;
       const int slot = v < nA ? aS + v : bS + (v - nA);
-      const int l = __ldg(sorted_l + slot);
+      const int l = sorted_l ? __ldg(sorted_l + slot) : slot;
       const int2 o = __ldg(i0 + slot);
       const float* w = wts + (size_t)slot * 2 * KW;
       float wv[2 * KW];
@@ -123,9 +131,9 @@ __global__ void __launch_bounds__(kWarps * 32, 2) spread_kernel(const float2* __
       }
     }
     __syncthreads();
-    // phase 2, one warp per sample: its 32 channels of P, and its y weight for each tile row
+    // phase 2, one warp per sample: its 32 channels of P (sample order), and its y weight for each tile row
     for (int s = warp; s < cn; s += kWarps) {
-      cp_async8(&sm.p[s][lane], live ? P + (size_t)sm.l[s] * F + f0 + lane : P, live);
+      if (sorted_l) cp_async8(&sm.p[s][lane], live ? P + (size_t)sm.l[s] * F + f0 + lane : P, live);
       if (lane < kTile) {
         const int d = lane - sm.oy[s];
         sm.wt[s][lane] = (d >= 0 && d < KW) ? sm.wy[s][d] : 0.f;

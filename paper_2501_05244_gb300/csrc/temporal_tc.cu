@@ -105,7 +105,7 @@ __device__ __forceinline__ void store_stage(TcSmem& sm, const Stage& st) {
 // One 128 x 128 output tile.
 __device__ __forceinline__ void tc_tile(TcSmem& sm, const float* __restrict__ A, const __half* __restrict__ Bh,
                                         const __half* __restrict__ Bl, float* __restrict__ C, int L, int K, int NC,
-                                        int m0, int n0) {
+                                        int m0, int n0, const int* __restrict__ row_slot) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int wm = (warp & 3) * 32, wn = (warp >> 2) * 64;  // warp tile origin (4 x 2 warps)
   float acc[2][8][4];
@@ -167,10 +167,11 @@ __device__ __forceinline__ void tc_tile(TcSmem& sm, const float* __restrict__ A,
       for (int h = 0; h < 2; ++h) {
         const int row = m0 + wm + i * 16 + g + h * 8;
         if (row < L) {
+          const int orow = row_slot ? __ldg(row_slot + row) : row;
           if (col + 1 < NC) {
-            *reinterpret_cast<float2*>(C + (size_t)row * NC + col) = make_float2(acc[i][j][2 * h], acc[i][j][2 * h + 1]);
+            *reinterpret_cast<float2*>(C + (size_t)orow * NC + col) = make_float2(acc[i][j][2 * h], acc[i][j][2 * h + 1]);
           } else if (col < NC) {
-            C[(size_t)row * NC + col] = acc[i][j][2 * h];
+            C[(size_t)orow * NC + col] = acc[i][j][2 * h];
           }
         }
       }
@@ -179,10 +180,10 @@ __device__ __forceinline__ void tc_tile(TcSmem& sm, const float* __restrict__ A,
 
 __global__ void __launch_bounds__(NT) temporal_tc_kernel(const float* __restrict__ A, const __half* __restrict__ Bh,
                                                         const __half* __restrict__ Bl, float* __restrict__ C, int L,
-                                                        int K, int NC) {
+                                                        int K, int NC, const int* __restrict__ row_slot) {
   extern __shared__ __align__(16) unsigned char raw[];
   TcSmem& sm = *reinterpret_cast<TcSmem*>(raw);
-  tc_tile(sm, A, Bh, Bl, C, L, K, NC, blockIdx.y * BM, blockIdx.x * BN);
+  tc_tile(sm, A, Bh, Bl, C, L, K, NC, blockIdx.y * BM, blockIdx.x * BN, row_slot);
 }
 
 // Persistent form over a ragged batch (tiles numbered consecutively across items,
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(NT) temporal_tc_batched_kernel(const TemporalB
     int b = 0;
     while (t >= bt.tile_start[b + 1]) ++b;
     const int local = t - bt.tile_start[b];
-    tc_tile(sm, bt.A[b], Bh, Bl, bt.C[b], bt.L[b], K, NC, (local / ncol) * BM, (local % ncol) * BN);
+    tc_tile(sm, bt.A[b], Bh, Bl, bt.C[b], bt.L[b], K, NC, (local / ncol) * BM, (local % ncol) * BN, nullptr);
   }
 }
 
@@ -222,14 +223,14 @@ cudaError_t configure() {
 }  // namespace
 
 cudaError_t launch_temporal_tc(const float* h, const void* Bh, const void* Bl, float* C, int L, int T, int twoF,
-                               cudaStream_t s) {
+                               cudaStream_t s, const int* row_slot) {
   if (L <= 0) return cudaSuccess;
   if (T % 8 != 0) return cudaErrorInvalidValue;
   cudaError_t e = configure();
   if (e != cudaSuccess) return e;
   dim3 grid((twoF + BN - 1) / BN, (L + BM - 1) / BM);
   temporal_tc_kernel<<<grid, NT, sizeof(TcSmem), s>>>(h, static_cast<const __half*>(Bh), static_cast<const __half*>(Bl),
-                                                      C, L, T, twoF);
+                                                      C, L, T, twoF, row_slot);
   return cudaGetLastError();
 }
 

@@ -9,7 +9,8 @@
 // zero (photon counts below 2048 are exact in fp16) skips the H_lo product.
 //
 // One CTA per SM walks 128-row tiles of H (tile blockIdx.x + j gridDim.x).  Warp roles:
-//   0-3  epilogue: tcgen05.ld of the 128 x 2F accumulator (one row per thread), fp32 stores;
+//   0-3  epilogue: tcgen05.ld of the 128 x 2F accumulator (one row per thread), fp32 stores
+//        (row l to row row_slot[l] when a slot order is given);
 //        two accumulators in tensor memory, so a tile's epilogue overlaps the next tile's MMAs
 //   4-11 H producers: global loads three K-blocks ahead (~96 KB per SM in flight), fp16
 //        head/tail split, stores into the 128-byte-swizzled K-major operand layout
@@ -152,7 +153,8 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
                                                                      float* __restrict__ C, int L, int T,
                                                                      const __grid_constant__ CUtensorMap tm_hi,
                                                                      const __grid_constant__ CUtensorMap tm_lo,
-                                                                     int* __restrict__ status) {
+                                                                     int* __restrict__ status,
+                                                                     const int* __restrict__ row_slot) {
   using S = UShape<N2>;
   extern __shared__ unsigned char raw[];
   const uint32_t raw_addr = sa(raw);
@@ -207,7 +209,8 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
         uint32_t r[32];
         tmem_ld32(tb + c0, r);
         if (row < L) {
-          float4* dst = reinterpret_cast<float4*>(C + (size_t)row * N2 + c0);
+          const int orow = row_slot ? __ldg(row_slot + row) : row;
+          float4* dst = reinterpret_cast<float4*>(C + (size_t)orow * N2 + c0);
 #pragma unroll
           for (int q = 0; q < 8; ++q)
             dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
@@ -379,7 +382,8 @@ bool encode_b(CUtensorMap* m, const void* ptr, int T, int rows) {
 }
 
 template <int N2>
-cudaError_t launch_n(const TemporalMaps& m, const float* h, float* C, int L, int T, int* status, cudaStream_t s) {
+cudaError_t launch_n(const TemporalMaps& m, const float* h, float* C, int L, int T, int* status, cudaStream_t s,
+                     const int* row_slot) {
   using S = UShape<N2>;
   static bool configured = false;
   static int sms = 0;
@@ -394,7 +398,7 @@ cudaError_t launch_n(const TemporalMaps& m, const float* h, float* C, int L, int
   }
   const int ntiles = (L + kBM - 1) / kBM;
   const int grid = std::min(ntiles, sms);
-  temporal_umma_kernel<N2><<<grid, kUThreads, S::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status);
+  temporal_umma_kernel<N2><<<grid, kUThreads, S::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status, row_slot);
   return cudaGetLastError();
 }
 
@@ -414,16 +418,16 @@ bool make_temporal_maps(const void* Bh, const void* Bl, int T, int twoF, Tempora
 }
 
 cudaError_t launch_temporal_umma(const TemporalMaps& m, const float* h, float* C, int L, int T, int twoF,
-                                 int* status, cudaStream_t s) {
+                                 int* status, cudaStream_t s, const int* row_slot) {
   if (L <= 0) return cudaSuccess;
   if (!m.ok || !temporal_umma_supported(T, twoF) || reinterpret_cast<uintptr_t>(h) % 16 != 0 ||
       reinterpret_cast<uintptr_t>(C) % 16 != 0)
     return cudaErrorInvalidValue;
   switch (twoF) {
-    case 32: return launch_n<32>(m, h, C, L, T, status, s);
-    case 64: return launch_n<64>(m, h, C, L, T, status, s);
-    case 128: return launch_n<128>(m, h, C, L, T, status, s);
-    default: return launch_n<256>(m, h, C, L, T, status, s);
+    case 32: return launch_n<32>(m, h, C, L, T, status, s, row_slot);
+    case 64: return launch_n<64>(m, h, C, L, T, status, s, row_slot);
+    case 128: return launch_n<128>(m, h, C, L, T, status, s, row_slot);
+    default: return launch_n<256>(m, h, C, L, T, status, s, row_slot);
   }
 }
 
