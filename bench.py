@@ -398,9 +398,8 @@ def run_ours(args, rank, world, local):
     d_hist = torch.from_numpy(wl.hist).cuda()
     out = plan.empty_output()
 
-    def step():
-        plan.set_points(d_xy)
-        plan.forward(d_hist, out=out)
+    def step():  # positions + histograms -> volume (the point sort beside the temporal transform)
+        plan.reconstruct(d_xy, d_hist, out=out)
 
     def barrier():
         if dist is not None:
@@ -464,8 +463,7 @@ def run_ours(args, rank, world, local):
                 upload(k + 1)
             stream.wait_event(up[k % 2])
             stream.wait_event(down[k % 2])  # this output buffer's previous download has finished
-            plan.set_points(dx[k % 2])
-            plan.forward(dh[k % 2], out=do[k % 2])
+            plan.reconstruct(dx[k % 2], dh[k % 2], out=do[k % 2])
             done[k % 2].record(stream)
             with torch.cuda.stream(copy):
                 copy.wait_event(done[k % 2])

@@ -183,6 +183,22 @@ int nursd_forward_phasor(nursd_plan_t plan, const nursd_c64* d_phasor, void* d_o
 int nursd_forward(nursd_plan_t plan, const float* d_hist, void* d_out, nursd_stream_t stream);
 
 /*
+ * The whole NURSD-1 reconstruction from raw inputs (Eq. NURSD1 with the frequency
+ * integral of Eq. PF_RSD_Defn): nursd_set_points(L, d_xy) followed by
+ * nursd_forward(d_hist, d_out), with the same result bit for bit.  The sample
+ * sort (NUFFT-1 step 1, Sec. 6) runs on a plan-internal stream beside the
+ * temporal transform and is joined before the spread; all work is ordered on
+ * `stream` as usual: it starts after earlier work on `stream`, and later work on
+ * `stream` starts after its last read of d_xy and d_hist.  The plan keeps the
+ * points (later calls see L samples).  d_xy [L][2] float32 (8-byte aligned),
+ * d_hist [L][T] float32 (16-byte aligned), d_out as for nursd_forward.
+ * Returns NURSD_ERR_INVALID_ARG for bad arguments, NURSD_ERR_CUDA on a failed
+ * stream, event or launch call.
+ */
+int nursd_reconstruct(nursd_plan_t plan, int32_t L, const float* d_xy, const float* d_hist, void* d_out,
+                      nursd_stream_t stream);
+
+/*
  * NURSD-2/3 output (Eqs. NURSD2 and NURSD3): the forward from phasors evaluated
  * at arbitrary voxels of each depth plane instead of the lattice:
  *   V_z(x_v) = M^-2 sum_k Y_z(k) exp(+i k . theta_v),  theta_v = 2 pi (x_v - c) / (M delta),

@@ -122,7 +122,13 @@ struct nursd_plan_s {
     p = static_cast<T*>(q);
     return true;
   }
+  // side stream of nursd_reconstruct (the point sort runs there, beside the temporal transform)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   ~nursd_plan_s() {
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
     for (auto& v : ev)
       for (auto& e : v) {
         cudaEventDestroy(e.first);
@@ -757,9 +763,9 @@ int nursd_plan_dims(nursd_plan_t plan, int32_t* M, int32_t* fine_n, int32_t* n_c
   return NURSD_OK;
 }
 
-int nursd_set_points(nursd_plan_t p, int32_t L, const float* d_xy, nursd_stream_t stream) {
-  if (check_plan(p) != NURSD_OK || L < 0 || L > p->maxL || (L > 0 && (!d_xy || !aligned(d_xy, 8))))
-    return NURSD_ERR_INVALID_ARG;
+namespace {
+// Coordinate map, weights and bin sort of L samples on stream s (Sec. 6, NUFFT-1 step 1).
+int set_points_on(nursd_plan_t p, int32_t L, const float* d_xy, cudaStream_t s) {
   PointsArgs a;
   a.xy = d_xy;
   a.L = L;
@@ -775,13 +781,19 @@ int nursd_set_points(nursd_plan_t p, int32_t L, const float* d_xy, nursd_stream_
   a.status = p->status;
   int rc;
   {
-    StageTimer t(p, NURSD_STAGE_POINTS, static_cast<cudaStream_t>(stream), L > 0 ? 5 : 0);
+    StageTimer t(p, NURSD_STAGE_POINTS, s, L > 0 ? 5 : 0);
     rc = from_cuda(launch_points(a, p->bin_of, p->i0_orig, p->w_orig, p->counts, p->bin_start, p->sorted_l,
-                                 p->i0_sorted, p->w_sorted, static_cast<cudaStream_t>(stream), p->frac_orig,
-                                 p->frac_sorted, p->slot_of));
+                                 p->i0_sorted, p->w_sorted, s, p->frac_orig, p->frac_sorted, p->slot_of));
   }
   if (rc == NURSD_OK) p->L = L;
   return rc;
+}
+}  // namespace
+
+int nursd_set_points(nursd_plan_t p, int32_t L, const float* d_xy, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || L < 0 || L > p->maxL || (L > 0 && (!d_xy || !aligned(d_xy, 8))))
+    return NURSD_ERR_INVALID_ARG;
+  return set_points_on(p, L, d_xy, static_cast<cudaStream_t>(stream));
 }
 
 int nursd_temporal_dft(nursd_plan_t p, int32_t L, const float* d_hist, nursd_c64* d_phasor, nursd_stream_t stream) {
@@ -824,6 +836,39 @@ int nursd_forward(nursd_plan_t p, const float* d_hist, void* d_out, nursd_stream
     rc = from_cuda(run_temporal(p, d_hist, reinterpret_cast<float*>(p->phasor), p->L, s, p->slot_of));
   }
   if (rc == NURSD_OK) rc = run_nufft1(p, p->phasor, p->U, s, true);
+  if (rc == NURSD_OK) rc = run_propagate(p, p->U, d_out, s);
+  return rc;
+}
+
+int nursd_reconstruct(nursd_plan_t p, int32_t L, const float* d_xy, const float* d_hist, void* d_out,
+                      nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || p->T <= 0 || L < 0 || L > p->maxL || !d_out || !aligned(d_out, 8))
+    return NURSD_ERR_INVALID_ARG;
+  if (L > 0 && (!d_xy || !aligned(d_xy, 8) || !d_hist || !aligned(d_hist, 16))) return NURSD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!p->side) {
+    if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return NURSD_ERR_CUDA;
+    }
+  }
+  // fork: the point sort waits for everything before this call on `stream`, then runs beside
+  // the temporal transform; the join orders it before the spread (and so before every later
+  // operation on `stream`)
+  int rc = from_cuda(cudaEventRecord(p->ev_fork, s));
+  if (rc == NURSD_OK) rc = from_cuda(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+  if (rc == NURSD_OK) rc = set_points_on(p, L, d_xy, p->side);
+  if (rc == NURSD_OK) rc = from_cuda(cudaEventRecord(p->ev_join, p->side));
+  if (rc != NURSD_OK) return rc;
+  {
+    StageTimer t(p, NURSD_STAGE_TEMPORAL, s, L > 0 ? 1 : 0);
+    rc = from_cuda(run_temporal(p, d_hist, reinterpret_cast<float*>(p->phasor), L, s));
+  }
+  const int rj = from_cuda(cudaStreamWaitEvent(s, p->ev_join, 0));  // join even if the temporal launch failed
+  if (rc == NURSD_OK) rc = rj;
+  if (rc == NURSD_OK) rc = run_nufft1(p, p->phasor, p->U, s);
   if (rc == NURSD_OK) rc = run_propagate(p, p->U, d_out, s);
   return rc;
 }

@@ -55,24 +55,29 @@ __global__ void points_prepare(const PointsArgs a, int2* __restrict__ i0_out, fl
 }
 
 // Exclusive scan of the bin counts in one CTA: bin_start[b] = first sorted slot of bin b.
-// The counts are staged in shared memory with coalesced loads (kScanChunk at a time);
-// each thread scans a contiguous run, the runs' totals are scanned with warp shuffles.
-constexpr int kScanThreads = 1024, kScanChunk = 8192;
+// The counts are staged in shared memory with coalesced loads (kScanChunk at a time), each
+// thread scans a contiguous run of `per` counts (runs padded by one word, so the threads of a
+// warp hit distinct banks), and the runs' totals are scanned with warp shuffles.  256 threads
+// and 17 KB: the CTA fits beside a resident tcgen05 temporal CTA.
+constexpr int kScanThreads = 256, kScanChunk = 4096;
+static_assert(kScanThreads % 32 == 0 && kScanThreads <= 1024 && kScanChunk % kScanThreads == 0, "scan shape");
 __global__ void __launch_bounds__(kScanThreads) points_scan(const int* __restrict__ counts, int nbins,
                                                            int* __restrict__ bin_start, int L) {
-  __shared__ int buf[kScanChunk];
-  __shared__ int warp_sum[kScanThreads / 32];
+  constexpr int per = kScanChunk / kScanThreads, nw = kScanThreads / 32;
+  __shared__ int buf[kScanThreads * (per + 1)];
+  __shared__ int warp_sum[nw];
   __shared__ int carry;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int per = kScanChunk / kScanThreads;
+  auto slot = [](int i) { return (i / per) * (per + 1) + i % per; };  // padded position of count i
   if (tid == 0) carry = 0;
   for (int c0 = 0; c0 < nbins; c0 += kScanChunk) {
     const int cn = min(kScanChunk, nbins - c0);
-    for (int i = tid; i < kScanChunk; i += kScanThreads) buf[i] = i < cn ? counts[c0 + i] : 0;
+    for (int i = tid; i < kScanChunk; i += kScanThreads) buf[slot(i)] = i < cn ? counts[c0 + i] : 0;
     __syncthreads();
+    int* run_p = buf + tid * (per + 1);
     int run = 0;
 #pragma unroll
-    for (int k = 0; k < per; ++k) run += buf[tid * per + k];
+    for (int k = 0; k < per; ++k) run += run_p[k];
     int incl = run;  // inclusive scan of the runs within the warp
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -81,27 +86,27 @@ __global__ void __launch_bounds__(kScanThreads) points_scan(const int* __restric
     }
     if (lane == 31) warp_sum[warp] = incl;
     __syncthreads();
-    if (warp == 0) {
-      int ws = warp_sum[lane];
+    if (warp == 0) {  // scan of the nw warp totals (lanes beyond them carry zeros)
+      const int ws = lane < nw ? warp_sum[lane] : 0;
       int wincl = ws;
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
         const int v = __shfl_up_sync(0xffffffffu, wincl, off);
         if (lane >= off) wincl += v;
       }
-      warp_sum[lane] = wincl - ws;  // exclusive
+      if (lane < nw) warp_sum[lane] = wincl - ws;  // exclusive
     }
     __syncthreads();
     int pos = carry + warp_sum[warp] + incl - run;
-    const int total = carry + warp_sum[kScanThreads / 32 - 1] + __shfl_sync(0xffffffffu, incl, 31);
+    const int total = carry + warp_sum[nw - 1] + __shfl_sync(0xffffffffu, incl, 31);
 #pragma unroll
     for (int k = 0; k < per; ++k) {
-      const int v = buf[tid * per + k];
-      buf[tid * per + k] = pos;
+      const int v = run_p[k];
+      run_p[k] = pos;
       pos += v;
     }
     __syncthreads();
-    for (int i = tid; i < cn; i += kScanThreads) bin_start[c0 + i] = buf[i];
+    for (int i = tid; i < cn; i += kScanThreads) bin_start[c0 + i] = buf[slot(i)];
     if (tid == kScanThreads - 1) carry = total;
     __syncthreads();
   }

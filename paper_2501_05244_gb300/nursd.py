@@ -33,6 +33,7 @@ EXPORTS = (
     "nursd_propagate", "nursd_forward_phasor", "nursd_forward", "nursd_sync_status",
     "nursd_profile_enable", "nursd_profile_read", "nursd_launch_count", "nursd_nufft1_noalloc",
     "nursd_forward_points", "nursd_adjoint", "nursd_grad_points", "srsd_forward", "nursd_forward_batched",
+    "nursd_reconstruct",
 )
 
 #: stage names in nursd_stage order
@@ -99,6 +100,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "nursd_grad_points": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
         "srsd_forward": (ctypes.c_int, [vp, vp, vp, vp]),
         "nursd_forward_batched": (ctypes.c_int, [vp, i32, ctypes.POINTER(_BatchItem), vp]),
+        "nursd_reconstruct": (ctypes.c_int, [vp, i32, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -282,6 +284,21 @@ class Plan:
             out = self.empty_output()
         o = _dev(out, self.out_dtype(), self.out_shape(), "out")
         _check(self._lib.nursd_forward(self._h, h, o, ctypes.c_void_p(_stream_ptr(stream))), "nursd_forward")
+        return out
+
+    def reconstruct(self, xy, hist, out=None, stream=None):
+        """Points and histograms -> volume in one call (set_points + forward, the point sort
+        overlapped with the temporal transform); the plan keeps the points."""
+        torch = _torch()
+        L = int(xy.shape[0])
+        p = _dev(xy, torch.float32, (L, 2), "xy")
+        h = _dev(hist, torch.float32, (L, self.T), "hist")
+        if out is None:
+            out = self.empty_output()
+        o = _dev(out, self.out_dtype(), self.out_shape(), "out")
+        _check(self._lib.nursd_reconstruct(self._h, L, p, h, o, ctypes.c_void_p(_stream_ptr(stream))),
+               "nursd_reconstruct")
+        self.L = L
         return out
 
     def forward_points(self, phasor, vox, out=None, stream=None):

@@ -278,3 +278,43 @@ def test_spad_lattice_variant_equals_direct_backprojection():
     vox = np.stack([(m[:, 0] - g.N // 2) * g.pitch, (m[:, 1] - g.N // 2) * g.pitch, g.depths[vz]], axis=1)
     ref = O.fbp_direct(P, wl.xy.astype(np.float64), om, vox)
     assert rel(V[vz, m[:, 1], m[:, 0]], ref) < TOL
+
+
+# ---------------------------------------------------- one-call reconstruction ---
+
+@pytest.mark.parametrize("wlf", [workload_c1, workload_mid])
+def test_reconstruct_equals_set_points_then_forward(wlf):
+    # the point sort runs on the plan's side stream beside the temporal transform; the
+    # result must be the two-call result bit for bit
+    wl = wlf()
+    g = wl.geom
+    plan = make_plan(g, len(wl.xy))
+    xy = torch.from_numpy(wl.xy).cuda()
+    h = torch.from_numpy(wl.hist).cuda()
+    plan.set_points(xy)
+    V1 = plan.forward(h).cpu().numpy()
+    V2 = plan.reconstruct(xy, h).cpu().numpy()
+    assert plan.sync_status() == 0
+    assert np.array_equal(V1, V2)
+
+
+def test_reconstruct_replays_in_a_cuda_graph():
+    wl = workload_mid()
+    g = wl.geom
+    plan = make_plan(g, len(wl.xy))
+    xy = torch.from_numpy(wl.xy).cuda()
+    h = torch.from_numpy(wl.hist).cuda()
+    out = plan.empty_output()
+    ref = plan.reconstruct(xy, h).cpu().numpy()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        plan.reconstruct(xy, h, out=out)  # warm-up on the capture stream
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        plan.reconstruct(xy, h, out=out)
+    out.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert plan.sync_status() == 0
+    assert np.array_equal(out.cpu().numpy(), ref)
