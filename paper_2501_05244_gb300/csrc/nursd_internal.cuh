@@ -112,7 +112,7 @@ cudaError_t launch_panel_bluestein(int logn, const PanelArgs& a, const float2* c
 cudaError_t launch_temporal_tc(const float* h, const void* Bh, const void* Bl, float* C, int L, int T, int twoF,
                                cudaStream_t s, const int* row_slot = nullptr);
 
-// The same transform with tcgen05.mma (temporal_umma.cu), for T % 64 == 0 and 2F in {32, 64, 128, 256}.
+// The same transform with tcgen05.mma (temporal_umma.cu), for T % 32 == 0 and 2F in {32, 64, 128, 256}.
 // TMA descriptors of B's head and tail ([2F][T] fp16) are encoded once per plan.
 struct TemporalMaps {
   CUtensorMap hi;

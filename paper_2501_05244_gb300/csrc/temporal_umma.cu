@@ -12,13 +12,14 @@
 //   0-3  epilogue: tcgen05.ld of the 128 x 2F accumulator (one row per thread), fp32 stores
 //        (row l to row row_slot[l] when a slot order is given);
 //        two accumulators in tensor memory, so a tile's epilogue overlaps the next tile's MMAs
-//   4-11 H producers: global loads three K-blocks ahead (~96 KB per SM in flight), fp16
-//        head/tail split, stores into the 128-byte-swizzled K-major operand layout
-//   12   B producer (one thread): TMA tiled copies of the 64 x 2F head and tail blocks
-//   13   MMA issuer (one thread): 4 k-steps of 16 per K-block, tcgen05.commit to the
+//   4-11 H producers: global loads six K-blocks ahead (~96 KB per SM in flight), fp16
+//        head/tail split, stores into the 64-byte-swizzled K-major operand layout
+//   12   B producer (one thread): TMA tiled copies of the 32 x 2F head and tail blocks
+//   13   MMA issuer (one thread): 2 k-steps of 16 per K-block, tcgen05.commit to the
 //        stage's "empty" barrier and, after the tile's last K-block, to the accumulator's
 //        "full" barrier
-// Stages (2) hold A_hi, A_lo (128 x 64 fp16 each) and B_hi, B_lo (2F x 64 fp16 each).
+// Four stages (K-blocks of 32) hold A_hi, A_lo (128 x 32 fp16 each) and B_hi, B_lo (2F x 32
+// fp16 each), so the next twiddle copies start three K-blocks before they are needed.
 // Every mbarrier wait is bounded: on time-out the waiting role sets an abort flag (and
 // status bit 4), every role stops issuing work, copies and MMAs in flight are drained,
 // and tensor memory is released before the CTA exits.
@@ -32,7 +33,7 @@
 namespace nursd {
 namespace {
 
-constexpr int kBM = 128, kBK = 64, kUStages = 2;
+constexpr int kBM = 128, kBK = 32, kUStages = 4;
 constexpr int kEpiWarps = 4, kCvtWarps = 8;
 constexpr int kProducerWarp = kEpiWarps + kCvtWarps, kMmaWarp = kProducerWarp + 1;
 constexpr int kUThreads = (kMmaWarp + 1) * 32;
@@ -40,8 +41,8 @@ constexpr long long kUSpin = 1LL << 22;
 
 template <int N2>
 struct UShape {
-  static constexpr int kA = kBM * 128;  // one A tile: 128 rows x 64 fp16
-  static constexpr int kB = N2 * 128;   // one B tile: N2 rows x 64 fp16
+  static constexpr int kA = kBM * 64;  // one A tile: 128 rows x 32 fp16 (64-byte rows)
+  static constexpr int kB = N2 * 64;   // one B tile: N2 rows x 32 fp16
   static constexpr int kStage = 2 * kA + 2 * kB;
   static constexpr int kAcc = N2 < 32 ? 32 : N2;  // tensor-memory columns per accumulator
   static constexpr size_t kSmem = 1024 + (size_t)kUStages * kStage + 512;
@@ -90,14 +91,15 @@ __device__ __forceinline__ void fence_before_sync() {
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
 }
 
-// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte swizzle layout
-// (rows of 128 bytes, 8-row groups 1024 bytes apart, tile base 1024-byte aligned).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+// Shared-memory matrix descriptor of a K-major operand tile in the 64-byte swizzle layout
+// (rows of 64 bytes whose 16-byte chunks are XOR-permuted by (row / 2) mod 4, 8-row groups
+// 512 bytes apart, tile base 1024-byte aligned).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t addr) {
   uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);  // start address
   d |= (uint64_t)1 << 16;                           // leading byte offset (unused for this layout)
-  d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset: next 8-row group
+  d |= (uint64_t)(512 >> 4) << 32;                  // stride byte offset: next 8-row group
   d |= (uint64_t)1 << 46;                           // descriptor version
-  d |= (uint64_t)2 << 61;                           // 128-byte swizzle
+  d |= (uint64_t)4 << 61;                           // 64-byte swizzle
   return d;
 }
 
@@ -224,30 +226,35 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
   } else if (warp < kEpiWarps + kCvtWarps) {
     // ---------------------------------------------------------------- H producers
     const int cw = warp - kEpiWarps, ct = cw * 32 + lane;
-    // task q < 4: row ct / 8 + 32 q of the tile, 16-byte chunk ct % 8 (8 consecutive K values)
-    const int r0 = ct >> 3, ch = ct & 7;
-    auto load = [&](float4 (&v)[8], int it) {
-      if (it >= my_iters) return;
-      const int j = it / nkb, kb = it - j * nkb;
-      const int m0 = ((int)blockIdx.x + j * (int)gridDim.x) * kBM;
-      const float* src = H + (size_t)(m0 + r0) * T + kb * kBK + ch * 8;
+    // task q < 2 of a K-block: row ct / 4 + 64 q of the tile, 16-byte chunk ct % 4 (8 consecutive K values)
+    const int r0 = ct >> 2, ch = ct & 3;
+    // a register set holds K-blocks 2 p and 2 p + 1 (4 float4 each)
+    auto load = [&](float4 (&v)[8], int pr) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const bool ok = m0 + r0 + 32 * q < L;
-        const float4* s4 = reinterpret_cast<const float4*>(src + (size_t)32 * q * T);
-        v[2 * q] = ok ? __ldg(s4) : make_float4(0.f, 0.f, 0.f, 0.f);
-        v[2 * q + 1] = ok ? __ldg(s4 + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int h = 0; h < 2; ++h) {
+        const int it = 2 * pr + h;
+        if (it >= my_iters) return;
+        const int j = it / nkb, kb = it - j * nkb;
+        const int m0 = ((int)blockIdx.x + j * (int)gridDim.x) * kBM;
+        const float* src = H + (size_t)(m0 + r0) * T + kb * kBK + ch * 8;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const bool ok = m0 + r0 + 64 * q < L;
+          const float4* s4 = reinterpret_cast<const float4*>(src + (size_t)64 * q * T);
+          v[4 * h + 2 * q] = ok ? __ldg(s4) : make_float4(0.f, 0.f, 0.f, 0.f);
+          v[4 * h + 2 * q + 1] = ok ? __ldg(s4 + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
       }
     };
-    auto stage = [&](const float4 (&v)[8], int it) -> bool {
+    auto stage_one = [&](const float4* v, int it) -> bool {
       const int st = it % kUStages, ph = (it / kUStages) & 1;
       if (!bar_wait(&ctl.empty[st], ph ^ 1, abort)) return false;
       unsigned char* ah = a_hi(st);
       unsigned char* al = a_lo(st);
       uint32_t any = 0;
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = r0 + 32 * q;
+      for (int q = 0; q < 2; ++q) {
+        const int r = r0 + 64 * q;
         const float4 x = v[2 * q], y = v[2 * q + 1];
         uint4 h, l;
         split2(x.x, x.y, h.x, l.x);
@@ -255,7 +262,7 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
         split2(y.x, y.y, h.z, l.z);
         split2(y.z, y.w, h.w, l.w);
         any |= (l.x | l.y | l.z | l.w) & 0x7fff7fffu;
-        const int off = r * 128 + ((ch ^ (r & 7)) << 4);
+        const int off = r * 64 + ((ch ^ ((r >> 1) & 3)) << 4);
         *reinterpret_cast<uint4*>(ah + off) = h;
         *reinterpret_cast<uint4*>(al + off) = l;
       }
@@ -268,18 +275,24 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
       }
       return true;
     };
-    // three register sets in rotation: K-blocks it + 1 .. it + 3 are in flight while `it` is staged
+    auto stage = [&](const float4 (&v)[8], int pr) -> bool {
+      const int it = 2 * pr;
+      if (!stage_one(v, it)) return false;
+      return it + 1 >= my_iters || stage_one(v + 4, it + 1);
+    };
+    // three register sets in rotation: six K-blocks (about 96 KB per SM) in flight
+    const int npairs = (my_iters + 1) / 2;
     float4 va[8], vb[8], vc[8];
     load(va, 0);
     load(vb, 1);
     load(vc, 2);
-    for (int it = 0; it < my_iters; it += 3) {
-      if (!stage(va, it)) break;
-      load(va, it + 3);
-      if (it + 1 >= my_iters || !stage(vb, it + 1)) break;
-      load(vb, it + 4);
-      if (it + 2 >= my_iters || !stage(vc, it + 2)) break;
-      load(vc, it + 5);
+    for (int pr = 0; pr < npairs; pr += 3) {
+      if (!stage(va, pr)) break;
+      load(va, pr + 3);
+      if (pr + 1 >= npairs || !stage(vb, pr + 1)) break;
+      load(vb, pr + 4);
+      if (pr + 2 >= npairs || !stage(vc, pr + 2)) break;
+      load(vc, pr + 5);
     }
   } else if (warp == kProducerWarp) {
     // ---------------------------------------------------------------- B producer
@@ -320,8 +333,8 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
           int lo = 0;
 #pragma unroll
           for (int w = 0; w < kCvtWarps; ++w) lo |= ctl.lo[st][w];
-          const uint64_t dah = sw128_desc(sa(a_hi(st))), dal = sw128_desc(sa(a_lo(st)));
-          const uint64_t dbh = sw128_desc(sa(b_hi(st))), dbl = sw128_desc(sa(b_lo(st)));
+          const uint64_t dah = sw64_desc(sa(a_hi(st))), dal = sw64_desc(sa(a_lo(st)));
+          const uint64_t dbh = sw64_desc(sa(b_hi(st))), dbl = sw64_desc(sa(b_lo(st)));
 #pragma unroll
           for (int kk = 0; kk < kBK / 16; ++kk) {  // 16 fp16 = 32 bytes along K per instruction
             const uint64_t adv = (uint64_t)(2 * kk);
@@ -368,7 +381,7 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// [rows][T] fp16, K-major, 64 x rows boxes in the 128-byte swizzle.
+// [rows][T] fp16, K-major, 32 x rows boxes in the 64-byte swizzle.
 bool encode_b(CUtensorMap* m, const void* ptr, int T, int rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
@@ -377,7 +390,7 @@ bool encode_b(CUtensorMap* m, const void* ptr, int T, int rows) {
   const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)rows};
   const cuuint32_t estr[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

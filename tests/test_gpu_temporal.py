@@ -1,6 +1,6 @@
 """GPU parity of the temporal transform (Eq. PF_Response with Eq. PFPacket) on both tensor-core forms.
 
-The tcgen05 form runs for T % 64 == 0 and 2F in {32, 64, 128, 256}; every other shape
+The tcgen05 form runs for T % 32 == 0 and 2F in {32, 64, 128, 256}; every other shape
 takes the mma.sync form.  Both split each operand into an fp16 head and tail, and a
 K-block of integer photon counts below 2048 skips the histogram-tail product, so the
 cases cover integer counts (tail skipped) and fractional values (tail used), ragged L
@@ -61,6 +61,12 @@ def test_temporal_tcgen05_shapes(F, kind):
 @pytest.mark.parametrize("L", [1, 127, 129])
 def test_temporal_short_inputs(L):
     assert run_case(L, 128, 128, "fractional", BASE_SEED + 70 + L) < 1e-5
+
+
+@pytest.mark.parametrize("T", [32, 96])
+def test_temporal_odd_k_block_counts(T):
+    # one K-block, and an odd number of K-blocks (the producers stage K-blocks in pairs)
+    assert run_case(700, T, 64, "fractional", BASE_SEED + 75 + T) < 1e-5
 
 
 @pytest.mark.parametrize("T,F", [(200, 16), (256, 24), (64, 256)])
