@@ -45,6 +45,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=60)
+    ap.add_argument("--no-graph", action="store_true", help="time eager steps instead of a captured CUDA graph")
     ap.add_argument("--no-rows", action="store_true",
                     help="skip the per-row measurements (type-2 voxels, SRSD, adjoint, gradients, batched)")
     ap.add_argument("--workload", choices=["spad", "grid128", "spad-z8", "spad-n128"], default="spad",
@@ -411,9 +412,30 @@ def run_ours(args, rank, world, local):
     if plan.sync_status() != 0:
         raise RuntimeError("device status error during warm-up")
 
-    # ---- timed region (device): K steps, events on the launching stream
-    plan.profile(True)
+    # One step captured as a CUDA graph (same kernels and launches; the replay avoids per-launch
+    # host and scheduling gaps between the 12 kernels of a step).  Eager steps if capture fails.
     launches0 = plan.launch_count
+    step()
+    launches_per_step = plan.launch_count - launches0
+    graph = None
+    if not args.no_graph:
+        try:
+            cap = torch.cuda.Stream()
+            cap.wait_stream(stream)
+            with torch.cuda.stream(cap):
+                step()
+            stream.wait_stream(cap)
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                step()
+            torch.cuda.synchronize()
+        except Exception:  # fall back to eager steps
+            graph = None
+            torch.cuda.synchronize()
+    run_step = graph.replay if graph is not None else step
+
+    # ---- timed region (device): K steps, events on the launching stream
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
@@ -421,15 +443,23 @@ def run_ours(args, rank, world, local):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        step()
+        run_step()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    launches = plan.launch_count - launches0
+    if plan.sync_status() != 0:
+        raise RuntimeError("device status error in the timed region")
+    launches = launches_per_step * args.steps
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps, dist, "cuda")
+
+    # ---- per-stage times: CUDA events around each stage of eager steps (outside the timed region)
+    plan.profile(True)
+    for _ in range(max(1, min(args.steps, 100))):
+        step()
+    torch.cuda.synchronize()
     stages = plan.profile_read()
     plan.profile(False)
-    ms = reduce_max(e0.elapsed_time(e1) / args.steps, dist, "cuda")
 
     # ---- end to end through the public API with host buffers (pinned), copies inside the timed region.
     # Each step uploads its histograms and samples, reconstructs and downloads the volume.  The
@@ -454,6 +484,10 @@ def run_ours(args, rank, world, local):
             dx[k % 2].copy_(h_xy, non_blocking=True)
             up[k % 2].record(copy)
 
+    # each step's reconstruction is an eager call here: a captured graph per buffer parity measured
+    # slower end to end (graph launches interleaved with the copy stream's waits)
+    recon = [lambda i=i: plan.reconstruct(dx[i], dh[i], out=do[i]) for i in range(2)]
+
     def e2e_run(steps):
         for e in done + down:
             e.record(stream)
@@ -463,7 +497,7 @@ def run_ours(args, rank, world, local):
                 upload(k + 1)
             stream.wait_event(up[k % 2])
             stream.wait_event(down[k % 2])  # this output buffer's previous download has finished
-            plan.reconstruct(dx[k % 2], dh[k % 2], out=do[k % 2])
+            recon[k % 2]()
             done[k % 2].record(stream)
             with torch.cuda.stream(copy):
                 copy.wait_event(done[k % 2])
@@ -511,6 +545,9 @@ def run_ours(args, rank, world, local):
                                 "spad-n128": "spad-n128: " + WORKLOAD.replace("256x256x128", "128x128x128")}[
                                     args.workload], "L": L, "T": g.T, "F": F, "N": N, "Z": Z, "M": M, "fine_n": plan.fine_n,
                    "parallelism": f"replicas x{world} (one reconstruction per GPU)",
+                   "launch": ("CUDA-graph replay of one nursd_reconstruct call (12 kernels)" if graph is not None
+                              else "eager nursd_reconstruct calls"),
+                   "stage_times": "CUDA events around each stage of 100 eager steps after the timed region",
                    "l2": "inputs larger than L2 (histograms 268 MB, transfer table %.2f GB); no flush" %
                          (plan.n_classes * F * Z * 8 / 1e9)},
         "recon_per_s": world * 1e3 / ms,
