@@ -762,17 +762,17 @@ __global__ void __launch_bounds__(R32Shape<LOGN, CP>::NT, R32Shape<LOGN, CP>::NT
         }
       }
     }
-    fft32_core<LOGN, CP, INV>(v, xbuf, j0, q, tw2, [&] {
-      // every thread has read the staged window: start the next panel's copy
-      cb += step_b;
-      cc += step_c;
-      if (cc >= nchunk) {
-        cc -= nchunk;
-        ++cb;
-      }
-      if (p + (int)gridDim.x < npanel) issue(cb, cc);
-      cp_async_commit();
-    });
+    __syncthreads();  // every thread holds its window: start the next panel's copy now, so it has
+                      // the whole transform to land
+    cb += step_b;
+    cc += step_c;
+    if (cc >= nchunk) {
+      cc -= nchunk;
+      ++cb;
+    }
+    if (p + (int)gridDim.x < npanel) issue(cb, cc);
+    cp_async_commit();
+    fft32_core<LOGN, CP, INV>(v, xbuf, j0, q, tw2, [] {});
     __syncthreads();  // every thread has read its stage-2 inputs
     store_bins32<LOGN, CP>(v, xbuf, j0, q);
     __syncthreads();
@@ -817,16 +817,16 @@ __global__ void __launch_bounds__(R32Shape<LOGN, CP>::NT, R32Shape<LOGN, CP>::NT
     for (int t = 0; t < 32; ++t) v[t] = rq[min((lpos + t * T) & (n - 1), a.nin) * CP];  // zero row outside
 #pragma unroll
     for (int t = 0; t < 32; ++t) v[t] = cmul(v[t], __ldg(cpre + min((lpos + t * T) & (n - 1), a.nin - 1)));
-    fft32_core<LOGN, CP, false>(v, xbuf, j0, q, tw2, [&] {
-      cb += step_b;
-      cc += step_c;
-      if (cc >= nchunk) {
-        cc -= nchunk;
-        ++cb;
-      }
-      if (p + (int)gridDim.x < npanel) issue(cb, cc);
-      cp_async_commit();
-    });
+    __syncthreads();  // every thread holds its window: start the next panel's copy
+    cb += step_b;
+    cc += step_c;
+    if (cc >= nchunk) {
+      cc -= nchunk;
+      ++cb;
+    }
+    if (p + (int)gridDim.x < npanel) issue(cb, cc);
+    cp_async_commit();
+    fft32_core<LOGN, CP, false>(v, xbuf, j0, q, tw2, [] {});
 #pragma unroll
     for (int m = 0; m < 32 / R2; ++m)
 #pragma unroll
