@@ -6,15 +6,15 @@
 // first footprint row), tile column major, so the samples that can touch the
 // tile -- first rows ty*16-w+1 .. ty*16+15 in this tile column and the one to
 // its left (a footprint of w <= 8 cells crosses at most one tile edge) -- are
-// two contiguous slot ranges.  The CTA stages them in shared memory (the 32
-// channels of each sample's phasor, its footprint origin and its x and y
-// weights) in chunks -- one round of loads when P is already in sorted-slot order,
+// two contiguous slot ranges.  The CTA stages them in shared memory in chunks
+// (the 32 channels of each sample's phasor, its footprint origin, its y weights
+// and its x weights laid out on the tile's 16 cells, zero where the footprint
+// misses a cell) -- one round of loads when P is already in sorted-slot order,
 // two when its rows are found through the sorted index -- and the warp for row y
-// adds the samples whose first row is in y-w+1 .. y (again two contiguous sub-ranges).  A sample's taps land on cells
-// o .. o+w-1 of the row, o = its first column minus the tile's; a warp-uniform
-// switch on o selects a fully unrolled update of the registers it touches.
-// Every window cell is written exactly once, and the summation order is the
-// sorted order, so results are reproducible run to run.
+// adds the samples whose first row is in y-w+1 .. y (again two contiguous
+// sub-ranges) to all 16 cells of its row with packed two-lane FMAs: no branch on
+// where the footprint starts.  Every window cell is written exactly once, and
+// the summation order is the sorted order, so results are reproducible run to run.
 #include <algorithm>
 
 #include "nursd_internal.cuh"
@@ -26,14 +26,18 @@ constexpr int kWarps = kTile;  // one warp per tile row
 constexpr int kCh = 32;        // channels per CTA
 constexpr int kCap = 256;      // samples staged per chunk
 
+// Cells of the tile row in packed pairs: for cell 2j + h, lane-wise, acc_re[j] holds the real part
+// in component h and acc_im[j] the imaginary part, so one fma.rn.f32x2 updates two cells.
+constexpr int kPairs = kTile / 2;
+constexpr int kRowPad = 8;                // x-weight row: cell c of the tile at index kRowPad + c
+constexpr int kRowLen = kRowPad + kTile;  // 24 floats; indices below kRowPad are never read
+
 struct SpreadSmem {
-  float2 p[kCap][kCh];   // phasor slices
-  float wx[kCap][8];     // x weights (first w used)
-  float wy[kCap][8];     // y weights
-  float wt[kCap][kTile]; // y weight of each row of the tile (0 where the footprint misses it)
-  int o[kCap];           // first footprint column relative to the tile's
-  int oy[kCap];          // first footprint row relative to the tile's
-  int l[kCap];           // sample index (row of P)
+  float2 p[kCap][kCh];    // phasor slices
+  float wx[kCap][kRowLen];  // x weight of each tile cell (0 where the footprint misses it)
+  float wy[kCap][8];      // y weights
+  int2 org[kCap];         // first footprint column and row relative to the tile's
+  int l[kCap];            // sample index (row of P)
 };
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc, bool valid) {
@@ -41,36 +45,20 @@ __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc, bool
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(valid ? 8 : 0) : "memory");
 }
 
-// acc[O + c] += v * wx[c] for the taps c < KW that fall inside the row (O is a constant).
-template <int KW, int O>
-__device__ __forceinline__ void add_taps(float2 (&acc)[kTile], float2 v, const float (&wx)[8]) {
-#pragma unroll
-  for (int c = 0; c < KW; ++c) {
-    if (O + c >= 0 && O + c < kTile) {
-      acc[O + c].x = fmaf(v.x, wx[c], acc[O + c].x);
-      acc[O + c].y = fmaf(v.y, wx[c], acc[O + c].y);
-    }
-  }
+// d = a * b + c, lane-wise on two fp32 values, one instruction.
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+  float2 r;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+      " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return r;
 }
 
-template <int KW>
-__device__ __forceinline__ void add_sample(float2 (&acc)[kTile], int o, float2 v, const float (&wx)[8]) {
-  switch (o) {
-#define NURSD_TAP_CASE(O) \
-  case O:                 \
-    add_taps<KW, O>(acc, v, wx); \
-    break;
-    NURSD_TAP_CASE(-7) NURSD_TAP_CASE(-6) NURSD_TAP_CASE(-5) NURSD_TAP_CASE(-4) NURSD_TAP_CASE(-3)
-    NURSD_TAP_CASE(-2) NURSD_TAP_CASE(-1) NURSD_TAP_CASE(0) NURSD_TAP_CASE(1) NURSD_TAP_CASE(2)
-    NURSD_TAP_CASE(3) NURSD_TAP_CASE(4) NURSD_TAP_CASE(5) NURSD_TAP_CASE(6) NURSD_TAP_CASE(7)
-    NURSD_TAP_CASE(8) NURSD_TAP_CASE(9) NURSD_TAP_CASE(10) NURSD_TAP_CASE(11) NURSD_TAP_CASE(12)
-    NURSD_TAP_CASE(13) NURSD_TAP_CASE(14) NURSD_TAP_CASE(15)
-#undef NURSD_TAP_CASE
-    default:
-      break;  // the footprint ends left of the tile
-  }
-}
-
+// One CTA per (tile, group of 32 channels); warp = tile row, lane = channel.  A staged sample
+// carries its x weights laid out on the tile's 16 cells (zeros outside its footprint), so the
+// warp adds it to every cell of its row with 16 packed FMAs and no branch on the offset; a
+// zero weight leaves a cell's sum unchanged, so the result equals the footprint-only sum.
 template <int KW>
 __global__ void __launch_bounds__(kWarps * 32, 2) spread_kernel(const float2* __restrict__ P, int F,
                                                                 const int* __restrict__ bin_start,
@@ -97,15 +85,18 @@ __global__ void __launch_bounds__(kWarps * 32, 2) spread_kernel(const float2* __
   const int wb0 = nA + bin_start[tx * W + wlo] - bS;
   const int wb1 = nA + bin_start[tx * W + y + 1] - bS;
 
-  float2 acc[kTile];
+  float2 acc_re[kPairs], acc_im[kPairs];
 #pragma unroll
-  for (int c = 0; c < kTile; ++c) acc[c] = make_float2(0.f, 0.f);
+  for (int j = 0; j < kPairs; ++j) {
+    acc_re[j] = make_float2(0.f, 0.f);
+    acc_im[j] = make_float2(0.f, 0.f);
+  }
   const bool live = f0 + lane < F;
   for (int c0 = 0; c0 < n; c0 += kCap) {
     const int cn = min(kCap, n - c0);
     __syncthreads();  // the previous chunk has been consumed
-    // phase 1, one thread per sample (all loads in flight at once): index, origin, weights; when P
-    // is in slot order its copies need no index and start here too
+    // one thread per sample (all loads in flight at once): index, origin, weights; when P is in
+    // slot order its copies need no index and start here too
     if (!sorted_l)
       for (int s = warp; s < cn; s += kWarps) {
         const int v = c0 + s;
@@ -121,54 +112,60 @@ __global__ void __launch_bounds__(kWarps * 32, 2) spread_kernel(const float2* __
       float wv[2 * KW];
 #pragma unroll
       for (int t = 0; t < 2 * KW; ++t) wv[t] = __ldg(w + t);
+      const int ox = o.x - col0;
       sm.l[s] = l;
-      sm.o[s] = o.x - col0;
-      sm.oy[s] = o.y - ty * kTile;
+      sm.org[s] = make_int2(ox, o.y - ty * kTile);
+      float4* row = reinterpret_cast<float4*>(&sm.wx[s][0]);
+#pragma unroll
+      for (int q = 0; q < kRowLen / 4; ++q) row[q] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int t = 0; t < KW; ++t) {
-        sm.wx[s][t] = wv[t];
+        const int c = kRowPad + ox + t;  // cells left of the tile fall below kRowPad, right of it past the row
+        if (c >= 0 && c < kRowLen) sm.wx[s][c] = wv[t];
         sm.wy[s][t] = wv[KW + t];
       }
     }
-    __syncthreads();
-    // phase 2, one warp per sample: its 32 channels of P (sample order), and its y weight for each tile row
-    for (int s = warp; s < cn; s += kWarps) {
-      if (sorted_l) cp_async8(&sm.p[s][lane], live ? P + (size_t)sm.l[s] * F + f0 + lane : P, live);
-      if (lane < kTile) {
-        const int d = lane - sm.oy[s];
-        sm.wt[s][lane] = (d >= 0 && d < KW) ? sm.wy[s][d] : 0.f;
-      }
+    if (sorted_l) {  // the phasor rows are found through the sample indices just stored
+      __syncthreads();
+      for (int s = warp; s < cn; s += kWarps) cp_async8(&sm.p[s][lane], live ? P + (size_t)sm.l[s] * F + f0 + lane : P, live);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     const int c1 = c0 + cn;
-    auto visit = [&](int s) {
-      const float wyv = sm.wt[s][warp];
-      float2 pv = sm.p[s][lane];
-      pv.x *= wyv;
-      pv.y *= wyv;
-      float wx[8];
-      const float4 w0 = *reinterpret_cast<const float4*>(&sm.wx[s][0]);
-      const float4 w1 = *reinterpret_cast<const float4*>(&sm.wx[s][4]);
-      wx[0] = w0.x; wx[1] = w0.y; wx[2] = w0.z; wx[3] = w0.w;
-      wx[4] = w1.x; wx[5] = w1.y; wx[6] = w1.z; wx[7] = w1.w;
-      add_sample<KW>(acc, sm.o[s], pv, wx);
+    auto visit = [&](int s, int2 og) {
+      const float wyv = sm.wy[s][warp - og.y];  // the warp's row is footprint row warp - oy (0 .. w-1)
+      const float2 pv = sm.p[s][lane];
+      const float2 re = make_float2(pv.x * wyv, pv.x * wyv), im = make_float2(pv.y * wyv, pv.y * wyv);
+      const float4* row = reinterpret_cast<const float4*>(&sm.wx[s][kRowPad]);
+#pragma unroll
+      for (int q = 0; q < kTile / 4; ++q) {
+        const float4 wq = row[q];
+        acc_re[2 * q] = pfma(re, make_float2(wq.x, wq.y), acc_re[2 * q]);
+        acc_im[2 * q] = pfma(im, make_float2(wq.x, wq.y), acc_im[2 * q]);
+        acc_re[2 * q + 1] = pfma(re, make_float2(wq.z, wq.w), acc_re[2 * q + 1]);
+        acc_im[2 * q + 1] = pfma(im, make_float2(wq.z, wq.w), acc_im[2 * q + 1]);
+      }
     };
     {  // left tile column: only samples whose footprint reaches this tile
       const int s1 = min(wa1, c1) - c0;
-      for (int s = max(wa0, c0) - c0; s < s1; ++s)
-        if (sm.o[s] > -KW) visit(s);
+      for (int s = max(wa0, c0) - c0; s < s1; ++s) {
+        const int2 og = sm.org[s];
+        if (og.x > -KW) visit(s, og);
+      }
     }
     {  // this tile column
       const int s1 = min(wb1, c1) - c0;
-      for (int s = max(wb0, c0) - c0; s < s1; ++s) visit(s);
+      for (int s = max(wb0, c0) - c0; s < s1; ++s) visit(s, sm.org[s]);
     }
   }
   if (live) {
     float2* dst = fine + ((size_t)y * W + col0) * F + f0 + lane;
 #pragma unroll
-    for (int c = 0; c < kTile; ++c) dst[(size_t)c * F] = acc[c];
+    for (int j = 0; j < kPairs; ++j) {
+      dst[(size_t)(2 * j) * F] = make_float2(acc_re[j].x, acc_im[j].x);
+      dst[(size_t)(2 * j + 1) * F] = make_float2(acc_re[j].y, acc_im[j].y);
+    }
   }
 }
 
