@@ -313,7 +313,7 @@ int64_t nursd_launch_count(nursd_plan_t plan);
  *
  * Its scratch is one fixed 24 MiB device array inside libnursd, present on
  * every GPU that loads the library until the process exits.  Per call it needs
- * 4M + 4 + L(24 + 16w) + 12 W tiles + 4 + 8 W F (W + M) bytes plus
+ * 4M + 4 + L(24 + 16w) + 24 W tiles + 4 + 8 W F (W + M) bytes plus
  * alignment, with W = 16 ceil((2N + w + 2)/16) and tiles = W/16 (for example
  * N = 64, F = 32, L = 16,384 and w = 6 take about 12 MiB); larger requests
  * return NURSD_ERR_UNSUPPORTED before any device work.

@@ -149,7 +149,7 @@ struct PointsArgs {
   float beta;                     // ES kernel shape
   int* status;                    // device error word
 };
-// Prepare and sort the relay samples by bin = (tile column, footprint row),
+// Prepare and sort the relay samples by bin = (tile column, edge flag, footprint row),
 // nbins = points_bins(W, tiles).  Scratch in original order: bin_of [L],
 // i0_orig [L], w_orig [L][2w]; counts needs 2*nbins ints.  Sorted outputs:
 // sorted_l [L] (original index), i0_sorted, w_sorted, and bin_start [nbins+1].

@@ -5,9 +5,10 @@
 // because |u| reaches sigma N / 2 = 256 cells and the fractional part must stay
 // exact to ~1e-9.  Its footprint is the w cells i0..i0+w-1, i0 = ceil(u - w/2),
 // with ES weights phi(2 (i - u) / w), phi(z) = exp(beta (sqrt(1 - z^2) - 1)).
-// Samples are then sorted by bin = (16-cell tile column, first footprint row), tile
-// column major, so the samples of one tile column over a run of rows are one
-// contiguous slot range:
+// Samples are then sorted by bin = (16-cell tile column, edge flag, first footprint
+// row), where the edge flag marks footprints that cross into the next tile column,
+// so the samples of one tile column (and of its edge part) over a run of rows are
+// one contiguous slot range:
 // counts, one exclusive scan, a scatter, an insertion sort of each (small) bin
 // by sample index and a gather of the per-sample data into sorted order.  The
 // order inside every bin is thus fixed, so the spread -- and the FP32 rounding
@@ -49,7 +50,9 @@ __global__ void points_prepare(const PointsArgs a, int2* __restrict__ i0_out, fl
   const int rx = min(max(ix - a.g0, 0), a.W - 1), ry = min(max(iy - a.g0, 0), a.W - 1);
   i0_out[l] = make_int2(rx, ry);
   if (frac_out) frac_out[l] = make_float2((float)(ux - ix), (float)(uy - iy));
-  const int bin = (rx / kTile) * a.W + ry;  // (tile column, footprint row)
+  // (tile column, whether the footprint crosses into the next tile column, footprint row)
+  const int edge = (rx % kTile) + a.width > kTile ? 1 : 0;
+  const int bin = ((rx / kTile) * 2 + edge) * a.W + ry;
   bin_of[l] = bin;
   atomicAdd(counts + bin, 1);
 }
@@ -171,7 +174,7 @@ __global__ void points_gather(const int* __restrict__ sorted_l, int L, int width
 
 }  // namespace
 
-int points_bins(int W, int tiles) { return W * tiles; }
+int points_bins(int W, int tiles) { return 2 * W * tiles; }
 
 cudaError_t launch_points(const PointsArgs& a, int* bin_of, int2* i0_orig, float* w_orig, int* counts,
                           int* bin_start, int* sorted_l, int2* i0_sorted, float* w_sorted, cudaStream_t s,

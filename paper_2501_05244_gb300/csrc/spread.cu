@@ -3,18 +3,21 @@
 // No atomics: one CTA owns a 16 x 16-cell tile of the fine-grid window for 32
 // channels; each of its 16 warps owns one tile row, each lane one channel, and
 // the row's 16 cells live in registers.  Samples are binned by (tile column,
-// first footprint row), tile column major, so the samples that can touch the
-// tile -- first rows ty*16-w+1 .. ty*16+15 in this tile column and the one to
-// its left (a footprint of w <= 8 cells crosses at most one tile edge) -- are
-// two contiguous slot ranges.  The CTA stages them in shared memory in chunks
-// (the 32 channels of each sample's phasor, its footprint origin, its y weights
-// and its x weights laid out on the tile's 16 cells, zero where the footprint
-// misses a cell) -- one round of loads when P is already in sorted-slot order,
-// two when its rows are found through the sorted index -- and the warp for row y
-// adds the samples whose first row is in y-w+1 .. y (again two contiguous
-// sub-ranges) to all 16 cells of its row with packed two-lane FMAs: no branch on
-// where the footprint starts.  Every window cell is written exactly once, and
-// the summation order is the sorted order, so results are reproducible run to run.
+// edge flag, first footprint row), tile column major, the edge flag marking
+// footprints that cross into the next tile column.  So the samples that touch
+// the tile -- first rows ty*16-w+1 .. ty*16+15 in this tile column, and in the
+// edge part of the column to its left (a footprint of w <= 8 cells crosses at
+// most one tile edge) -- are three contiguous slot ranges, none holding a sample
+// that misses the tile.  The CTA stages them in shared memory in chunks (the 32
+// channels of each sample's phasor, its footprint origin, its y weights and its
+// x weights laid out on the tile's 16 cells, zero where the footprint misses a
+// cell) -- one round of loads when P is already in sorted-slot order, two when
+// its rows are found through the sorted index -- and the warp for row y adds the
+// samples whose first row is in y-w+1 .. y (again contiguous sub-ranges) with
+// packed two-lane FMAs over each 8-cell half of its row that the footprint
+// reaches: no branch on where the footprint starts.  Every window cell is
+// written exactly once, and the summation order is the sorted order, so results
+// are reproducible run to run.
 #include <algorithm>
 
 #include "nursd_internal.cuh"
@@ -36,7 +39,7 @@ struct SpreadSmem {
   float2 p[kCap][kCh];    // phasor slices
   float wx[kCap][kRowLen];  // x weight of each tile cell (0 where the footprint misses it)
   float wy[kCap][8];      // y weights
-  int2 org[kCap];         // first footprint column and row relative to the tile's
+  int2 org[kCap];         // halves of the tile row reached (bit 0: cells 0..7, bit 1: 8..15), first row rel. to the tile's
   int l[kCap];            // sample index (row of P)
 };
 
@@ -72,18 +75,24 @@ __global__ void __launch_bounds__(kWarps * 32, 2) spread_kernel(const float2* __
   const int ty = blockIdx.x / tiles, tx = blockIdx.x % tiles;
   const int f0 = blockIdx.y * kCh;
   const int y = ty * kTile + warp, col0 = tx * kTile;
-  // slot ranges of the two tile columns over first rows rlo .. rhi (bin = column * W + row)
+  // Slot ranges over first rows rlo .. rhi (bin = (column * 2 + edge) * W + row): the left
+  // column's edge part (every such footprint reaches this tile), then this column's interior
+  // and edge parts; v indexes their concatenation.
   const int rlo = max(ty * kTile - KW + 1, 0), rhi1 = ty * kTile + kTile;
-  const int aS = tx > 0 ? bin_start[(tx - 1) * W + rlo] : 0;
-  const int nA = tx > 0 ? bin_start[(tx - 1) * W + rhi1] - aS : 0;
-  const int bS = bin_start[tx * W + rlo];
-  const int n = nA + bin_start[tx * W + rhi1] - bS;
-  // this warp's samples (first rows wlo .. y), as indices into the concatenated ranges
+  const int* bsA = bin_start + ((tx - 1) * 2 + 1) * W;  // read only when tx > 0
+  const int* bsB = bin_start + (tx * 2) * W;
+  const int* bsC = bin_start + (tx * 2 + 1) * W;
+  const int aS = tx > 0 ? bsA[rlo] : 0, nA = tx > 0 ? bsA[rhi1] - aS : 0;
+  const int bS = bsB[rlo], nB = bsB[rhi1] - bS;
+  const int cS = bsC[rlo], nAB = nA + nB;
+  const int n = nAB + bsC[rhi1] - cS;
+  // this warp's samples (first rows wlo .. y) in each range, as indices v
   const int wlo = max(y - KW + 1, 0);
-  const int wa0 = tx > 0 ? bin_start[(tx - 1) * W + wlo] - aS : 0;
-  const int wa1 = tx > 0 ? bin_start[(tx - 1) * W + y + 1] - aS : 0;
-  const int wb0 = nA + bin_start[tx * W + wlo] - bS;
-  const int wb1 = nA + bin_start[tx * W + y + 1] - bS;
+  int2 wr[3];
+  wr[0] = tx > 0 ? make_int2(bsA[wlo] - aS, bsA[y + 1] - aS) : make_int2(0, 0);
+  wr[1] = make_int2(nA + bsB[wlo] - bS, nA + bsB[y + 1] - bS);
+  wr[2] = make_int2(nAB + bsC[wlo] - cS, nAB + bsC[y + 1] - cS);
+  auto slot_of = [&](int v) { return v < nA ? aS + v : (v < nAB ? bS + (v - nA) : cS + (v - nAB)); };
 
   float2 acc_re[kPairs], acc_im[kPairs];
 #pragma unroll
@@ -99,13 +108,11 @@ __global__ void __launch_bounds__(kWarps * 32, 2) spread_kernel(const float2* __
     // slot order its copies need no index and start here too
     if (!sorted_l)
       for (int s = warp; s < cn; s += kWarps) {
-        const int v = c0 + s;
-        const int slot = v < nA ? aS + v : bS + (v - nA);
+        const int slot = slot_of(c0 + s);
         cp_async8(&sm.p[s][lane], live ? P + (size_t)slot * F + f0 + lane : P, live);
       }
     for (int s = threadIdx.x; s < cn; s += kWarps * 32) {
-      const int v = c0 + s;
-      const int slot = v < nA ? aS + v : bS + (v - nA);
+      const int slot = slot_of(c0 + s);
       const int l = sorted_l ? __ldg(sorted_l + slot) : slot;
       const int2 o = __ldg(i0 + slot);
       const float* w = wts + (size_t)slot * 2 * KW;
@@ -113,8 +120,10 @@ __global__ void __launch_bounds__(kWarps * 32, 2) spread_kernel(const float2* __
 #pragma unroll
       for (int t = 0; t < 2 * KW; ++t) wv[t] = __ldg(w + t);
       const int ox = o.x - col0;
+      // halves of the tile row (cells 0..7, 8..15) that the footprint ox .. ox+w-1 reaches (at least one)
+      const int halves = (ox < kTile / 2 && ox + KW > 0 ? 1 : 0) | (ox < kTile && ox + KW > kTile / 2 ? 2 : 0);
       sm.l[s] = l;
-      sm.org[s] = make_int2(ox, o.y - ty * kTile);
+      sm.org[s] = make_int2(halves, o.y - ty * kTile);
       float4* row = reinterpret_cast<float4*>(&sm.wx[s][0]);
 #pragma unroll
       for (int q = 0; q < kRowLen / 4; ++q) row[q] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -139,24 +148,24 @@ __global__ void __launch_bounds__(kWarps * 32, 2) spread_kernel(const float2* __
       const float2 re = make_float2(pv.x * wyv, pv.x * wyv), im = make_float2(pv.y * wyv, pv.y * wyv);
       const float4* row = reinterpret_cast<const float4*>(&sm.wx[s][kRowPad]);
 #pragma unroll
-      for (int q = 0; q < kTile / 4; ++q) {
-        const float4 wq = row[q];
-        acc_re[2 * q] = pfma(re, make_float2(wq.x, wq.y), acc_re[2 * q]);
-        acc_im[2 * q] = pfma(im, make_float2(wq.x, wq.y), acc_im[2 * q]);
-        acc_re[2 * q + 1] = pfma(re, make_float2(wq.z, wq.w), acc_re[2 * q + 1]);
-        acc_im[2 * q + 1] = pfma(im, make_float2(wq.z, wq.w), acc_im[2 * q + 1]);
+      for (int h = 0; h < 2; ++h) {
+        if (og.x & (1 << h)) {  // warp-uniform: this half of the row is reached
+#pragma unroll
+          for (int q = 2 * h; q < 2 * h + 2; ++q) {
+            const float4 wq = row[q];
+            acc_re[2 * q] = pfma(re, make_float2(wq.x, wq.y), acc_re[2 * q]);
+            acc_im[2 * q] = pfma(im, make_float2(wq.x, wq.y), acc_im[2 * q]);
+            acc_re[2 * q + 1] = pfma(re, make_float2(wq.z, wq.w), acc_re[2 * q + 1]);
+            acc_im[2 * q + 1] = pfma(im, make_float2(wq.z, wq.w), acc_im[2 * q + 1]);
+          }
+        }
       }
     };
-    {  // left tile column: only samples whose footprint reaches this tile
-      const int s1 = min(wa1, c1) - c0;
-      for (int s = max(wa0, c0) - c0; s < s1; ++s) {
-        const int2 og = sm.org[s];
-        if (og.x > -KW) visit(s, og);
-      }
-    }
-    {  // this tile column
-      const int s1 = min(wb1, c1) - c0;
-      for (int s = max(wb0, c0) - c0; s < s1; ++s) visit(s, sm.org[s]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const int s1 = min(wr[r].y, c1) - c0;
+#pragma unroll 1
+      for (int s = max(wr[r].x, c0) - c0; s < s1; ++s) visit(s, sm.org[s]);
     }
   }
   if (live) {
