@@ -1,11 +1,11 @@
 // NUFFT type-1 spreading (Sec. 6, step 1): b[g][f] = sum_l P[l][f] phi_x phi_y.
 //
-// No atomics: one CTA owns a 16 x 16-cell tile of the fine-grid window for 32
-// channels; each of its 16 warps owns one tile row, each lane one channel, and
-// the row's 16 cells live in registers.  Samples are binned by (tile column,
+// No atomics: one CTA owns a tile of the fine-grid window 16 cells wide and 8
+// rows high, for 32 channels; each of its 8 warps owns one tile row, each lane
+// one channel, and the row's 16 cells live in registers.  Samples are binned by (tile column,
 // edge flag, first footprint row), tile column major, the edge flag marking
 // footprints that cross into the next tile column.  So the samples that touch
-// the tile -- first rows ty*16-w+1 .. ty*16+15 in this tile column, and in the
+// the tile -- first rows ty*8-w+1 .. ty*8+7 in this tile column, and in the
 // edge part of the column to its left (a footprint of w <= 8 cells crosses at
 // most one tile edge) -- are three contiguous slot ranges, none holding a sample
 // that misses the tile.  The CTA stages them in shared memory in chunks (the 32
@@ -25,9 +25,10 @@
 namespace nursd {
 namespace {
 
-constexpr int kWarps = kTile;  // one warp per tile row
+constexpr int kRows = 8;       // tile height (rows); the tile is kTile cells wide
+constexpr int kWarps = kRows;  // one warp per tile row
 constexpr int kCh = 32;        // channels per CTA
-constexpr int kCap = 256;      // samples staged per chunk
+constexpr int kCap = 128;      // samples staged per chunk
 
 // Cells of the tile row in packed pairs: for cell 2j + h, lane-wise, acc_re[j] holds the real part
 // in component h and acc_im[j] the imaginary part, so one fma.rn.f32x2 updates two cells.
@@ -63,7 +64,7 @@ __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
 // warp adds it to every cell of its row with 16 packed FMAs and no branch on the offset; a
 // zero weight leaves a cell's sum unchanged, so the result equals the footprint-only sum.
 template <int KW>
-__global__ void __launch_bounds__(kWarps * 32, 2) spread_kernel(const float2* __restrict__ P, int F,
+__global__ void __launch_bounds__(kWarps * 32, 4) spread_kernel(const float2* __restrict__ P, int F,
                                                                 const int* __restrict__ bin_start,
                                                                 const int* __restrict__ sorted_l,
                                                                 const int2* __restrict__ i0,
@@ -74,11 +75,11 @@ __global__ void __launch_bounds__(kWarps * 32, 2) spread_kernel(const float2* __
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ty = blockIdx.x / tiles, tx = blockIdx.x % tiles;
   const int f0 = blockIdx.y * kCh;
-  const int y = ty * kTile + warp, col0 = tx * kTile;
+  const int y = ty * kRows + warp, col0 = tx * kTile;
   // Slot ranges over first rows rlo .. rhi (bin = (column * 2 + edge) * W + row): the left
   // column's edge part (every such footprint reaches this tile), then this column's interior
   // and edge parts; v indexes their concatenation.
-  const int rlo = max(ty * kTile - KW + 1, 0), rhi1 = ty * kTile + kTile;
+  const int rlo = max(ty * kRows - KW + 1, 0), rhi1 = ty * kRows + kRows;
   const int* bsA = bin_start + ((tx - 1) * 2 + 1) * W;  // read only when tx > 0
   const int* bsB = bin_start + (tx * 2) * W;
   const int* bsC = bin_start + (tx * 2 + 1) * W;
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) spread_kernel(const float2* __
       // halves of the tile row (cells 0..7, 8..15) that the footprint ox .. ox+w-1 reaches (at least one)
       const int halves = (ox < kTile / 2 && ox + KW > 0 ? 1 : 0) | (ox < kTile && ox + KW > kTile / 2 ? 2 : 0);
       sm.l[s] = l;
-      sm.org[s] = make_int2(halves, o.y - ty * kTile);
+      sm.org[s] = make_int2(halves, o.y - ty * kRows);
       float4* row = reinterpret_cast<float4*>(&sm.wx[s][0]);
 #pragma unroll
       for (int q = 0; q < kRowLen / 4; ++q) row[q] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -188,7 +189,7 @@ cudaError_t launch_kw(const float2* P, int F, const int* bin_start, const int* s
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  dim3 grid(tiles * tiles, (F + kCh - 1) / kCh);
+  dim3 grid((W / kRows) * tiles, (F + kCh - 1) / kCh);
   spread_kernel<KW><<<grid, kWarps * 32, smem, s>>>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine);
   return cudaGetLastError();
 }
