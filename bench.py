@@ -219,8 +219,10 @@ def _time(fn, steps, warmup, stream):
     return e0.elapsed_time(e1) / steps
 
 
-def _stage_ms(plan):
-    return {k: v[0] / max(v[1], 1) for k, v in plan.profile_read().items() if v[1]}
+def _stage_ms(plan, calls):
+    """Per-call stage times (ms) over the `calls` calls made since profiling was enabled; a stage
+    that runs as several launches per call (channel or depth groups) is summed over them."""
+    return {k: v[0] / calls for k, v in plan.profile_read().items() if v[1]}
 
 
 def measure_rows(wl, peak):
@@ -258,7 +260,7 @@ def measure_rows(wl, peak):
         out = torch.empty((g.Z, K), dtype=torch.complex64, device="cuda")
         plan.profile(True)
         ms = _time(lambda: plan.forward_points(P, vox, out), 10, 2, stream)
-        st = _stage_ms(plan)
+        st = _stage_ms(plan, 12)
         assert plan.sync_status() == 0
         plan.close()
         units = g.Z * K * g.F
@@ -274,11 +276,11 @@ def measure_rows(wl, peak):
         out = plan.empty_output()
         plan.profile(True)
         ms = _time(lambda: plan.srsd_forward(P, out), 3, 1, stream)
-        prof = plan.profile_read()
+        prof = plan.profile_read()  # 4 calls: the warm-up and the 3 timed
         plan.close()
         M, F, Z = 2 * g.N, g.F, len(depths)
         ncls = (M // 2 + 1) * (M // 2 + 2) // 2
-        s_ms = prof["srsd"][0] / 3
+        s_ms = prof["srsd"][0] / 4
         bytes_ = Z * (5 * M * M * F * 8 + ncls * F * 8 + M * M * 8) + 2 * 2 * M * M * F * 8
         flops = Z * 2 * (M * F) * 2 * 5 * (2 * M) * np.log2(2 * M)
         units = Z * g.N * g.N * F
@@ -287,7 +289,7 @@ def measure_rows(wl, peak):
                 "srsd_stage": {"ms": s_ms, "algorithmic_bytes": bytes_, "achieved_gbs": bytes_ / (s_ms / 1e3) / 1e9,
                                "hbm_frac": bytes_ / (s_ms / 1e3) / 1e9 / peak,
                                "fft_tflops": flops / (s_ms / 1e3) / 1e12},
-                "stages_ms": {k: v[0] / 3 for k, v in prof.items() if v[1]}}
+                "stages_ms": {k: v[0] / 4 for k, v in prof.items() if v[1]}}
 
     def adjoint():
         plan = nursd.Plan(g.N, g.pitch, g.center, g.depths, om, wt, max_points=L, adjoint=True)
@@ -298,7 +300,7 @@ def measure_rows(wl, peak):
         out = torch.empty((L, g.F), dtype=torch.complex64, device="cuda")
         plan.profile(True)
         ms = _time(lambda: plan.adjoint(V, out), 10, 2, stream)
-        st = _stage_ms(plan)
+        st = _stage_ms(plan, 12)
         plan.close()
         units = g.Z * g.N * g.N * g.F
         return {"workload": "spad-65k adjoint: 256^2 x 128 volume -> 65,536 x 128 phasors", "ms": ms,
@@ -320,7 +322,7 @@ def measure_rows(wl, peak):
 
         plan.profile(True)
         ms = _time(step, 10, 2, stream)
-        st = _stage_ms(plan)
+        st = _stage_ms(plan, 12)
         plan.close()
         return {"workload": "65,536 keystone samples, F=128, 128^2 x 64: forward + gradients w.r.t. phasors "
                             "and positions", "ms": ms, "stages_ms": st}
@@ -413,7 +415,7 @@ def run_ours(args, rank, world, local):
         raise RuntimeError("device status error during warm-up")
 
     # One step captured as a CUDA graph (same kernels and launches; the replay avoids per-launch
-    # host and scheduling gaps between the 12 kernels of a step).  Eager steps if capture fails.
+    # host and scheduling gaps between the kernels of a step).  Eager steps if capture fails.
     launches0 = plan.launch_count
     step()
     launches_per_step = plan.launch_count - launches0
@@ -455,7 +457,8 @@ def run_ours(args, rank, world, local):
 
     # ---- per-stage times: CUDA events around each stage of eager steps (outside the timed region)
     plan.profile(True)
-    for _ in range(max(1, min(args.steps, 100))):
+    n_prof = max(1, min(args.steps, 100))
+    for _ in range(n_prof):
         step()
     torch.cuda.synchronize()
     stages = plan.profile_read()
@@ -545,9 +548,11 @@ def run_ours(args, rank, world, local):
                                 "spad-n128": "spad-n128: " + WORKLOAD.replace("256x256x128", "128x128x128")}[
                                     args.workload], "L": L, "T": g.T, "F": F, "N": N, "Z": Z, "M": M, "fine_n": plan.fine_n,
                    "parallelism": f"replicas x{world} (one reconstruction per GPU)",
-                   "launch": ("CUDA-graph replay of one nursd_reconstruct call (12 kernels)" if graph is not None
+                   "launch": (f"CUDA-graph replay of one nursd_reconstruct call ({launches_per_step} kernels)"
+                              if graph is not None
                               else "eager nursd_reconstruct calls"),
-                   "stage_times": "CUDA events around each stage of 100 eager steps after the timed region",
+                   "stage_times": "CUDA events around each stage of 100 eager steps after the timed region, per step "
+                                  "(a stage run in channel or depth groups is summed over its launches)",
                    "l2": "inputs larger than L2 (histograms 268 MB, transfer table %.2f GB); no flush" %
                          (plan.n_classes * F * Z * 8 / 1e9)},
         "recon_per_s": world * 1e3 / ms,
@@ -558,7 +563,7 @@ def run_ours(args, rank, world, local):
                      "algorithmic_bytes": contract_bytes, "avg_launch_ms": c_avg},
         "step_hbm": {"algorithmic_bytes": step_bytes, "achieved_gbs": step_bytes / (ms / 1e3) / 1e9,
                      "frac": step_bytes / (ms / 1e3) / 1e9 / peak},
-        "stages_ms": {k: (v[0] / max(v[1], 1)) for k, v in stages.items()},
+        "stages_ms": {k: v[0] / n_prof for k, v in stages.items() if v[1]},
         "gpu_launches": int(launches),
         "e2e": {"value": job_throughput(units, world, ms_e2e), "unit": UNIT, "ms_per_step": ms_e2e,
                 "h2d_bytes_per_step": int(h_hist.numel() * 4 + h_xy.numel() * 4),
