@@ -93,6 +93,26 @@ def test_stages_match_oracle(wlf):
     assert rel(V1, V2) < 1e-6
 
 
+# ES-kernel accuracy at upsampling 2 improves about tenfold per extra tap (beta = 2.30 w), down
+# to the FP32 floor near 1e-6: relative L2 bounds for the type-1 stage by kernel width.
+WIDTH_TOL = {4: 1e-2, 5: 2e-3, 6: TOL, 7: 5e-5, 8: 5e-5}
+
+
+@pytest.mark.parametrize("width", [4, 5, 6, 7, 8])
+def test_nufft1_every_kernel_width_matches_exact_nudft(width):
+    # the spread is compiled per width, and the width decides which footprints cross a tile edge
+    g = geometry_c1()
+    xy = relay_uniform(16384, 0.5, seed=BASE_SEED + 90)
+    Pr = random_phasors(len(xy), g.F, seed=BASE_SEED + 91)
+    plan = make_plan(g, len(xy), kernel_width=width)
+    plan.set_points(torch.from_numpy(xy).cuda())
+    U_gpu = plan.nufft1(torch.from_numpy(Pr).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    plan.close()
+    U_ref = O.nudft_type1(Pr, O.relay_theta(xy, g.center, g.pitch, g.M), g.M)
+    assert rel(spectrum_to_oracle(U_gpu), U_ref) < WIDTH_TOL[width]
+
+
 def test_results_are_deterministic():
     # samples are sorted by (bin, index), so the spread's summation order is fixed
     wl = workload_c1()
