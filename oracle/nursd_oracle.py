@@ -38,6 +38,8 @@ __all__ = [
     "propagate_points", "idft_grid", "scaled_dft_matrix", "srsd_from_grid", "srsd_forward",
     "adjoint_spectrum", "nursd_adjoint", "nursd_loss", "nursd_gradients",
     "adjoint_spectrum_depthwise", "nudft_type1_lattice", "gradients_from_w", "frustum_volume", "frustum_extra_volume", "data_compression", "lateral_resolution",
+    "voxel_lattice", "propagate_per_frequency", "illumination_mask", "propagate_illuminated", "transient_frames",
+    "nursd_forward_illuminated", "nursd_transient_frames", "fbp_direct_per_frequency",
 ]
 
 
@@ -225,6 +227,107 @@ def fbp_direct(P, xy, omega, vox, chunk: int = 256) -> np.ndarray:
         for f in range(P.shape[1]):
             acc += (np.exp(1j * k[f] * r) / r) @ P[:, f]
         out[v0:v0 + chunk] = acc
+    return out
+
+
+# ------------------------------- per-frequency forms: illumination, video ---
+
+def voxel_lattice(center, pitch: float, N: int, depths) -> np.ndarray:
+    """Voxel positions x_v = (c_x + mx delta, c_y + my delta, z) of V[z][my][mx], m in I_N: [Z][N][N][3]."""
+    m = index_set(N).astype(np.float64) * pitch
+    Z = len(depths)
+    out = np.empty((Z, N, N, 3))
+    out[..., 0] = center[0] + m[None, None, :]
+    out[..., 1] = center[1] + m[None, :, None]
+    out[..., 2] = np.asarray(depths, dtype=np.float64)[:, None, None]
+    return out
+
+
+def propagate_per_frequency(U: np.ndarray, Ghat: np.ndarray, N: int) -> np.ndarray:
+    """Each frequency's reconstruction before the coherent sum (Eq. RSD_conv per frequency).
+
+    V_{z,f}[m] = M^-2 sum_k U_f(k) Ghat_{z,f}(k) exp(+2 pi i k.m / M), m in I_N^2.
+    U: [F][M][M], Ghat: [Z][F][M][M] -> [Z][F][N][N].
+    """
+    M = U.shape[-1]
+    B = _idft_crop_matrix(M, N)
+    Z, F = Ghat.shape[0], Ghat.shape[1]
+    out = np.empty((Z, F, N, N), dtype=np.complex128)
+    for z in range(Z):
+        for f in range(F):
+            out[z, f] = B @ (U[f] * Ghat[z, f]) @ B.T / (M * M)
+    return out
+
+
+def illumination_mask(xp, vox: np.ndarray, omega) -> np.ndarray:
+    """Illumination phase mask of Eq. PF_RSD_Defn, exp(+i k_f |x_p - x_v|), at voxels vox [...][3].
+
+    The sign follows the temporal transform's e^{-i w t}: the path x_p -> x_v delays the
+    phasor by e^{-i k |x_p - x_v|}, which this mask cancels.  Returns [F][...].
+    """
+    xp = np.asarray(xp, dtype=np.float64)
+    d = np.sqrt(np.sum((np.asarray(vox, dtype=np.float64) - xp) ** 2, axis=-1))
+    k = np.asarray(omega, dtype=np.float64) / C
+    return np.exp(1j * k.reshape((-1,) + (1,) * d.ndim) * d[None])
+
+
+def propagate_illuminated(U: np.ndarray, Ghat: np.ndarray, N: int, xp, center, pitch: float, depths,
+                          omega) -> np.ndarray:
+    """Single-illumination reconstruction (Eq. PF_RSD_Defn for one illumination point x_p).
+
+    V_z[m] = sum_f exp(+i k_f |x_p - x_v|) V_{z,f}[m]: the illumination mask varies per voxel and
+    frequency, so the frequency sum follows each frequency's inverse transform.  -> [Z][N][N].
+    """
+    Vf = propagate_per_frequency(U, Ghat, N)
+    vox = voxel_lattice(center, pitch, N, depths)  # [Z][N][N][3]
+    A = illumination_mask(xp, vox, omega)  # [F][Z][N][N]
+    return np.einsum("fzyx,zfyx->zyx", A, Vf)
+
+
+def transient_frames(U: np.ndarray, Ghat: np.ndarray, N: int, times, omega) -> np.ndarray:
+    """Time-resolved frames of the propagating virtual wave (Eq. Video_Voxel_Freq_Offset).
+
+    V_{t,z}[m] = sum_f exp(+i w_f t) V_{z,f}[m] for each time t (seconds, on the measurement's
+    clock).  -> [T][Z][N][N].
+    """
+    Vf = propagate_per_frequency(U, Ghat, N)
+    w = np.asarray(omega, dtype=np.float64)
+    A = np.exp(1j * np.outer(np.asarray(times, dtype=np.float64), w))  # [T][F]
+    return np.einsum("tf,zfyx->tzyx", A, Vf)
+
+
+def nursd_forward_illuminated(P, xy, center, pitch: float, N: int, depths, omega, xp) -> np.ndarray:
+    """Phasors at irregular relay samples -> single-illumination volume V[z][my][mx]."""
+    M = 2 * N
+    U = nudft_type1(P, relay_theta(xy, center, pitch, M), M)
+    return propagate_illuminated(U, transfer_functions(depths, omega, M, pitch), N, xp, center, pitch, depths,
+                                 omega)
+
+
+def nursd_transient_frames(P, xy, center, pitch: float, N: int, depths, omega, times) -> np.ndarray:
+    """Phasors at irregular relay samples -> frames V[t][z][my][mx]."""
+    M = 2 * N
+    U = nudft_type1(P, relay_theta(xy, center, pitch, M), M)
+    return transient_frames(U, transfer_functions(depths, omega, M, pitch), N, times, omega)
+
+
+def fbp_direct_per_frequency(P, xy, omega, vox, chunk: int = 256) -> np.ndarray:
+    """Direct back-projection of each frequency on its own (Eq. PF_RSD_Defn's inner integral).
+
+    R_f(x_v) = sum_l P[l, f] exp(+i k_f |x_v - x_l|) / |x_v - x_l|, relay samples on z = 0,
+    voxels ``vox`` [V][3].  -> [V][F].
+    """
+    P = np.asarray(P, dtype=np.complex128)
+    xy = np.asarray(xy, dtype=np.float64)
+    vox = np.asarray(vox, dtype=np.float64)
+    k = np.asarray(omega, dtype=np.float64) / C
+    out = np.zeros((vox.shape[0], P.shape[1]), dtype=np.complex128)
+    for v0 in range(0, vox.shape[0], chunk):
+        v = vox[v0:v0 + chunk]
+        r = np.sqrt((v[:, None, 0] - xy[None, :, 0]) ** 2 + (v[:, None, 1] - xy[None, :, 1]) ** 2
+                    + v[:, None, 2] ** 2)
+        for f in range(P.shape[1]):
+            out[v0:v0 + chunk, f] = (np.exp(1j * k[f] * r) / r) @ P[:, f]
     return out
 
 

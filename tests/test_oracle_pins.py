@@ -264,6 +264,76 @@ def test_lateral_psf_width_is_of_the_diffraction_limit_order():
     assert 0.5 * dx < fwhm < 2.0 * dx
 
 
+# ------------------------------------------- single illumination, video ---
+
+def _two_way_phasors(xy, xs, xp, omega):
+    """Analytic phasors of a point scatterer x_s lit from x_p: e^{-i k (|x_s - x_p| + d_l)} / d_l."""
+    d = np.sqrt((xy[:, 0] - xs[0]) ** 2 + (xy[:, 1] - xs[1]) ** 2 + xs[2] ** 2)
+    dp = float(np.linalg.norm(np.asarray(xs) - np.asarray(xp)))
+    k = np.asarray(omega) / O.C
+    return np.exp(-1j * np.outer(d + dp, k)) / d[:, None], d, dp
+
+
+def test_per_frequency_direct_sum_adds_up_to_direct_backprojection():
+    c = _lattice_case()
+    vox = np.array([[0.11, -0.02, 0.4], [0.05, -0.09, 0.7]])
+    per_f = O.fbp_direct_per_frequency(c["P"], c["xy"], c["omega"], vox)
+    assert rel(per_f.sum(axis=1), O.fbp_direct(c["P"], c["xy"], c["omega"], vox)) < 1e-13
+
+
+def test_illuminated_on_lattice_equals_direct_sum_with_the_mask():
+    # On the lattice each frequency's reconstruction is exactly the direct sum, so the
+    # illuminated volume is the mask-weighted sum of the per-frequency direct sums.
+    c = _lattice_case()
+    xp = (0.12, 0.0, 0.0)
+    V = O.nursd_forward_illuminated(c["P"], c["xy"], c["center"], c["pitch"], c["N"], c["depths"], c["omega"], xp)
+    vox = O.voxel_lattice(c["center"], c["pitch"], c["N"], c["depths"]).reshape(-1, 3)
+    R = O.fbp_direct_per_frequency(c["P"], c["xy"], c["omega"], vox)  # [V][F]
+    A = O.illumination_mask(xp, vox, c["omega"])  # [F][V]
+    assert rel(V.ravel(), np.einsum("fv,vf->v", A, R)) < 1e-12
+
+
+def test_illuminated_point_scatterer_focuses_in_closed_form():
+    # Two-way phasors e^{-i k (|x_s - x_p| + d_l)} / d_l: at x_s both the detection kernel and
+    # the illumination mask cancel their phases, so V(x_s) = F sum_l 1 / d_l^2 exactly; a
+    # wrong mask sign leaves e^{-2 i k |x_s - x_p|} in every term.
+    c = _lattice_case()
+    xp = (0.12, 0.0, 0.0)
+    iz, mx, my = 1, 2, -1
+    xs = (c["center"][0] + mx * c["pitch"], c["center"][1] + my * c["pitch"], c["depths"][iz])
+    P, d, _ = _two_way_phasors(c["xy"], xs, xp, c["omega"])
+    V = O.nursd_forward_illuminated(P, c["xy"], c["center"], c["pitch"], c["N"], c["depths"], c["omega"], xp)
+    want = len(c["omega"]) * np.sum(1 / d ** 2)
+    got = V[iz, my + c["N"] // 2, mx + c["N"] // 2]
+    assert abs(got - want) < 1e-12 * want
+
+
+def test_transient_frame_at_time_zero_is_the_collapsed_forward():
+    c = _lattice_case()
+    Vt = O.nursd_transient_frames(c["P"], c["xy"], c["center"], c["pitch"], c["N"], c["depths"], c["omega"],
+                                  [0.0])
+    V = O.nursd_forward(c["P"], c["xy"], c["center"], c["pitch"], c["N"], c["depths"], c["omega"])
+    assert rel(Vt[0], V) < 1e-12
+
+
+def test_transient_frames_of_a_point_scatterer_in_closed_form():
+    # Without the illumination mask the frame at time t keeps e^{i w (t - tau_p)}, tau_p the
+    # illumination delay: frame(x_s, t) = sum_f e^{i w_f (t - tau_p)} * sum_l 1 / d_l^2, which
+    # peaks (F sum 1/d^2) when the virtual wave reaches x_s, t = tau_p.
+    c = _lattice_case()
+    xp = (0.12, 0.0, 0.0)
+    iz, mx, my = 0, -3, 2
+    xs = (c["center"][0] + mx * c["pitch"], c["center"][1] + my * c["pitch"], c["depths"][iz])
+    P, d, dp = _two_way_phasors(c["xy"], xs, xp, c["omega"])
+    tau = dp / O.C
+    times = [tau, tau + 37e-12, tau - 120e-12]
+    Vt = O.nursd_transient_frames(P, c["xy"], c["center"], c["pitch"], c["N"], c["depths"], c["omega"], times)
+    s = np.sum(1 / d ** 2)
+    for i, t in enumerate(times):
+        want = s * sum(cmath.exp(1j * w * (t - tau)) for w in c["omega"])
+        assert abs(Vt[i, iz, my + c["N"] // 2, mx + c["N"] // 2] - want) < 1e-12 * s * len(c["omega"])
+
+
 # ------------------------------------------------------------------ a8 -----
 
 def test_type2_output_at_lattice_voxels_equals_lattice_crop():
