@@ -253,6 +253,39 @@ int nursd_grad_points(nursd_plan_t plan, const nursd_c64* d_w, const nursd_c64* 
 int srsd_forward(nursd_plan_t plan, const nursd_c64* d_phasor, void* d_out, nursd_stream_t stream);
 
 /*
+ * Single-illumination reconstruction (Eq. PF_RSD_Defn for one illumination
+ * point x_p): each frequency's reconstruction
+ *   V_{z,f}[m] = M^-2 sum_k U_f(k) Ghat_{z,f}(k) exp(+2 pi i k.m / M),  m in I_N^2,
+ * weighted by the illumination phase mask before the frequency sum:
+ *   V_z[m] = sum_f exp(+i k_f |x_p - x_v|) V_{z,f}[m],
+ *   x_v = (c_x + m_x delta, c_y + m_y delta, z_z),  k_f = w_f / c.
+ * The mask cancels the delay of the path x_p -> x_v (the temporal transform's
+ * e^{-i w t} convention), as the propagation kernel cancels the path back to
+ * the relay.  h_illum: host [3] doubles (x, y, z) metres in the relay frame
+ * (relay plane z = 0), read during the call.  d_phasor [L][F] -> d_out
+ * [Z][N][N] complex64.  Requires nursd_set_points.  The first call of either
+ * per-frequency form allocates the plan's workspace for them, about
+ * 8 C (M^2 + M N + N^2) bytes with C = F * min(Z, max(1, 512 / F)) channels,
+ * and uploads from host memory: neither call is capturable in a CUDA graph.
+ */
+int nursd_forward_illuminated(nursd_plan_t plan, const double* h_illum, const nursd_c64* d_phasor, nursd_c64* d_out,
+                              nursd_stream_t stream);
+
+/*
+ * Time-resolved frames of the virtual wave (Eq. Video_Voxel_Freq_Offset): the
+ * per-frequency reconstructions V_{z,f} (as in nursd_forward_illuminated)
+ * summed with exp(+i w_f t) for each of n_frames times t (seconds on the
+ * measurement's clock, the same origin as the descriptor's t0):
+ *   frames[t][z][m] = sum_f exp(+i w_f t) V_{z,f}[m].
+ * No illumination mask: a scatterer lights up when the virtual wave from the
+ * illumination point reaches it.  h_times: host [n_frames], 1 <= n_frames <=
+ * 4096.  d_phasor [L][F] -> d_out [n_frames][Z][N][N] complex64.  Requires
+ * nursd_set_points; workspace and capture as for nursd_forward_illuminated.
+ */
+int nursd_transient_frames(nursd_plan_t plan, int32_t n_frames, const double* h_times, const nursd_c64* d_phasor,
+                           nursd_c64* d_out, nursd_stream_t stream);
+
+/*
  * B independent reconstructions with their own relay samples and histograms
  * (uneven L_b <= max_points), sharing the plan's geometry and transfer table:
  * for each item, what nursd_set_points + nursd_forward compute.  The temporal
@@ -280,7 +313,8 @@ typedef enum {
   NURSD_STAGE_IFFT_X = 6,
   NURSD_STAGE_IFFT_Y = 7,
   NURSD_STAGE_SRSD = 8, /* scaled transforms and per-depth contractions of srsd_forward */
-  NURSD_NUM_STAGES = 9
+  NURSD_STAGE_PER_FREQUENCY = 9, /* per-depth products and weighted frequency sums of the per-frequency forms */
+  NURSD_NUM_STAGES = 10
 } nursd_stage;
 
 /*

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libnursd.so")
-SOURCES = ["api.cu", "fft.cu", "fft_reg.cu", "temporal_tc.cu", "temporal_umma.cu", "points.cu", "spread.cu", "contract.cu", "gtf.cu", "interp.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "fft.cu", "fft_reg.cu", "temporal_tc.cu", "temporal_umma.cu", "points.cu", "spread.cu", "contract.cu", "gtf.cu", "interp.cu", "illum.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
@@ -29,7 +29,8 @@ def nvcc_path() -> str:
 
 
 def _deps_mtime() -> float:
-    paths = [os.path.join(SRC, f) for f in os.listdir(SRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
+    paths = ([os.path.join(SRC, f) for f in os.listdir(SRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
+             + [os.path.abspath(__file__)])
     return max(os.path.getmtime(p) for p in paths)
 
 

@@ -122,6 +122,17 @@ struct nursd_plan_s {
     p = static_cast<T*>(q);
     return true;
   }
+  // per-frequency forms (nursd_forward_illuminated / nursd_transient_frames), allocated on first
+  // use: pf_zg depths per group, products [M][M][zg F], half inverse [M][N][zg F], per-frequency
+  // volumes [zg F][N][N], k_f / 2 pi [F] and depths [Z] in FP64, the frames' weights [T][F]
+  int pf_zg = 0;
+  float2 *pf_Y = nullptr, *pf_T = nullptr, *pf_V = nullptr, *pf_A = nullptr;
+  double *pf_kap = nullptr, *pf_depth = nullptr;
+  int pf_A_cap = 0;
+  bool pf_equispaced = false;
+  double pf_dkap = 0.0;
+  std::vector<float2> pf_A_host;
+  std::vector<double> pf_kap_host;
   // side stream of nursd_reconstruct (the point sort runs there, beside the temporal transform)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -350,25 +361,24 @@ int run_nufft1(nursd_plan_s* p, const float2* phasor, float2* spec, cudaStream_t
   return from_cuda(e);
 }
 
-// V[z][my][mx] = M^-2 sum_k Y[k][z] e^{+2 pi i k.m / M} on I_N^2 (two pruned inverse passes).
-int run_idft_crop(nursd_plan_s* p, void* out, cudaStream_t s, const float2* Ysrc = nullptr) {
-  if (!Ysrc) Ysrc = p->Y;
-  const int M = p->M, N = p->N, Z = p->Z;
+// out[c][my][mx] = M^-2 sum_k Ysrc[k][c] e^{+2 pi i k.m / M} on I_N^2 for C channels (two pruned
+// inverse passes through T [M][N][C]); out is complex, or |.| when mag.
+cudaError_t idft_crop(nursd_plan_s* p, const float2* Ysrc, int C, float2* T, void* out, bool mag, cudaStream_t s) {
+  const int M = p->M, N = p->N;
   const int logM = ilog2(M);
-  cudaError_t e = cudaSuccess;
+  cudaError_t e;
   {  // inverse FFT along kx, keep mx in I_N
     StageTimer t(p, NURSD_STAGE_IFFT_X, s, 1);
-    e = axis_pass(p, Ysrc, p->T1, logM, true, Z, M, (long long)M * Z, Z, (long long)N * Z, Z, M, -M / 2, N, -N / 2,
+    e = axis_pass(p, Ysrc, T, logM, true, C, M, (long long)M * C, C, (long long)N * C, C, M, -M / 2, N, -N / 2,
                   nullptr, nullptr, 1.f, s);
   }
-  if (e == cudaSuccess) {  // inverse FFT along ky for every (mx, z), keep my in I_N, write V[z][my][mx]
+  if (e == cudaSuccess) {  // inverse FFT along ky for every (mx, c), keep my in I_N, write out[c][my][mx]
     StageTimer t(p, NURSD_STAGE_IFFT_Y, s, 1);
     PanelArgs a = panel_base(p);
-    a.in = p->T1;
-    a.in_si = (long long)N * Z;
-    a.in_shi = Z;
+    a.in = T;
+    a.in_si = (long long)N * C;
+    a.in_shi = C;
     a.in_slo = 1;
-    const bool mag = (p->flags & NURSD_OUTPUT_MAGNITUDE) != 0;
     if (mag)
       a.out_mag = static_cast<float*>(out);
     else
@@ -381,15 +391,20 @@ int run_idft_crop(nursd_plan_s* p, void* out, cudaStream_t s, const float2* Ysrc
     a.nout = N;
     a.out_off = -N / 2;
     a.hi_total = N;
-    a.lo_total = Z;
+    a.lo_total = C;
     const int cp = panel_width(logM);
-    a.CLO = Z >= 4 ? 4 : (Z >= 2 ? 2 : 1);
+    a.CLO = C >= 4 ? 4 : (C >= 2 ? 2 : 1);
     a.CHI = cp / a.CLO;
     a.scale = 1.f / ((float)M * (float)M);
     a.store_hi_fastest = 1;
     e = launch_panel_fft(logM, true, a, s);
   }
-  return from_cuda(e);
+  return e;
+}
+
+// V[z][my][mx] = M^-2 sum_k Y[k][z] e^{+2 pi i k.m / M} on I_N^2 (two pruned inverse passes).
+int run_idft_crop(nursd_plan_s* p, void* out, cudaStream_t s, const float2* Ysrc = nullptr) {
+  return from_cuda(idft_crop(p, Ysrc ? Ysrc : p->Y, p->Z, p->T1, out, (p->flags & NURSD_OUTPUT_MAGNITUDE) != 0, s));
 }
 
 int run_propagate(nursd_plan_s* p, const float2* spec, void* out, cudaStream_t s) {
@@ -451,6 +466,70 @@ int run_srsd(nursd_plan_s* p, void* out, cudaStream_t s) {
   }
   if (e != cudaSuccess) return from_cuda(e);
   return run_idft_crop(p, out, s);
+}
+
+// Workspace of the per-frequency forms (see the plan members), allocated on first use.
+int ensure_per_frequency(nursd_plan_s* p, cudaStream_t s) {
+  if (p->pf_zg > 0) return NURSD_OK;
+  const int M = p->M, N = p->N, F = p->F, Z = p->Z;
+  const int zg = std::max(1, std::min(Z, 512 / F));
+  const size_t C = (size_t)zg * F;
+  if (!(p->alloc(p->pf_Y, (size_t)M * M * C) && p->alloc(p->pf_T, (size_t)M * N * C) &&
+        p->alloc(p->pf_V, C * N * N) && p->alloc(p->pf_kap, F) && p->alloc(p->pf_depth, Z)))
+    return NURSD_ERR_OOM;
+  std::vector<double> kap(F);
+  for (int f = 0; f < F; ++f) kap[f] = p->omega[f] / (2.0 * kPi * kC);
+  const double dk = F > 1 ? (kap[F - 1] - kap[0]) / (F - 1) : 0.0;
+  bool equi = true;
+  for (int f = 0; f < F; ++f) equi = equi && std::fabs(kap[f] - (kap[0] + f * dk)) <= 1e-13 * std::fabs(kap[F - 1]);
+  p->pf_equispaced = equi;
+  p->pf_dkap = dk;
+  // both host arrays are plan-owned and stay unchanged afterwards
+  cudaError_t e = cudaMemcpyAsync(p->pf_depth, p->depths.data(), sizeof(double) * Z, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    p->pf_kap_host = kap;
+    e = cudaMemcpyAsync(p->pf_kap, p->pf_kap_host.data(), sizeof(double) * F, cudaMemcpyHostToDevice, s);
+  }
+  if (e != cudaSuccess) return NURSD_ERR_CUDA;
+  p->pf_zg = zg;
+  return NURSD_OK;
+}
+
+// Per-frequency forms from the spectrum in p->U: for each group of pf_zg depths, the products
+// U_f Ghat_{z,f}, the two pruned inverse passes over all zg*F channels, then the weighted sum over
+// f -- by the illumination mask of *illum (frames == 0) or by exp(+i w_f t) for each of the
+// `frames` times (weights already in p->pf_A).
+int run_per_frequency(nursd_plan_s* p, const double* illum, int frames, float2* out, cudaStream_t s) {
+  const int M = p->M, N = p->N, F = p->F, Z = p->Z, zg = p->pf_zg;
+  IllumArgs ia;
+  std::memset(&ia, 0, sizeof(ia));
+  if (frames == 0) {
+    ia.xp = illum[0];
+    ia.yp = illum[1];
+    ia.zp = illum[2];
+    ia.cx = p->cx;
+    ia.cy = p->cy;
+    ia.pitch = p->pitch;
+    ia.depth = p->pf_depth;
+    ia.kap = p->pf_kap;
+    ia.dkap = p->pf_dkap;
+    ia.equispaced = p->pf_equispaced ? 1 : 0;
+  }
+  cudaError_t e = cudaSuccess;
+  for (int z0 = 0; z0 < Z && e == cudaSuccess; z0 += zg) {
+    const int n = std::min(zg, Z - z0), C = n * F;
+    {
+      StageTimer t(p, NURSD_STAGE_PER_FREQUENCY, s, 1);
+      e = launch_transfer_depths(p->U, p->Gc, M, F, Z, z0, n, p->pf_Y, s);
+    }
+    if (e == cudaSuccess) e = idft_crop(p, p->pf_Y, C, p->pf_T, p->pf_V, false, s);
+    if (e == cudaSuccess) {
+      StageTimer t(p, NURSD_STAGE_PER_FREQUENCY, s, 1);
+      e = frames == 0 ? launch_illum_sum(p->pf_V, F, N, z0, n, ia, out, s)
+                      : launch_frames_sum(p->pf_V, F, N, Z, z0, n, p->pf_A, frames, out, s);
+    }
+  }
+  return from_cuda(e);
 }
 
 // Adjoint of run_propagate up to the spectrum: R[k][f] = sum_z conj(Ghat) * M^-2 DFT_M[pad V_z](k),
@@ -976,6 +1055,52 @@ int srsd_forward(nursd_plan_t p, const nursd_c64* d_phasor, void* d_out, nursd_s
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc = run_nufft1(p, reinterpret_cast<const float2*>(d_phasor), p->U, s);
   if (rc == NURSD_OK) rc = run_srsd(p, d_out, s);
+  return rc;
+}
+
+int nursd_forward_illuminated(nursd_plan_t p, const double* h_illum, const nursd_c64* d_phasor, nursd_c64* d_out,
+                              nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || p->L < 0 || !h_illum || !d_out || !aligned(d_out, 8)) return NURSD_ERR_INVALID_ARG;
+  if (!(std::isfinite(h_illum[0]) && std::isfinite(h_illum[1]) && std::isfinite(h_illum[2])))
+    return NURSD_ERR_INVALID_ARG;
+  if (p->L > 0 && (!d_phasor || !aligned(d_phasor, 8))) return NURSD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = ensure_per_frequency(p, s);
+  if (rc == NURSD_OK) rc = run_nufft1(p, reinterpret_cast<const float2*>(d_phasor), p->U, s);
+  if (rc == NURSD_OK) rc = run_per_frequency(p, h_illum, 0, reinterpret_cast<float2*>(d_out), s);
+  return rc;
+}
+
+int nursd_transient_frames(nursd_plan_t p, int32_t n_frames, const double* h_times, const nursd_c64* d_phasor,
+                           nursd_c64* d_out, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || p->L < 0 || n_frames < 1 || n_frames > 4096 || !h_times || !d_out ||
+      !aligned(d_out, 8))
+    return NURSD_ERR_INVALID_ARG;
+  for (int t = 0; t < n_frames; ++t)
+    if (!std::isfinite(h_times[t])) return NURSD_ERR_INVALID_ARG;
+  if (p->L > 0 && (!d_phasor || !aligned(d_phasor, 8))) return NURSD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = ensure_per_frequency(p, s);
+  if (rc != NURSD_OK) return rc;
+  const int F = p->F;
+  if (n_frames > p->pf_A_cap) {
+    if (!p->alloc(p->pf_A, (size_t)n_frames * F)) return NURSD_ERR_OOM;
+    p->pf_A_cap = n_frames;
+  }
+  // weights exp(+i w_f t) with the phase reduced in FP64 (w_f t reaches ~1e3 rad), rounded to
+  // complex64, uploaded from a plan-owned host copy; stream order puts the upload before this
+  // call's sums and after an earlier call's.
+  p->pf_A_host.resize((size_t)n_frames * F);
+  for (int t = 0; t < n_frames; ++t)
+    for (int f = 0; f < F; ++f) {
+      const double ph = std::fmod(p->omega[f] * h_times[t], 2.0 * kPi);
+      p->pf_A_host[(size_t)t * F + f] = make_float2((float)std::cos(ph), (float)std::sin(ph));
+    }
+  if (cudaMemcpyAsync(p->pf_A, p->pf_A_host.data(), sizeof(float2) * p->pf_A_host.size(), cudaMemcpyHostToDevice, s) !=
+      cudaSuccess)
+    return NURSD_ERR_CUDA;
+  rc = run_nufft1(p, reinterpret_cast<const float2*>(d_phasor), p->U, s);
+  if (rc == NURSD_OK) rc = run_per_frequency(p, nullptr, n_frames, reinterpret_cast<float2*>(d_out), s);
   return rc;
 }
 

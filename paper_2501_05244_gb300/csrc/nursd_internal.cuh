@@ -225,6 +225,26 @@ cudaError_t launch_gtf_generate(float2* g, int M, double pitch, const double* d_
 // Gs[((z0 + zb) * ncls + c) * F + f] = Gfull[rep(c)][zb*F + f] (per-depth blocks, f fastest)
 cudaError_t launch_gtf_compress_depthmajor(const float2* Gfull, const int2* cls_pq, int ncls, int M, int F, int ZB,
                                            int z0, float2* Gs, cudaStream_t s);
+// ---------------------------------------------------------- per-frequency forms (illum.cu)
+// Y[k][zz*F + f] = U[k][f] * Gc[class(k)][f][z0 + zz] for zz < zg (no sum over f), U and Y
+// mode-major [M][M][...] with mode (kx, ky) at (ky + M/2) M + (kx + M/2).
+cudaError_t launch_transfer_depths(const float2* U, const float2* Gc, int M, int F, int Z, int z0, int zg, float2* Y,
+                                   cudaStream_t s);
+struct IllumArgs {
+  double xp, yp, zp;     // illumination point (m), relay frame
+  double cx, cy, pitch;  // voxel (mx, my) of a plane at (cx + (mx - N/2) pitch, cy + (my - N/2) pitch)
+  const double* depth;   // device [Z] plane depths (m)
+  const double* kap;     // device [F] k_f / (2 pi) = w_f / (2 pi c), cycles per metre
+  double dkap;           // kap[f + 1] - kap[f] when equispaced
+  int equispaced;        // kap[f] = kap[0] + f dkap to FP64 rounding
+};
+// out[z0 + zz][my][mx] = sum_f exp(+i k_f |x_p - x_v|) V[zz*F + f][my][mx], V channel-major
+// [zg*F][N][N], out [Z][N][N].
+cudaError_t launch_illum_sum(const float2* V, int F, int N, int z0, int zg, const IllumArgs& a, float2* out,
+                             cudaStream_t s);
+// out[t][z0 + zz][my][mx] = sum_f A[t][f] V[zz*F + f][my][mx], A [T][F], out [T][Z][N][N].
+cudaError_t launch_frames_sum(const float2* V, int F, int N, int Z, int z0, int zg, const float2* A, int T,
+                              float2* out, cudaStream_t s);
 // SRSD contraction for one depth: Y[k][z] = sum_f Phat[k][f] * Gs_z[cls(k)][f].
 cudaError_t launch_contract_depth(const float2* Phat, const float2* Gs_z, const int2* cls_pq, int ncls, int M, int F,
                                   int Z, int z, float2* Y, cudaStream_t s);

@@ -33,11 +33,12 @@ EXPORTS = (
     "nursd_propagate", "nursd_forward_phasor", "nursd_forward", "nursd_sync_status",
     "nursd_profile_enable", "nursd_profile_read", "nursd_launch_count", "nursd_nufft1_noalloc",
     "nursd_forward_points", "nursd_adjoint", "nursd_grad_points", "srsd_forward", "nursd_forward_batched",
-    "nursd_reconstruct",
+    "nursd_reconstruct", "nursd_forward_illuminated", "nursd_transient_frames",
 )
 
 #: stage names in nursd_stage order
-STAGES = ("points", "temporal", "spread", "fft_x", "fft_y", "contract", "ifft_x", "ifft_y", "srsd")
+STAGES = ("points", "temporal", "spread", "fft_x", "fft_y", "contract", "ifft_x", "ifft_y", "srsd",
+          "per_frequency")
 
 
 class NursdError(RuntimeError):
@@ -101,6 +102,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "srsd_forward": (ctypes.c_int, [vp, vp, vp, vp]),
         "nursd_forward_batched": (ctypes.c_int, [vp, i32, ctypes.POINTER(_BatchItem), vp]),
         "nursd_reconstruct": (ctypes.c_int, [vp, i32, vp, vp, vp, vp]),
+        "nursd_forward_illuminated": (ctypes.c_int, [vp, dp, vp, vp, vp]),
+        "nursd_transient_frames": (ctypes.c_int, [vp, i32, dp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -343,6 +346,36 @@ class Plan:
             out = self.empty_output()
         o = _dev(out, self.out_dtype(), self.out_shape(), "out")
         _check(self._lib.srsd_forward(self._h, p, o, ctypes.c_void_p(_stream_ptr(stream))), "srsd_forward")
+        return out
+
+    def forward_illuminated(self, phasor, illum, out=None, stream=None):
+        """Single-illumination volume [Z][N][N] complex64: each frequency's reconstruction weighted
+        by exp(+i k_f |x_p - x_v|) before the frequency sum; illum = (x, y, z) metres."""
+        torch = _torch()
+        self._need_points()
+        p = _dev(phasor, torch.complex64, (self.L, self.F), "phasor")
+        if out is None:
+            out = torch.empty((self.Z, self.N, self.N), dtype=torch.complex64, device=phasor.device)
+        o = _dev(out, torch.complex64, (self.Z, self.N, self.N), "out")
+        xp = (ctypes.c_double * 3)(*[float(v) for v in illum])
+        _check(self._lib.nursd_forward_illuminated(self._h, xp, p, o, ctypes.c_void_p(_stream_ptr(stream))),
+               "nursd_forward_illuminated")
+        return out
+
+    def transient_frames(self, phasor, times, out=None, stream=None):
+        """Frames [T][Z][N][N] complex64 of the virtual wave at the given times (seconds, the
+        measurement's clock): each frequency's reconstruction weighted by exp(+i w_f t)."""
+        torch = _torch()
+        self._need_points()
+        times = np.ascontiguousarray(times, dtype=np.float64).ravel()
+        T = int(times.shape[0])
+        p = _dev(phasor, torch.complex64, (self.L, self.F), "phasor")
+        if out is None:
+            out = torch.empty((T, self.Z, self.N, self.N), dtype=torch.complex64, device=phasor.device)
+        o = _dev(out, torch.complex64, (T, self.Z, self.N, self.N), "out")
+        tp = times.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _check(self._lib.nursd_transient_frames(self._h, T, tp, p, o, ctypes.c_void_p(_stream_ptr(stream))),
+               "nursd_transient_frames")
         return out
 
     def adjoint(self, vol, out=None, stream=None):
