@@ -327,6 +327,41 @@ def measure_rows(wl, peak):
         return {"workload": "65,536 keystone samples, F=128, 128^2 x 64: forward + gradients w.r.t. phasors "
                             "and positions", "ms": ms, "stages_ms": st}
 
+    def illuminated():
+        # next row 1: one illumination point's phase mask per voxel and frequency (Eq. PF_RSD_Defn),
+        # and transient frames (Eq. Video_Voxel_Freq_Offset); both keep every frequency's volume
+        plan = nursd.Plan(g.N, g.pitch, g.center, g.depths, om, wt, T=g.T, t0=g.t0, dt=g.dt, max_points=L)
+        plan.set_points(d_xy)
+        P = plan.temporal_dft(d_hist)
+        out = torch.empty((g.Z, g.N, g.N), dtype=torch.complex64, device="cuda")
+        xp = (0.0, 0.0, 0.0)  # the aperture centre
+        plan.profile(True)
+        ms = _time(lambda: plan.forward_illuminated(P, xp, out=out), 3, 1, stream)
+        st = _stage_ms(plan, 4)
+        plan.profile(False)
+        nt = 16
+        times = g.t0 + np.linspace(0.0, 4e-9, nt)
+        frames = torch.empty((nt, g.Z, g.N, g.N), dtype=torch.complex64, device="cuda")
+        ms_f = _time(lambda: plan.transient_frames(P, times, out=frames), 3, 1, stream)
+        assert plan.sync_status() == 0
+        M, F, Z, N = 2 * g.N, g.F, g.Z, g.N
+        ncls = (M // 2 + 1) * (M // 2 + 2) // 2
+        zg = min(Z, max(1, 512 // F))
+        # per group of zg depths (C = zg F channels): spectrum + zg table values per class and f in,
+        # the products, half inverse and per-frequency volumes each written and read once, volume out
+        per_group = lambda zn: (M * M * F + ncls * F * zn + 2 * M * M * zn * F + 2 * M * N * zn * F
+                                + 2 * N * N * zn * F + N * N * zn) * 8
+        groups = [min(zg, Z - z0) for z0 in range(0, Z, zg)]
+        bytes_pf = sum(per_group(zn) for zn in groups)
+        units = Z * N * N * F
+        return {"workload": "65,536 keystone samples -> 256^2 x 128, F=128: single illumination at the aperture "
+                            "centre; and 16 transient frames over 4 ns",
+                "ms": ms, "voxel_freq_per_s": units / (ms / 1e3), "ms_16_frames": ms_f,
+                "per_frequency_stages": {"algorithmic_bytes": bytes_pf,
+                                         "ms": ms - st.get("spread", 0) - st.get("fft_x", 0) - st.get("fft_y", 0),
+                                         "depth_group": zg},
+                "hbm_frac_of_call": (bytes_pf / (ms / 1e3) / 1e9) / peak, "stages_ms": st}
+
     def batched():
         gb = geometry_c4()
         sizes = batch_sizes_c4()
@@ -368,6 +403,7 @@ def measure_rows(wl, peak):
     guarded("a10_adjoint", adjoint)
     guarded("a11_gradients", grad)
     guarded("a12_batched", batched)
+    guarded("f1_single_illumination", illuminated)
     return rows
 
 
