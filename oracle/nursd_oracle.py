@@ -40,6 +40,7 @@ __all__ = [
     "adjoint_spectrum_depthwise", "nudft_type1_lattice", "gradients_from_w", "frustum_volume", "frustum_extra_volume", "data_compression", "lateral_resolution",
     "voxel_lattice", "propagate_per_frequency", "illumination_mask", "propagate_illuminated", "transient_frames",
     "nursd_forward_illuminated", "nursd_transient_frames", "fbp_direct_per_frequency",
+    "srsd_spectra", "srsd_points",
 ]
 
 
@@ -395,6 +396,41 @@ def srsd_forward(P, xy, center, pitch: float, N: int, depths, scales, omega) -> 
     M = 2 * N
     U = nudft_type1(P, relay_theta(xy, center, pitch, M), M)
     return srsd_from_grid(idft_grid(U), depths, scales, omega, pitch, N)
+
+
+def srsd_spectra(u: np.ndarray, depths, scales, omega, pitch: float) -> np.ndarray:
+    """The scaled spectra of :func:`srsd_from_grid` before its inverse transform.
+
+    Y^S_z = sum_f (A_z u_f A_z^T) . Ghat^(s_z)_{z,f}, A_z the scaled DFT with s_z and Ghat^(s_z)
+    the DFT of G sampled at pitch s_z delta.  u: [F][M][M] -> [Z][M][M].
+    """
+    M = u.shape[-1]
+    out = np.empty((len(depths), M, M), dtype=np.complex128)
+    for iz, (z, s) in enumerate(zip(np.asarray(depths, float), np.asarray(scales, float))):
+        A = scaled_dft_matrix(M, s)
+        Y = np.zeros((M, M), dtype=np.complex128)
+        for f, w in enumerate(np.asarray(omega, dtype=np.float64)):
+            Y += (A @ u[f] @ A.T) * transfer_function(rsd_kernel(M, s * pitch, z, w / C))
+        out[iz] = Y
+    return out
+
+
+def srsd_points(P, xy, center, pitch: float, N: int, depths, scales, omega, vox_xy) -> np.ndarray:
+    """SRSD + NURSD-2 (Eq. NURSD2_SRSD): the scaled reconstruction at arbitrary voxels of each plane.
+
+    V_z(x_v) = M^-2 sum_kappa Y^S_z(kappa) exp(+i kappa . theta_v) with theta_v = 2 pi (x_v - c) /
+    (M s_z delta): the type-2 sum on plane z's scaled lattice, whose lattice points
+    c + s_z delta m give back the SRSD output.  vox_xy: [Z][K][2] metres -> [Z][K].
+    """
+    M = 2 * N
+    U = nudft_type1(P, relay_theta(xy, center, pitch, M), M)
+    Y = srsd_spectra(idft_grid(U), depths, scales, omega, pitch)
+    vox = np.asarray(vox_xy, dtype=np.float64)
+    out = np.empty(vox.shape[:2], dtype=np.complex128)
+    for iz, s in enumerate(np.asarray(scales, float)):
+        theta = 2 * math.pi * (vox[iz] - np.asarray(center, dtype=np.float64)) / (M * s * pitch)
+        out[iz] = nudft_type2(Y[iz][None], theta)[:, 0] / (M * M)
+    return out
 
 
 # --------------------------------------------------- a10-a11: adjoint, grad ---

@@ -420,6 +420,37 @@ def test_srsd_with_input_on_the_scaled_lattice_equals_direct_sum():
     assert rel(V, want) < 1e-12
 
 
+def test_srsd_points_on_each_scaled_lattice_equal_the_srsd_volume():
+    # Eq. NURSD2_SRSD at voxels c + s_z delta m of plane z's own lattice is the SRSD output there.
+    c = _lattice_case()
+    N = c["N"]
+    xy = c["xy"] + np.random.default_rng(12).uniform(-0.4, 0.4, c["xy"].shape) * c["pitch"]
+    scales = np.array([1.3, 2.25])
+    V = O.srsd_forward(c["P"], xy, c["center"], c["pitch"], N, c["depths"], scales, c["omega"])
+    r = np.random.default_rng(13)
+    m = r.integers(-N // 2, N // 2, size=(len(scales), 11, 2))
+    vox = np.asarray(c["center"])[None, None, :] + m * (scales[:, None, None] * c["pitch"])
+    got = O.srsd_points(c["P"], xy, c["center"], c["pitch"], N, c["depths"], scales, c["omega"], vox)
+    want = np.stack([V[z, m[z, :, 1] + N // 2, m[z, :, 0] + N // 2] for z in range(len(scales))])
+    assert rel(got, want) < 1e-12
+
+
+def test_srsd_points_with_unit_scale_are_the_nursd2_output():
+    # s = 1 everywhere: the scaled lattice is the ordinary one and the off-lattice voxels give the
+    # NURSD-2 output (Eqs. NURSD2-3).
+    c = _lattice_case()
+    N, M = c["N"], 2 * c["N"]
+    xy = c["xy"] + np.random.default_rng(14).uniform(-0.4, 0.4, c["xy"].shape) * c["pitch"]
+    r = np.random.default_rng(15)
+    vox = np.asarray(c["center"]) + r.uniform(-0.5, 0.5, size=(len(c["depths"]), 9, 2)) * N * c["pitch"]
+    got = O.srsd_points(c["P"], xy, c["center"], c["pitch"], N, c["depths"], np.ones(len(c["depths"])),
+                        c["omega"], vox)
+    U = O.nudft_type1(c["P"], O.relay_theta(xy, c["center"], c["pitch"], M), M)
+    theta = np.stack([O.relay_theta(vox[z], c["center"], c["pitch"], M) for z in range(len(c["depths"]))])
+    want = O.propagate_points(U, O.transfer_functions(c["depths"], c["omega"], M, c["pitch"]), theta)
+    assert rel(got, want) < 1e-12
+
+
 # -------------------------------------------------------------- a10-a11 ----
 
 def test_adjoint_identity():
