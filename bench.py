@@ -362,6 +362,25 @@ def measure_rows(wl, peak):
                                          "depth_group": zg},
                 "hbm_frac_of_call": (bytes_pf / (ms / 1e3) / 1e9) / peak, "stages_ms": st}
 
+    def srsd_points():
+        # next row 2: SRSD + NURSD-2 (Eq. NURSD2_SRSD), 16,384 random voxels in each plane's scaled aperture
+        depths = srsd_depths_c3b()
+        pitches = srsd_pitches_c3b(depths)
+        plan = nursd.Plan(g.N, g.pitch, g.center, depths, om, wt, T=g.T, t0=g.t0, dt=g.dt, max_points=L,
+                          srsd_pitch=pitches)
+        plan.set_points(d_xy)
+        P = plan.temporal_dft(d_hist)
+        K = 16384
+        unit = random_plane_points(len(depths), K, 0.999, seed=BASE_SEED + 31)  # [Z][K][2] in a unit half-extent
+        vox = torch.from_numpy((unit * (0.5 * g.N * pitches)[:, None, None]).astype(np.float32)).cuda()
+        out = torch.empty((len(depths), K), dtype=torch.complex64, device="cuda")
+        ms = _time(lambda: plan.srsd_forward_points(P, vox, out=out), 3, 1, stream)
+        assert plan.sync_status() == 0
+        plan.close()
+        return {"workload": "65,536 keystone samples -> 128 scaled planes over 1-4 m (pitch 8 -> 32 mm) x 16,384 "
+                            "random voxels each, F=128",
+                "ms": ms, "voxel_freq_per_s": len(depths) * K * g.F / (ms / 1e3)}
+
     def batched():
         gb = geometry_c4()
         sizes = batch_sizes_c4()
@@ -404,6 +423,7 @@ def measure_rows(wl, peak):
     guarded("a11_gradients", grad)
     guarded("a12_batched", batched)
     guarded("f1_single_illumination", illuminated)
+    guarded("f2_srsd_points", srsd_points)
     return rows
 
 

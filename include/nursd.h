@@ -253,6 +253,20 @@ int nursd_grad_points(nursd_plan_t plan, const nursd_c64* d_w, const nursd_c64* 
 int srsd_forward(nursd_plan_t plan, const nursd_c64* d_phasor, void* d_out, nursd_stream_t stream);
 
 /*
+ * SRSD + NURSD-2 (Eq. NURSD2_SRSD): the scaled spectra of srsd_forward
+ *   Y^S_z(kappa) = sum_f Phat_{z,f}(kappa) Ghat^(s_z)_{z,f}(kappa)
+ * evaluated at arbitrary voxels of each plane's scaled lattice by type 2:
+ *   V_z(x_v) = M^-2 sum_kappa Y^S_z(kappa) exp(+i kappa . theta_v),
+ *   theta_v = 2 pi (x_v - c) / (M s_z delta),
+ * so voxels c + s_z delta m (m in I_N^2) give srsd_forward's output.
+ * d_vox_xy [Z][K][2] float32 metres, d_out [Z][K] complex64.  Voxels outside
+ * |x - c| <= N s_z delta / 2 give 0 and set the out-of-range status bit.
+ * Needs h_srsd_pitch at plan creation and nursd_set_points.
+ */
+int srsd_forward_points(nursd_plan_t plan, const nursd_c64* d_phasor, int32_t K, const float* d_vox_xy,
+                        nursd_c64* d_out, nursd_stream_t stream);
+
+/*
  * Single-illumination reconstruction (Eq. PF_RSD_Defn for one illumination
  * point x_p): each frequency's reconstruction
  *   V_{z,f}[m] = M^-2 sum_k U_f(k) Ghat_{z,f}(k) exp(+2 pi i k.m / M),  m in I_N^2,

@@ -72,6 +72,8 @@ struct nursd_plan_s {
   TemporalMaps tmaps{};   // TMA descriptors of Bth/Btl for the tcgen05 form (ok = 0: mma.sync form)
   // SRSD tables (h_srsd_pitch given): scaled transfer table [Z][ncls][F], chirps [Z][M], FFT(b)/(2M) [Z][2M]
   std::vector<double> srsd_pitch;
+  std::vector<double> srsd_scale;  // srsd_pitch / pitch (host copy of srsd_scale_d)
+  double* srsd_scale_d = nullptr;  // device [Z]
   float2* Gs = nullptr;
   float2* chirp = nullptr;
   float2* bhat = nullptr;
@@ -310,7 +312,12 @@ int build_srsd_chirps(nursd_plan_s* p, cudaStream_t s) {
     cudaGetLastError();
     return NURSD_ERR_OOM;
   }
+  p->srsd_scale.resize(Z);
+  for (int z = 0; z < Z; ++z) p->srsd_scale[z] = p->srsd_pitch[z] / p->pitch;
   int rc = from_cuda(cudaMemcpyAsync(p->chirp, ch.data(), sizeof(float2) * ch.size(), cudaMemcpyHostToDevice, s));
+  if (rc == NURSD_OK)
+    rc = from_cuda(
+        cudaMemcpyAsync(p->srsd_scale_d, p->srsd_scale.data(), sizeof(double) * Z, cudaMemcpyHostToDevice, s));
   if (rc == NURSD_OK) rc = from_cuda(cudaMemcpyAsync(db, b.data(), sizeof(float2) * b.size(), cudaMemcpyHostToDevice, s));
   if (rc == NURSD_OK) {  // FFT of each depth's contiguous row of 2M values
     const int logL = ilog2(L2);
@@ -417,8 +424,9 @@ int run_propagate(nursd_plan_s* p, const float2* spec, void* out, cudaStream_t s
   return run_idft_crop(p, out, s);
 }
 
-// Scaled RSD from a NUFFT-1 spectrum U (in p->U): see srsd_forward in nursd.h.
-int run_srsd(nursd_plan_s* p, void* out, cudaStream_t s) {
+// Scaled spectra Y^S_z [M][M][Z] (into p->Y) from a NUFFT-1 spectrum U (in p->U): see srsd_forward in
+// nursd.h.
+int run_srsd_spectra(nursd_plan_s* p, cudaStream_t s) {
   const int M = p->M, F = p->F, Z = p->Z;
   const int logM = ilog2(M), logL = logM + 1;
   cudaError_t e;
@@ -464,8 +472,7 @@ int run_srsd(nursd_plan_s* p, void* out, cudaStream_t s) {
     if (e == cudaSuccess)
       e = launch_contract_depth(p->U, p->Gs + (size_t)z * p->ncls * F, p->cls, p->ncls, M, F, Z, z, p->Y, s);
   }
-  if (e != cudaSuccess) return from_cuda(e);
-  return run_idft_crop(p, out, s);
+  return from_cuda(e);
 }
 
 // Workspace of the per-frequency forms (see the plan members), allocated on first use.
@@ -799,7 +806,7 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
          p->alloc(p->Y_all, (size_t)p->maxB * p->M * p->M * p->Z) && p->alloc(p->counter, 1);
   if (ok && !p->srsd_pitch.empty())
     ok = p->alloc(p->Gs, (size_t)p->ncls * p->F * p->Z) && p->alloc(p->chirp, (size_t)p->Z * p->M) &&
-         p->alloc(p->bhat, (size_t)p->Z * 2 * p->M);
+         p->alloc(p->bhat, (size_t)p->Z * 2 * p->M) && p->alloc(p->srsd_scale_d, p->Z);
   if (!ok) {
     delete p;
     return NURSD_ERR_OOM;
@@ -1013,6 +1020,38 @@ int nursd_grad_points(nursd_plan_t p, const nursd_c64* d_w, const nursd_c64* d_p
   return rc;
 }
 
+// Type-2 output of the depth spectra in p->Y at K voxels per plane (NURSD-2/3): deconvolve, pad,
+// inverse fine-grid transform per plane, ES interpolation.  plane_scale [Z] (device) or null:
+// plane z's lattice pitch over the plan's (SRSD's scaled planes).
+int run_points_output(nursd_plan_s* p, int K, const float* d_vox_xy, const double* plane_scale, nursd_c64* d_out,
+                      cudaStream_t s) {
+  const int M = p->M;
+  int rc = run_type2_to_fine(p, p->Y, p->Z, true, 1.f / ((float)M * (float)M), s);
+  if (rc == NURSD_OK && K > 0) {
+    StageTimer t(p, NURSD_STAGE_IFFT_Y, s, 1);
+    PlaneInterpArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.fine = p->fine;
+    a.W = p->W;
+    a.Z = p->Z;
+    a.K = K;
+    a.width = p->w;
+    a.g0 = p->g0;
+    a.beta = p->beta;
+    a.cx = p->cx;
+    a.cy = p->cy;
+    a.inv_fine_pitch = 2.0 / p->pitch;
+    a.half_extent = 0.5 * p->N * p->pitch;
+    a.plane_scale = plane_scale;
+    a.vox = d_vox_xy;
+    a.scale = 1.f;
+    a.out = reinterpret_cast<float2*>(d_out);
+    a.status = p->status;
+    rc = from_cuda(launch_interp_planes(a, s));
+  }
+  return rc;
+}
+
 int nursd_forward_points(nursd_plan_t p, const nursd_c64* d_phasor, int32_t K, const float* d_vox_xy,
                          nursd_c64* d_out, nursd_stream_t stream) {
   if (check_plan(p) != NURSD_OK || p->L < 0 || K < 0) return NURSD_ERR_INVALID_ARG;
@@ -1025,27 +1064,7 @@ int nursd_forward_points(nursd_plan_t p, const nursd_c64* d_phasor, int32_t K, c
     StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
     rc = from_cuda(launch_contract(p->U, p->Gc, p->cls, p->ncls, M, p->F, p->Z, p->Y, s, p->status));
   }
-  if (rc == NURSD_OK) rc = run_type2_to_fine(p, p->Y, p->Z, true, 1.f / ((float)M * (float)M), s);
-  if (rc == NURSD_OK && K > 0) {
-    StageTimer t(p, NURSD_STAGE_IFFT_Y, s, 1);
-    PlaneInterpArgs a;
-    a.fine = p->fine;
-    a.W = p->W;
-    a.Z = p->Z;
-    a.K = K;
-    a.width = p->w;
-    a.g0 = p->g0;
-    a.beta = p->beta;
-    a.cx = p->cx;
-    a.cy = p->cy;
-    a.inv_fine_pitch = 2.0 / p->pitch;
-    a.half_extent = 0.5 * p->N * p->pitch;
-    a.vox = d_vox_xy;
-    a.scale = 1.f;
-    a.out = reinterpret_cast<float2*>(d_out);
-    a.status = p->status;
-    rc = from_cuda(launch_interp_planes(a, s));
-  }
+  if (rc == NURSD_OK) rc = run_points_output(p, K, d_vox_xy, nullptr, d_out, s);
   return rc;
 }
 
@@ -1054,7 +1073,20 @@ int srsd_forward(nursd_plan_t p, const nursd_c64* d_phasor, void* d_out, nursd_s
   if (p->L > 0 && (!d_phasor || !aligned(d_phasor, 8))) return NURSD_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc = run_nufft1(p, reinterpret_cast<const float2*>(d_phasor), p->U, s);
-  if (rc == NURSD_OK) rc = run_srsd(p, d_out, s);
+  if (rc == NURSD_OK) rc = run_srsd_spectra(p, s);
+  if (rc == NURSD_OK) rc = run_idft_crop(p, d_out, s);
+  return rc;
+}
+
+int srsd_forward_points(nursd_plan_t p, const nursd_c64* d_phasor, int32_t K, const float* d_vox_xy, nursd_c64* d_out,
+                        nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || !p->Gs || p->L < 0 || K < 0) return NURSD_ERR_INVALID_ARG;
+  if (p->L > 0 && (!d_phasor || !aligned(d_phasor, 8))) return NURSD_ERR_INVALID_ARG;
+  if (K > 0 && (!d_vox_xy || !d_out || !aligned(d_vox_xy, 8) || !aligned(d_out, 8))) return NURSD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = run_nufft1(p, reinterpret_cast<const float2*>(d_phasor), p->U, s);
+  if (rc == NURSD_OK) rc = run_srsd_spectra(p, s);
+  if (rc == NURSD_OK) rc = run_points_output(p, K, d_vox_xy, p->srsd_scale_d, d_out, s);
   return rc;
 }
 

@@ -94,13 +94,16 @@ __global__ void __launch_bounds__(256) interp_planes_kernel(const PlaneInterpArg
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long long)a.Z * a.K) return;
   const int z = (int)(idx / a.K);
+  // plane z's lattice pitch is plane_scale[z] times the plan's (the scaled planes of SRSD)
+  const double sz = a.plane_scale ? __ldg(a.plane_scale + z) : 1.0;
+  const double half = a.half_extent * sz, inv = a.inv_fine_pitch / sz;
   const double dx = (double)a.vox[2 * idx] - a.cx, dy = (double)a.vox[2 * idx + 1] - a.cy;
-  if (!(fabs(dx) <= a.half_extent && fabs(dy) <= a.half_extent)) {
+  if (!(fabs(dx) <= half && fabs(dy) <= half)) {
     atomicOr(a.status, 1);
     a.out[idx] = make_float2(0.f, 0.f);
     return;
   }
-  const double ux = dx * a.inv_fine_pitch, uy = dy * a.inv_fine_pitch;
+  const double ux = dx * inv, uy = dy * inv;
   const int ix = (int)ceil(ux - 0.5 * WID), iy = (int)ceil(uy - 0.5 * WID);
   float wx[WID], wy[WID];
 #pragma unroll

@@ -210,6 +210,8 @@ struct PlaneInterpArgs {
   int W, Z, K, width, g0;
   float beta;
   double cx, cy, inv_fine_pitch, half_extent;
+  const double* plane_scale;  // [Z] or null: plane z's lattice pitch over the plan's (inv_fine_pitch
+                              // divided by it, half_extent multiplied)
   const float* vox;  // [Z][K][2]
   float scale;
   float2* out;       // [Z][K]

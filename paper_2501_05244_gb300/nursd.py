@@ -33,7 +33,7 @@ EXPORTS = (
     "nursd_propagate", "nursd_forward_phasor", "nursd_forward", "nursd_sync_status",
     "nursd_profile_enable", "nursd_profile_read", "nursd_launch_count", "nursd_nufft1_noalloc",
     "nursd_forward_points", "nursd_adjoint", "nursd_grad_points", "srsd_forward", "nursd_forward_batched",
-    "nursd_reconstruct", "nursd_forward_illuminated", "nursd_transient_frames",
+    "nursd_reconstruct", "nursd_forward_illuminated", "nursd_transient_frames", "srsd_forward_points",
 )
 
 #: stage names in nursd_stage order
@@ -104,6 +104,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "nursd_reconstruct": (ctypes.c_int, [vp, i32, vp, vp, vp, vp]),
         "nursd_forward_illuminated": (ctypes.c_int, [vp, dp, vp, vp, vp]),
         "nursd_transient_frames": (ctypes.c_int, [vp, i32, dp, vp, vp, vp]),
+        "srsd_forward_points": (ctypes.c_int, [vp, vp, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -376,6 +377,20 @@ class Plan:
         tp = times.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         _check(self._lib.nursd_transient_frames(self._h, T, tp, p, o, ctypes.c_void_p(_stream_ptr(stream))),
                "nursd_transient_frames")
+        return out
+
+    def srsd_forward_points(self, phasor, vox, out=None, stream=None):
+        """SRSD + NURSD-2: scaled reconstruction at per-plane voxels vox [Z][K][2] (metres) -> [Z][K]."""
+        torch = _torch()
+        self._need_points()
+        p = _dev(phasor, torch.complex64, (self.L, self.F), "phasor")
+        K = int(vox.shape[1])
+        v = _dev(vox, torch.float32, (self.Z, K, 2), "vox")
+        if out is None:
+            out = torch.empty((self.Z, K), dtype=torch.complex64, device=phasor.device)
+        o = _dev(out, torch.complex64, (self.Z, K), "out")
+        _check(self._lib.srsd_forward_points(self._h, p, K, v, o, ctypes.c_void_p(_stream_ptr(stream))),
+               "srsd_forward_points")
         return out
 
     def adjoint(self, vol, out=None, stream=None):

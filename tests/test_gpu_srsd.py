@@ -86,3 +86,41 @@ def test_srsd_at_the_65k_sample_size_sampled_planes():
     for z in (0, len(depths) - 1):
         ref = O.srsd_from_grid(u, depths[z:z + 1], out_pitch[z:z + 1] / pitch, om, pitch, N)[0]
         assert rel(V[z], ref) < TOL
+
+
+# ------------------------------------------------- SRSD + NURSD-2 (Eq. NURSD2_SRSD) ---
+
+def scaled_voxels(N, pitch, center, scales, K, seed):
+    # K voxels per plane, uniform over plane z's scaled aperture |x - c| <= N s_z delta / 2
+    r = np.random.default_rng(seed)
+    half = 0.5 * N * pitch * np.asarray(scales)[:, None, None]
+    return (r.uniform(-1.0, 1.0, (len(scales), K, 2)) * 0.999 * half + np.asarray(center)).astype(np.float32)
+
+
+@pytest.mark.parametrize("N,L,F,Z,seed", [(16, 300, 6, 5, 1), (32, 1200, 16, 7, 2)])
+def test_srsd_points_match_oracle(N, L, F, Z, seed):
+    xy, P, om, depths, out_pitch, pitch, center = case(N, L, F, Z, seed)
+    plan = nursd.Plan(N, pitch, center, depths, om, max_points=L, srsd_pitch=out_pitch)
+    plan.set_points(torch.from_numpy(xy).cuda())
+    vox = scaled_voxels(N, pitch, center, out_pitch / pitch, 333, seed + 50)  # ragged K
+    V = plan.srsd_forward_points(torch.from_numpy(P).cuda(), torch.from_numpy(vox).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    ref = O.srsd_points(P, xy, center, pitch, N, depths, out_pitch / pitch, om, vox.astype(np.float64))
+    assert rel(V, ref) < TOL
+
+
+def test_srsd_points_on_each_scaled_lattice_equal_srsd_forward():
+    N, L, F, Z = 32, 1200, 16, 7
+    xy, P, om, depths, out_pitch, pitch, center = case(N, L, F, Z, 6)
+    plan = nursd.Plan(N, pitch, center, depths, om, max_points=L, srsd_pitch=out_pitch)
+    plan.set_points(torch.from_numpy(xy).cuda())
+    Pg = torch.from_numpy(P).cuda()
+    V = plan.srsd_forward(Pg).cpu().numpy()
+    r = np.random.default_rng(7)
+    # interior lattice points: m = -N/2 lies on the aperture edge, where float32 may round it out
+    m = r.integers(-N // 2 + 1, N // 2, size=(Z, 64, 2))
+    vox = (np.asarray(center)[None, None, :] + m * out_pitch[:, None, None]).astype(np.float32)
+    Vp = plan.srsd_forward_points(Pg, torch.from_numpy(vox).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    want = np.stack([V[z, m[z, :, 1] + N // 2, m[z, :, 0] + N // 2] for z in range(Z)])
+    assert rel(Vp, want) < TOL
