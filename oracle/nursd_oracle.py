@@ -157,14 +157,19 @@ def transfer_function(g: np.ndarray) -> np.ndarray:
     return np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(g)))
 
 
-def transfer_functions(depths, omega, M: int, pitch: float) -> np.ndarray:
-    """Ghat[z][f][ky][kx] for every depth plane and frequency (k_f = w_f / c)."""
+def transfer_functions(depths, omega, M: int, pitch: float, confocal: bool = False) -> np.ndarray:
+    """Ghat[z][f][ky][kx] for every depth plane and frequency (k_f = w_f / c).
+
+    confocal: every relay point both illuminates and detects, so the phasor-field point source
+    radiates e^{i 2 k r} (Supp., confocal systems) and the kernel takes k_con = 2 k_f.
+    """
     depths = np.asarray(depths, dtype=np.float64)
     omega = np.asarray(omega, dtype=np.float64)
+    kmul = 2.0 if confocal else 1.0
     out = np.empty((len(depths), len(omega), M, M), dtype=np.complex128)
     for iz, z in enumerate(depths):
         for f, w in enumerate(omega):
-            out[iz, f] = transfer_function(rsd_kernel(M, pitch, z, w / C))
+            out[iz, f] = transfer_function(rsd_kernel(M, pitch, z, kmul * w / C))
     return out
 
 
@@ -198,15 +203,16 @@ def propagate_depth(U: np.ndarray, z: float, omega, pitch: float, N: int) -> np.
     return (B @ Y @ B.T) / (M * M)
 
 
-def nursd_forward(P, xy, center, pitch: float, N: int, depths, omega) -> np.ndarray:
+def nursd_forward(P, xy, center, pitch: float, N: int, depths, omega, confocal: bool = False) -> np.ndarray:
     """The full NURSD-1 operator: phasors at irregular relay samples -> V[z][my][mx].
 
     IFFT{ NUFFT-1{P_F(x_l)} . FFT{G(m delta, n delta, z_v)} } (Eq. NURSD1), with the
-    frequency integral of Eq. PF_RSD_Defn taken as the sum over the F phasor bins.
+    frequency integral of Eq. PF_RSD_Defn taken as the sum over the F phasor bins;
+    confocal as in :func:`transfer_functions`.
     """
     M = 2 * N
     U = nudft_type1(P, relay_theta(xy, center, pitch, M), M)
-    return propagate(U, transfer_functions(depths, omega, M, pitch), N)
+    return propagate(U, transfer_functions(depths, omega, M, pitch, confocal), N)
 
 
 def fbp_direct(P, xy, omega, vox, chunk: int = 256) -> np.ndarray:

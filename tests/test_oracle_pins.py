@@ -223,6 +223,32 @@ def test_point_source_focus_closed_form():
     assert abs(v - 16 * np.sum(1 / d ** 2)) < 1e-10 * abs(v)
 
 
+def test_confocal_point_source_focus_closed_form():
+    # Confocal acquisition: the relay point illuminates and detects, the round trip gives
+    # P = e^{-2 i k d} / d, and the confocal kernel e^{+2 i k r} / r refocuses it exactly on the
+    # lattice: V(x_s) = F sum_l 1/d_l^2.  The ordinary kernel leaves e^{-i k d} in every term.
+    c = _lattice_case()
+    iz, mx, my = 1, 1, -2
+    xs = (c["center"][0] + mx * c["pitch"], c["center"][1] + my * c["pitch"], c["depths"][iz])
+    d = np.sqrt((c["xy"][:, 0] - xs[0]) ** 2 + (c["xy"][:, 1] - xs[1]) ** 2 + xs[2] ** 2)
+    k = np.asarray(c["omega"]) / O.C
+    P = np.exp(-2j * np.outer(d, k)) / d[:, None]
+    V = O.nursd_forward(P, c["xy"], c["center"], c["pitch"], c["N"], c["depths"], c["omega"], confocal=True)
+    got = V[iz, my + c["N"] // 2, mx + c["N"] // 2]
+    want = len(k) * np.sum(1 / d ** 2)
+    assert abs(got - want) < 1e-12 * want
+    V1 = O.nursd_forward(P, c["xy"], c["center"], c["pitch"], c["N"], c["depths"], c["omega"])
+    assert abs(V1[iz, my + c["N"] // 2, mx + c["N"] // 2] - want) > 1e-3 * want
+
+
+def test_confocal_on_lattice_equals_direct_sum_with_doubled_wavenumber():
+    c = _lattice_case()
+    V = O.nursd_forward(c["P"], c["xy"], c["center"], c["pitch"], c["N"], c["depths"], c["omega"], confocal=True)
+    vox = O.voxel_lattice(c["center"], c["pitch"], c["N"], c["depths"]).reshape(-1, 3)
+    d = O.fbp_direct(c["P"], c["xy"], 2 * np.asarray(c["omega"]), vox)
+    assert rel(V.ravel(), d) < 1e-12
+
+
 def test_reconstruction_of_simulated_scatterers_focuses_on_them():
     # End to end through the temporal transform: the max-intensity projection of the
     # tiny workload's three on-axis scatterers (0.6/0.9/1.2 m) peaks at the centre of
