@@ -62,6 +62,10 @@ typedef enum {
 #define NURSD_OUTPUT_MAGNITUDE 0x1u /* nursd_forward* write |V| (float32) instead of V */
 #define NURSD_ENABLE_ADJOINT 0x2u   /* also build the transposed table used by nursd_adjoint and
                                        nursd_grad_points (doubles the table memory; Z <= 256) */
+#define NURSD_CONFOCAL 0x4u         /* confocal acquisition (Supp., confocal systems): each relay
+                                       point both illuminates and detects, the round trip doubles the
+                                       phase, so every table uses the kernel e^{+i 2 k r} / r.
+                                       nursd_forward_illuminated is unsupported on such plans. */
 
 /*
  * Plan descriptor.  Geometry of Sec. 3.1 / Eq. 4: an N x N output lattice of

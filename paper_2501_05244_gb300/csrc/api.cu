@@ -255,8 +255,10 @@ int build_table(nursd_plan_s* p, bool srsd, cudaStream_t s) {
     cudaGetLastError();
     rc = NURSD_ERR_OOM;
   }
+  // wavenumbers of the kernel e^{ikr}/r; a confocal round trip doubles them
+  const double kmul = (p->flags & NURSD_CONFOCAL) ? 2.0 : 1.0;
   std::vector<double> k(F);
-  for (int f = 0; f < F; ++f) k[f] = p->omega[f] / kC;
+  for (int f = 0; f < F; ++f) k[f] = kmul * p->omega[f] / kC;
   if (rc == NURSD_OK) {
     rc = from_cuda(cudaMemcpyAsync(dz, p->depths.data(), sizeof(double) * Z, cudaMemcpyHostToDevice, s));
     if (rc == NURSD_OK) rc = from_cuda(cudaMemcpyAsync(dk, k.data(), sizeof(double) * F, cudaMemcpyHostToDevice, s));
@@ -703,7 +705,7 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
   if (d->h_srsd_pitch)
     for (int i = 0; i < d->Z; ++i)
       if (!(d->h_srsd_pitch[i] > 0) || !std::isfinite(d->h_srsd_pitch[i])) return NURSD_ERR_INVALID_ARG;
-  if ((d->flags & ~(NURSD_OUTPUT_MAGNITUDE | NURSD_ENABLE_ADJOINT)) != 0) return NURSD_ERR_UNSUPPORTED;
+  if ((d->flags & ~(NURSD_OUTPUT_MAGNITUDE | NURSD_ENABLE_ADJOINT | NURSD_CONFOCAL)) != 0) return NURSD_ERR_UNSUPPORTED;
   if ((d->flags & NURSD_ENABLE_ADJOINT) && d->Z > 256) return NURSD_ERR_UNSUPPORTED;
 
   nursd_plan_s* p = new (std::nothrow) nursd_plan_s();
@@ -1093,6 +1095,7 @@ int srsd_forward_points(nursd_plan_t p, const nursd_c64* d_phasor, int32_t K, co
 int nursd_forward_illuminated(nursd_plan_t p, const double* h_illum, const nursd_c64* d_phasor, nursd_c64* d_out,
                               nursd_stream_t stream) {
   if (check_plan(p) != NURSD_OK || p->L < 0 || !h_illum || !d_out || !aligned(d_out, 8)) return NURSD_ERR_INVALID_ARG;
+  if (p->flags & NURSD_CONFOCAL) return NURSD_ERR_UNSUPPORTED;  // the illumination point is each relay point
   if (!(std::isfinite(h_illum[0]) && std::isfinite(h_illum[1]) && std::isfinite(h_illum[2])))
     return NURSD_ERR_INVALID_ARG;
   if (p->L > 0 && (!d_phasor || !aligned(d_phasor, 8))) return NURSD_ERR_INVALID_ARG;

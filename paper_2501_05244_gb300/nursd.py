@@ -25,6 +25,7 @@ NURSD_ERR_UNSUPPORTED = 5
 NURSD_ERR_POINT_OUT_OF_RANGE = 6
 NURSD_OUTPUT_MAGNITUDE = 0x1
 NURSD_ENABLE_ADJOINT = 0x2
+NURSD_CONFOCAL = 0x4
 
 #: every entry point declared in include/nursd.h
 EXPORTS = (
@@ -165,6 +166,7 @@ class Plan:
     def __init__(self, N: int, pitch: float, center, depths, omega, weight=None, T: int = 0, t0: float = 0.0,
                  dt: float = 0.0, max_points: int = 0, kernel_width: int = 6, upsample: int = 2,
                  magnitude: bool = False, adjoint: bool = False, srsd_pitch=None, max_batch: int = 0,
+                 confocal: bool = False,
                  stream=None):
         torch = _torch()
         if not torch.cuda.is_available():
@@ -187,7 +189,8 @@ class Plan:
                       else ctypes.POINTER(ctypes.c_double)())
         d.T, d.t0, d.dt = self.T, float(t0), float(dt)
         d.upsample, d.kernel_width = int(upsample), int(kernel_width)
-        d.flags = (NURSD_OUTPUT_MAGNITUDE if magnitude else 0) | (NURSD_ENABLE_ADJOINT if adjoint else 0)
+        d.flags = ((NURSD_OUTPUT_MAGNITUDE if magnitude else 0) | (NURSD_ENABLE_ADJOINT if adjoint else 0)
+                   | (NURSD_CONFOCAL if confocal else 0))
         d.max_points = int(max_points)
         self.srsd_pitch = None if srsd_pitch is None else np.ascontiguousarray(srsd_pitch, dtype=np.float64)
         d.h_srsd_pitch = (self.srsd_pitch.ctypes.data_as(ctypes.POINTER(ctypes.c_double))

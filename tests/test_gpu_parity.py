@@ -113,6 +113,35 @@ def test_nufft1_every_kernel_width_matches_exact_nudft(width):
     assert rel(spectrum_to_oracle(U_gpu), U_ref) < WIDTH_TOL[width]
 
 
+def test_confocal_plan_matches_oracle():
+    # confocal acquisition: the kernel e^{+2ikr}/r of the round trip (Supp., confocal systems)
+    wl = workload_mid()
+    g = wl.geom
+    plan = make_plan(g, len(wl.xy), confocal=True)
+    plan.set_points(torch.from_numpy(wl.xy).cuda())
+    Pr = random_phasors(len(wl.xy), g.F, seed=BASE_SEED + 95)
+    V = plan.forward_phasor(torch.from_numpy(Pr).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    om, _ = oracle_freqs(g)
+    ref = O.nursd_forward(Pr, wl.xy, g.center, g.pitch, g.N, g.depths, om, confocal=True)
+    assert rel(V, ref) < TOL
+    with pytest.raises(nursd.NursdError):  # each relay point is its own illumination point
+        plan.forward_illuminated(torch.from_numpy(Pr).cuda(), (0.0, 0.0, 0.0))
+
+
+def test_confocal_plan_equals_ordinary_plan_at_doubled_frequencies():
+    wl = workload_c1()
+    g = wl.geom
+    om, wt = nursd.phasor_frequencies(g.lambda_c, g.dt, g.t_pad, g.F)
+    xy = torch.from_numpy(wl.xy).cuda()
+    P = torch.from_numpy(random_phasors(len(wl.xy), g.F, seed=BASE_SEED + 96)).cuda()
+    a = nursd.Plan(g.N, g.pitch, g.center, g.depths, om, wt, max_points=len(wl.xy), confocal=True)
+    b = nursd.Plan(g.N, g.pitch, g.center, g.depths, 2 * om, wt, max_points=len(wl.xy))
+    a.set_points(xy)
+    b.set_points(xy)
+    assert rel(a.forward_phasor(P).cpu().numpy(), b.forward_phasor(P).cpu().numpy()) < 1e-6
+
+
 def test_results_are_deterministic():
     # samples are sorted by (bin, index), so the spread's summation order is fixed
     wl = workload_c1()
