@@ -140,3 +140,36 @@ def test_spad_lattice_illuminated_equals_direct_sum_with_mask():
     A = O.illumination_mask(xp, vox, om)  # [F][V]
     ref = np.einsum("fv,vf->v", A, R)
     assert rel(V[vz, m[:, 1], m[:, 0]], ref) < TOL
+
+
+def test_several_depth_groups_with_a_ragged_last_one():
+    # F = 128 puts 4 depths in a group (512 channels), so Z = 6 runs a group of 4 and one of 2
+    wl = workload_c1()
+    g = wl.geom
+    om, wt = nursd.phasor_frequencies(g.lambda_c, g.dt, g.t_pad, 128)
+    depths = np.linspace(0.55, 1.45, 6)
+    plan = nursd.Plan(g.N, g.pitch, g.center, depths, om, wt, max_points=len(wl.xy))
+    plan.set_points(torch.from_numpy(wl.xy).cuda())
+    P = random_phasors(len(wl.xy), len(om), seed=BASE_SEED + 125)
+    Pg = torch.from_numpy(P).cuda()
+    V = plan.forward_illuminated(Pg, ILLUM).cpu().numpy()
+    times = g.t0 + np.array([0.4e-9, 2.5e-9, 5.1e-9])
+    Vt = plan.transient_frames(Pg, times).cpu().numpy()
+    assert plan.sync_status() == 0
+    om_o, _ = O.phasor_frequencies(g.lambda_c, g.dt, g.t_pad, 128)
+    M = 2 * g.N
+    U = O.nudft_type1(P, O.relay_theta(wl.xy, g.center, g.pitch, M), M)
+    G = O.transfer_functions(depths, om_o, M, g.pitch)
+    assert rel(V, O.propagate_illuminated(U, G, g.N, ILLUM, g.center, g.pitch, depths, om_o)) < TOL
+    assert rel(Vt, O.transient_frames(U, G, g.N, times, om_o)) < TOL
+
+
+def test_empty_point_set_gives_zero_volume_and_frames():
+    wl = workload_c1()
+    g = wl.geom
+    plan = make_plan(g, 8)
+    plan.set_points(torch.zeros((0, 2), dtype=torch.float32, device="cuda"))
+    P = torch.zeros((0, g.F), dtype=torch.complex64, device="cuda")
+    assert float(plan.forward_illuminated(P, ILLUM).abs().max()) == 0.0
+    assert float(plan.transient_frames(P, [0.0, 1e-9]).abs().max()) == 0.0
+    assert plan.sync_status() == 0

@@ -124,3 +124,13 @@ def test_srsd_points_on_each_scaled_lattice_equal_srsd_forward():
     assert plan.sync_status() == 0
     want = np.stack([V[z, m[z, :, 1] + N // 2, m[z, :, 0] + N // 2] for z in range(Z)])
     assert rel(Vp, want) < TOL
+
+
+def test_srsd_points_with_no_voxels():
+    N, L, F, Z = 16, 300, 6, 5
+    xy, P, om, depths, out_pitch, pitch, center = case(N, L, F, Z, 8)
+    plan = nursd.Plan(N, pitch, center, depths, om, max_points=L, srsd_pitch=out_pitch)
+    plan.set_points(torch.from_numpy(xy).cuda())
+    out = plan.srsd_forward_points(torch.from_numpy(P).cuda(), torch.zeros((Z, 0, 2), dtype=torch.float32, device="cuda"))
+    assert tuple(out.shape) == (Z, 0)
+    assert plan.sync_status() == 0
