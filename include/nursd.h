@@ -281,10 +281,14 @@ int srsd_forward_points(nursd_plan_t plan, const nursd_c64* d_phasor, int32_t K,
  * e^{-i w t} convention), as the propagation kernel cancels the path back to
  * the relay.  h_illum: host [3] doubles (x, y, z) metres in the relay frame
  * (relay plane z = 0), read during the call.  d_phasor [L][F] -> d_out
- * [Z][N][N] complex64.  Requires nursd_set_points.  The first call of either
+ * [Z][N][N] complex64.  Requires nursd_set_points.  Depths are processed in
+ * groups.  When Z % 4 == 0, F is even and M is 512 or 1024, a group is 4
+ * depths (C = 4 F channels) whose products U_f Ghat_{z,f} are formed inside
+ * the first inverse pass; otherwise a group is min(Z, max(1, 512 / F)) depths
+ * and the products are written out first.  The first call of either
  * per-frequency form allocates the plan's workspace for them, about
- * 8 C (M^2 + M N + N^2) bytes with C = F * min(Z, max(1, 512 / F)) channels,
- * and uploads from host memory: neither call is capturable in a CUDA graph.
+ * 8 C (M N + N^2) bytes (plus 8 C M^2 without the in-pass products), and
+ * uploads from host memory: neither call is capturable in a CUDA graph.
  */
 int nursd_forward_illuminated(nursd_plan_t plan, const double* h_illum, const nursd_c64* d_phasor, nursd_c64* d_out,
                               nursd_stream_t stream);

@@ -370,18 +370,13 @@ int run_nufft1(nursd_plan_s* p, const float2* phasor, float2* spec, cudaStream_t
   return from_cuda(e);
 }
 
-// out[c][my][mx] = M^-2 sum_k Ysrc[k][c] e^{+2 pi i k.m / M} on I_N^2 for C channels (two pruned
-// inverse passes through T [M][N][C]); out is complex, or |.| when mag.
-cudaError_t idft_crop(nursd_plan_s* p, const float2* Ysrc, int C, float2* T, void* out, bool mag, cudaStream_t s) {
+// The second of the two pruned inverse passes: T [M][N][C] (ky, mx, c) -> out[c][my][mx], the
+// inverse FFT along ky for every (mx, c) with my kept in I_N and the M^-2 scale; complex, or |.|.
+cudaError_t idft_crop_y(nursd_plan_s* p, const float2* T, int C, void* out, bool mag, cudaStream_t s) {
   const int M = p->M, N = p->N;
   const int logM = ilog2(M);
   cudaError_t e;
-  {  // inverse FFT along kx, keep mx in I_N
-    StageTimer t(p, NURSD_STAGE_IFFT_X, s, 1);
-    e = axis_pass(p, Ysrc, T, logM, true, C, M, (long long)M * C, C, (long long)N * C, C, M, -M / 2, N, -N / 2,
-                  nullptr, nullptr, 1.f, s);
-  }
-  if (e == cudaSuccess) {  // inverse FFT along ky for every (mx, c), keep my in I_N, write out[c][my][mx]
+  {
     StageTimer t(p, NURSD_STAGE_IFFT_Y, s, 1);
     PanelArgs a = panel_base(p);
     a.in = T;
@@ -408,6 +403,21 @@ cudaError_t idft_crop(nursd_plan_s* p, const float2* Ysrc, int C, float2* T, voi
     a.store_hi_fastest = 1;
     e = launch_panel_fft(logM, true, a, s);
   }
+  return e;
+}
+
+// out[c][my][mx] = M^-2 sum_k Ysrc[k][c] e^{+2 pi i k.m / M} on I_N^2 for C channels (two pruned
+// inverse passes through T [M][N][C]); out is complex, or |.| when mag.
+cudaError_t idft_crop(nursd_plan_s* p, const float2* Ysrc, int C, float2* T, void* out, bool mag, cudaStream_t s) {
+  const int M = p->M, N = p->N;
+  const int logM = ilog2(M);
+  cudaError_t e;
+  {  // inverse FFT along kx, keep mx in I_N
+    StageTimer t(p, NURSD_STAGE_IFFT_X, s, 1);
+    e = axis_pass(p, Ysrc, T, logM, true, C, M, (long long)M * C, C, (long long)N * C, C, M, -M / 2, N, -N / 2,
+                  nullptr, nullptr, 1.f, s);
+  }
+  if (e == cudaSuccess) e = idft_crop_y(p, T, C, out, mag, s);
   return e;
 }
 
@@ -481,9 +491,12 @@ int run_srsd_spectra(nursd_plan_s* p, cudaStream_t s) {
 int ensure_per_frequency(nursd_plan_s* p, cudaStream_t s) {
   if (p->pf_zg > 0) return NURSD_OK;
   const int M = p->M, N = p->N, F = p->F, Z = p->Z;
-  const int zg = std::max(1, std::min(Z, 512 / F));
+  // groups of 4 depths where the kx pass forms the products itself (radix-32 lengths); otherwise
+  // as many depths as keep a group within 512 channels
+  const bool fusable = Z % 4 == 0 && F % 2 == 0 && (M == 512 || M == 1024);
+  const int zg = fusable ? 4 : std::max(1, std::min(Z, 512 / F));
   const size_t C = (size_t)zg * F;
-  if (!(p->alloc(p->pf_Y, (size_t)M * M * C) && p->alloc(p->pf_T, (size_t)M * N * C) &&
+  if (!(p->alloc(p->pf_Y, fusable ? 1 : (size_t)M * M * C) && p->alloc(p->pf_T, (size_t)M * N * C) &&
         p->alloc(p->pf_V, C * N * N) && p->alloc(p->pf_kap, F) && p->alloc(p->pf_depth, Z)))
     return NURSD_ERR_OOM;
   std::vector<double> kap(F);
@@ -527,15 +540,47 @@ int run_per_frequency(nursd_plan_s* p, const double* illum, int frames, float2* 
   cudaError_t e = cudaSuccess;
   for (int z0 = 0; z0 < Z && e == cudaSuccess; z0 += zg) {
     const int n = std::min(zg, Z - z0), C = n * F;
-    {
-      StageTimer t(p, NURSD_STAGE_PER_FREQUENCY, s, 1);
-      e = launch_transfer_depths(p->U, p->Gc, M, F, Z, z0, n, p->pf_Y, s);
+    // groups of 4 depths on the radix-32 lengths form the products inside the kx pass's window
+    // staging (channel 4 f + zz) instead of writing and re-reading them (channel zz F + f)
+    const bool fused = n == 4 && Z % 4 == 0 && F % 2 == 0 && (M == 512 || M == 1024);
+    if (fused) {
+      PanelArgs a = panel_base(p);
+      a.in = p->U;
+      a.in_sb = (long long)M * F;
+      a.in_si = F;
+      a.in_slo = 1;
+      a.prod_g = p->Gc;
+      a.prod_F = F;
+      a.prod_Z = Z;
+      a.prod_z0 = z0;
+      a.out = p->pf_T;
+      a.out_sb = (long long)N * C;
+      a.out_si = C;
+      a.out_slo = 1;
+      a.nin = M;
+      a.in_off = -M / 2;
+      a.nout = N;
+      a.out_off = -N / 2;
+      a.lo_total = C;
+      a.CLO = panel_width(ilog2(M));
+      a.batch = M;
+      {
+        StageTimer t(p, NURSD_STAGE_IFFT_X, s, 1);
+        e = launch_panel_fft(ilog2(M), true, a, s);
+      }
+      if (e == cudaSuccess) e = idft_crop_y(p, p->pf_T, C, p->pf_V, false, s);
+    } else {
+      {
+        StageTimer t(p, NURSD_STAGE_PER_FREQUENCY, s, 1);
+        e = launch_transfer_depths(p->U, p->Gc, M, F, Z, z0, n, p->pf_Y, s);
+      }
+      if (e == cudaSuccess) e = idft_crop(p, p->pf_Y, C, p->pf_T, p->pf_V, false, s);
     }
-    if (e == cudaSuccess) e = idft_crop(p, p->pf_Y, C, p->pf_T, p->pf_V, false, s);
+    const int cz = fused ? 1 : F, cf = fused ? n : 1;  // channel of (zz, f) = zz cz + f cf
     if (e == cudaSuccess) {
       StageTimer t(p, NURSD_STAGE_PER_FREQUENCY, s, 1);
-      e = frames == 0 ? launch_illum_sum(p->pf_V, F, N, z0, n, ia, out, s)
-                      : launch_frames_sum(p->pf_V, F, N, Z, z0, n, p->pf_A, frames, out, s);
+      e = frames == 0 ? launch_illum_sum(p->pf_V, F, N, z0, n, cz, cf, ia, out, s)
+                      : launch_frames_sum(p->pf_V, F, N, Z, z0, n, cz, cf, p->pf_A, frames, out, s);
     }
   }
   return from_cuda(e);

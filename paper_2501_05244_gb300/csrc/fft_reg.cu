@@ -370,21 +370,6 @@ __device__ __forceinline__ int small_div(int x, int d, float inv) {
 // vec2) and every (NT / channels)-th row, so consecutive threads store consecutive
 // addresses along the contiguous channel axis.
 template <int LOGN, int CP, int NT>
-// floor(x / d) for 0 <= x < 2^22 and d >= 1, with inv = 1.f / d: the rounded float
-// quotient is within 1 of the exact one, and one correction step makes it exact.
-__device__ __forceinline__ int small_div(int x, int d, float inv) {
-  int qt = __float2int_rz(__int2float_rz(x) * inv);
-  const int r = x - qt * d;
-  qt += (r >= d) - (r < 0);
-  return qt;
-}
-
-// Writes the kept bins of the panel held in xbuf as [bin][CP] (dense) to global memory:
-// output o = (bin - out_off) mod n for o < nout, scaled by scale * mul_b[b] * mul_o[o]
-// (or as magnitudes).  Threads take fixed channels (pairs of adjacent channels when
-// vec2) and every (NT / channels)-th row, so consecutive threads store consecutive
-// addresses along the contiguous channel axis.
-template <int LOGN, int CP, int NT>
 __device__ __forceinline__ void copy_out(const PanelArgs& a, const float2* xbuf, const float* mo, int b, int hi0,
                                          int lo0, int vec2) {
   constexpr int n = 1 << LOGN;
@@ -593,6 +578,42 @@ struct WindowStager {
   }
 };
 
+// Stages panel (b, chunk)'s transfer products (PanelArgs::prod_g) instead of a plain window: per
+// window row i, the two spectrum values U[b][i][f0..f0+1] and the table rows of those two
+// frequencies for the four depths, five 16-byte copies into a row of kProdRow values
+// [u0, u1, g(0, 0..3), g(1, 0..3)] (the caller commits).
+constexpr int kProdRow = 10;
+// Batch order of the product-staging pass: item j is mode row ky = 0, 1, -1, 2, -2, ..., then -M/2
+// (stored at b = ky + M/2), so the rows +ky and -ky, which use the same table classes, run back
+// to back and the second finds the classes in L2.
+__device__ __forceinline__ int prod_row(int j, int M) {
+  if (j == M - 1) return 0;
+  const int m = (j + 1) >> 1;
+  return M / 2 + ((j & 1) ? m : -m);
+}
+template <int NT>
+struct ProductStager {
+  const PanelArgs& a;
+  float2* ibuf;
+  int tid;
+  __device__ __forceinline__ void operator()(int b, int chunk) const {
+    const int M = a.nin, f0 = 2 * chunk, ay = abs(b - M / 2);
+    const float2* ub = a.in + (long long)b * a.in_sb + f0;
+    for (int idx = tid; idx < M * 5; idx += NT) {
+      const int i = idx / 5, part = idx - 5 * i;
+      float2* dst = ibuf + i * kProdRow;
+      if (part == 0) {
+        cp_async16(dst, ub + (long long)i * a.in_si, true);
+      } else {
+        const int ax = abs(i - M / 2), p = max(ax, ay), q = min(ax, ay);
+        const int j = (part - 1) >> 1, h = (part - 1) & 1;
+        const float2* g = a.prod_g + ((long long)(p * (p + 1) / 2 + q) * a.prod_F + f0 + j) * a.prod_Z + a.prod_z0 + 2 * h;
+        cp_async16(dst + 2 + 4 * j + 2 * h, g, true);
+      }
+    }
+  }
+};
+
 // ------------------------------------------------------------------ radix-32 form
 // For n = 512, 1024: two Stockham stages, radix 32 then R2 = n / 32.  T = n / 32 threads per
 // transform, 32 values each.  Stage 1: thread j0 < T does butterfly j0 (a 32-point DFT of
@@ -715,24 +736,32 @@ __device__ __forceinline__ void store_bins32(const float2* v, float2* xbuf, int 
 
 // Persistent radix-32 form: same panels, staging, zero row and copy-out as
 // panel_fft_pipe_kernel; four CTA barriers per panel.
-template <int LOGN, int CP, bool INV>
+// PROD: the window holds transfer products staged by ProductStager (CP = 8).
+template <int LOGN, int CP, bool INV, bool PROD = false>
 __global__ void __launch_bounds__(R32Shape<LOGN, CP>::NT, R32Shape<LOGN, CP>::NT >= 256 ? 2 : 3) panel_fft32_kernel(
     const PanelArgs a, int npanel, int in_vec2, int out_vec2) {
   using S = R32Shape<LOGN, CP>;
   constexpr int n = S::n, T = S::T, NT = S::NT;
+  constexpr int RS = PROD ? kProdRow : CP;  // staging row length
+  static_assert(!PROD || CP == 8, "transfer products are staged for 8-channel panels");
   extern __shared__ float2 sm[];
   float2* xbuf = sm;                   // exchange buffer [XROWS][CP], then the bins [n][CP]
-  float2* ibuf = sm + S::XROWS * CP;   // staging [nin + 1][CP]
+  float2* ibuf = sm + S::XROWS * CP;   // staging [nin + 1][RS]
   const int tid = threadIdx.x;
   const int q = tid % CP, j0 = tid / CP;
   const int nlo = (a.lo_total + a.CLO - 1) / a.CLO;
   const int nchunk = ((a.hi_total + a.CHI - 1) / a.CHI) * nlo;
   const float inv_nlo = 1.f / (float)nlo;
-  if (tid < CP) ibuf[a.nin * CP + tid] = make_float2(0.f, 0.f);  // the zero row
-  float* mo = reinterpret_cast<float*>(ibuf + (a.nin + 1) * CP);  // mul_o[0..nout), if any
+  if (tid < RS) ibuf[a.nin * RS + tid] = make_float2(0.f, 0.f);  // the zero row
+  float* mo = reinterpret_cast<float*>(ibuf + (a.nin + 1) * RS);  // mul_o[0..nout), if any
   if (a.mul_o)
     for (int o = tid; o < a.nout; o += NT) mo[o] = __ldg(a.mul_o + o);
-  const WindowStager<CP, NT> issue{a, ibuf, tid, nlo, in_vec2, inv_nlo};
+  auto issue = [&](int b, int chunk) {
+    if constexpr (PROD)
+      ProductStager<NT>{a, ibuf, tid}(prod_row(b, a.nin), chunk);
+    else
+      WindowStager<CP, NT>{a, ibuf, tid, nlo, in_vec2, inv_nlo}(b, chunk);
+  };
 
   const int lpos = (j0 - a.in_off) & (n - 1);  // input index at FFT position j0
   const float2* rq = ibuf + q;
@@ -747,10 +776,18 @@ __global__ void __launch_bounds__(R32Shape<LOGN, CP>::NT, R32Shape<LOGN, CP>::NT
     __syncthreads();  // the staged window is complete, and the previous panel's copy-out is done
     const int hc = small_div(cc, nlo, inv_nlo);
     const int hi0 = hc * a.CHI, lo0 = (cc - hc * nlo) * a.CLO;
-    const int b = cb;
+    const int b = PROD ? prod_row(cb, a.nin) : cb;
     float2 v[32];
+    if constexpr (PROD) {  // u * g of the staged row: u of frequency q / 4, g of channel q
 #pragma unroll
-    for (int t = 0; t < 32; ++t) v[t] = rq[min((lpos + t * T) & (n - 1), a.nin) * CP];
+      for (int t = 0; t < 32; ++t) {
+        const float2* row = ibuf + min((lpos + t * T) & (n - 1), a.nin) * RS;
+        v[t] = cmul(row[q >> 2], row[2 + q]);
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < 32; ++t) v[t] = rq[min((lpos + t * T) & (n - 1), a.nin) * CP];
+    }
     if (a.mul_i) {
 #pragma unroll
       for (int t = 0; t < 32; ++t) {
@@ -912,6 +949,32 @@ cudaError_t launch_reg(const PanelArgs& a, cudaStream_t s) {
   const int out_vec2 = a.out_slo == 1 && a.CLO % 2 == 0 && a.lo_total % 2 == 0 &&
                        reinterpret_cast<uintptr_t>(optr) % (a.out_mag ? 8 : 16) == 0 && a.out_sb % 2 == 0 &&
                        a.out_si % 2 == 0 && a.out_shi % 2 == 0;
+  if (a.prod_g) {  // transfer products on load: the radix-32 persistent form only
+    if constexpr ((LOGN == 9 || LOGN == 10) && CP == 8) {
+      using R = R32Shape<LOGN, CP>;
+      if (a.CHI != 1 || a.hi_total != 1 || a.lo_total % CP != 0 || a.prod_F % 2 != 0 || a.prod_Z % 4 != 0 ||
+          a.prod_z0 % 4 != 0 || a.nin != S::n || a.batch != a.nin || a.in_slo != 1 || a.mul_i || a.mul_o)
+        return cudaErrorInvalidValue;
+      const size_t smemp = sizeof(float2) * ((size_t)R::XROWS * CP + (size_t)(a.nin + 1) * kProdRow);
+      auto kern = panel_fft32_kernel<LOGN, CP, INV, true>;
+      static bool configured_p = false;
+      static int occ_p = 1;
+      if (!configured_p) {
+        cudaError_t e = configure(kern, 220 * 1024);
+        if (e != cudaSuccess) return e;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, R::NT, smemp);
+        if (e != cudaSuccess) return e;
+        occ_p = std::max(nb, 1);
+        configured_p = true;
+      }
+      const int grid = (int)std::min<long long>(npanel, (long long)sms * occ_p);
+      kern<<<grid, R::NT, smemp, s>>>(a, (int)npanel, 0, out_vec2);
+      return cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   if constexpr (LOGN == 9 || LOGN == 10) {  // radix-32 persistent form
     using R = R32Shape<LOGN, CP>;
     const size_t smem32 = sizeof(float2) * ((size_t)R::XROWS * CP + (size_t)(a.nin + 1) * CP) + mo_bytes;

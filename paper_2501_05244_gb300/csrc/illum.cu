@@ -49,13 +49,13 @@ __device__ __forceinline__ float2 phasor_cycles(double t) {
 
 constexpr int kReseed = 16;  // recurrence steps between FP64 re-evaluations of the mask
 
-// out[z0 + zz][my][mx] = sum_f exp(+i k_f |x_p - x_v|) V[zz F + f][my][mx], one thread per voxel,
+// out[z0 + zz][my][mx] = sum_f exp(+i k_f |x_p - x_v|) V[zz cz + f cf][my][mx], one thread per voxel,
 // x_v = (cx + (mx - N/2) pitch, cy + (my - N/2) pitch, depth[z0 + zz]).  k_f = 2 pi kap[f]; the
 // distance and each phase in cycles are taken in FP64 (|k d| reaches hundreds of radians).  With
 // equispaced frequencies (kap[f] = kap0 + f dkap) the mask advances by one complex rotation per
 // frequency and is re-evaluated in FP64 every kReseed frequencies; otherwise every phase is.
-__global__ void illum_sum_kernel(const float2* __restrict__ V, int F, int N, int z0, int zg, IllumArgs a,
-                                 float2* __restrict__ out) {
+__global__ void illum_sum_kernel(const float2* __restrict__ V, int F, int N, int z0, int zg, int cz, int cf,
+                                 IllumArgs a, float2* __restrict__ out) {
   const int nn = N * N;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= zg * nn) return;
@@ -65,7 +65,8 @@ __global__ void illum_sum_kernel(const float2* __restrict__ V, int F, int N, int
   const double dy = a.cy + (double)(my - N / 2) * a.pitch - a.yp;
   const double dz = __ldg(a.depth + z0 + zz) - a.zp;
   const double d = sqrt(dx * dx + dy * dy + dz * dz);
-  const float2* v = V + (size_t)zz * F * nn + m;
+  const float2* v = V + (size_t)zz * cz * nn + m;
+  const size_t fs = (size_t)cf * nn;  // from one frequency's channel to the next
   float2 acc = make_float2(0.f, 0.f);
   if (a.equispaced) {
     const float2 rot = phasor_cycles(a.dkap * d);
@@ -73,7 +74,7 @@ __global__ void illum_sum_kernel(const float2* __restrict__ V, int F, int N, int
       float2 ph = phasor_cycles(__ldg(a.kap + f0) * d);
       const int f1 = min(F, f0 + kReseed);
       for (int f = f0; f < f1; ++f) {
-        const float2 x = __ldg(v + (size_t)f * nn);
+        const float2 x = __ldg(v + f * fs);
         acc.x = fmaf(ph.x, x.x, fmaf(-ph.y, x.y, acc.x));
         acc.y = fmaf(ph.x, x.y, fmaf(ph.y, x.x, acc.y));
         ph = cmul(ph, rot);
@@ -82,7 +83,7 @@ __global__ void illum_sum_kernel(const float2* __restrict__ V, int F, int N, int
   } else {
     for (int f = 0; f < F; ++f) {
       const float2 ph = phasor_cycles(__ldg(a.kap + f) * d);
-      const float2 x = __ldg(v + (size_t)f * nn);
+      const float2 x = __ldg(v + f * fs);
       acc.x = fmaf(ph.x, x.x, fmaf(-ph.y, x.y, acc.x));
       acc.y = fmaf(ph.x, x.y, fmaf(ph.y, x.x, acc.y));
     }
@@ -92,22 +93,23 @@ __global__ void illum_sum_kernel(const float2* __restrict__ V, int F, int N, int
 
 constexpr int kFrameChunk = 8;  // frames accumulated per pass over a voxel's F values
 
-// out[t][z0 + zz][my][mx] = sum_f A[t][f] V[zz F + f][my][mx] for t < T, A[t][f] = exp(+i w_f t_t)
+// out[t][z0 + zz][my][mx] = sum_f A[t][f] V[zz cz + f cf][my][mx] for t < T, A[t][f] = exp(+i w_f t_t)
 // (evaluated in FP64 on the host).  One thread per voxel, kFrameChunk frames per pass.
-__global__ void frames_sum_kernel(const float2* __restrict__ V, int F, int N, int Z, int z0, int zg,
+__global__ void frames_sum_kernel(const float2* __restrict__ V, int F, int N, int Z, int z0, int zg, int cz, int cf,
                                   const float2* __restrict__ A, int T, float2* __restrict__ out) {
   const int nn = N * N;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= zg * nn) return;
   const int zz = idx / nn, m = idx - zz * nn;
-  const float2* v = V + (size_t)zz * F * nn + m;
+  const float2* v = V + (size_t)zz * cz * nn + m;
+  const size_t fs = (size_t)cf * nn;
   for (int t0 = 0; t0 < T; t0 += kFrameChunk) {
     float2 acc[kFrameChunk];
 #pragma unroll
     for (int j = 0; j < kFrameChunk; ++j) acc[j] = make_float2(0.f, 0.f);
     const int nt = min(kFrameChunk, T - t0);
     for (int f = 0; f < F; ++f) {
-      const float2 x = __ldg(v + (size_t)f * nn);
+      const float2 x = __ldg(v + f * fs);
 #pragma unroll
       for (int j = 0; j < kFrameChunk; ++j) {
         if (j < nt) {
@@ -136,21 +138,22 @@ cudaError_t launch_transfer_depths(const float2* U, const float2* Gc, int M, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_illum_sum(const float2* V, int F, int N, int z0, int zg, const IllumArgs& a, float2* out,
-                             cudaStream_t s) {
+cudaError_t launch_illum_sum(const float2* V, int F, int N, int z0, int zg, int cz, int cf, const IllumArgs& a,
+                             float2* out, cudaStream_t s) {
   const long long n = (long long)zg * N * N;
   if (F < 1 || N < 1 || zg < 1 || n >= (1LL << 31)) return cudaErrorInvalidValue;
   const int threads = 256;
-  illum_sum_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(V, F, N, z0, zg, a, out);
+  illum_sum_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(V, F, N, z0, zg, cz, cf, a, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_frames_sum(const float2* V, int F, int N, int Z, int z0, int zg, const float2* A, int T,
-                              float2* out, cudaStream_t s) {
+cudaError_t launch_frames_sum(const float2* V, int F, int N, int Z, int z0, int zg, int cz, int cf, const float2* A,
+                              int T, float2* out, cudaStream_t s) {
   const long long n = (long long)zg * N * N;
   if (F < 1 || N < 1 || zg < 1 || T < 1 || n >= (1LL << 31)) return cudaErrorInvalidValue;
   const int threads = 256;
-  frames_sum_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(V, F, N, Z, z0, zg, A, T, out);
+  frames_sum_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(V, F, N, Z, z0, zg, cz, cf, A, T,
+                                                                                out);
   return cudaGetLastError();
 }
 

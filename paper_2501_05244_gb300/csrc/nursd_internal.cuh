@@ -89,6 +89,13 @@ struct PanelArgs {
   int store_hi_fastest;  // consecutive threads store consecutive hi channels
   int store_o_fastest;   // consecutive threads store consecutive outputs o
   const float2* twiddle;  // the FFT table (kTwiddleEntries values, 16-byte aligned)
+  // Transfer products formed while the window is staged (radix-32 kernels, CP = 8): with
+  // prod_g set, channel 4 j + zz of panel chunk c (f0 = 2 c, j < 2, zz < 4) at window row i of
+  // batch item b is in[b in_sb + i in_si + f0 + j] * prod_g[class(i - nin/2, b - nin/2)][f0 + j]
+  // [prod_z0 + zz], the table [class][prod_F][prod_Z] of the symmetry classes
+  // {(+-p, +-q), (+-q, +-p)} at index p (p + 1) / 2 + q.
+  const float2* prod_g;
+  int prod_F, prod_Z, prod_z0;
 };
 
 // Launches the panel FFT of length 2^logn (4 <= 2^logn <= 2048). Returns a cudaError_t.
@@ -240,13 +247,13 @@ struct IllumArgs {
   double dkap;           // kap[f + 1] - kap[f] when equispaced
   int equispaced;        // kap[f] = kap[0] + f dkap to FP64 rounding
 };
-// out[z0 + zz][my][mx] = sum_f exp(+i k_f |x_p - x_v|) V[zz*F + f][my][mx], V channel-major
-// [zg*F][N][N], out [Z][N][N].
-cudaError_t launch_illum_sum(const float2* V, int F, int N, int z0, int zg, const IllumArgs& a, float2* out,
-                             cudaStream_t s);
-// out[t][z0 + zz][my][mx] = sum_f A[t][f] V[zz*F + f][my][mx], A [T][F], out [T][Z][N][N].
-cudaError_t launch_frames_sum(const float2* V, int F, int N, int Z, int z0, int zg, const float2* A, int T,
-                              float2* out, cudaStream_t s);
+// out[z0 + zz][my][mx] = sum_f exp(+i k_f |x_p - x_v|) V[zz*cz + f*cf][my][mx], V channel-major
+// [zg*F][N][N] (channel of depth zz and frequency f at zz*cz + f*cf), out [Z][N][N].
+cudaError_t launch_illum_sum(const float2* V, int F, int N, int z0, int zg, int cz, int cf, const IllumArgs& a,
+                             float2* out, cudaStream_t s);
+// out[t][z0 + zz][my][mx] = sum_f A[t][f] V[zz*cz + f*cf][my][mx], A [T][F], out [T][Z][N][N].
+cudaError_t launch_frames_sum(const float2* V, int F, int N, int Z, int z0, int zg, int cz, int cf, const float2* A,
+                              int T, float2* out, cudaStream_t s);
 // SRSD contraction for one depth: Y[k][z] = sum_f Phat[k][f] * Gs_z[cls(k)][f].
 cudaError_t launch_contract_depth(const float2* Phat, const float2* Gs_z, const int2* cls_pq, int ncls, int M, int F,
                                   int Z, int z, float2* Y, cudaStream_t s);

@@ -146,7 +146,7 @@ def test_several_depth_groups_with_a_ragged_last_one():
     # F = 128 puts 4 depths in a group (512 channels), so Z = 6 runs a group of 4 and one of 2
     wl = workload_c1()
     g = wl.geom
-    om, wt = nursd.phasor_frequencies(g.lambda_c, g.dt, g.t_pad, 128)
+    om, wt = nursd.phasor_frequencies(g.lambda_c, g.dt, 8192, 128)  # 128 bins of a longer DFT stay positive
     depths = np.linspace(0.55, 1.45, 6)
     plan = nursd.Plan(g.N, g.pitch, g.center, depths, om, wt, max_points=len(wl.xy))
     plan.set_points(torch.from_numpy(wl.xy).cuda())
@@ -156,7 +156,7 @@ def test_several_depth_groups_with_a_ragged_last_one():
     times = g.t0 + np.array([0.4e-9, 2.5e-9, 5.1e-9])
     Vt = plan.transient_frames(Pg, times).cpu().numpy()
     assert plan.sync_status() == 0
-    om_o, _ = O.phasor_frequencies(g.lambda_c, g.dt, g.t_pad, 128)
+    om_o, _ = O.phasor_frequencies(g.lambda_c, g.dt, 8192, 128)
     M = 2 * g.N
     U = O.nudft_type1(P, O.relay_theta(wl.xy, g.center, g.pitch, M), M)
     G = O.transfer_functions(depths, om_o, M, g.pitch)
@@ -173,3 +173,27 @@ def test_empty_point_set_gives_zero_volume_and_frames():
     assert float(plan.forward_illuminated(P, ILLUM).abs().max()) == 0.0
     assert float(plan.transient_frames(P, [0.0, 1e-9]).abs().max()) == 0.0
     assert plan.sync_status() == 0
+
+
+def test_products_formed_in_the_first_inverse_pass_match_oracle():
+    # M = 512 with Z % 4 == 0 and F even: the kx pass stages U and the table rows and forms the
+    # products itself (channels 4 f + zz); full outputs against the oracle
+    N, pitch, F = 256, 2.0 / 256, 8
+    r = np.random.default_rng(BASE_SEED + 126)
+    xy = r.uniform(-0.999, 0.999, (500, 2)).astype(np.float32)
+    om = 2 * math.pi * np.linspace(4.2e9, 5.8e9, F)
+    depths = np.array([0.6, 1.1, 1.7, 2.4])
+    plan = nursd.Plan(N, pitch, (0.0, 0.0), depths, om, max_points=len(xy))
+    plan.set_points(torch.from_numpy(xy).cuda())
+    P = random_phasors(len(xy), F, seed=BASE_SEED + 127)
+    Pg = torch.from_numpy(P).cuda()
+    xp = (0.35, -0.6, 0.0)
+    V = plan.forward_illuminated(Pg, xp).cpu().numpy()
+    times = np.array([3.0e-9, 6.5e-9])
+    Vt = plan.transient_frames(Pg, times).cpu().numpy()
+    assert plan.sync_status() == 0
+    M = 2 * N
+    U = O.nudft_type1(P, O.relay_theta(xy, (0.0, 0.0), pitch, M), M)
+    G = O.transfer_functions(depths, om, M, pitch)
+    assert rel(V, O.propagate_illuminated(U, G, N, xp, (0.0, 0.0), pitch, depths, om)) < TOL
+    assert rel(Vt, O.transient_frames(U, G, N, times, om)) < TOL
