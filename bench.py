@@ -346,11 +346,13 @@ def measure_rows(wl, peak):
         assert plan.sync_status() == 0
         M, F, Z, N = 2 * g.N, g.F, g.Z, g.N
         ncls = (M // 2 + 1) * (M // 2 + 2) // 2
-        zg = min(Z, max(1, 512 // F))
+        fused = Z % 4 == 0 and F % 2 == 0 and M in (512, 1024)  # products formed inside the kx pass
+        zg = 4 if fused else min(Z, max(1, 512 // F))
         # per group of zg depths (C = zg F channels): spectrum + zg table values per class and f in,
-        # the products, half inverse and per-frequency volumes each written and read once, volume out
-        per_group = lambda zn: (M * M * F + ncls * F * zn + 2 * M * M * zn * F + 2 * M * N * zn * F
-                                + 2 * N * N * zn * F + N * N * zn) * 8
+        # the half inverse and per-frequency volumes (and, unfused, the products) each written and
+        # read once, volume out
+        per_group = lambda zn: (M * M * F + ncls * F * zn + (0 if fused else 2 * M * M * zn * F)
+                                + 2 * M * N * zn * F + 2 * N * N * zn * F + N * N * zn) * 8
         groups = [min(zg, Z - z0) for z0 in range(0, Z, zg)]
         bytes_pf = sum(per_group(zn) for zn in groups)
         units = Z * N * N * F
@@ -359,7 +361,7 @@ def measure_rows(wl, peak):
                 "ms": ms, "voxel_freq_per_s": units / (ms / 1e3), "ms_16_frames": ms_f,
                 "per_frequency_stages": {"algorithmic_bytes": bytes_pf,
                                          "ms": ms - st.get("spread", 0) - st.get("fft_x", 0) - st.get("fft_y", 0),
-                                         "depth_group": zg},
+                                         "depth_group": zg, "products_in_kx_pass": fused},
                 "hbm_frac_of_call": (bytes_pf / (ms / 1e3) / 1e9) / peak, "stages_ms": st}
 
     def srsd_points():
