@@ -74,6 +74,15 @@ struct nursd_plan_s {
   std::vector<double> srsd_pitch;
   std::vector<double> srsd_scale;  // srsd_pitch / pitch (host copy of srsd_scale_d)
   double* srsd_scale_d = nullptr;  // device [Z]
+  // SRSD depths with scale >= 1 take the scaled DFT by interpolation of one oversampled spectrum:
+  // si_yh [2M][2M][F], scratch si_scr, per depth the first tap m0 [M] and weights [M][w] of the
+  // coordinates 2 kappa / s, and the rows ylo .. ylo + R - 1 its y taps reach
+  float2 *si_yh = nullptr, *si_scr = nullptr;
+  int* si_m0 = nullptr;
+  float* si_wt = nullptr;
+  std::vector<int> si_ylo, si_R;
+  std::vector<char> si_interp;
+  bool si_any = false;
   float2* Gs = nullptr;
   float2* chirp = nullptr;
   float2* bhat = nullptr;
@@ -316,10 +325,33 @@ int build_srsd_chirps(nursd_plan_s* p, cudaStream_t s) {
   }
   p->srsd_scale.resize(Z);
   for (int z = 0; z < Z; ++z) p->srsd_scale[z] = p->srsd_pitch[z] / p->pitch;
+  // interpolated depths: coordinate u = 2 kappa / s on the 2M-point grid, taps m0 .. m0 + w - 1 with
+  // ES weights phi(2 (m - u) / w) in FP64 (the same kernel and beta as the spatial NUFFT)
+  std::vector<int> m0v;
+  std::vector<float> wtv;
+  if (p->si_any) {
+    const int w = p->w;
+    const double beta = p->beta;  // the kernel whose transform the deconvolution table inverts
+    m0v.assign((size_t)Z * M, 0);
+    wtv.assign((size_t)Z * M * w, 0.f);
+    for (int z = 0; z < Z; ++z) {
+      if (!p->si_interp[z]) continue;
+      for (int i = 0; i < M; ++i) {
+        const double u = 2.0 * (i - M / 2) / p->srsd_scale[z];
+        const int m0 = (int)std::ceil(u - 0.5 * w);
+        m0v[(size_t)z * M + i] = m0;
+        for (int t = 0; t < w; ++t) wtv[((size_t)z * M + i) * w + t] = (float)es_kernel(2.0 * (m0 + t - u) / w, beta);
+      }
+    }
+  }
   int rc = from_cuda(cudaMemcpyAsync(p->chirp, ch.data(), sizeof(float2) * ch.size(), cudaMemcpyHostToDevice, s));
   if (rc == NURSD_OK)
     rc = from_cuda(
         cudaMemcpyAsync(p->srsd_scale_d, p->srsd_scale.data(), sizeof(double) * Z, cudaMemcpyHostToDevice, s));
+  if (rc == NURSD_OK && p->si_any)
+    rc = from_cuda(cudaMemcpyAsync(p->si_m0, m0v.data(), sizeof(int) * m0v.size(), cudaMemcpyHostToDevice, s));
+  if (rc == NURSD_OK && p->si_any)
+    rc = from_cuda(cudaMemcpyAsync(p->si_wt, wtv.data(), sizeof(float) * wtv.size(), cudaMemcpyHostToDevice, s));
   if (rc == NURSD_OK) rc = from_cuda(cudaMemcpyAsync(db, b.data(), sizeof(float2) * b.size(), cudaMemcpyHostToDevice, s));
   if (rc == NURSD_OK) {  // FFT of each depth's contiguous row of 2M values
     const int logL = ilog2(L2);
@@ -437,7 +469,8 @@ int run_propagate(nursd_plan_s* p, const float2* spec, void* out, cudaStream_t s
 }
 
 // Scaled spectra Y^S_z [M][M][Z] (into p->Y) from a NUFFT-1 spectrum U (in p->U): see srsd_forward in
-// nursd.h.
+// nursd.h.  Depths with scale >= 1 take the scaled DFT by ES interpolation of one oversampled spectrum
+// (srsd_interp.cu); the others by Bluestein's chirp-z.
 int run_srsd_spectra(nursd_plan_s* p, cudaStream_t s) {
   const int M = p->M, F = p->F, Z = p->Z;
   const int logM = ilog2(M), logL = logM + 1;
@@ -450,7 +483,52 @@ int run_srsd_spectra(nursd_plan_s* p, cudaStream_t s) {
       e = axis_pass(p, p->R1, p->fine, logM, true, F, M, F, (long long)M * F, F, (long long)M * F, M, -M / 2, M,
                     -M / 2, nullptr, nullptr, 1.f / ((float)M * (float)M), s);
   }
+  if (e == cudaSuccess && p->si_any) {  // oversampled spectrum of u / (psi_hat x psi_hat), shared by the
+                                        // interpolated depths: FFT_2M along nx, then along ny
+    StageTimer t(p, NURSD_STAGE_SRSD, s, 2);
+    const int L = 2 * M;
+    PanelArgs a = panel_base(p);  // u [ny][nx][F] -> si_scr [ny][mx][F]
+    a.in = p->fine;
+    a.in_sb = (long long)M * F;
+    a.in_si = F;
+    a.in_slo = 1;
+    a.mul_i = p->deconv;  // 1 / psi_hat(n), window index i <-> n = i - M/2
+    a.out = p->si_scr;
+    a.out_sb = (long long)L * F;
+    a.out_si = F;
+    a.out_slo = 1;
+    a.nin = M;
+    a.in_off = -M / 2;
+    a.nout = L;
+    a.out_off = -L / 2;
+    a.lo_total = F;
+    a.CLO = panel_width(logL);
+    a.batch = M;
+    e = launch_panel_fft(logL, false, a, s);
+    if (e == cudaSuccess) {  // si_scr columns -> si_yh [my][mx][F]
+      PanelArgs b = a;
+      b.in = p->si_scr;
+      b.in_sb = F;
+      b.in_si = (long long)L * F;
+      b.out = p->si_yh;
+      b.out_sb = F;
+      b.out_si = (long long)L * F;
+      b.batch = L;
+      e = launch_panel_fft(logL, false, b, s);
+    }
+  }
   for (int z = 0; e == cudaSuccess && z < Z; ++z) {
+    if (p->si_interp[z]) {  // scale >= 1: the x taps over the rows the y taps reach, then the y taps
+                            // fused with the depth's contraction
+      StageTimer t(p, NURSD_STAGE_SRSD, s, 2);
+      const int* m0 = p->si_m0 + (size_t)z * M;
+      const float* wt = p->si_wt + (size_t)z * M * p->w;
+      e = launch_srsd_interp_x(p->si_yh, 2 * M, M, F, p->si_ylo[z], p->si_R[z], p->w, m0, wt, p->si_scr, s);
+      if (e == cudaSuccess)
+        e = launch_srsd_interp_y_contract(p->si_scr, M, F, Z, z, p->si_ylo[z], p->w, m0, wt,
+                                          p->Gs + (size_t)z * p->ncls * F, p->Y, s);
+      continue;
+    }
     StageTimer t(p, NURSD_STAGE_SRSD, s, 3);
     const float2* ch = p->chirp + (size_t)z * M;
     const float2* bh = p->bhat + (size_t)z * 2 * M;
@@ -854,6 +932,30 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
   if (ok && !p->srsd_pitch.empty())
     ok = p->alloc(p->Gs, (size_t)p->ncls * p->F * p->Z) && p->alloc(p->chirp, (size_t)p->Z * p->M) &&
          p->alloc(p->bhat, (size_t)p->Z * 2 * p->M) && p->alloc(p->srsd_scale_d, p->Z);
+  if (ok && !p->srsd_pitch.empty()) {  // taps of the interpolated depths (scale >= 1)
+    const int M = p->M, w = p->w;
+    p->si_interp.assign(p->Z, 0);
+    p->si_ylo.assign(p->Z, 0);
+    p->si_R.assign(p->Z, 0);
+    int Rmax = 0;
+    for (int z = 0; z < p->Z; ++z) {
+      const double sc = p->srsd_pitch[z] / p->pitch;
+      if (!(sc >= 1.0) || p->F > 256) continue;
+      p->si_interp[z] = 1;
+      const int lo = (int)std::ceil(2.0 * (-M / 2) / sc - 0.5 * w);
+      const int hi = (int)std::ceil(2.0 * (M / 2 - 1) / sc - 0.5 * w) + w - 1;
+      p->si_ylo[z] = lo;
+      p->si_R[z] = hi - lo + 1;
+      Rmax = std::max(Rmax, hi - lo + 1);
+      p->si_any = true;
+    }
+    if (p->si_any) {
+      const size_t L = 2 * (size_t)M;
+      ok = p->alloc(p->si_yh, L * L * p->F) &&
+           p->alloc(p->si_scr, std::max(M * L, (size_t)Rmax * M) * p->F) &&
+           p->alloc(p->si_m0, (size_t)p->Z * M) && p->alloc(p->si_wt, (size_t)p->Z * M * w);
+    }
+  }
   if (!ok) {
     delete p;
     return NURSD_ERR_OOM;

@@ -1,0 +1,119 @@
+// Scaled DFT of SRSD (Sec. 4, Eq. SFFT) as a type-2 evaluation of one shared oversampled FFT.
+//
+// Along one axis the scaled DFT of x[n], n in I_M, is the DTFT at the frequencies 2 pi kappa / (M s),
+//   X(kappa) = sum_n x[n] exp(-2 pi i kappa n / (M s)),  kappa in I_M,
+// i.e. at coordinate u = L kappa / (M s) = 2 kappa / s of the L = 2M point grid.  With
+// xh[m] = FFT_L[x / psi_hat][m] (psi_hat the Fourier transform of the ES kernel phi, the same
+// deconvolution as the spatial NUFFT) the ES interpolation
+//   X(kappa) ~ sum_{t < w} phi(2 (m0 + t - u) / w) xh[m0 + t],  m0 = ceil(u - w / 2),
+// reproduces it to the kernel's accuracy (Poisson summation: exp(-2 pi i m n / L) summed against
+// phi over m gives psi_hat(n) exp(-2 pi i u n / L)).  The 2D FFT of u / (psi_hat x psi_hat) is taken
+// once per call for every depth; each depth then needs two w-tap passes over the rows and columns
+// its scale reaches, instead of four 2M-point FFTs per line.  The second pass is fused with the
+// depth's transfer contraction Y_z(kappa) = sum_f Phat_{z,f}(kappa) Gs_z[class(kappa)][f].
+#include "nursd_internal.cuh"
+
+namespace nursd {
+namespace {
+
+__device__ __forceinline__ int wrap_mod(int m, int L) {
+  const int r = m % L;
+  return r < 0 ? r + L : r;
+}
+
+// P1[r][kx][f] = sum_t wt[kx][t] Yh[row(ylo + r)][col(m0[kx] + t)][f]: the x pass of one depth over
+// the R rows its y taps reach.  Yh [L][L][F] at index m + L/2 (periodic in m); one thread per
+// (r, kx, f), f fastest.
+__global__ void srsd_interp_x_kernel(const float2* __restrict__ Yh, int L, int M, int F, int ylo, int R, int w,
+                                     const int* __restrict__ m0, const float* __restrict__ wt,
+                                     float2* __restrict__ P1) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)R * M * F) return;
+  const int f = (int)(idx % F);
+  const long long rest = idx / F;
+  const int kx = (int)(rest % M), r = (int)(rest / M);
+  const float2* row = Yh + (size_t)wrap_mod(ylo + r + L / 2, L) * L * F + f;
+  const int mb = __ldg(m0 + kx) + L / 2;
+  const float* wk = wt + (size_t)kx * w;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int t = 0; t < w; ++t) {
+    const float c = __ldg(wk + t);
+    const float2 v = __ldg(row + (size_t)wrap_mod(mb + t, L) * F);
+    acc.x = fmaf(c, v.x, acc.x);
+    acc.y = fmaf(c, v.y, acc.y);
+  }
+  P1[idx] = acc;
+}
+
+// Y[k][z] = sum_f Gs_z[class(k)][f] * sum_t wt[ky][t] P1[m0[ky] + t - ylo][kx][f], k = (ky, kx):
+// the y pass fused with the depth's contraction.  One warp per mode, lanes over f (F <= 32 * 8),
+// the warp's partial sums reduced by shuffles.
+constexpr int kMaxFPerLane = 8;
+__global__ void srsd_interp_y_contract_kernel(const float2* __restrict__ P1, int M, int F, int Z, int z, int ylo,
+                                              int w, const int* __restrict__ m0, const float* __restrict__ wt,
+                                              const float2* __restrict__ Gs_z, float2* __restrict__ Y) {
+  const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (warp >= M * M) return;
+  const int kyi = warp / M, kxi = warp - kyi * M;
+  const int ax = abs(kxi - M / 2), ay = abs(kyi - M / 2), p = max(ax, ay), q = min(ax, ay);
+  const float2* g = Gs_z + (size_t)(p * (p + 1) / 2 + q) * F;
+  const int r0 = __ldg(m0 + kyi) - ylo;
+  const float* wk = wt + (size_t)kyi * w;
+  float2 ph[kMaxFPerLane];
+#pragma unroll
+  for (int j = 0; j < kMaxFPerLane; ++j) ph[j] = make_float2(0.f, 0.f);
+  for (int t = 0; t < w; ++t) {
+    const float c = __ldg(wk + t);
+    const float2* row = P1 + ((size_t)(r0 + t) * M + kxi) * F;
+#pragma unroll
+    for (int j = 0; j < kMaxFPerLane; ++j) {
+      const int f = lane + 32 * j;
+      if (f < F) {
+        const float2 v = __ldg(row + f);
+        ph[j].x = fmaf(c, v.x, ph[j].x);
+        ph[j].y = fmaf(c, v.y, ph[j].y);
+      }
+    }
+  }
+  float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < kMaxFPerLane; ++j) {
+    const int f = lane + 32 * j;
+    if (f < F) {
+      const float2 gv = __ldg(g + f);
+      acc.x = fmaf(ph[j].x, gv.x, fmaf(-ph[j].y, gv.y, acc.x));
+      acc.y = fmaf(ph[j].x, gv.y, fmaf(ph[j].y, gv.x, acc.y));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane == 0) Y[(size_t)warp * Z + z] = acc;
+}
+
+}  // namespace
+
+cudaError_t launch_srsd_interp_x(const float2* Yh, int L, int M, int F, int ylo, int R, int w, const int* m0,
+                                 const float* wt, float2* P1, cudaStream_t s) {
+  const long long n = (long long)R * M * F;
+  if (L < 2 || M < 2 || F < 1 || R < 1 || w < 1 || n >= (1LL << 40)) return cudaErrorInvalidValue;
+  const int threads = 256;
+  const long long blocks = (n + threads - 1) / threads;
+  if (blocks >= (1LL << 31)) return cudaErrorInvalidValue;
+  srsd_interp_x_kernel<<<(unsigned)blocks, threads, 0, s>>>(Yh, L, M, F, ylo, R, w, m0, wt, P1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_srsd_interp_y_contract(const float2* P1, int M, int F, int Z, int z, int ylo, int w, const int* m0,
+                                          const float* wt, const float2* Gs_z, float2* Y, cudaStream_t s) {
+  if (M < 2 || F < 1 || F > 32 * kMaxFPerLane || z < 0 || z >= Z || w < 1) return cudaErrorInvalidValue;
+  const long long threads_total = (long long)M * M * 32;
+  const int threads = 256;
+  srsd_interp_y_contract_kernel<<<(unsigned)((threads_total + threads - 1) / threads), threads, 0, s>>>(
+      P1, M, F, Z, z, ylo, w, m0, wt, Gs_z, Y);
+  return cudaGetLastError();
+}
+
+}  // namespace nursd

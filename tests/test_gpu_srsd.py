@@ -134,3 +134,17 @@ def test_srsd_points_with_no_voxels():
     out = plan.srsd_forward_points(torch.from_numpy(P).cuda(), torch.zeros((Z, 0, 2), dtype=torch.float32, device="cuda"))
     assert tuple(out.shape) == (Z, 0)
     assert plan.sync_status() == 0
+
+
+def test_srsd_scales_below_and_above_one():
+    # depths with s < 1 take Bluestein's chirp-z, the others the interpolated scaled DFT
+    N, L, F, Z = 32, 1200, 16, 6
+    xy, P, om, depths, _, pitch, center = case(N, L, F, Z, 9)
+    scales = np.linspace(0.6, 1.8, Z)
+    plan = nursd.Plan(N, pitch, center, depths, om, max_points=L, srsd_pitch=scales * pitch)
+    plan.set_points(torch.from_numpy(xy).cuda())
+    V = plan.srsd_forward(torch.from_numpy(P).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    ref = O.srsd_forward(P, xy, center, pitch, N, depths, scales, om)
+    for z in range(Z):
+        assert rel(V[z], ref[z]) < TOL, (z, scales[z])
