@@ -46,51 +46,59 @@ __global__ void srsd_interp_x_kernel(const float2* __restrict__ Yh, int L, int M
 }
 
 // Y[k][z] = sum_f Gs_z[class(k)][f] * sum_t wt[ky][t] P1[m0[ky] + t - ylo][kx][f], k = (ky, kx):
-// the y pass fused with the depth's contraction.  One warp per mode, lanes over f (F <= 32 * 8),
-// the warp's partial sums reduced by shuffles.
+// the y pass fused with the depth's contraction.  One warp per column kx and run of kYRun
+// consecutive ky (consecutive warps take consecutive kx), lanes over f (F <= 32 * 8): ky and ky + 1
+// share all but about 2 / s of their w rows, so a warp finds most of its P1 rows in L1.  The f sum
+// is reduced by shuffles.
 constexpr int kMaxFPerLane = 8;
+constexpr int kYRun = 32;
 __global__ void srsd_interp_y_contract_kernel(const float2* __restrict__ P1, int M, int F, int Z, int z, int ylo,
                                               int w, const int* __restrict__ m0, const float* __restrict__ wt,
                                               const float2* __restrict__ Gs_z, float2* __restrict__ Y) {
   const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-  if (warp >= M * M) return;
-  const int kyi = warp / M, kxi = warp - kyi * M;
-  const int ax = abs(kxi - M / 2), ay = abs(kyi - M / 2), p = max(ax, ay), q = min(ax, ay);
-  const float2* g = Gs_z + (size_t)(p * (p + 1) / 2 + q) * F;
-  const int r0 = __ldg(m0 + kyi) - ylo;
-  const float* wk = wt + (size_t)kyi * w;
-  float2 ph[kMaxFPerLane];
+  const int nrun = (M + kYRun - 1) / kYRun;
+  if (warp >= M * nrun) return;
+  const int kxi = warp % M, run = warp / M;
+  const int ax = abs(kxi - M / 2);
+  const int ky1 = min(M, (run + 1) * kYRun);
+  for (int kyi = run * kYRun; kyi < ky1; ++kyi) {
+    const int ay = abs(kyi - M / 2), p = max(ax, ay), q = min(ax, ay);
+    const float2* g = Gs_z + (size_t)(p * (p + 1) / 2 + q) * F;
+    const int r0 = __ldg(m0 + kyi) - ylo;
+    const float* wk = wt + (size_t)kyi * w;
+    float2 ph[kMaxFPerLane];
 #pragma unroll
-  for (int j = 0; j < kMaxFPerLane; ++j) ph[j] = make_float2(0.f, 0.f);
-  for (int t = 0; t < w; ++t) {
-    const float c = __ldg(wk + t);
-    const float2* row = P1 + ((size_t)(r0 + t) * M + kxi) * F;
+    for (int j = 0; j < kMaxFPerLane; ++j) ph[j] = make_float2(0.f, 0.f);
+    for (int t = 0; t < w; ++t) {
+      const float c = __ldg(wk + t);
+      const float2* row = P1 + ((size_t)(r0 + t) * M + kxi) * F;
+#pragma unroll
+      for (int j = 0; j < kMaxFPerLane; ++j) {
+        const int f = lane + 32 * j;
+        if (f < F) {
+          const float2 v = __ldg(row + f);
+          ph[j].x = fmaf(c, v.x, ph[j].x);
+          ph[j].y = fmaf(c, v.y, ph[j].y);
+        }
+      }
+    }
+    float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < kMaxFPerLane; ++j) {
       const int f = lane + 32 * j;
       if (f < F) {
-        const float2 v = __ldg(row + f);
-        ph[j].x = fmaf(c, v.x, ph[j].x);
-        ph[j].y = fmaf(c, v.y, ph[j].y);
+        const float2 gv = __ldg(g + f);
+        acc.x = fmaf(ph[j].x, gv.x, fmaf(-ph[j].y, gv.y, acc.x));
+        acc.y = fmaf(ph[j].x, gv.y, fmaf(ph[j].y, gv.x, acc.y));
       }
     }
-  }
-  float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int j = 0; j < kMaxFPerLane; ++j) {
-    const int f = lane + 32 * j;
-    if (f < F) {
-      const float2 gv = __ldg(g + f);
-      acc.x = fmaf(ph[j].x, gv.x, fmaf(-ph[j].y, gv.y, acc.x));
-      acc.y = fmaf(ph[j].x, gv.y, fmaf(ph[j].y, gv.x, acc.y));
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
     }
+    if (lane == 0) Y[((size_t)kyi * M + kxi) * Z + z] = acc;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-  }
-  if (lane == 0) Y[(size_t)warp * Z + z] = acc;
 }
 
 }  // namespace
@@ -109,7 +117,7 @@ cudaError_t launch_srsd_interp_x(const float2* Yh, int L, int M, int F, int ylo,
 cudaError_t launch_srsd_interp_y_contract(const float2* P1, int M, int F, int Z, int z, int ylo, int w, const int* m0,
                                           const float* wt, const float2* Gs_z, float2* Y, cudaStream_t s) {
   if (M < 2 || F < 1 || F > 32 * kMaxFPerLane || z < 0 || z >= Z || w < 1) return cudaErrorInvalidValue;
-  const long long threads_total = (long long)M * M * 32;
+  const long long threads_total = (long long)M * ((M + kYRun - 1) / kYRun) * 32;
   const int threads = 256;
   srsd_interp_y_contract_kernel<<<(unsigned)((threads_total + threads - 1) / threads), threads, 0, s>>>(
       P1, M, F, Z, z, ylo, w, m0, wt, Gs_z, Y);
