@@ -75,12 +75,11 @@ struct nursd_plan_s {
   std::vector<double> srsd_scale;  // srsd_pitch / pitch (host copy of srsd_scale_d)
   double* srsd_scale_d = nullptr;  // device [Z]
   // SRSD depths with scale >= 1 take the scaled DFT by interpolation of one oversampled spectrum:
-  // si_yh [2M][2M][F], scratch si_scr, per depth the first tap m0 [M] and weights [M][w] of the
-  // coordinates 2 kappa / s, and the rows ylo .. ylo + R - 1 its y taps reach
+  // si_yh [2M][2M][F], its half-transformed rows si_scr [M][2M][F], and per depth the first tap
+  // m0 [M] and weights [M][w] of the coordinates 2 kappa / s
   float2 *si_yh = nullptr, *si_scr = nullptr;
   int* si_m0 = nullptr;
   float* si_wt = nullptr;
-  std::vector<int> si_ylo, si_R;
   std::vector<char> si_interp;
   bool si_any = false;
   float2* Gs = nullptr;
@@ -518,15 +517,11 @@ int run_srsd_spectra(nursd_plan_s* p, cudaStream_t s) {
     }
   }
   for (int z = 0; e == cudaSuccess && z < Z; ++z) {
-    if (p->si_interp[z]) {  // scale >= 1: the x taps over the rows the y taps reach, then the y taps
-                            // fused with the depth's contraction
-      StageTimer t(p, NURSD_STAGE_SRSD, s, 2);
-      const int* m0 = p->si_m0 + (size_t)z * M;
-      const float* wt = p->si_wt + (size_t)z * M * p->w;
-      e = launch_srsd_interp_x(p->si_yh, 2 * M, M, F, p->si_ylo[z], p->si_R[z], p->w, m0, wt, p->si_scr, s);
-      if (e == cudaSuccess)
-        e = launch_srsd_interp_y_contract(p->si_scr, M, F, Z, z, p->si_ylo[z], p->w, m0, wt,
-                                          p->Gs + (size_t)z * p->ncls * F, p->Y, s);
+    if (p->si_interp[z]) {  // scale >= 1: both taps and the depth's contraction in one pass
+      StageTimer t(p, NURSD_STAGE_SRSD, s, 1);
+      e = launch_srsd_interp_xy_contract(p->si_yh, 2 * M, M, F, Z, z, p->w, p->si_m0 + (size_t)z * M,
+                                         p->si_wt + (size_t)z * M * p->w, p->Gs + (size_t)z * p->ncls * F, p->Y,
+                                         s);
       continue;
     }
     StageTimer t(p, NURSD_STAGE_SRSD, s, 3);
@@ -935,24 +930,15 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
   if (ok && !p->srsd_pitch.empty()) {  // taps of the interpolated depths (scale >= 1)
     const int M = p->M, w = p->w;
     p->si_interp.assign(p->Z, 0);
-    p->si_ylo.assign(p->Z, 0);
-    p->si_R.assign(p->Z, 0);
-    int Rmax = 0;
     for (int z = 0; z < p->Z; ++z) {
       const double sc = p->srsd_pitch[z] / p->pitch;
       if (!(sc >= 1.0) || p->F > 256) continue;
       p->si_interp[z] = 1;
-      const int lo = (int)std::ceil(2.0 * (-M / 2) / sc - 0.5 * w);
-      const int hi = (int)std::ceil(2.0 * (M / 2 - 1) / sc - 0.5 * w) + w - 1;
-      p->si_ylo[z] = lo;
-      p->si_R[z] = hi - lo + 1;
-      Rmax = std::max(Rmax, hi - lo + 1);
       p->si_any = true;
     }
     if (p->si_any) {
       const size_t L = 2 * (size_t)M;
-      ok = p->alloc(p->si_yh, L * L * p->F) &&
-           p->alloc(p->si_scr, std::max(M * L, (size_t)Rmax * M) * p->F) &&
+      ok = p->alloc(p->si_yh, L * L * p->F) && p->alloc(p->si_scr, M * L * p->F) &&
            p->alloc(p->si_m0, (size_t)p->Z * M) && p->alloc(p->si_wt, (size_t)p->Z * M * w);
     }
   }

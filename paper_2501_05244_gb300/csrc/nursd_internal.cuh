@@ -235,12 +235,11 @@ cudaError_t launch_gtf_generate(float2* g, int M, double pitch, const double* d_
 cudaError_t launch_gtf_compress_depthmajor(const float2* Gfull, const int2* cls_pq, int ncls, int M, int F, int ZB,
                                            int z0, float2* Gs, cudaStream_t s);
 // ------------------------------------------------- SRSD by interpolation (srsd_interp.cu)
-// P1[r][kx][f] = sum_t wt[kx][t] Yh[ylo + r][m0[kx] + t][f] (Yh [L][L][F] at index m + L/2, periodic).
-cudaError_t launch_srsd_interp_x(const float2* Yh, int L, int M, int F, int ylo, int R, int w, const int* m0,
-                                 const float* wt, float2* P1, cudaStream_t s);
-// Y[k][z] = sum_f Gs_z[class(k)][f] sum_t wt[ky][t] P1[m0[ky] + t - ylo][kx][f], Y [M][M][Z], F <= 256.
-cudaError_t launch_srsd_interp_y_contract(const float2* P1, int M, int F, int Z, int z, int ylo, int w, const int* m0,
-                                          const float* wt, const float2* Gs_z, float2* Y, cudaStream_t s);
+// Yh [L][L][F] at index m + L/2 (periodic in m).
+// Both taps and the contraction in one pass (scales >= 1, 4 <= w <= 8):
+// Y[k][z] = sum_f Gs_z[class(k)][f] sum_ty wt[ky][ty] sum_tx wt[kx][tx] Yh[m0[ky] + ty][m0[kx] + tx][f].
+cudaError_t launch_srsd_interp_xy_contract(const float2* Yh, int L, int M, int F, int Z, int z, int w, const int* m0,
+                                           const float* wt, const float2* Gs_z, float2* Y, cudaStream_t s);
 // ---------------------------------------------------------- per-frequency forms (illum.cu)
 // Y[k][zz*F + f] = U[k][f] * Gc[class(k)][f][z0 + zz] for zz < zg (no sum over f), U and Y
 // mode-major [M][M][...] with mode (kx, ky) at (ky + M/2) M + (kx + M/2).

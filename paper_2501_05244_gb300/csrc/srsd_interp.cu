@@ -8,11 +8,9 @@
 //   X(kappa) ~ sum_{t < w} phi(2 (m0 + t - u) / w) xh[m0 + t],  m0 = ceil(u - w / 2),
 // reproduces it to the kernel's accuracy (Poisson summation: exp(-2 pi i m n / L) summed against
 // phi over m gives psi_hat(n) exp(-2 pi i u n / L)).  The 2D FFT of u / (psi_hat x psi_hat) is taken
-// once per call for every depth; each depth then needs two w-tap passes over the rows and columns
-// its scale reaches, instead of four 2M-point FFTs per line.  The second pass is fused with the
-// depth's transfer contraction Y_z(kappa) = sum_f Phat_{z,f}(kappa) Gs_z[class(kappa)][f].
-#include <type_traits>
-
+// once per call for every depth; each depth then needs w x w taps over the block its scale
+// reaches, instead of four 2M-point FFTs per line, taken in one pass together with the depth's
+// transfer contraction Y_z(kappa) = sum_f Phat_{z,f}(kappa) Gs_z[class(kappa)][f].
 #include "nursd_internal.cuh"
 
 namespace nursd {
@@ -23,86 +21,79 @@ __device__ __forceinline__ int wrap_mod(int m, int L) {
   return r < 0 ? r + L : r;
 }
 
-// P1[r][kx][f] = sum_t wt[kx][t] Yh[row(ylo + r)][col(m0[kx] + t)][f]: the x pass of one depth over
-// the R rows its y taps reach.  Yh [L][L][F] at index m + L/2 (periodic in m); one thread per
-// (r, kx) and FV adjacent channels (two as one 16-byte access when F is even), f fastest.
-template <int FV>
-__global__ void srsd_interp_x_kernel(const float2* __restrict__ Yh, int L, int M, int F, int ylo, int R, int w,
-                                     const int* __restrict__ m0, const float* __restrict__ wt,
-                                     float2* __restrict__ P1) {
-  using V = typename std::conditional<FV == 2, float4, float2>::type;
-  const int FG = F / FV;  // channel groups per (r, kx)
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)R * M * FG) return;
-  const int fg = (int)(idx % FG);
-  const long long rest = idx / FG;
-  const int kx = (int)(rest % M), r = (int)(rest / M);
-  const V* row = reinterpret_cast<const V*>(Yh + (size_t)wrap_mod(ylo + r + L / 2, L) * L * F) + fg;
-  const int mb = __ldg(m0 + kx) + L / 2;
-  const float* wk = wt + (size_t)kx * w;
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-  for (int t = 0; t < w; ++t) {
-    const float c = __ldg(wk + t);
-    const V v = __ldg(row + (size_t)wrap_mod(mb + t, L) * FG);
-    a0 = fmaf(c, v.x, a0);
-    a1 = fmaf(c, v.y, a1);
-    if constexpr (FV == 2) {
-      a2 = fmaf(c, v.z, a2);
-      a3 = fmaf(c, v.w, a3);
-    }
-  }
-  if constexpr (FV == 2)
-    reinterpret_cast<float4*>(P1)[idx] = make_float4(a0, a1, a2, a3);
-  else
-    P1[idx] = make_float2(a0, a1);
-}
-
-// Y[k][z] = sum_f Gs_z[class(k)][f] * sum_t wt[ky][t] P1[m0[ky] + t - ylo][kx][f], k = (ky, kx):
-// the y pass fused with the depth's contraction.  One warp per column kx and run of kYRun
-// consecutive ky (consecutive warps take consecutive kx), lanes over f (F <= 32 * 8): ky and ky + 1
-// share all but about 2 / s of their w rows, so a warp finds most of its P1 rows in L1.  The f sum
-// is reduced by shuffles.
 constexpr int kMaxFPerLane = 8;
 constexpr int kYRun = 32;
-template <int FPL>  // F <= 32 FPL
-__global__ void srsd_interp_y_contract_kernel(const float2* __restrict__ P1, int M, int F, int Z, int z, int ylo,
-                                              int w, const int* __restrict__ m0, const float* __restrict__ wt,
-                                              const float2* __restrict__ Gs_z, float2* __restrict__ Y) {
+
+// The three steps of one depth in one pass, without the x-tapped rows in memory:
+// Y[k][z] = sum_f Gs_z[class(k)][f] sum_ty wt[ky][ty] X[m0[ky] + ty][kx][f] with
+// X[m][kx][f] = sum_tx wt[kx][tx] Yh[m][m0[kx] + tx][f].  One warp per column kx and run of kYRun
+// consecutive ky, lanes over f (F <= 32 FPL).  The warp keeps X of the W rows its current ky needs
+// in registers; the next ky starts at most two rows further (the coordinate 2 ky / s advances by
+// 2 / s <= 2 for scales >= 1), so at most two new rows are x-tapped per step.
+template <int FPL, int W>
+__global__ void srsd_interp_xy_contract_kernel(const float2* __restrict__ Yh, int L, int M, int F, int Z, int z,
+                                               const int* __restrict__ m0, const float* __restrict__ wt,
+                                               const float2* __restrict__ Gs_z, float2* __restrict__ Y) {
   const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   const int nrun = (M + kYRun - 1) / kYRun;
   if (warp >= M * nrun) return;
   const int kxi = warp % M, run = warp / M;
   const int ax = abs(kxi - M / 2);
-  const int ky1 = min(M, (run + 1) * kYRun);
-  for (int kyi = run * kYRun; kyi < ky1; ++kyi) {
-    const int ay = abs(kyi - M / 2), p = max(ax, ay), q = min(ax, ay);
-    const float2* g = Gs_z + (size_t)(p * (p + 1) / 2 + q) * F;
-    const int r0 = __ldg(m0 + kyi) - ylo;
-    const float* wk = wt + (size_t)kyi * w;
-    float2 ph[FPL];
+  // x taps of this column: weights and the first column on the periodic 2M grid
+  float cx[W];
 #pragma unroll
-    for (int j = 0; j < FPL; ++j) ph[j] = make_float2(0.f, 0.f);
-    for (int t = 0; t < w; ++t) {
-      const float c = __ldg(wk + t);
-      const float2* row = P1 + ((size_t)(r0 + t) * M + kxi) * F;
+  for (int t = 0; t < W; ++t) cx[t] = __ldg(wt + (size_t)kxi * W + t);
+  const int cb = __ldg(m0 + kxi) + L / 2;
+  auto xtap = [&](int m, float2 (&out)[FPL]) {  // X[m][kx][f] for the lane's channels
+    const float2* row = Yh + (size_t)wrap_mod(m + L / 2, L) * L * F;
+#pragma unroll
+    for (int j = 0; j < FPL; ++j) out[j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+      const float2* cell = row + (size_t)wrap_mod(cb + t, L) * F;
 #pragma unroll
       for (int j = 0; j < FPL; ++j) {
         const int f = lane + 32 * j;
         if (f < F) {
-          const float2 v = __ldg(row + f);
-          ph[j].x = fmaf(c, v.x, ph[j].x);
-          ph[j].y = fmaf(c, v.y, ph[j].y);
+          const float2 v = __ldg(cell + f);
+          out[j].x = fmaf(cx[t], v.x, out[j].x);
+          out[j].y = fmaf(cx[t], v.y, out[j].y);
         }
       }
     }
+  };
+  const int ky0 = run * kYRun, ky1 = min(M, ky0 + kYRun);
+  float2 xr[W][FPL];  // X of rows rbase .. rbase + W - 1
+  int rbase = __ldg(m0 + ky0);
+#pragma unroll
+  for (int r = 0; r < W; ++r) xtap(rbase + r, xr[r]);
+  for (int kyi = ky0; kyi < ky1; ++kyi) {
+    const int mk = __ldg(m0 + kyi);
+    for (int d = mk - rbase; d > 0; --d) {  // slide the window by one row
+#pragma unroll
+      for (int r = 0; r + 1 < W; ++r)
+#pragma unroll
+        for (int j = 0; j < FPL; ++j) xr[r][j] = xr[r + 1][j];
+      ++rbase;
+      xtap(rbase + W - 1, xr[W - 1]);
+    }
+    const int ay = abs(kyi - M / 2), p = max(ax, ay), q = min(ax, ay);
+    const float2* g = Gs_z + (size_t)(p * (p + 1) / 2 + q) * F;
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < FPL; ++j) {
       const int f = lane + 32 * j;
+      float2 ph = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int t = 0; t < W; ++t) {
+        const float c = __ldg(wt + (size_t)kyi * W + t);
+        ph.x = fmaf(c, xr[t][j].x, ph.x);
+        ph.y = fmaf(c, xr[t][j].y, ph.y);
+      }
       if (f < F) {
         const float2 gv = __ldg(g + f);
-        acc.x = fmaf(ph[j].x, gv.x, fmaf(-ph[j].y, gv.y, acc.x));
-        acc.y = fmaf(ph[j].x, gv.y, fmaf(ph[j].y, gv.x, acc.y));
+        acc.x = fmaf(ph.x, gv.x, fmaf(-ph.y, gv.y, acc.x));
+        acc.y = fmaf(ph.x, gv.y, fmaf(ph.y, gv.x, acc.y));
       }
     }
 #pragma unroll
@@ -114,38 +105,33 @@ __global__ void srsd_interp_y_contract_kernel(const float2* __restrict__ P1, int
   }
 }
 
-}  // namespace
-
-cudaError_t launch_srsd_interp_x(const float2* Yh, int L, int M, int F, int ylo, int R, int w, const int* m0,
-                                 const float* wt, float2* P1, cudaStream_t s) {
-  const long long n = (long long)R * M * F;
-  if (L < 2 || M < 2 || F < 1 || R < 1 || w < 1 || n >= (1LL << 40)) return cudaErrorInvalidValue;
-  const int threads = 256;
-  const bool pairs = F % 2 == 0;  // 16-byte accesses: Yh and P1 rows start on 16 bytes
-  const long long blocks = (n / (pairs ? 2 : 1) + threads - 1) / threads;
-  if (blocks >= (1LL << 31)) return cudaErrorInvalidValue;
-  if (pairs)
-    srsd_interp_x_kernel<2><<<(unsigned)blocks, threads, 0, s>>>(Yh, L, M, F, ylo, R, w, m0, wt, P1);
-  else
-    srsd_interp_x_kernel<1><<<(unsigned)blocks, threads, 0, s>>>(Yh, L, M, F, ylo, R, w, m0, wt, P1);
-  return cudaGetLastError();
+template <int FPL>
+cudaError_t xy_width(const float2* Yh, int L, int M, int F, int Z, int z, int w, const int* m0, const float* wt,
+                     const float2* Gs_z, float2* Y, unsigned blocks, cudaStream_t s) {
+  switch (w) {
+#define NURSD_XY(W_)                                                                                            \
+  case W_:                                                                                                    \
+    srsd_interp_xy_contract_kernel<FPL, W_><<<blocks, 64, 0, s>>>(Yh, L, M, F, Z, z, m0, wt, Gs_z, Y);       \
+    return cudaGetLastError();
+    NURSD_XY(4) NURSD_XY(5) NURSD_XY(6) NURSD_XY(7) NURSD_XY(8)
+#undef NURSD_XY
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
-cudaError_t launch_srsd_interp_y_contract(const float2* P1, int M, int F, int Z, int z, int ylo, int w, const int* m0,
-                                          const float* wt, const float2* Gs_z, float2* Y, cudaStream_t s) {
-  if (M < 2 || F < 1 || F > 32 * kMaxFPerLane || z < 0 || z >= Z || w < 1) return cudaErrorInvalidValue;
+}  // namespace
+
+cudaError_t launch_srsd_interp_xy_contract(const float2* Yh, int L, int M, int F, int Z, int z, int w, const int* m0,
+                                           const float* wt, const float2* Gs_z, float2* Y, cudaStream_t s) {
+  if (L < 2 || M < 2 || F < 1 || F > 32 * kMaxFPerLane || z < 0 || z >= Z) return cudaErrorInvalidValue;
   const long long threads_total = (long long)M * ((M + kYRun - 1) / kYRun) * 32;
-  const int threads = 256;
-  const unsigned blocks = (unsigned)((threads_total + threads - 1) / threads);
-  if (F <= 32)
-    srsd_interp_y_contract_kernel<1><<<blocks, threads, 0, s>>>(P1, M, F, Z, z, ylo, w, m0, wt, Gs_z, Y);
-  else if (F <= 64)
-    srsd_interp_y_contract_kernel<2><<<blocks, threads, 0, s>>>(P1, M, F, Z, z, ylo, w, m0, wt, Gs_z, Y);
-  else if (F <= 128)
-    srsd_interp_y_contract_kernel<4><<<blocks, threads, 0, s>>>(P1, M, F, Z, z, ylo, w, m0, wt, Gs_z, Y);
-  else
-    srsd_interp_y_contract_kernel<8><<<blocks, threads, 0, s>>>(P1, M, F, Z, z, ylo, w, m0, wt, Gs_z, Y);
-  return cudaGetLastError();
+  // two warps per block: up to ~14 resident warps per SM at the ~140 registers of F = 128
+  const unsigned blocks = (unsigned)((threads_total + 63) / 64);
+  if (F <= 32) return xy_width<1>(Yh, L, M, F, Z, z, w, m0, wt, Gs_z, Y, blocks, s);
+  if (F <= 64) return xy_width<2>(Yh, L, M, F, Z, z, w, m0, wt, Gs_z, Y, blocks, s);
+  if (F <= 128) return xy_width<4>(Yh, L, M, F, Z, z, w, m0, wt, Gs_z, Y, blocks, s);
+  return xy_width<8>(Yh, L, M, F, Z, z, w, m0, wt, Gs_z, Y, blocks, s);
 }
 
 }  // namespace nursd
