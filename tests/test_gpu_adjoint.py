@@ -88,6 +88,22 @@ def test_adjoint_identity_on_gpu():
     assert abs(complex(lhs - rhs)) < 1e-5 * abs(complex(lhs))
 
 
+@pytest.mark.parametrize("width", [4, 5, 7, 8])
+def test_adjoint_identity_at_every_kernel_width(width):
+    # the type-2 interpolation (adjoint of the spread) is compiled per width; at any width it is the
+    # exact adjoint of the implemented type 1, so the identity holds to FP32 rounding
+    c = small_case(32, 1500, 8, 6, seed=20 + width)
+    plan = plan_for(c, kernel_width=width)
+    P = torch.from_numpy(c["P"]).cuda()
+    V = torch.from_numpy(cvec((6, 32, 32), 30 + width)).cuda()
+    AP = plan.forward_phasor(P)
+    AhV = plan.adjoint(V)
+    assert plan.sync_status() == 0
+    lhs = torch.vdot(V.flatten().to(torch.complex128), AP.flatten().to(torch.complex128))
+    rhs = torch.vdot(AhV.flatten().to(torch.complex128), P.flatten().to(torch.complex128))
+    assert abs(complex(lhs - rhs)) < 1e-5 * abs(complex(lhs))
+
+
 def test_adjoint_on_the_tiny_workload():
     wl = workload_c1()
     g = wl.geom
@@ -181,6 +197,22 @@ def test_type2_voxels_match_oracle(seed, N, L, F, Z, K):
     th = np.stack([O.relay_theta(vox[z], c["center"], c["pitch"], M) for z in range(Z)])
     ref = O.propagate_points(U, Gh, th)
     assert rel(got, ref) < TOL
+
+
+@pytest.mark.parametrize("width,tol", [(4, 1e-2), (5, 2e-3), (7, 5e-5), (8, 5e-5)])
+def test_type2_voxels_at_every_kernel_width(width, tol):
+    # the plane interpolation is compiled per width; ES accuracy at upsampling 2 bounds the error
+    c = small_case(32, 1500, 8, 4, seed=60 + width)
+    plan = plan_for(c, kernel_width=width)
+    half = 32 * c["pitch"] / 2 * 0.999
+    vox = random_plane_points(4, 500, half, c["center"], seed=70 + width)
+    got = plan.forward_points(torch.from_numpy(c["P"]).cuda(), torch.from_numpy(vox).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    M = 64
+    U = O.nudft_type1(c["P"], O.relay_theta(c["xy"], c["center"], c["pitch"], M), M)
+    Gh = O.transfer_functions(c["depths"], c["om"], M, c["pitch"])
+    th = np.stack([O.relay_theta(vox[z], c["center"], c["pitch"], M) for z in range(4)])
+    assert rel(got, O.propagate_points(U, Gh, th)) < tol
 
 
 def test_type2_at_lattice_voxels_equals_the_lattice_forward():
