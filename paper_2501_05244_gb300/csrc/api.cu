@@ -482,6 +482,8 @@ int run_srsd_spectra(nursd_plan_s* p, cudaStream_t s) {
       e = axis_pass(p, p->R1, p->fine, logM, true, F, M, F, (long long)M * F, F, (long long)M * F, M, -M / 2, M,
                     -M / 2, nullptr, nullptr, 1.f / ((float)M * (float)M), s);
   }
+  if (e == cudaSuccess && p->si_any)  // the interpolated depths add into Y when F > 64
+    e = cudaMemsetAsync(p->Y, 0, sizeof(float2) * (size_t)M * M * Z, s);
   if (e == cudaSuccess && p->si_any) {  // oversampled spectrum of u / (psi_hat x psi_hat), shared by the
                                         // interpolated depths: FFT_2M along nx, then along ny
     StageTimer t(p, NURSD_STAGE_SRSD, s, 2);

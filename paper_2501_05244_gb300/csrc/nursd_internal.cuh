@@ -236,7 +236,8 @@ cudaError_t launch_gtf_compress_depthmajor(const float2* Gfull, const int2* cls_
                                            int z0, float2* Gs, cudaStream_t s);
 // ------------------------------------------------- SRSD by interpolation (srsd_interp.cu)
 // Yh [L][L][F] at index m + L/2 (periodic in m).
-// Both taps and the contraction in one pass (scales >= 1, 4 <= w <= 8):
+// Both taps and the contraction in one pass (scales >= 1, 4 <= w <= 8); with F > 64 it adds into Y,
+// which must then be zero on entry:
 // Y[k][z] = sum_f Gs_z[class(k)][f] sum_ty wt[ky][ty] sum_tx wt[kx][tx] Yh[m0[ky] + ty][m0[kx] + tx][f].
 cudaError_t launch_srsd_interp_xy_contract(const float2* Yh, int L, int M, int F, int Z, int z, int w, const int* m0,
                                            const float* wt, const float2* Gs_z, float2* Y, cudaStream_t s);

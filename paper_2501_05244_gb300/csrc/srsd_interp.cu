@@ -30,13 +30,18 @@ constexpr int kYRun = 32;
 // consecutive ky, lanes over f (F <= 32 FPL).  The warp keeps X of the W rows its current ky needs
 // in registers; the next ky starts at most two rows further (the coordinate 2 ky / s advances by
 // 2 / s <= 2 for scales >= 1), so at most two new rows are x-tapped per step.
-template <int FPL, int W>
+// FS = 2: the channels of a mode are split over two warps (channel block fs), each adding its part
+// of the f sum to Y with an atomic add; Y starts at zero, and a sum of two terms onto zero does not
+// depend on their order, so the result is reproducible.
+template <int FPL, int W, int FS>
 __global__ void srsd_interp_xy_contract_kernel(const float2* __restrict__ Yh, int L, int M, int F, int Z, int z,
                                                const int* __restrict__ m0, const float* __restrict__ wt,
                                                const float2* __restrict__ Gs_z, float2* __restrict__ Y) {
-  const int warp = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  const int gw = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   const int nrun = (M + kYRun - 1) / kYRun;
-  if (warp >= M * nrun) return;
+  if (gw >= M * nrun * FS) return;
+  const int fs = gw % FS, warp = gw / FS;
+  const int fbase = fs * 32 * FPL;  // this warp's channels: fbase + lane + 32 j, j < FPL
   const int kxi = warp % M, run = warp / M;
   const int ax = abs(kxi - M / 2);
   // x taps of this column: weights and the first column on the periodic 2M grid
@@ -53,7 +58,7 @@ __global__ void srsd_interp_xy_contract_kernel(const float2* __restrict__ Yh, in
       const float2* cell = row + (size_t)wrap_mod(cb + t, L) * F;
 #pragma unroll
       for (int j = 0; j < FPL; ++j) {
-        const int f = lane + 32 * j;
+        const int f = fbase + lane + 32 * j;
         if (f < F) {
           const float2 v = __ldg(cell + f);
           out[j].x = fmaf(cx[t], v.x, out[j].x);
@@ -79,16 +84,18 @@ __global__ void srsd_interp_xy_contract_kernel(const float2* __restrict__ Yh, in
     }
     const int ay = abs(kyi - M / 2), p = max(ax, ay), q = min(ax, ay);
     const float2* g = Gs_z + (size_t)(p * (p + 1) / 2 + q) * F;
+    float cy[W];
+#pragma unroll
+    for (int t = 0; t < W; ++t) cy[t] = __ldg(wt + (size_t)kyi * W + t);
     float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int j = 0; j < FPL; ++j) {
-      const int f = lane + 32 * j;
+      const int f = fbase + lane + 32 * j;
       float2 ph = make_float2(0.f, 0.f);
 #pragma unroll
       for (int t = 0; t < W; ++t) {
-        const float c = __ldg(wt + (size_t)kyi * W + t);
-        ph.x = fmaf(c, xr[t][j].x, ph.x);
-        ph.y = fmaf(c, xr[t][j].y, ph.y);
+        ph.x = fmaf(cy[t], xr[t][j].x, ph.x);
+        ph.y = fmaf(cy[t], xr[t][j].y, ph.y);
       }
       if (f < F) {
         const float2 gv = __ldg(g + f);
@@ -101,17 +108,25 @@ __global__ void srsd_interp_xy_contract_kernel(const float2* __restrict__ Yh, in
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
     }
-    if (lane == 0) Y[((size_t)kyi * M + kxi) * Z + z] = acc;
+    if (lane == 0) {
+      float2* y = Y + ((size_t)kyi * M + kxi) * Z + z;
+      if constexpr (FS == 1) {
+        *y = acc;
+      } else {
+        atomicAdd(&y->x, acc.x);
+        atomicAdd(&y->y, acc.y);
+      }
+    }
   }
 }
 
-template <int FPL>
+template <int FPL, int FS>
 cudaError_t xy_width(const float2* Yh, int L, int M, int F, int Z, int z, int w, const int* m0, const float* wt,
                      const float2* Gs_z, float2* Y, unsigned blocks, cudaStream_t s) {
   switch (w) {
 #define NURSD_XY(W_)                                                                                            \
   case W_:                                                                                                    \
-    srsd_interp_xy_contract_kernel<FPL, W_><<<blocks, 64, 0, s>>>(Yh, L, M, F, Z, z, m0, wt, Gs_z, Y);       \
+    srsd_interp_xy_contract_kernel<FPL, W_, FS><<<blocks, 64, 0, s>>>(Yh, L, M, F, Z, z, m0, wt, Gs_z, Y);   \
     return cudaGetLastError();
     NURSD_XY(4) NURSD_XY(5) NURSD_XY(6) NURSD_XY(7) NURSD_XY(8)
 #undef NURSD_XY
@@ -125,13 +140,15 @@ cudaError_t xy_width(const float2* Yh, int L, int M, int F, int Z, int z, int w,
 cudaError_t launch_srsd_interp_xy_contract(const float2* Yh, int L, int M, int F, int Z, int z, int w, const int* m0,
                                            const float* wt, const float2* Gs_z, float2* Y, cudaStream_t s) {
   if (L < 2 || M < 2 || F < 1 || F > 32 * kMaxFPerLane || z < 0 || z >= Z) return cudaErrorInvalidValue;
-  const long long threads_total = (long long)M * ((M + kYRun - 1) / kYRun) * 32;
-  // two warps per block: up to ~14 resident warps per SM at the ~140 registers of F = 128
+  // above 64 channels a mode's channels are split over two warps (FS = 2: Y must be zero on entry)
+  const int FS = F > 64 ? 2 : 1;
+  const long long threads_total = (long long)M * ((M + kYRun - 1) / kYRun) * 32 * FS;
+  // two warps per block: more resident warps at the registers of the register-held window
   const unsigned blocks = (unsigned)((threads_total + 63) / 64);
-  if (F <= 32) return xy_width<1>(Yh, L, M, F, Z, z, w, m0, wt, Gs_z, Y, blocks, s);
-  if (F <= 64) return xy_width<2>(Yh, L, M, F, Z, z, w, m0, wt, Gs_z, Y, blocks, s);
-  if (F <= 128) return xy_width<4>(Yh, L, M, F, Z, z, w, m0, wt, Gs_z, Y, blocks, s);
-  return xy_width<8>(Yh, L, M, F, Z, z, w, m0, wt, Gs_z, Y, blocks, s);
+  if (F <= 32) return xy_width<1, 1>(Yh, L, M, F, Z, z, w, m0, wt, Gs_z, Y, blocks, s);
+  if (F <= 64) return xy_width<2, 1>(Yh, L, M, F, Z, z, w, m0, wt, Gs_z, Y, blocks, s);
+  if (F <= 128) return xy_width<2, 2>(Yh, L, M, F, Z, z, w, m0, wt, Gs_z, Y, blocks, s);
+  return xy_width<4, 2>(Yh, L, M, F, Z, z, w, m0, wt, Gs_z, Y, blocks, s);
 }
 
 }  // namespace nursd
