@@ -22,7 +22,7 @@ __device__ __forceinline__ int wrap_mod(int m, int L) {
 }
 
 constexpr int kMaxFPerLane = 8;
-constexpr int kYRun = 32;
+constexpr int kYRun = 16;
 
 // The three steps of one depth in one pass, without the x-tapped rows in memory:
 // Y[k][z] = sum_f Gs_z[class(k)][f] sum_ty wt[ky][ty] X[m0[ky] + ty][kx][f] with
