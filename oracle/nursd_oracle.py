@@ -6,8 +6,8 @@ and the CPU-baseline legs of ``bench.py``; never by the CUDA product path.
 Everything is a direct, unfused statement of the paper's definitions in FP64:
 non-uniform and scaled transforms are explicit sums (matrix products of
 explicit exponentials), uniform length-M DFTs of the transfer function use
-``numpy.fft`` as a textbook routine.  Conventions (paper ambiguities resolved;
-each is listed in DESIGN.md):
+``numpy.fft`` as a textbook routine.  Conventions (readings of the paper where it
+is ambiguous or silent):
 
 * index sets I_L = {l : -L/2 <= l < L/2} (Sec. 4.1), row-major arrays with x
   fastest: ``U[f][ky][kx]``, ``V[z][my][mx]``;
@@ -37,7 +37,7 @@ __all__ = [
     "transfer_functions", "propagate", "propagate_depth", "nursd_forward", "fbp_direct",
     "propagate_points", "idft_grid", "scaled_dft_matrix", "srsd_from_grid", "srsd_forward",
     "adjoint_spectrum", "nursd_adjoint", "nursd_loss", "nursd_gradients",
-    "adjoint_spectrum_depthwise", "nudft_type1_lattice", "gradients_from_w", "frustum_volume", "frustum_extra_volume", "data_compression", "lateral_resolution",
+    "adjoint_spectrum_depthwise", "nudft_type1_lattice", "gradients_from_w", "position_loss_differences", "frustum_volume", "frustum_extra_volume", "data_compression", "lateral_resolution",
     "voxel_lattice", "propagate_per_frequency", "illumination_mask", "propagate_illuminated", "transient_frames",
     "nursd_forward_illuminated", "nursd_transient_frames", "fbp_direct_per_frequency",
     "srsd_spectra", "srsd_points",
@@ -544,6 +544,48 @@ def gradients_from_w(R: np.ndarray, P_rows: np.ndarray, theta_rows: np.ndarray, 
     gx = np.real(np.sum(P_rows * np.conj(dx), axis=1)) * scale
     gy = np.real(np.sum(P_rows * np.conj(dy), axis=1)) * scale
     return gP, np.stack([gx, gy], axis=1)
+
+
+def position_loss_differences(residual, P_rows, xy_rows, axes, h: float, center, pitch: float, N: int, depths,
+                              omega) -> np.ndarray:
+    """Central differences of L = ||A(P, x) - V_t||^2 in one coordinate of one relay sample each.
+
+    Moving sample l changes only its own term of the forward sum (Eq. NURSD1), so with the residual
+    r = A(P, x) - V_t, L(x + d) - L(x - d) = 2 Re <r, dV+ - dV-> + ||dV+||^2 - ||dV-||^2, where
+    dV+ - dV- is the single-sample forward at x_l + h e minus that at x_l - h e: its NUDFT term
+    P_lf (e^{-i k.theta+} - e^{-i k.theta-}), the contraction with Ghat_{z,f} summed over f, and the
+    IDFT crop of each plane.  The inner product with r is taken on the spectrum side against
+    Rt_z = B^H r_z conj(B) (B the crop's matrix).  The quadratic terms differ by O(h^3), i.e.
+    O(h^2) relative to the difference, and are left out.  Ghat is built one depth at a time.
+
+    residual [Z][N][N]; P_rows [S][F]; xy_rows [S][2] metres; axes [S] in {0, 1} -> [S]
+    (L(x + h e) - L(x - h e)) / (2 h).
+    """
+    M = 2 * N
+    r = np.asarray(residual, dtype=np.complex128)
+    P_rows = np.asarray(P_rows, dtype=np.complex128)
+    xy_rows = np.asarray(xy_rows, dtype=np.float64)
+    axes = np.asarray(axes, dtype=int)
+    S = len(axes)
+    k = index_set(M).astype(np.float64)
+    B = _idft_crop_matrix(M, N)
+    dE = np.empty((S, M, M), dtype=np.complex128)  # e^{-i k.theta+} - e^{-i k.theta-}, [s][ky][kx]
+    for s_ in range(S):
+        d = np.zeros(2)
+        d[axes[s_]] = h
+        tp = relay_theta((xy_rows[s_] + d)[None], center, pitch, M)[0]
+        tm = relay_theta((xy_rows[s_] - d)[None], center, pitch, M)[0]
+        ep = np.outer(np.exp(-1j * k * tp[1]), np.exp(-1j * k * tp[0]))
+        em = np.outer(np.exp(-1j * k * tm[1]), np.exp(-1j * k * tm[0]))
+        dE[s_] = ep - em
+    acc = np.zeros(S)
+    omega = np.asarray(omega, dtype=np.float64)
+    for iz, z in enumerate(np.asarray(depths, dtype=np.float64)):
+        Gz = np.stack([transfer_function(rsd_kernel(M, pitch, z, w / C)) for w in omega])  # [F][M][M]
+        H = np.tensordot(P_rows, Gz, axes=(1, 0))  # [S][M][M]: sum_f P_lf Ghat_{z,f}
+        Rt = np.conj(B).T @ r[iz] @ np.conj(B)  # [ky][kx]
+        acc += 2.0 * np.real(np.einsum("yx,syx->s", np.conj(Rt), dE * H)) / (M * M)
+    return acc / (2.0 * h)
 
 
 # ------------------------------------------------ plan-level closed forms ---

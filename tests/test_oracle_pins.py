@@ -588,3 +588,76 @@ def test_lattice_type1_equals_the_general_sum():
     n = np.stack([r.integers(-M // 2, M // 2, L), r.integers(-M // 2, M // 2, L)], axis=1)
     P = r.standard_normal((L, F)) + 1j * r.standard_normal((L, F))
     assert rel(O.nudft_type1_lattice(P, n, M), O.nudft_type1(P, 2 * math.pi * n / M, M)) < 1e-13
+
+
+# ------------------------------------------- the depth-streamed propagation ----
+
+def pin_depth_streamed_equals_direct_backprojection(prop=None, case=None):
+    """max relative error of a depth-streamed propagation (default O.propagate_depth) of the exact
+    type-1 spectrum of on-lattice samples against direct back-projection at that depth's lattice."""
+    prop = prop or O.propagate_depth
+    c = case or _lattice_case(N=8, L=30, F=3, Z=2, seed=11)
+    M = 2 * c["N"]
+    U = O.nudft_type1(c["P"], O.relay_theta(c["xy"], c["center"], c["pitch"], M), M)
+    m = O.index_set(c["N"]) * c["pitch"]
+    X, Y = np.meshgrid(m + c["center"][0], m + c["center"][1], indexing="xy")
+    err = 0.0
+    for z in c["depths"]:
+        vox = np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], axis=1)
+        d = O.fbp_direct(c["P"], c["xy"], c["omega"], vox).reshape(X.shape)
+        err = max(err, rel(prop(U, z, c["omega"], c["pitch"], c["N"]), d))
+    return err
+
+
+def test_propagate_depth_equals_direct_backprojection_on_the_lattice():
+    # the same physical special case that pins the full operator: samples on the lattice,
+    # M = 2N (no wrap), so each plane is exactly the direct back-projection sum at that depth
+    assert pin_depth_streamed_equals_direct_backprojection() < 1e-12
+
+
+def test_propagate_depth_equals_each_plane_of_propagate():
+    c = _lattice_case(N=6, L=12, F=3, Z=2, seed=12)
+    r = np.random.default_rng(13)
+    xy = c["xy"] + r.uniform(-0.5, 0.5, c["xy"].shape) * c["pitch"]
+    M = 2 * c["N"]
+    U = O.nudft_type1(c["P"], O.relay_theta(xy, c["center"], c["pitch"], M), M)
+    V = O.propagate(U, O.transfer_functions(c["depths"], c["omega"], M, c["pitch"]), c["N"])
+    for iz, z in enumerate(c["depths"]):
+        assert rel(O.propagate_depth(U, z, c["omega"], c["pitch"], c["N"]), V[iz]) < 1e-13
+
+
+def test_planted_mistakes_in_the_depth_streamed_propagation_are_caught():
+    def no_norm(U, z, omega, pitch, N):  # dropped M^-2
+        return O.propagate_depth(U, z, omega, pitch, N) * U.shape[-1] ** 2
+
+    def wrong_pitch(U, z, omega, pitch, N):  # transfer function sampled at the wrong pitch
+        return O.propagate_depth(U, z, omega, 1.01 * pitch, N)
+
+    def wrong_depth(U, z, omega, pitch, N):  # another plane's kernel
+        return O.propagate_depth(U, 1.05 * z, omega, pitch, N)
+
+    for bad in (no_norm, wrong_pitch, wrong_depth):
+        assert pin_depth_streamed_equals_direct_backprojection(bad) > 1e-3, bad.__name__
+
+
+def test_single_sample_loss_differences_equal_brute_force_central_differences():
+    # the full-size gradient check differences one sample's forward term at a time; on a small case
+    # that must reproduce the central difference of the whole loss (up to the O(h^2) terms it drops)
+    c = _lattice_case(N=6, L=10, F=2, Z=2)
+    r = np.random.default_rng(14)
+    xy = c["xy"] + r.uniform(-0.5, 0.5, c["xy"].shape) * c["pitch"]
+    args = (c["center"], c["pitch"], c["N"], c["depths"], c["omega"])
+    Vt = r.standard_normal((2, 6, 6)) + 1j * r.standard_normal((2, 6, 6))
+    resid = O.nursd_forward(c["P"], xy, *args) - Vt
+    rows, axes, h = np.array([0, 3, 3, 9]), np.array([0, 0, 1, 1]), 1e-5
+    got = O.position_loss_differences(resid, c["P"][rows], xy[rows], axes, h, *args)
+    want = []
+    for l, a in zip(rows, axes):
+        xp = xy.copy(); xp[l, a] += h
+        xm = xy.copy(); xm[l, a] -= h
+        want.append((O.nursd_loss(c["P"], xp, *args, Vt) - O.nursd_loss(c["P"], xm, *args, Vt)) / (2 * h))
+    want = np.array(want)
+    assert np.max(np.abs(got - want)) < 1e-6 * np.max(np.abs(want)), (got, want)
+    # and the analytic gradient, which the differences must approach as h -> 0
+    _, gx = O.nursd_gradients(c["P"], xy, *args, Vt)
+    assert np.max(np.abs(got - gx[rows, axes])) < 1e-5 * np.max(np.abs(want))
