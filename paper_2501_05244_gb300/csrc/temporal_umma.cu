@@ -1,12 +1,20 @@
 // Temporal transform on the 5th-generation tensor cores (Eq. PF_Response with Eq. PFPacket):
-// C[L][2F] = H[L][T] * B[T][2F], B[n][2f] = w_f cos(w_f t_n), B[n][2f+1] = -w_f sin(w_f t_n),
-// as tcgen05.mma (kind::f16: fp16 operands, fp32 accumulation in tensor memory).
+// C[L][2F] = H[L][T] * B[T][2F] * diag(w), B[n][2f] = cos(w_f t_n), B[n][2f+1] = -sin(w_f t_n),
+// as tcgen05.mma (kind::f16: fp16 operands, fp32 accumulation in tensor memory); the weight
+// w_f of each column pair is applied in the epilogue, so B holds unit-modulus values only.
 //
 // FP32 accuracy from fp16 products, as in the mma.sync form: x = x_hi + x_lo with
 // x_lo = fp16(x - x_hi), and C = H_hi B_hi + H_hi B_lo + H_lo B_hi, every product
 // exact in the fp32 accumulator.  B's head and tail are split once at plan time
 // ([2F][T], K-major); H is split as it is staged, and a K-block whose H_lo is all
 // zero (photon counts below 2048 are exact in fp16) skips the H_lo product.
+//
+// FP32 range: the split keeps ~22 bits of every value of a row whose max |h| lies in
+// [2^-3, 65504) (an error below 2^-22 of the row's max).  The H producers track each row's
+// max; a row outside that window (a bin above fp16's range, or pre-normalised data) is listed
+// with the exponent e that brings its max into [2^14, 2^15), and a second launch of this
+// kernel in gather mode recomputes only the listed rows from h 2^-e (exact), multiplying the
+// accumulator by 2^e in the epilogue.  With nothing listed that launch exits at once.
 //
 // One CTA per SM walks 128-row tiles of H (tile blockIdx.x + j gridDim.x).  Warp roles:
 //   0-3  epilogue: tcgen05.ld of the 128 x 2F accumulator (one row per thread), fp32 stores
@@ -31,6 +39,7 @@
 #include "nursd_internal.cuh"
 
 namespace nursd {
+
 namespace {
 
 constexpr int kBM = 128, kBK = 32, kUStages = 4;
@@ -45,16 +54,18 @@ struct UShape {
   static constexpr int kB = N2 * 64;   // one B tile: N2 rows x 32 fp16
   static constexpr int kStage = 2 * kA + 2 * kB;
   static constexpr int kAcc = N2 < 32 ? 32 : N2;  // tensor-memory columns per accumulator
-  static constexpr size_t kSmem = 1024 + (size_t)kUStages * kStage + 512;
+  static constexpr size_t kSmem = 1024 + (size_t)kUStages * kStage + 3072;
 };
 
-struct Ctl {
+struct Ctl {  // control block after the stages (at most the 3072 bytes the shape reserves)
   unsigned long long full_a[kUStages], full_b[kUStages], empty[kUStages];
   unsigned long long acc_full[2], acc_empty[2], drain;
   unsigned tmem;
   int abort;
   int lo[kUStages][kCvtWarps];
+  float rmax[2][kCvtWarps * 32];  // running max |h| of each producer thread's two rows (first launch)
 };
+static_assert(sizeof(Ctl) <= 3072, "control block exceeds the shared memory reserved for it");
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -150,28 +161,48 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-template <int N2>
+// GATHER = false: rows 0 .. L-1 of H; rows whose max |h| lies outside the split's window are
+// listed in fix.  GATHER = true: the listed rows (fix.list[0 .. *fix.count), each row index below
+// L), scaled by 2^-e before the split and by 2^e in the epilogue.
+template <int N2, bool GATHER>
 __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float* __restrict__ H,
                                                                      float* __restrict__ C, int L, int T,
                                                                      const __grid_constant__ CUtensorMap tm_hi,
                                                                      const __grid_constant__ CUtensorMap tm_lo,
                                                                      int* __restrict__ status,
-                                                                     const int* __restrict__ row_slot) {
+                                                                     const int* __restrict__ row_slot,
+                                                                     const float* __restrict__ wcol,
+                                                                     const TemporalFix fix) {
   using S = UShape<N2>;
+  __shared__ int listed;
+  if (GATHER) {
+    if (threadIdx.x == 0) listed = temporal_fix_take(fix);
+    __syncthreads();
+  }
+  const int nrows = GATHER ? min(listed, fix.cap) : L;
+  const int ntiles = (nrows + kBM - 1) / kBM, nkb = T / kBK;
+  if (GATHER && (int)blockIdx.x >= ntiles) return;  // the whole CTA: nothing listed for it
   extern __shared__ unsigned char raw[];
   const uint32_t raw_addr = sa(raw);
   unsigned char* base = raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
-  const uint32_t base_addr = sa(base);
   Ctl& ctl = *reinterpret_cast<Ctl*>(base + kUStages * S::kStage);
   volatile int* abort = &ctl.abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntiles = (L + kBM - 1) / kBM, nkb = T / kBK;
   const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int my_iters = my_tiles * nkb;
   auto a_hi = [&](int st) { return base + st * S::kStage; };
   auto a_lo = [&](int st) { return base + st * S::kStage + S::kA; };
   auto b_hi = [&](int st) { return base + st * S::kStage + 2 * S::kA; };
   auto b_lo = [&](int st) { return base + st * S::kStage + 2 * S::kA + S::kB; };
+  // H row of tile position pos (-1: none) and, in the gather launch, its exponent
+  auto row_of = [&](int pos, int& x) -> int {
+    x = 0;
+    if (!GATHER) return pos < L ? pos : -1;
+    if (pos >= nrows) return -1;
+    const int4 en = fix.list[pos];
+    x = en.y;
+    return (en.x >= 0 && en.x < L) ? en.x : -1;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kUStages; ++s) {
@@ -202,21 +233,32 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
     // ---------------------------------------------------------------- epilogue
     for (int j = 0; j < my_tiles; ++j) {
       const int ab = j & 1;
-      if (!bar_wait(&ctl.acc_full[ab], (j >> 1) & 1, abort)) break;
+      if (!__all_sync(0xffffffffu, bar_wait(&ctl.acc_full[ab], (j >> 1) & 1, abort))) break;
       fence_after_sync();
-      const int row = ((int)blockIdx.x + j * (int)gridDim.x) * kBM + warp * 32 + lane;
+      int x = 0;
+      int orow = row_of(((int)blockIdx.x + j * (int)gridDim.x) * kBM + warp * 32 + lane, x);
+      if (orow >= 0 && row_slot) orow = __ldg(row_slot + orow);
       const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * S::kAcc);
 #pragma unroll 1
       for (int c0 = 0; c0 < N2; c0 += 32) {
         uint32_t r[32];
         tmem_ld32(tb + c0, r);
-        if (row < L) {
-          const int orow = row_slot ? __ldg(row_slot + row) : row;
+        if (orow >= 0) {
           float4* dst = reinterpret_cast<float4*>(C + (size_t)orow * N2 + c0);
+          const float4* w4 = reinterpret_cast<const float4*>(wcol + c0);
 #pragma unroll
-          for (int q = 0; q < 8; ++q)
-            dst[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
-                                 __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+          for (int q = 0; q < 8; ++q) {
+            const float4 w = __ldg(w4 + q);
+            float4 v = make_float4(__uint_as_float(r[4 * q]) * w.x, __uint_as_float(r[4 * q + 1]) * w.y,
+                                   __uint_as_float(r[4 * q + 2]) * w.z, __uint_as_float(r[4 * q + 3]) * w.w);
+            if (GATHER) {
+              v.x = ldexpf(v.x, x);
+              v.y = ldexpf(v.y, x);
+              v.z = ldexpf(v.z, x);
+              v.w = ldexpf(v.w, x);
+            }
+            dst[q] = v;
+          }
         }
       }
       fence_before_sync();
@@ -228,6 +270,8 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
     const int cw = warp - kEpiWarps, ct = cw * 32 + lane;
     // task q < 2 of a K-block: row ct / 4 + 64 q of the tile, 16-byte chunk ct % 4 (8 consecutive K values)
     const int r0 = ct >> 2, ch = ct & 3;
+    float* rmax0 = ctl.rmax[0] + ct;  // running max |h| of this thread's two rows over the tile's K-blocks
+    float* rmax1 = ctl.rmax[1] + ct;
     // a register set holds K-blocks 2 p and 2 p + 1 (4 float4 each)
     auto load = [&](float4 (&v)[8], int pr) {
 #pragma unroll
@@ -236,26 +280,39 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
         if (it >= my_iters) return;
         const int j = it / nkb, kb = it - j * nkb;
         const int m0 = ((int)blockIdx.x + j * (int)gridDim.x) * kBM;
-        const float* src = H + (size_t)(m0 + r0) * T + kb * kBK + ch * 8;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          const bool ok = m0 + r0 + 64 * q < L;
-          const float4* s4 = reinterpret_cast<const float4*>(src + (size_t)64 * q * T);
-          v[4 * h + 2 * q] = ok ? __ldg(s4) : make_float4(0.f, 0.f, 0.f, 0.f);
-          v[4 * h + 2 * q + 1] = ok ? __ldg(s4 + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+          int x;
+          const int row = row_of(m0 + r0 + 64 * q, x);
+          const float4* s4 = reinterpret_cast<const float4*>(H + (size_t)max(row, 0) * T + kb * kBK + ch * 8);
+          v[4 * h + 2 * q] = row >= 0 ? __ldg(s4) : make_float4(0.f, 0.f, 0.f, 0.f);
+          v[4 * h + 2 * q + 1] = row >= 0 ? __ldg(s4 + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
       }
     };
     auto stage_one = [&](const float4* v, int it) -> bool {
       const int st = it % kUStages, ph = (it / kUStages) & 1;
-      if (!bar_wait(&ctl.empty[st], ph ^ 1, abort)) return false;
+      const int j = it / nkb, kb = it - j * nkb;
+      const int m0 = ((int)blockIdx.x + j * (int)gridDim.x) * kBM;
+      if (!__all_sync(0xffffffffu, bar_wait(&ctl.empty[st], ph ^ 1, abort))) return false;
       unsigned char* ah = a_hi(st);
       unsigned char* al = a_lo(st);
       uint32_t any = 0;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const int r = r0 + 64 * q;
-        const float4 x = v[2 * q], y = v[2 * q + 1];
+        float4 x = v[2 * q], y = v[2 * q + 1];
+        if (GATHER) {
+          int e;
+          row_of(m0 + r, e);
+          x = make_float4(ldexpf(x.x, -e), ldexpf(x.y, -e), ldexpf(x.z, -e), ldexpf(x.w, -e));
+          y = make_float4(ldexpf(y.x, -e), ldexpf(y.y, -e), ldexpf(y.z, -e), ldexpf(y.w, -e));
+        } else {
+          const float m = fmaxf(fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))),
+                                fmaxf(fmaxf(fabsf(y.x), fabsf(y.y)), fmaxf(fabsf(y.z), fabsf(y.w))));
+          float* rm = q ? rmax1 : rmax0;
+          *rm = kb == 0 ? m : fmaxf(*rm, m);
+        }
         uint4 h, l;
         split2(x.x, x.y, h.x, l.x);
         split2(x.z, x.w, h.y, l.y);
@@ -272,6 +329,22 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
       if (lane == 0) {
         ctl.lo[st][cw] = warp_any;
         bar_arrive(&ctl.full_a[st]);
+      }
+      if (!GATHER && kb == nkb - 1) {  // the tile's rows are complete: the 4 lanes of a row agree on its max
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          float m = q ? *rmax1 : *rmax0;
+          m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+          m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+          const int row = m0 + r0 + 64 * q;
+          if (ch == 0 && row < L) {
+            const int e = temporal_row_exponent(m);
+            if (e != kRowInRange) {
+              const int slot = atomicAdd(fix.count, 1);
+              if (slot < fix.cap) fix.list[slot] = make_int4(row, e, 0, 0);
+            }
+          }
+        }
       }
       return true;
     };
@@ -394,24 +467,39 @@ bool encode_b(CUtensorMap* m, const void* ptr, int T, int rows) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int N2>
-cudaError_t launch_n(const TemporalMaps& m, const float* h, float* C, int L, int T, int* status, cudaStream_t s,
-                     const int* row_slot) {
-  using S = UShape<N2>;
+template <int N2, bool GATHER>
+cudaError_t configure_n() {
   static bool configured = false;
+  if (configured) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(temporal_umma_kernel<N2, GATHER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)UShape<N2>::kSmem);
+  if (e == cudaSuccess) configured = true;
+  return e;
+}
+
+template <int N2>
+cudaError_t launch_n(const TemporalMaps& m, const float* h, const float* wcol, float* C, int L, int T,
+                     const TemporalFix& fix, int* status, cudaStream_t s, const int* row_slot) {
+  using S = UShape<N2>;
   static int sms = 0;
-  if (!configured) {
-    cudaError_t e =
-        cudaFuncSetAttribute(temporal_umma_kernel<N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
-    if (e != cudaSuccess) return e;
+  if (sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    configured = true;
   }
+  cudaError_t e = configure_n<N2, false>();
+  if (e == cudaSuccess) e = configure_n<N2, true>();
+  if (e != cudaSuccess) return e;
   const int ntiles = (L + kBM - 1) / kBM;
-  const int grid = std::min(ntiles, sms);
-  temporal_umma_kernel<N2><<<grid, kUThreads, S::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status, row_slot);
+  temporal_umma_kernel<N2, false><<<std::min(ntiles, sms), kUThreads, S::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status,
+                                                                                     row_slot, wcol, fix);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // listed rows: at most min(L, cap); CTAs beyond the listed tiles return at once
+  const int gtiles = (std::min(L, fix.cap) + kBM - 1) / kBM;
+  if (gtiles <= 0) return cudaSuccess;
+  temporal_umma_kernel<N2, true><<<std::min(gtiles, sms), kUThreads, S::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status,
+                                                                                    row_slot, wcol, fix);
   return cudaGetLastError();
 }
 
@@ -430,17 +518,17 @@ bool make_temporal_maps(const void* Bh, const void* Bl, int T, int twoF, Tempora
   return true;
 }
 
-cudaError_t launch_temporal_umma(const TemporalMaps& m, const float* h, float* C, int L, int T, int twoF,
-                                 int* status, cudaStream_t s, const int* row_slot) {
+cudaError_t launch_temporal_umma(const TemporalMaps& m, const float* h, const float* wcol, float* C, int L, int T,
+                                 int twoF, const TemporalFix& fix, int* status, cudaStream_t s, const int* row_slot) {
   if (L <= 0) return cudaSuccess;
   if (!m.ok || !temporal_umma_supported(T, twoF) || reinterpret_cast<uintptr_t>(h) % 16 != 0 ||
-      reinterpret_cast<uintptr_t>(C) % 16 != 0)
+      reinterpret_cast<uintptr_t>(C) % 16 != 0 || reinterpret_cast<uintptr_t>(wcol) % 16 != 0)
     return cudaErrorInvalidValue;
   switch (twoF) {
-    case 32: return launch_n<32>(m, h, C, L, T, status, s, row_slot);
-    case 64: return launch_n<64>(m, h, C, L, T, status, s, row_slot);
-    case 128: return launch_n<128>(m, h, C, L, T, status, s, row_slot);
-    default: return launch_n<256>(m, h, C, L, T, status, s, row_slot);
+    case 32: return launch_n<32>(m, h, wcol, C, L, T, fix, status, s, row_slot);
+    case 64: return launch_n<64>(m, h, wcol, C, L, T, fix, status, s, row_slot);
+    case 128: return launch_n<128>(m, h, wcol, C, L, T, fix, status, s, row_slot);
+    default: return launch_n<256>(m, h, wcol, C, L, T, fix, status, s, row_slot);
   }
 }
 
