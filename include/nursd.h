@@ -342,9 +342,20 @@ typedef enum {
 /*
  * enable != 0: from now on every stage brackets its launches with a pair of
  * CUDA events recorded on the caller's stream; enable == 0 stops recording.
- * Either way the recorded events are discarded.
+ * Either way the recorded events are discarded.  While the stream is being
+ * captured into a CUDA graph the pair is recorded as two event-record nodes
+ * of the graph, so each replay of that graph times the stage again (one pair
+ * per captured stage execution: capture a graph per replay whose times are
+ * wanted, then read them after the replays).
  */
 int nursd_profile_enable(nursd_plan_t plan, int enable);
+
+/*
+ * As nursd_profile_enable(plan, 1) for the stages whose bit (1u << stage) is
+ * set in stage_mask only (0: recording off).  A single stage brackets fewer
+ * launches than every stage would, so it perturbs the timed sequence less.
+ */
+int nursd_profile_select(nursd_plan_t plan, uint32_t stage_mask);
 
 /*
  * For stage `stage`: *h_ms = summed device time of the launches recorded

@@ -67,8 +67,14 @@ struct nursd_plan_s {
   int2* cls = nullptr;
   float2* Gc = nullptr;
   float2* GcT = nullptr;  // transposed table [ncls][Z][F] for the adjoint (NURSD_ENABLE_ADJOINT)
-  __half* Bth = nullptr;  // temporal twiddles B^T [2F][T], fp16 head
+  // position gradients (NURSD_ENABLE_ADJOINT): deconv_k[i] = (i - M/2) deconv[i], and the type-2
+  // grids [W][W][F] of kx R and ky R
+  float* deconv_k = nullptr;
+  float2 *fine_dx = nullptr, *fine_dy = nullptr;
+  __half* Bth = nullptr;  // temporal twiddles B^T [2F][T] (unit modulus), fp16 head
   __half* Btl = nullptr;  // and tail (B - head)
+  float* wcol = nullptr;  // weight of each temporal output column [2F] (w_f twice)
+  TemporalFix tfix{};     // rows outside the fp16 split's window, recomputed scaled
   TemporalMaps tmaps{};   // TMA descriptors of Bth/Btl for the tcgen05 form (ok = 0: mma.sync form)
   // SRSD tables (h_srsd_pitch given): scaled transfer table [Z][ncls][F], chirps [Z][M], FFT(b)/(2M) [Z][2M]
   std::vector<double> srsd_pitch;
@@ -115,6 +121,7 @@ struct nursd_plan_s {
   std::vector<void*> allocs;
   // profiling: per stage, a list of (start, stop) events and how many are in use
   bool profiling = false;
+  uint32_t profile_mask = 0;  // stages recorded while profiling
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[NURSD_NUM_STAGES];
   size_t ev_used[NURSD_NUM_STAGES] = {};
   int64_t launches = 0;
@@ -166,7 +173,7 @@ class StageTimer {
  public:
   StageTimer(nursd_plan_s* p, int stage, cudaStream_t s, int launches) : p_(p), stage_(stage), s_(s) {
     p->launches += launches;
-    if (!p->profiling) return;
+    if (!p->profiling || !(p->profile_mask & (1u << stage))) return;
     auto& v = p->ev[stage];
     if (p->ev_used[stage] == v.size()) {
       std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
@@ -177,10 +184,10 @@ class StageTimer {
       v.push_back(e);
     }
     pair_ = &v[p->ev_used[stage]++];
-    cudaEventRecord(pair_->first, s);
+    record(pair_->first);
   }
   ~StageTimer() {
-    if (pair_) cudaEventRecord(pair_->second, s_);
+    if (pair_) record(pair_->second);
   }
 
  private:
@@ -188,6 +195,14 @@ class StageTimer {
   int stage_;
   cudaStream_t s_;
   std::pair<cudaEvent_t, cudaEvent_t>* pair_ = nullptr;
+  // an event-record node of the graph while s is being captured, a plain record otherwise
+  void record(cudaEvent_t e) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s_, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+      cudaEventRecordWithFlags(e, s_, cudaEventRecordExternal);
+    else
+      cudaEventRecord(e, s_);
+  }
 };
 
 }  // namespace
@@ -198,13 +213,15 @@ int from_cuda(cudaError_t e) { return e == cudaSuccess ? NURSD_OK : NURSD_ERR_CU
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-// C[L][2F] = H[L][T] B: tcgen05 form when the plan has its descriptors and both buffers are
-// 16-byte aligned, mma.sync form otherwise.  row_slot (optional): row l goes to row row_slot[l].
+// C[L][2F] = H[L][T] B diag(w): tcgen05 form when the plan has its descriptors and both buffers
+// are 16-byte aligned, mma.sync form otherwise; each issues a first launch and a gather launch of
+// the rows outside the fp16 split's window.  row_slot (optional): row l goes to row row_slot[l].
+constexpr int kTemporalLaunches = 2;
 cudaError_t run_temporal(const nursd_plan_s* p, const float* h, float* C, int L, cudaStream_t s,
                          const int* row_slot = nullptr) {
   if (p->tmaps.ok && aligned(h, 16) && aligned(C, 16))
-    return launch_temporal_umma(p->tmaps, h, C, L, p->T, 2 * p->F, p->status, s, row_slot);
-  return launch_temporal_tc(h, p->Bth, p->Btl, C, L, p->T, 2 * p->F, s, row_slot);
+    return launch_temporal_umma(p->tmaps, h, p->wcol, C, L, p->T, 2 * p->F, p->tfix, p->status, s, row_slot);
+  return launch_temporal_tc(h, p->Bth, p->Btl, p->wcol, C, L, p->T, 2 * p->F, p->tfix, s, row_slot);
 }
 
 PanelArgs panel_base(const nursd_plan_s* p) {
@@ -705,8 +722,14 @@ int run_adjoint_spectrum(nursd_plan_s* p, const float2* vol, cudaStream_t s) {
 // factors), zero-pad to the fine grid, inverse FFT along kx, then along ky.
 // plane_major = false: fine [W][W][C] (channel-last, for relay samples);
 // plane_major = true: fine [C][W][W] (one plane per channel, for voxel sets).
-int run_type2_to_fine(nursd_plan_s* p, const float2* spec, int C, bool plane_major, float scale, cudaStream_t s) {
+// mul_kx / mul_ky (default: the deconvolution table) are the real factors of kx and ky, and
+// fine_out (default: p->fine) the grid written.
+int run_type2_to_fine(nursd_plan_s* p, const float2* spec, int C, bool plane_major, float scale, cudaStream_t s,
+                      const float* mul_kx = nullptr, const float* mul_ky = nullptr, float2* fine_out = nullptr) {
   const int M = p->M, W = p->W;
+  if (!mul_kx) mul_kx = p->deconv;
+  if (!mul_ky) mul_ky = p->deconv;
+  if (!fine_out) fine_out = p->fine;
   const int logf = ilog2(p->nf);
   cudaError_t e;
   {
@@ -716,8 +739,8 @@ int run_type2_to_fine(nursd_plan_s* p, const float2* spec, int C, bool plane_maj
     a.in_sb = (long long)M * C;
     a.in_si = C;
     a.in_slo = 1;
-    a.mul_i = p->deconv;  // 1/psi_hat(kx), input index i <-> kx = i - M/2
-    a.mul_b = p->deconv;  // 1/psi_hat(ky), batch b <-> ky = b - M/2
+    a.mul_i = mul_kx;  // 1/psi_hat(kx), input index i <-> kx = i - M/2
+    a.mul_b = mul_ky;  // 1/psi_hat(ky), batch b <-> ky = b - M/2
     a.out = p->R1;
     a.out_sb = (long long)W * C;
     a.out_si = C;
@@ -739,7 +762,7 @@ int run_type2_to_fine(nursd_plan_s* p, const float2* spec, int C, bool plane_maj
     a.in_off = -M / 2;
     a.nout = W;
     a.out_off = p->g0;
-    a.out = p->fine;
+    a.out = fine_out;
     a.scale = scale;
     const int cp = panel_width(logf);
     if (!plane_major) {  // batch over x, channels c
@@ -887,16 +910,19 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
   cls.reserve(p->ncls);
   for (int pp = 0; pp <= half; ++pp)
     for (int qq = 0; qq <= pp; ++qq) cls.push_back(make_int2(pp, qq));
-  // temporal twiddles, transposed: B^T[2f][n] = w_f cos(w_f t_n), B^T[2f+1][n] = -w_f sin(w_f t_n)
-  // (FP64), stored as fp16 head + tail for the tensor-core GEMM
+  // temporal twiddles, transposed: B^T[2f][n] = cos(w_f t_n), B^T[2f+1][n] = -sin(w_f t_n)
+  // (FP64, phase reduced mod 2 pi), stored as fp16 head + tail for the tensor-core GEMM; the
+  // weight w_f multiplies the accumulator (column weights wc), so no weight is rounded to fp16
   std::vector<__half> Bth, Btl;
+  std::vector<float> wc(2 * (size_t)p->F);
+  for (int f = 0; f < p->F; ++f) wc[2 * f] = wc[2 * f + 1] = (float)p->weight[f];
   if (p->T > 0) {
     Bth.resize((size_t)p->T * 2 * p->F);
     Btl.resize(Bth.size());
     for (int f = 0; f < p->F; ++f)
       for (int n = 0; n < p->T; ++n) {
-        const double ph = p->omega[f] * (p->t0 + n * p->dt);
-        const double v[2] = {p->weight[f] * std::cos(ph), -p->weight[f] * std::sin(ph)};
+        const double ph = std::fmod(p->omega[f] * (p->t0 + n * p->dt), 2.0 * kPi);
+        const double v[2] = {std::cos(ph), -std::sin(ph)};
         for (int c = 0; c < 2; ++c) {
           const __half hi = __float2half_rn((float)v[c]);
           const size_t idx = (size_t)(2 * f + c) * p->T + n;
@@ -920,8 +946,16 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
             p->alloc(p->R1, (size_t)p->W * p->M * std::max(p->F, p->Z)) &&
             p->alloc(p->U, (size_t)p->M * p->M * p->F) && p->alloc(p->Y, (size_t)p->M * p->M * p->Z) &&
             p->alloc(p->T1, (size_t)p->M * p->N * p->Z);
-  if (ok && p->T > 0) ok = p->alloc(p->Bth, Bth.size()) && p->alloc(p->Btl, Btl.size());
-  if (ok && (p->flags & NURSD_ENABLE_ADJOINT)) ok = p->alloc(p->GcT, (size_t)p->ncls * p->F * p->Z);
+  if (ok && p->T > 0) {  // the row list holds every row a call can pass: maxL, or maxB items of maxL
+    const size_t rows = (size_t)maxL * std::max(1, p->maxB);
+    ok = p->alloc(p->Bth, Bth.size()) && p->alloc(p->Btl, Btl.size()) && p->alloc(p->wcol, wc.size()) &&
+         p->alloc(p->tfix.count, 2) && p->alloc(p->tfix.list, rows);
+    if (ok) p->tfix.done = p->tfix.count + 1;
+    p->tfix.cap = (int)std::min<size_t>(rows, 1u << 30);
+  }
+  if (ok && (p->flags & NURSD_ENABLE_ADJOINT))
+    ok = p->alloc(p->GcT, (size_t)p->ncls * p->F * p->Z) && p->alloc(p->deconv_k, p->M) &&
+         p->alloc(p->fine_dx, (size_t)p->W * p->W * p->F) && p->alloc(p->fine_dy, (size_t)p->W * p->W * p->F);
   if (ok && p->maxB > 0)
     ok = p->alloc(p->phasor_all, (size_t)p->maxB * maxL * p->F) &&
          p->alloc(p->U_all, (size_t)p->maxB * p->M * p->M * p->F) &&
@@ -951,12 +985,19 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
   int rc = from_cuda(cudaMemcpyAsync(p->twiddle, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice, s));
   if (rc == NURSD_OK)
     rc = from_cuda(cudaMemcpyAsync(p->deconv, dec.data(), sizeof(float) * dec.size(), cudaMemcpyHostToDevice, s));
+  std::vector<float> deck(p->M);
+  for (int i = 0; i < p->M; ++i) deck[i] = (float)((i - half) * (double)dec[i]);
+  if (rc == NURSD_OK && p->deconv_k)
+    rc = from_cuda(cudaMemcpyAsync(p->deconv_k, deck.data(), sizeof(float) * deck.size(), cudaMemcpyHostToDevice, s));
   if (rc == NURSD_OK)
     rc = from_cuda(cudaMemcpyAsync(p->cls, cls.data(), sizeof(int2) * cls.size(), cudaMemcpyHostToDevice, s));
   if (rc == NURSD_OK && p->T > 0)
     rc = from_cuda(cudaMemcpyAsync(p->Bth, Bth.data(), sizeof(__half) * Bth.size(), cudaMemcpyHostToDevice, s));
   if (rc == NURSD_OK && p->T > 0)
     rc = from_cuda(cudaMemcpyAsync(p->Btl, Btl.data(), sizeof(__half) * Btl.size(), cudaMemcpyHostToDevice, s));
+  if (rc == NURSD_OK && p->T > 0)
+    rc = from_cuda(cudaMemcpyAsync(p->wcol, wc.data(), sizeof(float) * wc.size(), cudaMemcpyHostToDevice, s));
+  if (rc == NURSD_OK && p->T > 0) rc = from_cuda(cudaMemsetAsync(p->tfix.count, 0, 2 * sizeof(int), s));
   if (rc == NURSD_OK) rc = from_cuda(cudaMemsetAsync(p->status, 0, sizeof(int), s));
   if (rc == NURSD_OK) rc = from_cuda(cudaMemsetAsync(p->bin_start, 0, sizeof(int) * (nbins + 1), s));
   if (rc == NURSD_OK && p->T > 0) make_temporal_maps(p->Bth, p->Btl, p->T, 2 * p->F, &p->tmaps);
@@ -1022,7 +1063,7 @@ int nursd_set_points(nursd_plan_t p, int32_t L, const float* d_xy, nursd_stream_
 int nursd_temporal_dft(nursd_plan_t p, int32_t L, const float* d_hist, nursd_c64* d_phasor, nursd_stream_t stream) {
   if (check_plan(p) != NURSD_OK || p->T <= 0 || L < 0 || L > p->maxL) return NURSD_ERR_INVALID_ARG;
   if (L > 0 && (!d_hist || !d_phasor || !aligned(d_hist, 16) || !aligned(d_phasor, 8))) return NURSD_ERR_INVALID_ARG;
-  StageTimer t(p, NURSD_STAGE_TEMPORAL, static_cast<cudaStream_t>(stream), L > 0 ? 1 : 0);
+  StageTimer t(p, NURSD_STAGE_TEMPORAL, static_cast<cudaStream_t>(stream), L > 0 ? kTemporalLaunches : 0);
   return from_cuda(run_temporal(p, d_hist, reinterpret_cast<float*>(d_phasor), L, static_cast<cudaStream_t>(stream)));
 }
 
@@ -1054,7 +1095,7 @@ int nursd_forward(nursd_plan_t p, const float* d_hist, void* d_out, nursd_stream
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc;
   {
-    StageTimer t(p, NURSD_STAGE_TEMPORAL, s, p->L > 0 ? 1 : 0);
+    StageTimer t(p, NURSD_STAGE_TEMPORAL, s, p->L > 0 ? kTemporalLaunches : 0);
     // phasors straight into the spread's sorted order (the internal buffer is read only by the spread)
     rc = from_cuda(run_temporal(p, d_hist, reinterpret_cast<float*>(p->phasor), p->L, s, p->slot_of));
   }
@@ -1086,7 +1127,7 @@ int nursd_reconstruct(nursd_plan_t p, int32_t L, const float* d_xy, const float*
   if (rc == NURSD_OK) rc = from_cuda(cudaEventRecord(p->ev_join, p->side));
   if (rc != NURSD_OK) return rc;
   {
-    StageTimer t(p, NURSD_STAGE_TEMPORAL, s, L > 0 ? 1 : 0);
+    StageTimer t(p, NURSD_STAGE_TEMPORAL, s, L > 0 ? kTemporalLaunches : 0);
     rc = from_cuda(run_temporal(p, d_hist, reinterpret_cast<float*>(p->phasor), L, s));
   }
   const int rj = from_cuda(cudaStreamWaitEvent(s, p->ev_join, 0));  // join even if the temporal launch failed
@@ -1115,7 +1156,6 @@ int nursd_adjoint(nursd_plan_t p, const nursd_c64* d_vol, nursd_c64* d_phasor, n
     a.sorted_l = p->sorted_l;
     a.i0 = p->i0_sorted;
     a.wts = p->w_sorted;
-    a.frac = p->frac_sorted;
     a.scale = 1.f;
     a.out = reinterpret_cast<float2*>(d_phasor);
     rc = from_cuda(launch_interp_points(a, s));
@@ -1132,22 +1172,27 @@ int nursd_grad_points(nursd_plan_t p, const nursd_c64* d_w, const nursd_c64* d_p
   if (p->L > 0 && d_grad_phasor && !aligned(d_grad_phasor, 8)) return NURSD_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc = run_adjoint_spectrum(p, reinterpret_cast<const float2*>(d_w), s);
-  if (rc == NURSD_OK) rc = run_type2_to_fine(p, p->U, p->F, false, 1.f, s);
+  if (rc == NURSD_OK && d_grad_phasor) rc = run_type2_to_fine(p, p->U, p->F, false, 1.f, s);
+  if (rc == NURSD_OK && d_grad_xy) {  // the spectral derivative: type 2 of kx R and of ky R
+    rc = run_type2_to_fine(p, p->U, p->F, false, 1.f, s, p->deconv_k, p->deconv, p->fine_dx);
+    if (rc == NURSD_OK) rc = run_type2_to_fine(p, p->U, p->F, false, 1.f, s, p->deconv, p->deconv_k, p->fine_dy);
+  }
   if (rc == NURSD_OK) {
     StageTimer t(p, NURSD_STAGE_SPREAD, s, p->L > 0 ? 1 : 0);
     InterpArgs a;
     std::memset(&a, 0, sizeof(a));
     a.fine = p->fine;
+    a.fine_dx = p->fine_dx;
+    a.fine_dy = p->fine_dy;
     a.W = p->W;
     a.F = p->F;
     a.width = p->w;
     a.L = p->L;
     a.beta = p->beta;
-    a.dudx = (float)(2.0 / p->pitch);
+    a.dudx = (float)(2.0 * kPi / (p->M * p->pitch));  // d theta / dx
     a.sorted_l = p->sorted_l;
     a.i0 = p->i0_sorted;
     a.wts = p->w_sorted;
-    a.frac = p->frac_sorted;
     a.scale = 1.f;
     a.out = reinterpret_cast<float2*>(d_grad_phasor);
     a.P = reinterpret_cast<const float2*>(d_phasor);
@@ -1288,7 +1333,7 @@ int nursd_forward_batched(nursd_plan_t p, int32_t B, const nursd_batch_item* ite
   const long long u_stride = (long long)M * M * F, y_stride = (long long)M * M * Z;
   int rc = NURSD_OK;
   {  // temporal transforms of every item: one persistent launch over the ragged tile list
-    StageTimer t(p, NURSD_STAGE_TEMPORAL, s, 1);
+    StageTimer t(p, NURSD_STAGE_TEMPORAL, s, kTemporalLaunches);
     TemporalBatch bt;
     bt.n = B;
     bt.tile_start[0] = 0;
@@ -1299,7 +1344,7 @@ int nursd_forward_batched(nursd_plan_t p, int32_t B, const nursd_batch_item* ite
       bt.L[b] = items[b].L;
       bt.tile_start[b + 1] = bt.tile_start[b] + ((items[b].L + 127) / 128) * ncol;
     }
-    rc = from_cuda(launch_temporal_tc_batched(bt, p->Bth, p->Btl, p->T, 2 * F, p->counter, s));
+    rc = from_cuda(launch_temporal_tc_batched(bt, p->Bth, p->Btl, p->wcol, p->T, 2 * F, p->tfix, p->counter, s));
   }
   for (int b = 0; rc == NURSD_OK && b < B; ++b) {  // per item: sort, spread, fine-grid FFTs -> U_all[b]
     rc = nursd_set_points(p, items[b].L, items[b].d_xy, stream);
@@ -1316,8 +1361,13 @@ int nursd_forward_batched(nursd_plan_t p, int32_t B, const nursd_batch_item* ite
 }
 
 int nursd_profile_enable(nursd_plan_t p, int enable) {
+  return nursd_profile_select(p, enable ? (1u << NURSD_NUM_STAGES) - 1u : 0u);
+}
+
+int nursd_profile_select(nursd_plan_t p, uint32_t stage_mask) {
   if (check_plan(p) != NURSD_OK) return NURSD_ERR_INVALID_ARG;
-  p->profiling = enable != 0;
+  p->profile_mask = stage_mask & ((1u << NURSD_NUM_STAGES) - 1u);
+  p->profiling = p->profile_mask != 0;
   for (auto& u : p->ev_used) u = 0;
   return NURSD_OK;
 }

@@ -7,8 +7,9 @@
 //
 // interp_points: relay samples on a channel-last grid [W][W][F]; one warp per
 //   sample, one lane per channel, so each tap is a 256-byte coalesced row.  With
-//   GRAD the same taps also give d/du of the value through phi'(z) and are
-//   reduced against the sample's phasors into the position gradient.
+//   GRAD the same taps interpolate two more grids, the type-2 grids of kx R and
+//   ky R (the spectral derivative), reduced against the sample's phasors into the
+//   position gradient.
 // interp_planes: voxels of each depth plane on a plane-major grid [Z][W][W];
 //   one thread per voxel (rows of w contiguous cells).
 #include "nursd_internal.cuh"
@@ -23,22 +24,11 @@ __global__ void __launch_bounds__(256) interp_points_kernel(const InterpArgs a) 
   if (slot >= a.L) return;
   const int l = __ldg(a.sorted_l + slot);
   const int2 o = __ldg(a.i0 + slot);
-  float wx[WID], wy[WID], dwx[WID], dwy[WID];
+  float wx[WID], wy[WID];
 #pragma unroll
   for (int t = 0; t < WID; ++t) {
     wx[t] = __ldg(a.wts + (size_t)slot * 2 * WID + t);
     wy[t] = __ldg(a.wts + (size_t)slot * 2 * WID + WID + t);
-  }
-  if (GRAD) {
-    // d/du phi(2 (i0 + t - u) / w) = phi(z) beta z (2/w) / sqrt(1 - z^2), z = 2 (t - frac) / w
-    const float2 fr = __ldg(a.frac + slot);
-#pragma unroll
-    for (int t = 0; t < WID; ++t) {
-      const float zx = 2.f * ((float)t - fr.x) / WID, zy = 2.f * ((float)t - fr.y) / WID;
-      const float qx = 1.f - zx * zx, qy = 1.f - zy * zy;
-      dwx[t] = qx > 0.f ? wx[t] * a.beta * zx * (2.f / WID) * rsqrtf(qx) : 0.f;
-      dwy[t] = qy > 0.f ? wy[t] * a.beta * zy * (2.f / WID) * rsqrtf(qy) : 0.f;
-    }
   }
   float gsx = 0.f, gsy = 0.f;
   for (int f0 = 0; f0 < a.F; f0 += 32) {
@@ -47,32 +37,40 @@ __global__ void __launch_bounds__(256) interp_points_kernel(const InterpArgs a) 
     float2 acc = make_float2(0.f, 0.f), ax = make_float2(0.f, 0.f), ay = make_float2(0.f, 0.f);
 #pragma unroll
     for (int ty = 0; ty < WID; ++ty) {
-      const float2* row = a.fine + ((size_t)(o.y + ty) * a.W + o.x) * a.F + f;
-      float2 rs = make_float2(0.f, 0.f), rd = make_float2(0.f, 0.f);
+      const size_t row = ((size_t)(o.y + ty) * a.W + o.x) * a.F + f;
+      float2 rs = make_float2(0.f, 0.f), rx = make_float2(0.f, 0.f), ry = make_float2(0.f, 0.f);
 #pragma unroll
       for (int tx = 0; tx < WID; ++tx) {
-        const float2 v = __ldg(row + (size_t)tx * a.F);
-        rs.x = fmaf(v.x, wx[tx], rs.x);
-        rs.y = fmaf(v.y, wx[tx], rs.y);
+        const size_t at = row + (size_t)tx * a.F;
+        if (a.out) {
+          const float2 v = __ldg(a.fine + at);
+          rs.x = fmaf(v.x, wx[tx], rs.x);
+          rs.y = fmaf(v.y, wx[tx], rs.y);
+        }
         if (GRAD) {
-          rd.x = fmaf(v.x, dwx[tx], rd.x);
-          rd.y = fmaf(v.y, dwx[tx], rd.y);
+          const float2 vx = __ldg(a.fine_dx + at), vy = __ldg(a.fine_dy + at);
+          rx.x = fmaf(vx.x, wx[tx], rx.x);
+          rx.y = fmaf(vx.y, wx[tx], rx.y);
+          ry.x = fmaf(vy.x, wx[tx], ry.x);
+          ry.y = fmaf(vy.y, wx[tx], ry.y);
         }
       }
       acc.x = fmaf(rs.x, wy[ty], acc.x);
       acc.y = fmaf(rs.y, wy[ty], acc.y);
       if (GRAD) {
-        ax.x = fmaf(rd.x, wy[ty], ax.x);
-        ax.y = fmaf(rd.y, wy[ty], ax.y);
-        ay.x = fmaf(rs.x, dwy[ty], ay.x);
-        ay.y = fmaf(rs.y, dwy[ty], ay.y);
+        ax.x = fmaf(rx.x, wy[ty], ax.x);
+        ax.y = fmaf(rx.y, wy[ty], ax.y);
+        ay.x = fmaf(ry.x, wy[ty], ay.x);
+        ay.y = fmaf(ry.y, wy[ty], ay.y);
       }
     }
     if (a.out) a.out[(size_t)l * a.F + f] = make_float2(acc.x * a.scale, acc.y * a.scale);
     if (GRAD) {
+      // d/dx of the type-2 value is i (2 pi / (M delta)) times the type 2 of kx R, so
+      // Re(p conj(d/dx)) = (2 pi / (M delta)) Im(p conj(ax))
       const float2 p = __ldg(a.P + (size_t)l * a.F + f);
-      gsx += p.x * ax.x + p.y * ax.y;  // Re(p conj(ax))
-      gsy += p.x * ay.x + p.y * ay.y;
+      gsx += p.y * ax.x - p.x * ax.y;
+      gsy += p.y * ay.x - p.x * ay.y;
     }
   }
   if (GRAD) {
@@ -153,7 +151,7 @@ cudaError_t planes_w(const PlaneInterpArgs& a, cudaStream_t s) {
 
 cudaError_t launch_interp_points(const InterpArgs& a, cudaStream_t s) {
   if (a.L <= 0) return cudaSuccess;
-  if (a.gxy && (!a.P || !a.frac)) return cudaErrorInvalidValue;
+  if (a.gxy && (!a.P || !a.fine_dx || !a.fine_dy)) return cudaErrorInvalidValue;
   switch (a.width) {
     case 4: return points_w<4>(a, s);
     case 5: return points_w<5>(a, s);

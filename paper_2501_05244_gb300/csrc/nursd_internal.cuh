@@ -113,11 +113,41 @@ cudaError_t launch_panel_bluestein(int logn, const PanelArgs& a, const float2* c
                                    const float2* cpost, cudaStream_t s);
 
 // ------------------------------------------------------------- temporal DFT
-// P[l][f] = sum_n h[l][n] * B[n][2f..2f+1] as a real GEMM C[L][2F] = H[L][T] B[T][2F] on the
-// tensor cores; Bh/Bl are the fp16 head and tail of B^T, [2F][T] (__half).  row_slot (optional):
-// row l of C is written at row row_slot[l] (the spread's sorted order).
-cudaError_t launch_temporal_tc(const float* h, const void* Bh, const void* Bl, float* C, int L, int T, int twoF,
-                               cudaStream_t s, const int* row_slot = nullptr);
+// P[l][f] = w_f sum_n h[l][n] * B[n][2f..2f+1] as a real GEMM C[L][2F] = H[L][T] B[T][2F] diag(wcol)
+// on the tensor cores; Bh/Bl are the fp16 head and tail of the unit-modulus B^T, [2F][T] (__half),
+// wcol [2F] the weight of each column (w_f twice).  row_slot (optional): row l of C is written at
+// row row_slot[l] (the spread's sorted order).
+//
+// Range: every operand is split into an fp16 head and tail, which carries ~22 bits of a value
+// whose row max m lies in [2^-3, 65504).  Rows outside that window are listed in a TemporalFix
+// (row, exponent e with m 2^-e in [2^14, 2^15), batch item) by the first launch, and a gather
+// launch recomputes exactly those rows from h 2^-e, scaling the result by 2^e.
+constexpr int kRowInRange = 0x7fffffff;
+__device__ __forceinline__ int temporal_row_exponent(float m) {
+  if (m == 0.f || !isfinite(m) || (m >= 0.125f && m < 65504.f)) return kRowInRange;
+  return ilogbf(m) - 14;
+}
+struct TemporalFix {
+  int* count;  // device: rows listed; zero between calls (the gather launch clears it)
+  int* done;   // device: gather CTAs that have read count (zero between calls)
+  int4* list;  // device [cap]: {row, e, batch item, 0}
+  int cap;
+};
+// Gather launch prologue, thread 0 of each CTA: reads the listed-row count, and the last CTA to do
+// so clears count and done for the next call.  Returns the count.
+__device__ __forceinline__ int temporal_fix_take(const TemporalFix& fix) {
+  const int n = *(volatile int*)fix.count;
+  __threadfence();
+  if (atomicAdd(fix.done, 1) == (int)(gridDim.x * gridDim.y * gridDim.z) - 1) {
+    __threadfence();
+    *(volatile int*)fix.count = 0;
+    *(volatile int*)fix.done = 0;
+  }
+  return n;
+}
+cudaError_t launch_temporal_tc(const float* h, const void* Bh, const void* Bl, const float* wcol, float* C, int L,
+                               int T, int twoF, const TemporalFix& fix, cudaStream_t s,
+                               const int* row_slot = nullptr);
 
 // The same transform with tcgen05.mma (temporal_umma.cu), for T % 32 == 0 and 2F in {32, 64, 128, 256}.
 // TMA descriptors of B's head and tail ([2F][T] fp16) are encoded once per plan.
@@ -128,9 +158,11 @@ struct TemporalMaps {
 };
 bool temporal_umma_supported(int T, int twoF);
 bool make_temporal_maps(const void* Bh, const void* Bl, int T, int twoF, TemporalMaps* m);
-// status: bit 4 is set if a barrier wait timed out (the output is then incomplete).
-cudaError_t launch_temporal_umma(const TemporalMaps& m, const float* h, float* C, int L, int T, int twoF,
-                                 int* status, cudaStream_t s, const int* row_slot = nullptr);
+// status: bit 4 is set if a barrier wait timed out (the output is then incomplete).  Both the
+// first launch and the gather launch of listed rows (see TemporalFix) are issued on s.
+cudaError_t launch_temporal_umma(const TemporalMaps& m, const float* h, const float* wcol, float* C, int L, int T,
+                                 int twoF, const TemporalFix& fix, int* status, cudaStream_t s,
+                                 const int* row_slot = nullptr);
 
 // Ragged batch of temporal transforms: item b has L[b] rows at A[b] -> C[b];
 // tile_start[b] = number of 128 x 128 output tiles of items 0..b-1.
@@ -141,8 +173,8 @@ struct TemporalBatch {
   int L[kMaxBatch];
   int tile_start[kMaxBatch + 1];
 };
-cudaError_t launch_temporal_tc_batched(const TemporalBatch& bt, const void* Bh, const void* Bl, int T, int twoF,
-                                       int* counter, cudaStream_t s);
+cudaError_t launch_temporal_tc_batched(const TemporalBatch& bt, const void* Bh, const void* Bl, const float* wcol,
+                                       int T, int twoF, const TemporalFix& fix, int* counter, cudaStream_t s);
 
 // ---------------------------------------------------------------- points
 struct PointsArgs {
@@ -191,16 +223,18 @@ cudaError_t launch_contract_adjoint(const float2* Yt, const float2* GcT, const i
 // ------------------------------------------------------------ interpolation
 // Type-2 interpolation at the sorted relay samples from a channel-last fine
 // grid [W][W][F]: out[l][f] = scale * sum_taps fine[i0y+ty][i0x+tx][f] wx wy.
-// With grad: also d/dx, d/dy of that value (ES kernel derivative) reduced
-// against P: gxy[l] = scale_g * Re sum_f P[l][f] conj(d out[l][f] / d(x,y)).
+// With gxy: the same taps on fine_dx / fine_dy, the type-2 grids of kx R and
+// ky R, give d/d(x, y) of that value as i dudx times their interpolants, reduced
+// against P: gxy[l] = scale * dudx * Im sum_f P[l][f] conj(interpolant).
 struct InterpArgs {
-  const float2* fine;
+  const float2* fine;         // value grid (read when out is set)
+  const float2* fine_dx;      // derivative grids (read when gxy is set)
+  const float2* fine_dy;
   int W, F, width, L;
-  float beta, dudx;           // ES shape; fine cells per metre (sigma / delta)
+  float beta, dudx;           // ES shape; d theta / dx = 2 pi / (M delta)
   const int* sorted_l;
   const int2* i0;
   const float* wts;           // [L][2w] sorted
-  const float2* frac;         // [L] sorted: u - i0 per axis
   float scale;
   float2* out;                // [L][F] (original sample order) or null
   const float2* P;            // [L][F] for the gradient reduction

@@ -32,7 +32,8 @@ EXPORTS = (
     "nursd_status_string", "nursd_phasor_frequencies", "nursd_plan_create", "nursd_plan_destroy",
     "nursd_plan_bytes", "nursd_plan_dims", "nursd_set_points", "nursd_temporal_dft", "nursd_nufft1",
     "nursd_propagate", "nursd_forward_phasor", "nursd_forward", "nursd_sync_status",
-    "nursd_profile_enable", "nursd_profile_read", "nursd_launch_count", "nursd_nufft1_noalloc",
+    "nursd_profile_enable", "nursd_profile_select", "nursd_profile_read", "nursd_launch_count",
+    "nursd_nufft1_noalloc",
     "nursd_forward_points", "nursd_adjoint", "nursd_grad_points", "srsd_forward", "nursd_forward_batched",
     "nursd_reconstruct", "nursd_forward_illuminated", "nursd_transient_frames", "srsd_forward_points",
 )
@@ -94,6 +95,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "nursd_forward": (ctypes.c_int, [vp, vp, vp, vp]),
         "nursd_sync_status": (ctypes.c_int, [vp, vp]),
         "nursd_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
+        "nursd_profile_select": (ctypes.c_int, [vp, ctypes.c_uint32]),
         "nursd_profile_read": (ctypes.c_int, [vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int64)]),
         "nursd_launch_count": (i64, [vp]),
         "nursd_nufft1_noalloc": (ctypes.c_int, [i32, dbl, dbl, dbl, i32, i32, vp, i32, vp, vp, vp]),
@@ -426,6 +428,13 @@ class Plan:
     # -- profiling
     def profile(self, enable: bool = True):
         _check(self._lib.nursd_profile_enable(self._h, 1 if enable else 0), "nursd_profile_enable")
+
+    def profile_stages(self, names):
+        """Time only the named stages (see STAGES); an empty list stops recording."""
+        mask = 0
+        for n in names:
+            mask |= 1 << STAGES.index(n)
+        _check(self._lib.nursd_profile_select(self._h, mask), "nursd_profile_select")
 
     def profile_read(self):
         """{stage: (total_ms, executions)} since profiling was enabled or last read."""

@@ -4,11 +4,12 @@ output at arbitrary voxels (a8), against the FP64 oracle, through the C ABI.
 Tolerances: 1e-4 relative L2 for complex outputs (the parity gate); the
 adjoint identity <A P, V> = <P, A^H V> on the GPU to 1e-5 relative (the
 NUFFT type-2 is the exact adjoint of the implemented type-1, so only FP32
-rounding remains); position gradients to 2e-3 relative L2, because they are
-the derivative of the ES-kernel interpolant (the exact derivative of the
-implemented operator), whose error relative to the exact operator's
-derivative is larger than the value error by about the kernel's slope
-(beta ~ 14 over half-width 3 cells), i.e. 10-100 x the 1e-5 value error.
+rounding remains).  Position gradients are the spectral derivative (type 2 of
+i kx R and i ky R), as accurate as a type-2 value, and are gated per coordinate
+against FP64 central differences: |g - fd| <= 1e-3 max(|fd|, 1e-2 rms(fd)) (a
+coordinate whose gradient is a hundred times below the typical one has no
+meaningful relative error, so its denominator is floored there), and to 1e-4
+relative L2 against the oracle's analytic gradient.
 """
 import math
 
@@ -24,7 +25,15 @@ from workloads import (BASE_SEED, random_phasors, random_plane_points, relay_key
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-4
-GRAD_TOL = 2e-3
+GRAD_TOL = 1e-4
+FD_REL = 1e-3
+
+
+def fd_gate(g, fd):
+    """Per-coordinate relative errors |g - fd| / max(|fd|, 1e-2 rms(fd))."""
+    g, fd = np.asarray(g, np.float64), np.asarray(fd, np.float64)
+    floor = 1e-2 * np.sqrt(np.mean(fd ** 2))
+    return np.abs(g - fd) / np.maximum(np.abs(fd), floor)
 
 
 def rel(a, b):
@@ -129,20 +138,22 @@ def test_gradients_match_oracle_and_finite_differences():
     gP_ref, gx_ref = O.nursd_gradients(c["P"], c["xy"], *oracle_args(c), Vt)
     assert rel(gP.cpu().numpy(), gP_ref) < TOL
     assert np.linalg.norm(gx.cpu().numpy() - gx_ref) / np.linalg.norm(gx_ref) < GRAD_TOL
-    # FP64 central differences of the oracle loss on random coordinates
+    # FP64 central differences of the oracle loss on random coordinates, each gated on its own
     r = np.random.default_rng(13)
     args = oracle_args(c)
     gxc = gx.cpu().numpy()
-    scale = np.abs(gx_ref).max()
-    for l in r.choice(len(c["xy"]), 12, replace=False):
+    got, fds = [], []
+    for l in r.choice(len(c["xy"]), 24, replace=False):
         a = int(r.integers(0, 2))
         h = 1e-6
         xp = c["xy"].astype(np.float64).copy()
         xm = xp.copy()
         xp[l, a] += h
         xm[l, a] -= h
-        fd = (O.nursd_loss(c["P"], xp, *args, Vt) - O.nursd_loss(c["P"], xm, *args, Vt)) / (2 * h)
-        assert abs(gxc[l, a] - fd) < GRAD_TOL * scale, (l, a, gxc[l, a], fd)
+        fds.append((O.nursd_loss(c["P"], xp, *args, Vt) - O.nursd_loss(c["P"], xm, *args, Vt)) / (2 * h))
+        got.append(gxc[l, a])
+    err = fd_gate(got, fds)
+    assert err.max() < FD_REL, (err.max(), np.median(err))
 
 
 def test_autograd_function_matches_oracle():
@@ -179,6 +190,39 @@ def test_gradient_operator_at_the_65k_sample_grid128_size():
     gP_ref, gx_ref = O.gradients_from_w(R, P[idx], th, pitch)
     assert rel(gP.cpu().numpy()[idx], gP_ref) < TOL
     assert np.linalg.norm(gx.cpu().numpy()[idx] - gx_ref) / np.linalg.norm(gx_ref) < GRAD_TOL
+
+
+def test_position_gradient_against_fp64_differences_at_the_65k_gradient_workload():
+    # The gradient workload: 65,536 keystone samples x_true, relay positions x = x_true + N(0, 2 mm),
+    # phasors of the simulated scene, target V_t = A(P, x_true), 128^2 x 64 voxels, F = 128.  The
+    # residual r = A(P, x) - V_t of the GPU forward is promoted to FP64 and shared by both sides:
+    # the GPU gradient from w = 2 r, and for 64 random coordinates the exact FP64 change of the loss
+    # when that one sample moves by +-1 um (its single-sample forward term, contracted and cropped).
+    from workloads import workload_c5
+    wl = workload_c5()
+    g = wl.geom
+    om, wt = nursd.phasor_frequencies(g.lambda_c, g.dt, g.t_pad, g.F)
+    rng = np.random.default_rng(BASE_SEED + 64)
+    half = g.N * g.pitch / 2
+    x_true = wl.xy
+    x_rel = np.clip(x_true + rng.normal(0.0, 2e-3, x_true.shape), -0.9999 * half, 0.9999 * half).astype(np.float32)
+    plan = nursd.Plan(g.N, g.pitch, g.center, g.depths, om, wt, T=g.T, t0=g.t0, dt=g.dt, max_points=len(x_true),
+                      adjoint=True)
+    P = plan.temporal_dft(torch.from_numpy(wl.hist).cuda())
+    plan.set_points(torch.from_numpy(x_true).cuda())
+    Vt = plan.forward_phasor(P).clone()
+    plan.set_points(torch.from_numpy(x_rel).cuda())
+    resid = plan.forward_phasor(P) - Vt
+    _, gx = plan.grad_points(2 * resid, P, want_phasor=False)
+    assert plan.sync_status() == 0
+    rows = rng.choice(len(x_rel), 64, replace=False)
+    axes = rng.integers(0, 2, 64)
+    P_rows = P.cpu().numpy()[rows].astype(np.complex128)
+    fd = O.position_loss_differences(resid.cpu().numpy().astype(np.complex128), P_rows,
+                                     x_rel[rows].astype(np.float64), axes, 1e-6, g.center, g.pitch, g.N, g.depths,
+                                     om)
+    err = fd_gate(gx.cpu().numpy()[rows, axes], fd)
+    assert err.max() < FD_REL, (err.max(), np.median(err))
 
 
 # ------------------------------------------------------------------ a8 ---
