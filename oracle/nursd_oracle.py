@@ -37,10 +37,11 @@ __all__ = [
     "transfer_functions", "propagate", "propagate_depth", "nursd_forward", "fbp_direct",
     "propagate_points", "idft_grid", "scaled_dft_matrix", "srsd_from_grid", "srsd_forward",
     "adjoint_spectrum", "nursd_adjoint", "nursd_loss", "nursd_gradients",
-    "adjoint_spectrum_depthwise", "nudft_type1_lattice", "gradients_from_w", "position_loss_differences", "frustum_volume", "frustum_extra_volume", "data_compression", "lateral_resolution",
+    "adjoint_spectrum_depthwise", "nudft_type1_lattice", "gradients_from_w", "position_loss_differences",
+    "downsampling_bound", "subsample_grid", "upsample_nearest", "upsample_linear", "frustum_volume", "frustum_extra_volume", "data_compression", "lateral_resolution",
     "voxel_lattice", "propagate_per_frequency", "illumination_mask", "propagate_illuminated", "transient_frames",
     "nursd_forward_illuminated", "nursd_transient_frames", "fbp_direct_per_frequency",
-    "srsd_spectra", "srsd_points",
+    "srsd_spectra", "srsd_points", "nu_sfft_spectra", "nu_sfft_forward",
 ]
 
 
@@ -439,6 +440,35 @@ def srsd_points(P, xy, center, pitch: float, N: int, depths, scales, omega, vox_
     return out
 
 
+def nu_sfft_spectra(P, xy, center, pitch: float, N: int, depths, scales, omega) -> np.ndarray:
+    """Scaled spectra of the non-uniform-input SRSD (NU-SFFT, Supp. C, SRSD on non-uniform acquisition).
+
+    The scaled DFT taken directly at the relay samples instead of a gridded input:
+    Phat_{z,f}(kappa) = sum_l P[l, f] exp(-i kappa . theta_l / s_z), kappa in I_M^2, theta_l the
+    rescaled positions of Sec. 6; then Y_z = sum_f Phat_{z,f} . Ghat^(s_z)_{z,f} as in SRSD.
+    P [L][F] -> [Z][M][M], M = 2N.
+    """
+    M = 2 * N
+    theta = relay_theta(xy, center, pitch, M)
+    out = np.empty((len(depths), M, M), dtype=np.complex128)
+    for iz, (z, s) in enumerate(zip(np.asarray(depths, float), np.asarray(scales, float))):
+        Ph = nudft_type1(P, theta / s, M)
+        Y = np.zeros((M, M), dtype=np.complex128)
+        for f, w in enumerate(np.asarray(omega, dtype=np.float64)):
+            Y += Ph[f] * transfer_function(rsd_kernel(M, s * pitch, z, w / C))
+        out[iz] = Y
+    return out
+
+
+def nu_sfft_forward(P, xy, center, pitch: float, N: int, depths, scales, omega) -> np.ndarray:
+    """NU-SFFT reconstruction: :func:`nu_sfft_spectra`, then V_z = M^-2 IDFT crop to I_N^2 (plane z on the
+    lattice c + s_z delta I_N^2, like SRSD).  -> [Z][N][N]."""
+    M = 2 * N
+    Y = nu_sfft_spectra(P, xy, center, pitch, N, depths, scales, omega)
+    B = _idft_crop_matrix(M, N)
+    return np.stack([B @ Y[iz] @ B.T for iz in range(Y.shape[0])]) / (M * M)
+
+
 # --------------------------------------------------- a10-a11: adjoint, grad ---
 
 def adjoint_spectrum(V: np.ndarray, Ghat: np.ndarray) -> np.ndarray:
@@ -586,6 +616,50 @@ def position_loss_differences(residual, P_rows, xy_rows, axes, h: float, center,
         Rt = np.conj(B).T @ r[iz] @ np.conj(B)  # [ky][kx]
         acc += 2.0 * np.real(np.einsum("yx,syx->s", np.conj(Rt), dE * H)) / (M * M)
     return acc / (2.0 * h)
+
+
+# --------------------------- subsampled acquisition (Methods: Sampling Criteria) ---
+
+def downsampling_bound(dx, dz):
+    """Largest lateral downsampling factor of Eq. upsample2: lambda_sx / lambda_sz = 2 |z_r - z_0| / |x_r - x_0|.
+
+    A point source at lateral offset dx and depth offset dz from a relay point may be sampled D times
+    more coarsely along the relay than the Nyquist pitch of the depth axis when D is below this ratio.
+    """
+    return 2.0 * abs(dz) / abs(dx)
+
+
+def subsample_grid(P, D: int) -> np.ndarray:
+    """Keep every D-th relay sample per axis (the compression step): [N][N][F] -> [Nc][Nc][F], Nc = ceil(N / D),
+    kept sample (i, j) being grid sample (D i, D j)."""
+    return np.asarray(P)[::D, ::D]
+
+
+def upsample_nearest(Pc, N: int, D: int) -> np.ndarray:
+    """Nearest-neighbour interpolation back to the N x N grid (step 2 of the compression algorithm).
+
+    Grid sample n takes the kept sample nearest to it, at D i with i = round(n / D); a sample halfway
+    between two kept ones takes the lower, and samples past the last kept one take the last.
+    [Nc][Nc][F] -> [N][N][F].
+    """
+    Pc = np.asarray(Pc)
+    nc = Pc.shape[0]
+    n = np.arange(N)
+    i = np.minimum(np.ceil(n / D - 0.5).astype(int), nc - 1)
+    return Pc[i][:, i]
+
+
+def upsample_linear(Pc, N: int, D: int) -> np.ndarray:
+    """Separable linear interpolation back to the N x N grid between the kept samples D i and D (i + 1);
+    past the last kept sample the value is held.  [Nc][Nc][F] -> [N][N][F] (complex128)."""
+    Pc = np.asarray(Pc, dtype=np.complex128)
+    nc = Pc.shape[0]
+    n = np.arange(N, dtype=np.float64)
+    i0 = np.minimum(np.floor(n / D).astype(int), nc - 1)
+    i1 = np.minimum(i0 + 1, nc - 1)
+    t = np.where(i1 > i0, n / D - i0, 0.0)
+    rows = (1.0 - t)[:, None, None] * Pc[i0] + t[:, None, None] * Pc[i1]  # along y (first axis)
+    return (1.0 - t)[None, :, None] * rows[:, i0] + t[None, :, None] * rows[:, i1]
 
 
 # ------------------------------------------------ plan-level closed forms ---

@@ -661,3 +661,111 @@ def test_single_sample_loss_differences_equal_brute_force_central_differences():
     # and the analytic gradient, which the differences must approach as h -> 0
     _, gx = O.nursd_gradients(c["P"], xy, *args, Vt)
     assert np.max(np.abs(got - gx[rows, axes])) < 1e-5 * np.max(np.abs(want))
+
+
+# ------------------------------- subsampled acquisition (Methods: Sampling Criteria) ----
+
+def test_nearest_upsampling_by_brute_force():
+    r = np.random.default_rng(21)
+    for N, D in ((7, 2), (9, 3), (10, 4), (5, 1)):
+        P = r.standard_normal((N, N, 2)) + 1j * r.standard_normal((N, N, 2))
+        Pc = O.subsample_grid(P, D)
+        got = O.upsample_nearest(Pc, N, D)
+        kept = np.arange(0, N, D)
+        for y in range(N):
+            for x in range(N):
+                iy = int(np.argmin(np.abs(kept - y)))  # first minimum: the lower of two equidistant samples
+                ix = int(np.argmin(np.abs(kept - x)))
+                assert np.array_equal(got[y, x], P[kept[iy], kept[ix]])
+
+
+def test_linear_upsampling_equals_scipy_and_holds_past_the_last_sample():
+    from scipy.interpolate import RegularGridInterpolator
+
+    r = np.random.default_rng(22)
+    N, D = 13, 4  # kept samples 0, 4, 8, 12: the grid ends on a kept sample
+    P = r.standard_normal((N, N, 3)) + 1j * r.standard_normal((N, N, 3))
+    Pc = O.subsample_grid(P, D)
+    got = O.upsample_linear(Pc, N, D)
+    kept = np.arange(0, N, D).astype(float)
+    yy, xx = np.meshgrid(np.arange(N, dtype=float), np.arange(N, dtype=float), indexing="ij")
+    pts = np.stack([yy.ravel(), xx.ravel()], axis=1)
+    for f in range(3):
+        want = (RegularGridInterpolator((kept, kept), Pc[..., f].real)(pts)
+                + 1j * RegularGridInterpolator((kept, kept), Pc[..., f].imag)(pts)).reshape(N, N)
+        assert np.max(np.abs(got[..., f] - want)) < 1e-13
+    # N = 11, D = 4: samples 9 and 10 lie past the last kept sample (8) and hold its value
+    P2 = P[:11, :11]
+    got2 = O.upsample_linear(O.subsample_grid(P2, 4), 11, 4)
+    assert np.array_equal(got2[9:, 9:], np.broadcast_to(P2[8, 8], got2[9:, 9:].shape))
+    # affine data is reproduced exactly wherever it is interpolated, and D = 1 is the identity
+    lin = (2.0 + 0.5 * yy - 1.5j * xx)[..., None]
+    assert np.max(np.abs(O.upsample_linear(O.subsample_grid(lin, D), N, D) - lin)) < 1e-12
+    assert np.array_equal(O.upsample_linear(P, N, 1), P) and np.array_equal(O.upsample_nearest(P, N, 1), P)
+
+
+def test_subsampled_point_source_still_focuses_within_the_bound_of_eq_upsample2():
+    # analytic phasors P = e^{-i k d} / d of a point source 1.2 m from a 32 x 32 relay lattice at
+    # 1.5 cm pitch (half-width 0.24 m): Eq. upsample2 allows D < 2 * 1.2 / 0.24 = 10 over the whole
+    # aperture.  Keeping every 2nd or 4th sample, nearest-neighbour or linear re-gridding, the
+    # reconstruction still peaks within one voxel of the source and keeps most of its focus.
+    N, pitch, z0 = 32, 0.015, 1.2
+    assert O.downsampling_bound(N * pitch / 2, z0) > 9.9
+    lat = relay_lattice(N, pitch, (0.0, 0.0), dtype=np.float64)
+    om = 2 * math.pi * np.array([4.6e9, 5.0e9, 5.4e9])
+    xs = np.array([0.0, 0.0, z0])
+    d = np.sqrt(np.sum((lat - xs[None, :2]) ** 2, axis=1) + z0 * z0)
+    P = np.exp(-1j * np.outer(d, om) / O.C) / d[:, None]  # [L][F], lattice order: row y, column x
+    grid = P.reshape(N, N, -1)
+    depths = np.array([1.0, 1.2, 1.4])
+    full = np.abs(O.nursd_forward(P, lat, (0.0, 0.0), pitch, N, depths, om))
+    peak = full.max()
+    for D in (2, 4):
+        for up in (O.upsample_nearest, O.upsample_linear):
+            Pg = up(O.subsample_grid(grid, D), N, D).reshape(N * N, -1)
+            V = np.abs(O.nursd_forward(Pg, lat, (0.0, 0.0), pitch, N, depths, om))
+            iz, iy, ix = np.unravel_index(np.argmax(V), V.shape)
+            # nearest-neighbour re-gridding displaces the field by up to half a kept interval, so the
+            # peak may move by one voxel; it stays at the source's depth
+            assert iz == 1 and abs(iy - N // 2) <= 1 and abs(ix - N // 2) <= 1, (D, up.__name__, (iz, iy, ix))
+            assert V.max() > 0.5 * peak, (D, up.__name__, V.max() / peak)
+
+
+# ------------------------------------------ NU-SFFT (SRSD on non-uniform acquisition) ----
+
+def test_nu_sfft_brute_force_tiny():
+    r = np.random.default_rng(31)
+    N, L, F, pitch, center = 4, 3, 2, 0.05, (0.01, -0.02)
+    M = 2 * N
+    xy = center + r.uniform(-0.09, 0.09, (L, 2))
+    P = r.standard_normal((L, F)) + 1j * r.standard_normal((L, F))
+    depths, scales, om = np.array([0.4, 0.7]), np.array([1.3, 2.2]), 2 * math.pi * np.array([4e9, 5e9])
+    Y = O.nu_sfft_spectra(P, xy, center, pitch, N, depths, scales, om)
+    for iz in range(2):
+        s = scales[iz]
+        for iy, ky in enumerate(range(-M // 2, M // 2)):
+            for ix, kx in enumerate(range(-M // 2, M // 2)):
+                acc = 0j
+                for f in range(F):
+                    ph = sum(P[l, f] * cmath.exp(-1j * (kx * 2 * math.pi * (xy[l, 0] - center[0]) / (M * pitch)
+                                                         + ky * 2 * math.pi * (xy[l, 1] - center[1]) / (M * pitch)) / s)
+                             for l in range(L))
+                    g = O.transfer_function(O.rsd_kernel(M, s * pitch, depths[iz], om[f] / O.C))[iy, ix]
+                    acc += ph * g
+                assert abs(Y[iz, iy, ix] - acc) < 1e-12 * (1 + abs(acc))
+
+
+def test_nu_sfft_on_the_lattice_equals_srsd_and_at_unit_scale_equals_nursd():
+    c = _lattice_case(N=8, L=30, F=3, Z=2, seed=32)
+    args = (c["center"], c["pitch"], c["N"], c["depths"])
+    scales = np.array([1.4, 2.9])
+    # samples on the input lattice: the gridded input of SRSD is exactly the samples
+    got = O.nu_sfft_forward(c["P"], c["xy"], *args, scales, c["omega"])
+    assert rel(got, O.srsd_forward(c["P"], c["xy"], *args, scales, c["omega"])) < 1e-12
+    # off the lattice at unit scale: the scaled DFT at integer modes is NURSD-1's type-1 sum
+    xy = c["xy"] + np.random.default_rng(33).uniform(-0.5, 0.5, c["xy"].shape) * c["pitch"]
+    got1 = O.nu_sfft_forward(c["P"], xy, *args, np.ones(2), c["omega"])
+    assert rel(got1, O.nursd_forward(c["P"], xy, *args, c["omega"])) < 1e-12
+    # and off the lattice at s > 1 it differs from SRSD's gridded input (the reason to fuse)
+    assert rel(O.nu_sfft_forward(c["P"], xy, *args, scales, c["omega"]),
+               O.srsd_forward(c["P"], xy, *args, scales, c["omega"])) > 1e-3
