@@ -7,4 +7,4 @@ does, and fails loudly if it has not been built.
 """
 from .build import build  # noqa: F401
 from .nursd import (EXPORTS, LIB_PATH, NursdError, Plan, load_library,  # noqa: F401
-                    phasor_frequencies, status_string)
+                    phasor_frequencies, status_string, subsample, upsample)

@@ -270,11 +270,19 @@ cudaError_t launch_gtf_compress_depthmajor(const float2* Gfull, const int2* cls_
                                            int z0, float2* Gs, cudaStream_t s);
 // ------------------------------------------------- SRSD by interpolation (srsd_interp.cu)
 // Yh [L][L][F] at index m + L/2 (periodic in m).
-// Both taps and the contraction in one pass (scales >= 1, 4 <= w <= 8); with F > 64 it adds into Y,
-// which must then be zero on entry:
-// Y[k][z] = sum_f Gs_z[class(k)][f] sum_ty wt[ky][ty] sum_tx wt[kx][tx] Yh[m0[ky] + ty][m0[kx] + tx][f].
-cudaError_t launch_srsd_interp_xy_contract(const float2* Yh, int L, int M, int F, int Z, int z, int w, const int* m0,
-                                           const float* wt, const float2* Gs_z, float2* Y, cudaStream_t s);
+// Both taps and the contraction in one pass for every depth z in zlist[0 .. nz) (device list; 4 <= w <= 8;
+// the tap table of each depth must advance by at most two cells per mode index):
+// Y[k][z] = sum_f Gs[z][class(k)][f] sum_ty wt[z][ky][ty] sum_tx wt[z][kx][tx] Yh[m0[z][ky] + ty][m0[z][kx] + tx][f].
+// When srsd_interp_adds(F) the channels of a mode are summed into Y, whose listed depths must then be
+// zero on entry.
+bool srsd_interp_adds(int F);
+cudaError_t launch_srsd_interp_xy_contract(const float2* Yh, int L, int M, int F, int Z, const int* zlist, int nz,
+                                           int w, const int* m0, const float* wt, const float2* Gs, int ncls,
+                                           float2* Y, cudaStream_t s);
+// ------------------------------------------------ subsampled acquisition (resample.cu)
+// kept [Nc][Nc][F] = full[::D, ::D]; full [N][N][F] from kept by nearest (linear = 0) or linear interpolation.
+cudaError_t launch_subsample(const float2* full, float2* kept, int N, int F, int D, cudaStream_t s);
+cudaError_t launch_upsample(const float2* kept, float2* full, int N, int F, int D, int linear, cudaStream_t s);
 // ---------------------------------------------------------- per-frequency forms (illum.cu)
 // Y[k][zz*F + f] = U[k][f] * Gc[class(k)][f][z0 + zz] for zz < zg (no sum over f), U and Y
 // mode-major [M][M][...] with mode (kx, ky) at (ky + M/2) M + (kx + M/2).

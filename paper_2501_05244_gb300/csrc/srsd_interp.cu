@@ -24,19 +24,37 @@ __device__ __forceinline__ int wrap_mod(int m, int L) {
 constexpr int kMaxFPerLane = 8;
 constexpr int kYRun = 16;
 
-// The three steps of one depth in one pass, without the x-tapped rows in memory:
+// d = a * (b.x, b.y) + c as one packed fma.rn.f32x2 (the same scalar on both halves).
+__device__ __forceinline__ float2 fma2s(float a, float2 b, float2 c) {
+  float2 r;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %2};\n mov.b64 rb, {%3, %4};\n mov.b64 rc, {%5, %6};\n"
+      " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return r;
+}
+// The three steps of one depth in one pass, without the x-tapped rows in memory (every listed depth
+// in one launch, blockIdx.y selecting it):
 // Y[k][z] = sum_f Gs_z[class(k)][f] sum_ty wt[ky][ty] X[m0[ky] + ty][kx][f] with
 // X[m][kx][f] = sum_tx wt[kx][tx] Yh[m][m0[kx] + tx][f].  One warp per column kx and run of kYRun
 // consecutive ky, lanes over f (F <= 32 FPL).  The warp keeps X of the W rows its current ky needs
-// in registers; the next ky starts at most two rows further (the coordinate 2 ky / s advances by
-// 2 / s <= 2 for scales >= 1), so at most two new rows are x-tapped per step.
+// in registers; the next ky starts at most two rows further (the tap tables must advance by at
+// most two cells per mode: the coordinate 2 ky / s of SRSD advances by 2 / s <= 2 for scales >= 1),
+// so at most two new rows are x-tapped per step.  Tap and contraction MACs are packed
+// fma.rn.f32x2 on (re, im) pairs.
 // FS = 2: the channels of a mode are split over two warps (channel block fs), each adding its part
 // of the f sum to Y with an atomic add; Y starts at zero, and a sum of two terms onto zero does not
 // depend on their order, so the result is reproducible.
 template <int FPL, int W, int FS>
-__global__ void srsd_interp_xy_contract_kernel(const float2* __restrict__ Yh, int L, int M, int F, int Z, int z,
-                                               const int* __restrict__ m0, const float* __restrict__ wt,
-                                               const float2* __restrict__ Gs_z, float2* __restrict__ Y) {
+__global__ void srsd_interp_xy_contract_kernel(const float2* __restrict__ Yh, int L, int M, int F, int Z,
+                                               const int* __restrict__ zlist, const int* __restrict__ m0_all,
+                                               const float* __restrict__ wt_all, const float2* __restrict__ Gs,
+                                               int ncls, float2* __restrict__ Y) {
+  // blockIdx.y: the depth (an entry of zlist), its taps [M] / [M][W] and table [ncls][F]
+  const int z = __ldg(zlist + blockIdx.y);
+  const int* __restrict__ m0 = m0_all + (size_t)z * M;
+  const float* __restrict__ wt = wt_all + (size_t)z * M * W;
+  const float2* __restrict__ Gs_z = Gs + (size_t)z * ncls * F;
   const int gw = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
   const int nrun = (M + kYRun - 1) / kYRun;
   if (gw >= M * nrun * FS) return;
@@ -59,11 +77,7 @@ __global__ void srsd_interp_xy_contract_kernel(const float2* __restrict__ Yh, in
 #pragma unroll
       for (int j = 0; j < FPL; ++j) {
         const int f = fbase + lane + 32 * j;
-        if (f < F) {
-          const float2 v = __ldg(cell + f);
-          out[j].x = fmaf(cx[t], v.x, out[j].x);
-          out[j].y = fmaf(cx[t], v.y, out[j].y);
-        }
+        if (f < F) out[j] = fma2s(cx[t], __ldg(cell + f), out[j]);
       }
     }
   };
@@ -93,14 +107,10 @@ __global__ void srsd_interp_xy_contract_kernel(const float2* __restrict__ Yh, in
       const int f = fbase + lane + 32 * j;
       float2 ph = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int t = 0; t < W; ++t) {
-        ph.x = fmaf(cy[t], xr[t][j].x, ph.x);
-        ph.y = fmaf(cy[t], xr[t][j].y, ph.y);
-      }
-      if (f < F) {
+      for (int t = 0; t < W; ++t) ph = fma2s(cy[t], xr[t][j], ph);
+      if (f < F) {  // acc += ph * g: (ph.x, ph.x) (gx, gy) + (ph.y, ph.y) (-gy, gx)
         const float2 gv = __ldg(g + f);
-        acc.x = fmaf(ph.x, gv.x, fmaf(-ph.y, gv.y, acc.x));
-        acc.y = fmaf(ph.x, gv.y, fmaf(ph.y, gv.x, acc.y));
+        acc = fma2s(ph.y, make_float2(-gv.y, gv.x), fma2s(ph.x, gv, acc));
       }
     }
 #pragma unroll
@@ -121,12 +131,13 @@ __global__ void srsd_interp_xy_contract_kernel(const float2* __restrict__ Yh, in
 }
 
 template <int FPL, int FS>
-cudaError_t xy_width(const float2* Yh, int L, int M, int F, int Z, int z, int w, const int* m0, const float* wt,
-                     const float2* Gs_z, float2* Y, unsigned blocks, cudaStream_t s) {
+cudaError_t xy_width(const float2* Yh, int L, int M, int F, int Z, const int* zlist, int nz, int w, const int* m0,
+                     const float* wt, const float2* Gs, int ncls, float2* Y, unsigned blocks, cudaStream_t s) {
+  const dim3 grid(blocks, (unsigned)nz);
   switch (w) {
-#define NURSD_XY(W_)                                                                                            \
-  case W_:                                                                                                    \
-    srsd_interp_xy_contract_kernel<FPL, W_, FS><<<blocks, 64, 0, s>>>(Yh, L, M, F, Z, z, m0, wt, Gs_z, Y);   \
+#define NURSD_XY(W_)                                                                                          \
+  case W_:                                                                                                  \
+    srsd_interp_xy_contract_kernel<FPL, W_, FS><<<grid, 64, 0, s>>>(Yh, L, M, F, Z, zlist, m0, wt, Gs, ncls, Y); \
     return cudaGetLastError();
     NURSD_XY(4) NURSD_XY(5) NURSD_XY(6) NURSD_XY(7) NURSD_XY(8)
 #undef NURSD_XY
@@ -137,18 +148,22 @@ cudaError_t xy_width(const float2* Yh, int L, int M, int F, int Z, int z, int w,
 
 }  // namespace
 
-cudaError_t launch_srsd_interp_xy_contract(const float2* Yh, int L, int M, int F, int Z, int z, int w, const int* m0,
-                                           const float* wt, const float2* Gs_z, float2* Y, cudaStream_t s) {
-  if (L < 2 || M < 2 || F < 1 || F > 32 * kMaxFPerLane || z < 0 || z >= Z) return cudaErrorInvalidValue;
+bool srsd_interp_adds(int F) { return F > 64; }
+
+cudaError_t launch_srsd_interp_xy_contract(const float2* Yh, int L, int M, int F, int Z, const int* zlist, int nz,
+                                           int w, const int* m0, const float* wt, const float2* Gs, int ncls,
+                                           float2* Y, cudaStream_t s) {
+  if (nz <= 0) return cudaSuccess;
+  if (L < 2 || M < 2 || F < 1 || F > 32 * kMaxFPerLane || nz > 65535 || !zlist) return cudaErrorInvalidValue;
   // above 64 channels a mode's channels are split over two warps (FS = 2: Y must be zero on entry)
-  const int FS = F > 64 ? 2 : 1;
+  const int FS = srsd_interp_adds(F) ? 2 : 1;
   const long long threads_total = (long long)M * ((M + kYRun - 1) / kYRun) * 32 * FS;
   // two warps per block: more resident warps at the registers of the register-held window
   const unsigned blocks = (unsigned)((threads_total + 63) / 64);
-  if (F <= 32) return xy_width<1, 1>(Yh, L, M, F, Z, z, w, m0, wt, Gs_z, Y, blocks, s);
-  if (F <= 64) return xy_width<2, 1>(Yh, L, M, F, Z, z, w, m0, wt, Gs_z, Y, blocks, s);
-  if (F <= 128) return xy_width<2, 2>(Yh, L, M, F, Z, z, w, m0, wt, Gs_z, Y, blocks, s);
-  return xy_width<4, 2>(Yh, L, M, F, Z, z, w, m0, wt, Gs_z, Y, blocks, s);
+  if (F <= 32) return xy_width<1, 1>(Yh, L, M, F, Z, zlist, nz, w, m0, wt, Gs, ncls, Y, blocks, s);
+  if (F <= 64) return xy_width<2, 1>(Yh, L, M, F, Z, zlist, nz, w, m0, wt, Gs, ncls, Y, blocks, s);
+  if (F <= 128) return xy_width<2, 2>(Yh, L, M, F, Z, zlist, nz, w, m0, wt, Gs, ncls, Y, blocks, s);
+  return xy_width<4, 2>(Yh, L, M, F, Z, zlist, nz, w, m0, wt, Gs, ncls, Y, blocks, s);
 }
 
 }  // namespace nursd

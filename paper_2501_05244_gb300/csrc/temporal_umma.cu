@@ -54,18 +54,23 @@ struct UShape {
   static constexpr int kB = N2 * 64;   // one B tile: N2 rows x 32 fp16
   static constexpr int kStage = 2 * kA + 2 * kB;
   static constexpr int kAcc = N2 < 32 ? 32 : N2;  // tensor-memory columns per accumulator
-  static constexpr size_t kSmem = 1024 + (size_t)kUStages * kStage + 3072;
+  // the stages, 1 KB of alignment slack and the control block: for N2 = 256 this stays within the
+  // 196 KB shared-memory carveout (a larger carveout leaves too little L1 for the histogram loads)
+  static constexpr size_t kSmem = 1024 + (size_t)kUStages * kStage + 1536;
 };
 
-struct Ctl {  // control block after the stages (at most the 3072 bytes the shape reserves)
+struct Ctl {  // control block after the stages (at most the 1536 bytes the shape reserves)
   unsigned long long full_a[kUStages], full_b[kUStages], empty[kUStages];
   unsigned long long acc_full[2], acc_empty[2], drain;
   unsigned tmem;
   int abort;
   int lo[kUStages][kCvtWarps];
-  float rmax[2][kCvtWarps * 32];  // running max |h| of each producer thread's two rows (first launch)
+  // running max |h| of each producer thread's two rows (first launch): the upper 16 bits of the
+  // FP32 magnitude rounded up, row q in bits 16 q .. 16 q + 15
+  uint32_t rmax[kCvtWarps * 32];
+  int listed;  // gather launch: rows listed by the first launch
 };
-static_assert(sizeof(Ctl) <= 3072, "control block exceeds the shared memory reserved for it");
+static_assert(sizeof(Ctl) <= 1536, "control block exceeds the shared memory reserved for it");
 
 __device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -174,18 +179,18 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
                                                                      const float* __restrict__ wcol,
                                                                      const TemporalFix fix) {
   using S = UShape<N2>;
-  __shared__ int listed;
-  if (GATHER) {
-    if (threadIdx.x == 0) listed = temporal_fix_take(fix);
-    __syncthreads();
-  }
-  const int nrows = GATHER ? min(listed, fix.cap) : L;
-  const int ntiles = (nrows + kBM - 1) / kBM, nkb = T / kBK;
-  if (GATHER && (int)blockIdx.x >= ntiles) return;  // the whole CTA: nothing listed for it
   extern __shared__ unsigned char raw[];
   const uint32_t raw_addr = sa(raw);
   unsigned char* base = raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
   Ctl& ctl = *reinterpret_cast<Ctl*>(base + kUStages * S::kStage);
+  if (GATHER) {
+    if (threadIdx.x == 0) ctl.listed = temporal_fix_take(fix);
+    __syncthreads();
+  }
+  const int nrows = GATHER ? min(ctl.listed, fix.cap) : L;
+  const int ntiles = (nrows + kBM - 1) / kBM, nkb = T / kBK;
+  const int kb_shift = (nkb & (nkb - 1)) == 0 ? __ffs(nkb) - 1 : -1;  // K-blocks per tile a power of two
+  if (GATHER && (int)blockIdx.x >= ntiles) return;  // the whole CTA: nothing listed for it
   volatile int* abort = &ctl.abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -270,15 +275,14 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
     const int cw = warp - kEpiWarps, ct = cw * 32 + lane;
     // task q < 2 of a K-block: row ct / 4 + 64 q of the tile, 16-byte chunk ct % 4 (8 consecutive K values)
     const int r0 = ct >> 2, ch = ct & 3;
-    float* rmax0 = ctl.rmax[0] + ct;  // running max |h| of this thread's two rows over the tile's K-blocks
-    float* rmax1 = ctl.rmax[1] + ct;
+    uint32_t* rmax = ctl.rmax + ct;  // this thread's two rows' running max over the tile's K-blocks
     // a register set holds K-blocks 2 p and 2 p + 1 (4 float4 each)
     auto load = [&](float4 (&v)[8], int pr) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int it = 2 * pr + h;
         if (it >= my_iters) return;
-        const int j = it / nkb, kb = it - j * nkb;
+        const int j = kb_shift >= 0 ? it >> kb_shift : it / nkb, kb = it - j * nkb;
         const int m0 = ((int)blockIdx.x + j * (int)gridDim.x) * kBM;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
@@ -292,12 +296,12 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
     };
     auto stage_one = [&](const float4* v, int it) -> bool {
       const int st = it % kUStages, ph = (it / kUStages) & 1;
-      const int j = it / nkb, kb = it - j * nkb;
+      const int j = kb_shift >= 0 ? it >> kb_shift : it / nkb, kb = it - j * nkb;
       const int m0 = ((int)blockIdx.x + j * (int)gridDim.x) * kBM;
       if (!__all_sync(0xffffffffu, bar_wait(&ctl.empty[st], ph ^ 1, abort))) return false;
       unsigned char* ah = a_hi(st);
       unsigned char* al = a_lo(st);
-      uint32_t any = 0;
+      uint32_t any = 0, mcode = 0;
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const int r = r0 + 64 * q;
@@ -310,8 +314,7 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
         } else {
           const float m = fmaxf(fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))),
                                 fmaxf(fmaxf(fabsf(y.x), fabsf(y.y)), fmaxf(fabsf(y.z), fabsf(y.w))));
-          float* rm = q ? rmax1 : rmax0;
-          *rm = kb == 0 ? m : fmaxf(*rm, m);
+          mcode |= ((__float_as_uint(m) + 0xffffu) >> 16) << (16 * q);  // rounded up: zero only for 0
         }
         uint4 h, l;
         split2(x.x, x.y, h.x, l.x);
@@ -330,18 +333,22 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
         ctl.lo[st][cw] = warp_any;
         bar_arrive(&ctl.full_a[st]);
       }
-      if (!GATHER && kb == nkb - 1) {  // the tile's rows are complete: the 4 lanes of a row agree on its max
+      if (!GATHER) {
+        const uint32_t rm = kb == 0 ? mcode : __vmaxu2(*rmax, mcode);
+        *rmax = rm;
+        if (kb == nkb - 1) {  // the tile's rows are complete: the 4 lanes of a row agree on its max
+          uint32_t m = rm;
+          m = __vmaxu2(m, __shfl_xor_sync(0xffffffffu, m, 1));
+          m = __vmaxu2(m, __shfl_xor_sync(0xffffffffu, m, 2));
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          float m = q ? *rmax1 : *rmax0;
-          m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
-          m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
-          const int row = m0 + r0 + 64 * q;
-          if (ch == 0 && row < L) {
-            const int e = temporal_row_exponent(m);
-            if (e != kRowInRange) {
-              const int slot = atomicAdd(fix.count, 1);
-              if (slot < fix.cap) fix.list[slot] = make_int4(row, e, 0, 0);
+          for (int q = 0; q < 2; ++q) {
+            const int row = m0 + r0 + 64 * q;
+            if (ch == 0 && row < L) {
+              const int e = temporal_row_exponent(__uint_as_float(((m >> (16 * q)) & 0xffffu) << 16));
+              if (e != kRowInRange) {
+                const int slot = atomicAdd(fix.count, 1);
+                if (slot < fix.cap) fix.list[slot] = make_int4(row, e, 0, 0);
+              }
             }
           }
         }

@@ -148,3 +148,42 @@ def test_srsd_scales_below_and_above_one():
     ref = O.srsd_forward(P, xy, center, pitch, N, depths, scales, om)
     for z in range(Z):
         assert rel(V[z], ref[z]) < TOL, (z, scales[z])
+
+
+@pytest.mark.parametrize("F", [48, 200])
+def test_srsd_channel_counts_beyond_64(F):
+    # channel counts that are not a multiple of the kernel's channel chunk, above 64 and above 128
+    N, L, Z = 16, 300, 4
+    xy, P, om, depths, out_pitch, pitch, center = case(N, L, F, Z, 10 + F)
+    plan = nursd.Plan(N, pitch, center, depths, om, max_points=L, srsd_pitch=out_pitch)
+    plan.set_points(torch.from_numpy(xy).cuda())
+    V = plan.srsd_forward(torch.from_numpy(P).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    ref = O.srsd_forward(P, xy, center, pitch, N, depths, out_pitch / pitch, om)
+    assert rel(V, ref) < TOL
+
+
+@pytest.mark.parametrize("width,tol", [(4, 1e-2), (5, 2e-3), (7, 5e-5), (8, 5e-5)])
+def test_srsd_at_every_kernel_width(width, tol):
+    # both the spatial NUFFT and the scaled DFT's interpolation use the plan's ES width; the error
+    # bounds are those of the type-2 output at the same widths
+    N, L, F, Z = 32, 1200, 8, 5
+    xy, P, om, depths, out_pitch, pitch, center = case(N, L, F, Z, 20 + width)
+    plan = nursd.Plan(N, pitch, center, depths, om, max_points=L, srsd_pitch=out_pitch, kernel_width=width)
+    plan.set_points(torch.from_numpy(xy).cuda())
+    V = plan.srsd_forward(torch.from_numpy(P).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    ref = O.srsd_forward(P, xy, center, pitch, N, depths, out_pitch / pitch, om)
+    assert rel(V, ref) < tol
+
+
+def test_srsd_with_more_depths_than_one_tile_wave():
+    # many depths (thousands of tiles) through the single persistent launch, scales 1 .. 4
+    N, L, F, Z = 64, 2000, 4, 40
+    xy, P, om, depths, out_pitch, pitch, center = case(N, L, F, Z, 30)
+    plan = nursd.Plan(N, pitch, center, depths, om, max_points=L, srsd_pitch=out_pitch)
+    plan.set_points(torch.from_numpy(xy).cuda())
+    V = plan.srsd_forward(torch.from_numpy(P).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    ref = O.srsd_forward(P, xy, center, pitch, N, depths, out_pitch / pitch, om)
+    assert rel(V, ref) < TOL
