@@ -230,10 +230,11 @@ int nursd_adjoint(nursd_plan_t plan, const nursd_c64* d_vol, nursd_c64* d_phasor
  *   d_grad_phasor [L][F] = A^H w                           (conjugate-Wirtinger
  *                                                            gradient w.r.t. P)
  *   d_grad_xy[l] = Re sum_f P[l][f] conj(d (A^H w)[l][f] / d(x_l, y_l))   [L][2]
- * The position derivative differentiates the ES interpolation, i.e. it is the
- * exact derivative of the implemented (NUFFT-approximated) operator.  Either
- * output may be NULL (not both); d_phasor is needed for d_grad_xy.  Needs
- * NURSD_ENABLE_ADJOINT.
+ * The position derivative is the spectral one: d/dx of sum_k R_f(k) e^{ik.theta_l}
+ * is i (2 pi / (M delta)) times the type-2 sum of kx R_f (likewise y), each
+ * evaluated by the same NUFFT type 2 as the value, so it carries the value's
+ * accuracy.  Either output may be NULL (not both); d_phasor is needed for
+ * d_grad_xy.  Needs NURSD_ENABLE_ADJOINT.
  */
 int nursd_grad_points(nursd_plan_t plan, const nursd_c64* d_w, const nursd_c64* d_phasor, nursd_c64* d_grad_phasor,
                       float* d_grad_xy, nursd_stream_t stream);
@@ -242,19 +243,40 @@ int nursd_grad_points(nursd_plan_t plan, const nursd_c64* d_w, const nursd_c64* 
  * Scaled RSD (Sec. 4, Eq. SRSD_conv with the SFFT of Supp. A.1, applied to a
  * non-uniform acquisition as in Supp. C): plane z is reconstructed on the
  * lattice c + delta_o(z) I_N^2 (delta_o from the descriptor's h_srsd_pitch,
- * scale s_z = delta_o(z) / delta >= any positive value).  From the NUFFT-1
+ * scale s_z = delta_o(z) / delta, any positive value).  From the NUFFT-1
  * spectrum U_f the gridded input u_f = M^-2 IDFT_M[U_f] (on I_M^2, pitch delta)
  * is formed, then per depth and frequency the scaled DFT
- *   Phat_{z,f}(kappa) = sum_{n in I_M^2} u_f[n] exp(-2 pi i kappa.n / (M s_z))
- * by Bluestein's chirp-z (separable x then y, convolution length 2M), the
- * frequency sum Y_z = sum_f Phat_{z,f} Ghat^(s_z)_{z,f} with G sampled at pitch
- * s_z delta, and the inverse DFT cropped to I_N^2:
+ *   Phat_{z,f}(kappa) = sum_{n in I_M^2} u_f[n] exp(-2 pi i kappa.n / (M s_z)),
+ * the frequency sum Y_z = sum_f Phat_{z,f} Ghat^(s_z)_{z,f} with G sampled at
+ * pitch s_z delta, and the inverse DFT cropped to I_N^2:
  *   V_z[m] = M^-2 sum_kappa Y_z(kappa) exp(+2 pi i kappa.m / M).
+ * Depths with s_z >= 1 take the scaled DFT as an ES interpolation of one
+ * oversampled 2M x 2M spectrum of u_f / psi_hat shared by all depths (to the
+ * NUFFT kernel's accuracy), all of them in one launch fused with the frequency
+ * sum; depths with s_z < 1 take Bluestein's chirp-z (separable, convolution
+ * length 2M).
  * d_phasor [L][F] -> d_out [Z][N][N] (complex64, or |V| with
  * NURSD_OUTPUT_MAGNITUDE).  Needs h_srsd_pitch at plan creation and
  * nursd_set_points.
  */
 int srsd_forward(nursd_plan_t plan, const nursd_c64* d_phasor, void* d_out, nursd_stream_t stream);
+
+/*
+ * NU-SFFT (Supp. C, SRSD on non-uniform acquisition schemes: the fusion the
+ * paper leaves to future work): the scaled DFT taken at the relay samples
+ * themselves instead of a gridded input,
+ *   Phat_{z,f}(kappa) = sum_l P[l][f] exp(-i kappa . theta_l / s_z),
+ * then the frequency sum with Ghat^(s_z) and the inverse DFT crop as in
+ * srsd_forward (the same output lattices).  Computed as the ES spread of the
+ * samples, one FFT of the whole 2M x 2M grid divided by psi_hat in space, and per
+ * depth ES taps at kappa / s_z divided by psi_hat(kappa / s_z), fused with the
+ * contraction.  On the input lattice it equals srsd_forward; off it, it avoids
+ * the band-limited gridding of u_f.  Every scale must be >= 1
+ * (NURSD_ERR_UNSUPPORTED otherwise).  The first call allocates the NU-SFFT
+ * tables and a [W][2M][F] buffer (W the spread window) and uploads the tables;
+ * make it before any stream capture.  Needs h_srsd_pitch and nursd_set_points.
+ */
+int srsd_forward_nonuniform(nursd_plan_t plan, const nursd_c64* d_phasor, void* d_out, nursd_stream_t stream);
 
 /*
  * SRSD + NURSD-2 (Eq. NURSD2_SRSD): the scaled spectra of srsd_forward
@@ -402,6 +424,29 @@ int nursd_nufft1_noalloc(int32_t N, double pitch, double center_x, double center
  * Returns NURSD_OK, NURSD_ERR_POINT_OUT_OF_RANGE or NURSD_ERR_TIMEOUT.
  */
 int nursd_sync_status(nursd_plan_t plan, nursd_stream_t stream);
+
+/*
+ * Subsampled acquisition (Methods: Sampling Criteria for NLOS, Eq. upsample2): a relay grid may be
+ * sampled D times more coarsely than the lattice when D < 2 |z_r - z_0| / |x_r - x_0| for the
+ * scene's points; the compression keeps every D-th sample per axis and re-grids the kept phasors to
+ * the full grid (nearest neighbour or linear) before a lattice reconstruction.  Plan-free and
+ * allocation-free; stream-ordered.  Arrays are channel-last complex64: the grid
+ * d_full [N][N][F] (row y, column x) and the kept samples d_kept [Nc][Nc][F], Nc = ceil(N / D), kept
+ * sample (i, j) being grid sample (D i, D j).
+ *
+ * nursd_subsample: d_kept = d_full[::D, ::D].
+ * nursd_upsample: d_full from d_kept; mode NURSD_UPSAMPLE_NEAREST: grid index n takes kept index
+ *   min(ceil(n / D - 1/2), Nc - 1) per axis (halfway between two kept samples: the lower);
+ *   NURSD_UPSAMPLE_LINEAR: separable linear interpolation between kept indices floor(n / D) and the
+ *   next, holding the last kept value past it.
+ * INVALID_ARG: N, F or D below 1, D > N, a null or misaligned (8-byte) pointer, an unknown mode.
+ */
+#define NURSD_UPSAMPLE_NEAREST 0
+#define NURSD_UPSAMPLE_LINEAR 1
+int nursd_subsample(int32_t N, int32_t F, int32_t D, const nursd_c64* d_full, nursd_c64* d_kept,
+                    nursd_stream_t stream);
+int nursd_upsample(int32_t N, int32_t F, int32_t D, int32_t mode, const nursd_c64* d_kept, nursd_c64* d_full,
+                   nursd_stream_t stream);
 
 #ifdef __cplusplus
 }

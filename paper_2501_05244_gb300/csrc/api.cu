@@ -88,6 +88,19 @@ struct nursd_plan_s {
   float* si_wt = nullptr;
   std::vector<char> si_interp;
   bool si_any = false;
+  int* si_zlist = nullptr;  // device list of the interpolated depths (one launch covers them all)
+  int si_nz = 0;
+  // NU-SFFT (srsd_forward_nonuniform), built on first use: 1 / psi_hat(g) over the spread window [W],
+  // taps [Z][M] / [Z][M][w] at kappa / s_z on the 2M grid (1 / psi_hat(kappa / s_z) folded into the
+  // weights), the half-transformed window rows [W][2M][F] and the list of every depth
+  float* nu_dec_w = nullptr;
+  int* nu_m0 = nullptr;
+  float* nu_wt = nullptr;
+  float2* nu_rows = nullptr;
+  int* nu_zlist = nullptr;
+  bool nu_ready = false;
+  std::vector<float> nu_host_f;
+  std::vector<int> nu_host_i;
   float2* Gs = nullptr;
   float2* chirp = nullptr;
   float2* bhat = nullptr;
@@ -360,7 +373,17 @@ int build_srsd_chirps(nursd_plan_s* p, cudaStream_t s) {
       }
     }
   }
+  std::vector<int> zl;
+  for (int z = 0; z < Z && p->si_any; ++z)
+    if (p->si_interp[z]) zl.push_back(z);
+  p->si_nz = (int)zl.size();
+  if (!zl.empty() && !p->alloc(p->si_zlist, zl.size())) {
+    cudaFree(db);
+    return NURSD_ERR_OOM;
+  }
   int rc = from_cuda(cudaMemcpyAsync(p->chirp, ch.data(), sizeof(float2) * ch.size(), cudaMemcpyHostToDevice, s));
+  if (rc == NURSD_OK && !zl.empty())
+    rc = from_cuda(cudaMemcpyAsync(p->si_zlist, zl.data(), sizeof(int) * zl.size(), cudaMemcpyHostToDevice, s));
   if (rc == NURSD_OK)
     rc = from_cuda(
         cudaMemcpyAsync(p->srsd_scale_d, p->srsd_scale.data(), sizeof(double) * Z, cudaMemcpyHostToDevice, s));
@@ -499,8 +522,6 @@ int run_srsd_spectra(nursd_plan_s* p, cudaStream_t s) {
       e = axis_pass(p, p->R1, p->fine, logM, true, F, M, F, (long long)M * F, F, (long long)M * F, M, -M / 2, M,
                     -M / 2, nullptr, nullptr, 1.f / ((float)M * (float)M), s);
   }
-  if (e == cudaSuccess && p->si_any)  // the interpolated depths add into Y when F > 64
-    e = cudaMemsetAsync(p->Y, 0, sizeof(float2) * (size_t)M * M * Z, s);
   if (e == cudaSuccess && p->si_any) {  // oversampled spectrum of u / (psi_hat x psi_hat), shared by the
                                         // interpolated depths: FFT_2M along nx, then along ny
     StageTimer t(p, NURSD_STAGE_SRSD, s, 2);
@@ -535,14 +556,15 @@ int run_srsd_spectra(nursd_plan_s* p, cudaStream_t s) {
       e = launch_panel_fft(logL, false, b, s);
     }
   }
+  if (e == cudaSuccess && p->si_any && srsd_interp_adds(F))  // channel halves are added into a zeroed Y
+    e = cudaMemsetAsync(p->Y, 0, sizeof(float2) * (size_t)M * M * Z, s);
+  if (e == cudaSuccess && p->si_any) {  // every depth with scale >= 1: taps and contraction, one launch
+    StageTimer t(p, NURSD_STAGE_SRSD, s, 1);
+    e = launch_srsd_interp_xy_contract(p->si_yh, 2 * M, M, F, Z, p->si_zlist, p->si_nz, p->w, p->si_m0, p->si_wt,
+                                       p->Gs, p->ncls, p->Y, s);
+  }
   for (int z = 0; e == cudaSuccess && z < Z; ++z) {
-    if (p->si_interp[z]) {  // scale >= 1: both taps and the depth's contraction in one pass
-      StageTimer t(p, NURSD_STAGE_SRSD, s, 1);
-      e = launch_srsd_interp_xy_contract(p->si_yh, 2 * M, M, F, Z, z, p->w, p->si_m0 + (size_t)z * M,
-                                         p->si_wt + (size_t)z * M * p->w, p->Gs + (size_t)z * p->ncls * F, p->Y,
-                                         s);
-      continue;
-    }
+    if (p->si_interp[z]) continue;
     StageTimer t(p, NURSD_STAGE_SRSD, s, 3);
     const float2* ch = p->chirp + (size_t)z * M;
     const float2* bh = p->bhat + (size_t)z * 2 * M;
@@ -575,6 +597,106 @@ int run_srsd_spectra(nursd_plan_s* p, cudaStream_t s) {
     }
     if (e == cudaSuccess)
       e = launch_contract_depth(p->U, p->Gs + (size_t)z * p->ncls * F, p->cls, p->ncls, M, F, Z, z, p->Y, s);
+  }
+  return from_cuda(e);
+}
+
+// psi_hat(a) = (w / 2) int_{-1}^{1} phi(z) cos(pi a w z / nf) dz, the transform of the ES kernel spread over
+// w cells of the nf-point fine grid, at a frequency or (for the dual interpolation) a spatial index a.
+double es_transform(double a, int w, double beta, int nf) {
+  static std::vector<double> gx, gw;
+  if (gx.empty()) gauss_legendre(256, gx, gw);
+  double s_ = 0.0;
+  for (size_t j = 0; j < gx.size(); ++j) s_ += gw[j] * es_kernel(gx[j], beta) * std::cos(kPi * a * w * gx[j] / nf);
+  return 0.5 * w * s_;
+}
+
+// Tables and workspace of the NU-SFFT, on first use; every depth must have scale >= 1.
+int ensure_nusfft(nursd_plan_s* p, cudaStream_t s) {
+  if (p->nu_ready) return NURSD_OK;
+  if (!p->Gs || !p->si_yh) return NURSD_ERR_INVALID_ARG;
+  const int M = p->M, Z = p->Z, w = p->w, W = p->W, nf = p->nf;
+  for (int z = 0; z < Z; ++z)
+    if (!(p->srsd_scale[z] >= 1.0)) return NURSD_ERR_UNSUPPORTED;
+  if (!(p->alloc(p->nu_dec_w, W) && p->alloc(p->nu_m0, (size_t)Z * M) && p->alloc(p->nu_wt, (size_t)Z * M * w) &&
+        p->alloc(p->nu_rows, (size_t)W * 2 * M * p->F) && p->alloc(p->nu_zlist, Z)))
+    return NURSD_ERR_OOM;
+  // host copies are plan-owned: the uploads below may complete after this call returns
+  p->nu_host_f.assign((size_t)W + (size_t)Z * M * w, 0.f);
+  p->nu_host_i.assign((size_t)Z * M + Z, 0);
+  float* dec = p->nu_host_f.data();
+  float* wt = dec + W;
+  int* m0 = p->nu_host_i.data();
+  int* zl = m0 + (size_t)Z * M;
+  for (int i = 0; i < W; ++i) dec[i] = (float)(1.0 / es_transform(p->g0 + i, w, p->beta, nf));
+  for (int z = 0; z < Z; ++z) {
+    zl[z] = z;
+    for (int i = 0; i < M; ++i) {
+      const double nu = (i - M / 2) / p->srsd_scale[z];  // frequency on the nf = 2M grid
+      const int a = (int)std::ceil(nu - 0.5 * w);
+      const double inv = 1.0 / es_transform(nu, w, p->beta, nf);
+      m0[(size_t)z * M + i] = a;
+      for (int t = 0; t < w; ++t)
+        wt[((size_t)z * M + i) * w + t] = (float)(es_kernel(2.0 * (a + t - nu) / w, p->beta) * inv);
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(p->nu_dec_w, dec, sizeof(float) * W, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->nu_wt, wt, sizeof(float) * Z * M * w, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->nu_m0, m0, sizeof(int) * Z * M, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(p->nu_zlist, zl, sizeof(int) * Z, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return NURSD_ERR_CUDA;
+  p->nu_ready = true;
+  return NURSD_OK;
+}
+
+// NU-SFFT spectra into p->Y from phasors in sample order: spread, FFT of the whole 2M x 2M grid of
+// b / (psi_hat x psi_hat) (spatial deconvolution), then per depth the ES taps at kappa / s_z fused
+// with the contraction.
+int run_nusfft_spectra(nursd_plan_s* p, const float2* phasor, cudaStream_t s) {
+  const int M = p->M, F = p->F, Z = p->Z, W = p->W, L2 = 2 * M;
+  const int logL = ilog2(L2);
+  cudaError_t e;
+  {
+    StageTimer t(p, NURSD_STAGE_SPREAD, s, 1);
+    e = launch_spread(phasor, F, p->bin_start, p->sorted_l, p->i0_sorted, p->w_sorted, p->w, p->tiles, W, p->fine, s);
+  }
+  if (e == cudaSuccess) {  // along x of every window row: [W][W][F] -> [W][2M][F]
+    StageTimer t(p, NURSD_STAGE_SRSD, s, 2);
+    PanelArgs a = panel_base(p);
+    a.in = p->fine;
+    a.in_sb = (long long)W * F;
+    a.in_si = F;
+    a.in_slo = 1;
+    a.mul_i = p->nu_dec_w;  // 1 / psi_hat(g), window index i <-> g = g0 + i
+    a.out = p->nu_rows;
+    a.out_sb = (long long)L2 * F;
+    a.out_si = F;
+    a.out_slo = 1;
+    a.nin = W;
+    a.in_off = p->g0;
+    a.nout = L2;
+    a.out_off = -M;
+    a.lo_total = F;
+    a.CLO = panel_width(logL);
+    a.batch = W;
+    e = launch_panel_fft(logL, false, a, s);
+    if (e == cudaSuccess) {  // along y of every column: [W][2M][F] -> [2M][2M][F]
+      PanelArgs b = a;
+      b.in = p->nu_rows;
+      b.in_sb = F;
+      b.in_si = (long long)L2 * F;
+      b.out = p->si_yh;
+      b.out_sb = F;
+      b.out_si = (long long)L2 * F;
+      b.batch = L2;
+      e = launch_panel_fft(logL, false, b, s);
+    }
+  }
+  if (e == cudaSuccess && srsd_interp_adds(F)) e = cudaMemsetAsync(p->Y, 0, sizeof(float2) * (size_t)M * M * Z, s);
+  if (e == cudaSuccess) {
+    StageTimer t(p, NURSD_STAGE_SRSD, s, 1);
+    e = launch_srsd_interp_xy_contract(p->si_yh, L2, M, F, Z, p->nu_zlist, Z, p->w, p->nu_m0, p->nu_wt, p->Gs,
+                                       p->ncls, p->Y, s);
   }
   return from_cuda(e);
 }
@@ -823,6 +945,23 @@ int nursd_phasor_frequencies(double lambda_c, double dt, int32_t t_pad, int32_t 
     h_weight[f] = std::exp(-(w - w_c) * (w - w_c) / (2.0 * sigma * sigma));
   }
   return NURSD_OK;
+}
+
+int nursd_subsample(int32_t N, int32_t F, int32_t D, const nursd_c64* d_full, nursd_c64* d_kept,
+                    nursd_stream_t stream) {
+  if (N < 1 || F < 1 || D < 1 || D > N || !d_full || !d_kept || !aligned(d_full, 8) || !aligned(d_kept, 8))
+    return NURSD_ERR_INVALID_ARG;
+  return from_cuda(launch_subsample(reinterpret_cast<const float2*>(d_full), reinterpret_cast<float2*>(d_kept), N, F,
+                                    D, static_cast<cudaStream_t>(stream)));
+}
+
+int nursd_upsample(int32_t N, int32_t F, int32_t D, int32_t mode, const nursd_c64* d_kept, nursd_c64* d_full,
+                   nursd_stream_t stream) {
+  if (N < 1 || F < 1 || D < 1 || D > N || !d_full || !d_kept || !aligned(d_full, 8) || !aligned(d_kept, 8) ||
+      (mode != NURSD_UPSAMPLE_NEAREST && mode != NURSD_UPSAMPLE_LINEAR))
+    return NURSD_ERR_INVALID_ARG;
+  return from_cuda(launch_upsample(reinterpret_cast<const float2*>(d_kept), reinterpret_cast<float2*>(d_full), N, F,
+                                   D, mode == NURSD_UPSAMPLE_LINEAR ? 1 : 0, static_cast<cudaStream_t>(stream)));
 }
 
 int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* out) {
@@ -1269,6 +1408,16 @@ int srsd_forward_points(nursd_plan_t p, const nursd_c64* d_phasor, int32_t K, co
   int rc = run_nufft1(p, reinterpret_cast<const float2*>(d_phasor), p->U, s);
   if (rc == NURSD_OK) rc = run_srsd_spectra(p, s);
   if (rc == NURSD_OK) rc = run_points_output(p, K, d_vox_xy, p->srsd_scale_d, d_out, s);
+  return rc;
+}
+
+int srsd_forward_nonuniform(nursd_plan_t p, const nursd_c64* d_phasor, void* d_out, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || !p->Gs || p->L < 0 || !d_out || !aligned(d_out, 8)) return NURSD_ERR_INVALID_ARG;
+  if (p->L > 0 && (!d_phasor || !aligned(d_phasor, 8))) return NURSD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = ensure_nusfft(p, s);
+  if (rc == NURSD_OK) rc = run_nusfft_spectra(p, reinterpret_cast<const float2*>(d_phasor), s);
+  if (rc == NURSD_OK) rc = run_idft_crop(p, d_out, s);
   return rc;
 }
 

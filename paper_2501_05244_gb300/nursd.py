@@ -26,6 +26,8 @@ NURSD_ERR_POINT_OUT_OF_RANGE = 6
 NURSD_OUTPUT_MAGNITUDE = 0x1
 NURSD_ENABLE_ADJOINT = 0x2
 NURSD_CONFOCAL = 0x4
+NURSD_UPSAMPLE_NEAREST = 0
+NURSD_UPSAMPLE_LINEAR = 1
 
 #: every entry point declared in include/nursd.h
 EXPORTS = (
@@ -36,6 +38,7 @@ EXPORTS = (
     "nursd_nufft1_noalloc",
     "nursd_forward_points", "nursd_adjoint", "nursd_grad_points", "srsd_forward", "nursd_forward_batched",
     "nursd_reconstruct", "nursd_forward_illuminated", "nursd_transient_frames", "srsd_forward_points",
+    "nursd_subsample", "nursd_upsample", "srsd_forward_nonuniform",
 )
 
 #: stage names in nursd_stage order
@@ -108,6 +111,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "nursd_forward_illuminated": (ctypes.c_int, [vp, dp, vp, vp, vp]),
         "nursd_transient_frames": (ctypes.c_int, [vp, i32, dp, vp, vp, vp]),
         "srsd_forward_points": (ctypes.c_int, [vp, vp, i32, vp, vp, vp]),
+        "nursd_subsample": (ctypes.c_int, [i32, i32, i32, vp, vp, vp]),
+        "srsd_forward_nonuniform": (ctypes.c_int, [vp, vp, vp, vp]),
+        "nursd_upsample": (ctypes.c_int, [i32, i32, i32, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -136,6 +142,35 @@ def phasor_frequencies(lambda_c: float, dt: float, t_pad: int, F: int):
     wt = (ctypes.c_double * F)()
     _check(lib.nursd_phasor_frequencies(lambda_c, dt, t_pad, F, om, wt), "nursd_phasor_frequencies")
     return np.array(om[:], dtype=np.float64), np.array(wt[:], dtype=np.float64)
+
+
+def subsample(grid, D: int, out=None, stream=None):
+    """Keep every D-th relay sample of a channel-last grid [N][N][F] complex64 -> [Nc][Nc][F], Nc = ceil(N / D)."""
+    torch = _torch()
+    N, F = int(grid.shape[0]), int(grid.shape[2])
+    g = _dev(grid, torch.complex64, (N, N, F), "grid")
+    nc = -(-N // int(D))
+    if out is None:
+        out = torch.empty((nc, nc, F), dtype=torch.complex64, device=grid.device)
+    o = _dev(out, torch.complex64, (nc, nc, F), "kept")
+    _check(load_library().nursd_subsample(N, F, int(D), g, o, ctypes.c_void_p(_stream_ptr(stream))),
+           "nursd_subsample")
+    return out
+
+
+def upsample(kept, N: int, D: int, linear: bool = False, out=None, stream=None):
+    """Re-grid kept samples [Nc][Nc][F] to the full N x N grid by nearest-neighbour or linear interpolation."""
+    torch = _torch()
+    nc, F = int(kept.shape[0]), int(kept.shape[2])
+    if nc != -(-int(N) // int(D)):
+        raise ValueError(f"kept grid must be ceil(N / D) = {-(-int(N) // int(D))} wide, got {nc}")
+    k = _dev(kept, torch.complex64, (nc, nc, F), "kept")
+    if out is None:
+        out = torch.empty((N, N, F), dtype=torch.complex64, device=kept.device)
+    o = _dev(out, torch.complex64, (N, N, F), "grid")
+    _check(load_library().nursd_upsample(int(N), F, int(D), NURSD_UPSAMPLE_LINEAR if linear else NURSD_UPSAMPLE_NEAREST,
+                                         k, o, ctypes.c_void_p(_stream_ptr(stream))), "nursd_upsample")
+    return out
 
 
 def _torch():
@@ -352,6 +387,18 @@ class Plan:
             out = self.empty_output()
         o = _dev(out, self.out_dtype(), self.out_shape(), "out")
         _check(self._lib.srsd_forward(self._h, p, o, ctypes.c_void_p(_stream_ptr(stream))), "srsd_forward")
+        return out
+
+    def srsd_forward_nonuniform(self, phasor, out=None, stream=None):
+        """NU-SFFT: the scaled DFT taken at the relay samples (every scale >= 1) -> [Z][N][N]."""
+        torch = _torch()
+        self._need_points()
+        p = _dev(phasor, torch.complex64, (self.L, self.F), "phasor")
+        if out is None:
+            out = self.empty_output()
+        o = _dev(out, self.out_dtype(), self.out_shape(), "out")
+        _check(self._lib.srsd_forward_nonuniform(self._h, p, o, ctypes.c_void_p(_stream_ptr(stream))),
+               "srsd_forward_nonuniform")
         return out
 
     def forward_illuminated(self, phasor, illum, out=None, stream=None):
