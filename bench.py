@@ -82,21 +82,18 @@ def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
 
 
 def measured_traffic():
-    """Per-launch DRAM traffic of the contraction from the committed ncu summary, or None
-    when the kernel source changed since the counters were taken."""
+    """Per-launch DRAM traffic of the contraction from the recorded ncu counters
+    (profiles/contract_traffic.json), or None when the kernel source changed since they were taken."""
     import hashlib
-    import re
 
     try:
-        text = open(os.path.join(ROOT, "profiles", "contract_kernel_spad65k.md")).read()
-        src = open(os.path.join(ROOT, "paper_2501_05244_gb300", "csrc", "contract.cu"), "rb").read()
-    except OSError:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "contract_traffic.json")))
+        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+    except (OSError, ValueError, KeyError):
         return None
-    m_t = re.search(r"traffic_bytes_per_launch:\s*(\d+)", text)
-    m_h = re.search(r"sha256\[:16\]\s*([0-9a-f]{16})", text)
-    if not m_t or not m_h or hashlib.sha256(src).hexdigest()[:16] != m_h.group(1):
+    if hashlib.sha256(src).hexdigest()[:16] != rec.get("source_sha256_16"):
         return None
-    return int(m_t.group(1))
+    return int(rec["traffic_bytes_per_launch"])
 
 
 def peaks():
@@ -162,13 +159,80 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- CPU side ---
+# The FP64 oracle runs on every host core: a pool of single-threaded worker processes (spawned,
+# so that no worker inherits a CUDA context), each back-projecting its own block of voxels.
+
+_POOL_STATE = {}
+
+
+def _oracle_worker_init(path_p, path_xy, path_om):
+    import numpy as np
+
+    _POOL_STATE["P"] = np.load(path_p)
+    _POOL_STATE["xy"] = np.load(path_xy)
+    _POOL_STATE["om"] = np.load(path_om)
+
+
+def _oracle_worker_fbp(task):
+    """Direct back-projection of one voxel block over frequency slice [f0, f1) (returns the count)."""
+    import numpy as np
+
+    import oracle as O
+
+    vox, f0, f1 = task
+    O.fbp_direct(_POOL_STATE["P"][:, f0:f1], _POOL_STATE["xy"], _POOL_STATE["om"][f0:f1], vox)
+    return vox.shape[0] * (f1 - f0)
+
+
+class OraclePool:
+    """os.cpu_count() spawned single-threaded processes sharing the phasors through .npy files."""
+
+    def __init__(self, P, xy, omega):
+        import multiprocessing as mp
+        import numpy as np
+
+        self.dir = tempfile.mkdtemp(prefix="nursd_oracle_")
+        paths = [os.path.join(self.dir, n) for n in ("P.npy", "xy.npy", "om.npy")]
+        for path, arr in zip(paths, (P, xy, omega)):
+            np.save(path, np.ascontiguousarray(arr))
+        self.cores = os.cpu_count() or 1
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_worker_init, initargs=paths)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+        self.pool.map(_oracle_worker_fbp, [(np.zeros((1, 3)) + [0.0, 0.0, 1.0], 0, 1)] * self.cores)  # warm up
+
+    def run(self, tasks):
+        return sum(self.pool.map(_oracle_worker_fbp, tasks, chunksize=1))
+
+    def close(self):
+        import shutil
+
+        self.pool.terminate()
+        self.pool.join()
+        shutil.rmtree(self.dir, ignore_errors=True)
+
+
+def _random_voxels(g, n, rng):
+    import numpy as np
+
+    m = rng.integers(0, g.N, size=(n, 2))
+    z = g.depths[rng.integers(0, g.Z, n)]
+    return np.stack([(m[:, 0] - g.N // 2) * g.pitch, (m[:, 1] - g.N // 2) * g.pitch, z], axis=1)
+
 
 def oracle_rate(wl, seconds: float, rng_seed: int = 7):
-    """Time the FP64 oracle (direct back-projection) on a bounded voxel sample.
+    """Time the FP64 oracle (direct back-projection) on a bounded voxel sample on all host cores.
 
-    Returns (voxel*freq/s, description, voxels).  The oracle's temporal
-    transform of all histograms is timed too and charged pro rata to the
-    sampled voxels' share of the full volume.
+    Returns (voxel*freq/s, description, cores).  The oracle's temporal transform of all histograms
+    is timed too and charged pro rata to the sampled voxels' share of the full volume.
     """
     import numpy as np
 
@@ -180,27 +244,151 @@ def oracle_rate(wl, seconds: float, rng_seed: int = 7):
     P = O.temporal_dft(wl.hist, g.t0, g.dt, om, wt)
     t_temporal = time.perf_counter() - t0
     rng = np.random.default_rng(rng_seed)
-
-    def voxels(n):
-        m = rng.integers(0, g.N, size=(n, 2))
-        z = g.depths[rng.integers(0, g.Z, n)]
-        return np.stack([(m[:, 0] - g.N // 2) * g.pitch, (m[:, 1] - g.N // 2) * g.pitch, z], axis=1)
-
-    t0 = time.perf_counter()
-    O.fbp_direct(P, wl.xy, om, voxels(2))
-    per_voxel = (time.perf_counter() - t0) / 2
-    nvox = max(2, int(seconds / max(per_voxel, 1e-6)))
-    vox = voxels(nvox)
-    t0 = time.perf_counter()
-    O.fbp_direct(P, wl.xy, om, vox)
-    t_fbp = time.perf_counter() - t0
+    pool = OraclePool(P, wl.xy, om)
+    try:
+        # cost of one voxel x all frequencies on one worker, then one voxel block per worker task
+        t0 = time.perf_counter()
+        pool.run([(_random_voxels(g, 1, rng), 0, g.F)])
+        per_voxel = time.perf_counter() - t0
+        per_task = max(1, int(2.0 / max(per_voxel, 1e-6)))
+        ntask = max(pool.cores, int(seconds * pool.cores / max(per_voxel * per_task, 1e-6)))
+        tasks = [(_random_voxels(g, per_task, rng), 0, g.F) for _ in range(ntask)]
+        t0 = time.perf_counter()
+        units = pool.run(tasks)
+        t_fbp = time.perf_counter() - t0
+    finally:
+        pool.close()
+    nvox = units // g.F
     full = g.Z * g.N * g.N
     t = t_fbp + t_temporal * nvox / full
-    rate = nvox * g.F / t
     desc = (f"oracle.fbp_direct (FP64 NumPy direct back-projection) of {nvox} random voxels x {g.F} frequencies "
-            f"over all {len(wl.xy)} relay samples ({t_fbp:.1f} s) + oracle.temporal_dft of all histograms "
-            f"({t_temporal:.1f} s, charged pro rata {nvox}/{full})")
-    return rate, desc, nvox
+            f"over all {len(wl.xy)} relay samples on {pool.cores} single-threaded worker processes "
+            f"({t_fbp:.1f} s) + oracle.temporal_dft of all histograms ({t_temporal:.1f} s, charged pro rata "
+            f"{nvox}/{full})")
+    return units / t, desc, pool.cores
+
+
+# The same fast algorithm in FP64 on the host (a secondary, fairer CPU baseline than direct
+# back-projection): ES spread as a sparse matrix, the oversampled 2D FFT (scipy.fft on every core),
+# deconvolution and truncation, the transfer-function multiply with the frequency sum (z blocks on a
+# thread pool), and one inverse FFT with crop per depth.  It is timed on a sample of the frequencies;
+# the per-frequency stages are scaled to all F, the per-depth inverse FFTs are timed in full.
+
+def _es_psi_hat(k, w: int, beta: float, nf: int, nodes: int = 200):
+    """Fourier transform of the ES kernel phi(z) = exp(beta (sqrt(1 - z^2) - 1)) spread over w
+    fine cells, at integer frequencies k of an nf-point grid (Gauss-Legendre quadrature)."""
+    import numpy as np
+
+    z, wq = np.polynomial.legendre.leggauss(nodes)
+    phi = np.exp(beta * (np.sqrt(1.0 - z * z) - 1.0))
+    return (w / 2.0) * (np.cos(np.pi * np.outer(k, z) * w / nf) @ (wq * phi))
+
+
+class CpuFastPlan:
+    """Plan-time tables of the FP64 host run: spread matrix, deconvolution, transfer functions."""
+
+    def __init__(self, xy, N, pitch, center, depths, omega, freqs, width=6):
+        import numpy as np
+        import scipy.sparse as sp
+
+        self.N, self.M, self.nf, self.w = N, 2 * N, 4 * N, width
+        self.depths, self.omega, self.freqs = np.asarray(depths, float), np.asarray(omega, float), list(freqs)
+        M, nf, w = self.M, self.nf, width
+        beta = 2.30 * w
+        t0 = time.perf_counter()
+        u = (np.asarray(xy, np.float64) - np.asarray(center, np.float64)[None, :]) * (2.0 / pitch)
+        i0 = np.ceil(u - 0.5 * w).astype(np.int64)
+        taps = np.arange(w)
+        zz = 2.0 * (i0[:, :, None] + taps[None, None, :] - u[:, :, None]) / w  # [L][2][w]
+        wt = np.where(np.abs(zz) < 1.0, np.exp(beta * (np.sqrt(np.maximum(1.0 - zz * zz, 0.0)) - 1.0)), 0.0)
+        gx = (i0[:, 0, None] + taps[None, :]) % nf
+        gy = (i0[:, 1, None] + taps[None, :]) % nf
+        rows = (gy[:, :, None] * nf + gx[:, None, :]).reshape(len(u), -1)
+        vals = (wt[:, 1, :, None] * wt[:, 0, None, :]).reshape(len(u), -1)
+        cols = np.repeat(np.arange(len(u)), w * w)
+        self.S = sp.csr_matrix((vals.ravel(), (rows.ravel(), cols)), shape=(nf * nf, len(u)))
+        self.t_points = time.perf_counter() - t0
+        k = np.fft.fftfreq(M, 1.0 / M)  # k in FFT order
+        ph = _es_psi_hat(k, w, beta, nf)
+        self.deconv = 1.0 / np.outer(ph, ph)
+        self.kidx = np.asarray(k, np.int64) % nf  # fine-grid bins kept
+        j = np.fft.fftfreq(M, 1.0 / M) * pitch  # offsets j delta in FFT order
+        r2 = j[None, :] ** 2 + j[:, None] ** 2
+        C = 299792458.0
+        self.G = np.empty((len(self.depths), len(self.freqs), M, M), np.complex128)
+        for iz, z in enumerate(self.depths):
+            r = np.sqrt(r2 + z * z)
+            for i, f in enumerate(self.freqs):
+                self.G[iz, i] = np.fft.fft2(np.exp(1j * self.omega[f] / C * r) / r)
+
+    def forward(self, P, workers):
+        """V[z][my][mx] summed over the plan's frequencies, and the stage times (s)."""
+        import concurrent.futures as cf
+
+        import numpy as np
+        import scipy.fft as sfft
+
+        M, N, nf, Z = self.M, self.N, self.nf, len(self.depths)
+        t = dict(spread=0.0, fft=0.0, deconv=0.0, contract=0.0, ifft=0.0)
+        Y = np.zeros((Z, M, M), np.complex128)
+        blocks = [slice(z0, min(Z, z0 + max(1, Z // workers))) for z0 in range(0, Z, max(1, Z // workers))]
+        with cf.ThreadPoolExecutor(workers) as ex:
+            for i, f in enumerate(self.freqs):
+                t0 = time.perf_counter()
+                fine = (self.S @ np.asarray(P[:, f], np.complex128)).reshape(nf, nf)
+                t1 = time.perf_counter()
+                bh = sfft.fft2(fine, workers=workers)
+                t2 = time.perf_counter()
+                U = bh[np.ix_(self.kidx, self.kidx)] * self.deconv
+                t3 = time.perf_counter()
+
+                def mac(b, U=U, i=i):
+                    Y[b] += U[None] * self.G[b, i]
+
+                list(ex.map(mac, blocks))
+                t4 = time.perf_counter()
+                t["spread"] += t1 - t0
+                t["fft"] += t2 - t1
+                t["deconv"] += t3 - t2
+                t["contract"] += t4 - t3
+        t0 = time.perf_counter()
+        v = sfft.ifft2(Y, axes=(-2, -1), workers=workers)
+        m = np.arange(-N // 2, N // 2) % M
+        V = v[:, m][:, :, m]
+        t["ifft"] = time.perf_counter() - t0
+        return V, t
+
+
+def cpu_fast_rate(wl, n_freq: int = 2):
+    """FP64 host run of the fast algorithm on all cores, per reconstruction: the temporal transform
+    and point preparation in full, the per-frequency stages on n_freq frequencies scaled to F, the
+    per-depth inverse FFTs in full.  Returns a row dict."""
+    import numpy as np
+
+    g = wl.geom
+    workers = os.cpu_count() or 1
+    C = 299792458.0
+    f_c = C / g.lambda_c
+    f0 = math.floor(f_c * g.t_pad * g.dt + 0.5) - g.F // 2
+    omega = 2 * math.pi * (f0 + np.arange(g.F)) / (g.t_pad * g.dt)
+    wt = np.exp(-((omega - 2 * math.pi * f_c) ** 2) / (2 * (2 * math.pi * f_c / 5) ** 2))
+    t0 = time.perf_counter()
+    tn = g.t0 + g.dt * np.arange(g.T)
+    P = (np.asarray(wl.hist, np.float64) @ np.exp(-1j * np.outer(tn, omega))) * wt[None, :]
+    t_temporal = time.perf_counter() - t0
+    freqs = list(np.linspace(0, g.F - 1, n_freq).round().astype(int))
+    plan = CpuFastPlan(wl.xy, g.N, g.pitch, g.center, g.depths, omega, freqs)
+    _, st = plan.forward(P, workers)
+    per_f = st["spread"] + st["fft"] + st["deconv"] + st["contract"]
+    t = t_temporal + plan.t_points + per_f * g.F / n_freq + st["ifft"]
+    units = g.Z * g.N * g.N * g.F
+    return {"value": units / t, "unit": UNIT, "cores": workers, "dtype": "f64", "s_per_reconstruction": t,
+            "stages_s": {"temporal": t_temporal, "points": plan.t_points,
+                         **{k: (v * g.F / n_freq if k != "ifft" else v) for k, v in st.items()}},
+            "sample": f"NumPy/SciPy FP64 fast algorithm (sparse ES spread, scipy.fft with workers={workers}, "
+                      f"contraction over a {workers}-thread pool); {n_freq} of {g.F} frequencies timed and "
+                      f"scaled, temporal transform, point preparation and the {g.Z} inverse FFTs timed in full; "
+                      f"transfer-function tables built outside the timing"}
 
 
 # ---------------------------------------------------------------- GPU side ---
@@ -226,7 +414,66 @@ def _stage_ms(plan, calls):
     return {k: v[0] / calls for k, v in plan.profile_read().items() if v[1]}
 
 
-def measure_rows(wl, peak):
+def fine_window(N: int, w: int = 6) -> int:
+    """Width of the fine-grid window the spread writes (16-cell tiles covering every footprint)."""
+    return (2 * N + w + 2 + 15) // 16 * 16
+
+
+def n_classes(N: int) -> int:
+    """8-fold symmetry classes of the transfer function on the M = 2N grid."""
+    return (N + 1) * (N + 2) // 2
+
+
+def bytes_type1(L: int, F: int, N: int) -> int:
+    """Spread (phasors in, window out), FFT along x (window in, rows out), FFT along y with
+    deconvolution (rows in, spectrum out): complex64 bytes."""
+    M, W = 2 * N, fine_window(N)
+    return 8 * (L * F + W * W * F + W * W * F + W * M * F + W * M * F + M * M * F)
+
+
+def bytes_contract(F: int, Z: int, N: int) -> int:
+    """Table once, spectrum in, depth spectra out."""
+    M = 2 * N
+    return 8 * (n_classes(N) * F * Z + M * M * F + M * M * Z)
+
+
+def bytes_idft(Z: int, N: int, mag: bool = False) -> int:
+    """Two pruned inverse passes: Y in, half inverse out and in, volume out."""
+    M = 2 * N
+    return 8 * (M * M * Z + 2 * M * N * Z) + (4 if mag else 8) * N * N * Z
+
+
+def bytes_type2_fine(C: int, N: int) -> int:
+    """Spectrum [M][M][C] in, rows [M][W][C] out and in, fine window [W][W][C] out."""
+    M, W = 2 * N, fine_window(N)
+    return 8 * (M * M * C + 2 * M * W * C + W * W * C)
+
+
+def bytes_adjoint_spectrum(F: int, Z: int, N: int) -> int:
+    """Volume in, half transform out and in, depth spectra out and in, table in, spectrum out."""
+    M = 2 * N
+    return 8 * (N * N * Z + 2 * N * M * Z + 2 * M * M * Z + n_classes(N) * Z * F + M * M * F)
+
+
+def bytes_srsd(N: int, F: int, scales, w: int = 6) -> int:
+    """SRSD spectra by interpolation of one oversampled spectrum: the gridded input (spectrum in, u
+    out and back in), the shared oversampled spectrum (half-transformed rows written and read, the
+    [2M][2M] spectrum written), and per depth the spectrum block its taps reach, its table and Y_z."""
+    M = 2 * N
+    Lg = 2 * M
+    b = (3 * M * M + 2 * M * Lg + Lg * Lg) * F * 8
+    for sc in scales:
+        R = (math.ceil(2.0 * (M // 2 - 1) / sc - 0.5 * w) + w - 1) - math.ceil(2.0 * (-M // 2) / sc - 0.5 * w) + 1
+        b += (R * R * F + n_classes(N) * F + M * M) * 8
+    return b
+
+
+def hbm_row(bytes_: int, ms: float, peak: float) -> dict:
+    gbs = bytes_ / (ms / 1e3) / 1e9
+    return {"algorithmic_bytes": int(bytes_), "achieved_gbs": gbs, "hbm_frac": gbs / peak}
+
+
+def measure_rows(wl, peak, stages_ms=None):
     """Per-row measurements of the other hot-path rows on the same GPU (one entry each)."""
     import numpy as np
     import torch
@@ -265,8 +512,11 @@ def measure_rows(wl, peak):
         assert plan.sync_status() == 0
         plan.close()
         units = g.Z * K * g.F
+        W = fine_window(g.N)
+        b = (bytes_type1(L, g.F, g.N) + bytes_contract(g.F, g.Z, g.N) + bytes_type2_fine(g.Z, g.N)
+             + 8 * (W * W * g.Z + 2 * g.Z * K))  # plane windows in, voxel positions in, values out
         return {"workload": "65,536 keystone samples -> 128 planes x 16,384 random voxels (2,097,152), F=128",
-                "ms": ms, "voxel_freq_per_s": units / (ms / 1e3), "stages_ms": st}
+                "ms": ms, "voxel_freq_per_s": units / (ms / 1e3), **hbm_row(b, ms, peak), "stages_ms": st}
 
     def srsd():
         depths = srsd_depths_c3b()
@@ -279,22 +529,14 @@ def measure_rows(wl, peak):
         ms = _time(lambda: plan.srsd_forward(P, out), 3, 1, stream)
         prof = plan.profile_read()  # 4 calls: the warm-up and the 3 timed
         plan.close()
-        M, F, Z, w = 2 * g.N, g.F, len(depths), 6
-        Lg = 2 * M
-        ncls = (M // 2 + 1) * (M // 2 + 2) // 2
+        F, Z = g.F, len(depths)
         s_ms = prof["srsd"][0] / 4
         scales = srsd_pitches_c3b(depths) / g.pitch  # all >= 1: every depth is interpolated
-        # gridded input (spectrum in, u out and back in) and the shared oversampled spectrum
-        # (half-transformed rows written and read, the [2M][2M] spectrum written)
-        bytes_ = (3 * M * M + 2 * M * Lg + Lg * Lg) * F * 8
-        for sc in scales:
-            # rows (and columns) the taps of this scale reach on the 2M grid
-            R = (math.ceil(2.0 * (M // 2 - 1) / sc - 0.5 * w) + w - 1) - math.ceil(2.0 * (-M // 2) / sc - 0.5 * w) + 1
-            # the reached spectrum block in, the depth's table in, Y_z out (taps and contraction in one pass)
-            bytes_ += (R * R * F + ncls * F + M * M) * 8
+        bytes_ = bytes_srsd(g.N, F, scales)
+        call_bytes = bytes_type1(L, F, g.N) + bytes_ + bytes_idft(Z, g.N)
         units = Z * g.N * g.N * F
         return {"workload": "65,536 keystone samples -> 256^2 x 128 planes over 1-4 m, pitch 8 -> 32 mm, F=128",
-                "ms": ms, "voxel_freq_per_s": units / (ms / 1e3),
+                "ms": ms, "voxel_freq_per_s": units / (ms / 1e3), **hbm_row(call_bytes, ms, peak),
                 "srsd_stage": {"ms": s_ms, "algorithmic_bytes": bytes_, "achieved_gbs": bytes_ / (s_ms / 1e3) / 1e9,
                                "hbm_frac": bytes_ / (s_ms / 1e3) / 1e9 / peak,
                                "method": "scaled DFT by ES interpolation of one oversampled spectrum"},
@@ -312,8 +554,11 @@ def measure_rows(wl, peak):
         st = _stage_ms(plan, 12)
         plan.close()
         units = g.Z * g.N * g.N * g.F
+        W = fine_window(g.N)
+        b = (bytes_adjoint_spectrum(g.F, g.Z, g.N) + bytes_type2_fine(g.F, g.N)
+             + 8 * (W * W * g.F + L * g.F))  # window in, phasors out
         return {"workload": "spad-65k adjoint: 256^2 x 128 volume -> 65,536 x 128 phasors", "ms": ms,
-                "voxel_freq_per_s": units / (ms / 1e3), "stages_ms": st}
+                "voxel_freq_per_s": units / (ms / 1e3), **hbm_row(b, ms, peak), "stages_ms": st}
 
     def grad():
         N, Z, F = 128, 64, 128
@@ -333,8 +578,14 @@ def measure_rows(wl, peak):
         ms = _time(step, 10, 2, stream)
         st = _stage_ms(plan, 12)
         plan.close()
+        Lg, W = len(xy), fine_window(N)
+        b = (bytes_type1(Lg, F, N) + bytes_contract(F, Z, N) + bytes_idft(Z, N)  # forward
+             + bytes_adjoint_spectrum(F, Z, N) + 3 * bytes_type2_fine(F, N)  # R, kx R, ky R on the window
+             + 8 * (3 * W * W * F + 2 * Lg * F + Lg))  # three windows and P in, grad P and grad x out
         return {"workload": "65,536 keystone samples, F=128, 128^2 x 64: forward + gradients w.r.t. phasors "
-                            "and positions", "ms": ms, "stages_ms": st}
+                            "and positions", "ms": ms, **hbm_row(b, ms, peak),
+                "bytes_exclude": "the residual 2 (V - V_t) formed by torch between the two calls",
+                "stages_ms": st}
 
     def illuminated():
         # next row 1: one illumination point's phase mask per voxel and frequency (Eq. PF_RSD_Defn),
@@ -371,7 +622,7 @@ def measure_rows(wl, peak):
                 "per_frequency_stages": {"algorithmic_bytes": bytes_pf,
                                          "ms": ms - st.get("spread", 0) - st.get("fft_x", 0) - st.get("fft_y", 0),
                                          "depth_group": zg, "products_in_kx_pass": fused},
-                "hbm_frac_of_call": (bytes_pf / (ms / 1e3) / 1e9) / peak, "stages_ms": st}
+                **hbm_row(bytes_type1(L, F, N) + bytes_pf, ms, peak), "stages_ms": st}
 
     def srsd_points():
         # next row 2: SRSD + NURSD-2 (Eq. NURSD2_SRSD), 16,384 random voxels in each plane's scaled aperture
@@ -388,9 +639,12 @@ def measure_rows(wl, peak):
         ms = _time(lambda: plan.srsd_forward_points(P, vox, out=out), 3, 1, stream)
         assert plan.sync_status() == 0
         plan.close()
+        Z, W = len(depths), fine_window(g.N)
+        b = (bytes_type1(L, g.F, g.N) + bytes_srsd(g.N, g.F, pitches / g.pitch) + bytes_type2_fine(Z, g.N)
+             + 8 * (W * W * Z + 2 * Z * K))
         return {"workload": "65,536 keystone samples -> 128 scaled planes over 1-4 m (pitch 8 -> 32 mm) x 16,384 "
                             "random voxels each, F=128",
-                "ms": ms, "voxel_freq_per_s": len(depths) * K * g.F / (ms / 1e3)}
+                "ms": ms, "voxel_freq_per_s": len(depths) * K * g.F / (ms / 1e3), **hbm_row(b, ms, peak)}
 
     def batched():
         gb = geometry_c4()
@@ -422,12 +676,42 @@ def measure_rows(wl, peak):
         ms_single = _time(singles, 3, 1, stream)
         plan.close()
         units = len(sizes) * gb.Z * gb.N * gb.N * gb.F
+        M = 2 * gb.N
+        b = 8 * n_classes(gb.N) * gb.F * gb.Z  # the shared table, read once
+        for Lb in sizes:  # per item: temporal, type 1, its spectrum and depth spectra, inverse passes
+            Lb = int(Lb)
+            b += (Lb * gb.T * 4 + Lb * gb.F * 8 + bytes_type1(Lb, gb.F, gb.N) + 8 * (M * M * gb.F + M * M * gb.Z)
+                  + bytes_idft(gb.Z, gb.N))
         return {"workload": "64 reconstructions, L log-uniform 4,096-65,536 (sum %d), T=512 @ 8 ps, F=64, "
                             "128^2 x 64 each" % int(sizes.sum()),
                 "ms_graph": ms_graph, "recon_per_s": len(sizes) / (ms_graph / 1e3),
-                "voxel_freq_per_s": units / (ms_graph / 1e3), "ms_64_single_calls": ms_single,
-                "speedup_vs_single_calls": ms_single / ms_graph}
+                "voxel_freq_per_s": units / (ms_graph / 1e3), **hbm_row(b, ms_graph, peak),
+                "ms_64_single_calls": ms_single, "speedup_vs_single_calls": ms_single / ms_graph}
 
+    def cufft():
+        # comparison only (timed, not part of the path): cuFFT through torch.fft on the full
+        # oversampled grid [F][4N][4N] and on the depth spectra [Z][2N][2N] with the crop, beside
+        # this library's pruned channel-last panel passes of the same two stages
+        M, nf, F, Z, N = 2 * g.N, 4 * g.N, g.F, g.Z, g.N
+        x = torch.randn((F, nf, nf), dtype=torch.complex64, device="cuda")
+        y = torch.empty_like(x)
+        ms_f = _time(lambda: torch.fft.fft2(x, out=y), 5, 2, stream)
+        del x, y
+        Yd = torch.randn((Z, M, M), dtype=torch.complex64, device="cuda")
+        m = torch.arange(-(N // 2), N - N // 2, device="cuda") % M
+        ms_i = _time(lambda: torch.fft.ifft2(Yd)[:, m][:, :, m], 5, 2, stream)
+        del Yd
+        st = stages_ms or {}
+        ours_f = st.get("fft_x", 0.0) + st.get("fft_y", 0.0)
+        ours_i = st.get("ifft_x", 0.0) + st.get("ifft_y", 0.0)
+        return {"workload": "forward fine-grid FFT (a4-a5) and inverse FFT with crop (a7) at spad-65k",
+                "cufft_forward_full_grid_ms": ms_f, "ours_forward_pruned_ms": ours_f,
+                "cufft_inverse_with_crop_ms": ms_i, "ours_inverse_pruned_ms": ours_i,
+                "note": "cuFFT transforms the whole 1024^2 oversampled grid of every frequency (plane-major) and "
+                        "every 512^2 depth spectrum before the crop; the library's passes transform only the "
+                        "spread window and keep only the retained bins, channel-last"}
+
+    guarded("d_cufft_comparison", cufft)
     guarded("a8_type2_voxels", type2)
     guarded("a9_srsd", srsd)
     guarded("a10_adjoint", adjoint)
@@ -481,12 +765,19 @@ def run_ours(args, rank, world, local):
     if plan.sync_status() != 0:
         raise RuntimeError("device status error during warm-up")
 
-    # One step captured as a CUDA graph (same kernels and launches; the replay avoids per-launch
-    # host and scheduling gaps between the kernels of a step).  Eager steps if capture fails.
+    # The timed region replays one captured CUDA graph per step (same kernels and launches as the
+    # eager call; the replay avoids per-launch host and scheduling gaps).  Each graph also holds the
+    # two event-record nodes the plan places around the contraction, so the dominant kernel is timed
+    # in every step of the timed region itself.  Eager steps if capture fails.
     launches0 = plan.launch_count
     step()
     launches_per_step = plan.launch_count - launches0
-    graph = None
+    plan.profile_stages(["contract"])
+    for _ in range(args.steps):  # creates the event pairs the captures use
+        step()
+    torch.cuda.synchronize()
+    plan.profile_read()
+    graphs = None
     if not args.no_graph:
         try:
             cap = torch.cuda.Stream()
@@ -495,14 +786,18 @@ def run_ours(args, rank, world, local):
                 step()
             stream.wait_stream(cap)
             torch.cuda.synchronize()
-            graph = torch.cuda.CUDAGraph()
-            with torch.cuda.graph(graph):
-                step()
+            plan.profile_read()
+            graphs = []
+            for _ in range(args.steps):
+                gr = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(gr):
+                    step()
+                graphs.append(gr)
             torch.cuda.synchronize()
         except Exception:  # fall back to eager steps
-            graph = None
+            graphs = None
             torch.cuda.synchronize()
-    run_step = graph.replay if graph is not None else step
+            plan.profile_read()
 
     # ---- timed region (device): K steps, events on the launching stream
     clocks = ClockSampler(local)
@@ -511,14 +806,20 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
-        run_step()
+    for i in range(args.steps):
+        if graphs is not None:
+            graphs[i].replay()
+        else:
+            step()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
     if plan.sync_status() != 0:
         raise RuntimeError("device status error in the timed region")
+    c_ms, c_n = plan.profile_read()["contract"]  # the contraction of each timed step
+    plan.profile(False)
+    graphs = None
     launches = launches_per_step * args.steps
     ms = reduce_max(e0.elapsed_time(e1) / args.steps, dist, "cuda")
 
@@ -594,7 +895,6 @@ def run_ours(args, rank, world, local):
     M, Z, F, N = plan.M, g.Z, g.F, g.N
     # algorithmic bytes of the contraction launch: table once, spectrum once, depth spectra once
     contract_bytes = plan.n_classes * F * Z * 8 + M * M * F * 8 + M * M * Z * 8
-    c_ms, c_n = stages["contract"]
     c_avg = c_ms / max(c_n, 1)
     achieved = contract_bytes / (c_avg / 1e3) / 1e9
     W = (2 * N + 6 + 2 + 15) // 16 * 16
@@ -615,9 +915,10 @@ def run_ours(args, rank, world, local):
                                 "spad-n128": "spad-n128: " + WORKLOAD.replace("256x256x128", "128x128x128")}[
                                     args.workload], "L": L, "T": g.T, "F": F, "N": N, "Z": Z, "M": M, "fine_n": plan.fine_n,
                    "parallelism": f"replicas x{world} (one reconstruction per GPU)",
-                   "launch": (f"CUDA-graph replay of one nursd_reconstruct call ({launches_per_step} kernels)"
-                              if graph is not None
-                              else "eager nursd_reconstruct calls"),
+                   "launch": (f"one captured CUDA graph of a nursd_reconstruct call ({launches_per_step} kernels) "
+                              f"replayed per step" if c_n and not args.no_graph else "eager nursd_reconstruct calls"),
+                   "roofline_timing": f"CUDA events around the contraction in each of the {c_n} timed steps "
+                                      f"(event-record nodes of the replayed graphs, on the launching stream)",
                    "stage_times": "CUDA events around each stage of 100 eager steps after the timed region, per step "
                                   "(a stage run in channel or depth groups is summed over its launches)",
                    "l2": "inputs larger than L2 (histograms 268 MB, transfer table %.2f GB); no flush" %
@@ -639,10 +940,14 @@ def run_ours(args, rank, world, local):
     }
     if rank == 0 and world == 1 and not args.no_rows and args.workload == "spad":
         plan.close()
-        line["rows"] = measure_rows(wl, peak)
+        line["rows"] = measure_rows(wl, peak, line["stages_ms"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, desc, _ = oracle_rate(wl, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        rate, desc, cores = oracle_rate(wl, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        try:
+            line["cpu_fast_fp64"] = cpu_fast_rate(wl)
+        except Exception as exc:  # a comparison row; its failure is reported, not fatal
+            line["cpu_fast_fp64"] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
@@ -652,6 +957,8 @@ def run_ours(args, rank, world, local):
 
 
 def run_reference(args, rank, world, local):
+    """The FP64 oracle (direct back-projection) on all host cores: each step back-projects one random
+    voxel x 16 frequencies per worker process over all relay samples."""
     if rank != 0:
         return
     import numpy as np
@@ -666,34 +973,40 @@ def run_reference(args, rank, world, local):
     P = O.temporal_dft(wl.hist, g.t0, g.dt, om, wt)
     t_temporal = time.perf_counter() - t0
     rng = np.random.default_rng(11)
-    nvox, nf = 1, 16  # each step: one voxel x 16 frequencies (cycling through the band)
-
-    def voxels(n):
-        m = rng.integers(0, g.N, size=(n, 2))
-        z = g.depths[rng.integers(0, g.Z, n)]
-        return np.stack([(m[:, 0] - g.N // 2) * g.pitch, (m[:, 1] - g.N // 2) * g.pitch, z], axis=1)
+    nf = 16  # each task: one voxel x 16 frequencies (cycling through the band)
+    pool = OraclePool(P, wl.xy, om)
+    cores = pool.cores
 
     def one(i):
-        fs = slice((i * nf) % g.F, (i * nf) % g.F + nf)
-        O.fbp_direct(P[:, fs], wl.xy, om[fs], voxels(nvox))
+        tasks = []
+        for c in range(cores):
+            f0 = ((i * cores + c) * nf) % g.F
+            tasks.append((_random_voxels(g, 1, rng), f0, f0 + nf))
+        return pool.run(tasks)
 
-    for i in range(args.warmup):
-        one(i)
-    t0 = time.perf_counter()
-    for i in range(args.steps):
-        one(i)
-    t = time.perf_counter() - t0
+    try:
+        for i in range(args.warmup):
+            one(i)
+        t0 = time.perf_counter()
+        units = 0
+        for i in range(args.steps):
+            units += one(args.warmup + i)
+        t = time.perf_counter() - t0
+    finally:
+        pool.close()
     full = g.Z * g.N * g.N * g.F
-    t_step = t / args.steps + t_temporal * nvox * nf / full
-    value = nvox * nf / t_step
-    desc = (f"each step: oracle.fbp_direct (FP64 NumPy direct back-projection) of {nvox} random voxel x {nf} "
-            f"frequencies over all {len(wl.xy)} relay samples, plus the oracle temporal transform of all "
-            f"histograms ({t_temporal:.1f} s) charged pro rata")
+    per_step = units / args.steps
+    t_step = t / args.steps + t_temporal * per_step / full
+    value = per_step / t_step
+    desc = (f"each step: oracle.fbp_direct (FP64 NumPy direct back-projection) of one random voxel x {nf} "
+            f"frequencies per worker on {cores} single-threaded worker processes, over all {len(wl.xy)} relay "
+            f"samples, plus the oracle temporal transform of all histograms ({t_temporal:.1f} s) charged pro rata")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "L": len(wl.xy), "T": g.T, "F": g.F, "N": g.N, "Z": g.Z},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "config": {"workload": WORKLOAD, "L": len(wl.xy), "T": g.T, "F": g.F, "N": g.N, "Z": g.Z,
+                       "M": 2 * g.N, "fine_n": 4 * g.N},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
