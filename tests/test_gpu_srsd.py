@@ -187,3 +187,53 @@ def test_srsd_with_more_depths_than_one_tile_wave():
     assert plan.sync_status() == 0
     ref = O.srsd_forward(P, xy, center, pitch, N, depths, out_pitch / pitch, om)
     assert rel(V, ref) < TOL
+
+
+# --------------------------------------------- NU-SFFT (SRSD on non-uniform acquisition) ---
+
+@pytest.mark.parametrize("N,L,F,Z,seed,width", [(16, 300, 6, 5, 41, 6), (32, 1500, 16, 7, 42, 6), (32, 900, 70, 3, 43, 7)])
+def test_nu_sfft_matches_oracle(N, L, F, Z, seed, width):
+    xy, P, om, depths, out_pitch, pitch, center = case(N, L, F, Z, seed)
+    plan = nursd.Plan(N, pitch, center, depths, om, max_points=L, srsd_pitch=out_pitch, kernel_width=width)
+    plan.set_points(torch.from_numpy(xy).cuda())
+    V = plan.srsd_forward_nonuniform(torch.from_numpy(P).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    ref = O.nu_sfft_forward(P, xy, center, pitch, N, depths, out_pitch / pitch, om)
+    assert rel(V, ref) < TOL
+
+
+def test_nu_sfft_on_the_lattice_equals_srsd_and_needs_scales_of_at_least_one():
+    N, F, Z, pitch, center = 32, 8, 4, 0.02, (0.01, -0.03)
+    lat = relay_lattice(N, pitch, center)
+    P = torch.from_numpy(random_phasors(len(lat), F, seed=44)).cuda()
+    om = 2 * math.pi * np.linspace(3e9, 6e9, F)
+    depths = np.linspace(0.3, 0.9, Z)
+    plan = nursd.Plan(N, pitch, center, depths, om, max_points=len(lat), srsd_pitch=np.linspace(1.0, 3.0, Z) * pitch)
+    plan.set_points(torch.from_numpy(lat).cuda())
+    assert rel(plan.srsd_forward_nonuniform(P).cpu().numpy(), plan.srsd_forward(P).cpu().numpy()) < TOL
+    low = nursd.Plan(N, pitch, center, depths, om, max_points=len(lat), srsd_pitch=np.linspace(0.7, 2.0, Z) * pitch)
+    low.set_points(torch.from_numpy(lat).cuda())
+    with pytest.raises(nursd.NursdError) as err:
+        low.srsd_forward_nonuniform(P)
+    assert err.value.status == nursd.nursd.NURSD_ERR_UNSUPPORTED
+
+
+def test_nu_sfft_at_the_65k_sample_size_sampled_planes():
+    # 65,536 samples on the 256^2 lattice, 128 planes over 1-4 m, pitch 8 -> 32 mm: on the lattice the
+    # NU-SFFT is the SRSD of the gridded samples, evaluated by the oracle on planes 0 and 127
+    N, pitch, F = 256, 2.0 / 256, 128
+    depths = srsd_depths_c3b()
+    out_pitch = srsd_pitches_c3b(depths)
+    lat = relay_lattice(N, pitch)
+    om, _ = O.phasor_frequencies(0.06, 4e-12, 8192, F)
+    plan = nursd.Plan(N, pitch, (0.0, 0.0), depths, om, max_points=len(lat), srsd_pitch=out_pitch)
+    plan.set_points(torch.from_numpy(lat).cuda())
+    P = random_phasors(len(lat), F, seed=BASE_SEED + 81)
+    V = plan.srsd_forward_nonuniform(torch.from_numpy(P).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    M = 2 * N
+    n_xy = np.rint(lat.astype(np.float64) / pitch).astype(int)
+    u = O.idft_grid(O.nudft_type1_lattice(P, n_xy, M))
+    for z in (0, len(depths) - 1):
+        ref = O.srsd_from_grid(u, depths[z:z + 1], out_pitch[z:z + 1] / pitch, om, pitch, N)[0]
+        assert rel(V[z], ref) < TOL
