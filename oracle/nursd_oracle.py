@@ -42,6 +42,7 @@ __all__ = [
     "voxel_lattice", "propagate_per_frequency", "illumination_mask", "propagate_illuminated", "transient_frames",
     "nursd_forward_illuminated", "nursd_transient_frames", "fbp_direct_per_frequency",
     "srsd_spectra", "srsd_points", "nu_sfft_spectra", "nu_sfft_forward",
+    "rsd_kernel_3d", "nursd3d_plane", "nursd3d_forward",
 ]
 
 
@@ -467,6 +468,61 @@ def nu_sfft_forward(P, xy, center, pitch: float, N: int, depths, scales, omega) 
     Y = nu_sfft_spectra(P, xy, center, pitch, N, depths, scales, omega)
     B = _idft_crop_matrix(M, N)
     return np.stack([B @ Y[iz] @ B.T for iz in range(Y.shape[0])]) / (M * M)
+
+
+# ------------------------------------------------ 3D NURSD (non-planar relays) ---
+
+def rsd_kernel_3d(M: int, pitch: float, Mz: int, dz: float, k: float) -> np.ndarray:
+    """G(j delta, jz dz) = exp(+i k r) / r on the offsets j in I_M^2, jz in I_Mz: [jz][jy][jx], r = sqrt((jx delta)^2 +
+    (jy delta)^2 + (jz dz)^2), with G = 0 at the zero offset where r = 0 (a reading: the paper leaves it undefined)."""
+    j = index_set(M).astype(np.float64) * pitch
+    jz = index_set(Mz).astype(np.float64) * dz
+    r = np.sqrt(jz[:, None, None] ** 2 + j[None, :, None] ** 2 + j[None, None, :] ** 2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        g = np.exp(1j * k * r) / r
+    g[r == 0.0] = 0.0
+    return g
+
+
+def nursd3d_plane(P, xyz, center, pitch: float, N: int, z0: float, dz: float, Mz: int, omega) -> np.ndarray:
+    """Stage 1 of 3D NURSD (Eq. 3D_NURSD, with Eq. 3d_rsd): each frequency's field on the N x N lattice of plane z0.
+
+    The 3D type-1 sum U_f(k) = sum_l P[l, f] exp(-i k . theta_l) over k in I_M^2 x I_Mz with
+    theta_l = (2 pi (x_l - c_x) / (M delta), 2 pi (y_l - c_y) / (M delta), 2 pi (z_l - z0) / (Mz dz)), times the 3D
+    DFT of the sampled kernel (rsd_kernel_3d), inverse-transformed and evaluated at the slice z = z0 and the
+    lattice m in I_N^2: W_f[m] = (M^2 Mz)^-1 sum_k U_f(k) Ghat_f(k) exp(+2 pi i (kx mx + ky my) / M).
+    P [L][F], xyz [L][3] metres -> [F][N][N].
+    """
+    M = 2 * N
+    P = np.asarray(P, dtype=np.complex128)
+    xyz = np.asarray(xyz, dtype=np.float64)
+    c = np.asarray(center, dtype=np.float64)
+    th = np.stack([2 * math.pi * (xyz[:, 0] - c[0]) / (M * pitch), 2 * math.pi * (xyz[:, 1] - c[1]) / (M * pitch),
+                   2 * math.pi * (xyz[:, 2] - z0) / (Mz * dz)], axis=1)
+    k = index_set(M).astype(np.float64)
+    kz = index_set(Mz).astype(np.float64)
+    Ex = np.exp(-1j * np.outer(k, th[:, 0]))   # [kx][l]
+    Ey = np.exp(-1j * np.outer(k, th[:, 1]))   # [ky][l]
+    Ez = np.exp(-1j * np.outer(kz, th[:, 2]))  # [kz][l]
+    B = _idft_crop_matrix(M, N)                # [m][k]
+    out = np.empty((P.shape[1], N, N), dtype=np.complex128)
+    for f, w in enumerate(np.asarray(omega, dtype=np.float64)):
+        U = np.einsum("zl,yl,xl,l->zyx", Ez, Ey, Ex, P[:, f])  # explicit 3D non-uniform sum
+        g = rsd_kernel_3d(M, pitch, Mz, dz, w / C)
+        G = np.fft.fftshift(np.fft.fftn(np.fft.ifftshift(g)))  # the 3D DFT (a library routine)
+        Wk = np.sum(U * G, axis=0) / Mz  # the slice z = z0 of the inverse transform along kz
+        out[f] = (B @ Wk @ B.T) / (M * M)
+    return out
+
+
+def nursd3d_forward(P, xyz, center, pitch: float, N: int, z0: float, dz: float, Mz: int, depths, omega) -> np.ndarray:
+    """3D NURSD: stage 1 to plane z0 (:func:`nursd3d_plane`), then stage 2, the standard RSD of that plane to each
+    depth (the planar operator with the plane's lattice field as relay samples, distances depths - z0, Supp. C).
+    -> [Z][N][N]."""
+    W = nursd3d_plane(P, xyz, center, pitch, N, z0, dz, Mz, omega)  # [F][N][N]
+    lat = voxel_lattice(center, pitch, N, [0.0])[0, :, :, :2].reshape(-1, 2)  # row y, column x
+    Pl = W.reshape(W.shape[0], -1).T  # [N*N][F] in the lattice's order
+    return nursd_forward(Pl, lat, center, pitch, N, np.asarray(depths, dtype=np.float64) - z0, omega)
 
 
 # --------------------------------------------------- a10-a11: adjoint, grad ---

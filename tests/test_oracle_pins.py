@@ -769,3 +769,81 @@ def test_nu_sfft_on_the_lattice_equals_srsd_and_at_unit_scale_equals_nursd():
     # and off the lattice at s > 1 it differs from SRSD's gridded input (the reason to fuse)
     assert rel(O.nu_sfft_forward(c["P"], xy, *args, scales, c["omega"]),
                O.srsd_forward(c["P"], xy, *args, scales, c["omega"])) > 1e-3
+
+
+# ---------------------------------------------------- 3D NURSD (non-planar relays) ----
+
+def _relay3d_case(on_grid, seed=41):
+    r = np.random.default_rng(seed)
+    N, pitch, dz, Mz, z0 = 6, 0.02, 0.015, 8, 0.1
+    L, F = 14, 2
+    if on_grid:
+        n = r.integers(-N // 2, N // 2, (L, 2))
+        nz = r.integers(-Mz // 4, Mz // 4, L)
+        xyz = np.column_stack([n * pitch, z0 + nz * dz])
+    else:
+        xyz = np.column_stack([r.uniform(-0.055, 0.055, (L, 2)), z0 + r.uniform(-0.028, 0.028, L)])
+    P = r.standard_normal((L, F)) + 1j * r.standard_normal((L, F))
+    om = 2 * math.pi * np.array([4e9, 5.5e9])
+    return P, xyz, (0.0, 0.0), pitch, N, z0, dz, Mz, om
+
+
+def test_3d_stage1_on_the_3d_grid_is_the_direct_sum_to_the_plane():
+    # samples on the lattice and on the z grid: the trigonometric interpolation is exact there, so the
+    # plane z0 holds sum_l P_l G(m delta - x_l, z0 - z_l) (G = 0 at the zero offset)
+    P, xyz, c, pitch, N, z0, dz, Mz, om = _relay3d_case(True)
+    W = O.nursd3d_plane(P, xyz, c, pitch, N, z0, dz, Mz, om)
+    m = O.index_set(N) * pitch
+    for f, w in enumerate(om):
+        k = w / O.C
+        want = np.zeros((N, N), complex)
+        for l in range(len(P)):
+            r = np.sqrt((m[None, :] - xyz[l, 0]) ** 2 + (m[:, None] - xyz[l, 1]) ** 2 + (z0 - xyz[l, 2]) ** 2)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                g = np.where(r > 0, np.exp(1j * k * r) / r, 0.0)
+            want += P[l, f] * g
+        assert rel(W[f], want) < 1e-12
+
+
+def test_3d_stage1_brute_force_tiny():
+    r = np.random.default_rng(42)
+    N, pitch, dz, Mz, z0 = 2, 0.03, 0.02, 4, 0.0
+    M = 2 * N
+    xyz = np.array([[0.004, -0.011, 0.013], [-0.017, 0.009, -0.006]])
+    P = (r.standard_normal((2, 1)) + 1j * r.standard_normal((2, 1)))
+    om = np.array([2 * math.pi * 5e9])
+    W = O.nursd3d_plane(P, xyz, (0.0, 0.0), pitch, N, z0, dz, Mz, om)[0]
+    k = om[0] / O.C
+    idx = list(range(-M // 2, M // 2))
+    idz = list(range(-Mz // 2, Mz // 2))
+
+    def g(jx, jy, jz):
+        rr = math.sqrt((jx * pitch) ** 2 + (jy * pitch) ** 2 + (jz * dz) ** 2)
+        return cmath.exp(1j * k * rr) / rr if rr > 0 else 0.0
+
+    for iy, my in enumerate(range(-N // 2, N // 2)):
+        for ix, mx in enumerate(range(-N // 2, N // 2)):
+            acc = 0j
+            for kz in idz:
+                for ky in idx:
+                    for kx in idx:
+                        U = sum(P[l, 0] * cmath.exp(-1j * (kx * 2 * math.pi * xyz[l, 0] / (M * pitch)
+                                                            + ky * 2 * math.pi * xyz[l, 1] / (M * pitch)
+                                                            + kz * 2 * math.pi * (xyz[l, 2] - z0) / (Mz * dz)))
+                                for l in range(2))
+                        G = sum(g(jx, jy, jz) * cmath.exp(-2j * math.pi * (kx * jx / M + ky * jy / M + kz * jz / Mz))
+                                for jz in idz for jy in idx for jx in idx)
+                        acc += U * G * cmath.exp(2j * math.pi * (kx * mx + ky * my) / M)
+            assert abs(W[iy, ix] - acc / (M * M * Mz)) < 1e-11 * (1 + abs(acc) / (M * M * Mz))
+
+
+def test_3d_nursd_stage2_is_the_direct_back_projection_of_the_plane():
+    P, xyz, c, pitch, N, z0, dz, Mz, om = _relay3d_case(False)
+    depths = np.array([0.5, 0.8])
+    V = O.nursd3d_forward(P, xyz, c, pitch, N, z0, dz, Mz, depths, om)
+    W = O.nursd3d_plane(P, xyz, c, pitch, N, z0, dz, Mz, om)
+    lat = O.voxel_lattice(c, pitch, N, [0.0])[0, :, :, :2].reshape(-1, 2)
+    for iz, z in enumerate(depths):
+        vox = np.column_stack([lat, np.full(len(lat), z - z0)])
+        d = O.fbp_direct(W.reshape(len(om), -1).T, lat, om, vox).reshape(N, N)
+        assert rel(V[iz], d) < 1e-12
