@@ -155,6 +155,9 @@ __global__ void __launch_bounds__(kClsPerCta * 32, 2) contract_kernel(const floa
 // global stores are contiguous across the warp.
 constexpr int kTmaWarps = 16, kStages = 3, kRows = 4;
 constexpr long long kWaitLimit = 1LL << 22;
+// Bound (mbarrier polls) of the data waits of the bulk-copy form; the default unless a test shortens it
+// (set_contract_wait_limit).  The drain after a time-out always uses kWaitLimit.
+__device__ long long g_contract_wait_limit = kWaitLimit;
 
 __device__ __forceinline__ unsigned sm_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -170,8 +173,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
                "l"(src), "r"(bytes), "r"(sm_addr(bar))
                : "memory");
 }
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  for (long long it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit = kWaitLimit) {
+  for (long long it = 0; it < limit; ++it) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -224,6 +227,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) contract_tma_kernel(const f
   constexpr int ZS = S::ZS;
   extern __shared__ __align__(16) unsigned char raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long wait_limit = g_contract_wait_limit;
   float2* myring = reinterpret_cast<float2*>(raw) + (size_t)warp * kStages * S::kStage;
   float4* myexp = reinterpret_cast<float4*>(raw + S::kRingBytes) + warp * 8 * kRows;
   // producer's source rows of its current unit (each slot is written and read by one lane only):
@@ -289,7 +293,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) contract_tma_kernel(const f
       for (int s = 0; s < 8; ++s) acc[i][s] = make_float2(0.f, 0.f);
     for (int ch = 0; ch < nchunk; ++ch) {
       const int st = cseq % kStages;
-      if (!mbar_wait(mybar + st, (cseq / kStages) & 1)) {
+      if (!mbar_wait(mybar + st, (cseq / kStages) & 1, wait_limit)) {
         ok = false;
         break;
       }
@@ -351,6 +355,15 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) contract_tma_kernel(const f
     }
   }
 }
+
+}  // namespace
+
+cudaError_t set_contract_wait_limit(long long polls, cudaStream_t s) {
+  const long long v = polls >= 0 ? polls : kWaitLimit;
+  return cudaMemcpyToSymbolAsync(g_contract_wait_limit, &v, sizeof(v), 0, cudaMemcpyHostToDevice, s);
+}
+
+namespace {
 
 template <int ZPL, bool CONJ>
 cudaError_t launch_tma(const float2* U, const float2* Gc, const int2* cls_pq, int ncls, int M, int F, int Z, float2* Y,

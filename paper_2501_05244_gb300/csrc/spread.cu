@@ -1,11 +1,11 @@
 // NUFFT type-1 spreading (Sec. 6, step 1): b[g][f] = sum_l P[l][f] phi_x phi_y.
 //
-// No atomics: one CTA owns a tile of the fine-grid window 16 cells wide and 8
-// rows high, for 32 channels; each of its 8 warps owns one tile row, each lane
+// No atomics: one CTA owns a tile of the fine-grid window 16 cells wide and ROWS
+// (4, 8 or 16, a plan setting) rows high, for 32 channels; each of its ROWS warps owns one tile row, each lane
 // one channel, and the row's 16 cells live in registers.  Samples are binned by (tile column,
 // edge flag, first footprint row), tile column major, the edge flag marking
 // footprints that cross into the next tile column.  So the samples that touch
-// the tile -- first rows ty*8-w+1 .. ty*8+7 in this tile column, and in the
+// the tile -- first rows ty*ROWS-w+1 .. ty*ROWS+ROWS-1 in this tile column, and in the
 // edge part of the column to its left (a footprint of w <= 8 cells crosses at
 // most one tile edge) -- are three contiguous slot ranges, none holding a sample
 // that misses the tile.  The CTA stages them in shared memory in chunks (the 32
@@ -25,8 +25,6 @@
 namespace nursd {
 namespace {
 
-constexpr int kRows = 8;       // tile height (rows); the tile is kTile cells wide
-constexpr int kWarps = kRows;  // one warp per tile row
 constexpr int kCh = 32;        // channels per CTA
 constexpr int kCap = 128;      // samples staged per chunk
 
@@ -63,8 +61,8 @@ __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
 // carries its x weights laid out on the tile's 16 cells (zeros outside its footprint), so the
 // warp adds it to every cell of its row with 16 packed FMAs and no branch on the offset; a
 // zero weight leaves a cell's sum unchanged, so the result equals the footprint-only sum.
-template <int KW>
-__global__ void __launch_bounds__(kWarps * 32, 4) spread_kernel(const float2* __restrict__ P, int F,
+template <int KW, int kRows>
+__global__ void __launch_bounds__(kRows * 32, 32 / kRows) spread_kernel(const float2* __restrict__ P, int F,
                                                                 const int* __restrict__ bin_start,
                                                                 const int* __restrict__ sorted_l,
                                                                 const int2* __restrict__ i0,
@@ -72,6 +70,7 @@ __global__ void __launch_bounds__(kWarps * 32, 4) spread_kernel(const float2* __
                                                                 float2* __restrict__ fine) {
   extern __shared__ __align__(16) unsigned char raw[];
   SpreadSmem& sm = *reinterpret_cast<SpreadSmem*>(raw);
+  constexpr int kWarps = kRows;  // one warp per tile row
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ty = blockIdx.x / tiles, tx = blockIdx.x % tiles;
   const int f0 = blockIdx.y * kCh;
@@ -179,32 +178,45 @@ __global__ void __launch_bounds__(kWarps * 32, 4) spread_kernel(const float2* __
   }
 }
 
-template <int KW>
+template <int KW, int kRows>
 cudaError_t launch_kw(const float2* P, int F, const int* bin_start, const int* sorted_l, const int2* i0,
                       const float* wts, int tiles, int W, float2* fine, cudaStream_t s) {
   const size_t smem = sizeof(SpreadSmem);
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(spread_kernel<KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(spread_kernel<KW, kRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   dim3 grid((W / kRows) * tiles, (F + kCh - 1) / kCh);
-  spread_kernel<KW><<<grid, kWarps * 32, smem, s>>>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine);
+  spread_kernel<KW, kRows><<<grid, kRows * 32, smem, s>>>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine);
   return cudaGetLastError();
+}
+
+template <int KW>
+cudaError_t launch_rows(const float2* P, int F, const int* bin_start, const int* sorted_l, const int2* i0,
+                        const float* wts, int tiles, int W, float2* fine, int rows, cudaStream_t s) {
+  switch (rows) {
+    case 4: return launch_kw<KW, 4>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, s);
+    case 16: return launch_kw<KW, 16>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, s);
+    default: return launch_kw<KW, 8>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, s);
+  }
 }
 
 }  // namespace
 
+bool spread_rows_supported(int rows) { return rows == 4 || rows == 8 || rows == 16; }
+
 cudaError_t launch_spread(const float2* P, int F, const int* bin_start, const int* sorted_l, const int2* i0,
-                          const float* wts, int width, int tiles, int W, float2* fine, cudaStream_t s) {
-  if (W != tiles * kTile) return cudaErrorInvalidValue;
+                          const float* wts, int width, int tiles, int W, float2* fine, cudaStream_t s, int rows) {
+  if (W != tiles * kTile || !spread_rows_supported(rows) || W % rows != 0) return cudaErrorInvalidValue;
   switch (width) {
-    case 4: return launch_kw<4>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, s);
-    case 5: return launch_kw<5>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, s);
-    case 6: return launch_kw<6>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, s);
-    case 7: return launch_kw<7>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, s);
-    case 8: return launch_kw<8>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, s);
+    case 4: return launch_rows<4>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, rows, s);
+    case 5: return launch_rows<5>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, rows, s);
+    case 6: return launch_rows<6>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, rows, s);
+    case 7: return launch_rows<7>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, rows, s);
+    case 8: return launch_rows<8>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, rows, s);
     default: return cudaErrorInvalidValue;
   }
 }

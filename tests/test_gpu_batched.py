@@ -105,3 +105,60 @@ def test_batched_workload_of_64_uneven_reconstructions():
     for b in {int(np.argmin(sizes)), int(np.argmax(sizes)), 7, 40}:
         plan.set_points(xys[b])
         assert rel(outs[b].cpu().numpy(), plan.forward(hists[b]).cpu().numpy()) < 1e-6, b
+
+
+@pytest.mark.parametrize("streams,rows", [(1, 8), (3, 4), (8, 16), (2, 16)])
+def test_batched_equals_single_calls_at_every_stream_count_and_tile_height(streams, rows):
+    # the items run round-robin on `streams` streams with their own workspaces; the spread's tile
+    # height changes only the launch shape
+    sizes = [700, 1, 0, 2049, 33, 400]
+    c = small_batch(sizes, seed=11)
+    plan = make_plan(c, len(sizes))
+    plan.tune("batch_streams", streams)
+    plan.tune("spread_rows", rows)
+    assert plan.tuning() == {"spread_rows": rows, "batch_streams": streams}
+    xys = [torch.from_numpy(x).cuda() for x in c["xys"]]
+    hists = [torch.from_numpy(h).cuda() for h in c["hists"]]
+    outs = plan.forward_batched(xys, hists)
+    single_plan = make_plan(c, 1)
+    for b in range(len(sizes)):
+        single_plan.set_points(xys[b])
+        single = single_plan.forward(hists[b]).cpu().numpy()
+        if sizes[b]:
+            assert rel(outs[b].cpu().numpy(), single) < 1e-6, b
+        else:
+            assert float(outs[b].abs().max()) == 0.0
+    # the plan keeps the last item's points, as a single call would
+    assert rel(plan.forward(hists[-1]).cpu().numpy(), outs[-1].cpu().numpy()) < 1e-6
+    assert plan.sync_status() == 0
+
+
+def test_unsupported_tunable_values_are_refused():
+    c = small_batch([10, 20])
+    plan = make_plan(c, 2)
+    for name, value in (("spread_rows", 6), ("batch_streams", 0), ("batch_streams", 17)):
+        with pytest.raises(nursd.NursdError) as err:
+            plan.tune(name, value)
+        assert err.value.status == nursd.nursd.NURSD_ERR_UNSUPPORTED
+
+
+def test_autotuner_keeps_the_results_and_caches_its_choice(tmp_path):
+    from paper_2501_05244_gb300.autotune import autotune
+
+    sizes = [300, 50, 1200, 800]
+    c = small_batch(sizes, seed=12)
+    plan = make_plan(c, len(sizes))
+    xys = [torch.from_numpy(x).cuda() for x in c["xys"]]
+    hists = [torch.from_numpy(h).cuda() for h in c["hists"]]
+    outs = [plan.empty_output() for _ in sizes]
+    plan.forward_batched(xys, hists, outs)
+    ref = [o.cpu().numpy() for o in outs]
+    path = str(tmp_path / "tune.json")
+    r = autotune(plan, lambda: plan.forward_batched(xys, hists, outs), workload="test", cache_path=path, reps=2)
+    assert not r["cached"] and r["choice"]["spread_rows"] in (4, 8, 16) and 1 <= r["choice"]["batch_streams"] <= 16
+    plan.forward_batched(xys, hists, outs)
+    for o, want in zip(outs, ref):
+        assert rel(o.cpu().numpy(), want) < 1e-6
+    plan2 = make_plan(c, len(sizes))
+    r2 = autotune(plan2, lambda: None, workload="test", cache_path=path)
+    assert r2["cached"] and plan2.tuning() == r["choice"]
