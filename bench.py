@@ -47,6 +47,9 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=60)
     ap.add_argument("--no-graph", action="store_true", help="time eager steps instead of a captured CUDA graph")
+    ap.add_argument("--shard", choices=["replicas", "depth"], default="replicas",
+                    help="replicas: one reconstruction per GPU (weak scaling); depth: one reconstruction whose "
+                         "depth planes are split over the GPUs and gathered (strong scaling)")
     ap.add_argument("--no-rows", action="store_true",
                     help="skip the per-row measurements (type-2 voxels, SRSD, adjoint, gradients, batched)")
     ap.add_argument("--workload", choices=["spad", "grid128", "spad-z8", "spad-n128"], default="spad",
@@ -468,6 +471,19 @@ def bytes_srsd(N: int, F: int, scales, w: int = 6) -> int:
     return b
 
 
+def bytes_nusfft(L: int, N: int, F: int, scales, w: int = 6) -> int:
+    """NU-SFFT spectra: spread (phasors in, window out), the window's rows transformed to 2M bins (in,
+    out), the columns to the 2M x 2M spectrum (in, out), and per depth the spectrum block its taps
+    reach (coordinates kappa / s on the 2M grid), its table and Y_z."""
+    M, W = 2 * N, fine_window(N)
+    Lg = 2 * M
+    b = 8 * (L * F + W * W * F + W * W * F + W * Lg * F + W * Lg * F + Lg * Lg * F)
+    for sc in scales:
+        R = (math.ceil((M // 2 - 1) / sc - 0.5 * w) + w - 1) - math.ceil((-M // 2) / sc - 0.5 * w) + 1
+        b += (R * R * F + n_classes(N) * F + M * M) * 8
+    return b
+
+
 def hbm_row(bytes_: int, ms: float, peak: float) -> dict:
     gbs = bytes_ / (ms / 1e3) / 1e9
     return {"algorithmic_bytes": int(bytes_), "achieved_gbs": gbs, "hbm_frac": gbs / peak}
@@ -658,6 +674,11 @@ def measure_rows(wl, peak, stages_ms=None):
         hists = [device_histograms(xys[b], *scenes[b], gb.T, gb.dt, gb.t0, seed=BASE_SEED + 500 + b)
                  for b in range(len(sizes))]
         outs = [plan.empty_output() for _ in sizes]
+        from paper_2501_05244_gb300.autotune import autotune
+
+        tuned = autotune(plan, lambda: plan.forward_batched(xys, hists, outs), workload="64 items, L 4096-65536",
+                         cache_path=os.path.join(tempfile.gettempdir(), f"nursd_tune_{os.getpid()}.json"),
+                         use_cache=False, reps=3)
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):
@@ -686,7 +707,8 @@ def measure_rows(wl, peak, stages_ms=None):
                             "128^2 x 64 each" % int(sizes.sum()),
                 "ms_graph": ms_graph, "recon_per_s": len(sizes) / (ms_graph / 1e3),
                 "voxel_freq_per_s": units / (ms_graph / 1e3), **hbm_row(b, ms_graph, peak),
-                "ms_64_single_calls": ms_single, "speedup_vs_single_calls": ms_single / ms_graph}
+                "ms_64_single_calls": ms_single, "speedup_vs_single_calls": ms_single / ms_graph,
+                "autotuned": {"choice": tuned["choice"], "ms_by_setting": tuned["results"]}}
 
     def cufft():
         # comparison only (timed, not part of the path): cuFFT through torch.fft on the full
@@ -717,6 +739,41 @@ def measure_rows(wl, peak, stages_ms=None):
     guarded("a10_adjoint", adjoint)
     guarded("a11_gradients", grad)
     guarded("a12_batched", batched)
+    def nusfft():
+        # next row 2, second half: SRSD taken directly at the 65,536 keystone samples (NU-SFFT)
+        depths = srsd_depths_c3b()
+        pitches = srsd_pitches_c3b(depths)
+        plan = nursd.Plan(g.N, g.pitch, g.center, depths, om, wt, T=g.T, t0=g.t0, dt=g.dt, max_points=L,
+                          srsd_pitch=pitches)
+        plan.set_points(d_xy)
+        P = plan.temporal_dft(d_hist)
+        out = plan.empty_output()
+        plan.srsd_forward_nonuniform(P, out)  # first call: tables and workspace
+        ms = _time(lambda: plan.srsd_forward_nonuniform(P, out), 3, 1, stream)
+        assert plan.sync_status() == 0
+        plan.close()
+        Z = len(depths)
+        b = bytes_nusfft(L, g.N, g.F, pitches / g.pitch) + bytes_idft(Z, g.N)
+        return {"workload": "65,536 keystone samples -> 256^2 x 128 planes over 1-4 m, pitch 8 -> 32 mm, F=128, "
+                            "scaled DFT at the samples (NU-SFFT)",
+                "ms": ms, "voxel_freq_per_s": Z * g.N * g.N * g.F / (ms / 1e3), **hbm_row(b, ms, peak)}
+
+    def resample():
+        # next row 4: keep every 5th relay sample of a 256 x 256 x 128 phasor grid, re-grid linearly
+        N, F, D = g.N, g.F, 5
+        grid = torch.from_numpy(random_phasors(N * N, F, seed=BASE_SEED + 32).reshape(N, N, F)).cuda()
+        kept = nursd.subsample(grid, D)
+        full = torch.empty_like(grid)
+        ms_s = _time(lambda: nursd.subsample(grid, D, out=kept), 20, 3, stream)
+        ms_u = _time(lambda: nursd.upsample(kept, N, D, linear=True, out=full), 20, 3, stream)
+        nc = kept.shape[0]
+        return {"workload": "256 x 256 x 128 phasor grid, every 5th sample kept (52 x 52), linear re-gridding",
+                "subsample_ms": ms_s, "upsample_ms": ms_u,
+                "subsample": hbm_row(8 * 2 * nc * nc * F, ms_s, peak),
+                "upsample": hbm_row(8 * (nc * nc * F + N * N * F), ms_u, peak)}
+
+    guarded("f2_nu_sfft", nusfft)
+    guarded("f4_subsample_regrid", resample)
     guarded("f1_single_illumination", illuminated)
     guarded("f2_srsd_points", srsd_points)
     return rows
@@ -956,6 +1013,97 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_sharded(args, rank, world, local):
+    """One spad-65k reconstruction per step with its depth planes split over the ranks (each rank holds
+    its slice of the transfer table) and gathered in depth order by an all_gather (NCCL): strong
+    scaling, eager steps (the gather is a collective between the ranks' launches)."""
+    import torch
+
+    from paper_2501_05244_gb300.nursd import phasor_frequencies
+    from paper_2501_05244_gb300.sharding import DepthShardedPlan, depth_slices
+    from workloads import BASE_SEED, workload_c2
+    import paper_2501_05244_gb300 as nursd
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", device_id=torch.device("cuda", local))
+    nursd.build()
+    wl = workload_c2(seed=BASE_SEED + 2)  # the same measurement on every rank
+    g = wl.geom
+    L = len(wl.xy)
+    om, wt = phasor_frequencies(g.lambda_c, g.dt, g.t_pad, g.F)
+    sp = DepthShardedPlan(g.N, g.pitch, g.center, g.depths, om, wt, rank=rank, world=world, dist=dist, T=g.T,
+                          t0=g.t0, dt=g.dt, max_points=L)
+    d_xy = torch.from_numpy(wl.xy).cuda()
+    d_hist = torch.from_numpy(wl.hist).cuda()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        sp.reconstruct(d_xy, d_hist)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        vol = sp.reconstruct(d_xy, d_hist)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = reduce_max(e0.elapsed_time(e1) / args.steps, dist, "cuda")
+    launches = (sp.plan.launch_count if sp.plan is not None else 0)
+    # end to end: pinned host inputs uploaded, the reconstruction, the gathered volume downloaded
+    h_hist = torch.from_numpy(wl.hist).pin_memory()
+    h_xy = torch.from_numpy(wl.xy).pin_memory()
+    h_out = torch.empty(tuple(vol.shape), dtype=vol.dtype).pin_memory()
+    ke = max(1, min(args.e2e_steps, args.steps))
+    barrier()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(ke):
+        d_hist.copy_(h_hist, non_blocking=True)
+        d_xy.copy_(h_xy, non_blocking=True)
+        vol = sp.reconstruct(d_xy, d_hist)
+        h_out.copy_(vol, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = reduce_max(f0.elapsed_time(f1) / ke, dist, "cuda")
+    units = g.Z * g.N * g.N * g.F
+    line = {
+        "metric": METRIC, "value": units / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+        "dtype": "c64", "data": "synthetic (seeded keystone layout, Poisson histograms of 5 point scatterers)",
+        "config": {"workload": WORKLOAD, "L": L, "T": g.T, "F": g.F, "N": g.N, "Z": g.Z,
+                   "parallelism": f"depth-sharded x{world} ({[b - a for a, b in depth_slices(g.Z, world)]} planes "
+                                  f"per rank, all_gather of the planes)",
+                   "launch": "eager nursd_reconstruct calls on each rank's depth slice, then the gather",
+                   "l2": "inputs larger than L2; no flush"},
+        "recon_per_s": 1e3 / ms,
+        "gpu_launches": int(launches),
+        "e2e": {"value": units / (ms_e2e / 1e3), "unit": UNIT, "ms_per_step": ms_e2e,
+                "h2d_bytes_per_step": int(h_hist.numel() * 4 + h_xy.numel() * 4),
+                "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size())},
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sp.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def run_reference(args, rank, world, local):
     """The FP64 oracle (direct back-projection) on all host cores: each step back-projects one random
     voxel x 16 frequencies per worker process over all relay samples."""
@@ -1016,6 +1164,8 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world, local)
+    elif args.shard == "depth":
+        run_sharded(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 
