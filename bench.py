@@ -772,6 +772,36 @@ def measure_rows(wl, peak, stages_ms=None):
                 "subsample": hbm_row(8 * 2 * nc * nc * F, ms_s, peak),
                 "upsample": hbm_row(8 * (nc * nc * F + N * N * F), ms_u, peak)}
 
+    def nursd3d():
+        # next row 3: 3D NURSD on a non-planar relay: the 65,536 keystone samples bent into a cylinder
+        # (heights within +-5 cm of the reference plane), 128^2 x 64 planes 0.5-3 m beyond it, F = 64,
+        # 16 z offsets of 1.5 cm
+        N, F, Z, Mz, dz = 128, 64, 64, 16, 0.015
+        xy = relay_keystone(seed=BASE_SEED + 7)
+        h = (0.05 * ((xy[:, 0].astype(np.float64) / 0.985) ** 2 * 2.0 - 1.0)).astype(np.float32)
+        om3, wt3 = om[::2].copy(), wt[::2].copy()
+        plan = nursd.Plan(N, 2.0 / N, (0.0, 0.0), np.linspace(0.5, 3.0, Z), om3, wt3, max_points=len(xy))
+        plan.enable_3d(dz, Mz)
+        plan.set_points_3d(torch.from_numpy(xy).cuda(), torch.from_numpy(h).cuda())
+        P = torch.from_numpy(random_phasors(len(xy), F, seed=BASE_SEED + 8)).cuda()
+        out = plan.empty_output()
+        plan.profile(True)
+        ms = _time(lambda: plan.forward_3d(P, out), 5, 2, stream)
+        st = _stage_ms(plan, 7)
+        assert plan.sync_status() == 0
+        plan.close()
+        M, W = 2 * N, fine_window(N)
+        Wz = min(2 * Mz, Mz + 6 + 2)
+        b = (Wz * (8 * (len(xy) * F) + bytes_type1(len(xy), F, N))  # per z slice: phasors, spread, lateral passes
+             + 8 * (Wz * M * M * F + M * M * Mz * F)  # the z pass
+             + 8 * (2 * M * M * Mz * F + M * M * F)  # the kz sum with the 3D table
+             + 8 * (M * M * F + 2 * M * N * F + N * N * F) + 8 * (N * N * F + 2 * N * M * F + M * M * F)  # crop, pad
+             + bytes_contract(F, Z, N) + bytes_idft(Z, N))  # stage 2
+        return {"workload": "65,536 keystone samples on a cylindrical relay (heights +-5 cm), F=64, 128^2 x 64 planes "
+                            "0.5-3 m, Mz=16 offsets of 1.5 cm",
+                "ms": ms, "voxel_freq_per_s": Z * N * N * F / (ms / 1e3), **hbm_row(b, ms, peak), "stages_ms": st}
+
+    guarded("f3_nursd3d", nursd3d)
     guarded("f2_nu_sfft", nusfft)
     guarded("f4_subsample_regrid", resample)
     guarded("f1_single_illumination", illuminated)
@@ -1047,6 +1077,7 @@ def run_sharded(args, rank, world, local):
     for _ in range(args.warmup):
         sp.reconstruct(d_xy, d_hist)
     torch.cuda.synchronize()
+    launches0 = sp.plan.launch_count if sp.plan is not None else 0
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
@@ -1060,7 +1091,7 @@ def run_sharded(args, rank, world, local):
     barrier()
     clk = clocks.stop()
     ms = reduce_max(e0.elapsed_time(e1) / args.steps, dist, "cuda")
-    launches = (sp.plan.launch_count if sp.plan is not None else 0)
+    launches = (sp.plan.launch_count if sp.plan is not None else 0) - launches0  # this rank's, the timed steps
     # end to end: pinned host inputs uploaded, the reconstruction, the gathered volume downloaded
     h_hist = torch.from_numpy(wl.hist).pin_memory()
     h_xy = torch.from_numpy(wl.xy).pin_memory()

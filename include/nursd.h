@@ -410,7 +410,8 @@ int64_t nursd_launch_count(nursd_plan_t plan);
  * The first call on each device does a one-time set-up with that device
  * current: it looks up the array's device address and fills its fixed tables
  * with a small kernel, synchronising `stream`.  Make that first call before any
- * stream capture.  Every call shares the same array and leaves its contents
+ * stream capture.  The set-up is repeated when the device's current context
+ * is a new one (after cudaDeviceReset, say), whose copy of the array is new.  Every call shares the same array and leaves its contents
  * behind, so calls that overlap on the GPU (different streams, or different
  * host threads) race and must be serialised by the caller.  Samples outside
  * |x - c| <= N pitch / 2 get zero weight; they are not reported.
@@ -424,6 +425,62 @@ int nursd_nufft1_noalloc(int32_t N, double pitch, double center_x, double center
  * Returns NURSD_OK, NURSD_ERR_POINT_OUT_OF_RANGE or NURSD_ERR_TIMEOUT.
  */
 int nursd_sync_status(nursd_plan_t plan, nursd_stream_t stream);
+
+/*
+ * 3D NURSD for non-planar relay surfaces (Sec. 3D NURSD, Eq. 3D_NURSD with the 3D RSD of Eq. 3d_rsd;
+ * stage 2 the standard RSD, Supp. C).  Relay samples lie at (x_l, y_l) with a height h_l = z_l - z0
+ * above or below a reference plane z0; the plan's depths are then the distances of the voxel planes
+ * from z0 (all > 0).  Stage 1 takes the field of every frequency on the N x N lattice of plane z0,
+ *   W_f[m] = (M^2 Mz)^-1 sum_k U_f(k) Ghat3_f(k) exp(+2 pi i (kx mx + ky my) / M),  m in I_N^2,
+ * with U_f the 3D type-1 sum of the samples at theta_l = (2 pi (x_l - c_x) / (M delta),
+ * 2 pi (y_l - c_y) / (M delta), 2 pi h_l / (Mz dz)), k in I_M^2 x I_Mz, and Ghat3_f the 3D DFT of
+ * G = exp(+i k_f r) / r on the offsets (j delta, jz dz), j in I_M^2, jz in I_Mz (G = 0 at the zero
+ * offset); stage 2 propagates W_f from z0 to every plane and sums over frequency as nursd_forward_phasor
+ * does for lattice samples.  Stage 1 is a 3D NUFFT: the ES spread along z (fine z grid of pitch dz / 2)
+ * is applied per fine z cell to the phasors, each cell spread and transformed laterally like the planar
+ * operator, then transformed along z.
+ *
+ * nursd_enable_3d: builds the 3D table (Mz a power of two, 8 <= Mz <= 512, Mz >= kernel_width + 2;
+ *   allocates about M^2 F (2 Mz + kernel_width + 2) complex values); heights must satisfy
+ *   |h| <= Mz dz / 4.  Synchronises the host like plan creation.  A second call with the same (dz, Mz)
+ *   does nothing; other values give INVALID_ARG.
+ * nursd_set_points_3d: d_xy [L][2] metres, d_h [L] heights (float32, device); sorts like
+ *   nursd_set_points; a height beyond the range sets the out-of-range status bit and gets no weight.
+ * nursd_forward_3d: d_phasor [L][F] -> d_out [Z][N][N] (complex64, or |V| with
+ *   NURSD_OUTPUT_MAGNITUDE).  INVALID_ARG unless nursd_set_points_3d gave the current points.
+ */
+int nursd_enable_3d(nursd_plan_t plan, double dz, int32_t Mz, nursd_stream_t stream);
+int nursd_set_points_3d(nursd_plan_t plan, int32_t L, const float* d_xy, const float* d_h, nursd_stream_t stream);
+int nursd_forward_3d(nursd_plan_t plan, const nursd_c64* d_phasor, void* d_out, nursd_stream_t stream);
+
+/*
+ * Tunables of a plan (no counterpart in the paper: launch shapes of this library), set by the
+ * autotuner of the Python package or by hand; they change only speed, never results beyond FP32
+ * summation order.  NURSD_TUNE_SPREAD_ROWS: height in fine cells (4, 8 or 16) of the spread's tiles
+ * (default 8).  NURSD_TUNE_BATCH_STREAMS: streams (1 .. 16) over which nursd_forward_batched runs its
+ * items' point sorts, spreads and FFT passes side by side (default 4).  nursd_plan_tune returns
+ * UNSUPPORTED for a value outside those sets, INVALID_ARG for an unknown parameter.
+ */
+#define NURSD_TUNE_SPREAD_ROWS 0
+#define NURSD_TUNE_BATCH_STREAMS 1
+int nursd_plan_tune(nursd_plan_t plan, int32_t param, int32_t value);
+int nursd_plan_get_tune(nursd_plan_t plan, int32_t param, int32_t* h_value);
+
+/*
+ * Test hooks (no counterpart in the paper), for the failure paths of this library.
+ *
+ * nursd_test_fail_allocation(after): process-wide; the after-th device allocation made by libnursd
+ * from now on (1 = the next one) fails as if the device were out of memory, so that the call making
+ * it returns NURSD_ERR_OOM and releases what it had allocated.  after <= 0 disarms the hook.
+ *
+ * nursd_test_set_wait_limit(polls, stream): on the current device, every plan's bulk-copy contraction
+ * gives up its data waits after `polls` mbarrier polls (0: at the first wait, without polling; a
+ * negative value restores the default of 2^22); a wait that runs out sets the plan's status word so
+ * that nursd_sync_status returns NURSD_ERR_TIMEOUT, lets the warp's own copies in flight land (with
+ * the default bound) and returns, leaving that call's output incomplete.  Stream-ordered on `stream`.
+ */
+int nursd_test_fail_allocation(int32_t after);
+int nursd_test_set_wait_limit(int64_t polls, nursd_stream_t stream);
 
 /*
  * Subsampled acquisition (Methods: Sampling Criteria for NLOS, Eq. upsample2): a relay grid may be

@@ -1,5 +1,6 @@
 // C ABI of libnursd: plan lifecycle, argument validation and the launch
 // sequences of each entry point (see include/nursd.h for the contract).
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -48,13 +49,53 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   }
 }
 
+// Test hook (nursd_test_fail_allocation): the device allocation that brings the countdown to zero fails.
+std::atomic<int> g_alloc_countdown{-1};
+
+// cudaMalloc, unless the test hook makes this allocation fail.
+cudaError_t dev_malloc(void** ptr, size_t bytes) {
+  int c = g_alloc_countdown.load();
+  while (c > 0 && !g_alloc_countdown.compare_exchange_weak(c, c - 1)) {
+  }
+  if (c == 1) {
+    *ptr = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(ptr, bytes);
+}
+
 // ES kernel phi(z) = exp(beta (sqrt(1 - z^2) - 1)) on |z| < 1.
 double es_kernel(double z, double beta) { return std::fabs(z) < 1.0 ? std::exp(beta * (std::sqrt(1.0 - z * z) - 1.0)) : 0.0; }
 
 }  // namespace
 
+// The per-call workspace of the point sort, the type-1 passes and the inverse passes.  The batched form
+// keeps one per concurrent stream and swaps it into the plan while it enqueues that stream's launches
+// (launches read the pointers when they are enqueued).
+struct Workspace {
+  int* bin_of = nullptr;
+  int2* i0_orig = nullptr;
+  int* slot_of = nullptr;
+  float* w_orig = nullptr;
+  int* counts = nullptr;
+  int* bin_start = nullptr;
+  int* sorted_l = nullptr;
+  int2* i0_sorted = nullptr;
+  float* w_sorted = nullptr;
+  float2* frac_orig = nullptr;
+  float2* frac_sorted = nullptr;
+  float2* fine = nullptr;
+  float2* R1 = nullptr;
+  float2* T1 = nullptr;
+};
+
+constexpr int kMaxBatchStreams = 16;
+
 struct nursd_plan_s {
   int device = 0;
+  // tunables (nursd_plan_tune): spread tile height; streams of the batched form
+  int spread_rows = 8;
+  int batch_streams = 4;
   // geometry
   int N = 0, M = 0, nf = 0, Z = 0, F = 0, T = 0, w = 0, W = 0, tiles = 0, g0 = 0, ncls = 0, maxL = 0, L = -1;
   double pitch = 0, cx = 0, cy = 0, t0 = 0, dt = 0;
@@ -101,6 +142,17 @@ struct nursd_plan_s {
   bool nu_ready = false;
   std::vector<float> nu_host_f;
   std::vector<int> nu_host_i;
+  // 3D NURSD (nursd_enable_3d): Mz z offsets of pitch dz, the window of Wz fine z cells from gz0, the 3D
+  // transfer table [M][M][Mz][F], 1 / psi_hat_z [Mz], the slices' spectra [Wz][M][M][F], the 3D spectrum
+  // [M][M][Mz][F], the plane's spectrum [M][M][F] and lattice field [F][N][N], a half transform [N][M][F],
+  // the slice phasors [maxL][F] and the samples' fine z coordinates [maxL] (slot order)
+  int nd_Mz = 0, nd_Wz = 0, nd_gz0 = 0;
+  double nd_dz = 0.0;
+  float2 *nd_G3 = nullptr, *nd_U3w = nullptr, *nd_U3 = nullptr, *nd_What = nullptr, *nd_field = nullptr;
+  float2 *nd_T = nullptr, *nd_Pz = nullptr;
+  float *nd_decz = nullptr, *nd_uz = nullptr;
+  bool nd_points = false;  // the current points carry heights (nursd_set_points_3d)
+  std::vector<float> nd_host;
   float2* Gs = nullptr;
   float2* chirp = nullptr;
   float2* bhat = nullptr;
@@ -143,7 +195,7 @@ struct nursd_plan_s {
   bool alloc(T*& p, size_t count) {
     if (count == 0) count = 1;
     void* q = nullptr;
-    if (cudaMalloc(&q, sizeof(T) * count) != cudaSuccess) {
+    if (dev_malloc(&q, sizeof(T) * count) != cudaSuccess) {
       cudaGetLastError();
       return false;
     }
@@ -166,10 +218,54 @@ struct nursd_plan_s {
   // side stream of nursd_reconstruct (the point sort runs there, beside the temporal transform)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // batched form: workspaces of streams 1 .. kMaxBatchStreams - 1 (stream 0 is the caller's, with the
+  // plan's own workspace), their streams and fork / join events
+  Workspace bws[kMaxBatchStreams];
+  cudaStream_t bstream[kMaxBatchStreams] = {};
+  cudaEvent_t bev_fork = nullptr, bev_join[kMaxBatchStreams] = {};
+  Workspace own() const {
+    Workspace w;
+    w.bin_of = bin_of;
+    w.i0_orig = i0_orig;
+    w.slot_of = slot_of;
+    w.w_orig = w_orig;
+    w.counts = counts;
+    w.bin_start = bin_start;
+    w.sorted_l = sorted_l;
+    w.i0_sorted = i0_sorted;
+    w.w_sorted = w_sorted;
+    w.frac_orig = frac_orig;
+    w.frac_sorted = frac_sorted;
+    w.fine = fine;
+    w.R1 = R1;
+    w.T1 = T1;
+    return w;
+  }
+  void use(const Workspace& w) {
+    bin_of = w.bin_of;
+    i0_orig = w.i0_orig;
+    slot_of = w.slot_of;
+    w_orig = w.w_orig;
+    counts = w.counts;
+    bin_start = w.bin_start;
+    sorted_l = w.sorted_l;
+    i0_sorted = w.i0_sorted;
+    w_sorted = w.w_sorted;
+    frac_orig = w.frac_orig;
+    frac_sorted = w.frac_sorted;
+    fine = w.fine;
+    R1 = w.R1;
+    T1 = w.T1;
+  }
   ~nursd_plan_s() {
     if (ev_fork) cudaEventDestroy(ev_fork);
     if (ev_join) cudaEventDestroy(ev_join);
     if (side) cudaStreamDestroy(side);
+    if (bev_fork) cudaEventDestroy(bev_fork);
+    for (int k = 0; k < kMaxBatchStreams; ++k) {
+      if (bev_join[k]) cudaEventDestroy(bev_join[k]);
+      if (bstream[k]) cudaStreamDestroy(bstream[k]);
+    }
     for (auto& v : ev)
       for (auto& e : v) {
         cudaEventDestroy(e.first);
@@ -286,10 +382,11 @@ int build_table(nursd_plan_s* p, bool srsd, cudaStream_t s) {
   float2 *g = nullptr, *tmp = nullptr;
   double *dz = nullptr, *dk = nullptr, *dp = nullptr;
   int rc = NURSD_OK;
-  if (cudaMalloc(&g, sizeof(float2) * per_depth * ZB) != cudaSuccess ||
-      cudaMalloc(&tmp, sizeof(float2) * per_depth * ZB) != cudaSuccess ||
-      cudaMalloc(&dz, sizeof(double) * Z) != cudaSuccess || cudaMalloc(&dk, sizeof(double) * F) != cudaSuccess ||
-      cudaMalloc(&dp, sizeof(double) * Z) != cudaSuccess) {
+  if (dev_malloc((void**)&g, sizeof(float2) * per_depth * ZB) != cudaSuccess ||
+      dev_malloc((void**)&tmp, sizeof(float2) * per_depth * ZB) != cudaSuccess ||
+      dev_malloc((void**)&dz, sizeof(double) * Z) != cudaSuccess ||
+      dev_malloc((void**)&dk, sizeof(double) * F) != cudaSuccess ||
+      dev_malloc((void**)&dp, sizeof(double) * Z) != cudaSuccess) {
     cudaGetLastError();
     rc = NURSD_ERR_OOM;
   }
@@ -348,7 +445,7 @@ int build_srsd_chirps(nursd_plan_s* p, cudaStream_t s) {
     }
   }
   float2* db = nullptr;
-  if (cudaMalloc(&db, sizeof(float2) * b.size()) != cudaSuccess) {
+  if (dev_malloc((void**)&db, sizeof(float2) * b.size()) != cudaSuccess) {
     cudaGetLastError();
     return NURSD_ERR_OOM;
   }
@@ -426,7 +523,7 @@ int run_nufft1(nursd_plan_s* p, const float2* phasor, float2* spec, cudaStream_t
   {
     StageTimer t(p, NURSD_STAGE_SPREAD, s, 1);
     e = launch_spread(phasor, F, p->bin_start, slot_ordered ? nullptr : p->sorted_l, p->i0_sorted, p->w_sorted, p->w,
-                      p->tiles, W, p->fine, s);
+                      p->tiles, W, p->fine, s, p->spread_rows);
   }
   if (e == cudaSuccess) {  // FFT along x of every window row, keep kx in I_M
     StageTimer t(p, NURSD_STAGE_FFT_X, s, 1);
@@ -658,7 +755,8 @@ int run_nusfft_spectra(nursd_plan_s* p, const float2* phasor, cudaStream_t s) {
   cudaError_t e;
   {
     StageTimer t(p, NURSD_STAGE_SPREAD, s, 1);
-    e = launch_spread(phasor, F, p->bin_start, p->sorted_l, p->i0_sorted, p->w_sorted, p->w, p->tiles, W, p->fine, s);
+    e = launch_spread(phasor, F, p->bin_start, p->sorted_l, p->i0_sorted, p->w_sorted, p->w, p->tiles, W, p->fine, s,
+                      p->spread_rows);
   }
   if (e == cudaSuccess) {  // along x of every window row: [W][W][F] -> [W][2M][F]
     StageTimer t(p, NURSD_STAGE_SRSD, s, 2);
@@ -699,6 +797,48 @@ int run_nusfft_spectra(nursd_plan_s* p, const float2* phasor, cudaStream_t s) {
                                        p->ncls, p->Y, s);
   }
   return from_cuda(e);
+}
+
+// The 3D transfer table Ghat3_f(k) = DFT_3[G(j delta, jz dz)], k in I_M^2 x I_Mz, stored [ky][kx][kz][f]:
+// the kernel sampled on the offset grid (G = 0 at the zero offset), the lateral passes, then along jz.
+int build_table_3d(nursd_plan_s* p, cudaStream_t s) {
+  const int M = p->M, F = p->F, Mz = p->nd_Mz;
+  const size_t n = (size_t)M * M * Mz * F;
+  float2 *g = nullptr, *tmp = nullptr;
+  double *djz = nullptr, *dk = nullptr;
+  int rc = NURSD_OK;
+  if (dev_malloc((void**)&g, sizeof(float2) * n) != cudaSuccess || dev_malloc((void**)&tmp, sizeof(float2) * n) != cudaSuccess ||
+      dev_malloc((void**)&djz, sizeof(double) * Mz) != cudaSuccess || dev_malloc((void**)&dk, sizeof(double) * F) != cudaSuccess) {
+    cudaGetLastError();
+    rc = NURSD_ERR_OOM;
+  }
+  std::vector<double> jz(Mz), k(F);
+  for (int i = 0; i < Mz; ++i) jz[i] = (i - Mz / 2) * p->nd_dz;
+  const double kmul = (p->flags & NURSD_CONFOCAL) ? 2.0 : 1.0;
+  for (int f = 0; f < F; ++f) k[f] = kmul * p->omega[f] / kC;
+  if (rc == NURSD_OK) rc = from_cuda(cudaMemcpyAsync(djz, jz.data(), sizeof(double) * Mz, cudaMemcpyHostToDevice, s));
+  if (rc == NURSD_OK) rc = from_cuda(cudaMemcpyAsync(dk, k.data(), sizeof(double) * F, cudaMemcpyHostToDevice, s));
+  const int C = Mz * F, logM = ilog2(M);
+  if (rc == NURSD_OK)  // g[jy][jx][jz F + f] with r = sqrt(|j delta|^2 + (jz dz)^2)
+    rc = from_cuda(launch_gtf_generate(g, M, p->pitch, djz, Mz, dk, F, s));
+  if (rc == NURSD_OK)  // the zero offset (index M/2, M/2, Mz/2), where r = 0: G = 0
+    rc = from_cuda(cudaMemsetAsync(g + ((size_t)(M / 2) * M + M / 2) * C + (size_t)(Mz / 2) * F, 0,
+                                   sizeof(float2) * F, s));
+  if (rc == NURSD_OK)
+    rc = from_cuda(axis_pass(p, g, tmp, logM, false, C, M, (long long)M * C, C, (long long)M * C, C, M, -M / 2, M,
+                             -M / 2, nullptr, nullptr, 1.f, s));
+  if (rc == NURSD_OK)
+    rc = from_cuda(axis_pass(p, tmp, g, logM, false, C, M, C, (long long)M * C, C, (long long)M * C, M, -M / 2, M,
+                             -M / 2, nullptr, nullptr, 1.f, s));
+  if (rc == NURSD_OK)  // along jz for every lateral mode: [ky][kx][jz][f] -> [ky][kx][kz][f]
+    rc = from_cuda(axis_pass(p, g, p->nd_G3, ilog2(Mz), false, F, M * M, C, F, C, F, Mz, -Mz / 2, Mz, -Mz / 2,
+                             nullptr, nullptr, 1.f, s));
+  if (rc == NURSD_OK) rc = from_cuda(cudaStreamSynchronize(s));
+  cudaFree(g);
+  cudaFree(tmp);
+  cudaFree(djz);
+  cudaFree(dk);
+  return rc;
 }
 
 // Workspace of the per-frequency forms (see the plan members), allocated on first use.
@@ -1095,6 +1235,25 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
   if (ok && (p->flags & NURSD_ENABLE_ADJOINT))
     ok = p->alloc(p->GcT, (size_t)p->ncls * p->F * p->Z) && p->alloc(p->deconv_k, p->M) &&
          p->alloc(p->fine_dx, (size_t)p->W * p->W * p->F) && p->alloc(p->fine_dy, (size_t)p->W * p->W * p->F);
+  for (int k = 1; ok && p->maxB > 0 && k < kMaxBatchStreams; ++k) {  // the batched form's other streams
+    Workspace& w = p->bws[k];
+    const size_t C = std::max(p->F, p->Z);
+    ok = p->alloc(w.bin_of, maxL) && p->alloc(w.i0_orig, maxL) && p->alloc(w.w_orig, (size_t)maxL * 2 * p->w) &&
+         p->alloc(w.counts, (size_t)2 * nbins) && p->alloc(w.bin_start, nbins + 1) && p->alloc(w.sorted_l, maxL) &&
+         p->alloc(w.slot_of, maxL) && p->alloc(w.i0_sorted, maxL) && p->alloc(w.w_sorted, (size_t)maxL * 2 * p->w) &&
+         p->alloc(w.frac_orig, maxL) && p->alloc(w.frac_sorted, maxL) && p->alloc(w.fine, (size_t)p->W * p->W * C) &&
+         p->alloc(w.R1, (size_t)p->W * p->M * C) && p->alloc(w.T1, (size_t)p->M * p->N * p->Z);
+    if (ok && (cudaStreamCreateWithFlags(&p->bstream[k], cudaStreamNonBlocking) != cudaSuccess ||
+               cudaEventCreateWithFlags(&p->bev_join[k], cudaEventDisableTiming) != cudaSuccess)) {
+      cudaGetLastError();
+      ok = false;
+    }
+    if (ok) ok = cudaMemsetAsync(w.bin_start, 0, sizeof(int) * (nbins + 1), s) == cudaSuccess;
+  }
+  if (ok && p->maxB > 0 && cudaEventCreateWithFlags(&p->bev_fork, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    ok = false;
+  }
   if (ok && p->maxB > 0)
     ok = p->alloc(p->phasor_all, (size_t)p->maxB * maxL * p->F) &&
          p->alloc(p->U_all, (size_t)p->maxB * p->M * p->M * p->F) &&
@@ -1196,6 +1355,7 @@ int set_points_on(nursd_plan_t p, int32_t L, const float* d_xy, cudaStream_t s) 
 int nursd_set_points(nursd_plan_t p, int32_t L, const float* d_xy, nursd_stream_t stream) {
   if (check_plan(p) != NURSD_OK || L < 0 || L > p->maxL || (L > 0 && (!d_xy || !aligned(d_xy, 8))))
     return NURSD_ERR_INVALID_ARG;
+  p->nd_points = false;
   return set_points_on(p, L, d_xy, static_cast<cudaStream_t>(stream));
 }
 
@@ -1421,6 +1581,118 @@ int srsd_forward_nonuniform(nursd_plan_t p, const nursd_c64* d_phasor, void* d_o
   return rc;
 }
 
+int nursd_enable_3d(nursd_plan_t p, double dz, int32_t Mz, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || !(dz > 0) || !std::isfinite(dz)) return NURSD_ERR_INVALID_ARG;
+  if (p->nd_Mz) return (Mz == p->nd_Mz && dz == p->nd_dz) ? NURSD_OK : NURSD_ERR_INVALID_ARG;
+  // the z window of footprints must fit one period of the 2 Mz fine grid
+  if (!is_pow2(Mz) || Mz < 8 || Mz > 512 || Mz < p->w + 2) return NURSD_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int M = p->M, N = p->N, F = p->F, maxL = std::max(1, p->maxL);
+  p->nd_Mz = Mz;
+  p->nd_dz = dz;
+  p->nd_Wz = std::min(2 * Mz, Mz + p->w + 2);
+  p->nd_gz0 = -(Mz / 2) - p->w / 2 - 1;
+  if (p->nd_Wz == 2 * Mz) p->nd_gz0 = -Mz;
+  if (!(p->alloc(p->nd_G3, (size_t)M * M * Mz * F) && p->alloc(p->nd_U3w, (size_t)p->nd_Wz * M * M * F) &&
+        p->alloc(p->nd_U3, (size_t)M * M * Mz * F) && p->alloc(p->nd_What, (size_t)M * M * F) &&
+        p->alloc(p->nd_field, (size_t)F * N * N) && p->alloc(p->nd_T, (size_t)N * M * F) &&
+        p->alloc(p->nd_Pz, (size_t)maxL * F) && p->alloc(p->nd_decz, Mz) && p->alloc(p->nd_uz, maxL))) {
+    p->nd_Mz = 0;
+    return NURSD_ERR_OOM;
+  }
+  p->nd_host.resize(Mz);
+  for (int i = 0; i < Mz; ++i) p->nd_host[i] = (float)(1.0 / es_transform(i - Mz / 2, p->w, p->beta, 2 * Mz));
+  int rc = from_cuda(cudaMemcpyAsync(p->nd_decz, p->nd_host.data(), sizeof(float) * Mz, cudaMemcpyHostToDevice, s));
+  if (rc == NURSD_OK) rc = build_table_3d(p, s);
+  if (rc != NURSD_OK) p->nd_Mz = 0;
+  return rc;
+}
+
+int nursd_set_points_3d(nursd_plan_t p, int32_t L, const float* d_xy, const float* d_h, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || !p->nd_Mz || L < 0 || L > p->maxL) return NURSD_ERR_INVALID_ARG;
+  if (L > 0 && (!d_xy || !d_h || !aligned(d_xy, 8) || !aligned(d_h, 4))) return NURSD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = set_points_on(p, L, d_xy, s);
+  if (rc == NURSD_OK)  // fine z coordinate h * 2 / dz, |h| <= Mz dz / 4 (theta_z in [-pi/2, pi/2])
+    rc = from_cuda(launch_z_coords(d_h, p->sorted_l, L, 2.0 / p->nd_dz, 0.25 * p->nd_Mz * p->nd_dz, p->nd_uz,
+                                   p->status, s));
+  p->nd_points = rc == NURSD_OK;
+  return rc;
+}
+
+int nursd_forward_3d(nursd_plan_t p, const nursd_c64* d_phasor, void* d_out, nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || !p->nd_Mz || !p->nd_points || p->L < 0 || !d_out || !aligned(d_out, 8))
+    return NURSD_ERR_INVALID_ARG;
+  if (p->L > 0 && (!d_phasor || !aligned(d_phasor, 8))) return NURSD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int M = p->M, N = p->N, F = p->F, W = p->W, Mz = p->nd_Mz, L = p->L;
+  const int logf = ilog2(p->nf), logM = ilog2(M);
+  const long long MMF = (long long)M * M * F;
+  cudaError_t e = cudaSuccess;
+  // stage 1, 3D type 1: per fine z cell of the window, the slice's phasors, the planar spread and the
+  // lateral passes with deconvolution -> the slice's lateral spectrum
+  for (int iz = 0; e == cudaSuccess && iz < p->nd_Wz; ++iz) {
+    {
+      StageTimer t(p, NURSD_STAGE_SPREAD, s, 2);
+      e = launch_z_slice_phasors(reinterpret_cast<const float2*>(d_phasor), p->sorted_l, p->nd_uz, L, F,
+                                 p->nd_gz0 + iz, p->w, p->beta, p->nd_Pz, s);
+      if (e == cudaSuccess)
+        e = launch_spread(p->nd_Pz, F, p->bin_start, nullptr, p->i0_sorted, p->w_sorted, p->w, p->tiles, W, p->fine,
+                          s, p->spread_rows);
+    }
+    if (e == cudaSuccess) {
+      StageTimer t(p, NURSD_STAGE_FFT_X, s, 1);
+      e = axis_pass(p, p->fine, p->R1, logf, false, F, W, (long long)W * F, F, (long long)M * F, F, W, p->g0, M,
+                    -M / 2, nullptr, nullptr, 1.f, s);
+    }
+    if (e == cudaSuccess) {
+      StageTimer t(p, NURSD_STAGE_FFT_Y, s, 1);
+      e = axis_pass(p, p->R1, p->nd_U3w + iz * MMF, logf, false, F, M, F, (long long)M * F, F, (long long)M * F, W,
+                    p->g0, M, -M / 2, p->deconv, p->deconv, 1.f, s);
+    }
+  }
+  if (e == cudaSuccess) {  // along z: the window's slices -> kz in I_Mz, divided by psi_hat_z(kz)
+    StageTimer t(p, NURSD_STAGE_FFT_Y, s, 1);
+    e = axis_pass(p, p->nd_U3w, p->nd_U3, ilog2(2 * Mz), false, F, M * M, F, MMF, (long long)Mz * F, F, p->nd_Wz,
+                  p->nd_gz0, Mz, -Mz / 2, p->nd_decz, nullptr, 1.f, s);
+  }
+  if (e == cudaSuccess) {  // the plane z0: sum over kz of the spectrum times the 3D table, / Mz
+    StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
+    e = launch_kz_sum(p->nd_U3, p->nd_G3, (long long)M * M, Mz, F, 1.f / (float)Mz, p->nd_What, s);
+  }
+  // the plane's field on the N x N lattice (M^-2 inverse, crop), then its padded DFT: stage 2's input
+  if (e == cudaSuccess) e = idft_crop(p, p->nd_What, F, p->nd_T, p->nd_field, false, s);
+  if (e == cudaSuccess) {  // DFT along mx of every (f, my) row of the field [F][N][N] -> [N][M][F]
+    StageTimer t(p, NURSD_STAGE_IFFT_Y, s, 1);
+    PanelArgs a = panel_base(p);
+    a.in = p->nd_field;
+    a.in_sb = N;
+    a.in_si = 1;
+    a.in_slo = (long long)N * N;
+    a.load_i_fastest = 1;
+    a.out = p->nd_T;
+    a.out_sb = (long long)M * F;
+    a.out_si = F;
+    a.out_slo = 1;
+    a.nin = N;
+    a.in_off = -N / 2;
+    a.nout = M;
+    a.out_off = -M / 2;
+    a.lo_total = F;
+    a.CLO = panel_width(logM);
+    a.batch = N;
+    e = launch_panel_fft(logM, false, a, s);
+  }
+  if (e == cudaSuccess) {  // DFT along my for every kx -> U [M][M][F]
+    StageTimer t(p, NURSD_STAGE_IFFT_X, s, 1);
+    e = axis_pass(p, p->nd_T, p->U, logM, false, F, M, F, (long long)M * F, F, (long long)M * F, N, -N / 2, M, -M / 2,
+                  nullptr, nullptr, 1.f, s);
+  }
+  if (e != cudaSuccess) return from_cuda(e);
+  // stage 2: the planar operator from z0 to each depth (the plan's depths are the distances from z0)
+  return run_propagate(p, p->U, d_out, s);
+}
+
 int nursd_forward_illuminated(nursd_plan_t p, const double* h_illum, const nursd_c64* d_phasor, nursd_c64* d_out,
                               nursd_stream_t stream) {
   if (check_plan(p) != NURSD_OK || p->L < 0 || !h_illum || !d_out || !aligned(d_out, 8)) return NURSD_ERR_INVALID_ARG;
@@ -1495,18 +1767,89 @@ int nursd_forward_batched(nursd_plan_t p, int32_t B, const nursd_batch_item* ite
     }
     rc = from_cuda(launch_temporal_tc_batched(bt, p->Bth, p->Btl, p->wcol, p->T, 2 * F, p->tfix, p->counter, s));
   }
-  for (int b = 0; rc == NURSD_OK && b < B; ++b) {  // per item: sort, spread, fine-grid FFTs -> U_all[b]
-    rc = nursd_set_points(p, items[b].L, items[b].d_xy, stream);
-    if (rc == NURSD_OK) rc = run_nufft1(p, p->phasor_all + b * phasor_stride, p->U_all + b * u_stride, s);
-  }
+  // Per item: point sort, spread and the forward fine-grid passes (-> U_all[b]), then after the batched
+  // contraction the inverse passes; items go round-robin to S streams (the caller's stream with the
+  // plan's own workspace, and up to kMaxBatchStreams - 1 side streams with their own), forked from and
+  // joined into the caller's stream, so that the items' small launches run side by side.  The last
+  // item runs on the plan's own workspace, so the plan keeps its points as a single call would.
+  const int S = std::max(1, std::min(p->batch_streams, B));
+  const Workspace own = p->own();
+  auto fork = [&]() -> int {
+    int r = from_cuda(cudaEventRecord(p->bev_fork, s));
+    for (int k = 1; r == NURSD_OK && k < S; ++k) r = from_cuda(cudaStreamWaitEvent(p->bstream[k], p->bev_fork, 0));
+    return r;
+  };
+  auto join = [&]() -> int {
+    int r = NURSD_OK;
+    for (int k = 1; k < S; ++k) {  // join every stream that was forked, even after an error
+      const int a = from_cuda(cudaEventRecord(p->bev_join[k], p->bstream[k]));
+      const int b = from_cuda(cudaStreamWaitEvent(s, p->bev_join[k], 0));
+      if (r == NURSD_OK) r = a != NURSD_OK ? a : b;
+    }
+    return r;
+  };
+  auto each_item = [&](auto&& fn) -> int {
+    int r = fork();
+    for (int b = 0; r == NURSD_OK && b < B; ++b) {
+      const int k = (B - 1 - b) % S;
+      cudaStream_t sk = k == 0 ? s : p->bstream[k];
+      p->use(k == 0 ? own : p->bws[k]);
+      r = fn(b, sk);
+      p->use(own);
+    }
+    const int j = join();
+    return r != NURSD_OK ? r : j;
+  };
+  if (rc == NURSD_OK)
+    rc = each_item([&](int b, cudaStream_t sk) {
+      int r = set_points_on(p, items[b].L, items[b].d_xy, sk);
+      if (r == NURSD_OK) r = run_nufft1(p, p->phasor_all + b * phasor_stride, p->U_all + b * u_stride, sk);
+      return r;
+    });
   if (rc == NURSD_OK) {
     StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
     rc = from_cuda(
         launch_contract_batched(p->U_all, u_stride, p->Gc, p->cls, p->ncls, M, F, Z, p->Y_all, y_stride, B, s,
                                 p->status));
   }
-  for (int b = 0; rc == NURSD_OK && b < B; ++b) rc = run_idft_crop(p, items[b].d_out, s, p->Y_all + b * y_stride);
+  if (rc == NURSD_OK)
+    rc = each_item([&](int b, cudaStream_t sk) { return run_idft_crop(p, items[b].d_out, sk, p->Y_all + b * y_stride); });
+  if (rc == NURSD_OK) p->L = items[B - 1].L;
   return rc;
+}
+
+int nursd_plan_tune(nursd_plan_t p, int32_t param, int32_t value) {
+  if (check_plan(p) != NURSD_OK) return NURSD_ERR_INVALID_ARG;
+  switch (param) {
+    case NURSD_TUNE_SPREAD_ROWS:
+      if (!spread_rows_supported(value) || p->W % value != 0) return NURSD_ERR_UNSUPPORTED;
+      p->spread_rows = value;
+      return NURSD_OK;
+    case NURSD_TUNE_BATCH_STREAMS:
+      if (value < 1 || value > kMaxBatchStreams) return NURSD_ERR_UNSUPPORTED;
+      p->batch_streams = value;
+      return NURSD_OK;
+    default:
+      return NURSD_ERR_INVALID_ARG;
+  }
+}
+
+int nursd_plan_get_tune(nursd_plan_t p, int32_t param, int32_t* value) {
+  if (check_plan(p) != NURSD_OK || !value) return NURSD_ERR_INVALID_ARG;
+  switch (param) {
+    case NURSD_TUNE_SPREAD_ROWS: *value = p->spread_rows; return NURSD_OK;
+    case NURSD_TUNE_BATCH_STREAMS: *value = p->batch_streams; return NURSD_OK;
+    default: return NURSD_ERR_INVALID_ARG;
+  }
+}
+
+int nursd_test_fail_allocation(int32_t after) {
+  g_alloc_countdown.store(after > 0 ? after : -1);
+  return NURSD_OK;
+}
+
+int nursd_test_set_wait_limit(int64_t polls, nursd_stream_t stream) {
+  return from_cuda(set_contract_wait_limit(polls, static_cast<cudaStream_t>(stream)));
 }
 
 int nursd_profile_enable(nursd_plan_t p, int enable) {

@@ -36,6 +36,7 @@ static __device__ __align__(256) unsigned char g_nursd_noalloc_scratch[kNoAllocS
 struct DeviceScratch {
   bool ready = false;
   unsigned char* base = nullptr;  // device address of g_nursd_noalloc_scratch on this device
+  CUcontext ctx = nullptr;        // the context that address and the tables belong to
 };
 std::mutex g_mutex;
 DeviceScratch g_devices[kMaxDevices];
@@ -100,14 +101,37 @@ struct Layout {
   }
 };
 
-// Once per device, with that device current: look up the array's device
-// address and fill the fixed tables (synchronising `s`).
+// The current context, through the driver entry point (the library does not link the driver).
+CUcontext current_context() {
+  using Fn = CUresult (*)(CUcontext*);
+  static Fn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<Fn>(p);
+    else
+      cudaGetLastError();
+  }
+  CUcontext c = nullptr;
+  if (fn && fn(&c) != CUDA_SUCCESS) c = nullptr;
+  return c;
+}
+
+// Once per device and context, with that device current: look up the array's device address and fill
+// the fixed tables (synchronising `s`).  A new context on the device (after cudaDeviceReset, say) has
+// its own copy of the array, so the address and tables are taken again.
 int device_scratch(cudaStream_t s, unsigned char** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return NURSD_ERR_CUDA;
+  if (cudaFree(nullptr) != cudaSuccess) return NURSD_ERR_CUDA;  // make sure the device's context exists
+  const CUcontext ctx = current_context();
   std::lock_guard<std::mutex> lock(g_mutex);
   DeviceScratch& d = g_devices[dev];
-  if (!d.ready) {
+  if (!d.ready || d.ctx != ctx) {
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_nursd_noalloc_scratch) != cudaSuccess || ptr == nullptr) {
       cudaGetLastError();
@@ -120,6 +144,7 @@ int device_scratch(cudaStream_t s, unsigned char** out) {
     noalloc_tables_kernel<<<(kTwiddleEntries + 255) / 256, 256, 0, s>>>(tw, gx, gw);
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return NURSD_ERR_CUDA;
     d.base = base;
+    d.ctx = ctx;
     d.ready = true;
   }
   *out = d.base;
@@ -177,14 +202,11 @@ extern "C" int nursd_nufft1_noalloc(int32_t N, double pitch, double center_x, do
   float2* fine = reinterpret_cast<float2*>(call + o_fine);
   float2* R1 = reinterpret_cast<float2*>(call + o_r1);
 
-  // The array keeps the previous call's contents.  Everything below is fully
-  // rewritten before it is read (the sort writes every count and bin start,
-  // the spread writes every window cell), except the status word: clear it.
-  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
-  if (e == cudaSuccess) {
-    noalloc_deconv_kernel<<<(M + 127) / 128, 128, 0, s>>>(gx, gw, M, nf, w, (double)beta, dec);
-    e = cudaGetLastError();
-  }
+  // The array keeps the previous call's contents.  Everything below is fully rewritten before it is
+  // read (the sort writes every count and bin start, the spread writes every window cell).  The status
+  // word only absorbs the sort's out-of-aperture flags, which this entry point does not report.
+  noalloc_deconv_kernel<<<(M + 127) / 128, 128, 0, s>>>(gx, gw, M, nf, w, (double)beta, dec);
+  cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) {
     PointsArgs a;
     a.xy = d_xy;

@@ -200,10 +200,12 @@ cudaError_t launch_points(const PointsArgs& a, int* bin_of, int2* i0_orig, float
                           float2* frac_orig = nullptr, float2* frac_sorted = nullptr, int* slot_of = nullptr);
 
 // ---------------------------------------------------------------- spread
-// sorted_l == nullptr: P is already in sorted-slot order (row s of P is sorted sample s).
+// sorted_l == nullptr: P is already in sorted-slot order (row s of P is sorted sample s).  rows: tile
+// height (spread_rows_supported: 4, 8 or 16; W must be a multiple of it).
+bool spread_rows_supported(int rows);
 cudaError_t launch_spread(const float2* P, int F, const int* bin_start, const int* sorted_l,
                           const int2* i0, const float* wts, int width, int tiles, int W,
-                          float2* fine, cudaStream_t s);
+                          float2* fine, cudaStream_t s, int rows = 8);
 
 // ------------------------------------------------------------- contraction
 // Y[k][z] = sum_f U[k][f] * Gc[cls(k)][f][z] for every mode k of every class.
@@ -216,6 +218,10 @@ cudaError_t launch_contract(const float2* U, const float2* Gc, const int2* cls_p
 cudaError_t launch_contract_batched(const float2* U, long long u_stride, const float2* Gc, const int2* cls_pq,
                                    int ncls, int M, int F, int Z, float2* Y, long long y_stride, int B,
                                    cudaStream_t s, int* status = nullptr);
+// Test only: the bound (mbarrier polls) of the bulk-copy contraction's data waits on the current device
+// (polls < 0: the default; 0: give up at the first wait); a wait that runs out sets status bit 2, drains
+// the warp's copies and returns.
+cudaError_t set_contract_wait_limit(long long polls, cudaStream_t s);
 // Adjoint: R[k][f] = sum_z Yt[k][z] * conj(GcT[cls(k)][z][f]).
 cudaError_t launch_contract_adjoint(const float2* Yt, const float2* GcT, const int2* cls_pq, int ncls, int M, int F,
                                     int Z, float2* R, cudaStream_t s, int* status = nullptr);
@@ -279,6 +285,16 @@ bool srsd_interp_adds(int F);
 cudaError_t launch_srsd_interp_xy_contract(const float2* Yh, int L, int M, int F, int Z, const int* zlist, int nz,
                                            int w, const int* m0, const float* wt, const float2* Gs, int ncls,
                                            float2* Y, cudaStream_t s);
+// ------------------------------------------------ 3D NURSD (nursd3d.cu)
+// uz_sorted[s] = h[sorted_l[s]] inv_fine_dz (|h| > half_extent: status bit 1, no weight).
+cudaError_t launch_z_coords(const float* h, const int* sorted_l, int L, double inv_fine_dz, double half_extent,
+                            float* uz_sorted, int* status, cudaStream_t s);
+// Pz[s][f] = P[sorted_l[s]][f] phi(2 (gz - uz[s]) / w) (slot order).
+cudaError_t launch_z_slice_phasors(const float2* P, const int* sorted_l, const float* uz, int L, int F, int gz, int w,
+                                   float beta, float2* Pz, cudaStream_t s);
+// What[k][f] = scale sum_kz U3[k][kz][f] G3[k][kz][f] for nk lateral modes k.
+cudaError_t launch_kz_sum(const float2* U3, const float2* G3, long long nk, int Mz, int F, float scale, float2* What,
+                          cudaStream_t s);
 // ------------------------------------------------ subsampled acquisition (resample.cu)
 // kept [Nc][Nc][F] = full[::D, ::D]; full [N][N][F] from kept by nearest (linear = 0) or linear interpolation.
 cudaError_t launch_subsample(const float2* full, float2* kept, int N, int F, int D, cudaStream_t s);

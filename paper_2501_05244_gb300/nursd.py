@@ -28,6 +28,8 @@ NURSD_ENABLE_ADJOINT = 0x2
 NURSD_CONFOCAL = 0x4
 NURSD_UPSAMPLE_NEAREST = 0
 NURSD_UPSAMPLE_LINEAR = 1
+#: plan tunables (nursd_plan_tune)
+TUNABLES = {"spread_rows": 0, "batch_streams": 1}
 
 #: every entry point declared in include/nursd.h
 EXPORTS = (
@@ -38,7 +40,9 @@ EXPORTS = (
     "nursd_nufft1_noalloc",
     "nursd_forward_points", "nursd_adjoint", "nursd_grad_points", "srsd_forward", "nursd_forward_batched",
     "nursd_reconstruct", "nursd_forward_illuminated", "nursd_transient_frames", "srsd_forward_points",
-    "nursd_subsample", "nursd_upsample", "srsd_forward_nonuniform",
+    "nursd_subsample", "nursd_upsample", "srsd_forward_nonuniform", "nursd_plan_tune", "nursd_plan_get_tune",
+    "nursd_test_fail_allocation", "nursd_test_set_wait_limit", "nursd_enable_3d", "nursd_set_points_3d",
+    "nursd_forward_3d",
 )
 
 #: stage names in nursd_stage order
@@ -113,6 +117,13 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "srsd_forward_points": (ctypes.c_int, [vp, vp, i32, vp, vp, vp]),
         "nursd_subsample": (ctypes.c_int, [i32, i32, i32, vp, vp, vp]),
         "srsd_forward_nonuniform": (ctypes.c_int, [vp, vp, vp, vp]),
+        "nursd_plan_tune": (ctypes.c_int, [vp, i32, i32]),
+        "nursd_test_fail_allocation": (ctypes.c_int, [i32]),
+        "nursd_enable_3d": (ctypes.c_int, [vp, dbl, i32, vp]),
+        "nursd_set_points_3d": (ctypes.c_int, [vp, i32, vp, vp, vp]),
+        "nursd_forward_3d": (ctypes.c_int, [vp, vp, vp, vp]),
+        "nursd_test_set_wait_limit": (ctypes.c_int, [i64, vp]),
+        "nursd_plan_get_tune": (ctypes.c_int, [vp, i32, ip]),
         "nursd_upsample": (ctypes.c_int, [i32, i32, i32, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -389,6 +400,33 @@ class Plan:
         _check(self._lib.srsd_forward(self._h, p, o, ctypes.c_void_p(_stream_ptr(stream))), "srsd_forward")
         return out
 
+    # -- 3D NURSD (non-planar relays)
+    def enable_3d(self, dz: float, Mz: int, stream=None):
+        """Build the 3D transfer table for heights sampled at dz over Mz offsets (|h| <= Mz dz / 4)."""
+        _check(self._lib.nursd_enable_3d(self._h, float(dz), int(Mz), ctypes.c_void_p(_stream_ptr(stream))),
+               "nursd_enable_3d")
+
+    def set_points_3d(self, xy, h, stream=None):
+        """Relay samples xy [L][2] with heights h [L] (metres, relative to the reference plane)."""
+        torch = _torch()
+        L = int(xy.shape[0])
+        p = _dev(xy, torch.float32, (L, 2), "xy")
+        hh = _dev(h, torch.float32, (L,), "h")
+        _check(self._lib.nursd_set_points_3d(self._h, L, p, hh, ctypes.c_void_p(_stream_ptr(stream))),
+               "nursd_set_points_3d")
+        self.L = L
+
+    def forward_3d(self, phasor, out=None, stream=None):
+        """3D NURSD: the field at the reference plane, then propagated to the plan's depths -> [Z][N][N]."""
+        torch = _torch()
+        self._need_points()
+        p = _dev(phasor, torch.complex64, (self.L, self.F), "phasor")
+        if out is None:
+            out = self.empty_output()
+        o = _dev(out, self.out_dtype(), self.out_shape(), "out")
+        _check(self._lib.nursd_forward_3d(self._h, p, o, ctypes.c_void_p(_stream_ptr(stream))), "nursd_forward_3d")
+        return out
+
     def srsd_forward_nonuniform(self, phasor, out=None, stream=None):
         """NU-SFFT: the scaled DFT taken at the relay samples (every scale >= 1) -> [Z][N][N]."""
         torch = _torch()
@@ -471,6 +509,19 @@ class Plan:
 
     def sync_status(self, stream=None) -> int:
         return int(self._lib.nursd_sync_status(self._h, ctypes.c_void_p(_stream_ptr(stream))))
+
+    # -- tunables
+    def tune(self, name: str, value: int):
+        """Set a launch-shape tunable (see TUNABLES); results do not depend on it."""
+        _check(self._lib.nursd_plan_tune(self._h, TUNABLES[name], int(value)), "nursd_plan_tune")
+
+    def tuning(self) -> dict:
+        out = {}
+        for name, key in TUNABLES.items():
+            v = ctypes.c_int32()
+            _check(self._lib.nursd_plan_get_tune(self._h, key, ctypes.byref(v)), "nursd_plan_get_tune")
+            out[name] = v.value
+        return out
 
     # -- profiling
     def profile(self, enable: bool = True):
