@@ -11,6 +11,8 @@
 // Pruning: the input is a window of `nin` elements (the rest is zero) and only
 // `nout` output bins are written, which is how the NUFFT keeps the central
 // M modes of its 2M grid and the IFFT keeps the N x N crop.
+#include <algorithm>
+
 #include "nursd_internal.cuh"
 
 namespace nursd {
@@ -291,9 +293,23 @@ cudaError_t launch_panel_bluestein(int logn, const PanelArgs& a, const float2* c
 }
 
 cudaError_t launch_panel_fft(int logn, bool inverse, const PanelArgs& a, cudaStream_t s) {
-  if (a.CHI * a.CLO != panel_width(logn) || a.nin > (1 << logn) || a.nout > (1 << logn) || a.batch < 1 ||
-      a.batch > 65535)
+  if (a.CHI * a.CLO != panel_width(logn) || a.nin > (1 << logn) || a.nout > (1 << logn) || a.batch < 1)
     return cudaErrorInvalidValue;
+  if (a.batch > 65535) {  // the batch is a grid dimension: launch it in chunks
+    if (a.prod_g) return cudaErrorInvalidValue;  // its mode classes follow the batch index
+    constexpr int kChunk = 32768;
+    for (int b0 = 0; b0 < a.batch; b0 += kChunk) {
+      PanelArgs c = a;
+      c.batch = std::min(kChunk, a.batch - b0);
+      c.in = a.in + b0 * a.in_sb;
+      if (a.out) c.out = a.out + b0 * a.out_sb;
+      if (a.out_mag) c.out_mag = a.out_mag + b0 * a.out_sb;
+      if (a.mul_b) c.mul_b = a.mul_b + b0;
+      const cudaError_t e = launch_panel_fft(logn, inverse, c, s);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
   switch (logn) {
     case 3: return launch_dir<3, 16, 128>(inverse, a, s);
     case 4: return launch_dir<4, 16, 128>(inverse, a, s);

@@ -77,3 +77,17 @@ def test_3d_arguments_and_out_of_range_heights():
     plan.set_points_3d(torch.from_numpy(xy).cuda(), torch.from_numpy(h2).cuda())
     plan.forward_3d(Pg)
     assert plan.sync_status() == nursd.nursd.NURSD_ERR_POINT_OUT_OF_RANGE
+
+
+def test_3d_nursd_at_a_lattice_of_128():
+    # M = 256: the z pass and the table's z transform run over 65,536 lateral modes (more than one grid
+    # dimension holds), a few samples keep the oracle short
+    xy, h, P, om, dist, pitch, dz = case(128, 20, 1, 2, 8, 6, pitch=0.015)
+    plan = nursd.Plan(128, pitch, (0.0, 0.0), dist, om, max_points=20)
+    plan.enable_3d(dz, 8)
+    plan.set_points_3d(torch.from_numpy(xy).cuda(), torch.from_numpy(h).cuda())
+    V = plan.forward_3d(torch.from_numpy(P).cuda()).cpu().numpy()
+    assert plan.sync_status() == 0
+    xyz = np.column_stack([xy.astype(np.float64), h.astype(np.float64)])
+    ref = O.nursd3d_forward(P, xyz, (0.0, 0.0), pitch, 128, 0.0, dz, 8, dist, om)
+    assert rel(V, ref) < TOL
