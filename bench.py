@@ -52,6 +52,12 @@ def parse_args():
                          "depth planes are split over the GPUs and gathered (strong scaling)")
     ap.add_argument("--no-rows", action="store_true",
                     help="skip the per-row measurements (type-2 voxels, SRSD, adjoint, gradients, batched)")
+    ap.add_argument("--rows", default="",
+                    help="comma-separated names of the rows to measure (default: every row); given, the rows run "
+                         "with any --workload")
+    ap.add_argument("--row-depths", type=int, default=128,
+                    help="depth planes of the scaled-plane rows (SRSD, NU-SFFT, SRSD at voxels); 128 is the "
+                         "measured workload, fewer make a small case for profiler captures")
     ap.add_argument("--workload", choices=["spad", "grid128", "spad-z8", "spad-n128"], default="spad",
                     help="spad: the 65k-sample 256^2x128 workload (the metric); grid128: the same samples on "
                          "128^2x64 voxels; spad-z8: the spad workload with 8 of its 128 depth planes (same "
@@ -489,7 +495,7 @@ def hbm_row(bytes_: int, ms: float, peak: float) -> dict:
     return {"algorithmic_bytes": int(bytes_), "achieved_gbs": gbs, "hbm_frac": gbs / peak}
 
 
-def measure_rows(wl, peak, stages_ms=None):
+def measure_rows(wl, peak, stages_ms=None, only=(), row_depths=128):
     """Per-row measurements of the other hot-path rows on the same GPU (one entry each)."""
     import numpy as np
     import torch
@@ -508,6 +514,8 @@ def measure_rows(wl, peak, stages_ms=None):
     d_hist = torch.from_numpy(wl.hist).cuda()
 
     def guarded(name, fn):
+        if only and name not in only:
+            return
         try:
             rows[name] = fn()
         except Exception as exc:  # a failing row is reported, not fatal to the headline line
@@ -535,7 +543,7 @@ def measure_rows(wl, peak, stages_ms=None):
                 "ms": ms, "voxel_freq_per_s": units / (ms / 1e3), **hbm_row(b, ms, peak), "stages_ms": st}
 
     def srsd():
-        depths = srsd_depths_c3b()
+        depths = srsd_depths_c3b(row_depths)
         plan = nursd.Plan(g.N, g.pitch, g.center, depths, om, wt, T=g.T, t0=g.t0, dt=g.dt, max_points=L,
                           srsd_pitch=srsd_pitches_c3b(depths))
         plan.set_points(d_xy)
@@ -551,7 +559,7 @@ def measure_rows(wl, peak, stages_ms=None):
         bytes_ = bytes_srsd(g.N, F, scales)
         call_bytes = bytes_type1(L, F, g.N) + bytes_ + bytes_idft(Z, g.N)
         units = Z * g.N * g.N * F
-        return {"workload": "65,536 keystone samples -> 256^2 x 128 planes over 1-4 m, pitch 8 -> 32 mm, F=128",
+        return {"workload": f"65,536 keystone samples -> 256^2 x {Z} planes over 1-4 m, pitch 8 -> 32 mm, F=128",
                 "ms": ms, "voxel_freq_per_s": units / (ms / 1e3), **hbm_row(call_bytes, ms, peak),
                 "srsd_stage": {"ms": s_ms, "algorithmic_bytes": bytes_, "achieved_gbs": bytes_ / (s_ms / 1e3) / 1e9,
                                "hbm_frac": bytes_ / (s_ms / 1e3) / 1e9 / peak,
@@ -642,7 +650,7 @@ def measure_rows(wl, peak, stages_ms=None):
 
     def srsd_points():
         # next row 2: SRSD + NURSD-2 (Eq. NURSD2_SRSD), 16,384 random voxels in each plane's scaled aperture
-        depths = srsd_depths_c3b()
+        depths = srsd_depths_c3b(row_depths)
         pitches = srsd_pitches_c3b(depths)
         plan = nursd.Plan(g.N, g.pitch, g.center, depths, om, wt, T=g.T, t0=g.t0, dt=g.dt, max_points=L,
                           srsd_pitch=pitches)
@@ -658,7 +666,7 @@ def measure_rows(wl, peak, stages_ms=None):
         Z, W = len(depths), fine_window(g.N)
         b = (bytes_type1(L, g.F, g.N) + bytes_srsd(g.N, g.F, pitches / g.pitch) + bytes_type2_fine(Z, g.N)
              + 8 * (W * W * Z + 2 * Z * K))
-        return {"workload": "65,536 keystone samples -> 128 scaled planes over 1-4 m (pitch 8 -> 32 mm) x 16,384 "
+        return {"workload": f"65,536 keystone samples -> {Z} scaled planes over 1-4 m (pitch 8 -> 32 mm) x 16,384 "
                             "random voxels each, F=128",
                 "ms": ms, "voxel_freq_per_s": len(depths) * K * g.F / (ms / 1e3), **hbm_row(b, ms, peak)}
 
@@ -741,7 +749,7 @@ def measure_rows(wl, peak, stages_ms=None):
     guarded("a12_batched", batched)
     def nusfft():
         # next row 2, second half: SRSD taken directly at the 65,536 keystone samples (NU-SFFT)
-        depths = srsd_depths_c3b()
+        depths = srsd_depths_c3b(row_depths)
         pitches = srsd_pitches_c3b(depths)
         plan = nursd.Plan(g.N, g.pitch, g.center, depths, om, wt, T=g.T, t0=g.t0, dt=g.dt, max_points=L,
                           srsd_pitch=pitches)
@@ -754,7 +762,7 @@ def measure_rows(wl, peak, stages_ms=None):
         plan.close()
         Z = len(depths)
         b = bytes_nusfft(L, g.N, g.F, pitches / g.pitch) + bytes_idft(Z, g.N)
-        return {"workload": "65,536 keystone samples -> 256^2 x 128 planes over 1-4 m, pitch 8 -> 32 mm, F=128, "
+        return {"workload": f"65,536 keystone samples -> 256^2 x {Z} planes over 1-4 m, pitch 8 -> 32 mm, F=128, "
                             "scaled DFT at the samples (NU-SFFT)",
                 "ms": ms, "voxel_freq_per_s": Z * g.N * g.N * g.F / (ms / 1e3), **hbm_row(b, ms, peak)}
 
@@ -1025,9 +1033,10 @@ def run_ours(args, rank, world, local):
                 "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size())},
         "clocks": clk,
     }
-    if rank == 0 and world == 1 and not args.no_rows and args.workload == "spad":
+    only = tuple(r for r in args.rows.split(",") if r)
+    if rank == 0 and world == 1 and not args.no_rows and (args.workload == "spad" or only):
         plan.close()
-        line["rows"] = measure_rows(wl, peak, line["stages_ms"])
+        line["rows"] = measure_rows(wl, peak, line["stages_ms"], only, args.row_depths)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, desc, cores = oracle_rate(wl, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}

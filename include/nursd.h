@@ -422,7 +422,9 @@ int nursd_nufft1_noalloc(int32_t N, double pitch, double center_x, double center
 
 /*
  * Synchronise `stream`, read and clear the plan's device error word.
- * Returns NURSD_OK, NURSD_ERR_POINT_OUT_OF_RANGE or NURSD_ERR_TIMEOUT.
+ * Returns NURSD_OK, NURSD_ERR_POINT_OUT_OF_RANGE, NURSD_ERR_TIMEOUT (a bounded
+ * device wait gave up) or NURSD_ERR_UNSUPPORTED (an SRSD tap table that the
+ * interpolation kernels cannot follow; not produced by the plan's own tables).
  */
 int nursd_sync_status(nursd_plan_t plan, nursd_stream_t stream);
 

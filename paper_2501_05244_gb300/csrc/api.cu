@@ -653,12 +653,12 @@ int run_srsd_spectra(nursd_plan_s* p, cudaStream_t s) {
       e = launch_panel_fft(logL, false, b, s);
     }
   }
-  if (e == cudaSuccess && p->si_any && srsd_interp_adds(F))  // channel halves are added into a zeroed Y
+  if (e == cudaSuccess && p->si_any && srsd_interp_adds(F, 2 * M, p->w))  // channel halves are added into a zeroed Y
     e = cudaMemsetAsync(p->Y, 0, sizeof(float2) * (size_t)M * M * Z, s);
   if (e == cudaSuccess && p->si_any) {  // every depth with scale >= 1: taps and contraction, one launch
     StageTimer t(p, NURSD_STAGE_SRSD, s, 1);
     e = launch_srsd_interp_xy_contract(p->si_yh, 2 * M, M, F, Z, p->si_zlist, p->si_nz, p->w, p->si_m0, p->si_wt,
-                                       p->Gs, p->ncls, p->Y, s);
+                                       p->Gs, p->ncls, p->Y, p->status, s);
   }
   for (int z = 0; e == cudaSuccess && z < Z; ++z) {
     if (p->si_interp[z]) continue;
@@ -790,11 +790,12 @@ int run_nusfft_spectra(nursd_plan_s* p, const float2* phasor, cudaStream_t s) {
       e = launch_panel_fft(logL, false, b, s);
     }
   }
-  if (e == cudaSuccess && srsd_interp_adds(F)) e = cudaMemsetAsync(p->Y, 0, sizeof(float2) * (size_t)M * M * Z, s);
+  if (e == cudaSuccess && srsd_interp_adds(F, L2, p->w))
+    e = cudaMemsetAsync(p->Y, 0, sizeof(float2) * (size_t)M * M * Z, s);
   if (e == cudaSuccess) {
     StageTimer t(p, NURSD_STAGE_SRSD, s, 1);
     e = launch_srsd_interp_xy_contract(p->si_yh, L2, M, F, Z, p->nu_zlist, Z, p->w, p->nu_m0, p->nu_wt, p->Gs,
-                                       p->ncls, p->Y, s);
+                                       p->ncls, p->Y, p->status, s);
   }
   return from_cuda(e);
 }
@@ -1890,7 +1891,8 @@ int nursd_sync_status(nursd_plan_t p, nursd_stream_t stream) {
   if (cudaMemcpyAsync(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return NURSD_ERR_CUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return NURSD_ERR_CUDA;
   if (h != 0 && cudaMemsetAsync(p->status, 0, sizeof(int), s) != cudaSuccess) return NURSD_ERR_CUDA;
-  if (h & 6) return NURSD_ERR_TIMEOUT;  // a bounded barrier wait gave up (contraction: 2, temporal: 4)
+  if (h & 6) return NURSD_ERR_TIMEOUT;  // a bounded barrier wait gave up (contraction, SRSD: 2, temporal: 4)
+  if (h & 8) return NURSD_ERR_UNSUPPORTED;  // an SRSD tap table broke the interpolation's step rule
   if (h & 1) return NURSD_ERR_POINT_OUT_OF_RANGE;
   return NURSD_OK;
 }

@@ -198,6 +198,17 @@ int points_bins(int W, int tiles);
 cudaError_t launch_points(const PointsArgs& a, int* bin_of, int2* i0_orig, float* w_orig, int* counts,
                           int* bin_start, int* sorted_l, int2* i0_sorted, float* w_sorted, cudaStream_t s,
                           float2* frac_orig = nullptr, float2* frac_sorted = nullptr, int* slot_of = nullptr);
+// The same for the n items of a batched call (a.L and a.xy unused): item b has items.L[b] samples at
+// items.xy[b]; its per-sample arrays (scratch and sorted) start at b * pts, its counts at b * 2 nbins
+// and its bin_start at b * (nbins + 1).  An item with no samples gets an all-zero bin_start.
+struct PointsItems {
+  int L[kMaxBatch];
+  const float* xy[kMaxBatch];
+};
+cudaError_t launch_points_batched(const PointsArgs& a, const PointsItems& items, int n, long long pts, int* bin_of,
+                                  int2* i0_orig, float* w_orig, int* counts, int* bin_start, int* sorted_l,
+                                  int2* i0_sorted, float* w_sorted, float2* frac_orig, float2* frac_sorted,
+                                  int* slot_of, cudaStream_t s);
 
 // ---------------------------------------------------------------- spread
 // sorted_l == nullptr: P is already in sorted-slot order (row s of P is sorted sample s).  rows: tile
@@ -277,14 +288,15 @@ cudaError_t launch_gtf_compress_depthmajor(const float2* Gfull, const int2* cls_
 // ------------------------------------------------- SRSD by interpolation (srsd_interp.cu)
 // Yh [L][L][F] at index m + L/2 (periodic in m).
 // Both taps and the contraction in one pass for every depth z in zlist[0 .. nz) (device list; 4 <= w <= 8;
-// the tap table of each depth must advance by at most two cells per mode index):
+// the tap table of each depth must advance by 0, 1 or 2 cells per mode index):
 // Y[k][z] = sum_f Gs[z][class(k)][f] sum_ty wt[z][ky][ty] sum_tx wt[z][kx][tx] Yh[m0[z][ky] + ty][m0[z][kx] + tx][f].
-// When srsd_interp_adds(F) the channels of a mode are summed into Y, whose listed depths must then be
-// zero on entry.
-bool srsd_interp_adds(int F);
+// When srsd_interp_adds(F, L, w) the channels of a mode are summed into Y, whose listed depths must then
+// be zero on entry.  status (device int): bit 2 when a bounded barrier wait gave up, bit 8 when a tap
+// table breaks the step rule (nothing is written for the modes concerned).
+bool srsd_interp_adds(int F, int L, int w);
 cudaError_t launch_srsd_interp_xy_contract(const float2* Yh, int L, int M, int F, int Z, const int* zlist, int nz,
                                            int w, const int* m0, const float* wt, const float2* Gs, int ncls,
-                                           float2* Y, cudaStream_t s);
+                                           float2* Y, int* status, cudaStream_t s);
 // ------------------------------------------------ 3D NURSD (nursd3d.cu)
 // uz_sorted[s] = h[sorted_l[s]] inv_fine_dz (|h| > half_extent: status bit 1, no weight).
 cudaError_t launch_z_coords(const float* h, const int* sorted_l, int L, double inv_fine_dz, double half_extent,

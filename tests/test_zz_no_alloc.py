@@ -17,6 +17,7 @@ torch = pytest.importorskip("torch")
 
 import paper_2501_05244_gb300 as nursd
 from paper_2501_05244_gb300 import nursd as binding
+from oracle import nursd_oracle as O
 from workloads import BASE_SEED, random_phasors, workload_c1, workload_mid
 
 pytestmark = pytest.mark.gpu
@@ -75,6 +76,16 @@ def test_no_alloc_matches_the_plan_entry_point_on_consecutive_calls(lib):
     assert rel(no_alloc(lib, *a), ref_a) < TOL
     assert rel(no_alloc(lib, *b), ref_b) < TOL
     assert rel(no_alloc(lib, *a), ref_a) < TOL
+
+
+def test_no_alloc_matches_the_exact_nonuniform_dft(lib):
+    # against the FP64 oracle's explicit sum, not only against the plan path: its own deconvolution
+    # and quadrature tables are checked on their own
+    g, xy, P = case(workload_c1(), BASE_SEED + 92)  # N = 32, 1,024 samples, F = 16
+    U = no_alloc(lib, g, xy, P)
+    M = 2 * g.N
+    ref = O.nudft_type1(P.cpu().numpy().astype(np.complex128), O.relay_theta(xy.cpu().numpy(), g.center, g.pitch, M), M)
+    assert rel(np.transpose(U, (2, 0, 1)), ref) < TOL
 
 
 def test_no_alloc_rejects_sizes_beyond_its_scratch(lib):
