@@ -681,7 +681,7 @@ def measure_rows(wl, peak, stages_ms=None, only=(), row_depths=128):
         xys = [torch.from_numpy(x).cuda() for x in layouts]
         hists = [device_histograms(xys[b], *scenes[b], gb.T, gb.dt, gb.t0, seed=BASE_SEED + 500 + b)
                  for b in range(len(sizes))]
-        outs = [plan.empty_output() for _ in sizes]
+        outs = list(plan.empty_batch_output(len(sizes)))  # side by side: the grouped launches
         from paper_2501_05244_gb300.autotune import autotune
 
         tuned = autotune(plan, lambda: plan.forward_batched(xys, hists, outs), workload="64 items, L 4096-65536",

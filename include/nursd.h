@@ -459,12 +459,24 @@ int nursd_forward_3d(nursd_plan_t plan, const nursd_c64* d_phasor, void* d_out, 
  * Tunables of a plan (no counterpart in the paper: launch shapes of this library), set by the
  * autotuner of the Python package or by hand; they change only speed, never results beyond FP32
  * summation order.  NURSD_TUNE_SPREAD_ROWS: height in fine cells (4, 8 or 16) of the spread's tiles
- * (default 8).  NURSD_TUNE_BATCH_STREAMS: streams (1 .. 16) over which nursd_forward_batched runs its
- * items' point sorts, spreads and FFT passes side by side (default 4).  nursd_plan_tune returns
- * UNSUPPORTED for a value outside those sets, INVALID_ARG for an unknown parameter.
+ * (default 8).  NURSD_TUNE_BATCH_GROUPED: 1 (default) lets nursd_forward_batched run each stage as
+ * one launch over a group of items when the items' outputs lie side by side (equally spaced, at least
+ * one volume apart); 0 always takes the per-item form.  NURSD_TUNE_BATCH_STREAMS: streams (1 .. 16)
+ * over which the per-item form runs its items' point sorts, spreads and FFT passes side by side
+ * (default 4).  NURSD_TUNE_BATCH_GROUP: items per grouped launch, 1 .. the plan's capacity (default:
+ * the capacity, max_batch or as many items as 8 GiB of item workspaces hold; 0 on plans without a
+ * batch).  NURSD_TUNE_BATCH_TENSOR: 1 (default) runs the batched contraction (two or more items) as
+ * tensor-core products per symmetry class where the shape allows (M a power of two, F a multiple of 8,
+ * Z = 32, 64 or 128), 0 keeps the FP32 SIMT kernel; the two agree to FP32 rounding (the tensor form
+ * splits each operand into tf32 head and tail and keeps the three leading products).
+ * nursd_plan_tune returns UNSUPPORTED for a value outside those sets, INVALID_ARG for an unknown
+ * parameter.
  */
 #define NURSD_TUNE_SPREAD_ROWS 0
 #define NURSD_TUNE_BATCH_STREAMS 1
+#define NURSD_TUNE_BATCH_GROUPED 2
+#define NURSD_TUNE_BATCH_GROUP 3
+#define NURSD_TUNE_BATCH_TENSOR 4
 int nursd_plan_tune(nursd_plan_t plan, int32_t param, int32_t value);
 int nursd_plan_get_tune(nursd_plan_t plan, int32_t param, int32_t* h_value);
 

@@ -1,4 +1,4 @@
-"""Autotuner of a plan's launch shapes (the spread's tile height, the batched form's stream count).
+"""Autotuner of a plan's launch shapes (the spread's tile height, the batched form's grouping and stream count).
 
 The tunables change only speed: every setting computes the same operator (up to FP32 summation
 order).  :func:`autotune` times a caller-supplied step -- one call of the operation being tuned, on
@@ -17,7 +17,8 @@ from typing import Callable, Dict, Iterable, Optional
 from .nursd import NursdError
 
 #: candidate values of each tunable
-DEFAULT_SPACE: Dict[str, Iterable[int]] = {"spread_rows": (4, 8, 16), "batch_streams": (1, 2, 4, 8, 16)}
+DEFAULT_SPACE: Dict[str, Iterable[int]] = {"batch_grouped": (1, 0), "spread_rows": (4, 8, 16),
+                                           "batch_streams": (1, 2, 4, 8, 16)}
 
 
 def default_cache_path() -> str:

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libnursd.so")
-SOURCES = ["api.cu", "fft.cu", "fft_reg.cu", "temporal_tc.cu", "temporal_umma.cu", "points.cu", "spread.cu", "contract.cu", "gtf.cu", "interp.cu", "illum.cu", "srsd_interp.cu", "resample.cu", "nursd3d.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "fft.cu", "fft_reg.cu", "temporal_tc.cu", "temporal_umma.cu", "points.cu", "spread.cu", "contract.cu", "contract_umma.cu", "gtf.cu", "interp.cu", "illum.cu", "srsd_interp.cu", "resample.cu", "nursd3d.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

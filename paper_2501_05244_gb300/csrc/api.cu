@@ -96,6 +96,9 @@ struct nursd_plan_s {
   // tunables (nursd_plan_tune): spread tile height; streams of the batched form
   int spread_rows = 8;
   int batch_streams = 4;
+  int batch_grouped = 1;
+  int batch_tensor = 1;  // the batched contraction on the tensor cores where supported
+  int group_size = 0;  // items per grouped launch (1 .. group; 0 until the workspaces exist)
   // geometry
   int N = 0, M = 0, nf = 0, Z = 0, F = 0, T = 0, w = 0, W = 0, tiles = 0, g0 = 0, ncls = 0, maxL = 0, L = -1;
   double pitch = 0, cx = 0, cy = 0, t0 = 0, dt = 0;
@@ -218,9 +221,32 @@ struct nursd_plan_s {
   // side stream of nursd_reconstruct (the point sort runs there, beside the temporal transform)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  // batched form: workspaces of streams 1 .. kMaxBatchStreams - 1 (stream 0 is the caller's, with the
-  // plan's own workspace), their streams and fork / join events
-  Workspace bws[kMaxBatchStreams];
+  // batched form: `group` item workspaces side by side (gws: item b's arrays at b times the strides
+  // below), used together by the batched launches and one per stream by the per-item form; the
+  // streams 1 .. kMaxBatchStreams - 1 of that form (stream 0 is the caller's) and fork / join events
+  int group = 0;
+  Workspace gws;
+  struct ItemStrides {
+    size_t pts = 0, wts = 0, counts = 0, bins = 0, fine = 0, R1 = 0, T1 = 0;
+  } gst;
+  Workspace group_item(int b) const {
+    Workspace w;
+    w.bin_of = gws.bin_of + b * gst.pts;
+    w.i0_orig = gws.i0_orig + b * gst.pts;
+    w.slot_of = gws.slot_of + b * gst.pts;
+    w.w_orig = gws.w_orig + b * gst.wts;
+    w.counts = gws.counts + b * gst.counts;
+    w.bin_start = gws.bin_start + b * gst.bins;
+    w.sorted_l = gws.sorted_l + b * gst.pts;
+    w.i0_sorted = gws.i0_sorted + b * gst.pts;
+    w.w_sorted = gws.w_sorted + b * gst.wts;
+    w.frac_orig = gws.frac_orig + b * gst.pts;
+    w.frac_sorted = gws.frac_sorted + b * gst.pts;
+    w.fine = gws.fine + b * gst.fine;
+    w.R1 = gws.R1 + b * gst.R1;
+    w.T1 = gws.T1 + b * gst.T1;
+    return w;
+  }
   cudaStream_t bstream[kMaxBatchStreams] = {};
   cudaEvent_t bev_fork = nullptr, bev_join[kMaxBatchStreams] = {};
   Workspace own() const {
@@ -345,13 +371,18 @@ PanelArgs panel_base(const nursd_plan_s* p) {
 }
 
 // Channel-last 1-D pass along an axis of length n_axis (window nin at offset in_off,
-// nout bins at out_off), for C contiguous channels and `batch` items.
+// nout bins at out_off), for C contiguous channels and `batch` items, optionally for nhi blocks of
+// them at in_shi / out_shi.
 cudaError_t axis_pass(const nursd_plan_s* p, const float2* in, float2* out, int logn, bool inv, int C, int batch,
                       long long in_sb, long long in_si, long long out_sb, long long out_si, int nin, int in_off,
-                      int nout, int out_off, const float* mul_o, const float* mul_b, float scale, cudaStream_t s) {
+                      int nout, int out_off, const float* mul_o, const float* mul_b, float scale, cudaStream_t s,
+                      int nhi = 1, long long in_shi = 0, long long out_shi = 0) {
   PanelArgs a = panel_base(p);
   a.in = in;
   a.out = out;
+  a.hi_total = nhi;  // an outer channel index (the items of a batched call), one per panel
+  a.in_shi = in_shi;
+  a.out_shi = out_shi;
   a.in_sb = in_sb;
   a.in_si = in_si;
   a.in_slo = 1;
@@ -540,7 +571,9 @@ int run_nufft1(nursd_plan_s* p, const float2* phasor, float2* spec, cudaStream_t
 
 // The second of the two pruned inverse passes: T [M][N][C] (ky, mx, c) -> out[c][my][mx], the
 // inverse FFT along ky for every (mx, c) with my kept in I_N and the M^-2 scale; complex, or |.|.
-cudaError_t idft_crop_y(nursd_plan_s* p, const float2* T, int C, void* out, bool mag, cudaStream_t s) {
+// batch > 1: items b < batch of T at b in_sb, written at out + b out_sb (elements of the output type).
+cudaError_t idft_crop_y(nursd_plan_s* p, const float2* T, int C, void* out, bool mag, cudaStream_t s, int batch = 1,
+                        long long in_sb = 0, long long out_sb = 0) {
   const int M = p->M, N = p->N;
   const int logM = ilog2(M);
   cudaError_t e;
@@ -569,6 +602,9 @@ cudaError_t idft_crop_y(nursd_plan_s* p, const float2* T, int C, void* out, bool
     a.CHI = cp / a.CLO;
     a.scale = 1.f / ((float)M * (float)M);
     a.store_hi_fastest = 1;
+    a.batch = batch;
+    a.in_sb = in_sb;
+    a.out_sb = out_sb;
     e = launch_panel_fft(logM, true, a, s);
   }
   return e;
@@ -1236,20 +1272,36 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
   if (ok && (p->flags & NURSD_ENABLE_ADJOINT))
     ok = p->alloc(p->GcT, (size_t)p->ncls * p->F * p->Z) && p->alloc(p->deconv_k, p->M) &&
          p->alloc(p->fine_dx, (size_t)p->W * p->W * p->F) && p->alloc(p->fine_dy, (size_t)p->W * p->W * p->F);
-  for (int k = 1; ok && p->maxB > 0 && k < kMaxBatchStreams; ++k) {  // the batched form's other streams
-    Workspace& w = p->bws[k];
+  if (ok && p->maxB > 0) {  // the batched form's item workspaces, as many items as fit in 8 GiB
+    auto& g = p->gst;
     const size_t C = std::max(p->F, p->Z);
-    ok = p->alloc(w.bin_of, maxL) && p->alloc(w.i0_orig, maxL) && p->alloc(w.w_orig, (size_t)maxL * 2 * p->w) &&
-         p->alloc(w.counts, (size_t)2 * nbins) && p->alloc(w.bin_start, nbins + 1) && p->alloc(w.sorted_l, maxL) &&
-         p->alloc(w.slot_of, maxL) && p->alloc(w.i0_sorted, maxL) && p->alloc(w.w_sorted, (size_t)maxL * 2 * p->w) &&
-         p->alloc(w.frac_orig, maxL) && p->alloc(w.frac_sorted, maxL) && p->alloc(w.fine, (size_t)p->W * p->W * C) &&
-         p->alloc(w.R1, (size_t)p->W * p->M * C) && p->alloc(w.T1, (size_t)p->M * p->N * p->Z);
-    if (ok && (cudaStreamCreateWithFlags(&p->bstream[k], cudaStreamNonBlocking) != cudaSuccess ||
-               cudaEventCreateWithFlags(&p->bev_join[k], cudaEventDisableTiming) != cudaSuccess)) {
+    g.pts = maxL;
+    g.wts = (size_t)maxL * 2 * p->w;
+    g.counts = (size_t)2 * nbins;
+    g.bins = (size_t)nbins + 1;
+    g.fine = (size_t)p->W * p->W * C;
+    g.R1 = (size_t)p->W * p->M * C;
+    g.T1 = (size_t)p->M * p->N * p->Z;
+    const size_t per_item = g.pts * (3 * sizeof(int) + 4 * sizeof(int2)) + g.wts * 2 * sizeof(float) +
+                            (g.counts + g.bins) * sizeof(int) + (g.fine + g.R1 + g.T1) * sizeof(float2);
+    const size_t budget = size_t(8) << 30;
+    p->group = (int)std::min<size_t>(p->maxB, std::max<size_t>(1, budget / per_item));
+    p->group_size = p->group;
+    const size_t G = p->group;
+    Workspace& w = p->gws;
+    ok = p->alloc(w.bin_of, G * g.pts) && p->alloc(w.i0_orig, G * g.pts) && p->alloc(w.w_orig, G * g.wts) &&
+         p->alloc(w.counts, G * g.counts) && p->alloc(w.bin_start, G * g.bins) && p->alloc(w.sorted_l, G * g.pts) &&
+         p->alloc(w.slot_of, G * g.pts) && p->alloc(w.i0_sorted, G * g.pts) && p->alloc(w.w_sorted, G * g.wts) &&
+         p->alloc(w.frac_orig, G * g.pts) && p->alloc(w.frac_sorted, G * g.pts) && p->alloc(w.fine, G * g.fine) &&
+         p->alloc(w.R1, G * g.R1) && p->alloc(w.T1, G * g.T1);
+    if (ok) ok = cudaMemsetAsync(w.bin_start, 0, sizeof(int) * G * g.bins, s) == cudaSuccess;
+  }
+  for (int k = 1; ok && p->maxB > 0 && k < kMaxBatchStreams; ++k) {  // the per-item form's other streams
+    if (cudaStreamCreateWithFlags(&p->bstream[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->bev_join[k], cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       ok = false;
     }
-    if (ok) ok = cudaMemsetAsync(w.bin_start, 0, sizeof(int) * (nbins + 1), s) == cudaSuccess;
   }
   if (ok && p->maxB > 0 && cudaEventCreateWithFlags(&p->bev_fork, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
@@ -1328,7 +1380,7 @@ int nursd_plan_dims(nursd_plan_t plan, int32_t* M, int32_t* fine_n, int32_t* n_c
 
 namespace {
 // Coordinate map, weights and bin sort of L samples on stream s (Sec. 6, NUFFT-1 step 1).
-int set_points_on(nursd_plan_t p, int32_t L, const float* d_xy, cudaStream_t s) {
+PointsArgs points_args(const nursd_plan_s* p, int32_t L, const float* d_xy) {
   PointsArgs a;
   a.xy = d_xy;
   a.L = L;
@@ -1342,6 +1394,11 @@ int set_points_on(nursd_plan_t p, int32_t L, const float* d_xy, cudaStream_t s) 
   a.width = p->w;
   a.beta = p->beta;
   a.status = p->status;
+  return a;
+}
+
+int set_points_on(nursd_plan_t p, int32_t L, const float* d_xy, cudaStream_t s) {
+  const PointsArgs a = points_args(p, L, d_xy);
   int rc;
   {
     StageTimer t(p, NURSD_STAGE_POINTS, s, L > 0 ? 5 : 0);
@@ -1741,6 +1798,18 @@ int nursd_transient_frames(nursd_plan_t p, int32_t n_frames, const double* h_tim
   return rc;
 }
 
+namespace {
+// The contraction of B items sharing the table: on the tensor cores when the shape allows (a dense
+// product per symmetry class once several items share it), else the bulk-copy SIMT kernel.
+cudaError_t contract_items(nursd_plan_s* p, long long u_stride, long long y_stride, int B, cudaStream_t s) {
+  if (B >= 2 && p->batch_tensor && contract_umma_supported(p->M, p->F, p->Z, B, u_stride, y_stride))
+    return launch_contract_umma(p->U_all, u_stride, p->Gc, p->cls, p->ncls, p->M, p->F, p->Z, p->Y_all, y_stride, B,
+                                p->status, s);
+  return launch_contract_batched(p->U_all, u_stride, p->Gc, p->cls, p->ncls, p->M, p->F, p->Z, p->Y_all, y_stride, B,
+                                 s, p->status);
+}
+}  // namespace
+
 int nursd_forward_batched(nursd_plan_t p, int32_t B, const nursd_batch_item* items, nursd_stream_t stream) {
   if (check_plan(p) != NURSD_OK || p->maxB <= 0 || B < 1 || B > p->maxB || !items) return NURSD_ERR_INVALID_ARG;
   for (int b = 0; b < B; ++b) {
@@ -1773,7 +1842,7 @@ int nursd_forward_batched(nursd_plan_t p, int32_t B, const nursd_batch_item* ite
   // plan's own workspace, and up to kMaxBatchStreams - 1 side streams with their own), forked from and
   // joined into the caller's stream, so that the items' small launches run side by side.  The last
   // item runs on the plan's own workspace, so the plan keeps its points as a single call would.
-  const int S = std::max(1, std::min(p->batch_streams, B));
+  const int S = std::max(1, std::min(std::min(p->batch_streams, B), p->group));
   const Workspace own = p->own();
   auto fork = [&]() -> int {
     int r = from_cuda(cudaEventRecord(p->bev_fork, s));
@@ -1794,13 +1863,99 @@ int nursd_forward_batched(nursd_plan_t p, int32_t B, const nursd_batch_item* ite
     for (int b = 0; r == NURSD_OK && b < B; ++b) {
       const int k = (B - 1 - b) % S;
       cudaStream_t sk = k == 0 ? s : p->bstream[k];
-      p->use(k == 0 ? own : p->bws[k]);
+      p->use(k == 0 ? own : p->group_item(k));
       r = fn(b, sk);
       p->use(own);
     }
     const int j = join();
     return r != NURSD_OK ? r : j;
   };
+  // Grouped form: when the outputs lie side by side (one stride apart) and the plan has it enabled,
+  // every stage runs as one launch over a group of up to p->group items (the item index a grid or
+  // panel dimension): point sort, spread, both forward passes; then the contraction over all items;
+  // then both inverse passes.  The launch count depends on ceil(B / group), not on B.
+  const bool mag = (p->flags & NURSD_OUTPUT_MAGNITUDE) != 0;
+  const long long ebytes = mag ? (long long)sizeof(float) : (long long)sizeof(float2);
+  const long long vol_bytes = (long long)p->N * p->N * Z * ebytes;
+  long long out_step = 0;  // elements between consecutive items' outputs
+  bool side_by_side = p->batch_grouped != 0 && p->group > 0;
+  if (side_by_side && B > 1) {
+    const long long d = static_cast<const char*>(items[1].d_out) - static_cast<const char*>(items[0].d_out);
+    side_by_side = d >= vol_bytes && d % ebytes == 0;
+    for (int b = 2; side_by_side && b < B; ++b)
+      side_by_side = static_cast<const char*>(items[b].d_out) - static_cast<const char*>(items[0].d_out) == b * d;
+    out_step = d / ebytes;
+  }
+  if (rc == NURSD_OK && side_by_side) {
+    const int N = p->N, W = p->W, G = std::max(1, std::min(p->group_size, p->group));
+    const int logf = ilog2(p->nf), logM = ilog2(M);
+    const nursd_plan_s::ItemStrides& g = p->gst;
+    const Workspace& gw = p->gws;
+    const long long fine_st = (long long)W * W * F, r1_st = (long long)W * M * F, t1_st = (long long)M * N * Z;
+    // the plan keeps the last item's points, as a single call would: sorted on stream 1 beside the batch
+    rc = from_cuda(cudaEventRecord(p->bev_fork, s));
+    if (rc == NURSD_OK) rc = from_cuda(cudaStreamWaitEvent(p->bstream[1], p->bev_fork, 0));
+    if (rc == NURSD_OK) rc = set_points_on(p, items[B - 1].L, items[B - 1].d_xy, p->bstream[1]);
+    const int rj = from_cuda(cudaEventRecord(p->bev_join[1], p->bstream[1]));
+    if (rc == NURSD_OK) rc = rj;
+    const PointsArgs pa = points_args(p, 0, nullptr);
+    for (int g0 = 0; rc == NURSD_OK && g0 < B; g0 += G) {
+      const int n = std::min(G, B - g0);
+      PointsItems it;
+      for (int b = 0; b < n; ++b) {
+        it.L[b] = items[g0 + b].L;
+        it.xy[b] = items[g0 + b].d_xy;
+      }
+      {
+        StageTimer t(p, NURSD_STAGE_POINTS, s, 5);
+        rc = from_cuda(launch_points_batched(pa, it, n, (long long)g.pts, gw.bin_of, gw.i0_orig, gw.w_orig, gw.counts,
+                                             gw.bin_start, gw.sorted_l, gw.i0_sorted, gw.w_sorted, nullptr, nullptr,
+                                             nullptr, s));
+      }
+      if (rc == NURSD_OK) {
+        StageTimer t(p, NURSD_STAGE_SPREAD, s, 1);
+        SpreadItems si;
+        si.n = n;
+        si.p_stride = (long long)phasor_stride;
+        si.pts = (long long)g.pts;
+        si.fine_stride = fine_st;
+        si.bstride = (int)g.bins;
+        rc = from_cuda(launch_spread(p->phasor_all + g0 * phasor_stride, F, gw.bin_start, gw.sorted_l, gw.i0_sorted,
+                                     gw.w_sorted, p->w, p->tiles, W, gw.fine, s, p->spread_rows, si));
+      }
+      if (rc == NURSD_OK) {  // FFT along x of every window row of every item (rows of items back to back)
+        StageTimer t(p, NURSD_STAGE_FFT_X, s, 1);
+        rc = from_cuda(axis_pass(p, gw.fine, gw.R1, logf, false, F, n * W, (long long)W * F, F, (long long)M * F, F,
+                                 W, p->g0, M, -M / 2, nullptr, nullptr, 1.f, s));
+      }
+      if (rc == NURSD_OK) {  // FFT along y of every kx column with the deconvolution, items as outer channels
+        StageTimer t(p, NURSD_STAGE_FFT_Y, s, 1);
+        rc = from_cuda(axis_pass(p, gw.R1, p->U_all + g0 * u_stride, logf, false, F, M, F, (long long)M * F, F,
+                                 (long long)M * F, W, p->g0, M, -M / 2, p->deconv, p->deconv, 1.f, s, n, r1_st,
+                                 u_stride));
+      }
+    }
+    if (rc == NURSD_OK) {
+      StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
+      rc = from_cuda(contract_items(p, u_stride, y_stride, B, s));
+    }
+    for (int g0 = 0; rc == NURSD_OK && g0 < B; g0 += G) {
+      const int n = std::min(G, B - g0);
+      {  // inverse along kx of every ky row of every item, keep mx in I_N
+        StageTimer t(p, NURSD_STAGE_IFFT_X, s, 1);
+        rc = from_cuda(axis_pass(p, p->Y_all + g0 * y_stride, gw.T1, logM, true, Z, n * M, (long long)M * Z, Z,
+                                 (long long)N * Z, Z, M, -M / 2, N, -N / 2, nullptr, nullptr, 1.f, s));
+      }
+      if (rc == NURSD_OK) {
+        char* out0 = static_cast<char*>(items[g0].d_out);
+        rc = from_cuda(idft_crop_y(p, gw.T1, Z, out0, mag, s, n, t1_st, out_step));
+      }
+    }
+    const int rw = from_cuda(cudaStreamWaitEvent(s, p->bev_join[1], 0));  // join even after an error
+    if (rc == NURSD_OK) rc = rw;
+    if (rc == NURSD_OK) p->L = items[B - 1].L;
+    return rc;
+  }
   if (rc == NURSD_OK)
     rc = each_item([&](int b, cudaStream_t sk) {
       int r = set_points_on(p, items[b].L, items[b].d_xy, sk);
@@ -1809,9 +1964,7 @@ int nursd_forward_batched(nursd_plan_t p, int32_t B, const nursd_batch_item* ite
     });
   if (rc == NURSD_OK) {
     StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
-    rc = from_cuda(
-        launch_contract_batched(p->U_all, u_stride, p->Gc, p->cls, p->ncls, M, F, Z, p->Y_all, y_stride, B, s,
-                                p->status));
+    rc = from_cuda(contract_items(p, u_stride, y_stride, B, s));
   }
   if (rc == NURSD_OK)
     rc = each_item([&](int b, cudaStream_t sk) { return run_idft_crop(p, items[b].d_out, sk, p->Y_all + b * y_stride); });
@@ -1830,6 +1983,18 @@ int nursd_plan_tune(nursd_plan_t p, int32_t param, int32_t value) {
       if (value < 1 || value > kMaxBatchStreams) return NURSD_ERR_UNSUPPORTED;
       p->batch_streams = value;
       return NURSD_OK;
+    case NURSD_TUNE_BATCH_GROUPED:
+      if (value != 0 && value != 1) return NURSD_ERR_UNSUPPORTED;
+      p->batch_grouped = value;
+      return NURSD_OK;
+    case NURSD_TUNE_BATCH_GROUP:
+      if (value < 1 || value > p->group) return NURSD_ERR_UNSUPPORTED;
+      p->group_size = value;
+      return NURSD_OK;
+    case NURSD_TUNE_BATCH_TENSOR:
+      if (value != 0 && value != 1) return NURSD_ERR_UNSUPPORTED;
+      p->batch_tensor = value;
+      return NURSD_OK;
     default:
       return NURSD_ERR_INVALID_ARG;
   }
@@ -1840,6 +2005,9 @@ int nursd_plan_get_tune(nursd_plan_t p, int32_t param, int32_t* value) {
   switch (param) {
     case NURSD_TUNE_SPREAD_ROWS: *value = p->spread_rows; return NURSD_OK;
     case NURSD_TUNE_BATCH_STREAMS: *value = p->batch_streams; return NURSD_OK;
+    case NURSD_TUNE_BATCH_GROUPED: *value = p->batch_grouped; return NURSD_OK;
+    case NURSD_TUNE_BATCH_GROUP: *value = p->group_size; return NURSD_OK;
+    case NURSD_TUNE_BATCH_TENSOR: *value = p->batch_tensor; return NURSD_OK;
     default: return NURSD_ERR_INVALID_ARG;
   }
 }

@@ -214,9 +214,16 @@ cudaError_t launch_points_batched(const PointsArgs& a, const PointsItems& items,
 // sorted_l == nullptr: P is already in sorted-slot order (row s of P is sorted sample s).  rows: tile
 // height (spread_rows_supported: 4, 8 or 16; W must be a multiple of it).
 bool spread_rows_supported(int rows);
+// n items of a batched call (grid z): item b's phasors at P + b p_stride, its sorted per-sample arrays
+// at b pts (weights b pts 2w), its bin_start at b bstride and its window at fine + b fine_stride.
+struct SpreadItems {
+  int n = 1;
+  long long p_stride = 0, pts = 0, fine_stride = 0;
+  int bstride = 0;
+};
 cudaError_t launch_spread(const float2* P, int F, const int* bin_start, const int* sorted_l,
                           const int2* i0, const float* wts, int width, int tiles, int W,
-                          float2* fine, cudaStream_t s, int rows = 8);
+                          float2* fine, cudaStream_t s, int rows = 8, const SpreadItems& items = SpreadItems());
 
 // ------------------------------------------------------------- contraction
 // Y[k][z] = sum_f U[k][f] * Gc[cls(k)][f][z] for every mode k of every class.
@@ -285,6 +292,15 @@ cudaError_t launch_gtf_generate(float2* g, int M, double pitch, const double* d_
 // Gs[((z0 + zb) * ncls + c) * F + f] = Gfull[rep(c)][zb*F + f] (per-depth blocks, f fastest)
 cudaError_t launch_gtf_compress_depthmajor(const float2* Gfull, const int2* cls_pq, int ncls, int M, int F, int ZB,
                                            int z0, float2* Gs, cudaStream_t s);
+// ------------------------------------------- batched contraction on the tensor cores (contract_umma.cu)
+// Y[b][k][z] = sum_f U[b][k][f] * Gc[cls(k)][f][z] for every mode k and item b < B (item b's spectrum
+// at U + b u_stride, its depth spectra at Y + b y_stride), as tcgen05 kind::tf32 products with a
+// head/tail split (FP32 accuracy).  Supported for M a power of two, F a multiple of 8 and Z in
+// {32, 64, 128}; status (device int) gets bit 2 when a bounded wait gave up.
+bool contract_umma_supported(int M, int F, int Z, int B, long long u_stride, long long y_stride);
+cudaError_t launch_contract_umma(const float2* U, long long u_stride, const float2* Gc, const int2* cls_pq, int ncls,
+                                 int M, int F, int Z, float2* Y, long long y_stride, int B, int* status,
+                                 cudaStream_t s);
 // ------------------------------------------------- SRSD by interpolation (srsd_interp.cu)
 // Yh [L][L][F] at index m + L/2 (periodic in m).
 // Both taps and the contraction in one pass for every depth z in zlist[0 .. nz) (device list; 4 <= w <= 8;

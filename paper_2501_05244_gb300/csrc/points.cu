@@ -13,16 +13,47 @@
 // by sample index and a gather of the per-sample data into sorted order.  The
 // order inside every bin is thus fixed, so the spread -- and the FP32 rounding
 // of its sums -- is reproducible run to run.
+#include <algorithm>
+
 #include "nursd_internal.cuh"
 
 namespace nursd {
 namespace {
 
-__global__ void points_prepare(const PointsArgs a, int2* __restrict__ i0_out, float* __restrict__ w_out,
-                               int* __restrict__ bin_of, float2* __restrict__ frac_out, int* __restrict__ counts) {
+// The samples of one call (OneItem) or of the items of a batched call (PointsItems, item = blockIdx.y,
+// its per-sample arrays at item * pts, its counts at item * cstride and its bin_start at item * bstride).
+struct OneItem {
+  int L;
+  const float* xy;
+  __device__ int len(int) const { return L; }
+  __device__ const float* pos(int) const { return xy; }
+};
+struct ManyItems {
+  PointsItems it;
+  __device__ int len(int b) const { return it.L[b]; }
+  __device__ const float* pos(int b) const { return it.xy[b]; }
+};
+struct Strides {
+  long long pts;  // per-sample arrays
+  int cstride;    // counts and cursors (2 nbins)
+  int bstride;    // bin_start (nbins + 1)
+};
+
+template <class Src>
+__global__ void points_prepare(const PointsArgs a, const Src src, const Strides st, int2* __restrict__ i0_out,
+                               float* __restrict__ w_out, int* __restrict__ bin_of, float2* __restrict__ frac_out,
+                               int* __restrict__ counts) {
+  const int item = blockIdx.y;
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= a.L) return;
-  double dx = (double)a.xy[2 * l] - a.cx, dy = (double)a.xy[2 * l + 1] - a.cy;
+  if (l >= src.len(item)) return;
+  const float* xy = src.pos(item);
+  const long long po = item * st.pts;
+  i0_out += po;
+  w_out += po * 2 * a.width;
+  bin_of += po;
+  if (frac_out) frac_out += po;
+  counts += (size_t)item * st.cstride;
+  double dx = (double)xy[2 * l] - a.cx, dy = (double)xy[2 * l + 1] - a.cy;
   const bool ok = (fabs(dx) <= a.half_extent) && (fabs(dy) <= a.half_extent);
   if (!ok) {
     atomicOr(a.status, 1);
@@ -64,9 +95,15 @@ __global__ void points_prepare(const PointsArgs a, int2* __restrict__ i0_out, fl
 // and 17 KB: the CTA fits beside a resident tcgen05 temporal CTA.
 constexpr int kScanThreads = 256, kScanChunk = 4096;
 static_assert(kScanThreads % 32 == 0 && kScanThreads <= 1024 && kScanChunk % kScanThreads == 0, "scan shape");
+// One CTA per item (blockIdx.x).
+template <class Src>
 __global__ void __launch_bounds__(kScanThreads) points_scan(const int* __restrict__ counts, int nbins,
-                                                           int* __restrict__ bin_start, int L) {
+                                                           int* __restrict__ bin_start, const Src src,
+                                                           const Strides st) {
   constexpr int per = kScanChunk / kScanThreads, nw = kScanThreads / 32;
+  const int L = src.len(blockIdx.x);
+  counts += (size_t)blockIdx.x * st.cstride;
+  bin_start += (size_t)blockIdx.x * st.bstride;
   __shared__ int buf[kScanThreads * (per + 1)];
   __shared__ int warp_sum[nw];
   __shared__ int carry;
@@ -116,10 +153,16 @@ __global__ void __launch_bounds__(kScanThreads) points_scan(const int* __restric
   if (tid == 0) bin_start[nbins] = L;
 }
 
-__global__ void points_scatter(const int* __restrict__ bin_of, const int* __restrict__ bin_start, int L,
-                               int* __restrict__ cursor, int* __restrict__ sorted_l) {
+template <class Src>
+__global__ void points_scatter(const int* __restrict__ bin_of, const int* __restrict__ bin_start, const Src src,
+                               const Strides st, int* __restrict__ cursor, int* __restrict__ sorted_l) {
+  const int item = blockIdx.y;
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= L) return;
+  if (l >= src.len(item)) return;
+  bin_of += item * st.pts;
+  sorted_l += item * st.pts;
+  bin_start += (size_t)item * st.bstride;
+  cursor += (size_t)item * st.cstride;
   const int b = bin_of[l];
   sorted_l[bin_start[b] + atomicAdd(cursor + b, 1)] = l;
 }
@@ -128,9 +171,12 @@ __global__ void points_scatter(const int* __restrict__ bin_of, const int* __rest
 // the spread's summation order does not depend on the scatter's arrival order.  Bins of
 // up to kSortLocal samples are sorted in a thread-local array, larger ones in place.
 constexpr int kSortLocal = 32;
-__global__ void points_sort_bins(const int* __restrict__ bin_start, int nbins, int* __restrict__ sorted_l) {
+__global__ void points_sort_bins(const int* __restrict__ bin_start, int nbins, int* __restrict__ sorted_l,
+                                 const Strides st) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= nbins) return;
+  bin_start += (size_t)blockIdx.y * st.bstride;
+  sorted_l += blockIdx.y * st.pts;
   const int s = bin_start[b], e = bin_start[b + 1];
   if (e - s <= kSortLocal) {
     int v[kSortLocal];
@@ -159,12 +205,23 @@ __global__ void points_sort_bins(const int* __restrict__ bin_start, int nbins, i
   }
 }
 
-__global__ void points_gather(const int* __restrict__ sorted_l, int L, int width, const int2* __restrict__ i0_in,
-                              const float* __restrict__ w_in, const float2* __restrict__ frac_in,
-                              int2* __restrict__ i0_out, float* __restrict__ w_out, float2* __restrict__ frac_out,
-                              int* __restrict__ slot_of) {
+template <class Src>
+__global__ void points_gather(const int* __restrict__ sorted_l, const Src src, const Strides st, int width,
+                              const int2* __restrict__ i0_in, const float* __restrict__ w_in,
+                              const float2* __restrict__ frac_in, int2* __restrict__ i0_out,
+                              float* __restrict__ w_out, float2* __restrict__ frac_out, int* __restrict__ slot_of) {
+  const int item = blockIdx.y;
   const int pos = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pos >= L) return;
+  if (pos >= src.len(item)) return;
+  const long long po = item * st.pts;
+  sorted_l += po;
+  i0_in += po;
+  i0_out += po;
+  w_in += po * 2 * width;
+  w_out += po * 2 * width;
+  if (frac_in) frac_in += po;
+  if (frac_out) frac_out += po;
+  if (slot_of) slot_of += po;
   const int l = sorted_l[pos];
   if (slot_of) slot_of[l] = pos;
   i0_out[pos] = i0_in[l];
@@ -176,6 +233,24 @@ __global__ void points_gather(const int* __restrict__ sorted_l, int L, int width
 
 int points_bins(int W, int tiles) { return 2 * W * tiles; }
 
+namespace {
+template <class Src>
+cudaError_t launch_points_on(const PointsArgs& a, const Src& src, int n, int maxL, const Strides& st, int* bin_of,
+                             int2* i0_orig, float* w_orig, int* counts, int* bin_start, int* sorted_l,
+                             int2* i0_sorted, float* w_sorted, cudaStream_t s, float2* frac_orig, float2* frac_sorted,
+                             int* slot_of) {
+  const int nbins = points_bins(a.W, a.tiles);
+  const dim3 grid((unsigned)std::max(1, (maxL + 255) / 256), (unsigned)n);
+  points_prepare<<<grid, 256, 0, s>>>(a, src, st, i0_orig, w_orig, bin_of, frac_orig, counts);
+  points_scan<<<n, kScanThreads, 0, s>>>(counts, nbins, bin_start, src, st);
+  points_scatter<<<grid, 256, 0, s>>>(bin_of, bin_start, src, st, counts + nbins, sorted_l);
+  points_sort_bins<<<dim3((nbins + 255) / 256, (unsigned)n), 256, 0, s>>>(bin_start, nbins, sorted_l, st);
+  points_gather<<<grid, 256, 0, s>>>(sorted_l, src, st, a.width, i0_orig, w_orig, frac_orig, i0_sorted, w_sorted,
+                                     frac_sorted, slot_of);
+  return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_points(const PointsArgs& a, int* bin_of, int2* i0_orig, float* w_orig, int* counts,
                           int* bin_start, int* sorted_l, int2* i0_sorted, float* w_sorted, cudaStream_t s,
                           float2* frac_orig, float2* frac_sorted, int* slot_of) {
@@ -185,14 +260,25 @@ cudaError_t launch_points(const PointsArgs& a, int* bin_of, int2* i0_orig, float
   cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int) * 2 * nbins, s);
   if (e != cudaSuccess) return e;
   if (a.L <= 0) return cudaMemsetAsync(bin_start, 0, sizeof(int) * (nbins + 1), s);
-  const int blocks = (a.L + 255) / 256;
-  points_prepare<<<blocks, 256, 0, s>>>(a, i0_orig, w_orig, bin_of, frac_orig, counts);
-  points_scan<<<1, kScanThreads, 0, s>>>(counts, nbins, bin_start, a.L);
-  points_scatter<<<blocks, 256, 0, s>>>(bin_of, bin_start, a.L, counts + nbins, sorted_l);
-  points_sort_bins<<<(nbins + 255) / 256, 256, 0, s>>>(bin_start, nbins, sorted_l);
-  points_gather<<<blocks, 256, 0, s>>>(sorted_l, a.L, a.width, i0_orig, w_orig, frac_orig, i0_sorted, w_sorted,
-                                      frac_sorted, slot_of);
-  return cudaGetLastError();
+  return launch_points_on(a, OneItem{a.L, a.xy}, 1, a.L, Strides{0, 0, 0}, bin_of, i0_orig, w_orig, counts,
+                          bin_start, sorted_l, i0_sorted, w_sorted, s, frac_orig, frac_sorted, slot_of);
+}
+
+cudaError_t launch_points_batched(const PointsArgs& a, const PointsItems& items, int n, long long pts, int* bin_of,
+                                  int2* i0_orig, float* w_orig, int* counts, int* bin_start, int* sorted_l,
+                                  int2* i0_sorted, float* w_sorted, float2* frac_orig, float2* frac_sorted,
+                                  int* slot_of, cudaStream_t s) {
+  if (n < 1 || n > kMaxBatch || (frac_orig == nullptr) != (frac_sorted == nullptr)) return cudaErrorInvalidValue;
+  const int nbins = points_bins(a.W, a.tiles);
+  int maxL = 0;
+  for (int b = 0; b < n; ++b) {
+    if (items.L[b] < 0 || items.L[b] > pts) return cudaErrorInvalidValue;
+    maxL = std::max(maxL, items.L[b]);
+  }
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int) * 2 * nbins * (size_t)n, s);
+  if (e != cudaSuccess) return e;
+  return launch_points_on(a, ManyItems{items}, n, maxL, Strides{pts, 2 * nbins, nbins + 1}, bin_of, i0_orig, w_orig,
+                          counts, bin_start, sorted_l, i0_sorted, w_sorted, s, frac_orig, frac_sorted, slot_of);
 }
 
 }  // namespace nursd

@@ -67,8 +67,17 @@ __global__ void __launch_bounds__(kRows * 32, 32 / kRows) spread_kernel(const fl
                                                                 const int* __restrict__ sorted_l,
                                                                 const int2* __restrict__ i0,
                                                                 const float* __restrict__ wts, int tiles, int W,
-                                                                float2* __restrict__ fine) {
+                                                                float2* __restrict__ fine, const SpreadItems it) {
   extern __shared__ __align__(16) unsigned char raw[];
+  {  // item blockIdx.z of a batched call: its phasors, sorted samples, bins and window
+    const long long item = blockIdx.z;
+    P += item * it.p_stride;
+    bin_start += item * it.bstride;
+    if (sorted_l) sorted_l += item * it.pts;
+    i0 += item * it.pts;
+    wts += item * it.pts * 2 * KW;
+    fine += item * it.fine_stride;
+  }
   SpreadSmem& sm = *reinterpret_cast<SpreadSmem*>(raw);
   constexpr int kWarps = kRows;  // one warp per tile row
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -180,7 +189,7 @@ __global__ void __launch_bounds__(kRows * 32, 32 / kRows) spread_kernel(const fl
 
 template <int KW, int kRows>
 cudaError_t launch_kw(const float2* P, int F, const int* bin_start, const int* sorted_l, const int2* i0,
-                      const float* wts, int tiles, int W, float2* fine, cudaStream_t s) {
+                      const float* wts, int tiles, int W, float2* fine, const SpreadItems& it, cudaStream_t s) {
   const size_t smem = sizeof(SpreadSmem);
   static bool configured = false;
   if (!configured) {
@@ -189,18 +198,19 @@ cudaError_t launch_kw(const float2* P, int F, const int* bin_start, const int* s
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  dim3 grid((W / kRows) * tiles, (F + kCh - 1) / kCh);
-  spread_kernel<KW, kRows><<<grid, kRows * 32, smem, s>>>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine);
+  dim3 grid((W / kRows) * tiles, (F + kCh - 1) / kCh, it.n);
+  spread_kernel<KW, kRows><<<grid, kRows * 32, smem, s>>>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, it);
   return cudaGetLastError();
 }
 
 template <int KW>
 cudaError_t launch_rows(const float2* P, int F, const int* bin_start, const int* sorted_l, const int2* i0,
-                        const float* wts, int tiles, int W, float2* fine, int rows, cudaStream_t s) {
+                        const float* wts, int tiles, int W, float2* fine, int rows, const SpreadItems& it,
+                        cudaStream_t s) {
   switch (rows) {
-    case 4: return launch_kw<KW, 4>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, s);
-    case 16: return launch_kw<KW, 16>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, s);
-    default: return launch_kw<KW, 8>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, s);
+    case 4: return launch_kw<KW, 4>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, it, s);
+    case 16: return launch_kw<KW, 16>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, it, s);
+    default: return launch_kw<KW, 8>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, it, s);
   }
 }
 
@@ -209,14 +219,16 @@ cudaError_t launch_rows(const float2* P, int F, const int* bin_start, const int*
 bool spread_rows_supported(int rows) { return rows == 4 || rows == 8 || rows == 16; }
 
 cudaError_t launch_spread(const float2* P, int F, const int* bin_start, const int* sorted_l, const int2* i0,
-                          const float* wts, int width, int tiles, int W, float2* fine, cudaStream_t s, int rows) {
-  if (W != tiles * kTile || !spread_rows_supported(rows) || W % rows != 0) return cudaErrorInvalidValue;
+                          const float* wts, int width, int tiles, int W, float2* fine, cudaStream_t s, int rows,
+                          const SpreadItems& it) {
+  if (W != tiles * kTile || !spread_rows_supported(rows) || W % rows != 0 || it.n < 1 || it.n > 65535)
+    return cudaErrorInvalidValue;
   switch (width) {
-    case 4: return launch_rows<4>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, rows, s);
-    case 5: return launch_rows<5>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, rows, s);
-    case 6: return launch_rows<6>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, rows, s);
-    case 7: return launch_rows<7>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, rows, s);
-    case 8: return launch_rows<8>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, rows, s);
+    case 4: return launch_rows<4>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, rows, it, s);
+    case 5: return launch_rows<5>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, rows, it, s);
+    case 6: return launch_rows<6>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, rows, it, s);
+    case 7: return launch_rows<7>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, rows, it, s);
+    case 8: return launch_rows<8>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, rows, it, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -29,7 +29,7 @@ NURSD_CONFOCAL = 0x4
 NURSD_UPSAMPLE_NEAREST = 0
 NURSD_UPSAMPLE_LINEAR = 1
 #: plan tunables (nursd_plan_tune)
-TUNABLES = {"spread_rows": 0, "batch_streams": 1}
+TUNABLES = {"spread_rows": 0, "batch_streams": 1, "batch_grouped": 2, "batch_group": 3, "batch_tensor": 4}
 
 #: every entry point declared in include/nursd.h
 EXPORTS = (
@@ -282,6 +282,11 @@ class Plan:
         torch = _torch()
         return torch.empty(self.out_shape(), dtype=self.out_dtype(), device="cuda")
 
+    def empty_batch_output(self, B: int):
+        """[B][Z][N][N] outputs side by side: forward_batched runs such a batch with grouped launches."""
+        torch = _torch()
+        return torch.empty((B,) + self.out_shape(), dtype=self.out_dtype(), device="cuda")
+
     # -- entry points
     def set_points(self, xy, stream=None):
         torch = _torch()
@@ -375,7 +380,7 @@ class Plan:
         torch = _torch()
         B = len(xys)
         if outs is None:
-            outs = [self.empty_output() for _ in range(B)]
+            outs = list(self.empty_batch_output(B))
         items = (_BatchItem * B)()
         for b in range(B):
             L = int(xys[b].shape[0])

@@ -11,7 +11,7 @@ class FakePlan:
     N, F, Z, T = 128, 64, 64, 512
 
     def __init__(self):
-        self.values = {"spread_rows": 8, "batch_streams": 4}
+        self.values = {"batch_grouped": 1, "spread_rows": 8, "batch_streams": 4}
 
     def tune(self, name, value):
         if name == "spread_rows" and value not in (4, 8, 16):
@@ -29,12 +29,12 @@ def fake_timer(plan, cost):
 
 def test_coordinate_descent_picks_the_fastest_setting_and_caches_it(tmp_path):
     plan = FakePlan()
-    cost = lambda v: abs(v["spread_rows"] - 16) + abs(v["batch_streams"] - 2) * 3 + 1.0
+    cost = lambda v: abs(v["spread_rows"] - 16) + abs(v["batch_streams"] - 2) * 3 + (1 - v["batch_grouped"]) * 5 + 1.0
     path = str(tmp_path / "tune.json")
     r = at.autotune(plan, lambda: None, workload="B=64", cache_path=path, timer=fake_timer(plan, cost), gpu="GB300")
-    assert r["choice"] == {"spread_rows": 16, "batch_streams": 2} and not r["cached"]
+    assert r["choice"] == {"batch_grouped": 1, "spread_rows": 16, "batch_streams": 2} and not r["cached"]
     assert plan.values == r["choice"] and r["ms"] == 1.0
-    assert len(r["results"]) == 3 + 5
+    assert len(r["results"]) == 2 + 3 + 5
     stored = json.load(open(path))
     assert r["key"] in stored and stored[r["key"]]["choice"] == r["choice"]
     # a second plan of the same key takes the cached choice without timing

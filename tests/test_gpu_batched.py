@@ -88,6 +88,36 @@ def test_batched_call_replays_from_a_cuda_graph():
         assert rel(o.cpu().numpy(), r.cpu().numpy()) < 1e-6
 
 
+def test_grouped_batch_replays_from_a_cuda_graph_and_counts_launches_independent_of_b():
+    sizes = [300, 50, 1200, 0, 900, 64]
+    c = small_batch(sizes, seed=13)
+    xys = [torch.from_numpy(x).cuda() for x in c["xys"]]
+    hists = [torch.from_numpy(h).cuda() for h in c["hists"]]
+    counts = []
+    for B in (2, 6):
+        plan = make_plan(c, 6)
+        out = plan.empty_batch_output(B)
+        n0 = plan.launch_count
+        plan.forward_batched(xys[:B], hists[:B], list(out))
+        counts.append(plan.launch_count - n0)
+        torch.cuda.synchronize()
+        ref = out.clone()
+        out.zero_()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            plan.forward_batched(xys[:B], hists[:B], list(out))
+        graph.replay()
+        torch.cuda.synchronize()
+        assert rel(out.cpu().numpy(), ref.cpu().numpy()) < 1e-6
+        for b in range(B):
+            plan.set_points(xys[b])
+            if sizes[b]:
+                assert rel(out[b].cpu().numpy(), plan.forward(hists[b]).cpu().numpy()) < 1e-6, b
+    assert counts[0] == counts[1], counts
+
+
 def test_batched_workload_of_64_uneven_reconstructions():
     # 64 reconstructions with L_b log-uniform in [4096, 65536], T = 512 @ 8 ps, F = 64,
     # 128^2 x 64 voxels; four items (smallest, largest, two others) against single calls.
@@ -102,24 +132,32 @@ def test_batched_workload_of_64_uneven_reconstructions():
     hists = [device_histograms(xys[b], *scenes[b], g.T, g.dt, g.t0, seed=BASE_SEED + 500 + b)
              for b in range(len(sizes))]
     outs = plan.forward_batched(xys, hists)
+    # the batch's contraction runs on the tensor cores (tf32 head/tail products, about 2^-22 of each
+    # product): 2e-6 against the FP32 single calls
     for b in {int(np.argmin(sizes)), int(np.argmax(sizes)), 7, 40}:
         plan.set_points(xys[b])
-        assert rel(outs[b].cpu().numpy(), plan.forward(hists[b]).cpu().numpy()) < 1e-6, b
+        assert rel(outs[b].cpu().numpy(), plan.forward(hists[b]).cpu().numpy()) < 2e-6, b
 
 
-@pytest.mark.parametrize("streams,rows", [(1, 8), (3, 4), (8, 16), (2, 16)])
-def test_batched_equals_single_calls_at_every_stream_count_and_tile_height(streams, rows):
-    # the items run round-robin on `streams` streams with their own workspaces; the spread's tile
-    # height changes only the launch shape
+@pytest.mark.parametrize("grouped,group,streams,rows",
+                         [(0, 6, 1, 8), (0, 6, 3, 4), (0, 6, 8, 16), (0, 6, 2, 16),
+                          (1, 6, 4, 8), (1, 2, 4, 4), (1, 4, 4, 16), (1, 1, 4, 8)])
+def test_batched_equals_single_calls_at_every_setting(grouped, group, streams, rows):
+    # grouped: each stage one launch over `group` items at a time (outputs side by side); else the items
+    # run round-robin on `streams` streams with their own workspaces; the spread's tile height changes
+    # only the launch shape
     sizes = [700, 1, 0, 2049, 33, 400]
     c = small_batch(sizes, seed=11)
     plan = make_plan(c, len(sizes))
+    plan.tune("batch_grouped", grouped)
+    plan.tune("batch_group", group)
     plan.tune("batch_streams", streams)
     plan.tune("spread_rows", rows)
-    assert plan.tuning() == {"spread_rows": rows, "batch_streams": streams}
+    assert plan.tuning() == {"spread_rows": rows, "batch_streams": streams, "batch_grouped": grouped,
+                             "batch_group": group, "batch_tensor": 1}
     xys = [torch.from_numpy(x).cuda() for x in c["xys"]]
     hists = [torch.from_numpy(h).cuda() for h in c["hists"]]
-    outs = plan.forward_batched(xys, hists)
+    outs = plan.forward_batched(xys, hists)  # side by side
     single_plan = make_plan(c, 1)
     for b in range(len(sizes)):
         single_plan.set_points(xys[b])
@@ -133,10 +171,37 @@ def test_batched_equals_single_calls_at_every_stream_count_and_tile_height(strea
     assert plan.sync_status() == 0
 
 
+@pytest.mark.parametrize("F,Z,B", [(8, 32, 19), (16, 64, 3), (24, 128, 17)])
+def test_tensor_core_contraction_equals_the_fp32_kernel(F, Z, B):
+    # the batched contraction as tf32 head/tail tensor-core products per symmetry class (16 items x 8
+    # members per tile; B = 19 and 17 leave a partial item block) against the FP32 SIMT kernel, and one
+    # item against the oracle
+    sizes = [(37 * b) % 300 for b in range(B)]  # item 0 is empty
+    c = small_batch(sizes, F=F, Z=Z, seed=20 + F)
+    xys = [torch.from_numpy(x).cuda() for x in c["xys"]]
+    hists = [torch.from_numpy(h).cuda() for h in c["hists"]]
+    outs = {}
+    for tensor in (1, 0):
+        plan = make_plan(c, B)
+        plan.tune("batch_tensor", tensor)
+        outs[tensor] = plan.forward_batched(xys, hists)
+        assert plan.sync_status() == 0
+    for b in range(B):
+        if sizes[b]:
+            assert rel(outs[1][b].cpu().numpy(), outs[0][b].cpu().numpy()) < 2e-6, b
+        else:
+            assert float(outs[1][b].abs().max()) == 0.0
+    k = B - 1  # a non-empty item
+    P = O.temporal_dft(c["hists"][k], c["t0"], c["dt"], c["om"], np.ones(len(c["om"])))
+    ref = O.nursd_forward(P, c["xys"][k], c["center"], c["pitch"], c["N"], c["depths"], c["om"])
+    assert rel(outs[1][k].cpu().numpy(), ref) < TOL
+
+
 def test_unsupported_tunable_values_are_refused():
     c = small_batch([10, 20])
     plan = make_plan(c, 2)
-    for name, value in (("spread_rows", 6), ("batch_streams", 0), ("batch_streams", 17)):
+    for name, value in (("spread_rows", 6), ("batch_streams", 0), ("batch_streams", 17), ("batch_grouped", 2),
+                        ("batch_group", 0), ("batch_group", 3), ("batch_tensor", 2)):
         with pytest.raises(nursd.NursdError) as err:
             plan.tune(name, value)
         assert err.value.status == nursd.nursd.NURSD_ERR_UNSUPPORTED
@@ -161,4 +226,4 @@ def test_autotuner_keeps_the_results_and_caches_its_choice(tmp_path):
         assert rel(o.cpu().numpy(), want) < 1e-6
     plan2 = make_plan(c, len(sizes))
     r2 = autotune(plan2, lambda: None, workload="test", cache_path=path)
-    assert r2["cached"] and plan2.tuning() == r["choice"]
+    assert r2["cached"] and {k: plan2.tuning()[k] for k in r["choice"]} == r["choice"]
