@@ -1835,7 +1835,17 @@ int nursd_forward_batched(nursd_plan_t p, int32_t B, const nursd_batch_item* ite
       bt.L[b] = items[b].L;
       bt.tile_start[b + 1] = bt.tile_start[b] + ((items[b].L + 127) / 128) * ncol;
     }
-    rc = from_cuda(launch_temporal_tc_batched(bt, p->Bth, p->Btl, p->wcol, p->T, 2 * F, p->tfix, p->counter, s));
+    bool umma = p->tmaps.ok != 0;
+    for (int b = 0; umma && b < B; ++b) umma = aligned(items[b].d_hist, 16) && aligned(bt.C[b], 16);
+    if (umma) {  // the tcgen05 form over 128-row tiles of every item, then the gather of listed rows
+      TemporalBatch bu = bt;
+      for (int b = 0; b < B; ++b) bu.tile_start[b + 1] = bu.tile_start[b] + (items[b].L + 127) / 128;
+      rc = from_cuda(launch_temporal_umma_batched(p->tmaps, bu, p->wcol, p->T, 2 * F, p->tfix, p->status, s));
+      if (rc == NURSD_OK)
+        rc = from_cuda(launch_temporal_tc_gather(bu, p->Bth, p->Btl, p->wcol, p->T, 2 * F, p->tfix, s));
+    } else {
+      rc = from_cuda(launch_temporal_tc_batched(bt, p->Bth, p->Btl, p->wcol, p->T, 2 * F, p->tfix, p->counter, s));
+    }
   }
   // Per item: point sort, spread and the forward fine-grid passes (-> U_all[b]), then after the batched
   // contraction the inverse passes; items go round-robin to S streams (the caller's stream with the

@@ -316,7 +316,11 @@ cudaError_t launch_panel_fft(int logn, bool inverse, const PanelArgs& a, cudaStr
     case 5: return launch_dir<5, 16, 128>(inverse, a, s);
     case 6: return launch_dir<6, 16, 256>(inverse, a, s);
     case 7: return launch_dir<7, 16, 256>(inverse, a, s);
-    case 8: return launch_dir<8, 16, 256>(inverse, a, s);
+    case 8: {
+      const cudaError_t e = launch_panel_fft32_256(inverse, a, s);
+      if (e != cudaErrorNotSupported) return e;
+      return launch_dir<8, 16, 256>(inverse, a, s);
+    }
     case 9:
     case 10:
     case 11: return launch_panel_fft_reg(logn, inverse, a, s);

@@ -716,10 +716,12 @@ __device__ __forceinline__ void fft32_core(float2* v, float2* xbuf, int j0, int 
 #pragma unroll
     for (int t = 0; t < R2; ++t) v[m * R2 + t] = r[t * (32 + PADX) * CP];
     twiddle_row<R2, INV>(v + m * R2, tw2 + j * R2);
-    if (R2 == 32)
+    if constexpr (R2 == 32)
       dft32<INV>(v + m * R2);
-    else
+    else if constexpr (R2 == 16)
       dft16<INV>(v + m * R2);
+    else
+      dft8<INV>(v + m * R2);
   }
 }
 
@@ -1089,6 +1091,51 @@ cudaError_t launch_bluestein_reg(const PanelArgs& a, const float2* cpre, const f
 
 // Panel widths (channels per CTA) of the register kernels.
 int panel_width_reg(int logn) { return logn == 11 ? 4 : 8; }
+
+// n = 256 as 32 x 8 in the radix-32 persistent form, 16-channel panels (the width of the shared-memory
+// form it replaces); cudaErrorNotSupported when the launch is too small for a persistent grid.
+cudaError_t launch_panel_fft32_256(bool inverse, const PanelArgs& a, cudaStream_t s) {
+  constexpr int LOGN = 8, CP = 16;
+  using R = R32Shape<LOGN, CP>;
+  if (a.CHI * a.CLO != CP || a.prod_g || !axis_offsets_fit(R::n, a)) return cudaErrorNotSupported;
+  const int nhi = (a.hi_total + a.CHI - 1) / a.CHI;
+  const int nlo = (a.lo_total + a.CLO - 1) / a.CLO;
+  const long long npanel = (long long)nhi * nlo * a.batch;
+  const int sms = sm_count();
+  const size_t mo_bytes = a.mul_o ? sizeof(float) * (size_t)a.nout : 0;
+  const size_t smem = sizeof(float2) * ((size_t)R::XROWS * CP + (size_t)(a.nin + 1) * CP) + mo_bytes;
+  if (npanel < 4LL * sms || npanel >= (1LL << 31) || smem > 220 * 1024 || (long long)nhi * nlo >= (1LL << 22))
+    return cudaErrorNotSupported;
+  const void* optr = a.out_mag ? static_cast<const void*>(a.out_mag) : static_cast<const void*>(a.out);
+  const int in_vec2 = !a.load_i_fastest && a.in_slo == 1 && a.CLO % 2 == 0 && a.lo_total % 2 == 0 &&
+                      reinterpret_cast<uintptr_t>(a.in) % 16 == 0 && a.in_sb % 2 == 0 && a.in_si % 2 == 0 &&
+                      a.in_shi % 2 == 0;
+  const int out_vec2 = a.out_slo == 1 && a.CLO % 2 == 0 && a.lo_total % 2 == 0 &&
+                       reinterpret_cast<uintptr_t>(optr) % (a.out_mag ? 8 : 16) == 0 && a.out_sb % 2 == 0 &&
+                       a.out_si % 2 == 0 && a.out_shi % 2 == 0;
+  auto run = [&](auto kern, int& occ, size_t& occ_smem, bool& configured) -> cudaError_t {
+    if (!configured) {
+      cudaError_t e = configure(kern, 220 * 1024);
+      if (e != cudaSuccess) return e;
+      configured = true;
+    }
+    if (occ_smem != smem) {
+      int nb = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, R::NT, smem);
+      if (e != cudaSuccess) return e;
+      occ = std::max(nb, 1);
+      occ_smem = smem;
+    }
+    const int grid = (int)std::min<long long>(npanel, (long long)sms * occ);
+    kern<<<grid, R::NT, smem, s>>>(a, (int)npanel, in_vec2, out_vec2);
+    return cudaGetLastError();
+  };
+  static int occ_f = 1, occ_i = 1;
+  static size_t sm_f = 0, sm_i = 0;
+  static bool cf = false, ci = false;
+  return inverse ? run(panel_fft32_kernel<LOGN, CP, true>, occ_i, sm_i, ci)
+                 : run(panel_fft32_kernel<LOGN, CP, false>, occ_f, sm_f, cf);
+}
 
 cudaError_t launch_panel_fft_reg(int logn, bool inverse, const PanelArgs& a, cudaStream_t s) {
   switch (logn) {

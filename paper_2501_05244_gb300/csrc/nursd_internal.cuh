@@ -29,14 +29,14 @@ constexpr int kMaxBatch = 256;     // reconstructions per batched call
 //   kTw2Offset + 16 k + t       W_256^{k t}            (k, t < 16; the radix-16 x 16 middle stage)
 //   tw3_offset(lg) + R j + t    W_{2^lg}^{j t}         (j < 256, t < R = 2^lg / 256; the last stage)
 //   tw32_offset(lg) + R j + t   W_{2^lg}^{j t}         (j < 32, t < R = 2^lg / 32; the second stage of
-//                                                       the radix-32 form, lg = 9, 10)
+//                                                       the radix-32 form, lg = 9, 10, then 8)
 // so that a thread reads its whole row of twiddles at one base address.
 constexpr int kTw2Offset = 1 << kTwiddleLog;
 constexpr int kTw3Offset = kTw2Offset + 256;
 __host__ __device__ constexpr int tw3_offset(int lg) { return kTw3Offset + (lg == 9 ? 0 : (lg == 10 ? 512 : 1536)); }
 constexpr int kTw32Offset = kTw3Offset + 512 + 1024 + 2048;
-__host__ __device__ constexpr int tw32_offset(int lg) { return kTw32Offset + (lg == 9 ? 0 : 512); }
-constexpr int kTwiddleEntries = kTw32Offset + 512 + 1024;
+__host__ __device__ constexpr int tw32_offset(int lg) { return kTw32Offset + (lg == 9 ? 0 : (lg == 10 ? 512 : 1536)); }
+constexpr int kTwiddleEntries = kTw32Offset + 512 + 1024 + 256;
 // Entry e of the table is exp(-2 pi i num / 2^lg).
 __host__ __device__ inline void twiddle_exponent(int e, int* num, int* lg) {
   if (e < kTw2Offset) {
@@ -52,7 +52,7 @@ __host__ __device__ inline void twiddle_exponent(int e, int* num, int* lg) {
     *num = (r / R) * (r % R);
     *lg = l;
   } else {
-    const int l = e < tw32_offset(10) ? 9 : 10;
+    const int l = e < tw32_offset(10) ? 9 : (e < tw32_offset(8) ? 10 : 8);
     const int r = e - tw32_offset(l), R = 1 << (l - 5);
     *num = (r / R) * (r % R);
     *lg = l;
@@ -100,6 +100,9 @@ struct PanelArgs {
 
 // Launches the panel FFT of length 2^logn (4 <= 2^logn <= 2048). Returns a cudaError_t.
 cudaError_t launch_panel_fft(int logn, bool inverse, const PanelArgs& a, cudaStream_t s);
+// Length 256 in the persistent radix-32 register form (16-channel panels); cudaErrorNotSupported
+// (nothing launched) when the pass has too few panels for it.
+cudaError_t launch_panel_fft32_256(bool inverse, const PanelArgs& a, cudaStream_t s);
 // Panel width (channels per CTA) used for a given transform length.
 int panel_width(int logn);
 // Register-resident kernels for 2^9..2^11 (fft_reg.cu).
@@ -175,6 +178,14 @@ struct TemporalBatch {
 };
 cudaError_t launch_temporal_tc_batched(const TemporalBatch& bt, const void* Bh, const void* Bl, const float* wcol,
                                        int T, int twoF, const TemporalFix& fix, int* counter, cudaStream_t s);
+// The listed rows of every item of bt (TemporalFix entries {row, e, item, 0}) recomputed from h 2^-e
+// by the mma.sync form (the second launch of the batched transforms).
+cudaError_t launch_temporal_tc_gather(const TemporalBatch& bt, const void* Bh, const void* Bl, const float* wcol,
+                                      int T, int twoF, const TemporalFix& fix, cudaStream_t s);
+// The tcgen05 transform of every item of bt in one persistent launch (bt.tile_start counting 128-row
+// tiles); rows outside the split's window are listed in fix for launch_temporal_tc_gather.
+cudaError_t launch_temporal_umma_batched(const TemporalMaps& m, const TemporalBatch& bt, const float* wcol, int T,
+                                         int twoF, const TemporalFix& fix, int* status, cudaStream_t s);
 
 // ---------------------------------------------------------------- points
 struct PointsArgs {

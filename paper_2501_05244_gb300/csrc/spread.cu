@@ -61,7 +61,7 @@ __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
 // carries its x weights laid out on the tile's 16 cells (zeros outside its footprint), so the
 // warp adds it to every cell of its row with 16 packed FMAs and no branch on the offset; a
 // zero weight leaves a cell's sum unchanged, so the result equals the footprint-only sum.
-template <int KW, int kRows>
+template <int KW, int kRows, bool BATCH>
 __global__ void __launch_bounds__(kRows * 32, 32 / kRows) spread_kernel(const float2* __restrict__ P, int F,
                                                                 const int* __restrict__ bin_start,
                                                                 const int* __restrict__ sorted_l,
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(kRows * 32, 32 / kRows) spread_kernel(const fl
                                                                 const float* __restrict__ wts, int tiles, int W,
                                                                 float2* __restrict__ fine, const SpreadItems it) {
   extern __shared__ __align__(16) unsigned char raw[];
-  {  // item blockIdx.z of a batched call: its phasors, sorted samples, bins and window
+  if constexpr (BATCH) {  // item blockIdx.z of a batched call: its phasors, sorted samples, bins and window
     const long long item = blockIdx.z;
     P += item * it.p_stride;
     bin_start += item * it.bstride;
@@ -194,12 +194,19 @@ cudaError_t launch_kw(const float2* P, int F, const int* bin_start, const int* s
   static bool configured = false;
   if (!configured) {
     cudaError_t e =
-        cudaFuncSetAttribute(spread_kernel<KW, kRows>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(spread_kernel<KW, kRows, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(spread_kernel<KW, kRows, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   dim3 grid((W / kRows) * tiles, (F + kCh - 1) / kCh, it.n);
-  spread_kernel<KW, kRows><<<grid, kRows * 32, smem, s>>>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, it);
+  if (it.n > 1)
+    spread_kernel<KW, kRows, true><<<grid, kRows * 32, smem, s>>>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine,
+                                                                  it);
+  else
+    spread_kernel<KW, kRows, false><<<grid, kRows * 32, smem, s>>>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine,
+                                                                   it);
   return cudaGetLastError();
 }
 

@@ -375,6 +375,16 @@ cudaError_t launch_temporal_tc(const float* h, const void* Bh, const void* Bl, c
   return launch_gather(bt, Bh, Bl, wcol, T, twoF, L, fix, row_slot, s);
 }
 
+cudaError_t launch_temporal_tc_gather(const TemporalBatch& bt, const void* Bh, const void* Bl, const float* wcol,
+                                      int T, int twoF, const TemporalFix& fix, cudaStream_t s) {
+  if (T % 8 != 0 || bt.n < 1 || bt.n > kMaxBatch) return cudaErrorInvalidValue;
+  const cudaError_t e = configure();
+  if (e != cudaSuccess) return e;
+  long long rows = 0;
+  for (int b = 0; b < bt.n; ++b) rows += bt.L[b];
+  return launch_gather(bt, Bh, Bl, wcol, T, twoF, (int)std::min<long long>(rows, 1LL << 30), fix, nullptr, s);
+}
+
 cudaError_t launch_temporal_tc_batched(const TemporalBatch& bt, const void* Bh, const void* Bl, const float* wcol,
                                        int T, int twoF, const TemporalFix& fix, int* counter, cudaStream_t s) {
   if (T % 8 != 0 || bt.n < 1 || bt.n > kMaxBatch) return cudaErrorInvalidValue;

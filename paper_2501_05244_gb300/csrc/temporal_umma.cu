@@ -166,10 +166,21 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// GATHER = false: rows 0 .. L-1 of H; rows whose max |h| lies outside the split's window are
-// listed in fix.  GATHER = true: the listed rows (fix.list[0 .. *fix.count), each row index below
+// Per-item inputs of the batch mode: item b's H, C and row count, and its first 128-row tile
+// (tile_start[n] = all tiles); nothing in the other modes.
+template <int MODE>
+struct UItems {};
+template <>
+struct UItems<2> {
+  TemporalBatch bt;
+};
+
+// MODE 0: rows 0 .. L-1 of H; rows whose max |h| lies outside the split's window are listed in fix
+// (as {row, e, 0, 0}).  MODE 2: the same for every item of a batch (tile t of item b is row block
+// t - tile_start[b] of item b; listed as {row, e, b, 0}).  MODE 1 (gather): the listed rows
+// (fix.list[0 .. *fix.count), each row index below
 // L), scaled by 2^-e before the split and by 2^e in the epilogue.
-template <int N2, bool GATHER>
+template <int N2, int MODE>
 __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float* __restrict__ H,
                                                                      float* __restrict__ C, int L, int T,
                                                                      const __grid_constant__ CUtensorMap tm_hi,
@@ -177,7 +188,9 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
                                                                      int* __restrict__ status,
                                                                      const int* __restrict__ row_slot,
                                                                      const float* __restrict__ wcol,
-                                                                     const TemporalFix fix) {
+                                                                     const TemporalFix fix,
+                                                                     const __grid_constant__ UItems<MODE> ui) {
+  constexpr bool GATHER = MODE == 1, BATCH = MODE == 2;
   using S = UShape<N2>;
   extern __shared__ unsigned char raw[];
   const uint32_t raw_addr = sa(raw);
@@ -188,7 +201,9 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
     __syncthreads();
   }
   const int nrows = GATHER ? min(ctl.listed, fix.cap) : L;
-  const int ntiles = (nrows + kBM - 1) / kBM, nkb = T / kBK;
+  int ntiles = (nrows + kBM - 1) / kBM;
+  if constexpr (BATCH) ntiles = ui.bt.tile_start[ui.bt.n];
+  const int nkb = T / kBK;
   const int kb_shift = (nkb & (nkb - 1)) == 0 ? __ffs(nkb) - 1 : -1;  // K-blocks per tile a power of two
   if (GATHER && (int)blockIdx.x >= ntiles) return;  // the whole CTA: nothing listed for it
   volatile int* abort = &ctl.abort;
@@ -199,10 +214,35 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
   auto a_lo = [&](int st) { return base + st * S::kStage + S::kA; };
   auto b_hi = [&](int st) { return base + st * S::kStage + 2 * S::kA; };
   auto b_lo = [&](int st) { return base + st * S::kStage + 2 * S::kA + S::kB; };
-  // H row of tile position pos (-1: none) and, in the gather launch, its exponent
-  auto row_of = [&](int pos, int& x) -> int {
+  // Batch mode: the item of tile t (tiles come in increasing order per role, so the search resumes
+  // from the last item found) and its rows; other modes: item 0, H, C, L
+  struct Src {
+    int b, t0;  // item, its first tile
+    const float* h;
+    float* c;
+    int L;
+  };
+  auto item_of = [&](int t, Src& sc) {
+    if constexpr (BATCH) {
+      int b = sc.b;
+      while (b + 1 < ui.bt.n && t >= ui.bt.tile_start[b + 1]) ++b;
+      sc.b = b;
+      sc.t0 = ui.bt.tile_start[b];
+      sc.h = ui.bt.A[b];
+      sc.c = ui.bt.C[b];
+      sc.L = ui.bt.L[b];
+    } else {
+      sc.b = 0;
+      sc.t0 = 0;
+      sc.h = H;
+      sc.c = C;
+      sc.L = L;
+    }
+  };
+  // H row of position pos of the item (-1: none) and, in the gather launch, its exponent
+  auto row_of = [&](int pos, int& x, int Lr) -> int {
     x = 0;
-    if (!GATHER) return pos < L ? pos : -1;
+    if (!GATHER) return pos < Lr ? pos : -1;
     if (pos >= nrows) return -1;
     const int4 en = fix.list[pos];
     x = en.y;
@@ -236,20 +276,24 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
 
   if (warp < kEpiWarps) {
     // ---------------------------------------------------------------- epilogue
+    Src esrc{0, 0, H, C, L};
     for (int j = 0; j < my_tiles; ++j) {
       const int ab = j & 1;
       if (!__all_sync(0xffffffffu, bar_wait(&ctl.acc_full[ab], (j >> 1) & 1, abort))) break;
       fence_after_sync();
       int x = 0;
-      int orow = row_of(((int)blockIdx.x + j * (int)gridDim.x) * kBM + warp * 32 + lane, x);
+      const int t = (int)blockIdx.x + j * (int)gridDim.x;
+      item_of(t, esrc);
+      int orow = row_of((t - esrc.t0) * kBM + warp * 32 + lane, x, esrc.L);
       if (orow >= 0 && row_slot) orow = __ldg(row_slot + orow);
+      float* const Cb = esrc.c;
       const uint32_t tb = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ab * S::kAcc);
 #pragma unroll 1
       for (int c0 = 0; c0 < N2; c0 += 32) {
         uint32_t r[32];
         tmem_ld32(tb + c0, r);
         if (orow >= 0) {
-          float4* dst = reinterpret_cast<float4*>(C + (size_t)orow * N2 + c0);
+          float4* dst = reinterpret_cast<float4*>(Cb + (size_t)orow * N2 + c0);
           const float4* w4 = reinterpret_cast<const float4*>(wcol + c0);
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
@@ -277,18 +321,21 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
     const int r0 = ct >> 2, ch = ct & 3;
     uint32_t* rmax = ctl.rmax + ct;  // this thread's two rows' running max over the tile's K-blocks
     // a register set holds K-blocks 2 p and 2 p + 1 (4 float4 each)
+    Src lsrc{0, 0, H, C, L}, ssrc{0, 0, H, C, L};  // the loads' and the staging's current item
     auto load = [&](float4 (&v)[8], int pr) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int it = 2 * pr + h;
         if (it >= my_iters) return;
         const int j = kb_shift >= 0 ? it >> kb_shift : it / nkb, kb = it - j * nkb;
-        const int m0 = ((int)blockIdx.x + j * (int)gridDim.x) * kBM;
+        const int t = (int)blockIdx.x + j * (int)gridDim.x;
+        item_of(t, lsrc);
+        const int m0 = (t - lsrc.t0) * kBM;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           int x;
-          const int row = row_of(m0 + r0 + 64 * q, x);
-          const float4* s4 = reinterpret_cast<const float4*>(H + (size_t)max(row, 0) * T + kb * kBK + ch * 8);
+          const int row = row_of(m0 + r0 + 64 * q, x, lsrc.L);
+          const float4* s4 = reinterpret_cast<const float4*>(lsrc.h + (size_t)max(row, 0) * T + kb * kBK + ch * 8);
           v[4 * h + 2 * q] = row >= 0 ? __ldg(s4) : make_float4(0.f, 0.f, 0.f, 0.f);
           v[4 * h + 2 * q + 1] = row >= 0 ? __ldg(s4 + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -297,7 +344,9 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
     auto stage_one = [&](const float4* v, int it) -> bool {
       const int st = it % kUStages, ph = (it / kUStages) & 1;
       const int j = kb_shift >= 0 ? it >> kb_shift : it / nkb, kb = it - j * nkb;
-      const int m0 = ((int)blockIdx.x + j * (int)gridDim.x) * kBM;
+      const int t = (int)blockIdx.x + j * (int)gridDim.x;
+      item_of(t, ssrc);
+      const int m0 = (t - ssrc.t0) * kBM;
       if (!__all_sync(0xffffffffu, bar_wait(&ctl.empty[st], ph ^ 1, abort))) return false;
       unsigned char* ah = a_hi(st);
       unsigned char* al = a_lo(st);
@@ -308,7 +357,7 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
         float4 x = v[2 * q], y = v[2 * q + 1];
         if (GATHER) {
           int e;
-          row_of(m0 + r, e);
+          row_of(m0 + r, e, ssrc.L);
           x = make_float4(ldexpf(x.x, -e), ldexpf(x.y, -e), ldexpf(x.z, -e), ldexpf(x.w, -e));
           y = make_float4(ldexpf(y.x, -e), ldexpf(y.y, -e), ldexpf(y.z, -e), ldexpf(y.w, -e));
         } else {
@@ -343,11 +392,11 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
             const int row = m0 + r0 + 64 * q;
-            if (ch == 0 && row < L) {
+            if (ch == 0 && row < ssrc.L) {
               const int e = temporal_row_exponent(__uint_as_float(((m >> (16 * q)) & 0xffffu) << 16));
               if (e != kRowInRange) {
                 const int slot = atomicAdd(fix.count, 1);
-                if (slot < fix.cap) fix.list[slot] = make_int4(row, e, 0, 0);
+                if (slot < fix.cap) fix.list[slot] = make_int4(row, e, ssrc.b, 0);
               }
             }
           }
@@ -474,11 +523,11 @@ bool encode_b(CUtensorMap* m, const void* ptr, int T, int rows) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int N2, bool GATHER>
+template <int N2, int MODE>
 cudaError_t configure_n() {
   static bool configured = false;
   if (configured) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(temporal_umma_kernel<N2, GATHER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(temporal_umma_kernel<N2, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)UShape<N2>::kSmem);
   if (e == cudaSuccess) configured = true;
   return e;
@@ -494,19 +543,42 @@ cudaError_t launch_n(const TemporalMaps& m, const float* h, const float* wcol, f
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
-  cudaError_t e = configure_n<N2, false>();
-  if (e == cudaSuccess) e = configure_n<N2, true>();
+  cudaError_t e = configure_n<N2, 0>();
+  if (e == cudaSuccess) e = configure_n<N2, 1>();
   if (e != cudaSuccess) return e;
   const int ntiles = (L + kBM - 1) / kBM;
-  temporal_umma_kernel<N2, false><<<std::min(ntiles, sms), kUThreads, S::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status,
-                                                                                     row_slot, wcol, fix);
+  temporal_umma_kernel<N2, 0><<<std::min(ntiles, sms), kUThreads, S::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status,
+                                                                                 row_slot, wcol, fix, UItems<0>{});
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // listed rows: at most min(L, cap); CTAs beyond the listed tiles return at once
   const int gtiles = (std::min(L, fix.cap) + kBM - 1) / kBM;
   if (gtiles <= 0) return cudaSuccess;
-  temporal_umma_kernel<N2, true><<<std::min(gtiles, sms), kUThreads, S::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status,
-                                                                                    row_slot, wcol, fix);
+  temporal_umma_kernel<N2, 1><<<std::min(gtiles, sms), kUThreads, S::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status,
+                                                                                 row_slot, wcol, fix, UItems<1>{});
+  return cudaGetLastError();
+}
+
+// Batch mode: bt.tile_start counts 128-row tiles.  The listed rows of every item are then
+// recomputed by the mma.sync form's gather launch (temporal_tc.cu).
+template <int N2>
+cudaError_t launch_batch_n(const TemporalMaps& m, const TemporalBatch& bt, const float* wcol, int T,
+                           const TemporalFix& fix, int* status, cudaStream_t s) {
+  using S = UShape<N2>;
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const cudaError_t e = configure_n<N2, 2>();
+  if (e != cudaSuccess) return e;
+  const int ntiles = bt.tile_start[bt.n];
+  if (ntiles <= 0) return cudaSuccess;
+  UItems<2> ui;
+  ui.bt = bt;
+  temporal_umma_kernel<N2, 2><<<std::min(ntiles, sms), kUThreads, S::kSmem, s>>>(nullptr, nullptr, 0, T, m.hi, m.lo,
+                                                                                 status, nullptr, wcol, fix, ui);
   return cudaGetLastError();
 }
 
@@ -523,6 +595,25 @@ bool make_temporal_maps(const void* Bh, const void* Bl, int T, int twoF, Tempora
   if (!encode_b(&m->hi, Bh, T, twoF) || !encode_b(&m->lo, Bl, T, twoF)) return false;
   m->ok = 1;
   return true;
+}
+
+cudaError_t launch_temporal_umma_batched(const TemporalMaps& m, const TemporalBatch& bt, const float* wcol, int T,
+                                         int twoF, const TemporalFix& fix, int* status, cudaStream_t s) {
+  if (!m.ok || !temporal_umma_supported(T, twoF) || bt.n < 1 || bt.n > kMaxBatch ||
+      reinterpret_cast<uintptr_t>(wcol) % 16 != 0)
+    return cudaErrorInvalidValue;
+  for (int b = 0; b < bt.n; ++b) {
+    if (bt.tile_start[b + 1] - bt.tile_start[b] != (bt.L[b] + kBM - 1) / kBM || bt.L[b] < 0)
+      return cudaErrorInvalidValue;
+    if (bt.L[b] > 0 && (reinterpret_cast<uintptr_t>(bt.A[b]) % 16 != 0 || reinterpret_cast<uintptr_t>(bt.C[b]) % 16 != 0))
+      return cudaErrorInvalidValue;
+  }
+  switch (twoF) {
+    case 32: return launch_batch_n<32>(m, bt, wcol, T, fix, status, s);
+    case 64: return launch_batch_n<64>(m, bt, wcol, T, fix, status, s);
+    case 128: return launch_batch_n<128>(m, bt, wcol, T, fix, status, s);
+    default: return launch_batch_n<256>(m, bt, wcol, T, fix, status, s);
+  }
 }
 
 cudaError_t launch_temporal_umma(const TemporalMaps& m, const float* h, const float* wcol, float* C, int L, int T,
