@@ -58,6 +58,9 @@ def parse_args():
     ap.add_argument("--row-depths", type=int, default=128,
                     help="depth planes of the scaled-plane rows (SRSD, NU-SFFT, SRSD at voxels); 128 is the "
                          "measured workload, fewer make a small case for profiler captures")
+    ap.add_argument("--row-items", type=int, default=64,
+                    help="reconstructions of the batched row (the first of its 64 items); 64 is the measured "
+                         "workload, fewer make a small case for profiler captures")
     ap.add_argument("--workload", choices=["spad", "grid128", "spad-z8", "spad-n128"], default="spad",
                     help="spad: the 65k-sample 256^2x128 workload (the metric); grid128: the same samples on "
                          "128^2x64 voxels; spad-z8: the spad workload with 8 of its 128 depth planes (same "
@@ -495,7 +498,7 @@ def hbm_row(bytes_: int, ms: float, peak: float) -> dict:
     return {"algorithmic_bytes": int(bytes_), "achieved_gbs": gbs, "hbm_frac": gbs / peak}
 
 
-def measure_rows(wl, peak, stages_ms=None, only=(), row_depths=128):
+def measure_rows(wl, peak, stages_ms=None, only=(), row_depths=128, row_items=64):
     """Per-row measurements of the other hot-path rows on the same GPU (one entry each)."""
     import numpy as np
     import torch
@@ -672,9 +675,10 @@ def measure_rows(wl, peak, stages_ms=None, only=(), row_depths=128):
 
     def batched():
         gb = geometry_c4()
-        sizes = batch_sizes_c4()
-        layouts = batch_layouts_c4(sizes)
-        scenes = batch_scenes_c4(len(sizes))
+        all_sizes = batch_sizes_c4()
+        layouts = batch_layouts_c4(all_sizes)[:row_items]
+        scenes = batch_scenes_c4(len(all_sizes))[:row_items]
+        sizes = all_sizes[:row_items]
         omb, wtb = nursd.phasor_frequencies(gb.lambda_c, gb.dt, gb.t_pad, gb.F)
         plan = nursd.Plan(gb.N, gb.pitch, gb.center, gb.depths, omb, wtb, T=gb.T, t0=gb.t0, dt=gb.dt,
                           max_points=int(sizes.max()), max_batch=len(sizes))
@@ -711,8 +715,8 @@ def measure_rows(wl, peak, stages_ms=None, only=(), row_depths=128):
             Lb = int(Lb)
             b += (Lb * gb.T * 4 + Lb * gb.F * 8 + bytes_type1(Lb, gb.F, gb.N) + 8 * (M * M * gb.F + M * M * gb.Z)
                   + bytes_idft(gb.Z, gb.N))
-        return {"workload": "64 reconstructions, L log-uniform 4,096-65,536 (sum %d), T=512 @ 8 ps, F=64, "
-                            "128^2 x 64 each" % int(sizes.sum()),
+        return {"workload": "%d reconstructions, L log-uniform 4,096-65,536 (sum %d), T=512 @ 8 ps, F=64, "
+                            "128^2 x 64 each" % (len(sizes), int(sizes.sum())),
                 "ms_graph": ms_graph, "recon_per_s": len(sizes) / (ms_graph / 1e3),
                 "voxel_freq_per_s": units / (ms_graph / 1e3), **hbm_row(b, ms_graph, peak),
                 "ms_64_single_calls": ms_single, "speedup_vs_single_calls": ms_single / ms_graph,
@@ -1036,7 +1040,7 @@ def run_ours(args, rank, world, local):
     only = tuple(r for r in args.rows.split(",") if r)
     if rank == 0 and world == 1 and not args.no_rows and (args.workload == "spad" or only):
         plan.close()
-        line["rows"] = measure_rows(wl, peak, line["stages_ms"], only, args.row_depths)
+        line["rows"] = measure_rows(wl, peak, line["stages_ms"], only, args.row_depths, args.row_items)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, desc, cores = oracle_rate(wl, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}

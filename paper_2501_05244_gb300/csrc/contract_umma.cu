@@ -23,7 +23,7 @@
 //   0-3   epilogue: tcgen05.ld of the 128 x 2Z accumulator (one row per thread), complex stores;
 //         two accumulators, so a tile's epilogue overlaps the next tile's MMAs
 //   4-11  producers: per 8-frequency block, the 128 rows' U values and the class's table rows
-//         are loaded (three blocks ahead), split into tf32 head and tail and stored in the
+//         are loaded (five blocks ahead), split into tf32 head and tail and stored in the
 //         64-byte-swizzled K-major operand layout
 //   12    MMA issuer (one thread): per block two k-steps of 8 x 3 products, tcgen05.commit to the
 //         stage's "empty" barrier, and after the tile's last block to the accumulator's "full"
@@ -42,7 +42,7 @@ constexpr int kCEpiWarps = 4, kCProdWarps = 8;
 constexpr int kCMmaWarp = kCEpiWarps + kCProdWarps;
 constexpr int kCThreads = (kCMmaWarp + 1) * 32;
 constexpr long long kCSpin = 1LL << 22;
-constexpr int kCAhead = 3;  // 8-frequency blocks of loads in flight per producer thread
+constexpr int kCAhead = 5;  // 8-frequency blocks of loads in flight per producer thread
 
 template <int N2>
 struct CShape {
@@ -241,10 +241,11 @@ __global__ void __launch_bounds__(kCThreads, 1) contract_umma_kernel(const float
     }
   } else if (warp < kCMmaWarp) {
     // ---------------------------------------------------------------- producers
-    // task of a block: A row ra = pt / 2, frequencies 4 ha .. 4 ha + 3 of the block (ha = pt % 2);
-    // B row z = pt / 2 (z < Z), frequencies 4 hb .. 4 hb + 3 (hb = pt % 2)
+    // task of a block: A row ra, frequencies 4 ha .. 4 ha + 3 of the block; B row z = ra (z < Z), the
+    // same frequencies.  Each 8 lanes take 8 consecutive rows of one half (ra = 8 (pt / 16) + pt % 8,
+    // ha = (pt / 8) % 2), so their 16-byte chunk stores meet 8 different bank groups of the swizzle.
     const int pt = (warp - kCEpiWarps) * 32 + lane;
-    const int ra = pt >> 1, ha = pt & 1;
+    const int ra = ((pt >> 4) << 3) | (pt & 7), ha = (pt >> 3) & 1;
     const bool has_b = pt < 2 * Z;
     struct Regs {
       float4 a0, a1;  // U[f0 + 4 ha .. + 3] of row ra (two complex values each)
