@@ -959,7 +959,29 @@ int run_per_frequency(nursd_plan_s* p, const double* illum, int frames, float2* 
         StageTimer t(p, NURSD_STAGE_IFFT_X, s, 1);
         e = launch_panel_fft(ilog2(M), true, a, s);
       }
-      if (e == cudaSuccess) e = idft_crop_y(p, p->pf_T, C, p->pf_V, false, s);
+      if (e == cudaSuccess && frames == 0) {  // channel-last volumes [N][N][C] for the warp-per-voxel sum
+        StageTimer t(p, NURSD_STAGE_IFFT_Y, s, 1);
+        PanelArgs b = panel_base(p);
+        b.in = p->pf_T;
+        b.in_si = (long long)N * C;
+        b.in_shi = C;
+        b.in_slo = 1;
+        b.out = p->pf_V;
+        b.out_si = (long long)N * C;
+        b.out_shi = C;
+        b.out_slo = 1;
+        b.nin = M;
+        b.in_off = -M / 2;
+        b.nout = N;
+        b.out_off = -N / 2;
+        b.hi_total = N;
+        b.lo_total = C;
+        b.CLO = panel_width(ilog2(M));
+        b.scale = 1.f / ((float)M * (float)M);
+        e = launch_panel_fft(ilog2(M), true, b, s);
+      } else if (e == cudaSuccess) {
+        e = idft_crop_y(p, p->pf_T, C, p->pf_V, false, s);
+      }
     } else {
       {
         StageTimer t(p, NURSD_STAGE_PER_FREQUENCY, s, 1);
@@ -970,8 +992,11 @@ int run_per_frequency(nursd_plan_s* p, const double* illum, int frames, float2* 
     const int cz = fused ? 1 : F, cf = fused ? n : 1;  // channel of (zz, f) = zz cz + f cf
     if (e == cudaSuccess) {
       StageTimer t(p, NURSD_STAGE_PER_FREQUENCY, s, 1);
-      e = frames == 0 ? launch_illum_sum(p->pf_V, F, N, z0, n, cz, cf, ia, out, s)
-                      : launch_frames_sum(p->pf_V, F, N, Z, z0, n, cz, cf, p->pf_A, frames, out, s);
+      if (frames == 0)
+        e = fused ? launch_illum_sum_cl(p->pf_V, F, N, z0, n, ia, out, s)
+                  : launch_illum_sum(p->pf_V, F, N, z0, n, cz, cf, ia, out, s);
+      else
+        e = launch_frames_sum(p->pf_V, F, N, Z, z0, n, cz, cf, p->pf_A, frames, out, s);
     }
   }
   return from_cuda(e);

@@ -91,6 +91,47 @@ __global__ void illum_sum_kernel(const float2* __restrict__ V, int F, int N, int
   out[(size_t)(z0 + zz) * nn + m] = acc;
 }
 
+// The same sum with V channel-last [N][N][zg F] and the channel of depth zz and frequency f at
+// f zg + zz: one thread per (voxel, depth), depth fastest, so the zg threads of a voxel read its zg
+// channels of one frequency as one contiguous run (a 32-byte sector at zg = 4) and the next
+// frequency's run follows in the same cache line.  The mask as in illum_sum_kernel.
+__global__ void illum_sum_cl_kernel(const float2* __restrict__ V, int F, int N, int z0, int zg, IllumArgs a,
+                                    float2* __restrict__ out) {
+  const int nn = N * N;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)zg * nn) return;
+  const int m = (int)(idx / zg), zz = (int)(idx - (long long)m * zg);
+  const int my = m / N, mx = m - my * N;
+  const double dx = a.cx + (double)(mx - N / 2) * a.pitch - a.xp;
+  const double dy = a.cy + (double)(my - N / 2) * a.pitch - a.yp;
+  const double dz = __ldg(a.depth + z0 + zz) - a.zp;
+  const double d = sqrt(dx * dx + dy * dy + dz * dz);
+  const float2* v = V + (size_t)m * zg * F + zz;
+  float2 acc = make_float2(0.f, 0.f);
+  if (a.equispaced) {
+    const float2 rot = phasor_cycles(a.dkap * d);
+    for (int f0 = 0; f0 < F; f0 += kReseed) {
+      float2 ph = phasor_cycles(__ldg(a.kap + f0) * d);
+      const int f1 = min(F, f0 + kReseed);
+#pragma unroll 4
+      for (int f = f0; f < f1; ++f) {
+        const float2 x = __ldg(v + (size_t)f * zg);
+        acc.x = fmaf(ph.x, x.x, fmaf(-ph.y, x.y, acc.x));
+        acc.y = fmaf(ph.x, x.y, fmaf(ph.y, x.x, acc.y));
+        ph = cmul(ph, rot);
+      }
+    }
+  } else {
+    for (int f = 0; f < F; ++f) {
+      const float2 ph = phasor_cycles(__ldg(a.kap + f) * d);
+      const float2 x = __ldg(v + (size_t)f * zg);
+      acc.x = fmaf(ph.x, x.x, fmaf(-ph.y, x.y, acc.x));
+      acc.y = fmaf(ph.x, x.y, fmaf(ph.y, x.x, acc.y));
+    }
+  }
+  out[(size_t)(z0 + zz) * nn + m] = acc;
+}
+
 constexpr int kFrameChunk = 8;  // frames accumulated per pass over a voxel's F values
 
 // out[t][z0 + zz][my][mx] = sum_f A[t][f] V[zz cz + f cf][my][mx] for t < T, A[t][f] = exp(+i w_f t_t)
@@ -144,6 +185,14 @@ cudaError_t launch_illum_sum(const float2* V, int F, int N, int z0, int zg, int 
   if (F < 1 || N < 1 || zg < 1 || n >= (1LL << 31)) return cudaErrorInvalidValue;
   const int threads = 256;
   illum_sum_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(V, F, N, z0, zg, cz, cf, a, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_illum_sum_cl(const float2* V, int F, int N, int z0, int zg, const IllumArgs& a, float2* out,
+                                cudaStream_t s) {
+  const long long threads = (long long)N * N * zg;
+  if (F < 1 || N < 1 || zg < 1 || threads >= (1LL << 31)) return cudaErrorInvalidValue;
+  illum_sum_cl_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(V, F, N, z0, zg, a, out);
   return cudaGetLastError();
 }
 

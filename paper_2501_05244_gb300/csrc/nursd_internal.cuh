@@ -355,6 +355,9 @@ struct IllumArgs {
 // [zg*F][N][N] (channel of depth zz and frequency f at zz*cz + f*cf), out [Z][N][N].
 cudaError_t launch_illum_sum(const float2* V, int F, int N, int z0, int zg, int cz, int cf, const IllumArgs& a,
                              float2* out, cudaStream_t s);
+// The same with V channel-last [N][N][zg*F], the channel of depth zz and frequency f at f*zg + zz.
+cudaError_t launch_illum_sum_cl(const float2* V, int F, int N, int z0, int zg, const IllumArgs& a, float2* out,
+                                cudaStream_t s);
 // out[t][z0 + zz][my][mx] = sum_f A[t][f] V[zz*cz + f*cf][my][mx], A [T][F], out [T][Z][N][N].
 cudaError_t launch_frames_sum(const float2* V, int F, int N, int Z, int z0, int zg, int cz, int cf, const float2* A,
                               int T, float2* out, cudaStream_t s);

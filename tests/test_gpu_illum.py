@@ -175,13 +175,17 @@ def test_empty_point_set_gives_zero_volume_and_frames():
     assert plan.sync_status() == 0
 
 
-def test_products_formed_in_the_first_inverse_pass_match_oracle():
+@pytest.mark.parametrize("F,equispaced", [(8, True), (6, False)])
+def test_products_formed_in_the_first_inverse_pass_match_oracle(F, equispaced):
     # M = 512 with Z % 4 == 0 and F even: the kx pass stages U and the table rows and forms the
-    # products itself (channels 4 f + zz); full outputs against the oracle
-    N, pitch, F = 256, 2.0 / 256, 8
+    # products itself (channels 4 f + zz), the second pass writes channel-last volumes and the
+    # masked sum runs a warp per voxel (fewer channels than lanes at F = 6; irregular frequencies
+    # take the FP64 mask of every frequency); full outputs against the oracle
+    N, pitch = 256, 2.0 / 256
     r = np.random.default_rng(BASE_SEED + 126)
     xy = r.uniform(-0.999, 0.999, (500, 2)).astype(np.float32)
-    om = 2 * math.pi * np.linspace(4.2e9, 5.8e9, F)
+    om = 2 * math.pi * (np.linspace(4.2e9, 5.8e9, F) if equispaced
+                        else np.array([4.2e9, 4.4e9, 4.9e9, 5.05e9, 5.5e9, 5.8e9]))
     depths = np.array([0.6, 1.1, 1.7, 2.4])
     plan = nursd.Plan(N, pitch, (0.0, 0.0), depths, om, max_points=len(xy))
     plan.set_points(torch.from_numpy(xy).cuda())
