@@ -80,7 +80,8 @@ typedef struct {
   const double* h_depths;    /* [Z] plane depths z_v > 0 [m] (copied)              */
   int32_t F;                 /* number of frequencies, 1..256                      */
   const double* h_omega;     /* [F] angular frequencies w_f [rad/s] (copied)       */
-  const double* h_weight;    /* [F] filter weights w_f, or NULL for all ones       */
+  const double* h_weight;    /* [F] filter weights w_f, or NULL: the Gaussian of    */
+                             /* Eq. PFPacket from lambda_c (all ones if it is 0)  */
   int32_t T;                 /* histogram bins (0 = no histogram input)            */
   double t0, dt;             /* time of bin 0 and bin width [s]                    */
   int32_t upsample;          /* NUFFT oversampling sigma (only 2 is built)         */
@@ -90,6 +91,9 @@ typedef struct {
   const double* h_srsd_pitch; /* [Z] SRSD output pitch delta_o(z) per depth [m] (copied),
                                  or NULL: no SRSD tables are built                  */
   int32_t max_batch;          /* capacity of nursd_forward_batched (0: not used), <= 256 */
+  double lambda_c;            /* central wavelength [m] of the phasor-field band-pass: with
+                                 h_weight NULL, w_f = exp(-(w_f - w_c)^2 / (2 (w_c / 5)^2)),
+                                 w_c = 2 pi c / lambda_c (as nursd_phasor_frequencies); 0: none */
 } nursd_desc;
 
 /* One reconstruction of a batch: L relay samples d_xy [L][2], histograms
@@ -124,6 +128,8 @@ int nursd_phasor_frequencies(double lambda_c, double dt, int32_t t_pad, int32_t 
  * is leaked.
  */
 int nursd_plan_create(const nursd_desc* desc, nursd_stream_t stream, nursd_plan_t* out);
+/* The same call under the name of the interface statement (nursd_plan(desc, stream, &plan)). */
+int nursd_plan(const nursd_desc* desc, nursd_stream_t stream, nursd_plan_t* out);
 
 /* Free a plan and all its device memory (NULL is accepted). */
 int nursd_plan_destroy(nursd_plan_t plan);
@@ -260,6 +266,17 @@ int nursd_grad_points(nursd_plan_t plan, const nursd_c64* d_w, const nursd_c64* 
  * nursd_set_points.
  */
 int srsd_forward(nursd_plan_t plan, const nursd_c64* d_phasor, void* d_out, nursd_stream_t stream);
+
+/*
+ * srsd_forward with the output pitch of each depth given at the call, as in the interface
+ * statement (srsd_forward(plan, pitch_per_depth, in, out, stream)): h_pitch [Z] host, metres,
+ * each > 0.  When the pitches differ from the plan's current SRSD pitches (or the plan was
+ * created without h_srsd_pitch) the scaled table, the chirps and the interpolation taps are
+ * rebuilt first: that call allocates on first use and synchronises like nursd_plan_create, so
+ * only calls with unchanged pitches can be captured in a CUDA graph.  Then as srsd_forward.
+ */
+int srsd_forward_at(nursd_plan_t plan, const double* h_pitch, const nursd_c64* d_phasor, void* d_out,
+                    nursd_stream_t stream);
 
 /*
  * NU-SFFT (Supp. C, SRSD on non-uniform acquisition schemes: the fusion the

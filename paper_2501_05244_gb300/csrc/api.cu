@@ -505,7 +505,7 @@ int build_srsd_chirps(nursd_plan_s* p, cudaStream_t s) {
   for (int z = 0; z < Z && p->si_any; ++z)
     if (p->si_interp[z]) zl.push_back(z);
   p->si_nz = (int)zl.size();
-  if (!zl.empty() && !p->alloc(p->si_zlist, zl.size())) {
+  if (!zl.empty() && !p->si_zlist && !p->alloc(p->si_zlist, (size_t)Z)) {
     cudaFree(db);
     return NURSD_ERR_OOM;
   }
@@ -751,7 +751,8 @@ int ensure_nusfft(nursd_plan_s* p, cudaStream_t s) {
   const int M = p->M, Z = p->Z, w = p->w, W = p->W, nf = p->nf;
   for (int z = 0; z < Z; ++z)
     if (!(p->srsd_scale[z] >= 1.0)) return NURSD_ERR_UNSUPPORTED;
-  if (!(p->alloc(p->nu_dec_w, W) && p->alloc(p->nu_m0, (size_t)Z * M) && p->alloc(p->nu_wt, (size_t)Z * M * w) &&
+  if (!p->nu_m0 &&  // first use (the buffers stay when new SRSD pitches only change the taps)
+      !(p->alloc(p->nu_dec_w, W) && p->alloc(p->nu_m0, (size_t)Z * M) && p->alloc(p->nu_wt, (size_t)Z * M * w) &&
         p->alloc(p->nu_rows, (size_t)W * 2 * M * p->F) && p->alloc(p->nu_zlist, Z)))
     return NURSD_ERR_OOM;
   // host copies are plan-owned: the uploads below may complete after this call returns
@@ -1119,6 +1120,30 @@ int run_type2_to_fine(nursd_plan_s* p, const float2* spec, int C, bool plane_maj
 
 int check_plan(nursd_plan_t p) { return p ? NURSD_OK : NURSD_ERR_INVALID_ARG; }
 
+// SRSD buffers for the pitches in p->srsd_pitch (allocated on first use) and the choice of the
+// interpolated depths (scale >= 1), with their workspace.
+int alloc_srsd(nursd_plan_s* p) {
+  const int M = p->M, w = p->w;
+  if (!p->Gs && !(p->alloc(p->Gs, (size_t)p->ncls * p->F * p->Z) && p->alloc(p->chirp, (size_t)p->Z * M) &&
+                  p->alloc(p->bhat, (size_t)p->Z * 2 * M) && p->alloc(p->srsd_scale_d, p->Z)))
+    return NURSD_ERR_OOM;
+  p->si_interp.assign(p->Z, 0);
+  p->si_any = false;
+  for (int z = 0; z < p->Z; ++z) {
+    const double sc = p->srsd_pitch[z] / p->pitch;
+    if (!(sc >= 1.0) || p->F > 256) continue;
+    p->si_interp[z] = 1;
+    p->si_any = true;
+  }
+  if (p->si_any && !p->si_yh) {
+    const size_t L = 2 * (size_t)M;
+    if (!(p->alloc(p->si_yh, L * L * p->F) && p->alloc(p->si_scr, M * L * p->F) &&
+          p->alloc(p->si_m0, (size_t)p->Z * M) && p->alloc(p->si_wt, (size_t)p->Z * M * w)))
+      return NURSD_ERR_OOM;
+  }
+  return NURSD_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1180,6 +1205,7 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
     if (!std::isfinite(d->h_omega[i]) || d->h_omega[i] < 0) return NURSD_ERR_INVALID_ARG;
     if (d->h_weight && !std::isfinite(d->h_weight[i])) return NURSD_ERR_INVALID_ARG;
   }
+  if (!std::isfinite(d->lambda_c) || d->lambda_c < 0) return NURSD_ERR_INVALID_ARG;
   if (d->T < 0 || (d->T > 0 && (d->T % 8 != 0 || !(d->dt > 0) || !std::isfinite(d->t0)))) return NURSD_ERR_INVALID_ARG;
   if (d->upsample != 2) return NURSD_ERR_UNSUPPORTED;
   if (d->kernel_width < 4 || d->kernel_width > kMaxKernelWidth) return NURSD_ERR_UNSUPPORTED;
@@ -1215,6 +1241,13 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
   p->depths.assign(d->h_depths, d->h_depths + d->Z);
   p->omega.assign(d->h_omega, d->h_omega + d->F);
   p->weight.assign(d->F, 1.0);
+  if (!d->h_weight && d->lambda_c > 0) {  // the band-pass of Eq. PFPacket (sigma_w = w_c / 5)
+    const double w_c = 2.0 * kPi * kC / d->lambda_c, sigma = w_c / 5.0;
+    for (int f = 0; f < d->F; ++f) {
+      const double dw = d->h_omega[f] - w_c;
+      p->weight[f] = std::exp(-dw * dw / (2.0 * sigma * sigma));
+    }
+  }
   if (d->h_srsd_pitch) p->srsd_pitch.assign(d->h_srsd_pitch, d->h_srsd_pitch + d->Z);
   if (d->h_weight) p->weight.assign(d->h_weight, d->h_weight + d->F);
   // fine-grid window: every footprint of a sample with |x - c| <= N delta / 2, plus a margin
@@ -1336,24 +1369,7 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
     ok = p->alloc(p->phasor_all, (size_t)p->maxB * maxL * p->F) &&
          p->alloc(p->U_all, (size_t)p->maxB * p->M * p->M * p->F) &&
          p->alloc(p->Y_all, (size_t)p->maxB * p->M * p->M * p->Z) && p->alloc(p->counter, 1);
-  if (ok && !p->srsd_pitch.empty())
-    ok = p->alloc(p->Gs, (size_t)p->ncls * p->F * p->Z) && p->alloc(p->chirp, (size_t)p->Z * p->M) &&
-         p->alloc(p->bhat, (size_t)p->Z * 2 * p->M) && p->alloc(p->srsd_scale_d, p->Z);
-  if (ok && !p->srsd_pitch.empty()) {  // taps of the interpolated depths (scale >= 1)
-    const int M = p->M, w = p->w;
-    p->si_interp.assign(p->Z, 0);
-    for (int z = 0; z < p->Z; ++z) {
-      const double sc = p->srsd_pitch[z] / p->pitch;
-      if (!(sc >= 1.0) || p->F > 256) continue;
-      p->si_interp[z] = 1;
-      p->si_any = true;
-    }
-    if (p->si_any) {
-      const size_t L = 2 * (size_t)M;
-      ok = p->alloc(p->si_yh, L * L * p->F) && p->alloc(p->si_scr, M * L * p->F) &&
-           p->alloc(p->si_m0, (size_t)p->Z * M) && p->alloc(p->si_wt, (size_t)p->Z * M * w);
-    }
-  }
+  if (ok && !p->srsd_pitch.empty()) ok = alloc_srsd(p) == NURSD_OK;
   if (!ok) {
     delete p;
     return NURSD_ERR_OOM;
@@ -1386,6 +1402,10 @@ int nursd_plan_create(const nursd_desc* d, nursd_stream_t stream, nursd_plan_t* 
   }
   *out = p;
   return NURSD_OK;
+}
+
+int nursd_plan(const nursd_desc* desc, nursd_stream_t stream, nursd_plan_t* out) {
+  return nursd_plan_create(desc, stream, out);
 }
 
 int nursd_plan_destroy(nursd_plan_t plan) {
@@ -1640,6 +1660,26 @@ int srsd_forward(nursd_plan_t p, const nursd_c64* d_phasor, void* d_out, nursd_s
   if (rc == NURSD_OK) rc = run_srsd_spectra(p, s);
   if (rc == NURSD_OK) rc = run_idft_crop(p, d_out, s);
   return rc;
+}
+
+int srsd_forward_at(nursd_plan_t p, const double* h_pitch, const nursd_c64* d_phasor, void* d_out,
+                    nursd_stream_t stream) {
+  if (check_plan(p) != NURSD_OK || !h_pitch) return NURSD_ERR_INVALID_ARG;
+  for (int z = 0; z < p->Z; ++z)
+    if (!(h_pitch[z] > 0) || !std::isfinite(h_pitch[z])) return NURSD_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->srsd_pitch.size() != (size_t)p->Z || !std::equal(p->srsd_pitch.begin(), p->srsd_pitch.end(), h_pitch)) {
+    // new pitches: the tables in use may still be read by work queued on the stream
+    if (cudaStreamSynchronize(s) != cudaSuccess) return NURSD_ERR_CUDA;
+    p->srsd_pitch.assign(h_pitch, h_pitch + p->Z);
+    p->nu_ready = false;  // the NU-SFFT taps follow the scales
+    int rc = alloc_srsd(p);
+    if (rc == NURSD_OK) rc = build_table(p, true, s);
+    if (rc == NURSD_OK) rc = build_srsd_chirps(p, s);
+    if (rc == NURSD_OK) rc = from_cuda(cudaStreamSynchronize(s));
+    if (rc != NURSD_OK) return rc;
+  }
+  return srsd_forward(p, d_phasor, d_out, stream);
 }
 
 int srsd_forward_points(nursd_plan_t p, const nursd_c64* d_phasor, int32_t K, const float* d_vox_xy, nursd_c64* d_out,

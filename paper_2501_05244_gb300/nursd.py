@@ -38,7 +38,8 @@ EXPORTS = (
     "nursd_propagate", "nursd_forward_phasor", "nursd_forward", "nursd_sync_status",
     "nursd_profile_enable", "nursd_profile_select", "nursd_profile_read", "nursd_launch_count",
     "nursd_nufft1_noalloc",
-    "nursd_forward_points", "nursd_adjoint", "nursd_grad_points", "srsd_forward", "nursd_forward_batched",
+    "nursd_forward_points", "nursd_adjoint", "nursd_grad_points", "srsd_forward", "srsd_forward_at", "nursd_plan",
+    "nursd_forward_batched",
     "nursd_reconstruct", "nursd_forward_illuminated", "nursd_transient_frames", "srsd_forward_points",
     "nursd_subsample", "nursd_upsample", "srsd_forward_nonuniform", "nursd_plan_tune", "nursd_plan_get_tune",
     "nursd_test_fail_allocation", "nursd_test_set_wait_limit", "nursd_enable_3d", "nursd_set_points_3d",
@@ -65,6 +66,7 @@ class _Desc(ctypes.Structure):
         ("dt", ctypes.c_double), ("upsample", ctypes.c_int32), ("kernel_width", ctypes.c_int32),
         ("flags", ctypes.c_uint32), ("max_points", ctypes.c_int32),
         ("h_srsd_pitch", ctypes.POINTER(ctypes.c_double)), ("max_batch", ctypes.c_int32),
+        ("lambda_c", ctypes.c_double),
     ]
 
 
@@ -110,6 +112,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "nursd_adjoint": (ctypes.c_int, [vp, vp, vp, vp]),
         "nursd_grad_points": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
         "srsd_forward": (ctypes.c_int, [vp, vp, vp, vp]),
+        "srsd_forward_at": (ctypes.c_int, [vp, dp, vp, vp, vp]),
+        "nursd_plan": (ctypes.c_int, [ctypes.POINTER(_Desc), vp, ctypes.POINTER(vp)]),
         "nursd_forward_batched": (ctypes.c_int, [vp, i32, ctypes.POINTER(_BatchItem), vp]),
         "nursd_reconstruct": (ctypes.c_int, [vp, i32, vp, vp, vp, vp]),
         "nursd_forward_illuminated": (ctypes.c_int, [vp, dp, vp, vp, vp]),
@@ -214,7 +218,7 @@ class Plan:
     def __init__(self, N: int, pitch: float, center, depths, omega, weight=None, T: int = 0, t0: float = 0.0,
                  dt: float = 0.0, max_points: int = 0, kernel_width: int = 6, upsample: int = 2,
                  magnitude: bool = False, adjoint: bool = False, srsd_pitch=None, max_batch: int = 0,
-                 confocal: bool = False,
+                 confocal: bool = False, lambda_c: float = 0.0,
                  stream=None):
         torch = _torch()
         if not torch.cuda.is_available():
@@ -244,6 +248,7 @@ class Plan:
         d.h_srsd_pitch = (self.srsd_pitch.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
                           if self.srsd_pitch is not None else ctypes.POINTER(ctypes.c_double)())
         d.max_batch = int(max_batch)
+        d.lambda_c = float(lambda_c)  # with weight None: the Gaussian band-pass of this central wavelength
         self._desc = d
         h = ctypes.c_void_p()
         _check(self._lib.nursd_plan_create(ctypes.byref(d), ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(h)),
@@ -394,15 +399,24 @@ class Plan:
         self.L = int(xys[-1].shape[0])
         return outs
 
-    def srsd_forward(self, phasor, out=None, stream=None):
-        """Scaled RSD: plane z on the lattice of pitch srsd_pitch[z] -> [Z][N][N]."""
+    def srsd_forward(self, phasor, out=None, stream=None, pitch=None):
+        """Scaled RSD: plane z on the lattice of pitch srsd_pitch[z] -> [Z][N][N].  With `pitch` ([Z] metres)
+        the plane pitches are given at the call (the plan's SRSD tables are rebuilt when they change)."""
         torch = _torch()
         self._need_points()
         p = _dev(phasor, torch.complex64, (self.L, self.F), "phasor")
         if out is None:
             out = self.empty_output()
         o = _dev(out, self.out_dtype(), self.out_shape(), "out")
-        _check(self._lib.srsd_forward(self._h, p, o, ctypes.c_void_p(_stream_ptr(stream))), "srsd_forward")
+        if pitch is None:
+            _check(self._lib.srsd_forward(self._h, p, o, ctypes.c_void_p(_stream_ptr(stream))), "srsd_forward")
+        else:
+            hp = np.ascontiguousarray(pitch, dtype=np.float64)
+            if hp.shape != (self.Z,):
+                raise ValueError(f"pitch: expected {self.Z} values")
+            _check(self._lib.srsd_forward_at(self._h, hp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), p, o,
+                                             ctypes.c_void_p(_stream_ptr(stream))), "srsd_forward_at")
+            self.srsd_pitch = hp
         return out
 
     # -- 3D NURSD (non-planar relays)

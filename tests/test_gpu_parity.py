@@ -367,3 +367,34 @@ def test_reconstruct_replays_in_a_cuda_graph():
     torch.cuda.synchronize()
     assert plan.sync_status() == 0
     assert np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_lambda_c_gives_the_band_pass_weights_and_nursd_plan_is_plan_create():
+    # with no weights, a central wavelength in the descriptor gives the Gaussian of Eq. PFPacket, the
+    # same weights nursd_phasor_frequencies returns; nursd_plan is nursd_plan_create under the
+    # interface statement's name
+    g = geometry_c1()
+    om, wt = O.phasor_frequencies(g.lambda_c, g.dt, g.t_pad, g.F)
+    xy = relay_uniform(300, 0.49, seed=BASE_SEED + 140)
+    h = np.random.default_rng(BASE_SEED + 141).poisson(3.0, (300, g.T)).astype(np.float32)
+    outs = []
+    for kw in (dict(weight=wt), dict(lambda_c=g.lambda_c)):
+        plan = nursd.Plan(g.N, g.pitch, g.center, g.depths, om, T=g.T, t0=g.t0, dt=g.dt, max_points=300, **kw)
+        outs.append(plan.reconstruct(torch.from_numpy(xy).cuda(), torch.from_numpy(h).cuda()).cpu().numpy())
+        plan.close()
+    assert rel(outs[1], outs[0]) < 1e-6
+    import ctypes
+    from paper_2501_05244_gb300 import nursd as binding
+    lib = binding.load_library()
+    d = binding._Desc()
+    depths = np.ascontiguousarray(g.depths, dtype=np.float64)
+    omv = np.ascontiguousarray(om, dtype=np.float64)
+    d.N, d.pitch, d.center_x, d.center_y, d.Z = g.N, g.pitch, g.center[0], g.center[1], len(depths)
+    d.h_depths = depths.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.F, d.h_omega = len(omv), omv.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.upsample, d.kernel_width, d.max_points, d.lambda_c = 2, 6, 16, -1.0
+    h_out = ctypes.c_void_p()
+    assert lib.nursd_plan(ctypes.byref(d), None, ctypes.byref(h_out)) == binding.NURSD_ERR_INVALID_ARG
+    d.lambda_c = g.lambda_c
+    assert lib.nursd_plan(ctypes.byref(d), None, ctypes.byref(h_out)) == 0 and h_out.value
+    assert lib.nursd_plan_destroy(h_out) == 0

@@ -49,6 +49,26 @@ def test_srsd_matches_oracle(N, L, F, Z, seed):
     assert rel(V, ref) < TOL
 
 
+def test_srsd_pitch_given_at_the_call():
+    # the interface statement's form srsd_forward(plan, pitch_per_depth, in, out): on a plan created
+    # without SRSD tables, then with other pitches (scales below and above 1), then the first ones again
+    N, L, F, Z = 32, 1200, 16, 6
+    xy, P, om, depths, pitch_a, pitch, center = case(N, L, F, Z, 31)
+    pitch_b = np.linspace(0.7, 2.5, Z) * pitch
+    plan = nursd.Plan(N, pitch, center, depths, om, max_points=L)
+    plan.set_points(torch.from_numpy(xy).cuda())
+    Pg = torch.from_numpy(P).cuda()
+    Va = plan.srsd_forward(Pg, pitch=pitch_a).cpu().numpy()
+    assert rel(Va, O.srsd_forward(P, xy, center, pitch, N, depths, pitch_a / pitch, om)) < TOL
+    Vb = plan.srsd_forward(Pg, pitch=pitch_b).cpu().numpy()
+    assert rel(Vb, O.srsd_forward(P, xy, center, pitch, N, depths, pitch_b / pitch, om)) < TOL
+    assert np.array_equal(plan.srsd_forward(Pg, pitch=pitch_a).cpu().numpy(), Va)
+    assert np.array_equal(plan.srsd_forward(Pg).cpu().numpy(), Va)  # the last pitches stay in the plan
+    with pytest.raises(nursd.NursdError):
+        plan.srsd_forward(Pg, pitch=np.full(Z, -1.0))
+    assert plan.sync_status() == 0
+
+
 def test_srsd_with_unit_scale_equals_nursd_on_gpu():
     xy, P, om, depths, _, pitch, center = case(32, 900, 8, 4, 5)
     plan = nursd.Plan(32, pitch, center, depths, om, max_points=900, srsd_pitch=np.full(4, pitch))
