@@ -441,7 +441,9 @@ int nursd_nufft1_noalloc(int32_t N, double pitch, double center_x, double center
  * Synchronise `stream`, read and clear the plan's device error word.
  * Returns NURSD_OK, NURSD_ERR_POINT_OUT_OF_RANGE, NURSD_ERR_TIMEOUT (a bounded
  * device wait gave up) or NURSD_ERR_UNSUPPORTED (an SRSD tap table that the
- * interpolation kernels cannot follow; not produced by the plan's own tables).
+ * interpolation kernels cannot follow; not produced by the plan's own tables), or, in
+ * the checked build (libnursd_checked.so, compiled with -DNURSD_CHECKED), NURSD_ERR_CUDA
+ * when a bounds check of a data-dependent index failed (the access was skipped).
  */
 int nursd_sync_status(nursd_plan_t plan, nursd_stream_t stream);
 

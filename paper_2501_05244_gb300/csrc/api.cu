@@ -553,8 +553,10 @@ int run_nufft1(nursd_plan_s* p, const float2* phasor, float2* spec, cudaStream_t
   cudaError_t e;
   {
     StageTimer t(p, NURSD_STAGE_SPREAD, s, 1);
+    SpreadItems one;
+    one.status = p->status;
     e = launch_spread(phasor, F, p->bin_start, slot_ordered ? nullptr : p->sorted_l, p->i0_sorted, p->w_sorted, p->w,
-                      p->tiles, W, p->fine, s, p->spread_rows);
+                      p->tiles, W, p->fine, s, p->spread_rows, one);
   }
   if (e == cudaSuccess) {  // FFT along x of every window row, keep kx in I_M
     StageTimer t(p, NURSD_STAGE_FFT_X, s, 1);
@@ -1995,6 +1997,7 @@ int nursd_forward_batched(nursd_plan_t p, int32_t B, const nursd_batch_item* ite
         si.pts = (long long)g.pts;
         si.fine_stride = fine_st;
         si.bstride = (int)g.bins;
+        si.status = p->status;
         rc = from_cuda(launch_spread(p->phasor_all + g0 * phasor_stride, F, gw.bin_start, gw.sorted_l, gw.i0_sorted,
                                      gw.w_sorted, p->w, p->tiles, W, gw.fine, s, p->spread_rows, si));
       }
@@ -2136,6 +2139,7 @@ int nursd_sync_status(nursd_plan_t p, nursd_stream_t stream) {
   if (h != 0 && cudaMemsetAsync(p->status, 0, sizeof(int), s) != cudaSuccess) return NURSD_ERR_CUDA;
   if (h & 6) return NURSD_ERR_TIMEOUT;  // a bounded barrier wait gave up (contraction, SRSD: 2, temporal: 4)
   if (h & 8) return NURSD_ERR_UNSUPPORTED;  // an SRSD tap table broke the interpolation's step rule
+  if (h & 16) return NURSD_ERR_CUDA;  // checked build: an internal index check failed
   if (h & 1) return NURSD_ERR_POINT_OUT_OF_RANGE;
   return NURSD_OK;
 }

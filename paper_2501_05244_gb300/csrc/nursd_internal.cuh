@@ -19,6 +19,15 @@
 
 namespace nursd {
 
+// Checks of data-dependent indices, compiled in with -DNURSD_CHECKED (the library's checked build):
+// a failed check sets status bit 16 (NURSD_ERR_CUDA from nursd_sync_status) and the access is
+// skipped; without the flag a check is the constant true.
+#ifdef NURSD_CHECKED
+#define NURSD_CHECK(cond, status) ((cond) ? true : (((status) ? atomicOr((status), 16) : 0), false))
+#else
+#define NURSD_CHECK(cond, status) true
+#endif
+
 constexpr int kTile = 16;          // spreading tile edge (fine cells)
 constexpr int kTwiddleLog = 12;    // shared FFT twiddle table has 2^12 entries, then the per-thread rows below
 constexpr int kMaxKernelWidth = 8;
@@ -231,6 +240,8 @@ struct SpreadItems {
   int n = 1;
   long long p_stride = 0, pts = 0, fine_stride = 0;
   int bstride = 0;
+  int* status = nullptr;  // checked build: a staged sample whose first footprint row misses the tile's
+                          // reach (a bin out of order) sets bit 16 and is not spread
 };
 cudaError_t launch_spread(const float2* P, int F, const int* bin_start, const int* sorted_l,
                           const int2* i0, const float* wts, int width, int tiles, int W,

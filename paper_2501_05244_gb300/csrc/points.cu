@@ -155,7 +155,8 @@ __global__ void __launch_bounds__(kScanThreads) points_scan(const int* __restric
 
 template <class Src>
 __global__ void points_scatter(const int* __restrict__ bin_of, const int* __restrict__ bin_start, const Src src,
-                               const Strides st, int* __restrict__ cursor, int* __restrict__ sorted_l) {
+                               const Strides st, int* __restrict__ cursor, int* __restrict__ sorted_l,
+                               int nbins, int* __restrict__ status) {
   const int item = blockIdx.y;
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= src.len(item)) return;
@@ -164,7 +165,9 @@ __global__ void points_scatter(const int* __restrict__ bin_of, const int* __rest
   bin_start += (size_t)item * st.bstride;
   cursor += (size_t)item * st.cstride;
   const int b = bin_of[l];
-  sorted_l[bin_start[b] + atomicAdd(cursor + b, 1)] = l;
+  if (!NURSD_CHECK(b >= 0 && b < nbins, status)) return;
+  const int slot = bin_start[b] + atomicAdd(cursor + b, 1);
+  if (NURSD_CHECK(slot >= 0 && slot < src.len(item), status)) sorted_l[slot] = l;
 }
 
 // Order each bin by sample index (insertion sort; bins hold a handful of samples), so
@@ -209,7 +212,8 @@ template <class Src>
 __global__ void points_gather(const int* __restrict__ sorted_l, const Src src, const Strides st, int width,
                               const int2* __restrict__ i0_in, const float* __restrict__ w_in,
                               const float2* __restrict__ frac_in, int2* __restrict__ i0_out,
-                              float* __restrict__ w_out, float2* __restrict__ frac_out, int* __restrict__ slot_of) {
+                              float* __restrict__ w_out, float2* __restrict__ frac_out, int* __restrict__ slot_of,
+                              int* __restrict__ status) {
   const int item = blockIdx.y;
   const int pos = blockIdx.x * blockDim.x + threadIdx.x;
   if (pos >= src.len(item)) return;
@@ -223,6 +227,7 @@ __global__ void points_gather(const int* __restrict__ sorted_l, const Src src, c
   if (frac_out) frac_out += po;
   if (slot_of) slot_of += po;
   const int l = sorted_l[pos];
+  if (!NURSD_CHECK(l >= 0 && l < src.len(item), status)) return;
   if (slot_of) slot_of[l] = pos;
   i0_out[pos] = i0_in[l];
   if (frac_out) frac_out[pos] = frac_in[l];
@@ -243,10 +248,10 @@ cudaError_t launch_points_on(const PointsArgs& a, const Src& src, int n, int max
   const dim3 grid((unsigned)std::max(1, (maxL + 255) / 256), (unsigned)n);
   points_prepare<<<grid, 256, 0, s>>>(a, src, st, i0_orig, w_orig, bin_of, frac_orig, counts);
   points_scan<<<n, kScanThreads, 0, s>>>(counts, nbins, bin_start, src, st);
-  points_scatter<<<grid, 256, 0, s>>>(bin_of, bin_start, src, st, counts + nbins, sorted_l);
+  points_scatter<<<grid, 256, 0, s>>>(bin_of, bin_start, src, st, counts + nbins, sorted_l, nbins, a.status);
   points_sort_bins<<<dim3((nbins + 255) / 256, (unsigned)n), 256, 0, s>>>(bin_start, nbins, sorted_l, st);
   points_gather<<<grid, 256, 0, s>>>(sorted_l, src, st, a.width, i0_orig, w_orig, frac_orig, i0_sorted, w_sorted,
-                                     frac_sorted, slot_of);
+                                     frac_sorted, slot_of, a.status);
   return cudaGetLastError();
 }
 }  // namespace

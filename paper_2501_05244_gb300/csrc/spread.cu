@@ -130,9 +130,11 @@ __global__ void __launch_bounds__(kRows * 32, 32 / kRows) spread_kernel(const fl
       for (int t = 0; t < 2 * KW; ++t) wv[t] = __ldg(w + t);
       const int ox = o.x - col0;
       // halves of the tile row (cells 0..7, 8..15) that the footprint ox .. ox+w-1 reaches (at least one)
-      const int halves = (ox < kTile / 2 && ox + KW > 0 ? 1 : 0) | (ox < kTile && ox + KW > kTile / 2 ? 2 : 0);
+      int halves = (ox < kTile / 2 && ox + KW > 0 ? 1 : 0) | (ox < kTile && ox + KW > kTile / 2 ? 2 : 0);
+      const int oy = o.y - ty * kRows;
+      if (!NURSD_CHECK(oy > -KW && oy < kRows && ox > -KW && ox < kTile, it.status)) halves = 0;
       sm.l[s] = l;
-      sm.org[s] = make_int2(halves, o.y - ty * kRows);
+      sm.org[s] = make_int2(halves, oy);
       float4* row = reinterpret_cast<float4*>(&sm.wx[s][0]);
 #pragma unroll
       for (int q = 0; q < kRowLen / 4; ++q) row[q] = make_float4(0.f, 0.f, 0.f, 0.f);
