@@ -150,6 +150,8 @@ struct nursd_plan_s {
   // [M][M][Mz][F], the plane's spectrum [M][M][F] and lattice field [F][N][N], a half transform [N][M][F],
   // the slice phasors [maxL][F] and the samples' fine z coordinates [maxL] (slot order)
   int nd_Mz = 0, nd_Wz = 0, nd_gz0 = 0;
+  int nd_G = 0;  // z slices per group of stage 1's slice launches (their phasors, windows and rows side by side)
+  float2 *nd_fine = nullptr, *nd_R1 = nullptr;
   double nd_dz = 0.0;
   float2 *nd_G3 = nullptr, *nd_U3w = nullptr, *nd_U3 = nullptr, *nd_What = nullptr, *nd_field = nullptr;
   float2 *nd_T = nullptr, *nd_Pz = nullptr;
@@ -1721,9 +1723,19 @@ int nursd_enable_3d(nursd_plan_t p, double dz, int32_t Mz, nursd_stream_t stream
   if (!(p->alloc(p->nd_G3, (size_t)M * M * Mz * F) && p->alloc(p->nd_U3w, (size_t)p->nd_Wz * M * M * F) &&
         p->alloc(p->nd_U3, (size_t)M * M * Mz * F) && p->alloc(p->nd_What, (size_t)M * M * F) &&
         p->alloc(p->nd_field, (size_t)F * N * N) && p->alloc(p->nd_T, (size_t)N * M * F) &&
-        p->alloc(p->nd_Pz, (size_t)maxL * F) && p->alloc(p->nd_decz, Mz) && p->alloc(p->nd_uz, maxL))) {
+        p->alloc(p->nd_decz, Mz) && p->alloc(p->nd_uz, maxL))) {
     p->nd_Mz = 0;
     return NURSD_ERR_OOM;
+  }
+  {  // stage 1 in groups of z slices: each slice's phasors, window and rows, as many slices as 4 GiB hold
+    const size_t per_slice = sizeof(float2) * ((size_t)maxL * F + (size_t)p->W * p->W * F + (size_t)p->W * M * F);
+    p->nd_G = (int)std::max<size_t>(1, std::min<size_t>(p->nd_Wz, (size_t(4) << 30) / per_slice));
+    const size_t G = p->nd_G;
+    if (!(p->alloc(p->nd_Pz, G * maxL * F) && p->alloc(p->nd_fine, G * p->W * p->W * F) &&
+          p->alloc(p->nd_R1, G * p->W * M * F))) {
+      p->nd_Mz = 0;
+      return NURSD_ERR_OOM;
+    }
   }
   p->nd_host.resize(Mz);
   for (int i = 0; i < Mz; ++i) p->nd_host[i] = (float)(1.0 / es_transform(i - Mz / 2, p->w, p->beta, 2 * Mz));
@@ -1755,25 +1767,34 @@ int nursd_forward_3d(nursd_plan_t p, const nursd_c64* d_phasor, void* d_out, nur
   const long long MMF = (long long)M * M * F;
   cudaError_t e = cudaSuccess;
   // stage 1, 3D type 1: per fine z cell of the window, the slice's phasors, the planar spread and the
-  // lateral passes with deconvolution -> the slice's lateral spectrum
-  for (int iz = 0; e == cudaSuccess && iz < p->nd_Wz; ++iz) {
+  // lateral passes with deconvolution -> the slice's lateral spectrum; each step one launch over a
+  // group of nd_G slices (the slice the outer index of the phasors, windows and rows)
+  const long long pz_stride = (long long)std::max(1, p->maxL) * F;
+  for (int iz0 = 0; e == cudaSuccess && iz0 < p->nd_Wz; iz0 += p->nd_G) {
+    const int n = std::min(p->nd_G, p->nd_Wz - iz0);
     {
       StageTimer t(p, NURSD_STAGE_SPREAD, s, 2);
       e = launch_z_slice_phasors(reinterpret_cast<const float2*>(d_phasor), p->sorted_l, p->nd_uz, L, F,
-                                 p->nd_gz0 + iz, p->w, p->beta, p->nd_Pz, s);
-      if (e == cudaSuccess)
-        e = launch_spread(p->nd_Pz, F, p->bin_start, nullptr, p->i0_sorted, p->w_sorted, p->w, p->tiles, W, p->fine,
-                          s, p->spread_rows);
+                                 p->nd_gz0 + iz0, n, pz_stride, p->w, p->beta, p->nd_Pz, s);
+      if (e == cudaSuccess) {
+        SpreadItems si;  // the same sorted samples for every slice, its own phasors and window
+        si.n = n;
+        si.p_stride = pz_stride;
+        si.fine_stride = (long long)W * W * F;
+        si.status = p->status;
+        e = launch_spread(p->nd_Pz, F, p->bin_start, nullptr, p->i0_sorted, p->w_sorted, p->w, p->tiles, W,
+                          p->nd_fine, s, p->spread_rows, si);
+      }
     }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess) {  // along x: the windows' rows back to back
       StageTimer t(p, NURSD_STAGE_FFT_X, s, 1);
-      e = axis_pass(p, p->fine, p->R1, logf, false, F, W, (long long)W * F, F, (long long)M * F, F, W, p->g0, M,
-                    -M / 2, nullptr, nullptr, 1.f, s);
+      e = axis_pass(p, p->nd_fine, p->nd_R1, logf, false, F, n * W, (long long)W * F, F, (long long)M * F, F, W,
+                    p->g0, M, -M / 2, nullptr, nullptr, 1.f, s);
     }
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess) {  // along y with the deconvolution, the slice as the panels' outer channel index
       StageTimer t(p, NURSD_STAGE_FFT_Y, s, 1);
-      e = axis_pass(p, p->R1, p->nd_U3w + iz * MMF, logf, false, F, M, F, (long long)M * F, F, (long long)M * F, W,
-                    p->g0, M, -M / 2, p->deconv, p->deconv, 1.f, s);
+      e = axis_pass(p, p->nd_R1, p->nd_U3w + iz0 * MMF, logf, false, F, M, F, (long long)M * F, F, (long long)M * F,
+                    W, p->g0, M, -M / 2, p->deconv, p->deconv, 1.f, s, n, (long long)W * M * F, MMF);
     }
   }
   if (e == cudaSuccess) {  // along z: the window's slices -> kz in I_Mz, divided by psi_hat_z(kz)

@@ -32,13 +32,15 @@ __global__ void z_coords_kernel(const float* __restrict__ h_rel, const int* __re
   uz_sorted[s] = (float)(h * inv_fine_dz);
 }
 
-// Pz[s][f] = P[sorted_l[s]][f] phi(2 (gz - uz[s]) / w) for the z cell gz (phi the ES kernel, zero for
-// |2 (gz - uz) / w| >= 1), in slot order: one thread per (slot, channel).
+// Pz[j][s][f] = P[sorted_l[s]][f] phi(2 (gz - uz[s]) / w) for the z cells gz = gz_first + j (blockIdx.y;
+// phi the ES kernel, zero for |2 (gz - uz) / w| >= 1), in slot order: one thread per (slot, channel).
 __global__ void z_slice_phasors_kernel(const float2* __restrict__ P, const int* __restrict__ sorted_l,
-                                       const float* __restrict__ uz, int L, int F, int gz, int w, float beta,
-                                       float2* __restrict__ Pz) {
+                                       const float* __restrict__ uz, int L, int F, int gz_first, long long pz_stride,
+                                       int w, float beta, float2* __restrict__ Pz) {
   const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (e >= (long long)L * F) return;
+  const int gz = gz_first + (int)blockIdx.y;
+  Pz += blockIdx.y * pz_stride;
   const int s = (int)(e / F), f = (int)(e % F);
   const float zz = 2.f * ((float)gz - __ldg(uz + s)) / (float)w;
   float2 v = make_float2(0.f, 0.f);
@@ -79,10 +81,12 @@ cudaError_t launch_z_coords(const float* h, const int* sorted_l, int L, double i
   return cudaGetLastError();
 }
 
-cudaError_t launch_z_slice_phasors(const float2* P, const int* sorted_l, const float* uz, int L, int F, int gz, int w,
-                                   float beta, float2* Pz, cudaStream_t s) {
+cudaError_t launch_z_slice_phasors(const float2* P, const int* sorted_l, const float* uz, int L, int F, int gz_first,
+                                   int n, long long pz_stride, int w, float beta, float2* Pz, cudaStream_t s) {
   if (L <= 0) return cudaSuccess;
-  z_slice_phasors_kernel<<<blocks_for((long long)L * F), 256, 0, s>>>(P, sorted_l, uz, L, F, gz, w, beta, Pz);
+  if (n < 1 || n > 65535 || pz_stride < (long long)L * F) return cudaErrorInvalidValue;
+  z_slice_phasors_kernel<<<dim3(blocks_for((long long)L * F), (unsigned)n), 256, 0, s>>>(P, sorted_l, uz, L, F, gz_first,
+                                                                                       pz_stride, w, beta, Pz);
   return cudaGetLastError();
 }
 

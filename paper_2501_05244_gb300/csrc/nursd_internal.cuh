@@ -339,9 +339,10 @@ cudaError_t launch_srsd_interp_xy_contract(const float2* Yh, int L, int M, int F
 // uz_sorted[s] = h[sorted_l[s]] inv_fine_dz (|h| > half_extent: status bit 1, no weight).
 cudaError_t launch_z_coords(const float* h, const int* sorted_l, int L, double inv_fine_dz, double half_extent,
                             float* uz_sorted, int* status, cudaStream_t s);
-// Pz[s][f] = P[sorted_l[s]][f] phi(2 (gz - uz[s]) / w) (slot order).
-cudaError_t launch_z_slice_phasors(const float2* P, const int* sorted_l, const float* uz, int L, int F, int gz, int w,
-                                   float beta, float2* Pz, cudaStream_t s);
+// Pz[j][s][f] = P[sorted_l[s]][f] phi(2 (gz - uz[s]) / w), gz = gz_first + j for j < n (slot order;
+// slice j at Pz + j pz_stride).
+cudaError_t launch_z_slice_phasors(const float2* P, const int* sorted_l, const float* uz, int L, int F, int gz_first,
+                                   int n, long long pz_stride, int w, float beta, float2* Pz, cudaStream_t s);
 // What[k][f] = scale sum_kz U3[k][kz][f] G3[k][kz][f] for nk lateral modes k.
 cudaError_t launch_kz_sum(const float2* U3, const float2* G3, long long nk, int Mz, int F, float scale, float2* What,
                           cudaStream_t s);
