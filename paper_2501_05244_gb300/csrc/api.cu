@@ -1782,6 +1782,8 @@ int nursd_forward_3d(nursd_plan_t p, const nursd_c64* d_phasor, void* d_out, nur
         si.p_stride = pz_stride;
         si.fine_stride = (long long)W * W * F;
         si.status = p->status;
+        si.uz = p->nd_uz;  // each slice spreads only the samples its z cell reaches
+        si.gz_first = p->nd_gz0 + iz0;
         e = launch_spread(p->nd_Pz, F, p->bin_start, nullptr, p->i0_sorted, p->w_sorted, p->w, p->tiles, W,
                           p->nd_fine, s, p->spread_rows, si);
       }

@@ -242,6 +242,10 @@ struct SpreadItems {
   int bstride = 0;
   int* status = nullptr;  // checked build: a staged sample whose first footprint row misses the tile's
                           // reach (a bin out of order) sets bit 16 and is not spread
+  // 3D slices (item j = fine z cell gz_first + j): with uz (the samples' fine z coordinates, slot
+  // order), samples whose z footprint misses the item's cell (zero phasors there) are skipped
+  const float* uz = nullptr;
+  int gz_first = 0;
 };
 cudaError_t launch_spread(const float2* P, int F, const int* bin_start, const int* sorted_l,
                           const int2* i0, const float* wts, int width, int tiles, int W,

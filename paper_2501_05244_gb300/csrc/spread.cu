@@ -102,6 +102,11 @@ __global__ void __launch_bounds__(kRows * 32, 32 / kRows) spread_kernel(const fl
   wr[1] = make_int2(nA + bsB[wlo] - bS, nA + bsB[y + 1] - bS);
   wr[2] = make_int2(nAB + bsC[wlo] - cS, nAB + bsC[y + 1] - cS);
   auto slot_of = [&](int v) { return v < nA ? aS + v : (v < nAB ? bS + (v - nA) : cS + (v - nAB)); };
+  // 3D slices: does the sample's z footprint reach this item's cell (the test the slice phasors use)?
+  auto z_reaches = [&](int slot) {
+    const float zz = 2.f * ((float)(it.gz_first + (int)blockIdx.z) - __ldg(it.uz + slot)) / (float)KW;
+    return fabsf(zz) < 1.f;
+  };
 
   float2 acc_re[kPairs], acc_im[kPairs];
 #pragma unroll
@@ -118,7 +123,8 @@ __global__ void __launch_bounds__(kRows * 32, 32 / kRows) spread_kernel(const fl
     if (!sorted_l)
       for (int s = warp; s < cn; s += kWarps) {
         const int slot = slot_of(c0 + s);
-        cp_async8(&sm.p[s][lane], live ? P + (size_t)slot * F + f0 + lane : P, live);
+        const bool use = live && (!BATCH || !it.uz || z_reaches(slot));
+        cp_async8(&sm.p[s][lane], use ? P + (size_t)slot * F + f0 + lane : P, use);
       }
     for (int s = threadIdx.x; s < cn; s += kWarps * 32) {
       const int slot = slot_of(c0 + s);
@@ -133,6 +139,7 @@ __global__ void __launch_bounds__(kRows * 32, 32 / kRows) spread_kernel(const fl
       int halves = (ox < kTile / 2 && ox + KW > 0 ? 1 : 0) | (ox < kTile && ox + KW > kTile / 2 ? 2 : 0);
       const int oy = o.y - ty * kRows;
       if (!NURSD_CHECK(oy > -KW && oy < kRows && ox > -KW && ox < kTile, it.status)) halves = 0;
+      if (BATCH && it.uz && !z_reaches(slot)) halves = 0;  // a zero phasor in this slice: nothing to add
       sm.l[s] = l;
       sm.org[s] = make_int2(halves, oy);
       float4* row = reinterpret_cast<float4*>(&sm.wx[s][0]);
