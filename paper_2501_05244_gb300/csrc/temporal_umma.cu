@@ -547,8 +547,11 @@ cudaError_t launch_n(const TemporalMaps& m, const float* h, const float* wcol, f
   if (e == cudaSuccess) e = configure_n<N2, 1>();
   if (e != cudaSuccess) return e;
   const int ntiles = (L + kBM - 1) / kBM;
-  temporal_umma_kernel<N2, 0><<<std::min(ntiles, sms), kUThreads, S::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status,
-                                                                                 row_slot, wcol, fix, UItems<0>{});
+  // the fewest CTAs with the same most tiles per CTA (the critical path): the SMs left over run the
+  // work queued beside the transform (the relay-sample sort of a reconstruction)
+  const int per_cta = (ntiles + sms - 1) / sms, grid = (ntiles + per_cta - 1) / per_cta;
+  temporal_umma_kernel<N2, 0><<<grid, kUThreads, S::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status, row_slot, wcol, fix,
+                                                                UItems<0>{});
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // listed rows: at most min(L, cap); CTAs beyond the listed tiles return at once
