@@ -93,13 +93,31 @@ def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
     return units_per_rank * world / (ms_max / 1e3)
 
 
-def measured_traffic():
+CONTRACT_KERNELS = {
+    "tc": ("contract_tc_kernel (tensor cores: tf32 head/tail products, table as the A operand by TMA)",
+           "paper_2501_05244_gb300/csrc/contract_tc.cu"),
+    "fp32": ("contract_tma_kernel (FP32 packed FMAs, bulk-copy rings)", "paper_2501_05244_gb300/csrc/contract.cu"),
+}
+
+
+def contract_kernel(plan, F, Z, adjoint_plan=False):
+    """Key of CONTRACT_KERNELS for the kernel a plan's forward contraction runs (the library's rule:
+    the tensor form when tuned on, on a plan with the adjoint enabled, Z = 128 rows and F a multiple
+    of 16 up to 208)."""
+    ok = plan.tuning()["contract_tc"] == 1 and adjoint_plan and Z == 128 and F % 16 == 0 and 16 <= F <= 208
+    return "tc" if ok else "fp32"
+
+
+def measured_traffic(source):
     """Per-launch DRAM traffic of the contraction from the recorded ncu counters
-    (profiles/contract_traffic.json), or None when the kernel source changed since they were taken."""
+    (profiles/contract_traffic.json), or None when they were taken on another kernel or its source
+    changed since."""
     import hashlib
 
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "contract_traffic.json")))
+        if rec["source"] != source:
+            return None
         src = open(os.path.join(ROOT, rec["source"]), "rb").read()
     except (OSError, ValueError, KeyError):
         return None
@@ -892,6 +910,7 @@ def run_ours(args, rank, world, local):
     om, wt = nursd.phasor_frequencies(g.lambda_c, g.dt, g.t_pad, g.F)
     stream = torch.cuda.current_stream()
     plan = nursd.Plan(g.N, g.pitch, g.center, g.depths, om, wt, T=g.T, t0=g.t0, dt=g.dt, max_points=L)
+    ckernel = CONTRACT_KERNELS[contract_kernel(plan, g.F, len(g.depths))]
     d_xy = torch.from_numpy(wl.xy).cuda()
     d_hist = torch.from_numpy(wl.hist).cuda()
     out = plan.empty_output()
@@ -1068,10 +1087,10 @@ def run_ours(args, rank, world, local):
                    "l2": "inputs larger than L2 (histograms 268 MB, transfer table %.2f GB); no flush" %
                          (plan.n_classes * F * Z * 8 / 1e9)},
         "recon_per_s": world * 1e3 / ms,
-        "roofline": {"bound": "hbm", "kernel": "contract_kernel (transfer-function multiply + frequency sum)",
+        "roofline": {"bound": "hbm", "kernel": ckernel[0],
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": f"{peak_src} hbm_gbs",
-                     "traffic": measured_traffic() if args.workload == "spad" else None,
+                     "traffic": measured_traffic(ckernel[1]) if args.workload == "spad" else None,
                      "algorithmic_bytes": contract_bytes, "avg_launch_ms": c_avg},
         "step_hbm": {"algorithmic_bytes": step_bytes, "achieved_gbs": step_bytes / (ms / 1e3) / 1e9,
                      "frac": step_bytes / (ms / 1e3) / 1e9 / peak},

@@ -488,6 +488,14 @@ int nursd_forward_3d(nursd_plan_t plan, const nursd_c64* d_phasor, void* d_out, 
  * tensor-core products per symmetry class where the shape allows (M a power of two, F a multiple of 8,
  * Z = 32, 64 or 128), 0 keeps the FP32 SIMT kernel; the two agree to FP32 rounding (the tensor form
  * splits each operand into tf32 head and tail and keeps the three leading products).
+ * NURSD_TUNE_CONTRACT_TC: 0 (default) runs the contraction of a single reconstruction (and of the
+ * adjoint) on the FP32 bulk-copy kernel; 1 runs it on the tensor cores where the shape allows (M a
+ * power of two; forward: Z = 128, F a multiple of 16 up to 208, and a plan created with
+ * NURSD_ENABLE_ADJOINT, whose [class][z][f] table copy the forward reads; adjoint: F = 128, Z a
+ * multiple of 16 up to 208), else keeps the FP32 kernel.  With one reconstruction a class's product
+ * has only 16 real output columns, and on this shape the tensor form is the slower of the two.  The
+ * tensor form's error stays within about 3 (2K / 8) 2^-23 relative of the FP32 kernel's (K the
+ * summed length: its accumulations are rounded toward zero).
  * nursd_plan_tune returns UNSUPPORTED for a value outside those sets, INVALID_ARG for an unknown
  * parameter.
  */
@@ -496,6 +504,7 @@ int nursd_forward_3d(nursd_plan_t plan, const nursd_c64* d_phasor, void* d_out, 
 #define NURSD_TUNE_BATCH_GROUPED 2
 #define NURSD_TUNE_BATCH_GROUP 3
 #define NURSD_TUNE_BATCH_TENSOR 4
+#define NURSD_TUNE_CONTRACT_TC 5
 int nursd_plan_tune(nursd_plan_t plan, int32_t param, int32_t value);
 int nursd_plan_get_tune(nursd_plan_t plan, int32_t param, int32_t* h_value);
 

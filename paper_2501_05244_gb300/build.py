@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libnursd.so")
 LIB_CHECKED = os.path.join(LIBDIR, "libnursd_checked.so")  # -DNURSD_CHECKED: bounds checks into the status word
-SOURCES = ["api.cu", "fft.cu", "fft_reg.cu", "temporal_tc.cu", "temporal_umma.cu", "points.cu", "spread.cu", "contract.cu", "contract_umma.cu", "gtf.cu", "interp.cu", "illum.cu", "srsd_interp.cu", "resample.cu", "nursd3d.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "fft.cu", "fft_reg.cu", "temporal_tc.cu", "temporal_umma.cu", "points.cu", "spread.cu", "contract.cu", "contract_umma.cu", "contract_tc.cu", "gtf.cu", "interp.cu", "illum.cu", "srsd_interp.cu", "resample.cu", "nursd3d.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

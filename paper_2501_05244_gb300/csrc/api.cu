@@ -98,6 +98,7 @@ struct nursd_plan_s {
   int batch_streams = 4;
   int batch_grouped = 1;
   int batch_tensor = 1;  // the batched contraction on the tensor cores where supported
+  int contract_tc = 0;   // the single-reconstruction contraction (and its adjoint) on the tensor cores (opt-in)
   int group_size = 0;  // items per grouped launch (1 .. group; 0 until the workspaces exist)
   // geometry
   int N = 0, M = 0, nf = 0, Z = 0, F = 0, T = 0, w = 0, W = 0, tiles = 0, g0 = 0, ncls = 0, maxL = 0, L = -1;
@@ -634,11 +635,19 @@ int run_idft_crop(nursd_plan_s* p, void* out, cudaStream_t s, const float2* Ysrc
   return from_cuda(idft_crop(p, Ysrc ? Ysrc : p->Y, p->Z, p->T1, out, (p->flags & NURSD_OUTPUT_MAGNITUDE) != 0, s));
 }
 
+// Y[k][z] = sum_f spec[k][f] G[cls(k)][f][z]: the FP32 bulk-copy form on Gc, or, when the plan opts in
+// and keeps the transposed table (adjoint plans), the tensor-core form with GcT as the A operand.
+cudaError_t contract_forward(nursd_plan_s* p, const float2* spec, cudaStream_t s) {
+  if (p->contract_tc && p->GcT && contract_tc_supported(p->M, p->Z, p->F))
+    return launch_contract_tc(spec, p->GcT, p->cls, p->ncls, p->M, p->Z, p->F, false, p->Y, s, p->status);
+  return launch_contract(spec, p->Gc, p->cls, p->ncls, p->M, p->F, p->Z, p->Y, s, p->status);
+}
+
 int run_propagate(nursd_plan_s* p, const float2* spec, void* out, cudaStream_t s) {
   cudaError_t e;
   {
     StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
-    e = launch_contract(spec, p->Gc, p->cls, p->ncls, p->M, p->F, p->Z, p->Y, s, p->status);
+    e = contract_forward(p, spec, s);
   }
   if (e != cudaSuccess) return from_cuda(e);
   return run_idft_crop(p, out, s);
@@ -1041,7 +1050,10 @@ int run_adjoint_spectrum(nursd_plan_s* p, const float2* vol, cudaStream_t s) {
   }
   if (e == cudaSuccess) {
     StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
-    e = launch_contract_adjoint(p->Y, p->GcT, p->cls, p->ncls, M, F, Z, p->U, s, p->status);
+    if (p->contract_tc && contract_tc_supported(M, F, Z))  // U[k][f] = sum_z conj(Gc[c][f][z]) Y[k][z]
+      e = launch_contract_tc(p->Y, p->Gc, p->cls, p->ncls, M, F, Z, true, p->U, s, p->status);
+    else
+      e = launch_contract_adjoint(p->Y, p->GcT, p->cls, p->ncls, M, F, Z, p->U, s, p->status);
   }
   return from_cuda(e);
 }
@@ -1650,7 +1662,7 @@ int nursd_forward_points(nursd_plan_t p, const nursd_c64* d_phasor, int32_t K, c
   int rc = run_nufft1(p, reinterpret_cast<const float2*>(d_phasor), p->U, s);
   if (rc == NURSD_OK) {
     StageTimer t(p, NURSD_STAGE_CONTRACT, s, 1);
-    rc = from_cuda(launch_contract(p->U, p->Gc, p->cls, p->ncls, M, p->F, p->Z, p->Y, s, p->status));
+    rc = from_cuda(contract_forward(p, p->U, s));
   }
   if (rc == NURSD_OK) rc = run_points_output(p, K, d_vox_xy, nullptr, d_out, s);
   return rc;
@@ -2096,6 +2108,10 @@ int nursd_plan_tune(nursd_plan_t p, int32_t param, int32_t value) {
       if (value != 0 && value != 1) return NURSD_ERR_UNSUPPORTED;
       p->batch_tensor = value;
       return NURSD_OK;
+    case NURSD_TUNE_CONTRACT_TC:
+      if (value != 0 && value != 1) return NURSD_ERR_UNSUPPORTED;
+      p->contract_tc = value;
+      return NURSD_OK;
     default:
       return NURSD_ERR_INVALID_ARG;
   }
@@ -2109,6 +2125,7 @@ int nursd_plan_get_tune(nursd_plan_t p, int32_t param, int32_t* value) {
     case NURSD_TUNE_BATCH_GROUPED: *value = p->batch_grouped; return NURSD_OK;
     case NURSD_TUNE_BATCH_GROUP: *value = p->group_size; return NURSD_OK;
     case NURSD_TUNE_BATCH_TENSOR: *value = p->batch_tensor; return NURSD_OK;
+    case NURSD_TUNE_CONTRACT_TC: *value = p->contract_tc; return NURSD_OK;
     default: return NURSD_ERR_INVALID_ARG;
   }
 }

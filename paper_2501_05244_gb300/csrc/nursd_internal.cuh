@@ -269,6 +269,14 @@ cudaError_t set_contract_wait_limit(long long polls, cudaStream_t s);
 // Adjoint: R[k][f] = sum_z Yt[k][z] * conj(GcT[cls(k)][z][f]).
 cudaError_t launch_contract_adjoint(const float2* Yt, const float2* GcT, const int2* cls_pq, int ncls, int M, int F,
                                     int Z, float2* R, cudaStream_t s, int* status = nullptr);
+// Tensor-core form with the table as the A operand (contract_tc.cu): for every mode k of every class,
+// out[k][r] = sum_i A[cls(k)][r][i] X[k][i] (conj = false) or sum_i conj(A[cls(k)][r][i]) X[k][i]
+// (conj = true), table [ncls][rows][inner].  The forward is (X = U, A = GcT, rows Z, inner F), the
+// adjoint (X = Y, A = Gc, rows F, inner Z, conj).  Needs rows = 128 and inner a multiple of 16;
+// cudaErrorInvalidValue otherwise.  status: wait time-outs set bit 2.
+bool contract_tc_supported(int M, int rows, int inner);
+cudaError_t launch_contract_tc(const float2* X, const float2* table, const int2* cls_pq, int ncls, int M, int rows,
+                               int inner, bool conj, float2* out, cudaStream_t s, int* status);
 
 // ------------------------------------------------------------ interpolation
 // Type-2 interpolation at the sorted relay samples from a channel-last fine

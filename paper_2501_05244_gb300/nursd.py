@@ -29,7 +29,8 @@ NURSD_CONFOCAL = 0x4
 NURSD_UPSAMPLE_NEAREST = 0
 NURSD_UPSAMPLE_LINEAR = 1
 #: plan tunables (nursd_plan_tune)
-TUNABLES = {"spread_rows": 0, "batch_streams": 1, "batch_grouped": 2, "batch_group": 3, "batch_tensor": 4}
+TUNABLES = {"spread_rows": 0, "batch_streams": 1, "batch_grouped": 2, "batch_group": 3, "batch_tensor": 4,
+            "contract_tc": 5}
 
 #: every entry point declared in include/nursd.h
 EXPORTS = (
