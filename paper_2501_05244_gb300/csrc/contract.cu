@@ -143,9 +143,11 @@ __global__ void __launch_bounds__(kClsPerCta * 32, 2) contract_kernel(const floa
 // a transaction count; the ring runs on across unit boundaries, so the next
 // unit's rows are in flight while the current one finishes.  A stage holds
 // kRows table rows (one contiguous copy of kRows x ZS values, or one per row when
-// the column is narrower than the row) and the class's 8 spectrum segments of
-// those rows.  Used when every column is full (J % (32 ZPL) == 0) and
-// R % kRows == 0, so every copy is a whole number of 16-byte units.  Every
+// the column is narrower than the row); the class's 8 spectrum values of those rows
+// come by plain loads, one per lane, issued as many stages ahead and held in
+// registers until their stage is consumed.  Used when every column is full
+// (J % (32 ZPL) == 0) and R % kRows == 0, so every copy is a whole number of
+// 16-byte units.  Every
 // barrier wait is bounded: on time-out the kernel sets status bit 2 and returns.
 //
 // Arithmetic: each spectrum value u is expanded once per stage to (ux, ux, -uy, uy)
@@ -200,8 +202,7 @@ template <int ZPL>
 struct TmaShape {
   static constexpr int ZS = 32 * ZPL;
   static constexpr int kStageTable = kRows * ZS;  // float2
-  static constexpr int kStageU = 8 * kRows;       // float2
-  static constexpr int kStage = kStageTable + kStageU;
+  static constexpr int kStage = kStageTable;
   static constexpr size_t kRingBytes = sizeof(float2) * kTmaWarps * kStages * kStage;
   static constexpr size_t kExpBytes = sizeof(float4) * kTmaWarps * 8 * kRows;  // expanded spectrum values
   static constexpr size_t kPtrBytes = sizeof(void*) * kTmaWarps * 9;            // producer's source rows
@@ -227,7 +228,6 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) contract_tma_kernel(const f
   constexpr int ZS = S::ZS;
   extern __shared__ __align__(16) unsigned char raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long wait_limit = g_contract_wait_limit;
   float2* myring = reinterpret_cast<float2*>(raw) + (size_t)warp * kStages * S::kStage;
   float4* myexp = reinterpret_cast<float4*>(raw + S::kRingBytes) + warp * 8 * kRows;
   // producer's source rows of its current unit (each slot is written and read by one lane only):
@@ -242,8 +242,9 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) contract_tma_kernel(const f
   if (w0 >= nunit) return;  // whole warp; nothing below synchronises across warps
 
   // ---- producer: unit iu, chunk ich, ring sequence number seq; lane 0 copies the table rows,
-  // lanes 0..7 each copy one member's spectrum segment
+  // every lane loads one member's spectrum value of the stage
   int iu = w0, ich = 0;
+  float2 uring[kStages];  // spectrum values of the stages in flight, oldest first
   auto issue = [&](unsigned seq) {
     if (iu >= nunit) return;
     if (ich == 0) {
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) contract_tma_kernel(const f
     }
     const int st = seq % kStages, f0 = ich * kRows;
     float2* dst = myring + st * S::kStage;
-    if (lane == 0) mbar_expect(mybar + st, (unsigned)(sizeof(float2) * (kRows * ZS + 8 * kRows)));
+    if (lane == 0) mbar_expect(mybar + st, (unsigned)(sizeof(float2) * kRows * ZS));
     __syncwarp();
     if (lane == 0) {
       const float2* g = mysrc[8];
@@ -266,9 +267,9 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) contract_tma_kernel(const f
           bulk_g2s(dst + r * ZS, g + (size_t)(f0 + r) * Z, (unsigned)(sizeof(float2) * ZS), mybar + st);
       }
     }
-    if (lane < 8)
-      bulk_g2s(dst + S::kStageTable + lane * kRows, mysrc[lane] + f0, (unsigned)(sizeof(float2) * kRows),
-               mybar + st);
+    // lane s * kRows + r: member s's spectrum value at frequency f0 + r, into the register ring (eight
+    // 32-byte bulk copies per stage would quadruple the copy operations the SM issues)
+    uring[kStages - 1] = __ldg(mysrc[lane / kRows] + f0 + lane % kRows);
     if (++ich == nchunk) {
       ich = 0;
       iu += W;
@@ -279,7 +280,14 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) contract_tma_kernel(const f
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncwarp();
-  for (unsigned k = 0; k < kStages; ++k) issue(k);
+  auto rotate = [&] {
+#pragma unroll
+    for (int q = 0; q + 1 < kStages; ++q) uring[q] = uring[q + 1];
+  };
+  for (unsigned k = 0; k < kStages; ++k) {
+    rotate();
+    issue(k);
+  }
 
   // ---- consumer
   unsigned cseq = 0;
@@ -293,13 +301,14 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) contract_tma_kernel(const f
       for (int s = 0; s < 8; ++s) acc[i][s] = make_float2(0.f, 0.f);
     for (int ch = 0; ch < nchunk; ++ch) {
       const int st = cseq % kStages;
-      if (!mbar_wait(mybar + st, (cseq / kStages) & 1, wait_limit)) {
+      // the bound is read at each wait (not held in a register across the loop)
+      if (!mbar_wait(mybar + st, (cseq / kStages) & 1, *reinterpret_cast<volatile long long*>(&g_contract_wait_limit))) {
         ok = false;
         break;
       }
       const float2* stage = myring + st * S::kStage;
       {  // expand this stage's 8 x kRows spectrum values, one per lane
-        const float2 u = stage[S::kStageTable + lane];
+        const float2 u = uring[0];
         myexp[lane] = CONJ ? make_float4(u.x, u.x, u.y, -u.y) : make_float4(u.x, u.x, -u.y, u.y);
       }
       __syncwarp();
@@ -326,6 +335,7 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) contract_tma_kernel(const f
         }
       }
       __syncwarp();  // every lane has read this stage and the expanded values
+      rotate();
       issue(cseq + kStages);
       ++cseq;
     }

@@ -154,7 +154,7 @@ def test_batched_equals_single_calls_at_every_setting(grouped, group, streams, r
     plan.tune("batch_streams", streams)
     plan.tune("spread_rows", rows)
     assert plan.tuning() == {"spread_rows": rows, "batch_streams": streams, "batch_grouped": grouped,
-                             "batch_group": group, "batch_tensor": 1}
+                             "batch_group": group, "batch_tensor": 1, "contract_tc": 0}
     xys = [torch.from_numpy(x).cuda() for x in c["xys"]]
     hists = [torch.from_numpy(h).cuda() for h in c["hists"]]
     outs = plan.forward_batched(xys, hists)  # side by side
