@@ -1,8 +1,9 @@
 // NUFFT type-1 spreading (Sec. 6, step 1): b[g][f] = sum_l P[l][f] phi_x phi_y.
 //
 // No atomics: one CTA owns a tile of the fine-grid window 16 cells wide and ROWS
-// (4, 8 or 16, a plan setting) rows high, for 32 channels; each of its ROWS warps owns one tile row, each lane
-// one channel, and the row's 16 cells live in registers.  Samples are binned by (tile column,
+// (4, 8 or 16, a plan setting) rows high, for 32 or 64 channels; each of its ROWS warps owns one tile
+// row, each lane one channel (two adjacent ones when F is even and at least 64), and the row's 16
+// cells live in registers.  Samples are binned by (tile column,
 // edge flag, first footprint row), tile column major, the edge flag marking
 // footprints that cross into the next tile column.  So the samples that touch
 // the tile -- first rows ty*ROWS-w+1 .. ty*ROWS+ROWS-1 in this tile column, and in the
@@ -25,7 +26,6 @@
 namespace nursd {
 namespace {
 
-constexpr int kCh = 32;        // channels per CTA
 constexpr int kCap = 128;      // samples staged per chunk
 
 // Cells of the tile row in packed pairs: for cell 2j + h, lane-wise, acc_re[j] holds the real part
@@ -34,8 +34,9 @@ constexpr int kPairs = kTile / 2;
 constexpr int kRowPad = 8;                // x-weight row: cell c of the tile at index kRowPad + c
 constexpr int kRowLen = kRowPad + kTile;  // 24 floats; indices below kRowPad are never read
 
+template <int CPL>  // channels per lane; a CTA covers 32 CPL channels
 struct SpreadSmem {
-  float2 p[kCap][kCh];    // phasor slices
+  float2 p[kCap][32 * CPL];  // phasor slices
   float wx[kCap][kRowLen];  // x weight of each tile cell (0 where the footprint misses it)
   float wy[kCap][8];      // y weights
   int2 org[kCap];         // halves of the tile row reached (bit 0: cells 0..7, bit 1: 8..15), first row rel. to the tile's
@@ -45,6 +46,18 @@ struct SpreadSmem {
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc, bool valid) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(gsrc), "r"(valid ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(valid ? 16 : 0) : "memory");
+}
+// The CPL channels of this lane's phasor slice of staged sample s: one copy of 8 CPL bytes.
+template <int CPL>
+__device__ __forceinline__ void copy_slice(float2* dst, const float2* src, bool valid) {
+  if constexpr (CPL == 1)
+    cp_async8(dst, src, valid);
+  else
+    cp_async16(dst, src, valid);
 }
 
 // d = a * b + c, lane-wise on two fp32 values, one instruction.
@@ -57,12 +70,14 @@ __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
   return r;
 }
 
-// One CTA per (tile, group of 32 channels); warp = tile row, lane = channel.  A staged sample
-// carries its x weights laid out on the tile's 16 cells (zeros outside its footprint), so the
-// warp adds it to every cell of its row with 16 packed FMAs and no branch on the offset; a
-// zero weight leaves a cell's sum unchanged, so the result equals the footprint-only sum.
-template <int KW, int kRows, bool BATCH>
-__global__ void __launch_bounds__(kRows * 32, 32 / kRows) spread_kernel(const float2* __restrict__ P, int F,
+// One CTA per (tile, group of 32 CPL channels); warp = tile row, lane = CPL adjacent channels.  A
+// staged sample carries its x weights laid out on the tile's 16 cells (zeros outside its
+// footprint), so the warp adds it to every cell of its row with 16 packed FMAs per channel and no
+// branch on the offset; a zero weight leaves a cell's sum unchanged, so the result equals the
+// footprint-only sum.  With CPL = 2 a visit's shared loads of the sample's weights serve twice
+// the channels.
+template <int KW, int kRows, bool BATCH, int CPL>
+__global__ void __launch_bounds__(kRows * 32, (CPL == 1 ? 32 : 16) / kRows) spread_kernel(const float2* __restrict__ P, int F,
                                                                 const int* __restrict__ bin_start,
                                                                 const int* __restrict__ sorted_l,
                                                                 const int2* __restrict__ i0,
@@ -78,7 +93,8 @@ __global__ void __launch_bounds__(kRows * 32, 32 / kRows) spread_kernel(const fl
     wts += item * it.pts * 2 * KW;
     fine += item * it.fine_stride;
   }
-  SpreadSmem& sm = *reinterpret_cast<SpreadSmem*>(raw);
+  SpreadSmem<CPL>& sm = *reinterpret_cast<SpreadSmem<CPL>*>(raw);
+  constexpr int kCh = 32 * CPL;
   constexpr int kWarps = kRows;  // one warp per tile row
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ty = blockIdx.x / tiles, tx = blockIdx.x % tiles;
@@ -108,13 +124,16 @@ __global__ void __launch_bounds__(kRows * 32, 32 / kRows) spread_kernel(const fl
     return fabsf(zz) < 1.f;
   };
 
-  float2 acc_re[kPairs], acc_im[kPairs];
+  float2 acc_re[kPairs][CPL], acc_im[kPairs][CPL];
 #pragma unroll
-  for (int j = 0; j < kPairs; ++j) {
-    acc_re[j] = make_float2(0.f, 0.f);
-    acc_im[j] = make_float2(0.f, 0.f);
-  }
-  const bool live = f0 + lane < F;
+  for (int j = 0; j < kPairs; ++j)
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      acc_re[j][c] = make_float2(0.f, 0.f);
+      acc_im[j][c] = make_float2(0.f, 0.f);
+    }
+  const int fl = f0 + lane * CPL;  // this lane's first channel; CPL = 2 needs F even (whole pairs)
+  const bool live = fl < F;
   for (int c0 = 0; c0 < n; c0 += kCap) {
     const int cn = min(kCap, n - c0);
     __syncthreads();  // the previous chunk has been consumed
@@ -124,7 +143,7 @@ __global__ void __launch_bounds__(kRows * 32, 32 / kRows) spread_kernel(const fl
       for (int s = warp; s < cn; s += kWarps) {
         const int slot = slot_of(c0 + s);
         const bool use = live && (!BATCH || !it.uz || z_reaches(slot));
-        cp_async8(&sm.p[s][lane], use ? P + (size_t)slot * F + f0 + lane : P, use);
+        copy_slice<CPL>(&sm.p[s][lane * CPL], use ? P + (size_t)slot * F + fl : P, use);
       }
     for (int s = threadIdx.x; s < cn; s += kWarps * 32) {
       const int slot = slot_of(c0 + s);
@@ -154,7 +173,8 @@ __global__ void __launch_bounds__(kRows * 32, 32 / kRows) spread_kernel(const fl
     }
     if (sorted_l) {  // the phasor rows are found through the sample indices just stored
       __syncthreads();
-      for (int s = warp; s < cn; s += kWarps) cp_async8(&sm.p[s][lane], live ? P + (size_t)sm.l[s] * F + f0 + lane : P, live);
+      for (int s = warp; s < cn; s += kWarps)
+        copy_slice<CPL>(&sm.p[s][lane * CPL], live ? P + (size_t)sm.l[s] * F + fl : P, live);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -162,8 +182,20 @@ __global__ void __launch_bounds__(kRows * 32, 32 / kRows) spread_kernel(const fl
     const int c1 = c0 + cn;
     auto visit = [&](int s, int2 og) {
       const float wyv = sm.wy[s][warp - og.y];  // the warp's row is footprint row warp - oy (0 .. w-1)
-      const float2 pv = sm.p[s][lane];
-      const float2 re = make_float2(pv.x * wyv, pv.x * wyv), im = make_float2(pv.y * wyv, pv.y * wyv);
+      float2 pv[CPL];
+      if constexpr (CPL == 1) {
+        pv[0] = sm.p[s][lane];
+      } else {
+        const float4 t = *reinterpret_cast<const float4*>(&sm.p[s][lane * 2]);
+        pv[0] = make_float2(t.x, t.y);
+        pv[1] = make_float2(t.z, t.w);
+      }
+      float2 re[CPL], im[CPL];
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        re[c] = make_float2(pv[c].x * wyv, pv[c].x * wyv);
+        im[c] = make_float2(pv[c].y * wyv, pv[c].y * wyv);
+      }
       const float4* row = reinterpret_cast<const float4*>(&sm.wx[s][kRowPad]);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -171,10 +203,13 @@ __global__ void __launch_bounds__(kRows * 32, 32 / kRows) spread_kernel(const fl
 #pragma unroll
           for (int q = 2 * h; q < 2 * h + 2; ++q) {
             const float4 wq = row[q];
-            acc_re[2 * q] = pfma(re, make_float2(wq.x, wq.y), acc_re[2 * q]);
-            acc_im[2 * q] = pfma(im, make_float2(wq.x, wq.y), acc_im[2 * q]);
-            acc_re[2 * q + 1] = pfma(re, make_float2(wq.z, wq.w), acc_re[2 * q + 1]);
-            acc_im[2 * q + 1] = pfma(im, make_float2(wq.z, wq.w), acc_im[2 * q + 1]);
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) {
+              acc_re[2 * q][c] = pfma(re[c], make_float2(wq.x, wq.y), acc_re[2 * q][c]);
+              acc_im[2 * q][c] = pfma(im[c], make_float2(wq.x, wq.y), acc_im[2 * q][c]);
+              acc_re[2 * q + 1][c] = pfma(re[c], make_float2(wq.z, wq.w), acc_re[2 * q + 1][c]);
+              acc_im[2 * q + 1][c] = pfma(im[c], make_float2(wq.z, wq.w), acc_im[2 * q + 1][c]);
+            }
           }
         }
       }
@@ -187,36 +222,54 @@ __global__ void __launch_bounds__(kRows * 32, 32 / kRows) spread_kernel(const fl
     }
   }
   if (live) {
-    float2* dst = fine + ((size_t)y * W + col0) * F + f0 + lane;
+    float2* dst = fine + ((size_t)y * W + col0) * F + fl;
 #pragma unroll
     for (int j = 0; j < kPairs; ++j) {
-      dst[(size_t)(2 * j) * F] = make_float2(acc_re[j].x, acc_im[j].x);
-      dst[(size_t)(2 * j + 1) * F] = make_float2(acc_re[j].y, acc_im[j].y);
+      if constexpr (CPL == 1) {
+        dst[(size_t)(2 * j) * F] = make_float2(acc_re[j][0].x, acc_im[j][0].x);
+        dst[(size_t)(2 * j + 1) * F] = make_float2(acc_re[j][0].y, acc_im[j][0].y);
+      } else {
+        *reinterpret_cast<float4*>(dst + (size_t)(2 * j) * F) =
+            make_float4(acc_re[j][0].x, acc_im[j][0].x, acc_re[j][1].x, acc_im[j][1].x);
+        *reinterpret_cast<float4*>(dst + (size_t)(2 * j + 1) * F) =
+            make_float4(acc_re[j][0].y, acc_im[j][0].y, acc_re[j][1].y, acc_im[j][1].y);
+      }
     }
   }
 }
 
-template <int KW, int kRows>
-cudaError_t launch_kw(const float2* P, int F, const int* bin_start, const int* sorted_l, const int2* i0,
-                      const float* wts, int tiles, int W, float2* fine, const SpreadItems& it, cudaStream_t s) {
-  const size_t smem = sizeof(SpreadSmem);
+template <int KW, int kRows, int CPL>
+cudaError_t launch_cpl(const float2* P, int F, const int* bin_start, const int* sorted_l, const int2* i0,
+                       const float* wts, int tiles, int W, float2* fine, const SpreadItems& it, cudaStream_t s) {
+  const size_t smem = sizeof(SpreadSmem<CPL>);
   static bool configured = false;
   if (!configured) {
-    cudaError_t e =
-        cudaFuncSetAttribute(spread_kernel<KW, kRows, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(spread_kernel<KW, kRows, false, CPL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(spread_kernel<KW, kRows, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaFuncSetAttribute(spread_kernel<KW, kRows, true, CPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  dim3 grid((W / kRows) * tiles, (F + kCh - 1) / kCh, it.n);
+  dim3 grid((W / kRows) * tiles, (F + 32 * CPL - 1) / (32 * CPL), it.n);
   if (it.n > 1)
-    spread_kernel<KW, kRows, true><<<grid, kRows * 32, smem, s>>>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine,
-                                                                  it);
+    spread_kernel<KW, kRows, true, CPL><<<grid, kRows * 32, smem, s>>>(P, F, bin_start, sorted_l, i0, wts, tiles, W,
+                                                                       fine, it);
   else
-    spread_kernel<KW, kRows, false><<<grid, kRows * 32, smem, s>>>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine,
-                                                                   it);
+    spread_kernel<KW, kRows, false, CPL><<<grid, kRows * 32, smem, s>>>(P, F, bin_start, sorted_l, i0, wts, tiles, W,
+                                                                        fine, it);
   return cudaGetLastError();
+}
+
+// Two channels per lane where the channels come in whole pairs and fill at least one 64-channel group
+// (at 65,536 samples, F = 128: 0.130 vs 0.146 ms for one channel per lane).
+template <int KW, int kRows>
+cudaError_t launch_kw(const float2* P, int F, const int* bin_start, const int* sorted_l, const int2* i0,
+                      const float* wts, int tiles, int W, float2* fine, const SpreadItems& it, cudaStream_t s) {
+  if (F % 2 == 0 && F >= 64)
+    return launch_cpl<KW, kRows, 2>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, it, s);
+  return launch_cpl<KW, kRows, 1>(P, F, bin_start, sorted_l, i0, wts, tiles, W, fine, it, s);
 }
 
 template <int KW>
