@@ -20,14 +20,19 @@
 //   0-3  epilogue: tcgen05.ld of the 128 x 2F accumulator (one row per thread), fp32 stores
 //        (row l to row row_slot[l] when a slot order is given);
 //        two accumulators in tensor memory, so a tile's epilogue overlaps the next tile's MMAs
-//   4-11 H producers: global loads six K-blocks ahead (~96 KB per SM in flight), fp16
-//        head/tail split, stores into the 64-byte-swizzled K-major operand layout
+//   4-11 H producers: each K-block's 128 x 32 values of H (plain launch: from a ring of TMA
+//        boxes; gather and batch launches: global loads six K-blocks ahead, ~96 KB per SM in
+//        flight), fp16 head/tail split, stores into the 64-byte-swizzled K-major operand layout
 //   12   B producer (one thread): TMA tiled copies of the 32 x 2F head and tail blocks
 //   13   MMA issuer (one thread): 2 k-steps of 16 per K-block, tcgen05.commit to the
 //        stage's "empty" barrier and, after the tile's last K-block, to the accumulator's
 //        "full" barrier
-// Four stages (K-blocks of 32) hold A_hi, A_lo (128 x 32 fp16 each) and B_hi, B_lo (2F x 32
-// fp16 each), so the next twiddle copies start three K-blocks before they are needed.
+//   14   H copier (plain launch, one thread): TMA tiled copies of H's 128 x 32 boxes (128-byte
+//        swizzle, rows past L read as zero) into a ring of 5 to 8 slots
+// Stages (K-blocks of 32; three in the plain launch, four otherwise) hold A_hi, A_lo (128 x 32
+// fp16 each) and B_hi, B_lo (2F x 32 fp16 each), so the next twiddle copies start two or three
+// K-blocks before they are needed.  In the plain launch the ring keeps 80 to 128 KB of H in flight
+// per SM (at 65,536 x 1,024 samples: 0.110 ms against 0.123 ms for the load-based producers).
 // Every mbarrier wait is bounded: on time-out the waiting role sets an abort flag (and
 // status bit 4), every role stops issuing work, copies and MMAs in flight are drained,
 // and tensor memory is released before the CTA exits.
@@ -44,23 +49,36 @@ namespace {
 
 constexpr int kBM = 128, kBK = 32, kUStages = 4;
 constexpr int kEpiWarps = 4, kCvtWarps = 8;
-constexpr int kProducerWarp = kEpiWarps + kCvtWarps, kMmaWarp = kProducerWarp + 1;
-constexpr int kUThreads = (kMmaWarp + 1) * 32;
+constexpr int kProducerWarp = kEpiWarps + kCvtWarps, kMmaWarp = kProducerWarp + 1, kHWarp = kMmaWarp + 1;
+constexpr int kUThreads = (kHWarp + 1) * 32;
+constexpr int kRawBox = kBM * kBK * 4;  // one box of H: 128 rows x 32 fp32 (16 KB)
+constexpr int kRawMax = 8;
+constexpr size_t kSmemMax = 232448;     // dynamic shared memory of one CTA
 constexpr long long kUSpin = 1LL << 22;
 
-template <int N2>
+template <int N2, int MODE>
 struct UShape {
   static constexpr int kA = kBM * 64;  // one A tile: 128 rows x 32 fp16 (64-byte rows)
   static constexpr int kB = N2 * 64;   // one B tile: N2 rows x 32 fp16
   static constexpr int kStage = 2 * kA + 2 * kB;
   static constexpr int kAcc = N2 < 32 ? 32 : N2;  // tensor-memory columns per accumulator
-  // the stages, 1 KB of alignment slack and the control block: for N2 = 256 this stays within the
-  // 196 KB shared-memory carveout (a larger carveout leaves too little L1 for the histogram loads)
-  static constexpr size_t kSmem = 1024 + (size_t)kUStages * kStage + 1536;
+  static constexpr bool kTma = MODE == 0;  // H by TMA boxes (plain launch)
+  static constexpr int kNS = kTma ? 3 : kUStages;
+  // 1 KB of alignment slack, the stages, the H ring (plain launch) and the control block.  Without
+  // the ring, for N2 = 256 this stays within the 196 KB shared-memory carveout (a larger carveout
+  // leaves too little L1 for the histogram loads); with it, as many 16 KB slots as fit (up to 8).
+  static constexpr size_t kBase = 1024 + (size_t)kNS * kStage;
+  static constexpr int kNR =
+      kTma ? ((kSmemMax - 1536 - kBase) / kRawBox < kRawMax ? (int)((kSmemMax - 1536 - kBase) / kRawBox) : kRawMax)
+           : 0;
+  static constexpr size_t kSmem = kBase + (size_t)kNR * kRawBox + 1536;
+  static_assert(!kTma || kNR >= 4, "the H ring needs at least four slots");
+  static_assert(kSmem <= kSmemMax, "shared memory of one CTA exceeded");
 };
 
 struct Ctl {  // control block after the stages (at most the 1536 bytes the shape reserves)
   unsigned long long full_a[kUStages], full_b[kUStages], empty[kUStages];
+  unsigned long long raw_full[kRawMax], raw_empty[kRawMax];  // H ring (plain launch)
   unsigned long long acc_full[2], acc_empty[2], drain;
   unsigned tmem;
   int abort;
@@ -189,13 +207,16 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
                                                                      const int* __restrict__ row_slot,
                                                                      const float* __restrict__ wcol,
                                                                      const TemporalFix fix,
-                                                                     const __grid_constant__ UItems<MODE> ui) {
+                                                                     const __grid_constant__ UItems<MODE> ui,
+                                                                     const __grid_constant__ CUtensorMap tm_h) {
   constexpr bool GATHER = MODE == 1, BATCH = MODE == 2;
-  using S = UShape<N2>;
+  using S = UShape<N2, MODE>;
+  constexpr int NS = S::kNS;
   extern __shared__ unsigned char raw[];
   const uint32_t raw_addr = sa(raw);
   unsigned char* base = raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
-  Ctl& ctl = *reinterpret_cast<Ctl*>(base + kUStages * S::kStage);
+  unsigned char* hring = base + NS * S::kStage;  // H boxes (plain launch)
+  Ctl& ctl = *reinterpret_cast<Ctl*>(hring + S::kNR * kRawBox);
   if (GATHER) {
     if (threadIdx.x == 0) ctl.listed = temporal_fix_take(fix);
     __syncthreads();
@@ -250,10 +271,14 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
   };
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kUStages; ++s) {
+    for (int s = 0; s < NS; ++s) {
       bar_init(&ctl.full_a[s], kCvtWarps);
       bar_init(&ctl.full_b[s], 1);
       bar_init(&ctl.empty[s], 1);
+    }
+    for (int s = 0; s < S::kNR; ++s) {
+      bar_init(&ctl.raw_full[s], 1);
+      bar_init(&ctl.raw_empty[s], kCvtWarps);
     }
     for (int s = 0; s < 2; ++s) {
       bar_init(&ctl.acc_full[s], 1);
@@ -342,7 +367,7 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
       }
     };
     auto stage_one = [&](const float4* v, int it) -> bool {
-      const int st = it % kUStages, ph = (it / kUStages) & 1;
+      const int st = it % NS, ph = (it / NS) & 1;
       const int j = kb_shift >= 0 ? it >> kb_shift : it / nkb, kb = it - j * nkb;
       const int t = (int)blockIdx.x + j * (int)gridDim.x;
       item_of(t, ssrc);
@@ -409,6 +434,23 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
       if (!stage_one(v, it)) return false;
       return it + 1 >= my_iters || stage_one(v + 4, it + 1);
     };
+    if constexpr (S::kTma) {  // this thread's two rows' 32 bytes of each K-block's box
+      for (int it = 0; it < my_iters; ++it) {
+        const int rs = it % S::kNR;
+        if (!__all_sync(0xffffffffu, bar_wait(&ctl.raw_full[rs], (it / S::kNR) & 1, abort))) break;
+        const unsigned char* box = hring + rs * kRawBox;
+        float4 v[4];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {  // row r: 128 bytes whose 16-byte chunks are XOR-permuted by r mod 8
+          const int r = r0 + 64 * q;
+          v[2 * q] = *reinterpret_cast<const float4*>(box + r * 128 + (((2 * ch) ^ (r & 7)) << 4));
+          v[2 * q + 1] = *reinterpret_cast<const float4*>(box + r * 128 + (((2 * ch + 1) ^ (r & 7)) << 4));
+        }
+        __syncwarp();
+        if (lane == 0) bar_arrive(&ctl.raw_empty[rs]);
+        if (!stage_one(v, it)) break;
+      }
+    } else {
     // three register sets in rotation: six K-blocks (about 96 KB per SM) in flight
     const int npairs = (my_iters + 1) / 2;
     float4 va[8], vb[8], vc[8];
@@ -423,12 +465,13 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
       if (pr + 2 >= npairs || !stage(vc, pr + 2)) break;
       load(vc, pr + 5);
     }
+    }
   } else if (warp == kProducerWarp) {
     // ---------------------------------------------------------------- B producer
     if (lane == 0) {
       int issued = 0;
       for (int it = 0; it < my_iters; ++it) {
-        const int kb = it % nkb, st = it % kUStages, ph = (it / kUStages) & 1;
+        const int kb = it % nkb, st = it % NS, ph = (it / NS) & 1;
         if (!bar_wait(&ctl.empty[st], ph ^ 1, abort)) break;
         bar_expect_tx(&ctl.full_b[st], (unsigned)(2 * S::kB));
         tma_2d(b_hi(st), &tm_hi, kb * kBK, 0, &ctl.full_b[st]);
@@ -436,9 +479,29 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
         issued = it + 1;
       }
       // the last copies have landed before the CTA can exit (already true unless a role aborted)
-      for (int it = max(0, issued - kUStages); it < issued; ++it) {
+      for (int it = max(0, issued - NS); it < issued; ++it) {
         for (long long i = 0; i < kUSpin; ++i)
-          if (bar_try(&ctl.full_b[it % kUStages], (it / kUStages) & 1)) break;
+          if (bar_try(&ctl.full_b[it % NS], (it / NS) & 1)) break;
+      }
+    }
+  } else if (warp == kHWarp) {
+    // ---------------------------------------------------------------- H copier (plain launch)
+    if constexpr (S::kTma) {
+      if (lane == 0) {
+      int issued = 0;
+      for (int it = 0; it < my_iters; ++it) {
+        const int rs = it % S::kNR;
+        if (!bar_wait(&ctl.raw_empty[rs], ((it / S::kNR) & 1) ^ 1, abort)) break;
+        const int j = kb_shift >= 0 ? it >> kb_shift : it / nkb, kb = it - j * nkb;
+        const int t = (int)blockIdx.x + j * (int)gridDim.x;
+        bar_expect_tx(&ctl.raw_full[rs], (unsigned)kRawBox);
+        tma_2d(hring + rs * kRawBox, &tm_h, kb * kBK, t * kBM, &ctl.raw_full[rs]);
+        issued = it + 1;
+      }
+      // the last boxes have landed before the CTA can exit (already true unless a role aborted)
+      for (int it = max(0, issued - S::kNR); it < issued; ++it)
+        for (long long i = 0; i < kUSpin; ++i)
+          if (bar_try(&ctl.raw_full[it % S::kNR], (it / S::kNR) & 1)) break;
       }
     }
   } else {
@@ -453,7 +516,7 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
         fence_after_sync();
         const uint32_t d = tmem + (uint32_t)(ab * S::kAcc);
         for (int kb = 0; kb < nkb; ++kb, ++it) {
-          const int st = it % kUStages, ph = (it / kUStages) & 1;
+          const int st = it % NS, ph = (it / NS) & 1;
           if (!bar_wait(&ctl.full_b[st], ph, abort) || !bar_wait(&ctl.full_a[st], ph, abort)) {
             ok = false;
             break;
@@ -528,15 +591,29 @@ cudaError_t configure_n() {
   static bool configured = false;
   if (configured) return cudaSuccess;
   cudaError_t e = cudaFuncSetAttribute(temporal_umma_kernel<N2, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)UShape<N2>::kSmem);
+                                       (int)UShape<N2, MODE>::kSmem);
   if (e == cudaSuccess) configured = true;
   return e;
+}
+
+// H [L][T] fp32 as 32 x 128 boxes in the 128-byte swizzle (rows past L read as zero).
+bool encode_h(CUtensorMap* m, const float* h, int L, int T) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)T, (cuuint64_t)L};
+  const cuuint64_t strides[1] = {(cuuint64_t)T * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(h), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <int N2>
 cudaError_t launch_n(const TemporalMaps& m, const float* h, const float* wcol, float* C, int L, int T,
                      const TemporalFix& fix, int* status, cudaStream_t s, const int* row_slot) {
-  using S = UShape<N2>;
+  using S0 = UShape<N2, 0>;
+  using S1 = UShape<N2, 1>;
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;
@@ -550,15 +627,18 @@ cudaError_t launch_n(const TemporalMaps& m, const float* h, const float* wcol, f
   // the fewest CTAs with the same most tiles per CTA (the critical path): the SMs left over run the
   // work queued beside the transform (the relay-sample sort of a reconstruction)
   const int per_cta = (ntiles + sms - 1) / sms, grid = (ntiles + per_cta - 1) / per_cta;
-  temporal_umma_kernel<N2, 0><<<grid, kUThreads, S::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status, row_slot, wcol, fix,
-                                                                UItems<0>{});
+  CUtensorMap tm_h;
+  if (!encode_h(&tm_h, h, L, T)) return cudaErrorInvalidValue;
+  temporal_umma_kernel<N2, 0><<<grid, kUThreads, S0::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status, row_slot, wcol, fix,
+                                                                 UItems<0>{}, tm_h);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // listed rows: at most min(L, cap); CTAs beyond the listed tiles return at once
   const int gtiles = (std::min(L, fix.cap) + kBM - 1) / kBM;
   if (gtiles <= 0) return cudaSuccess;
-  temporal_umma_kernel<N2, 1><<<std::min(gtiles, sms), kUThreads, S::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status,
-                                                                                 row_slot, wcol, fix, UItems<1>{});
+  temporal_umma_kernel<N2, 1><<<std::min(gtiles, sms), kUThreads, S1::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status,
+                                                                                  row_slot, wcol, fix, UItems<1>{},
+                                                                                  tm_h);
   return cudaGetLastError();
 }
 
@@ -567,7 +647,7 @@ cudaError_t launch_n(const TemporalMaps& m, const float* h, const float* wcol, f
 template <int N2>
 cudaError_t launch_batch_n(const TemporalMaps& m, const TemporalBatch& bt, const float* wcol, int T,
                            const TemporalFix& fix, int* status, cudaStream_t s) {
-  using S = UShape<N2>;
+  using S = UShape<N2, 2>;
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;
@@ -581,7 +661,8 @@ cudaError_t launch_batch_n(const TemporalMaps& m, const TemporalBatch& bt, const
   UItems<2> ui;
   ui.bt = bt;
   temporal_umma_kernel<N2, 2><<<std::min(ntiles, sms), kUThreads, S::kSmem, s>>>(nullptr, nullptr, 0, T, m.hi, m.lo,
-                                                                                 status, nullptr, wcol, fix, ui);
+                                                                                 status, nullptr, wcol, fix, ui,
+                                                                                 CUtensorMap{});
   return cudaGetLastError();
 }
 
