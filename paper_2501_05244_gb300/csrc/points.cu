@@ -89,11 +89,13 @@ __global__ void points_prepare(const PointsArgs a, const Src src, const Strides 
 }
 
 // Exclusive scan of the bin counts in one CTA: bin_start[b] = first sorted slot of bin b.
-// The counts are staged in shared memory with coalesced loads (kScanChunk at a time), each
-// thread scans a contiguous run of `per` counts (runs padded by one word, so the threads of a
-// warp hit distinct banks), and the runs' totals are scanned with warp shuffles.  256 threads
-// and 17 KB: the CTA fits beside a resident tcgen05 temporal CTA.
-constexpr int kScanThreads = 256, kScanChunk = 4096;
+// The counts are staged in shared memory with coalesced loads (kScanChunk at a time, all of a
+// chunk's loads in flight at once), each thread scans a contiguous run of `per` counts (runs
+// padded by one word, so the threads of a warp hit distinct banks), and the runs' totals are
+// scanned with warp shuffles.  1024 threads and a 36,864-count chunk (148 KB): the 34,848 bins of
+// a 528-cell window in one pass (nine 4,096-count passes took 30 us, each waiting on its loads).
+constexpr int kScanThreads = 1024, kScanChunk = 36864;
+constexpr size_t kScanSmem = sizeof(int) * (size_t)kScanThreads * (kScanChunk / kScanThreads + 1);
 static_assert(kScanThreads % 32 == 0 && kScanThreads <= 1024 && kScanChunk % kScanThreads == 0, "scan shape");
 // One CTA per item (blockIdx.x).
 template <class Src>
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(kScanThreads) points_scan(const int* __restric
   const int L = src.len(blockIdx.x);
   counts += (size_t)blockIdx.x * st.cstride;
   bin_start += (size_t)blockIdx.x * st.bstride;
-  __shared__ int buf[kScanThreads * (per + 1)];
+  extern __shared__ int buf[];  // kScanThreads runs of per + 1 words
   __shared__ int warp_sum[nw];
   __shared__ int carry;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -112,7 +114,17 @@ __global__ void __launch_bounds__(kScanThreads) points_scan(const int* __restric
   if (tid == 0) carry = 0;
   for (int c0 = 0; c0 < nbins; c0 += kScanChunk) {
     const int cn = min(kScanChunk, nbins - c0);
-    for (int i = tid; i < kScanChunk; i += kScanThreads) buf[slot(i)] = i < cn ? counts[c0 + i] : 0;
+    // every count of the chunk copied at once (past cn: zero-filled)
+#pragma unroll
+    for (int k = 0; k < per; ++k) {
+      const int i = tid + k * kScanThreads;
+      const unsigned d = (unsigned)__cvta_generic_to_shared(buf + slot(i));
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(counts + (i < cn ? c0 + i : 0)),
+                   "r"(i < cn ? 4 : 0)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     int* run_p = buf + tid * (per + 1);
     int run = 0;
@@ -247,7 +259,14 @@ cudaError_t launch_points_on(const PointsArgs& a, const Src& src, int n, int max
   const int nbins = points_bins(a.W, a.tiles);
   const dim3 grid((unsigned)std::max(1, (maxL + 255) / 256), (unsigned)n);
   points_prepare<<<grid, 256, 0, s>>>(a, src, st, i0_orig, w_orig, bin_of, frac_orig, counts);
-  points_scan<<<n, kScanThreads, 0, s>>>(counts, nbins, bin_start, src, st);
+  static bool scan_configured = false;  // per Src instantiation
+  if (!scan_configured) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(points_scan<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kScanSmem);
+    if (e != cudaSuccess) return e;
+    scan_configured = true;
+  }
+  points_scan<<<n, kScanThreads, kScanSmem, s>>>(counts, nbins, bin_start, src, st);
   points_scatter<<<grid, 256, 0, s>>>(bin_of, bin_start, src, st, counts + nbins, sorted_l, nbins, a.status);
   points_sort_bins<<<dim3((nbins + 255) / 256, (unsigned)n), 256, 0, s>>>(bin_start, nbins, sorted_l, st);
   points_gather<<<grid, 256, 0, s>>>(sorted_l, src, st, a.width, i0_orig, w_orig, frac_orig, i0_sorted, w_sorted,
