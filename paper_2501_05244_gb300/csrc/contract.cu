@@ -227,6 +227,8 @@ __global__ void __launch_bounds__(kTmaWarps * 32, 1) contract_tma_kernel(const f
   using S = TmaShape<ZPL>;
   constexpr int ZS = S::ZS;
   extern __shared__ __align__(16) unsigned char raw[];
+  pdl_wait();  // the spectra come from the kernel before
+  pdl_trigger();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* myring = reinterpret_cast<float2*>(raw) + (size_t)warp * kStages * S::kStage;
   float4* myexp = reinterpret_cast<float4*>(raw + S::kRingBytes) + warp * 8 * kRows;
@@ -394,9 +396,8 @@ cudaError_t launch_tma(const float2* U, const float2* Gc, const int2* cls_pq, in
   const long long nunit = (long long)ncls * (Z / ZS) * B;
   if (nunit >= (1LL << 31)) return cudaErrorInvalidValue;
   const int grid = (int)std::min<long long>(sms, (nunit + kTmaWarps - 1) / kTmaWarps);
-  contract_tma_kernel<ZPL, CONJ><<<grid, kTmaWarps * 32, smem, s>>>(U, Gc, cls_pq, ncls, M, F, Z, Y, u_stride,
-                                                                   y_stride, B, status);
-  return cudaGetLastError();
+  return launch_pdl(contract_tma_kernel<ZPL, CONJ>, dim3(grid), dim3(kTmaWarps * 32), smem, s, U, Gc, cls_pq, ncls, M,
+                    F, Z, Y, u_stride, y_stride, B, status);
 }
 
 template <int ZPL, bool CONJ>

@@ -774,6 +774,8 @@ __device__ __forceinline__ void store_direct32(const PanelArgs& a, const float2*
 template <int LOGN, int CP, bool INV, bool PROD = false>
 __global__ void __launch_bounds__(R32Shape<LOGN, CP>::NT, R32Shape<LOGN, CP>::NT >= 256 ? 2 : 3) panel_fft32_kernel(
     const PanelArgs a, int npanel, int in_vec2, int out_vec2, int direct) {
+  pdl_wait();  // the input comes from the kernel before (and the output may be what it read)
+  pdl_trigger();
   using S = R32Shape<LOGN, CP>;
   constexpr int n = S::n, T = S::T, NT = S::NT;
   constexpr int RS = PROD ? kProdRow : CP;  // staging row length
@@ -1037,8 +1039,7 @@ cudaError_t launch_reg(const PanelArgs& a, cudaStream_t s) {
       // bins straight from registers where a panel column is one contiguous channel (fine FFT x and y:
       // 0.154 and 0.168 ms vs 0.158 and 0.183 ms through the shared-memory copy-out)
       const int direct = !a.out_mag && a.CHI == 1 && a.CLO == CP && a.out_slo == 1 && !a.store_hi_fastest;
-      kern<<<grid, R::NT, smem32, s>>>(a, (int)npanel, in_vec2, out_vec2, direct);
-      return cudaGetLastError();
+      return launch_pdl(kern, dim3(grid), dim3(R::NT), smem32, s, a, (int)npanel, in_vec2, out_vec2, direct);
     }
   }
   if (npanel >= 4LL * sms && smem_pipe <= 220 * 1024 && (long long)nhi * nlo < (1LL << 22)) {  // persistent form

@@ -15,9 +15,34 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "../../include/nursd.h"
 
 namespace nursd {
+
+// Programmatic dependent launch: a kernel launched by launch_pdl may start, and run the part of its
+// prologue that touches no global memory written by others, while the previous kernel in the stream
+// finishes.  Such a kernel calls pdl_wait() before its first read of what that kernel wrote and
+// before its first global write; pdl_wait() returns once the previous kernel has completed and its
+// writes are visible (at once when there is no programmatic dependency).  pdl_trigger() lets the next
+// kernel launch early once every CTA of this grid has called it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Checks of data-dependent indices, compiled in with -DNURSD_CHECKED (the library's checked build):
 // a failed check sets status bit 16 (NURSD_ERR_CUDA from nursd_sync_status) and the access is

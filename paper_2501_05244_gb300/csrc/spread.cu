@@ -95,6 +95,8 @@ __global__ void __launch_bounds__(kRows * 32, (CPL == 1 ? 32 : 16) / kRows) spre
   }
   SpreadSmem<CPL>& sm = *reinterpret_cast<SpreadSmem<CPL>*>(raw);
   constexpr int kCh = 32 * CPL;
+  pdl_wait();  // the phasors, sorted samples and bins come from the kernels before
+  pdl_trigger();
   constexpr int kWarps = kRows;  // one warp per tile row
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ty = blockIdx.x / tiles, tx = blockIdx.x % tiles;
@@ -254,12 +256,10 @@ cudaError_t launch_cpl(const float2* P, int F, const int* bin_start, const int* 
   }
   dim3 grid((W / kRows) * tiles, (F + 32 * CPL - 1) / (32 * CPL), it.n);
   if (it.n > 1)
-    spread_kernel<KW, kRows, true, CPL><<<grid, kRows * 32, smem, s>>>(P, F, bin_start, sorted_l, i0, wts, tiles, W,
-                                                                       fine, it);
-  else
-    spread_kernel<KW, kRows, false, CPL><<<grid, kRows * 32, smem, s>>>(P, F, bin_start, sorted_l, i0, wts, tiles, W,
-                                                                        fine, it);
-  return cudaGetLastError();
+    return launch_pdl(spread_kernel<KW, kRows, true, CPL>, grid, dim3(kRows * 32), smem, s, P, F, bin_start, sorted_l,
+                      i0, wts, tiles, W, fine, it);
+  return launch_pdl(spread_kernel<KW, kRows, false, CPL>, grid, dim3(kRows * 32), smem, s, P, F, bin_start, sorted_l,
+                    i0, wts, tiles, W, fine, it);
 }
 
 // Two channels per lane where the channels come in whole pairs and fill at least one 64-channel group

@@ -212,6 +212,8 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
   constexpr bool GATHER = MODE == 1, BATCH = MODE == 2;
   using S = UShape<N2, MODE>;
   constexpr int NS = S::kNS;
+  pdl_wait();  // the gather launch reads the list the plain launch before it wrote
+  pdl_trigger();
   extern __shared__ unsigned char raw[];
   const uint32_t raw_addr = sa(raw);
   unsigned char* base = raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
@@ -629,13 +631,14 @@ cudaError_t launch_n(const TemporalMaps& m, const float* h, const float* wcol, f
   const int per_cta = (ntiles + sms - 1) / sms, grid = (ntiles + per_cta - 1) / per_cta;
   CUtensorMap tm_h;
   if (!encode_h(&tm_h, h, L, T)) return cudaErrorInvalidValue;
-  temporal_umma_kernel<N2, 0><<<grid, kUThreads, S0::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status, row_slot, wcol, fix,
-                                                                 UItems<0>{}, tm_h);
-  e = cudaGetLastError();
+  e = launch_pdl(temporal_umma_kernel<N2, 0>, dim3(grid), dim3(kUThreads), S0::kSmem, s, h, C, L, T, m.hi, m.lo, status,
+                 row_slot, wcol, fix, UItems<0>{}, tm_h);
   if (e != cudaSuccess) return e;
   // listed rows: at most min(L, cap); CTAs beyond the listed tiles return at once
   const int gtiles = (std::min(L, fix.cap) + kBM - 1) / kBM;
   if (gtiles <= 0) return cudaSuccess;
+  // an ordinary launch: launched early, its CTAs would hold the SMs the plain launch leaves to the
+  // work beside it (the relay-sample sort) while they wait
   temporal_umma_kernel<N2, 1><<<std::min(gtiles, sms), kUThreads, S1::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status,
                                                                                   row_slot, wcol, fix, UItems<1>{},
                                                                                   tm_h);
