@@ -997,13 +997,15 @@ def run_ours(args, rank, world, local):
 
     # ---- end to end through the public API with host buffers (pinned), copies inside the timed region.
     # Each step uploads its histograms and samples, reconstructs and downloads the volume.  The
-    # upload of step k+1 and the download of step k-1 run on a copy stream while step k
-    # computes (double-buffered device inputs and outputs); every copy is inside the region.
+    # upload of step k+1 and the download of step k-1 run on two copy streams (one per direction of
+    # the host link) while step k computes (double-buffered device inputs and outputs); every copy is
+    # inside the region.
     h_hist = torch.from_numpy(wl.hist).pin_memory()
     h_xy = torch.from_numpy(wl.xy).pin_memory()
     h_out = torch.empty(out.shape, dtype=out.dtype).pin_memory()
     ke = max(1, min(args.e2e_steps, args.steps))
     copy = torch.cuda.Stream()
+    copy_down = torch.cuda.Stream()
     dh = [d_hist, torch.empty_like(d_hist)]
     dx = [d_xy, torch.empty_like(d_xy)]
     do = [out, torch.empty_like(out)]
@@ -1033,11 +1035,12 @@ def run_ours(args, rank, world, local):
             stream.wait_event(down[k % 2])  # this output buffer's previous download has finished
             recon[k % 2]()
             done[k % 2].record(stream)
-            with torch.cuda.stream(copy):
-                copy.wait_event(done[k % 2])
+            with torch.cuda.stream(copy_down):
+                copy_down.wait_event(done[k % 2])
                 h_out.copy_(do[k % 2], non_blocking=True)
-                down[k % 2].record(copy)
+                down[k % 2].record(copy_down)
         stream.wait_stream(copy)
+        stream.wait_stream(copy_down)
 
     e2e_run(2)
     torch.cuda.synchronize()

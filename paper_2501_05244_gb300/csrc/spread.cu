@@ -27,6 +27,7 @@ namespace nursd {
 namespace {
 
 constexpr int kCap = 128;      // samples staged per chunk
+constexpr int kSeg = 8;        // cells per segment of a tile row that a visit skips when the footprint misses it
 
 // Cells of the tile row in packed pairs: for cell 2j + h, lane-wise, acc_re[j] holds the real part
 // in component h and acc_im[j] the imaginary part, so one fma.rn.f32x2 updates two cells.
@@ -39,7 +40,7 @@ struct SpreadSmem {
   float2 p[kCap][32 * CPL];  // phasor slices
   float wx[kCap][kRowLen];  // x weight of each tile cell (0 where the footprint misses it)
   float wy[kCap][8];      // y weights
-  int2 org[kCap];         // halves of the tile row reached (bit 0: cells 0..7, bit 1: 8..15), first row rel. to the tile's
+  int2 org[kCap];         // segments of the tile row reached (bit h: cells kSeg h .. kSeg h + kSeg - 1), first row rel. to the tile's
   int l[kCap];            // sample index (row of P)
 };
 
@@ -156,8 +157,10 @@ __global__ void __launch_bounds__(kRows * 32, (CPL == 1 ? 32 : 16) / kRows) spre
 #pragma unroll
       for (int t = 0; t < 2 * KW; ++t) wv[t] = __ldg(w + t);
       const int ox = o.x - col0;
-      // halves of the tile row (cells 0..7, 8..15) that the footprint ox .. ox+w-1 reaches (at least one)
-      int halves = (ox < kTile / 2 && ox + KW > 0 ? 1 : 0) | (ox < kTile && ox + KW > kTile / 2 ? 2 : 0);
+      // segments of the tile row that the footprint ox .. ox+w-1 reaches (at least one)
+      int halves = 0;
+#pragma unroll
+      for (int h = 0; h < kTile / kSeg; ++h) halves |= (ox < kSeg * (h + 1) && ox + KW > kSeg * h ? 1 : 0) << h;
       const int oy = o.y - ty * kRows;
       if (!NURSD_CHECK(oy > -KW && oy < kRows && ox > -KW && ox < kTile, it.status)) halves = 0;
       if (BATCH && it.uz && !z_reaches(slot)) halves = 0;  // a zero phasor in this slice: nothing to add
@@ -200,10 +203,10 @@ __global__ void __launch_bounds__(kRows * 32, (CPL == 1 ? 32 : 16) / kRows) spre
       }
       const float4* row = reinterpret_cast<const float4*>(&sm.wx[s][kRowPad]);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (og.x & (1 << h)) {  // warp-uniform: this half of the row is reached
+      for (int h = 0; h < kTile / kSeg; ++h) {
+        if (og.x & (1 << h)) {  // warp-uniform: this segment of the row is reached
 #pragma unroll
-          for (int q = 2 * h; q < 2 * h + 2; ++q) {
+          for (int q = h * kSeg / 4; q < (h + 1) * kSeg / 4; ++q) {
             const float4 wq = row[q];
 #pragma unroll
             for (int c = 0; c < CPL; ++c) {
