@@ -213,7 +213,9 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
   using S = UShape<N2, MODE>;
   constexpr int NS = S::kNS;
   pdl_wait();  // the gather launch reads the list the plain launch before it wrote
-  pdl_trigger();
+  // the plain launch lets its dependent (the gather launch) start only at its end, so that launch's
+  // CTAs never wait on SMs that the work beside this kernel (the relay-sample sort) runs on
+  if constexpr (MODE != 0) pdl_trigger();
   extern __shared__ unsigned char raw[];
   const uint32_t raw_addr = sa(raw);
   unsigned char* base = raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
@@ -547,6 +549,7 @@ __global__ void __launch_bounds__(kUThreads, 1) temporal_umma_kernel(const float
     }
   }
   __syncthreads();
+  if constexpr (MODE == 0) pdl_trigger();
   if (threadIdx.x == 0 && ctl.abort) atomicOr(status, 4);
   if (warp == 0) {
     fence_after_sync();
@@ -637,12 +640,8 @@ cudaError_t launch_n(const TemporalMaps& m, const float* h, const float* wcol, f
   // listed rows: at most min(L, cap); CTAs beyond the listed tiles return at once
   const int gtiles = (std::min(L, fix.cap) + kBM - 1) / kBM;
   if (gtiles <= 0) return cudaSuccess;
-  // an ordinary launch: launched early, its CTAs would hold the SMs the plain launch leaves to the
-  // work beside it (the relay-sample sort) while they wait
-  temporal_umma_kernel<N2, 1><<<std::min(gtiles, sms), kUThreads, S1::kSmem, s>>>(h, C, L, T, m.hi, m.lo, status,
-                                                                                  row_slot, wcol, fix, UItems<1>{},
-                                                                                  tm_h);
-  return cudaGetLastError();
+  return launch_pdl(temporal_umma_kernel<N2, 1>, dim3(std::min(gtiles, sms)), dim3(kUThreads), S1::kSmem, s, h, C, L,
+                    T, m.hi, m.lo, status, row_slot, wcol, fix, UItems<1>{}, tm_h);
 }
 
 // Batch mode: bt.tile_start counts 128-row tiles.  The listed rows of every item are then
