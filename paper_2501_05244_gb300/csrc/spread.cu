@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kRows * 32, (CPL == 1 ? 32 : 16) / kRows) spre
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const int s1 = min(wr[r].y, c1) - c0;
-#pragma unroll 1
+#pragma unroll 2  // two visits in flight: the next one's shared loads overlap this one's FMAs
       for (int s = max(wr[r].x, c0) - c0; s < s1; ++s) visit(s, sm.org[s]);
     }
   }
