@@ -39,6 +39,15 @@ def test_every_declared_entry_point_is_exported(lib):
     assert set(binding.EXPORTS) <= names
 
 
+def test_binding_tunables_and_stages_match_the_header():
+    # the Python names of the plan tunables and profiling stages must carry the header's numbers
+    text = open(os.path.join(ROOT, "include", "nursd.h")).read()
+    tunes = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"#define NURSD_TUNE_(\w+) (\d+)", text)}
+    assert tunes == binding.TUNABLES
+    stages = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"NURSD_STAGE_(\w+) = (\d+)", text)}
+    assert {name: i for i, name in enumerate(binding.STAGES)} == {k: v for k, v in stages.items() if k != "count"}
+
+
 def test_status_strings(lib):
     assert nursd.status_string(0) == "ok"
     assert "aperture" in nursd.status_string(binding.NURSD_ERR_POINT_OUT_OF_RANGE)
